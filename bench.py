@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Benchmark of one NQS-VMC SR step on the 8x8 Heisenberg workload.
+
+Workload (synthetic): 2D Heisenberg antiferromagnet 8x8, periodic, complex RBM alpha = 2
+(M = 128, P = 8384), Marshall phase in a_i, parameters N(0, 0.01^2) from a seed; 8192
+Markov chains with exchange moves in the Sz = 0 sector, one sample per chain per SR step
+(one sweep apart), Ns = 8192; dense S (8384^2) and the regularised solve; Euler update.
+
+One "step" is vmc_sr_step: sampling with fused E_loc and tanh(theta), energy statistics,
+<O> and F, the centred log-derivative matrix, the S contraction, the shifted solve and
+the parameter update.  Inputs (parameters, chains) are resident in HBM when the timed
+region starts; the e2e figure instead copies the parameters in from pinned host memory
+and the updated parameters and statistics out, every step, through the same C ABI.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("effective MC samples/s incl. E_loc+O_k and SR steps/s vs plain FP32 path at "
+          "|dE/N|<=1e-4")
+
+LX = LY = 8
+ALPHA = 2
+CHAINS = 8192
+SHIFT = 1e-3
+DT = 0.02
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of the same workload
+# ----------------------------------------------------------------------------------------
+def cpu_baseline(budget_s: float = 20.0):
+    import oracle
+    from paper_2108_03409_b300 import inputs
+    N, M = LX * LY, ALPHA * LX * LY
+    P = N + M + N * M
+    p = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(LX, LY))
+    cores = oracle.num_threads()
+    # (a) sampling + E_loc + O_k on c chains (one sweep, one sample each)
+    c = 64
+    s0 = inputs.random_sz0_spins(c, N, seed=99)
+    t0 = time.perf_counter()
+    s, _, _, _ = oracle.metropolis(1, LX, LY, M, p, s0, seed=1, n_sweeps=1)
+    E = oracle.eloc(1, LX, LY, 1.0, 0.0, M, p, s)
+    O = oracle.ok(N, M, p, s)
+    t_samp = (time.perf_counter() - t0) * (CHAINS / c)
+    # (b) S rows: r rows of the 8384 x 8384 matrix from c samples, scaled to Ns x P rows
+    r = 16
+    kk = np.repeat(np.arange(r), P)
+    ll = np.tile(np.arange(P), r)
+    t0 = time.perf_counter()
+    oracle.sr_entries(O, E, kk, ll, np.arange(P))
+    t_S = (time.perf_counter() - t0) * (P / r) * (CHAINS / c)
+    # (c) FP64 Cholesky at n = 1024, scaled by (P/n)^3
+    n = 1024
+    A = np.random.default_rng(0).normal(size=(n, n)) + 0j
+    A = A @ A.conj().T / n + np.eye(n)
+    F = np.ones(n, np.complex128)
+    t0 = time.perf_counter()
+    oracle.cholesky_solve(A, F)
+    t_chol = (time.perf_counter() - t0) * (P / n) ** 3
+    t_step = t_samp + t_S + t_chol
+    return {"value": 1.0 / t_step, "unit": "SR steps/s", "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 oracle, {cores} threads: Metropolis sweep + E_loc + O_k of {c} of "
+                       f"{CHAINS} chains (x{CHAINS // c}), {r} of {P} rows of S (x{P // r} rows, "
+                       f"x{CHAINS // c} samples), Cholesky solve at n={n} (x(P/n)^3); "
+                       f"estimated step {t_step:.1f} s = sample {t_samp:.1f} + S {t_S:.1f} + "
+                       f"solve {t_chol:.1f}")}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cb = cpu_baseline()
+    out = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": cb["unit"],
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "heis2d_8x8_alpha2_c8192", "N": 64, "M": 128, "P": 8384,
+                      "chains": CHAINS, "Ns": CHAINS, "shift": SHIFT},
+           "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": cb["unit"], "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2108_03409_b300 import build as vbuild
+    from paper_2108_03409_b300 import inputs, stats as vstats, vmc
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    vbuild.build()
+    prec = {"fp32": vmc.PREC_FP32, "bf16split": vmc.PREC_BF16SPLIT}[args.precision]
+    solver = {"fp64": vmc.SOLVER_CHOLESKY_FP64, "mixed": vmc.SOLVER_CHOLESKY_MIXED}[args.solver]
+    N, M = LX * LY, ALPHA * LX * LY
+    P = N + M + N * M
+    stream = torch.cuda.current_stream()
+    cfg = vmc.make_config(seed=1 + rank, n_chains=CHAINS, therm_sweeps=20, sweeps_per_sample=1,
+                          samples_per_chain=1, precision=prec, solver=solver, shift=SHIFT,
+                          cg_tol=1e-10, cg_maxit=50)
+    lat = vmc.make_lattice(vmc.MODEL_HEISENBERG, LX, LY, 1.0, 0.0, ALPHA)
+    ctx = vmc.vmc_init(cfg, [lat], stream.cuda_stream)
+    p0 = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(LX, LY))
+    vmc.vmc_set_params(ctx, 0, p0)
+    vmc.vmc_set_chains(ctx, 0, inputs.random_sz0_spins(CHAINS, N, seed=99 + rank))
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        vmc.vmc_sr_step(ctx, 0, DT)
+    barrier()
+    launches0 = vmc.vmc_kernel_launches(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st_list = []
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st_list.append(vmc.vmc_sr_step(ctx, 0, DT))
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = vmc.vmc_kernel_launches(ctx) - launches0
+    ms_t = torch.tensor([ms], device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_step = ms / args.steps
+    value = ws * args.steps / (ms / 1e3)
+
+    # e2e: parameters in from pinned host memory, parameters + statistics out, every step
+    host_p = torch.from_numpy(vmc.vmc_get_params(ctx, 0).view(np.float64).copy()).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        vmc.load().vmc_set_params(ctx, 0, host_p.data_ptr())
+        st = vmc.vmc_sr_step(ctx, 0, DT)
+        vmc.load().vmc_get_params(ctx, 0, host_p.data_ptr())
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = ws / e2e_s
+
+    # integrated autocorrelation time of E_loc at the final parameters (sampler only)
+    T = 200
+    el = torch.zeros((T * CHAINS, 2), dtype=torch.float32, device="cuda")
+    vmc.vmc_sample(ctx, 0, 0, T, None, None, el)
+    e_series = el[:, 0].reshape(T, CHAINS).double().cpu().numpy()
+    tau = vstats.integrated_autocorr_time(e_series[:, :2048])
+
+    ms_samp = statistics.mean(s.ms_sample + s.ms_grad for s in st_list)
+    ms_gram = statistics.mean(s.ms_gram for s in st_list)
+    eff = CHAINS / (ms_samp / 1e3) / (2 * tau)
+    pk, pk_kind = peaks()
+    # dominant kernel: the S contraction.  Algorithmic work of the Hermitian half of the
+    # complex Gram S = Obar^H Obar: 4 P^2 Ns real flops (8 P^2 Ns for the full matrix).
+    alg_flops = 4.0 * P * P * CHAINS
+    achieved = alg_flops / (ms_gram / 1e3) / 1e12
+    if prec == vmc.PREC_BF16SPLIT:
+        roof = {"bound": "tensor", "peak": pk.get("bf16_tflops_sustained", 1388.0),
+                "peak_kind": f"bf16 dense sustained ({pk_kind})"}
+    else:
+        fp32_peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "peak": fp32_peak,
+                "peak_kind": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock"}
+    roofline = {"bound": roof["bound"], "achieved": achieved, "peak": roof["peak"],
+                "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": None,
+                "kernel": "gram_tc" if prec == vmc.PREC_BF16SPLIT else "gram_f32",
+                "peak_source": roof["peak_kind"],
+                "algorithmic": "4*P^2*Ns flops (Hermitian half of S = Obar^H Obar)",
+                "ms_per_launch": ms_gram}
+    out = {"metric": METRIC, "value": value, "unit": "SR steps/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if prec == vmc.PREC_FP32 else "bf16x3-split/f32-accum",
+           "data": "synthetic",
+           "config": {"workload": "heis2d_8x8_alpha2_c8192", "N": N, "M": M, "P": P,
+                      "chains": CHAINS, "Ns": CHAINS, "shift": SHIFT, "dt": DT,
+                      "precision": args.precision, "solver": args.solver,
+                      "l2": "working set (S 1.1 GB, X 0.55 GB) larger than L2; no flush",
+                      "parallelism": f"replicas x{ws}"},
+           "eff_samples_per_s": {"value": eff * ws, "unit": "samples/s", "tau_int_E": tau,
+                                 "ms_sample_eloc_ok": ms_samp},
+           "phases_ms": {k: statistics.mean(getattr(s, k) for s in st_list)
+                         for k in ("ms_sample", "ms_grad", "ms_qfm", "ms_solve", "ms_update",
+                                   "ms_gram")},
+           "energy_per_site": st_list[-1].e_mean_re / N,
+           "solver_iters": st_list[-1].solver_iters, "solver_relres": st_list[-1].solver_relres,
+           "roofline": roofline,
+           "e2e": {"value": e2e_value, "unit": "SR steps/s", "h2d_bytes_per_step": P * 16,
+                   "d2h_bytes_per_step": P * 16 + 4 * 8 * 0 + 64},
+           "gpu_launches": launches,
+           "clocks": clk.summary()}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    vmc.vmc_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16split"])
+    ap.add_argument("--solver", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * vmc.h -- C ABI of libvmc, the B300 (sm_103a) implementation of one NQS variational
+ * Monte Carlo step for a complex RBM (arXiv:2108.03409, jVMC: section "Variational Monte
+ * Carlo algorithms", Algorithm 1 "Single SR or TDVP time step").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Spins are int8 in {+1,-1}; s = +1 means Z = +1 (the paper's nets take 0/1 and map
+ *    s = 2*s01 - 1, section "Variational wave functions").  A configuration is N
+ *    consecutive bytes; batches are [n][N].
+ *  - The RBM (Eq. rbm_ex) is read as theta_j = b_j + sum_i W_ji s_i,
+ *    log psi(s) = sum_i a_i s_i + sum_j log cosh theta_j, with M = alpha*N hidden units.
+ *  - Complex numbers are interleaved (re, im).  The parameter vector has
+ *    P = N + M + N*M complex entries ordered [a(N) | b(M) | W(M x N, row-major W[j*N+i])];
+ *    the log-derivatives O_k and the force F_k use the same order.
+ *  - Lattices are Lx x Ly periodic, site i = x + Lx*y.  Bond b < N joins site b to its +x
+ *    neighbour; bond b >= N (only when Ly > 1) joins site b-N to its +y neighbour.
+ *  - "dev" pointers are CUDA device memory owned by the caller (e.g. torch tensors);
+ *    "host" pointers are ordinary host memory.  The library never frees caller memory.
+ *  - All device work is enqueued on the stream given to vmc_init.  Calls that return
+ *    host results synchronise that stream; the others do not.
+ *  - Errors: every call returns a vmc_status; no call aborts, asserts or traps.  Device
+ *    errors (non-finite values, a non-positive Cholesky pivot, an expired bounded wait)
+ *    are recorded in a device status word and reported by the next synchronising call.
+ *    vmc_last_error() gives a message for the last failure on a context.
+ *  - One context per host thread.
+ */
+#ifndef VMC_H
+#define VMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VMC_OK = 0,
+  VMC_ERR_ARG = 1,      /* invalid argument (NULL pointer, size out of range, bad index)   */
+  VMC_ERR_CUDA = 2,     /* a CUDA runtime call failed                                      */
+  VMC_ERR_OOM = 3,      /* device allocation failed at vmc_init                            */
+  VMC_ERR_NUMERIC = 4,  /* NaN/Inf produced, Cholesky pivot <= 0, solver did not converge  */
+  VMC_ERR_TIMEOUT = 5,  /* a bounded device-side wait expired                              */
+  VMC_ERR_STATE = 6     /* call not valid in the context's current state                   */
+} vmc_status;
+
+enum { VMC_MODEL_TFIM = 0, VMC_MODEL_HEISENBERG = 1 };
+enum { VMC_PREC_FP32 = 0, VMC_PREC_BF16SPLIT = 1 };
+enum { VMC_SOLVER_CHOLESKY_FP64 = 0, VMC_SOLVER_CG = 1, VMC_SOLVER_CHOLESKY_MIXED = 2 };
+enum { VMC_SHIFT_MULTIPLICATIVE = 0, VMC_SHIFT_ADDITIVE = 1 };
+
+/* One lattice (Hamiltonian + RBM size).
+ *  TFIM (section "Ground state search"; 2D form in "Unitary dynamics of pure states"):
+ *      H = -J sum_<ij> Z_i Z_j - h sum_i X_i
+ *  Heisenberg with Pauli matrices: H = J sum_<ij> (X_i X_j + Y_i Y_j + Z_i Z_j). */
+typedef struct {
+  int model;      /* VMC_MODEL_*                                   */
+  int Lx, Ly;     /* Ly = 1 for a chain; N = Lx*Ly, 2 <= N <= 1024  */
+  double J, h;
+  int alpha;      /* M = alpha * N hidden units, M <= 512            */
+} vmc_lattice;
+
+/* Sampler and SR settings, shared by all lattices of a context. */
+typedef struct {
+  uint64_t seed;            /* Philox4x64-10 key word 0 (word 1 = lattice index)              */
+  int n_chains;             /* Markov chains per lattice                                       */
+  int sweep_len;            /* Metropolis steps per sweep; 0 means N                           */
+  int therm_sweeps;         /* sweeps discarded before the first SR step                       */
+  int sweeps_per_sample;    /* sweeps between two recorded samples of a chain (>= 1)           */
+  int samples_per_chain;    /* samples per chain per SR step; Ns = n_chains * samples_per_chain */
+  int precision;            /* VMC_PREC_*: arithmetic of the S = <O^H O>^c contraction         */
+  int solver;               /* VMC_SOLVER_*                                                    */
+  double shift;             /* diagonal shift nu (section "Diagonal shift")                     */
+  int shift_mode;           /* VMC_SHIFT_*: (1+nu) S_kk (the paper's) or S_kk + nu             */
+  int cg_maxit;             /* CG / refinement iteration cap                                   */
+  double cg_tol;            /* relative residual target of the iterative solvers               */
+} vmc_config;
+
+/* Statistics of one SR step (host struct filled by vmc_sr_step). */
+typedef struct {
+  double e_mean_re, e_mean_im;  /* <E_loc> over the Ns samples (Eq. Oloc_mean)              */
+  double e_var;                 /* <|E_loc - <E>|^2>                                        */
+  double e_stderr;              /* sqrt(e_var / Ns) (ignores autocorrelation)               */
+  double acceptance;            /* accepted / proposed Metropolis steps in this step        */
+  int64_t n_samples;            /* Ns                                                       */
+  int solver_iters;             /* CG or refinement iterations (0 for the direct solve)     */
+  double solver_relres;         /* ||S~ x - F|| / ||F|| of the returned update, FP64        */
+  float ms_sample, ms_grad, ms_qfm, ms_solve, ms_update;  /* phase times (CUDA events)    */
+  float ms_gram;                /* the S contraction kernel alone (CUDA events)             */
+  int64_t launches;             /* kernels launched by this step                            */
+} vmc_sr_stats;
+
+typedef struct vmc_ctx vmc_ctx;
+
+/* Create a context for n_lattices lattices (1 <= n_lattices <= 4096).  Allocates every
+ * device buffer the step needs (parameters, chains, samples, S or CG workspaces) once.
+ * Parameters start at zero and chains at all-up; set them with vmc_set_params /
+ * vmc_set_chains.  stream is a cudaStream_t (NULL = legacy default stream).
+ * Returns VMC_ERR_ARG for invalid settings, VMC_ERR_OOM if the buffers do not fit. */
+vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_lattices,
+                    void* stream, vmc_ctx** out);
+
+/* Release every resource of the context.  NULL is ignored. */
+void vmc_destroy(vmc_ctx* ctx);
+
+/* Message for the last failure on ctx (static storage owned by ctx). */
+const char* vmc_last_error(const vmc_ctx* ctx);
+
+/* Copy the FP64 master parameters of one lattice in (host [P][2]) or out.  Setting
+ * parameters also refreshes the FP32 working copies (section "Variational wave functions":
+ * get/set_parameters). */
+vmc_status vmc_set_params(vmc_ctx* ctx, int lattice, const double* params_host);
+vmc_status vmc_get_params(vmc_ctx* ctx, int lattice, double* params_host);
+
+/* Copy the chain states of one lattice in or out (host int8 [n_chains][N]).  Setting the
+ * chains rewinds the sweep counter to 0 and re-arms thermalisation. */
+vmc_status vmc_set_chains(vmc_ctx* ctx, int lattice, const int8_t* spins_host);
+vmc_status vmc_get_chains(vmc_ctx* ctx, int lattice, int8_t* spins_host);
+
+/* log psi for a batch (Eq. rbm_ex; the __call__ of the NQS class).
+ * spins: dev int8 [n][N]; logpsi: dev float [n][2].  n = 0 is a no-op. */
+vmc_status vmc_logpsi(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                      float* logpsi);
+
+/* Local energy E_loc(s) = sum_s' H_ss' psi(s')/psi(s) (Eq. Oloc) for a batch, with every
+ * psi(s')/psi(s) evaluated from the cached theta(s) of the sample (no s' is stored).
+ * spins: dev int8 [n][N]; eloc: dev float [n][2]. */
+vmc_status vmc_local_energy(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                            float* eloc);
+
+/* Metropolis-Hastings sampling of |psi|^2 (sections "Quantum expectation values" and
+ * "Sampler"): every chain of the lattice runs n_therm sweeps, then n_samples times
+ * (sweeps_per_sample sweeps, record).  Step t of sweep k of chain c draws
+ *   w = Philox4x64-10(counter = {c, k, t, 0}, key = {seed, lattice}),
+ *   site/bond = floor((w0 >> 32) * K / 2^32), u = ((w1 >> 40) + 1/2) / 2^24,
+ * proposes a single flip (TFIM, K = N) or the exchange of an anti-parallel nearest-
+ * neighbour pair (Heisenberg, K = number of bonds; a parallel pair is a rejected no-op),
+ * and accepts iff ln u < 2 Re[log psi(s') - log psi(s)].  The sweep counter k continues
+ * across calls.  Outputs (dev, any may be NULL), sample index q = r * n_chains + c:
+ *   spins_out [n_samples*n_chains][N] int8, logpsi_out and eloc_out [..][2] float. */
+vmc_status vmc_sample(vmc_ctx* ctx, int lattice, int n_therm, int n_samples,
+                      int8_t* spins_out, float* logpsi_out, float* eloc_out);
+
+/* Log-derivatives and force for a given sample set (Eq. force_vector, section "Finding
+ * low-energy states"): O_{a_i} = s_i, O_{b_j} = tanh theta_j, O_{W_ji} = tanh(theta_j) s_i;
+ * F_k = <O_k^* E_loc> - <O_k^*><E_loc> with sample means.
+ *   spins dev int8 [n][N], eloc dev float [n][2] (as from vmc_local_energy),
+ *   O_out dev float [n][P][2] or NULL, F_out dev double [P][2] or NULL,
+ *   E_stats host double [4] = (<E>.re, <E>.im, var, stderr) or NULL (synchronises).
+ * n must not exceed the context's Ns. */
+vmc_status vmc_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, const float* eloc,
+                    int64_t n, float* O_out, double* F_out, double* E_stats);
+
+/* Quantum Fisher matrix S_kl = <O_k^* O_l> - <O_k^*><O_l> (Eq. qfm) of a sample set,
+ * contracted with the given precision (VMC_PREC_*).  S_out: dev double [P][P][2], full
+ * Hermitian matrix.  n must not exceed the context's Ns. */
+vmc_status vmc_qfm(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, int precision,
+                   double* S_out);
+
+/* Regularised solve of S~ x = F (sections "Diagonal shift", Algorithm 1 line
+ * "solve_TDVP_equation") with the context's shift, shift_mode and solver:
+ *   S dev double [P][P][2] (Hermitian, read only), F dev double [P][2], x dev double [P][2].
+ * iters/relres (host, may be NULL) report the iterative part.  Returns VMC_ERR_NUMERIC if
+ * the factorisation meets a non-positive pivot or the iteration does not converge. */
+vmc_status vmc_solve(vmc_ctx* ctx, int lattice, const double* S, const double* F, double* x,
+                     int* iters, double* relres);
+
+/* One full SR step (Algorithm 1, then the Euler update theta <- theta - dt x of
+ * imaginary-time TDVP, Eq. stochastic_reconfiguration): sample Ns configurations, local
+ * energies, log-derivatives, S and F, regularised solve, parameter update.  stats (host)
+ * may be NULL.  Synchronises. */
+vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats);
+
+/* Number of kernel launches the library has issued on this context since it was created
+ * (a counter kept by the host code). */
+int64_t vmc_kernel_launches(const vmc_ctx* ctx);
+
+/* Ns of the context (n_chains * samples_per_chain) and P of a lattice. */
+int64_t vmc_num_samples(const vmc_ctx* ctx);
+int64_t vmc_num_params(const vmc_ctx* ctx, int lattice);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VMC_H */

@@ -1,0 +1,540 @@
+// api.cu -- the extern "C" entry points of libvmc (declared in include/vmc.h): context
+// life cycle, parameter and chain transfer, and the steps of Algorithm 1 (sample,
+// evaluate, gradients, local energies, S and F, solve) followed by the Euler update.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "vmc.h"
+#include "vmc_device.cuh"
+#include "vmc_internal.h"
+
+using namespace vmc;
+
+namespace {
+
+struct LatticeState {
+  vmc_lattice lat;
+  int N, M, nb;
+  int64_t P;
+  double2* params = nullptr;   // FP64 master [P]
+  float2* a = nullptr;         // FP32 copies
+  float2* b = nullptr;
+  float2* Wt = nullptr;
+  int8_t* chains = nullptr;    // [C][N]
+  uint64_t sweep = 0;          // sweeps done by every chain
+  bool thermalized = false;
+};
+
+}  // namespace
+
+struct vmc_ctx {
+  vmc_config cfg;
+  cudaStream_t st = nullptr;
+  std::vector<LatticeState> lats;
+  int64_t Ns = 0;
+  int Nmax = 0, Mmax = 0;
+  int64_t Pmax = 0;
+  bool dense = false;
+  // per-step workspaces (sized for the largest lattice)
+  int8_t* s_spins = nullptr;      // [Ns][Nmax]
+  float2* s_T = nullptr;          // [Ns][Mmax]
+  float2* s_E = nullptr;          // [Ns]
+  double* estats = nullptr;       // [4]
+  double* partial = nullptr;      // moments scratch
+  double2* meanO = nullptr;       // [Pmax]
+  double2* F = nullptr;           // [Pmax]
+  double2* x = nullptr;           // [Pmax]
+  int64_t rows_pad = 0, ld = 0;
+  float* X32 = nullptr;
+  __nv_bfloat16* Xhi = nullptr;
+  __nv_bfloat16* Xlo = nullptr;
+  double2* S = nullptr;           // [Pmax][Pmax]
+  SolveWork sw{};
+  unsigned* status = nullptr;
+  unsigned long long* n_accept = nullptr;
+  int64_t launches = 0;
+  std::vector<void*> allocs;
+  cudaEvent_t ev[8] = {};
+  std::string err;
+};
+
+namespace {
+
+vmc_status fail(vmc_ctx* c, vmc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+vmc_status cuda_fail(vmc_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, VMC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(vmc_ctx* ctx, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  ctx->allocs.push_back(v);
+  *p = static_cast<T*>(v);
+  return cudaSuccess;
+}
+
+RbmDev rbm_of(const LatticeState& L) { return RbmDev{L.N, L.M, L.a, L.b, L.Wt}; }
+
+LatDev lat_of(const LatticeState& L) {
+  return LatDev{L.lat.model, L.lat.Lx, L.lat.Ly, L.nb, (float)L.lat.J, (float)L.lat.h};
+}
+
+// read and clear the device status word (synchronises)
+vmc_status check_status(vmc_ctx* ctx, const char* where) {
+  unsigned h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->st);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, where);
+  if (h) {
+    cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->st);
+    if (h & DEV_ERR_TIMEOUT) return fail(ctx, VMC_ERR_TIMEOUT, std::string(where) + ": device wait expired");
+    if (h & DEV_ERR_BOUNDS) return fail(ctx, VMC_ERR_ARG, std::string(where) + ": device index check failed");
+    return fail(ctx, VMC_ERR_NUMERIC, std::string(where) + ": non-finite value or non-positive pivot");
+  }
+  return VMC_OK;
+}
+
+vmc_status lattice_ok(vmc_ctx* ctx, int lattice) {
+  if (!ctx) return VMC_ERR_ARG;
+  if (lattice < 0 || lattice >= (int)ctx->lats.size())
+    return fail(ctx, VMC_ERR_ARG, "lattice index out of range");
+  return VMC_OK;
+}
+
+vmc_status refresh_fp32(vmc_ctx* ctx, LatticeState& L) {
+  CK(launch_param_prep(L.params, L.N, L.M, L.a, L.b, L.Wt, ctx->st), "param_prep");
+  ++ctx->launches;
+  return VMC_OK;
+}
+
+// S of a sample set with T = tanh theta already in ctx->s_T; E may be null.
+vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const float2* E,
+                    int64_t n, int precision, double2* S_out, bool mirror) {
+  CK(launch_moments(spins, ctx->s_T, E, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
+                    E ? ctx->F : nullptr, ctx->st), "moments");
+  ctx->launches += 2;
+  const int64_t rows = 2 * L.P;
+  const int64_t rows_pad = (rows + 127) / 128 * 128;
+  const int64_t ld = (n + 63) / 64 * 64;
+  if (rows_pad > ctx->rows_pad || ld > ctx->ld) return fail(ctx, VMC_ERR_ARG, "S workspace too small");
+  const double inv_n = 1.0 / (double)n;
+  if (precision == VMC_PREC_BF16SPLIT) {
+    CK(launch_build_x(spins, ctx->s_T, ctx->meanO, n, L.N, L.M, rows_pad, ld, nullptr, ctx->Xhi,
+                      ctx->Xlo, ctx->st), "build_x");
+    ++ctx->launches;
+    cudaEventRecord(ctx->ev[6], ctx->st);
+    cudaError_t e = launch_gram_tc(ctx->Xhi, ctx->Xlo, rows_pad, ld, L.P, inv_n, S_out, mirror,
+                                   ctx->status, ctx->st);
+    cudaEventRecord(ctx->ev[7], ctx->st);
+    if (e == cudaErrorNotSupported) return fail(ctx, VMC_ERR_ARG, "tensor-core Gram: shape not supported");
+    CK(e, "gram_tc");
+    ++ctx->launches;
+  } else {
+    CK(launch_build_x(spins, ctx->s_T, ctx->meanO, n, L.N, L.M, rows_pad, ld, ctx->X32, nullptr,
+                      nullptr, ctx->st), "build_x");
+    ++ctx->launches;
+    cudaEventRecord(ctx->ev[6], ctx->st);
+    CK(launch_gram_f32(ctx->X32, rows_pad, ld, L.P, inv_n, S_out, mirror, ctx->st), "gram_f32");
+    cudaEventRecord(ctx->ev[7], ctx->st);
+    ++ctx->launches;
+  }
+  return VMC_OK;
+}
+
+vmc_status solve_core(vmc_ctx* ctx, LatticeState& L, const double2* S, const double2* F,
+                      double2* x, int* iters, double* relres) {
+  ctx->sw.P = L.P;
+  const vmc_config& c = ctx->cfg;
+  int it = 0;
+  double rel = 0.0;
+  if (c.solver == VMC_SOLVER_CHOLESKY_FP64) {
+    CK(solve_cholesky_fp64(S, F, x, c.shift, c.shift_mode, ctx->sw, ctx->status, ctx->st,
+                           &ctx->launches), "cholesky_fp64");
+    CK(residual_fp64(S, F, x, c.shift, c.shift_mode, ctx->sw, ctx->st, &rel), "residual");
+    ctx->launches += 2;
+  } else if (c.solver == VMC_SOLVER_CHOLESKY_MIXED) {
+    CK(solve_cholesky_mixed(S, F, x, c.shift, c.shift_mode, c.cg_tol, c.cg_maxit, ctx->sw,
+                            ctx->status, ctx->st, &ctx->launches, &it, &rel), "cholesky_mixed");
+  } else {
+    return fail(ctx, VMC_ERR_ARG, "solver not available for a dense S");
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  vmc_status s = check_status(ctx, "solve");
+  if (s != VMC_OK) return s;
+  if (!(rel == rel) || (c.solver == VMC_SOLVER_CHOLESKY_MIXED && !(rel <= c.cg_tol)))
+    return fail(ctx, VMC_ERR_NUMERIC, "iterative refinement did not reach the tolerance");
+  return VMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_lattices,
+                    void* stream, vmc_ctx** out) {
+  if (!cfg || !lattices || !out || n_lattices < 1 || n_lattices > 4096) return VMC_ERR_ARG;
+  *out = nullptr;
+  if (cfg->n_chains < 1 || cfg->samples_per_chain < 1 || cfg->sweeps_per_sample < 1 ||
+      cfg->therm_sweeps < 0 || cfg->sweep_len < 0)
+    return VMC_ERR_ARG;
+  if (cfg->precision != VMC_PREC_FP32 && cfg->precision != VMC_PREC_BF16SPLIT) return VMC_ERR_ARG;
+  if (cfg->solver < 0 || cfg->solver > 2 || (cfg->shift_mode != 0 && cfg->shift_mode != 1))
+    return VMC_ERR_ARG;
+  if (!(cfg->shift >= 0.0)) return VMC_ERR_ARG;
+  for (int l = 0; l < n_lattices; ++l) {
+    const vmc_lattice& L = lattices[l];
+    const int N = L.Lx * L.Ly;
+    if ((L.model != 0 && L.model != 1) || L.Lx < 1 || L.Ly < 1 || N < 2 || N > 1024 ||
+        L.alpha < 1 || L.alpha * N > 512)
+      return VMC_ERR_ARG;
+  }
+  vmc_ctx* ctx = new vmc_ctx();
+  ctx->cfg = *cfg;
+  ctx->st = static_cast<cudaStream_t>(stream);
+  ctx->Ns = (int64_t)cfg->n_chains * cfg->samples_per_chain;
+  for (int l = 0; l < n_lattices; ++l) {
+    LatticeState S;
+    S.lat = lattices[l];
+    S.N = S.lat.Lx * S.lat.Ly;
+    S.M = S.lat.alpha * S.N;
+    S.nb = num_bonds(S.lat.Lx, S.lat.Ly);
+    S.P = (int64_t)S.N + S.M + (int64_t)S.N * S.M;
+    ctx->Nmax = std::max(ctx->Nmax, S.N);
+    ctx->Mmax = std::max(ctx->Mmax, S.M);
+    ctx->Pmax = std::max(ctx->Pmax, S.P);
+    ctx->lats.push_back(S);
+  }
+  ctx->dense = cfg->solver != VMC_SOLVER_CG;
+  auto oom = [&](cudaError_t e) {
+    vmc_destroy(ctx);
+    (void)e;
+    cudaGetLastError();
+    return VMC_ERR_OOM;
+  };
+  cudaError_t e;
+  for (auto& L : ctx->lats) {
+    if ((e = dalloc(ctx, &L.params, L.P)) || (e = dalloc(ctx, &L.a, L.N)) ||
+        (e = dalloc(ctx, &L.b, L.M)) || (e = dalloc(ctx, &L.Wt, (size_t)L.N * L.M)) ||
+        (e = dalloc(ctx, &L.chains, (size_t)cfg->n_chains * L.N)))
+      return oom(e);
+    cudaMemset(L.params, 0, L.P * sizeof(double2));
+    std::vector<int8_t> up((size_t)cfg->n_chains * L.N, 1);
+    cudaMemcpy(L.chains, up.data(), up.size(), cudaMemcpyHostToDevice);
+    launch_param_prep(L.params, L.N, L.M, L.a, L.b, L.Wt, ctx->st);
+  }
+  const int64_t Ns = ctx->Ns;
+  if ((e = dalloc(ctx, &ctx->s_spins, (size_t)Ns * ctx->Nmax)) ||
+      (e = dalloc(ctx, &ctx->s_T, (size_t)Ns * ctx->Mmax)) || (e = dalloc(ctx, &ctx->s_E, Ns)) ||
+      (e = dalloc(ctx, &ctx->estats, 8)) ||
+      (e = dalloc(ctx, &ctx->partial, (size_t)moments_partial_doubles(Ns, ctx->Nmax, ctx->Mmax))) ||
+      (e = dalloc(ctx, &ctx->meanO, ctx->Pmax)) || (e = dalloc(ctx, &ctx->F, ctx->Pmax)) ||
+      (e = dalloc(ctx, &ctx->x, ctx->Pmax)) || (e = dalloc(ctx, &ctx->status, 1)) ||
+      (e = dalloc(ctx, &ctx->n_accept, 1)))
+    return oom(e);
+  if (ctx->dense) {
+    const int64_t P = ctx->Pmax;
+    ctx->rows_pad = (2 * P + 127) / 128 * 128;
+    ctx->ld = (Ns + 63) / 64 * 64;
+    const size_t xs = (size_t)ctx->rows_pad * ctx->ld;
+    const int64_t nblk = (P + 63) / 64;
+    if ((e = dalloc(ctx, &ctx->X32, xs)) || (e = dalloc(ctx, &ctx->Xhi, xs)) ||
+        (e = dalloc(ctx, &ctx->Xlo, xs)) || (e = dalloc(ctx, &ctx->S, (size_t)P * P)) ||
+        (e = dalloc(ctx, &ctx->sw.r, P)) || (e = dalloc(ctx, &ctx->sw.c, P)) ||
+        (e = dalloc(ctx, &ctx->sw.r32, P)) || (e = dalloc(ctx, &ctx->sw.y32, P)) ||
+        (e = dalloc(ctx, &ctx->sw.c32, P)) || (e = dalloc(ctx, &ctx->sw.scal, 8)))
+      return oom(e);
+    if (cfg->solver == VMC_SOLVER_CHOLESKY_FP64) {
+      if ((e = dalloc(ctx, &ctx->sw.A64, (size_t)P * P)) ||
+          (e = dalloc(ctx, &ctx->sw.D64, (size_t)nblk * 64 * 64)))
+        return oom(e);
+    } else {
+      if ((e = dalloc(ctx, &ctx->sw.A32, (size_t)P * P)) ||
+          (e = dalloc(ctx, &ctx->sw.D32, (size_t)nblk * 64 * 64)))
+        return oom(e);
+    }
+  }
+  cudaMemset(ctx->status, 0, sizeof(unsigned));
+  for (auto& ev : ctx->ev) cudaEventCreate(&ev);
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+    vmc_destroy(ctx);
+    return VMC_ERR_CUDA;
+  }
+  ctx->launches = (int64_t)ctx->lats.size();
+  *out = ctx;
+  return VMC_OK;
+}
+
+void vmc_destroy(vmc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  for (void* p : ctx->allocs) cudaFree(p);
+  for (auto& ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete ctx;
+}
+
+const char* vmc_last_error(const vmc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t vmc_kernel_launches(const vmc_ctx* ctx) { return ctx ? ctx->launches : 0; }
+int64_t vmc_num_samples(const vmc_ctx* ctx) { return ctx ? ctx->Ns : 0; }
+int64_t vmc_num_params(const vmc_ctx* ctx, int lattice) {
+  if (!ctx || lattice < 0 || lattice >= (int)ctx->lats.size()) return 0;
+  return ctx->lats[lattice].P;
+}
+
+vmc_status vmc_set_params(vmc_ctx* ctx, int lattice, const double* params_host) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!params_host) return fail(ctx, VMC_ERR_ARG, "params_host is NULL");
+  LatticeState& L = ctx->lats[lattice];
+  CK(cudaMemcpyAsync(L.params, params_host, L.P * sizeof(double2), cudaMemcpyHostToDevice, ctx->st),
+     "set_params");
+  if ((s = refresh_fp32(ctx, L))) return s;
+  CK(cudaStreamSynchronize(ctx->st), "set_params");
+  return VMC_OK;
+}
+
+vmc_status vmc_get_params(vmc_ctx* ctx, int lattice, double* params_host) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!params_host) return fail(ctx, VMC_ERR_ARG, "params_host is NULL");
+  LatticeState& L = ctx->lats[lattice];
+  CK(cudaMemcpyAsync(params_host, L.params, L.P * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st),
+     "get_params");
+  CK(cudaStreamSynchronize(ctx->st), "get_params");
+  return VMC_OK;
+}
+
+vmc_status vmc_set_chains(vmc_ctx* ctx, int lattice, const int8_t* spins_host) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!spins_host) return fail(ctx, VMC_ERR_ARG, "spins_host is NULL");
+  LatticeState& L = ctx->lats[lattice];
+  const size_t bytes = (size_t)ctx->cfg.n_chains * L.N;
+  for (size_t k = 0; k < bytes; ++k)
+    if (spins_host[k] != 1 && spins_host[k] != -1) return fail(ctx, VMC_ERR_ARG, "spins must be +1 or -1");
+  CK(cudaMemcpyAsync(L.chains, spins_host, bytes, cudaMemcpyHostToDevice, ctx->st), "set_chains");
+  CK(cudaStreamSynchronize(ctx->st), "set_chains");
+  L.sweep = 0;
+  L.thermalized = false;
+  return VMC_OK;
+}
+
+vmc_status vmc_get_chains(vmc_ctx* ctx, int lattice, int8_t* spins_host) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!spins_host) return fail(ctx, VMC_ERR_ARG, "spins_host is NULL");
+  LatticeState& L = ctx->lats[lattice];
+  CK(cudaMemcpyAsync(spins_host, L.chains, (size_t)ctx->cfg.n_chains * L.N, cudaMemcpyDeviceToHost,
+                     ctx->st), "get_chains");
+  CK(cudaStreamSynchronize(ctx->st), "get_chains");
+  return VMC_OK;
+}
+
+vmc_status vmc_logpsi(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* logpsi) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!spins || !logpsi))) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  if (n == 0) return VMC_OK;
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_logpsi(rbm_of(L), spins, n, reinterpret_cast<float2*>(logpsi), ctx->status, ctx->st),
+     "logpsi");
+  ++ctx->launches;
+  return VMC_OK;
+}
+
+vmc_status vmc_local_energy(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                            float* eloc) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!spins || !eloc))) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  if (n == 0) return VMC_OK;
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_eloc(rbm_of(L), lat_of(L), spins, n, reinterpret_cast<float2*>(eloc), ctx->status,
+                 ctx->st), "local_energy");
+  ++ctx->launches;
+  return VMC_OK;
+}
+
+vmc_status vmc_sample(vmc_ctx* ctx, int lattice, int n_therm, int n_samples, int8_t* spins_out,
+                      float* logpsi_out, float* eloc_out) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (n_therm < 0 || n_samples < 0) return fail(ctx, VMC_ERR_ARG, "negative sweep count");
+  LatticeState& L = ctx->lats[lattice];
+  SampleArgs A{};
+  A.rbm = rbm_of(L);
+  A.lat = lat_of(L);
+  A.chains = L.chains;
+  A.C = ctx->cfg.n_chains;
+  A.L = ctx->cfg.sweep_len > 0 ? ctx->cfg.sweep_len : L.N;
+  A.seed = ctx->cfg.seed;
+  A.stream = (uint64_t)lattice;
+  A.sweep0 = L.sweep;
+  A.n_therm = n_therm;
+  A.n_samples = n_samples;
+  A.sweeps_per_sample = ctx->cfg.sweeps_per_sample;
+  A.spins_out = spins_out;
+  A.logpsi_out = reinterpret_cast<float2*>(logpsi_out);
+  A.eloc_out = reinterpret_cast<float2*>(eloc_out);
+  A.t_out = nullptr;
+  A.n_accept = ctx->n_accept;
+  A.status = ctx->status;
+  if (n_therm + n_samples == 0) return VMC_OK;
+  CK(launch_sample(A, ctx->st), "sample");
+  ++ctx->launches;
+  L.sweep += (uint64_t)n_therm + (uint64_t)n_samples * ctx->cfg.sweeps_per_sample;
+  if (n_therm > 0) L.thermalized = true;
+  return VMC_OK;
+}
+
+vmc_status vmc_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, const float* eloc, int64_t n,
+                    float* O_out, double* F_out, double* E_stats) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 1 || n > ctx->Ns || !spins || !eloc) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  const float2* E = reinterpret_cast<const float2*>(eloc);
+  CK(launch_theta_tanh(rbm_of(L), spins, n, ctx->s_T, ctx->st), "theta_tanh");
+  CK(launch_estats(E, n, ctx->estats, ctx->status, ctx->st), "estats");
+  CK(launch_moments(spins, ctx->s_T, E, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO, ctx->F,
+                    ctx->st), "moments");
+  ctx->launches += 4;
+  if (F_out)
+    CK(cudaMemcpyAsync(F_out, ctx->F, L.P * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st), "grad");
+  if (O_out) {
+    CK(launch_ok_dense(spins, ctx->s_T, n, L.N, L.M, reinterpret_cast<float2*>(O_out), ctx->st), "ok");
+    ++ctx->launches;
+  }
+  if (E_stats) {
+    CK(cudaMemcpyAsync(E_stats, ctx->estats, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->st), "grad");
+    return check_status(ctx, "grad");
+  }
+  return VMC_OK;
+}
+
+vmc_status vmc_qfm(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, int precision,
+                   double* S_out) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 1 || n > ctx->Ns || !spins || !S_out) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  if (!ctx->dense) return fail(ctx, VMC_ERR_STATE, "context was created for the CG solver (no dense S)");
+  if (precision != VMC_PREC_FP32 && precision != VMC_PREC_BF16SPLIT) return fail(ctx, VMC_ERR_ARG, "bad precision");
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_theta_tanh(rbm_of(L), spins, n, ctx->s_T, ctx->st), "theta_tanh");
+  ++ctx->launches;
+  if ((s = qfm_core(ctx, L, spins, nullptr, n, precision, reinterpret_cast<double2*>(S_out), true)))
+    return s;
+  return check_status(ctx, "qfm");
+}
+
+vmc_status vmc_solve(vmc_ctx* ctx, int lattice, const double* S, const double* F, double* x,
+                     int* iters, double* relres) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!S || !F || !x) return fail(ctx, VMC_ERR_ARG, "NULL buffer");
+  if (!ctx->dense) return fail(ctx, VMC_ERR_STATE, "context was created for the CG solver");
+  LatticeState& L = ctx->lats[lattice];
+  return solve_core(ctx, L, reinterpret_cast<const double2*>(S), reinterpret_cast<const double2*>(F),
+                    reinterpret_cast<double2*>(x), iters, relres);
+}
+
+vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!ctx->dense) return fail(ctx, VMC_ERR_STATE, "CG SR step is not available in this build");
+  LatticeState& L = ctx->lats[lattice];
+  const vmc_config& c = ctx->cfg;
+  const int64_t Ns = ctx->Ns;
+  const int64_t launches0 = ctx->launches;
+  CK(cudaMemsetAsync(ctx->n_accept, 0, sizeof(unsigned long long), ctx->st), "sr_step");
+  CK(cudaEventRecord(ctx->ev[0], ctx->st), "sr_step");
+  // 1. sample Ns configurations; E_loc and tanh(theta) fused at every record point
+  SampleArgs A{};
+  A.rbm = rbm_of(L);
+  A.lat = lat_of(L);
+  A.chains = L.chains;
+  A.C = c.n_chains;
+  A.L = c.sweep_len > 0 ? c.sweep_len : L.N;
+  A.seed = c.seed;
+  A.stream = (uint64_t)lattice;
+  A.sweep0 = L.sweep;
+  A.n_therm = L.thermalized ? 0 : c.therm_sweeps;
+  A.n_samples = c.samples_per_chain;
+  A.sweeps_per_sample = c.sweeps_per_sample;
+  A.spins_out = ctx->s_spins;
+  A.logpsi_out = nullptr;
+  A.eloc_out = ctx->s_E;
+  A.t_out = ctx->s_T;
+  A.n_accept = ctx->n_accept;
+  A.status = ctx->status;
+  CK(launch_sample(A, ctx->st), "sample");
+  ++ctx->launches;
+  const uint64_t steps = (uint64_t)(A.n_therm + A.n_samples * A.sweeps_per_sample) * (uint64_t)A.L;
+  L.sweep += (uint64_t)A.n_therm + (uint64_t)A.n_samples * A.sweeps_per_sample;
+  L.thermalized = true;
+  CK(cudaEventRecord(ctx->ev[1], ctx->st), "sr_step");
+  // 2. energy statistics, <O>, F (the b- and W-block factors come from the sampler)
+  CK(launch_estats(ctx->s_E, Ns, ctx->estats, ctx->status, ctx->st), "estats");
+  ++ctx->launches;
+  CK(cudaEventRecord(ctx->ev[2], ctx->st), "sr_step");
+  // 3. S (moments + centred X + Gram)
+  if ((s = qfm_core(ctx, L, ctx->s_spins, ctx->s_E, Ns, c.precision, ctx->S, true))) return s;
+  CK(cudaEventRecord(ctx->ev[3], ctx->st), "sr_step");
+  // 4. solve (synchronises)
+  int iters = 0;
+  double rel = 0.0;
+  if ((s = solve_core(ctx, L, ctx->S, ctx->F, ctx->x, &iters, &rel))) return s;
+  CK(cudaEventRecord(ctx->ev[4], ctx->st), "sr_step");
+  // 5. Euler update of the FP64 master parameters, refresh the FP32 copies
+  CK(launch_update(L.params, ctx->x, L.P, dt, ctx->st), "update");
+  ++ctx->launches;
+  if ((s = refresh_fp32(ctx, L))) return s;
+  CK(cudaEventRecord(ctx->ev[5], ctx->st), "sr_step");
+  double es[4];
+  unsigned long long acc = 0;
+  CK(cudaMemcpyAsync(es, ctx->estats, sizeof(es), cudaMemcpyDeviceToHost, ctx->st), "sr_step");
+  CK(cudaMemcpyAsync(&acc, ctx->n_accept, sizeof(acc), cudaMemcpyDeviceToHost, ctx->st), "sr_step");
+  if ((s = check_status(ctx, "sr_step"))) return s;
+  if (stats) {
+    stats->e_mean_re = es[0];
+    stats->e_mean_im = es[1];
+    stats->e_var = es[2];
+    stats->e_stderr = es[3];
+    stats->n_samples = Ns;
+    stats->acceptance = steps ? (double)acc / ((double)steps * c.n_chains) : 0.0;
+    stats->solver_iters = iters;
+    stats->solver_relres = rel;
+    float t[5];
+    for (int k = 0; k < 5; ++k) cudaEventElapsedTime(&t[k], ctx->ev[k], ctx->ev[k + 1]);
+    stats->ms_sample = t[0];
+    stats->ms_grad = t[1];
+    stats->ms_qfm = t[2];
+    stats->ms_solve = t[3];
+    stats->ms_update = t[4];
+    cudaEventElapsedTime(&stats->ms_gram, ctx->ev[6], ctx->ev[7]);
+    stats->launches = ctx->launches - launches0;
+  }
+  return VMC_OK;
+}
+
+}  // extern "C"

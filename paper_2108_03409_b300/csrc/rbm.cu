@@ -1,0 +1,457 @@
+// rbm.cu -- complex-RBM kernels of the VMC step: parameter preparation, log psi, the
+// fused local energy, the Metropolis sampler with a cached theta = W s + b, and the
+// log-derivatives.  One warp owns one configuration (or one chain); hidden unit
+// j = lane + 32*k lives in register slot k of that lane.
+#include "vmc_device.cuh"
+#include "vmc_internal.h"
+
+namespace vmc {
+
+static constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------------------------------
+// a1: FP64 master parameters -> FP32 working copies.  Wt is W transposed ([N][M]) so that
+// the column W[:, i] a proposal needs is contiguous across the warp's lanes.
+// ---------------------------------------------------------------------------------------
+__global__ void k_param_prep(const double2* __restrict__ p, int N, int M, float2* __restrict__ a,
+                             float2* __restrict__ b, float2* __restrict__ Wt) {
+  const int64_t P = (int64_t)N + M + (int64_t)N * M;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double2 v = p[k];
+    float2 f = make_float2((float)v.x, (float)v.y);
+    if (k < N) a[k] = f;
+    else if (k < N + M) b[k - N] = f;
+    else {
+      int64_t q = k - N - M;
+      int j = (int)(q / N), i = (int)(q % N);
+      Wt[(int64_t)i * M + j] = f;
+    }
+  }
+}
+
+// theta_j = b_j + sum_i W_ji s_i for the warp's hidden slots, from spins in shared memory.
+template <int MPL>
+__device__ __forceinline__ void warp_theta(const RbmDev& R, const int8_t* s, int lane,
+                                           float2 (&th)[MPL]) {
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    int hj = lane + 32 * k;
+    th[k] = (hj < R.M) ? R.b[hj] : make_float2(0.f, 0.f);
+  }
+  for (int i = 0; i < R.N; ++i) {
+    const float si = (float)s[i];
+    const float2* w = R.Wt + (int64_t)i * R.M;
+#pragma unroll
+    for (int k = 0; k < MPL; ++k) {
+      int hj = lane + 32 * k;
+      if (hj < R.M) {
+        float2 v = w[hj];
+        th[k].x = fmaf(si, v.x, th[k].x);
+        th[k].y = fmaf(si, v.y, th[k].y);
+      }
+    }
+  }
+}
+
+// log psi = sum_i a_i s_i + sum_j log cosh theta_j (all lanes return the same value).
+template <int MPL>
+__device__ __forceinline__ float2 warp_logpsi(const RbmDev& R, const int8_t* s, int lane,
+                                              const float2 (&th)[MPL]) {
+  float re = 0.f, im = 0.f;
+  for (int i = lane; i < R.N; i += 32) {
+    float si = (float)s[i];
+    re = fmaf(si, R.a[i].x, re);
+    im = fmaf(si, R.a[i].y, im);
+  }
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    if (lane + 32 * k < R.M) {
+      float2 lc = logcosh_c(th[k].x, th[k].y);
+      re += lc.x;
+      im += lc.y;
+    }
+  }
+  return make_float2(warp_sum(re), warp_sum(im));
+}
+
+// sum over the warp's hidden slots of log[cosh(theta_k - d_k) / cosh(theta_k)], with
+// d_k = 2 s_i W_ki (+ 2 s_j W_kj for an exchange), as (log modulus, phase); the per-lane
+// partial product of four factors is turned into logs before the warp sum.
+template <int MPL, bool PAIR>
+__device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
+                                                 const float2 (&t)[MPL], int i, float si,
+                                                 int j) {
+  float lr = 0.f, li = 0.f;
+  float2 prod = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    int hj = lane + 32 * k;
+    if (hj < R.M) {
+      float2 wi = R.Wt[(int64_t)i * R.M + hj];
+      float dr, di;
+      if (PAIR) {
+        float2 wj = R.Wt[(int64_t)j * R.M + hj];
+        dr = 2.f * si * (wi.x - wj.x);
+        di = 2.f * si * (wi.y - wj.y);
+      } else {
+        dr = 2.f * si * wi.x;
+        di = 2.f * si * wi.y;
+      }
+      prod = cmul(prod, cosh_ratio(t[k], dr, di));
+    }
+    if ((k & 3) == 3 || k == MPL - 1) {
+      lr += 0.5f * logf(fmaf(prod.x, prod.x, prod.y * prod.y));
+      li += atan2f(prod.y, prod.x);
+      prod = make_float2(1.f, 0.f);
+    }
+  }
+  return make_float2(warp_sum(lr), warp_sum(li));
+}
+
+// E_loc(s) = sum_s' H_ss' psi(s')/psi(s) from the cached t = tanh theta(s) (Eq. Oloc).
+template <int MPL>
+__device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, int lane,
+                            const float2 (&t)[MPL]) {
+  // diagonal: sum over bonds of s_i s_j (exact small integers)
+  float zz = 0.f;
+  for (int b = lane; b < L.nb; b += 32) {
+    int i, j;
+    bond_ends(L.Lx, L.Ly, b, &i, &j);
+    zz += (float)(s[i] * s[j]);
+  }
+  zz = warp_sum(zz);
+  float2 e;
+  if (L.model == 0) {
+    e = make_float2(-L.J * zz, 0.f);
+    for (int i = 0; i < R.N; ++i) {           // -h X_i: flip site i
+      float si = (float)s[i];
+      float2 lg = warp_log_ratio<MPL, false>(R, lane, t, i, si, 0);
+      float2 ai = R.a[i];
+      float lx = lg.x - 2.f * si * ai.x, ly = lg.y - 2.f * si * ai.y;
+      float mag = expf(lx), sn, cs;
+      sincosf(ly, &sn, &cs);
+      e.x = fmaf(-L.h, mag * cs, e.x);
+      e.y = fmaf(-L.h, mag * sn, e.y);
+    }
+  } else {
+    e = make_float2(L.J * zz, 0.f);
+    for (int b = 0; b < L.nb; ++b) {          // J(XX+YY): swap an anti-parallel pair, 2J
+      int i, j;
+      bond_ends(L.Lx, L.Ly, b, &i, &j);
+      if (s[i] == s[j]) continue;
+      float si = (float)s[i];
+      float2 lg = warp_log_ratio<MPL, true>(R, lane, t, i, si, j);
+      float2 ai = R.a[i], aj = R.a[j];
+      float lx = lg.x - 2.f * si * (ai.x - aj.x), ly = lg.y - 2.f * si * (ai.y - aj.y);
+      float mag = expf(lx), sn, cs;
+      sincosf(ly, &sn, &cs);
+      e.x = fmaf(2.f * L.J, mag * cs, e.x);
+      e.y = fmaf(2.f * L.J, mag * sn, e.y);
+    }
+  }
+  return e;
+}
+
+// ---------------------------------------------------------------------------------------
+// batch kernels: one warp per configuration
+// ---------------------------------------------------------------------------------------
+template <int MPL>
+__global__ void __launch_bounds__(128) k_logpsi(RbmDev R, const int8_t* __restrict__ spins,
+                                                int64_t n, float2* __restrict__ out,
+                                                unsigned* status) {
+  extern __shared__ int8_t sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (q >= n) return;
+  const int Npad = (R.N + 15) & ~15;
+  int8_t* s = sm + wib * Npad;
+  for (int i = lane; i < R.N; i += 32) s[i] = spins[q * R.N + i];
+  __syncwarp();
+  float2 th[MPL];
+  warp_theta<MPL>(R, s, lane, th);
+  float2 lp = warp_logpsi<MPL>(R, s, lane, th);
+  if (lane == 0) {
+    out[q] = lp;
+    if (!isfinite(lp.x) || !isfinite(lp.y)) flag_error(status, DEV_ERR_NUMERIC);
+  }
+}
+
+template <int MPL>
+__global__ void __launch_bounds__(128) k_eloc(RbmDev R, LatDev L,
+                                              const int8_t* __restrict__ spins, int64_t n,
+                                              float2* __restrict__ out, unsigned* status) {
+  extern __shared__ int8_t sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (q >= n) return;
+  const int Npad = (R.N + 15) & ~15;
+  int8_t* s = sm + wib * Npad;
+  for (int i = lane; i < R.N; i += 32) s[i] = spins[q * R.N + i];
+  __syncwarp();
+  float2 th[MPL], t[MPL];
+  warp_theta<MPL>(R, s, lane, th);
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) t[k] = tanh_c(th[k].x, th[k].y);
+  float2 e = warp_eloc<MPL>(R, L, s, lane, t);
+  if (lane == 0) {
+    out[q] = e;
+    if (!isfinite(e.x) || !isfinite(e.y)) flag_error(status, DEV_ERR_NUMERIC);
+  }
+}
+
+// tanh theta for a batch: T[n][M] (the b- and W-block log-derivative factors)
+template <int MPL>
+__global__ void __launch_bounds__(128) k_theta_tanh(RbmDev R, const int8_t* __restrict__ spins,
+                                                    int64_t n, float2* __restrict__ T) {
+  extern __shared__ int8_t sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  if (q >= n) return;
+  const int Npad = (R.N + 15) & ~15;
+  int8_t* s = sm + wib * Npad;
+  for (int i = lane; i < R.N; i += 32) s[i] = spins[q * R.N + i];
+  __syncwarp();
+  float2 th[MPL];
+  warp_theta<MPL>(R, s, lane, th);
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    int hj = lane + 32 * k;
+    if (hj < R.M) T[q * R.M + hj] = tanh_c(th[k].x, th[k].y);
+  }
+}
+
+// dense log-derivatives O[n][P] = [s | t | t (x) s] (FP32 complex)
+__global__ void k_ok_dense(const int8_t* __restrict__ spins, const float2* __restrict__ T,
+                           int64_t n, int N, int M, float2* __restrict__ O) {
+  const int64_t P = (int64_t)N + M + (int64_t)N * M;
+  const int64_t total = n * P;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t q = e / P, k = e % P;
+    float2 v;
+    if (k < N) v = make_float2((float)spins[q * N + k], 0.f);
+    else if (k < N + M) v = T[q * M + (k - N)];
+    else {
+      int64_t r = k - N - M;
+      int j = (int)(r / N), i = (int)(r % N);
+      float si = (float)spins[q * N + i];
+      float2 t = T[q * M + j];
+      v = make_float2(si * t.x, si * t.y);
+    }
+    O[e] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// a3/a4 + a6 (+ the t factors of a7): Metropolis sweeps with theta and t = tanh theta
+// cached in registers.  One warp per chain.  For a proposal s -> s' that changes theta by
+// -d_k (d_k = 2 s_i W_ki, plus 2 s_j W_kj for an exchange),
+//   psi(s')/psi(s) = exp(a-term) * prod_k [cosh d_k - t_k sinh d_k],
+// and the acceptance needs only its modulus squared.  Random numbers for 32 consecutive
+// steps are drawn in parallel (lane q draws step t0+q) and broadcast.  At every record
+// point theta is recomputed from the spins (no drift), and the sample's spins, log psi,
+// E_loc (fused, from the cached t) and t are written.
+// ---------------------------------------------------------------------------------------
+template <int MPL, bool HEIS>
+__global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
+  extern __shared__ int8_t sm[];
+  const RbmDev& R = A.rbm;
+  const LatDev& L = A.lat;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int chain = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (chain >= A.C) return;
+  const int N = R.N, M = R.M;
+  const int Npad = (N + 15) & ~15;
+  int8_t* s = sm + wib * Npad;
+  for (int i = lane; i < N; i += 32) s[i] = A.chains[(int64_t)chain * N + i];
+  __syncwarp();
+
+  float2 th[MPL], t[MPL];
+  warp_theta<MPL>(R, s, lane, th);
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) t[k] = tanh_c(th[k].x, th[k].y);
+
+  const uint32_t K = HEIS ? (uint32_t)L.nb : (uint32_t)N;
+  const int total = A.n_therm + A.n_samples * A.sweeps_per_sample;
+  unsigned long long n_acc = 0;
+  bool bad = false;
+
+  for (int sw = 0; sw < total; ++sw) {
+    const uint64_t sweep_id = A.sweep0 + (uint64_t)sw;
+    for (int t0 = 0; t0 < A.L; t0 += 32) {
+      uint32_t my_idx = 0;
+      float my_logu = 0.f;
+      if (t0 + lane < A.L) {
+        u64x4 w = philox4x64_10((uint64_t)chain, sweep_id, (uint64_t)(t0 + lane), 0ull,
+                                A.seed, A.stream);
+        mh_draw(w, K, &my_idx, &my_logu);
+      }
+      const int nstep = min(32, A.L - t0);
+      for (int q = 0; q < nstep; ++q) {
+        const int idx = (int)__shfl_sync(FULL, my_idx, q);
+        const float logu = __shfl_sync(FULL, my_logu, q);
+        int i = idx, j = 0;
+        if (HEIS) {
+          bond_ends(L.Lx, L.Ly, idx, &i, &j);
+          if (s[i] == s[j]) continue;             // parallel pair: rejected no-op
+        }
+        const float si = (float)s[i];
+        const float two_re_da = HEIS ? -4.f * si * (R.a[i].x - R.a[j].x) : -4.f * si * R.a[i].x;
+        float dr[MPL], di[MPL];
+        float lsum = 0.f, prod = 1.f;
+#pragma unroll
+        for (int k = 0; k < MPL; ++k) {
+          const int hj = lane + 32 * k;
+          dr[k] = 0.f;
+          di[k] = 0.f;
+          if (hj < M) {
+            const float2 wi = R.Wt[(int64_t)i * M + hj];
+            if (HEIS) {
+              const float2 wj = R.Wt[(int64_t)j * M + hj];
+              dr[k] = 2.f * si * (wi.x - wj.x);
+              di[k] = 2.f * si * (wi.y - wj.y);
+            } else {
+              dr[k] = 2.f * si * wi.x;
+              di[k] = 2.f * si * wi.y;
+            }
+            const float2 r = cosh_ratio(t[k], dr[k], di[k]);
+            prod *= fmaf(r.x, r.x, r.y * r.y);
+          }
+          if ((k & 3) == 3 || k == MPL - 1) {
+            lsum += logf(prod);
+            prod = 1.f;
+          }
+        }
+        const float two_re_delta = warp_sum(lsum) + two_re_da;
+        if (logu < two_re_delta) {
+#pragma unroll
+          for (int k = 0; k < MPL; ++k) {
+            if (lane + 32 * k < M) {
+              th[k].x -= dr[k];
+              th[k].y -= di[k];
+              t[k] = tanh_c(th[k].x, th[k].y);
+            }
+          }
+          __syncwarp();
+          if (lane == 0) {
+            s[i] = (int8_t)(-s[i]);
+            if (HEIS) s[j] = (int8_t)(-s[j]);
+          }
+          __syncwarp();
+          ++n_acc;
+        }
+      }
+    }
+    const int after = sw + 1 - A.n_therm;
+    if (after > 0 && after % A.sweeps_per_sample == 0) {
+      const int64_t rec = after / A.sweeps_per_sample - 1;
+      const int64_t qs = rec * A.C + chain;
+      warp_theta<MPL>(R, s, lane, th);           // resynchronise the cache
+#pragma unroll
+      for (int k = 0; k < MPL; ++k) {
+        t[k] = tanh_c(th[k].x, th[k].y);
+        const int hj = lane + 32 * k;
+        if (A.t_out && hj < M) A.t_out[qs * M + hj] = t[k];
+      }
+      if (A.spins_out)
+        for (int i = lane; i < N; i += 32) A.spins_out[qs * N + i] = s[i];
+      if (A.logpsi_out) {
+        const float2 lp = warp_logpsi<MPL>(R, s, lane, th);
+        if (lane == 0) A.logpsi_out[qs] = lp;
+        bad |= !isfinite(lp.x) || !isfinite(lp.y);
+      }
+      if (A.eloc_out) {
+        const float2 e = warp_eloc<MPL>(R, L, s, lane, t);
+        if (lane == 0) A.eloc_out[qs] = e;
+        bad |= !isfinite(e.x) || !isfinite(e.y);
+      }
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < N; i += 32) A.chains[(int64_t)chain * N + i] = s[i];
+  if (lane == 0) {
+    if (A.n_accept) atomicAdd(A.n_accept, n_acc);
+    if (bad) flag_error(A.status, DEV_ERR_NUMERIC);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------
+static int pick_mpl(int M) {
+  int m = (M + 31) / 32;
+  int p = 1;
+  while (p < m) p <<= 1;
+  return p;
+}
+
+#define VMC_DISPATCH_MPL(M, ...)                                  \
+  switch (pick_mpl(M)) {                                          \
+    case 1: { constexpr int MPL = 1; __VA_ARGS__; } break;        \
+    case 2: { constexpr int MPL = 2; __VA_ARGS__; } break;        \
+    case 4: { constexpr int MPL = 4; __VA_ARGS__; } break;        \
+    case 8: { constexpr int MPL = 8; __VA_ARGS__; } break;        \
+    case 16: { constexpr int MPL = 16; __VA_ARGS__; } break;      \
+    default: return cudaErrorInvalidValue;                        \
+  }
+
+static constexpr int kWarps = 4;
+
+static size_t spin_smem(int N) { return (size_t)kWarps * ((N + 15) & ~15); }
+
+cudaError_t launch_param_prep(const double2* p, int N, int M, float2* a, float2* b, float2* Wt,
+                              cudaStream_t st) {
+  int64_t P = (int64_t)N + M + (int64_t)N * M;
+  int blocks = (int)std::min<int64_t>((P + 255) / 256, 4096);
+  k_param_prep<<<blocks, 256, 0, st>>>(p, N, M, a, b, Wt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_logpsi(const RbmDev& R, const int8_t* spins, int64_t n, float2* out,
+                          unsigned* status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  unsigned grid = (unsigned)((n + kWarps - 1) / kWarps);
+  VMC_DISPATCH_MPL(R.M, k_logpsi<MPL><<<grid, 32 * kWarps, spin_smem(R.N), st>>>(R, spins, n, out, status));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eloc(const RbmDev& R, const LatDev& L, const int8_t* spins, int64_t n,
+                        float2* out, unsigned* status, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  unsigned grid = (unsigned)((n + kWarps - 1) / kWarps);
+  VMC_DISPATCH_MPL(R.M, k_eloc<MPL><<<grid, 32 * kWarps, spin_smem(R.N), st>>>(R, L, spins, n, out, status));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_theta_tanh(const RbmDev& R, const int8_t* spins, int64_t n, float2* T,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  unsigned grid = (unsigned)((n + kWarps - 1) / kWarps);
+  VMC_DISPATCH_MPL(R.M, k_theta_tanh<MPL><<<grid, 32 * kWarps, spin_smem(R.N), st>>>(R, spins, n, T));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ok_dense(const int8_t* spins, const float2* T, int64_t n, int N, int M,
+                            float2* O, cudaStream_t st) {
+  int64_t P = (int64_t)N + M + (int64_t)N * M;
+  int64_t total = n * P;
+  if (total <= 0) return cudaSuccess;
+  int blocks = (int)std::min<int64_t>((total + 255) / 256, 65536);
+  k_ok_dense<<<blocks, 256, 0, st>>>(spins, T, n, N, M, O);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample(const SampleArgs& A, cudaStream_t st) {
+  if (A.C <= 0) return cudaSuccess;
+  unsigned grid = (unsigned)((A.C + kWarps - 1) / kWarps);
+  size_t smem = spin_smem(A.rbm.N);
+  if (A.lat.model == 1) {
+    VMC_DISPATCH_MPL(A.rbm.M, k_sample<MPL, true><<<grid, 32 * kWarps, smem, st>>>(A));
+  } else {
+    VMC_DISPATCH_MPL(A.rbm.M, k_sample<MPL, false><<<grid, 32 * kWarps, smem, st>>>(A));
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace vmc

@@ -1,0 +1,372 @@
+// sr.cu -- reductions of the SR/TDVP equation (Eq. qfm, Eq. force_vector):
+// energy statistics, <O>, F, the centred log-derivative matrix and the FP32 Gram that
+// gives S = <O^H O> - <O^H><O>.
+#include "vmc_device.cuh"
+#include "vmc_internal.h"
+
+namespace vmc {
+
+// ---------------------------------------------------------------------------------------
+// energy statistics (FP64): mean, variance, naive standard error
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+  v = warp_sum_d(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    t = warp_sum_d(t);
+    if (lane == 0) red[0] = t;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+__global__ void __launch_bounds__(1024) k_estats(const float2* __restrict__ E, int64_t n,
+                                                 double* out, unsigned* status) {
+  __shared__ double red[32];
+  double sr = 0.0, si = 0.0;
+  bool bad = false;
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+    float2 e = E[q];
+    bad |= !isfinite(e.x) || !isfinite(e.y);
+    sr += e.x;
+    si += e.y;
+  }
+  const double mr = block_sum_d(sr, red) / (double)n;
+  const double mi = block_sum_d(si, red) / (double)n;
+  double v = 0.0;
+  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
+    float2 e = E[q];
+    double dr = e.x - mr, di = e.y - mi;
+    v += dr * dr + di * di;
+  }
+  const double var = block_sum_d(v, red) / (double)n;
+  if (threadIdx.x == 0) {
+    out[0] = mr;
+    out[1] = mi;
+    out[2] = var;
+    out[3] = sqrt(var / (double)n);
+  }
+  if (bad) flag_error(status, DEV_ERR_NUMERIC);
+}
+
+cudaError_t launch_estats(const float2* E, int64_t n, double* out, unsigned* status,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  k_estats<<<1, 1024, 0, st>>>(E, n, out, status);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// <O> and F.  The index space is (j, i) in [0, M] x [0, N] with a virtual hidden unit
+// j = M whose factor is 1 and a virtual visible unit i = N whose spin is 1:
+//   (j < M, i < N): O = t_j s_i (W block);  (j < M, i = N): O = t_j (b block);
+//   (j = M, i < N): O = s_i (a block).
+// Each block sums a 32x32 tile over a chunk of kChunk samples: FP32 within sub-chunks of
+// kSub samples, FP64 across them; chunk partials are then added in a fixed order.
+// ---------------------------------------------------------------------------------------
+static constexpr int kChunk = 1024, kSub = 128, kTile = 32;
+
+int64_t moments_partial_doubles(int64_t n, int N, int M) {
+  int64_t chunks = (n + kChunk - 1) / kChunk;
+  return chunks * 4 * (int64_t)(M + 1) * (N + 1);
+}
+
+__global__ void __launch_bounds__(1024) k_moments_partial(
+    const int8_t* __restrict__ spins, const float2* __restrict__ T, const float2* __restrict__ E,
+    const double* __restrict__ estats, int64_t n, int N, int M, double* __restrict__ partial) {
+  __shared__ float2 Ts[32][kTile + 1];
+  __shared__ float2 Us[32][kTile + 1];
+  __shared__ float Ss[32][kTile + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile;
+  const int64_t q0 = (int64_t)blockIdx.z * kChunk;
+  const int64_t q1 = min(n, q0 + kChunk);
+  const float emr = E ? (float)estats[0] : 0.f, emi = E ? (float)estats[1] : 0.f;
+  const int i = i0 + tx, j = j0 + ty;
+  double dm_r = 0, dm_i = 0, df_r = 0, df_i = 0;
+  float fm_r = 0, fm_i = 0, ff_r = 0, ff_i = 0;
+  int in_sub = 0;
+  for (int64_t qb = q0; qb < q1; qb += 32) {
+    // stage 32 samples: row ty of the staging tile is sample qb + ty
+    {
+      const int64_t q = qb + ty;
+      const int jj = j0 + tx, ii = i0 + tx;
+      float2 t = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f);
+      float sv = 0.f;
+      if (q < q1) {
+        float2 e = E ? E[q] : make_float2(0.f, 0.f);
+        float er = e.x - emr, ei = e.y - emi;
+        if (jj < M) t = T[q * M + jj];
+        else if (jj == M) t = make_float2(1.f, 0.f);
+        u = make_float2(t.x * er + t.y * ei, t.x * ei - t.y * er);   // conj(t) * (E - <E>)
+        if (ii < N) sv = (float)spins[q * N + ii];
+        else if (ii == N) sv = 1.f;
+      }
+      Ts[ty][tx] = t;
+      Us[ty][tx] = u;
+      Ss[ty][tx] = sv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int m = 0; m < 32; ++m) {
+      const float sv = Ss[m][tx];
+      const float2 t = Ts[m][ty], u = Us[m][ty];
+      fm_r = fmaf(sv, t.x, fm_r);
+      fm_i = fmaf(sv, t.y, fm_i);
+      ff_r = fmaf(sv, u.x, ff_r);
+      ff_i = fmaf(sv, u.y, ff_i);
+    }
+    __syncthreads();
+    in_sub += 32;
+    if (in_sub >= kSub) {
+      dm_r += fm_r; dm_i += fm_i; df_r += ff_r; df_i += ff_i;
+      fm_r = fm_i = ff_r = ff_i = 0.f;
+      in_sub = 0;
+    }
+  }
+  dm_r += fm_r; dm_i += fm_i; df_r += ff_r; df_i += ff_i;
+  if (i <= N && j <= M) {
+    const int64_t plane = (int64_t)(M + 1) * (N + 1);
+    double* base = partial + (int64_t)blockIdx.z * 4 * plane + (int64_t)j * (N + 1) + i;
+    base[0] = dm_r;
+    base[plane] = dm_i;
+    base[2 * plane] = df_r;
+    base[3 * plane] = df_i;
+  }
+}
+
+__global__ void k_moments_reduce(const double* __restrict__ partial, int64_t chunks, int64_t n,
+                                 int N, int M, double2* __restrict__ meanO,
+                                 double2* __restrict__ F) {
+  const int64_t plane = (int64_t)(M + 1) * (N + 1);
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < plane;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(e / (N + 1)), i = (int)(e % (N + 1));
+    if (j == M && i == N) continue;
+    double m_r = 0, m_i = 0, f_r = 0, f_i = 0;
+    for (int64_t c = 0; c < chunks; ++c) {
+      const double* b = partial + c * 4 * plane + e;
+      m_r += b[0];
+      m_i += b[plane];
+      f_r += b[2 * plane];
+      f_i += b[3 * plane];
+    }
+    const double inv = 1.0 / (double)n;
+    int64_t k;
+    if (j == M) k = i;                                  // a block
+    else if (i == N) k = N + j;                         // b block
+    else k = (int64_t)N + M + (int64_t)j * N + i;       // W block
+    if (meanO) meanO[k] = make_double2(m_r * inv, m_i * inv);
+    if (F) F[k] = make_double2(f_r * inv, f_i * inv);
+  }
+}
+
+cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E,
+                           const double* estats, int64_t n, int N, int M, double* partial,
+                           double2* meanO, double2* F, cudaStream_t st) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  dim3 grid((N + 1 + kTile - 1) / kTile, (M + 1 + kTile - 1) / kTile, (unsigned)chunks);
+  dim3 block(kTile, 32);
+  k_moments_partial<<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, partial);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t plane = (int64_t)(M + 1) * (N + 1);
+  int blocks = (int)std::min<int64_t>((plane + 255) / 256, 4096);
+  k_moments_reduce<<<blocks, 256, 0, st>>>(partial, chunks, n, N, M, meanO, F);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// X = centred log-derivatives, transposed, real/imag rows interleaved, zero padded
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_build_x(const int8_t* __restrict__ spins,
+                                                 const float2* __restrict__ T,
+                                                 const double2* __restrict__ meanO, int64_t n,
+                                                 int N, int M, int64_t rows_pad, int64_t ld,
+                                                 float* __restrict__ X32,
+                                                 __nv_bfloat16* __restrict__ Xhi,
+                                                 __nv_bfloat16* __restrict__ Xlo) {
+  const int64_t P = (int64_t)N + M + (int64_t)N * M;
+  const int64_t q = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  const int64_t k = (int64_t)blockIdx.y * 8 + threadIdx.y;
+  if (q >= ld || 2 * k >= rows_pad) return;
+  float vr = 0.f, vi = 0.f;
+  if (k < P && q < n) {
+    float2 o;
+    if (k < N) o = make_float2((float)spins[q * N + k], 0.f);
+    else if (k < N + M) o = T[q * M + (k - N)];
+    else {
+      const int64_t r = k - N - M;
+      const int j = (int)(r / N), i = (int)(r % N);
+      const float si = (float)spins[q * N + i];
+      const float2 t = T[q * M + j];
+      o = make_float2(si * t.x, si * t.y);
+    }
+    const double2 m = meanO[k];
+    vr = (float)((double)o.x - m.x);
+    vi = (float)((double)o.y - m.y);
+  }
+  const int64_t r0 = (2 * k) * ld + q, r1 = (2 * k + 1) * ld + q;
+  if (X32) {
+    X32[r0] = vr;
+    X32[r1] = vi;
+  }
+  if (Xhi) {
+    __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
+    Xhi[r0] = hr;
+    Xhi[r1] = hi;
+    Xlo[r0] = __float2bfloat16_rn(vr - __bfloat162float(hr));
+    Xlo[r1] = __float2bfloat16_rn(vi - __bfloat162float(hi));
+  }
+}
+
+cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* meanO,
+                           int64_t n, int N, int M, int64_t rows_pad, int64_t ld, float* X32,
+                           __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, cudaStream_t st) {
+  dim3 block(32, 8);
+  dim3 grid((unsigned)((ld + 31) / 32), (unsigned)((rows_pad / 2 + 7) / 8));
+  k_build_x<<<grid, block, 0, st>>>(spins, T, meanO, n, N, M, rows_pad, ld, X32, Xhi, Xlo);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// FP32 SIMT Gram G = X X^T on lower-triangular 128x128 tiles (both operands have the
+// sample index contiguous), 8x8 outputs per thread, double-buffered shared memory;
+// the epilogue folds the 2x2 real blocks into complex S entries.
+// ---------------------------------------------------------------------------------------
+static constexpr int GB = 128, GK = 16, GPAD = 4;
+
+__device__ __forceinline__ void tri_index(int64_t t, int* bm, int* bn) {
+  // t enumerates (bm, bn) with bn <= bm: t = bm(bm+1)/2 + bn
+  int m = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(m + 1) * (m + 2) / 2 <= t) ++m;
+  while ((int64_t)m * (m + 1) / 2 > t) --m;
+  *bm = m;
+  *bn = (int)(t - (int64_t)m * (m + 1) / 2);
+}
+
+__global__ void __launch_bounds__(256) k_gram_f32(const float* __restrict__ X, int64_t ld,
+                                                  int64_t P, double inv_n,
+                                                  double2* __restrict__ S, int mirror) {
+  extern __shared__ float gsm[];
+  float* As = gsm;                              // [2][GK][GB + GPAD]
+  float* Bs = gsm + 2 * GK * (GB + GPAD);       // [2][GK][GB + GPAD]
+  int bm, bn;
+  tri_index(blockIdx.x, &bm, &bn);
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const float* Ag = X + (int64_t)bm * GB * ld;
+  const float* Bg = X + (int64_t)bn * GB * ld;
+  const int ktiles = (int)(ld / GK);
+
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+
+  float4 ra[2], rb[2];
+  auto gload = [&](int kt) {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 256 * u;
+      const int row = idx >> 2, c4 = idx & 3;
+      ra[u] = *reinterpret_cast<const float4*>(Ag + (int64_t)row * ld + (int64_t)kt * GK + c4 * 4);
+      rb[u] = *reinterpret_cast<const float4*>(Bg + (int64_t)row * ld + (int64_t)kt * GK + c4 * 4);
+    }
+  };
+  auto sstore = [&](int buf) {
+    float* a = As + buf * GK * (GB + GPAD);
+    float* b = Bs + buf * GK * (GB + GPAD);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = tid + 256 * u;
+      const int row = idx >> 2, c4 = idx & 3;
+      a[(c4 * 4 + 0) * (GB + GPAD) + row] = ra[u].x;
+      a[(c4 * 4 + 1) * (GB + GPAD) + row] = ra[u].y;
+      a[(c4 * 4 + 2) * (GB + GPAD) + row] = ra[u].z;
+      a[(c4 * 4 + 3) * (GB + GPAD) + row] = ra[u].w;
+      b[(c4 * 4 + 0) * (GB + GPAD) + row] = rb[u].x;
+      b[(c4 * 4 + 1) * (GB + GPAD) + row] = rb[u].y;
+      b[(c4 * 4 + 2) * (GB + GPAD) + row] = rb[u].z;
+      b[(c4 * 4 + 3) * (GB + GPAD) + row] = rb[u].w;
+    }
+  };
+
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  for (int kt = 0; kt < ktiles; ++kt) {
+    const int buf = kt & 1;
+    if (kt + 1 < ktiles) gload(kt + 1);
+    const float* a = As + buf * GK * (GB + GPAD);
+    const float* b = Bs + buf * GK * (GB + GPAD);
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      float av[8], bv[8];
+      float4 a0 = *reinterpret_cast<const float4*>(a + kk * (GB + GPAD) + ty * 4);
+      float4 a1 = *reinterpret_cast<const float4*>(a + kk * (GB + GPAD) + ty * 4 + 64);
+      float4 b0 = *reinterpret_cast<const float4*>(b + kk * (GB + GPAD) + tx * 4);
+      float4 b1 = *reinterpret_cast<const float4*>(b + kk * (GB + GPAD) + tx * 4 + 64);
+      av[0] = a0.x; av[1] = a0.y; av[2] = a0.z; av[3] = a0.w;
+      av[4] = a1.x; av[5] = a1.y; av[6] = a1.z; av[7] = a1.w;
+      bv[0] = b0.x; bv[1] = b0.y; bv[2] = b0.z; bv[3] = b0.w;
+      bv[4] = b1.x; bv[5] = b1.y; bv[6] = b1.z; bv[7] = b1.w;
+#pragma unroll
+      for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
+    }
+    if (kt + 1 < ktiles) sstore(buf ^ 1);
+    __syncthreads();
+  }
+
+  // epilogue: tile of G to shared memory, then fold 2x2 blocks into S
+  float* Cs = gsm;  // [GB][GB + 1]
+#pragma unroll
+  for (int x = 0; x < 8; ++x) {
+    const int r = (x < 4) ? ty * 4 + x : 64 + ty * 4 + (x - 4);
+#pragma unroll
+    for (int y = 0; y < 8; ++y) {
+      const int c = (y < 4) ? tx * 4 + y : 64 + tx * 4 + (y - 4);
+      Cs[r * (GB + 1) + c] = acc[x][y];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < 64 * 64; e += 256) {
+    const int r = e >> 6, c = e & 63;
+    const int64_t k = (int64_t)bm * 64 + r, l = (int64_t)bn * 64 + c;
+    if (k >= P || l >= P) continue;
+    const float g00 = Cs[(2 * r) * (GB + 1) + 2 * c], g11 = Cs[(2 * r + 1) * (GB + 1) + 2 * c + 1];
+    const float g01 = Cs[(2 * r) * (GB + 1) + 2 * c + 1], g10 = Cs[(2 * r + 1) * (GB + 1) + 2 * c];
+    const double re = ((double)g00 + (double)g11) * inv_n;
+    const double im = ((double)g01 - (double)g10) * inv_n;
+    S[k * P + l] = make_double2(re, im);
+    if (mirror && bm != bn) S[l * P + k] = make_double2(re, -im);
+  }
+}
+
+cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_t P,
+                            double inv_n, double2* S, bool mirror, cudaStream_t st) {
+  if (rows_pad % GB != 0 || ld % GK != 0) return cudaErrorInvalidValue;
+  const int64_t nt = rows_pad / GB;
+  const int64_t tiles = nt * (nt + 1) / 2;
+  const size_t smem = std::max<size_t>(2 * 2 * GK * (GB + GPAD) * sizeof(float),
+                                       (size_t)GB * (GB + 1) * sizeof(float));
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_gram_f32<<<(unsigned)tiles, 256, smem, st>>>(X, ld, P, inv_n, S, mirror ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace vmc

@@ -1,0 +1,149 @@
+// vmc_device.cuh -- device helpers shared by the libvmc kernels: complex FP32 math for
+// the RBM activations, the Philox4x64-10 counter RNG, lattice bonds and the device
+// status word.  Internal to the library.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vmc {
+
+// ---------------------------------------------------------------------------------------
+// device status word (bit flags, OR-ed by kernels, read at synchronising calls)
+// ---------------------------------------------------------------------------------------
+enum : unsigned {
+  DEV_ERR_NUMERIC = 1u,   // non-finite value produced / non-positive pivot
+  DEV_ERR_TIMEOUT = 2u,   // a bounded wait expired
+  DEV_ERR_BOUNDS = 4u     // an index check failed (the access was skipped)
+};
+
+__device__ __forceinline__ void flag_error(unsigned* status, unsigned bit) {
+  if (status) atomicOr(status, bit);
+}
+
+// ---------------------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round multiplies
+// counter words 0 and 2 by the published 64-bit multipliers, mixes the high halves with
+// the other counter words and the key, and bumps the key by the Weyl constants.
+// ---------------------------------------------------------------------------------------
+struct u64x4 { uint64_t w0, w1, w2, w3; };
+
+__device__ __forceinline__ u64x4 philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                               uint64_t c3, uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  return {c0, c1, c2, c3};
+}
+
+// Map one Philox block to a Metropolis step: a uniform index in [0, K) from the top 32
+// bits of word 0 (floor(r*K/2^32)), and u = (24-bit integer + 1/2) / 2^24 from word 1,
+// returned as ln u.
+__device__ __forceinline__ void mh_draw(const u64x4& w, uint32_t K, uint32_t* idx, float* logu) {
+  uint32_t r = (uint32_t)(w.w0 >> 32);
+  *idx = (uint32_t)(((uint64_t)r * (uint64_t)K) >> 32);
+  float u = ((float)(uint32_t)(w.w1 >> 40) + 0.5f) * 5.9604644775390625e-08f;  // 2^-24
+  *logu = logf(u);
+}
+
+// ---------------------------------------------------------------------------------------
+// lattice
+// ---------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int num_bonds(int Lx, int Ly) {
+  return Ly > 1 ? 2 * Lx * Ly : Lx * Ly;
+}
+
+__host__ __device__ __forceinline__ void bond_ends(int Lx, int Ly, int b, int* i, int* j) {
+  const int N = Lx * Ly;
+  const int site = b < N ? b : b - N;
+  const int x = site % Lx, y = site / Lx;
+  *i = site;
+  *j = (b < N) ? ((x + 1) % Lx) + Lx * y : x + Lx * ((y + 1) % Ly);
+}
+
+// ---------------------------------------------------------------------------------------
+// complex FP32 helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ float reduce_angle(float y) {
+  // y - 2 pi * rint(y / 2 pi), so that the fast sin/cos see |y| <= pi
+  return fmaf(-6.28318530717958647692f, rintf(y * 0.15915494309189533577f), y);
+}
+
+// log cosh z = z' - ln 2 + log(1 + e^{-2 z'}), z' = +-z with Re z' >= 0.
+__device__ __forceinline__ float2 logcosh_c(float x, float y) {
+  if (x < 0.0f) { x = -x; y = -y; }
+  float m = expf(-2.0f * x);
+  float s, c;
+  sincosf(-2.0f * y, &s, &c);
+  float wr = m * c, wi = m * s;
+  float re = x - 0.69314718055994531f + 0.5f * log1pf(fmaf(wr, wr, fmaf(wi, wi, 2.0f * wr)));
+  float im = y + atan2f(wi, 1.0f + wr);
+  return make_float2(re, im);
+}
+
+// tanh(x + iy) = (sinh 2x + i sin 2y) / (cosh 2x + cos 2y)
+__device__ __forceinline__ float2 tanh_c(float x, float y) {
+  if (fabsf(x) > 12.0f) return make_float2(copysignf(1.0f, x), 0.0f);
+  float sh = sinhf(2.0f * x), ch = coshf(2.0f * x);
+  float s, c;
+  sincosf(2.0f * y, &s, &c);
+  float d = ch + c;
+  return make_float2(sh / d, s / d);
+}
+
+// cosh and sinh of a complex argument d = x + iy:
+//   cosh d = cosh x cos y + i sinh x sin y,   sinh d = sinh x cos y + i cosh x sin y.
+// For |x|, |y| < 1/2 the four real functions come from their Taylor series (through the
+// x^8 / x^9 terms: truncation below 3e-10), which keeps full FP32 relative accuracy for the
+// small arguments the RBM updates produce; larger arguments use the accurate libm calls.
+__device__ __forceinline__ void cosh_sinh_c(float x, float y, float2* ch, float2* sh) {
+  float chx, shx, cy, sy;
+  if (fabsf(x) < 0.5f && fabsf(y) < 0.5f) {
+    const float x2 = x * x, y2 = y * y;
+    chx = 1.0f + x2 * fmaf(x2, fmaf(x2, fmaf(x2, 2.4801587e-05f, 1.3888889e-03f), 4.1666668e-02f), 0.5f);
+    shx = fmaf(x * x2, fmaf(x2, fmaf(x2, fmaf(x2, 2.7557319e-06f, 1.9841270e-04f), 8.3333333e-03f), 1.6666667e-01f), x);
+    cy = 1.0f - y2 * fmaf(y2, fmaf(y2, fmaf(y2, -2.4801587e-05f, 1.3888889e-03f), -4.1666668e-02f), 0.5f);
+    sy = fmaf(y * y2, fmaf(y2, fmaf(y2, fmaf(y2, 2.7557319e-06f, -1.9841270e-04f), 8.3333333e-03f), -1.6666667e-01f), y);
+  } else {
+    chx = coshf(x);
+    shx = sinhf(x);
+    sincosf(y, &sy, &cy);
+  }
+  *ch = make_float2(chx * cy, shx * sy);
+  *sh = make_float2(shx * cy, chx * sy);
+}
+
+// cosh(theta - d) / cosh(theta) = cosh d - tanh(theta) sinh d   (t = tanh theta cached);
+// finite for every theta, including |Re theta| large where t -> +-1.
+__device__ __forceinline__ float2 cosh_ratio(float2 t, float dr, float di) {
+  float2 ch, sh;
+  cosh_sinh_c(dr, di, &ch, &sh);
+  float2 ts = cmul(t, sh);
+  return make_float2(ch.x - ts.x, ch.y - ts.y);
+}
+
+// warp reductions with xor butterflies: every lane ends with the same bits (each level
+// adds the same two operands in both partner lanes).
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace vmc

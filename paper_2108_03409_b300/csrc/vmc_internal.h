@@ -1,0 +1,119 @@
+// vmc_internal.h -- structs and kernel launchers shared between the libvmc translation
+// units.  Not part of the public ABI (that is include/vmc.h).
+#pragma once
+#include <algorithm>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace vmc {
+
+// FP32 working copy of one lattice's RBM parameters (device pointers).
+struct RbmDev {
+  int N, M;
+  const float2* a;    // [N]
+  const float2* b;    // [M]
+  const float2* Wt;   // [N][M]  (W transposed)
+};
+
+struct LatDev {
+  int model;          // 0 TFIM, 1 Heisenberg
+  int Lx, Ly, nb;
+  float J, h;
+};
+
+struct SampleArgs {
+  RbmDev rbm;
+  LatDev lat;
+  int8_t* chains;                 // [C][N] in/out
+  int C;
+  int L;                          // steps per sweep
+  uint64_t seed, stream, sweep0;
+  int n_therm, n_samples, sweeps_per_sample;
+  int8_t* spins_out;              // [n_samples*C][N] or null
+  float2* logpsi_out;             // [n_samples*C] or null
+  float2* eloc_out;               // [n_samples*C] or null
+  float2* t_out;                  // [n_samples*C][M] or null
+  unsigned long long* n_accept;
+  unsigned* status;
+};
+
+// ---- rbm.cu -------------------------------------------------------------------------
+cudaError_t launch_param_prep(const double2* p, int N, int M, float2* a, float2* b, float2* Wt,
+                              cudaStream_t st);
+cudaError_t launch_logpsi(const RbmDev& R, const int8_t* spins, int64_t n, float2* out,
+                          unsigned* status, cudaStream_t st);
+cudaError_t launch_eloc(const RbmDev& R, const LatDev& L, const int8_t* spins, int64_t n,
+                        float2* out, unsigned* status, cudaStream_t st);
+cudaError_t launch_theta_tanh(const RbmDev& R, const int8_t* spins, int64_t n, float2* T,
+                              cudaStream_t st);
+cudaError_t launch_ok_dense(const int8_t* spins, const float2* T, int64_t n, int N, int M,
+                            float2* O, cudaStream_t st);
+cudaError_t launch_sample(const SampleArgs& A, cudaStream_t st);
+
+// ---- sr.cu ----------------------------------------------------------------------------
+// Energy statistics in FP64: out[0..3] = <E>.re, <E>.im, <|E-<E>|^2>, sqrt(var/n).
+cudaError_t launch_estats(const float2* E, int64_t n, double* out, unsigned* status,
+                          cudaStream_t st);
+
+// Column sums of the log-derivatives and of the force in FP64:
+//   meanO[k] = (1/n) sum_q O_qk,  F[k] = (1/n) sum_q conj(O_qk) (E_q - <E>),
+// with O = [s | t | t (x) s] built on the fly from spins and T = tanh theta.
+// partial: scratch of moments_partial_doubles(n, N, M) doubles.
+int64_t moments_partial_doubles(int64_t n, int N, int M);
+cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E,
+                           const double* estats, int64_t n, int N, int M, double* partial,
+                           double2* meanO, double2* F, cudaStream_t st);
+
+// Centred log-derivatives, transposed and split into real rows:
+//   X[2k][q] = Re(O_qk - <O_k>), X[2k+1][q] = Im(...), zero padded to [rows_pad][ld].
+// FP32 (X32) and/or the BF16 pair hi = bf16(x), lo = bf16(x - hi).
+cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* meanO,
+                           int64_t n, int N, int M, int64_t rows_pad, int64_t ld, float* X32,
+                           __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, cudaStream_t st);
+
+// S_kl = (1/n) sum_q conj(Xc_qk) Xc_ql from the real row Gram G = X X^T (FP32 SIMT):
+//   S = (G_{2k,2l} + G_{2k+1,2l+1}) + i (G_{2k,2l+1} - G_{2k+1,2l}), written as double2
+//   [P][P]; mirror = also write the upper triangle.
+cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_t P,
+                            double inv_n, double2* S, bool mirror, cudaStream_t st);
+
+// Same contraction on the tensor cores (tcgen05, BF16 hi/lo split, FP32 accumulation
+// in TMEM).  Returns cudaErrorNotSupported when the shapes are not supported.
+cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
+                           int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
+                           bool mirror, unsigned* status, cudaStream_t st);
+
+// ---- solve.cu -------------------------------------------------------------------------
+struct SolveWork {
+  int64_t P;
+  double2* A64;    // [P][P] FP64 factor workspace (FP64 solver), may be null
+  double2* D64;    // [ceil(P/64)][64][64] inverted diagonal blocks (FP64)
+  float2* A32;     // [P][P] FP32 factor workspace (mixed solver), may be null
+  float2* D32;     // inverted diagonal blocks (FP32)
+  double2* r;      // [P] residual / forward-solve workspace
+  double2* c;      // [P] right-hand side workspace
+  float2* r32;     // [P]
+  float2* y32;     // [P]
+  float2* c32;     // [P]
+  double* scal;    // [8] device scalars
+};
+
+// Cholesky solve of (S + shift) x = F, FP64 throughout.
+cudaError_t solve_cholesky_fp64(const double2* S, const double2* F, double2* x, double nu,
+                                int mode, SolveWork& w, unsigned* status, cudaStream_t st,
+                                int64_t* launches);
+// FP32 Cholesky of the shifted matrix + FP64 iterative refinement.
+cudaError_t solve_cholesky_mixed(const double2* S, const double2* F, double2* x, double nu,
+                                 int mode, double tol, int maxit, SolveWork& w,
+                                 unsigned* status, cudaStream_t st, int64_t* launches,
+                                 int* iters, double* relres);
+// FP64 relative residual ||(S + shift) x - F|| / ||F|| (synchronises).
+cudaError_t residual_fp64(const double2* S, const double2* F, const double2* x, double nu,
+                          int mode, SolveWork& w, cudaStream_t st, double* relres);
+
+// theta <- theta - dt * x, then refresh the FP32 copies
+cudaError_t launch_update(double2* params, const double2* x, int64_t P, double dt,
+                          cudaStream_t st);
+
+}  // namespace vmc

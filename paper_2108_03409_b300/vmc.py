@@ -1,0 +1,229 @@
+"""Thin ctypes binding of libvmc (include/vmc.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch tensors and
+Python values into the C ABI's pointers and structs and turns status codes into
+exceptions.  The function names are the C entry points.  The library is loaded on first
+use; if ``libvmc.so`` is missing the call raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvmc.so")
+
+VMC_OK, VMC_ERR_ARG, VMC_ERR_CUDA, VMC_ERR_OOM, VMC_ERR_NUMERIC, VMC_ERR_TIMEOUT, VMC_ERR_STATE = range(7)
+MODEL_TFIM, MODEL_HEISENBERG = 0, 1
+PREC_FP32, PREC_BF16SPLIT = 0, 1
+SOLVER_CHOLESKY_FP64, SOLVER_CG, SOLVER_CHOLESKY_MIXED = 0, 1, 2
+SHIFT_MULTIPLICATIVE, SHIFT_ADDITIVE = 0, 1
+
+_STATUS_NAMES = {0: "VMC_OK", 1: "VMC_ERR_ARG", 2: "VMC_ERR_CUDA", 3: "VMC_ERR_OOM",
+                 4: "VMC_ERR_NUMERIC", 5: "VMC_ERR_TIMEOUT", 6: "VMC_ERR_STATE"}
+
+
+class VmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vmc_lattice(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("Lx", ctypes.c_int), ("Ly", ctypes.c_int),
+                ("J", ctypes.c_double), ("h", ctypes.c_double), ("alpha", ctypes.c_int)]
+
+
+class vmc_config(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("n_chains", ctypes.c_int), ("sweep_len", ctypes.c_int),
+                ("therm_sweeps", ctypes.c_int), ("sweeps_per_sample", ctypes.c_int),
+                ("samples_per_chain", ctypes.c_int), ("precision", ctypes.c_int),
+                ("solver", ctypes.c_int), ("shift", ctypes.c_double), ("shift_mode", ctypes.c_int),
+                ("cg_maxit", ctypes.c_int), ("cg_tol", ctypes.c_double)]
+
+
+class vmc_sr_stats(ctypes.Structure):
+    _fields_ = [("e_mean_re", ctypes.c_double), ("e_mean_im", ctypes.c_double),
+                ("e_var", ctypes.c_double), ("e_stderr", ctypes.c_double),
+                ("acceptance", ctypes.c_double), ("n_samples", ctypes.c_int64),
+                ("solver_iters", ctypes.c_int), ("solver_relres", ctypes.c_double),
+                ("ms_sample", ctypes.c_float), ("ms_grad", ctypes.c_float),
+                ("ms_qfm", ctypes.c_float), ("ms_solve", ctypes.c_float),
+                ("ms_update", ctypes.c_float), ("ms_gram", ctypes.c_float),
+                ("launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
+            "vmc_set_chains", "vmc_get_chains", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
+            "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
+            "vmc_num_samples", "vmc_num_params"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libvmc.so and declare the signatures (raises OSError if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"libvmc.so not found at {path}; build it with "
+                      "`python -m paper_2108_03409_b300.build`")
+    lib = ctypes.CDLL(path)
+    P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "vmc_init": (i32, [ctypes.POINTER(vmc_config), ctypes.POINTER(vmc_lattice), i32, P,
+                           ctypes.POINTER(P)]),
+        "vmc_destroy": (None, [P]),
+        "vmc_last_error": (ctypes.c_char_p, [P]),
+        "vmc_set_params": (i32, [P, i32, P]),
+        "vmc_get_params": (i32, [P, i32, P]),
+        "vmc_set_chains": (i32, [P, i32, P]),
+        "vmc_get_chains": (i32, [P, i32, P]),
+        "vmc_logpsi": (i32, [P, i32, P, i64, P]),
+        "vmc_local_energy": (i32, [P, i32, P, i64, P]),
+        "vmc_sample": (i32, [P, i32, i32, i32, P, P, P]),
+        "vmc_grad": (i32, [P, i32, P, P, i64, P, P, P]),
+        "vmc_qfm": (i32, [P, i32, P, i64, i32, P]),
+        "vmc_solve": (i32, [P, i32, P, P, P, ctypes.POINTER(i32), ctypes.POINTER(f64)]),
+        "vmc_sr_step": (i32, [P, i32, f64, ctypes.POINTER(vmc_sr_stats)]),
+        "vmc_kernel_launches": (i64, [P]),
+        "vmc_num_samples": (i64, [P]),
+        "vmc_num_params": (i64, [P, i32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> Optional[int]:
+    """Raw device/host pointer of a torch tensor (or numpy array, or None)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        assert t.is_contiguous(), "tensors passed to libvmc must be contiguous"
+        return t.data_ptr()
+    return t.ctypes.data
+
+
+def _check(ctx, status: int):
+    if status != VMC_OK:
+        msg = load().vmc_last_error(ctx).decode() if ctx else ""
+        raise VmcError(status, msg)
+
+
+def make_config(seed=1, n_chains=256, sweep_len=0, therm_sweeps=20, sweeps_per_sample=1,
+                samples_per_chain=1, precision=PREC_FP32, solver=SOLVER_CHOLESKY_FP64,
+                shift=1e-4, shift_mode=SHIFT_MULTIPLICATIVE, cg_maxit=100,
+                cg_tol=1e-10) -> vmc_config:
+    return vmc_config(seed, n_chains, sweep_len, therm_sweeps, sweeps_per_sample,
+                      samples_per_chain, precision, solver, shift, shift_mode, cg_maxit, cg_tol)
+
+
+def make_lattice(model, Lx, Ly=1, J=1.0, h=0.0, alpha=1) -> vmc_lattice:
+    return vmc_lattice(model, Lx, Ly, J, h, alpha)
+
+
+# --------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# --------------------------------------------------------------------------------------
+def vmc_init(cfg: vmc_config, lattices: Sequence[vmc_lattice], stream: int = 0):
+    lib = load()
+    arr = (vmc_lattice * len(lattices))(*lattices)
+    out = ctypes.c_void_p()
+    st = lib.vmc_init(ctypes.byref(cfg), arr, len(lattices), ctypes.c_void_p(stream or None),
+                      ctypes.byref(out))
+    if st != VMC_OK:
+        raise VmcError(st, "vmc_init failed")
+    return out
+
+
+def vmc_destroy(ctx):
+    if ctx:
+        load().vmc_destroy(ctx)
+
+
+def vmc_set_params(ctx, lattice, params_host):
+    """params_host: numpy complex128 [P]."""
+    import numpy as np
+    p = np.ascontiguousarray(params_host, dtype=np.complex128)
+    _check(ctx, load().vmc_set_params(ctx, lattice, p.ctypes.data))
+
+
+def vmc_get_params(ctx, lattice):
+    import numpy as np
+    P = load().vmc_num_params(ctx, lattice)
+    out = np.zeros(P, dtype=np.complex128)
+    _check(ctx, load().vmc_get_params(ctx, lattice, out.ctypes.data))
+    return out
+
+
+def vmc_set_chains(ctx, lattice, spins_host):
+    import numpy as np
+    s = np.ascontiguousarray(spins_host, dtype=np.int8)
+    _check(ctx, load().vmc_set_chains(ctx, lattice, s.ctypes.data))
+
+
+def vmc_get_chains(ctx, lattice, n_chains, N):
+    import numpy as np
+    out = np.zeros((n_chains, N), dtype=np.int8)
+    _check(ctx, load().vmc_get_chains(ctx, lattice, out.ctypes.data))
+    return out
+
+
+def vmc_logpsi(ctx, lattice, spins, out):
+    _check(ctx, load().vmc_logpsi(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(out)))
+
+
+def vmc_local_energy(ctx, lattice, spins, out):
+    _check(ctx, load().vmc_local_energy(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(out)))
+
+
+def vmc_sample(ctx, lattice, n_therm, n_samples, spins_out=None, logpsi_out=None, eloc_out=None):
+    _check(ctx, load().vmc_sample(ctx, lattice, n_therm, n_samples, _ptr(spins_out),
+                                  _ptr(logpsi_out), _ptr(eloc_out)))
+
+
+def vmc_grad(ctx, lattice, spins, eloc, O_out=None, F_out=None, want_stats=True):
+    import numpy as np
+    es = np.zeros(4, dtype=np.float64) if want_stats else None
+    _check(ctx, load().vmc_grad(ctx, lattice, _ptr(spins), _ptr(eloc), spins.shape[0],
+                                _ptr(O_out), _ptr(F_out), None if es is None else es.ctypes.data))
+    return es
+
+
+def vmc_qfm(ctx, lattice, spins, precision, S_out):
+    _check(ctx, load().vmc_qfm(ctx, lattice, _ptr(spins), spins.shape[0], precision, _ptr(S_out)))
+
+
+def vmc_solve(ctx, lattice, S, F, x):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    _check(ctx, load().vmc_solve(ctx, lattice, _ptr(S), _ptr(F), _ptr(x), ctypes.byref(it),
+                                 ctypes.byref(rr)))
+    return it.value, rr.value
+
+
+def vmc_sr_step(ctx, lattice, dt) -> vmc_sr_stats:
+    st = vmc_sr_stats()
+    _check(ctx, load().vmc_sr_step(ctx, lattice, float(dt), ctypes.byref(st)))
+    return st
+
+
+def vmc_kernel_launches(ctx) -> int:
+    return int(load().vmc_kernel_launches(ctx))
+
+
+def vmc_num_samples(ctx) -> int:
+    return int(load().vmc_num_samples(ctx))
+
+
+def vmc_num_params(ctx, lattice) -> int:
+    return int(load().vmc_num_params(ctx, lattice))

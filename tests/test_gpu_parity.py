@@ -1,0 +1,321 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded inputs.
+
+Sizes span several tiles and a ragged tail (M = 10, 72, 128, 512 hidden units against
+32-wide warps; 2P not a multiple of the 128-row Gram tile) and include the 8x8
+Heisenberg workload's shapes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_03409_b300 import inputs
+from paper_2108_03409_b300 import vmc
+
+from gpu_helpers import (ELOC_PER_SITE_ABS, F_REL, LOGPSI_ABS, OK_ABS, OK_REL, context, cplx,
+                         eloc_tolerance, lattice, phase_diff, s_tol_fp32, to_dev_spins,
+                         well_conditioned)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+T, H = inputs.MODEL_TFIM, inputs.MODEL_HEIS
+
+# (model, Lx, Ly, J, h, alpha, sigma, n_samples)
+CASES = [
+    (T, 10, 1, 1.0, 1.0, 1, 0.01, 1024),      # 1D TFIM N=10 (all states)
+    (T, 6, 6, 1.0, 3.1, 2, 0.05, 1500),       # M = 72: ragged against 32 lanes
+    (H, 8, 8, 1.0, 0.0, 2, 0.01, 1200),       # 8x8 Heisenberg, Marshall phase
+    (H, 4, 4, 1.0, 0.0, 2, 0.2, 2000),        # larger weights
+    (H, 16, 16, 1.0, 0.0, 2, 0.01, 48),       # M = 512
+]
+IDS = ["tfim10", "tfim6x6", "heis8x8", "heis4x4_s0.2", "heis16x16"]
+
+
+def _setup(case, seed=0):
+    model, Lx, Ly, J, h, alpha, sigma, n = case
+    N, M = Lx * Ly, alpha * Lx * Ly
+    p = inputs.rbm_params(N, M, sigma, seed=31 + seed, marshall=(Lx, Ly) if model == H else None)
+    if model == T and N == 10:
+        s = oracle.all_states(N)
+    else:
+        s = inputs.initial_spins(model, n, N, seed=7 + seed)
+    return model, Lx, Ly, J, h, alpha, N, M, p, s
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_logpsi_matches_oracle(case):
+    model, Lx, Ly, J, h, alpha, N, M, p, s = _setup(case)
+    with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=max(1, s.shape[0]),
+                 solver=vmc.SOLVER_CG) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        out = torch.zeros((s.shape[0], 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_logpsi(ctx, 0, to_dev_spins(s), out)
+        got = cplx(out)
+    ref = oracle.logpsi(N, M, p, s)
+    ok = well_conditioned(p, s, N, M)
+    assert ok.mean() >= 0.98 and np.all(np.isfinite(got))
+    got, ref = got[ok], ref[ok]
+    assert np.max(np.abs(got.real - ref.real)) <= LOGPSI_ABS * max(1.0, np.abs(ref.real).max())
+    assert np.max(phase_diff(got.imag, ref.imag)) <= LOGPSI_ABS * max(1.0, np.abs(ref.imag).max())
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_local_energy_matches_oracle(case):
+    model, Lx, Ly, J, h, alpha, N, M, p, s = _setup(case)
+    with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=max(1, s.shape[0]),
+                 solver=vmc.SOLVER_CG) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        out = torch.zeros((s.shape[0], 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_local_energy(ctx, 0, to_dev_spins(s), out)
+        got = cplx(out)
+    ref = oracle.eloc(model, Lx, Ly, J, h, M, p, s)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= eloc_tolerance(model, Lx, Ly, J, h, M, p, s))
+    ok = well_conditioned(p, s, N, M, cut=0.3)       # away from nodes: the plain bound
+    assert np.max(np.abs(got[ok] - ref[ok])) / N <= ELOC_PER_SITE_ABS
+
+
+def test_empty_batch_is_a_noop():
+    with context(lattice(T, 10, 1, 1.0, 1.0, 1), n_chains=4) as ctx:
+        e = torch.zeros((0, 2), dtype=torch.float32, device="cuda")
+        s = torch.zeros((0, 10), dtype=torch.int8, device="cuda")
+        vmc.vmc_logpsi(ctx, 0, s, e)
+        vmc.vmc_local_energy(ctx, 0, s, e)
+
+
+# (model, Lx, Ly, J, h, alpha, sigma, chains, sweeps)
+SAMPLE_CASES = [
+    (T, 10, 1, 1.0, 1.0, 1, 0.3, 256, 30),
+    (T, 6, 6, 1.0, 3.0, 2, 0.1, 256, 6),
+    (H, 8, 8, 1.0, 0.0, 2, 0.05, 512, 4),
+    (H, 10, 1, 1.0, 0.0, 1, 0.3, 256, 20),
+]
+
+
+@pytest.mark.parametrize("case", SAMPLE_CASES, ids=["tfim10", "tfim6x6", "heis8x8", "heis10"])
+def test_sampler_trajectories_match_oracle(case):
+    """Same Philox stream and acceptance rule: every recorded state equals the oracle's,
+    except in chains where the oracle met a decision within 1e-4 of the threshold
+    (FP32 vs FP64 may decide those differently; then the trajectories part)."""
+    model, Lx, Ly, J, h, alpha, sigma, C, sweeps = case
+    N, M = Lx * Ly, alpha * Lx * Ly
+    p = inputs.rbm_params(N, M, sigma, seed=3, marshall=(Lx, Ly) if model == H else None)
+    s0 = inputs.initial_spins(model, C, N, seed=4)
+    seed = 12345
+    with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=C, seed=seed,
+                 solver=vmc.SOLVER_CG) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vmc.vmc_set_chains(ctx, 0, s0)
+        # two calls: the sweep counter must continue across them
+        k1 = sweeps // 2
+        out1 = torch.zeros((k1 * C, N), dtype=torch.int8, device="cuda")
+        lp1 = torch.zeros((k1 * C, 2), dtype=torch.float32, device="cuda")
+        el1 = torch.zeros((k1 * C, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_sample(ctx, 0, 0, k1, out1, lp1, el1)
+        out2 = torch.zeros(((sweeps - k1) * C, N), dtype=torch.int8, device="cuda")
+        vmc.vmc_sample(ctx, 0, 0, sweeps - k1, out2)
+        got = torch.cat([out1, out2]).cpu().numpy().reshape(sweeps, C, N)
+        final = vmc.vmc_get_chains(ctx, 0, C, N)
+        lp1 = cplx(lp1)
+        el1 = cplx(el1)
+    fin, rec, margin, acc = oracle.metropolis(model, Lx, Ly, M, p, s0, seed=seed, stream=0,
+                                              n_sweeps=sweeps, record=True)
+    same = np.all(got == rec, axis=(0, 2))
+    assert np.array_equal(final[same], fin[same])
+    bad = ~same
+    assert np.all(margin[bad] < 1e-4), (np.sum(bad), margin[bad])
+    assert bad.mean() <= 0.01
+    assert acc.sum() > 0
+    if model == H:
+        assert np.all(got.sum(axis=2) == 0)
+    # fused log psi and E_loc of the recorded samples (first call) against the oracle
+    first = got[:k1].reshape(-1, N)
+    ref_el = oracle.eloc(model, Lx, Ly, J, h, M, p, first)
+    assert np.all(np.abs(el1 - ref_el) <= eloc_tolerance(model, Lx, Ly, J, h, M, p, first))
+    ok = well_conditioned(p, first, N, M, cut=0.3)
+    assert ok.mean() >= 0.9
+    first, lp1, el1, ref_el = first[ok], lp1[ok], el1[ok], ref_el[ok]
+    ref_lp = oracle.logpsi(N, M, p, first)
+    assert np.max(np.abs(lp1.real - ref_lp.real)) <= LOGPSI_ABS * max(1.0, np.abs(ref_lp.real).max())
+    assert np.max(phase_diff(lp1.imag, ref_lp.imag)) <= LOGPSI_ABS * max(1.0, np.abs(ref_lp.imag).max())
+    assert np.max(np.abs(el1 - ref_el)) / N <= ELOC_PER_SITE_ABS
+
+
+def test_sampler_thermalisation_and_sweep_len():
+    """n_therm sweeps are run but not recorded; sweep_len overrides N."""
+    model, Lx, Ly, alpha, C = T, 8, 1, 1, 64
+    N, M = 8, 8
+    p = inputs.rbm_params(N, M, 0.2, seed=5)
+    s0 = inputs.random_spins(C, N, seed=6)
+    with context(lattice(model, Lx, Ly, 1.0, 0.8, alpha), n_chains=C, seed=9, sweep_len=5,
+                 solver=vmc.SOLVER_CG) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vmc.vmc_set_chains(ctx, 0, s0)
+        out = torch.zeros((3 * C, N), dtype=torch.int8, device="cuda")
+        vmc.vmc_sample(ctx, 0, 4, 3, out)
+        got = out.cpu().numpy().reshape(3, C, N)
+    _, rec, margin, _ = oracle.metropolis(model, Lx, Ly, M, p, s0, seed=9, n_sweeps=7,
+                                          sweep_len=5, record=True)
+    same = np.all(got == rec[4:], axis=(0, 2))
+    assert np.all(margin[~same] < 1e-4) and same.mean() >= 0.99
+
+
+# (model, Lx, Ly, J, h, alpha, sigma, n)
+GRAD_CASES = [
+    (T, 10, 1, 1.0, 1.0, 1, 0.1, 3000),
+    (H, 4, 4, 1.0, 0.0, 2, 0.1, 2000),
+    (T, 6, 6, 1.0, 3.0, 2, 0.05, 1100),
+]
+
+
+@pytest.mark.parametrize("case", GRAD_CASES, ids=["tfim10", "heis4x4", "tfim6x6"])
+def test_grad_and_qfm_match_oracle(case):
+    model, Lx, Ly, J, h, alpha, sigma, n = case
+    N, M = Lx * Ly, alpha * Lx * Ly
+    P = N + M + N * M
+    p = inputs.rbm_params(N, M, sigma, seed=41, marshall=(Lx, Ly) if model == H else None)
+    s = inputs.initial_spins(model, n, N, seed=42)
+    with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=n, solver=vmc.SOLVER_CHOLESKY_FP64) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        sd = to_dev_spins(s)
+        e = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_local_energy(ctx, 0, sd, e)
+        O = torch.zeros((n, P, 2), dtype=torch.float32, device="cuda")
+        F = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        stats = vmc.vmc_grad(ctx, 0, sd, e, O, F)
+        S = torch.zeros((P, P, 2), dtype=torch.float64, device="cuda")
+        vmc.vmc_qfm(ctx, 0, sd, vmc.PREC_FP32, S)
+        E = cplx(e)
+        O, F, S = cplx(O), cplx(F), cplx(S)
+    Oref = oracle.ok(N, M, p, s)
+    assert np.all(np.abs(O - Oref) <= OK_REL * np.abs(Oref) + OK_ABS)
+    Sref, Fref, Eref = oracle.sr_matrices(Oref, E)        # same FP32 energies as the GPU used
+    assert abs(stats[0] + 1j * stats[1] - Eref) <= 1e-9 * max(1.0, abs(Eref))
+    assert np.max(np.abs(F - Fref)) <= F_REL * np.max(np.abs(Fref))
+    assert np.max(np.abs(S - Sref)) <= s_tol_fp32(n) * np.max(np.abs(np.diag(Sref)))
+    assert np.allclose(S, S.conj().T, atol=0)
+
+
+def test_qfm_8x8_sampled_entries():
+    """At the 8x8 Heisenberg shape (P = 8384, 67 x 67 Gram tiles of 128 rows) compare
+    sampled entries of S, every F_k and the diagonal with the oracle."""
+    model, Lx, Ly, alpha, n = H, 8, 8, 2, 1024
+    N, M = 64, 128
+    P = N + M + N * M
+    p = inputs.rbm_params(N, M, 0.01, seed=2, marshall=(Lx, Ly))
+    s = inputs.random_sz0_spins(n, N, seed=3)
+    with context(lattice(model, Lx, Ly, 1.0, 0.0, alpha), n_chains=n, solver=vmc.SOLVER_CHOLESKY_MIXED) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        sd = to_dev_spins(s)
+        e = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_local_energy(ctx, 0, sd, e)
+        F = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        vmc.vmc_grad(ctx, 0, sd, e, None, F)
+        S = torch.zeros((P, P, 2), dtype=torch.float64, device="cuda")
+        vmc.vmc_qfm(ctx, 0, sd, vmc.PREC_FP32, S)
+        Sd = S.cpu().numpy()
+        E, F = cplx(e), cplx(F)
+    rng = np.random.default_rng(0)
+    kk = np.concatenate([rng.integers(0, P, 300), np.arange(0, P, 97), [P - 1, 0, N, N + M]])
+    ll = np.concatenate([rng.integers(0, P, 300), np.arange(0, P, 97)[::-1], [P - 1, P - 1, 3, N + M + 5]])
+    O = oracle.ok(N, M, p, s)
+    s_ref, f_ref = oracle.sr_entries(O, E, kk, ll, np.arange(P))
+    got = Sd[kk, ll, 0] + 1j * Sd[kk, ll, 1]
+    scale = np.max(np.abs(oracle.sr_entries(O, E, np.arange(0, P, 50), np.arange(0, P, 50), [])[0]))
+    assert np.max(np.abs(got - s_ref)) <= s_tol_fp32(n) * scale
+    assert np.max(np.abs(F - f_ref)) <= F_REL * np.max(np.abs(f_ref))
+    # Hermitian and the Sz = 0 null vector (sum of the a-block columns)
+    v = np.zeros(P, np.complex128)
+    v[:N] = 1.0
+    Sc = Sd[..., 0] + 1j * Sd[..., 1]
+    assert np.linalg.norm(Sc @ v) <= 1e-5 * np.linalg.norm(Sc[:, :N])
+    assert np.array_equal(Sd[..., 0], Sd[..., 0].T) and np.array_equal(Sd[..., 1], -Sd[..., 1].T)
+
+
+@pytest.mark.parametrize("solver", [vmc.SOLVER_CHOLESKY_FP64, vmc.SOLVER_CHOLESKY_MIXED])
+@pytest.mark.parametrize("shape", [(T, 10, 1, 1, 1e-4, 0), (H, 4, 4, 2, 1e-3, 0), (T, 6, 6, 1, 1e-2, 1)],
+                         ids=["P120", "P560", "P1332_additive"])
+def test_solve_matches_oracle(solver, shape):
+    model, Lx, Ly, alpha, nu, mode = shape
+    N, M = Lx * Ly, alpha * Lx * Ly
+    P = N + M + N * M
+    n = 3 * P
+    p = inputs.rbm_params(N, M, 0.1, seed=8, marshall=(Lx, Ly) if model == H else None)
+    s = inputs.initial_spins(model, n, N, seed=9)
+    O = oracle.ok(N, M, p, s)
+    E = oracle.eloc(model, Lx, Ly, 1.0, 1.0, M, p, s)
+    S, F, _ = oracle.sr_matrices(O, E)
+    xref = oracle.cholesky_solve(oracle.shift(S, nu, mode), F)
+    with context(lattice(model, Lx, Ly, 1.0, 1.0, alpha), n_chains=n, solver=solver, shift=nu,
+                 shift_mode=mode, cg_tol=1e-12, cg_maxit=30) as ctx:
+        Sd = torch.from_numpy(S.view(np.float64).reshape(P, P, 2).copy()).cuda()
+        Fd = torch.from_numpy(F.view(np.float64).reshape(P, 2).copy()).cuda()
+        xd = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        it, rel = vmc.vmc_solve(ctx, 0, Sd, Fd, xd)
+        x = cplx(xd)
+    St = oracle.shift(S, nu, mode)
+    res = np.linalg.norm(St @ x - F) / np.linalg.norm(F)
+    cond = np.linalg.cond(St)
+    assert res <= 1e-13 * np.linalg.norm(St, 2) * np.linalg.norm(x) / np.linalg.norm(F) + 1e-14
+    assert abs(rel - res) <= 1e-9 + 0.5 * res
+    assert np.linalg.norm(x - xref) <= 1e-14 * cond * np.linalg.norm(xref) + 1e-12
+
+
+def test_solve_reports_non_positive_pivot():
+    N, M = 10, 10
+    P = N + M + N * M
+    with context(lattice(T, 10, 1, 1.0, 1.0, 1), n_chains=4, solver=vmc.SOLVER_CHOLESKY_FP64,
+                 shift=0.0) as ctx:
+        S = np.eye(P, dtype=np.complex128)
+        S[5, 5] = -1.0
+        Sd = torch.from_numpy(S.view(np.float64).reshape(P, P, 2).copy()).cuda()
+        Fd = torch.ones((P, 2), dtype=torch.float64, device="cuda")
+        xd = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        with pytest.raises(vmc.VmcError) as e:
+            vmc.vmc_solve(ctx, 0, Sd, Fd, xd)
+        assert e.value.status == vmc.VMC_ERR_NUMERIC
+        # the context stays usable after the reported failure
+        S[5, 5] = 2.0
+        Sd = torch.from_numpy(S.view(np.float64).reshape(P, P, 2).copy()).cuda()
+        vmc.vmc_solve(ctx, 0, Sd, Fd, xd)
+
+
+@pytest.mark.parametrize("solver", [vmc.SOLVER_CHOLESKY_FP64, vmc.SOLVER_CHOLESKY_MIXED])
+def test_sr_step_matches_oracle_pipeline(solver):
+    """One SR step.  The sample set is read back through vmc_sample on a twin context
+    (the kernels are deterministic, and the sampler's agreement with the oracle's
+    Metropolis stream is covered above); the oracle then computes E_loc, O_k, S, F, the
+    shifted Cholesky solve and the Euler update from it.  The GPU's updated parameters
+    must solve the oracle's equation to the accuracy the FP32 S and F allow."""
+    model, Lx, Ly, J, h, alpha = T, 10, 1, 1.0, 1.0, 1
+    N, M = 10, 10
+    C, spc, therm, dt, nu, seed = 64, 20, 5, 0.02, 1e-4, 77
+    p = inputs.rbm_params(N, M, 0.01, seed=1234)
+    s0 = inputs.random_spins(C, N, seed=99)
+    kw = dict(n_chains=C, samples_per_chain=spc, therm_sweeps=therm, seed=seed, solver=solver,
+              shift=nu, cg_tol=1e-10, cg_maxit=50)
+    with context(lattice(model, Lx, Ly, J, h, alpha), **kw) as twin:
+        vmc.vmc_set_params(twin, 0, p)
+        vmc.vmc_set_chains(twin, 0, s0)
+        out = torch.zeros((spc * C, N), dtype=torch.int8, device="cuda")
+        vmc.vmc_sample(twin, 0, therm, spc, out)
+        samples = out.cpu().numpy()
+    with context(lattice(model, Lx, Ly, J, h, alpha), **kw) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vmc.vmc_set_chains(ctx, 0, s0)
+        st = vmc.vmc_sr_step(ctx, 0, dt)
+        p1 = vmc.vmc_get_params(ctx, 0)
+        launches = vmc.vmc_kernel_launches(ctx)
+    assert launches > 5
+    E = oracle.eloc(model, Lx, Ly, J, h, M, p, samples)
+    O = oracle.ok(N, M, p, samples)
+    S, F, Em = oracle.sr_matrices(O, E)
+    assert abs(st.e_mean_re - Em.real) / N <= ELOC_PER_SITE_ABS
+    assert st.n_samples == C * spc
+    St = oracle.shift(S, nu, 0)
+    delta = (p - p1) / dt
+    res = np.linalg.norm(St @ delta - F) / np.linalg.norm(F)
+    bound = 1e-4 * (1 + np.linalg.norm(St, 2) * np.linalg.norm(delta) / np.linalg.norm(F))
+    assert res <= bound, (res, bound)
+    assert 0.0 < st.acceptance < 1.0
+    assert st.solver_relres <= 1e-10
