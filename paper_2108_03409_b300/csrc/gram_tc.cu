@@ -1,12 +1,303 @@
-// gram_tc.cu -- S = <O^H O>^c on the 5th-generation tensor cores (placeholder until the
-// tcgen05 kernel lands).
+// gram_tc.cu -- S = <O^H O>^c (Eq. qfm) on the 5th-generation tensor cores.
+//
+// The centred log-derivatives are stored as real rows X (row 2k = Re Obar_k, row 2k+1 =
+// Im Obar_k, samples contiguous), split into BF16 pairs X = hi + lo.  The real Gram
+// G = X X^T is accumulated in FP32 in tensor memory as hi.hi^T + hi.lo^T + lo.hi^T (the
+// lo.lo^T term is 2^-16 below the others), one 128 x 128 tile of G per CTA, lower tiles
+// only.  The epilogue folds each 2x2 block of G into one complex entry of S:
+//   S_kl = (G[2k][2l] + G[2k+1][2l+1] + i (G[2k][2l+1] - G[2k+1][2l])) / n.
+//
+// Data movement: TMA (cp.async.bulk.tensor, 128-byte swizzle, no multicast) into a
+// 3-stage shared-memory ring guarded by mbarriers; one thread issues tcgen05.mma
+// (kind::f16, BF16 inputs, FP32 accumulator, M = N = 128, K = 16); tcgen05.commit frees
+// ring stages and signals the epilogue; tcgen05.ld reads the accumulator back.  Every
+// mbarrier wait is bounded (iteration and clock limits); on expiry the kernel records
+// DEV_ERR_TIMEOUT, skips the remaining work, frees its tensor memory and returns.
+#include <cuda.h>
+
+#include "vmc_device.cuh"
 #include "vmc_internal.h"
 
 namespace vmc {
 
-cudaError_t launch_gram_tc(const __nv_bfloat16*, const __nv_bfloat16*, int64_t, int64_t, int64_t,
-                           double, double2*, bool, unsigned*, cudaStream_t) {
-  return cudaErrorNotSupported;
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 64;      // tile; BK = one 128-byte swizzle row of BF16
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * BK * 2;         // 16 KB per operand tile
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;     // A_hi, A_lo, B_hi, B_lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int THREADS = 128;
+constexpr int TMEM_COLS = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after 2^24 polls or ~2e9 SM cycles, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  for (uint32_t it = 0; it < (1u << 24); ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 255u) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > 2000000000ll) break;
+    }
+  }
+  *abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile written by TMA with 128-byte
+// swizzle: rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart (stride byte offset),
+// descriptor version 1, layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(1) << 16;                     // leading byte offset (unused for this layout)
+  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;                       // version
+  d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+}  // namespace tc
+
+__global__ void __launch_bounds__(tc::THREADS, 1)
+k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
+          int nk, int64_t P, double inv_n, double2* __restrict__ S, int mirror,
+          unsigned* status) {
+  using namespace tc;
+  extern __shared__ uint8_t gsm_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
+                                             ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars[0..STAGES): full, bars[STAGES..2 STAGES): empty, bars[2 STAGES]: accumulator done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  // tile (bm, bn), bn <= bm, from the triangular block index
+  const int64_t t = blockIdx.x;
+  int bm = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(bm + 1) * (bm + 2) / 2 <= t) ++bm;
+  while ((int64_t)bm * (bm + 1) / 2 > t) --bm;
+  const int bn = (int)(t - (int64_t)bm * (bm + 1) / 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(smem_u32(&bars[STAGES + s]), ((kb / STAGES) + 1) & 1, abort_flag))
+        break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const uint32_t full = smem_u32(&bars[s]);
+      mbar_expect_tx(full, STAGE_BYTES);
+      tma_load_2d(smem_u32(st + 0 * TILE_BYTES), &map_hi, kb * BK, bm * BM, full);
+      tma_load_2d(smem_u32(st + 1 * TILE_BYTES), &map_lo, kb * BK, bm * BM, full);
+      tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &map_hi, kb * BK, bn * BN, full);
+      tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &map_lo, kb * BK, bn * BN, full);
+      issued = kb + 1;
+    }
+    if (*abort_flag) {
+      // let the copies already in flight land before the CTA exits (bounded)
+      volatile int dummy = 0;
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        mbar_wait(smem_u32(&bars[kb % STAGES]), (kb / STAGES) & 1, &dummy);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(smem_u32(&bars[s]), (kb / STAGES) & 1, abort_flag)) break;
+      fence_after();
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const uint64_t ah = smem_desc_sw128(smem_u32(st + 0 * TILE_BYTES));
+      const uint64_t al = smem_desc_sw128(smem_u32(st + 1 * TILE_BYTES));
+      const uint64_t bh = smem_desc_sw128(smem_u32(st + 2 * TILE_BYTES));
+      const uint64_t bl = smem_desc_sw128(smem_u32(st + 3 * TILE_BYTES));
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
+        mma_bf16(tmem, ah + off, bh + off, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_bf16(tmem, ah + off, bl + off, idesc, 1u);
+        mma_bf16(tmem, al + off, bh + off, idesc, 1u);
+      }
+      mma_commit(smem_u32(&bars[STAGES + s]));    // frees the stage when these MMAs finish
+    }
+    mma_commit(smem_u32(&bars[2 * STAGES]));      // accumulator complete
+  }
+  __syncwarp();
+
+  // ---------------- epilogue: all 4 warps, TMEM lane = tile row ----------------
+  const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0, abort_flag) && !*abort_flag;
+  fence_after();
+  if (ok) {
+    const int r = warp * 32 + lane;                // tile row held by this thread
+    const bool even = (r & 1) == 0;
+    const int64_t k = (int64_t)bm * (BM / 2) + (r >> 1);
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        // row 2k holds G[2k][2l], G[2k][2l+1]; row 2k+1 holds G[2k+1][2l], G[2k+1][2l+1]
+        const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
+        const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
+        const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
+        const double re = even ? (double)mine0 + (double)oth1 : (double)oth0 + (double)mine1;
+        const double im = even ? (double)mine1 - (double)oth0 : (double)oth1 - (double)mine0;
+        const int64_t l = (int64_t)bn * (BN / 2) + (c0 >> 1) + q;
+        // Off-diagonal tiles: the even row writes S_kl, the odd row its mirror.  In a
+        // diagonal tile the accumulation order of (k,l) and (l,k) differs, so only l <= k
+        // is taken and mirrored, which keeps S exactly Hermitian.
+        if (k < P && l < P && (bm != bn || l <= k)) {
+          if (even) S[k * P + l] = make_double2(re * inv_n, (l == k) ? 0.0 : im * inv_n);
+          else if (mirror && l != k) S[l * P + k] = make_double2(re * inv_n, -im * inv_n);
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) flag_error(status, DEV_ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+static cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows,
+                            int64_t ld) {
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {tc::BK, tc::BM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                                      const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
+                           int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
+                           bool mirror, unsigned* status, cudaStream_t st) {
+  if (rows_pad % tc::BM != 0 || ld % tc::BK != 0 || ld < tc::BK) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(Xhi) | reinterpret_cast<uintptr_t>(Xlo)) & 15)
+    return cudaErrorNotSupported;
+  CUtensorMap mhi, mlo;
+  cudaError_t e;
+  if ((e = make_map(&mhi, Xhi, rows_pad, ld)) != cudaSuccess) return e;
+  if ((e = make_map(&mlo, Xlo, rows_pad, ld)) != cudaSuccess) return e;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t nt = rows_pad / tc::BM;
+  const int64_t tiles = nt * (nt + 1) / 2;
+  k_gram_tc<<<(unsigned)tiles, tc::THREADS, tc::SMEM_BYTES, st>>>(
+      mhi, mlo, (int)(ld / tc::BK), P, inv_n, S, mirror ? 1 : 0, status);
+  return cudaGetLastError();
 }
 
 }  // namespace vmc

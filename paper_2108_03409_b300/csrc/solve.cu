@@ -62,67 +62,82 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
 }
 
 // Factor the diagonal block (rows/cols k0..k0+kw) in shared memory and store its inverse.
+// 256 threads: column c is scaled, then the trailing lower triangle (r, cc), c < cc <= r,
+// is updated with all threads striding over it; the inverse is built row by row
+// (Linv[rr][c] = -sum_{m=c}^{rr-1} L[rr][m] Linv[m][c] / L[rr][rr]) with four threads per
+// column sharing the sum.
+constexpr int POTRF_THREADS = 256;
+
 template <typename C>
-__global__ void __launch_bounds__(NB) k_potrf_diag(C* __restrict__ A, int64_t P, int64_t k0,
-                                                   int kw, C* __restrict__ Dinv,
-                                                   unsigned* status) {
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A, int64_t P,
+                                                              int64_t k0, int kw,
+                                                              C* __restrict__ Dinv,
+                                                              unsigned* status) {
   typedef typename RealOf<C>::T R;
   extern __shared__ unsigned char psm[];
   C* a = reinterpret_cast<C*>(psm);           // [NB][NB+1]
   C* inv = a + NB * (NB + 1);                 // [NB][NB+1]
-  const int r = threadIdx.x;
-  if (r < kw)
-    for (int c = 0; c <= r; ++c) a[r * (NB + 1) + c] = A[(k0 + r) * P + k0 + c];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
+    const int r = e / NB, c = e % NB;
+    a[r * (NB + 1) + c] = (r < kw && c <= r) ? A[(k0 + r) * P + k0 + c] : mk<C>(0.0, 0.0);
+    inv[r * (NB + 1) + c] = mk<C>(0.0, 0.0);
+  }
   __syncthreads();
   bool bad = false;
   for (int c = 0; c < kw; ++c) {
     R d = a[c * (NB + 1) + c].x;
     if (!(d > (R)0) || !isfinite(d)) { bad = true; d = (R)1; }
     const R lcc = sqrt(d);
-    __syncthreads();
-    if (r > c && r < kw) {
+    const R ilcc = (R)1 / lcc;
+    __syncthreads();                          // everyone has read the pivot
+    for (int r = c + 1 + tid; r < kw; r += POTRF_THREADS) {
       C v = a[r * (NB + 1) + c];
-      v.x /= lcc;
-      v.y /= lcc;
+      v.x *= ilcc;
+      v.y *= ilcc;
       a[r * (NB + 1) + c] = v;
     }
+    if (tid == 0) a[c * (NB + 1) + c] = mk<C>((double)lcc, 0.0);
     __syncthreads();
-    if (r == c) a[c * (NB + 1) + c] = mk<C>((double)lcc, 0.0);
-    if (r > c && r < kw) {
-      const C lrc = a[r * (NB + 1) + c];
-      for (int cc = c + 1; cc <= r; ++cc) {
-        C v = a[r * (NB + 1) + cc];
-        const C lcc2 = a[cc * (NB + 1) + c];
-        // v -= l_rc * conj(l_cc,c)
-        v.x -= lrc.x * lcc2.x + lrc.y * lcc2.y;
-        v.y -= lrc.y * lcc2.x - lrc.x * lcc2.y;
-        a[r * (NB + 1) + cc] = v;
-      }
+    const int m = kw - c - 1;
+    for (int e = tid; e < m * m; e += POTRF_THREADS) {
+      const int rr = c + 1 + e / m, cc = c + 1 + e % m;
+      if (cc > rr) continue;
+      const C lr = a[rr * (NB + 1) + c], lc = a[cc * (NB + 1) + c];
+      C v = a[rr * (NB + 1) + cc];
+      v.x -= lr.x * lc.x + lr.y * lc.y;       // v -= l_rc * conj(l_cc,c)
+      v.y -= lr.y * lc.x - lr.x * lc.y;
+      a[rr * (NB + 1) + cc] = v;
     }
     __syncthreads();
   }
-  if (bad && r == 0) flag_error(status, DEV_ERR_NUMERIC);
-  if (r < kw)
-    for (int c = 0; c <= r; ++c) A[(k0 + r) * P + k0 + c] = a[r * (NB + 1) + c];
-  // inverse of the lower-triangular block: thread c owns column c
-  {
-    const int c = threadIdx.x;
-    if (c < kw) {
-      for (int rr = 0; rr < kw; ++rr) inv[rr * (NB + 1) + c] = mk<C>(0.0, 0.0);
-      const C lcc = a[c * (NB + 1) + c];
-      inv[c * (NB + 1) + c] = mk<C>(1.0 / (double)lcc.x, 0.0);
-      for (int rr = c + 1; rr < kw; ++rr) {
-        C s = mk<C>(0.0, 0.0);
-        for (int m = c; m < rr; ++m) cfma(s, a[rr * (NB + 1) + m], inv[m * (NB + 1) + c]);
-        const R lrr = a[rr * (NB + 1) + rr].x;
-        inv[rr * (NB + 1) + c] = mk<C>(-(double)s.x / (double)lrr, -(double)s.y / (double)lrr);
-      }
-    }
+  if (bad && tid == 0) flag_error(status, DEV_ERR_NUMERIC);
+  for (int e = tid; e < kw * kw; e += POTRF_THREADS) {
+    const int r = e / kw, c = e % kw;
+    if (c <= r) A[(k0 + r) * P + k0 + c] = a[r * (NB + 1) + c];
   }
+  // inverse of the lower-triangular block, row by row
+  if (tid < kw) inv[tid * (NB + 1) + tid] = mk<C>(1.0 / (double)a[tid * (NB + 1) + tid].x, 0.0);
   __syncthreads();
-  if (r < kw)
-    for (int c = 0; c < NB; ++c)
-      Dinv[r * NB + c] = (c < kw) ? inv[r * (NB + 1) + c] : mk<C>(0.0, 0.0);
+  const int col = tid >> 2, part = tid & 3;
+  for (int rr = 1; rr < kw; ++rr) {
+    C s = mk<C>(0.0, 0.0);
+    if (col < rr)
+      for (int mm = col + part; mm < rr; mm += 4) cfma(s, a[rr * (NB + 1) + mm], inv[mm * (NB + 1) + col]);
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
+    if (col < rr && part == 0) {
+      const R lrr = a[rr * (NB + 1) + rr].x;
+      inv[rr * (NB + 1) + col] = mk<C>(-(double)s.x / (double)lrr, -(double)s.y / (double)lrr);
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
+    const int r = e / NB, c = e % NB;
+    Dinv[e] = (r < kw && c < kw) ? inv[r * (NB + 1) + c] : mk<C>(0.0, 0.0);
+  }
 }
 
 // Panel: X = B L_kk^{-H}, X[r][c] = sum_{m<=c} B[r][m] conj(Linv[c][m]) for the rows
@@ -362,7 +377,7 @@ static cudaError_t factor(C* A, C* Dinv, int64_t P, unsigned* status, cudaStream
   for (int64_t kb = 0; kb < nblk; ++kb) {
     const int64_t k0 = kb * NB;
     const int kw = (int)std::min<int64_t>(NB, P - k0);
-    k_potrf_diag<C><<<1, NB, s2, st>>>(A, P, k0, kw, Dinv + kb * NB * NB, status);
+    k_potrf_diag<C><<<1, POTRF_THREADS, s2, st>>>(A, P, k0, kw, Dinv + kb * NB * NB, status);
     ++*launches;
     const int64_t rest = P - k0 - kw;
     if (rest > 0) {
