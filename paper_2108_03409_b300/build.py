@@ -52,8 +52,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
         for rc, cmd in zip(ex.map(subprocess.call, cmds), cmds):
             if rc != 0:
                 raise subprocess.CalledProcessError(rc, cmd)
-    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", LIB, *objs,
-           "-lcuda"]
+    cmd = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", LIB, *objs]
     subprocess.check_call(cmd)
     return LIB
 

@@ -14,6 +14,7 @@
 // mbarrier wait is bounded (iteration and clock limits); on expiry the kernel records
 // DEV_ERR_TIMEOUT, skips the remaining work, frees its tensor memory and returns.
 #include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "vmc_device.cuh"
 #include "vmc_internal.h"
@@ -262,13 +263,31 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
+// cuTensorMapEncodeTiled is a driver-API function; it is looked up through the runtime so
+// that the library has no link-time dependency on libcuda (it still loads on machines
+// without a GPU driver, where only argument checking is possible).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
 static cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows,
                             int64_t ld) {
+  PFN_cuTensorMapEncodeTiled_v12000 encode = encode_tiled();
+  if (!encode) return cudaErrorNotSupported;
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
   cuuint32_t box[2] = {tc::BK, tc::BM};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = cuTensorMapEncodeTiled(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                                       const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
                                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
