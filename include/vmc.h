@@ -180,6 +180,33 @@ int64_t vmc_kernel_launches(const vmc_ctx* ctx);
 int64_t vmc_num_samples(const vmc_ctx* ctx);
 int64_t vmc_num_params(const vmc_ctx* ctx, int lattice);
 
+/* The <O> / F reduction of vmc_grad without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc, for
+ * example code running inside a framework that has already reserved the GPU's memory
+ * for its own pool, or a step loop that must not allocate after start-up.  It needs no
+ * context; the caller passes every input and output:
+ *   spins      dev int8 [n][N]
+ *   tanh_theta dev float [n][M][2]   (tanh theta_j of each sample, i.e. O_{b_j})
+ *   eloc       dev float [n][2]
+ *   F_out      dev double [P][2]     F_k = <O_k^* E_loc> - <O_k^*><E_loc>
+ *   meanO_out  dev double [P][2] or NULL   <O_k>
+ *   stream     cudaStream_t (NULL = legacy default stream); nothing is synchronised.
+ * with P = N + M + N*M and the parameter order of this header.
+ * Scratch: one file-scope device array of 2^21 doubles (16 MiB) that every GPU loading
+ * the library holds until the process exits.  The call needs
+ * 8 + ceil(n/1024) * 4 * (M+1) * (N+1) doubles of it and returns VMC_ERR_ARG when that
+ * exceeds the array (e.g. N = 64, M = 128 allows n <= 62 * 1024).  It also returns
+ * VMC_ERR_ARG for NULL inputs or sizes outside 1 <= N <= 1024, 1 <= M <= 512, n >= 1, and
+ * VMC_ERR_CUDA if a launch fails.  Non-finite inputs give non-finite outputs (no status
+ * word is kept).
+ * The first call on a device looks up the array's device address with that device
+ * current (a one-time set-up per device); make that first call before any stream
+ * capture.  All calls share the array and leave their partial sums in it: two calls
+ * whose work overlaps on the GPU (different streams, no ordering) race on it. */
+vmc_status vmc_force_noalloc(const int8_t* spins, const float* tanh_theta, const float* eloc,
+                             int64_t n, int N, int M, double* F_out, double* meanO_out,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -60,7 +60,7 @@ class vmc_sr_stats(ctypes.Structure):
 EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
             "vmc_set_chains", "vmc_get_chains", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
             "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
-            "vmc_num_samples", "vmc_num_params"]
+            "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc"]
 
 _lib = None
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "vmc_kernel_launches": (i64, [P]),
         "vmc_num_samples": (i64, [P]),
         "vmc_num_params": (i64, [P, i32]),
+        "vmc_force_noalloc": (i32, [P, P, P, i64, i32, i32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -227,3 +228,11 @@ def vmc_num_samples(ctx) -> int:
 
 def vmc_num_params(ctx, lattice) -> int:
     return int(load().vmc_num_params(ctx, lattice))
+
+
+def vmc_force_noalloc(spins, tanh_theta, eloc, N, M, F_out, meanO_out=None, stream=0):
+    """F (and optionally <O>) without device allocation; scratch is a fixed static array."""
+    st = load().vmc_force_noalloc(_ptr(spins), _ptr(tanh_theta), _ptr(eloc), spins.shape[0], N, M,
+                                  _ptr(F_out), _ptr(meanO_out), ctypes.c_void_p(stream or None))
+    if st != VMC_OK:
+        raise VmcError(st, "vmc_force_noalloc failed")
