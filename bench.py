@@ -34,11 +34,21 @@ sys.path.insert(0, ROOT)
 METRIC = ("effective MC samples/s incl. E_loc+O_k and SR steps/s vs plain FP32 path at "
           "|dE/N|<=1e-4")
 
-LX = LY = 8
-ALPHA = 2
-CHAINS = 8192
-SHIFT = 1e-3
 DT = 0.02
+
+# workloads: (model, Lx, Ly, J, h, alpha, chains, samples per chain, shift, solver)
+WORKLOADS = {
+    "heis2d_8x8_alpha2_c8192": dict(model=1, Lx=8, Ly=8, J=1.0, h=0.0, alpha=2, chains=8192,
+                                    spc=1, shift=1e-3, solver="tc", marshall=True),
+    "heis2d_16x16_alpha2_c65536": dict(model=1, Lx=16, Ly=16, J=1.0, h=0.0, alpha=2,
+                                       chains=65536, spc=1, shift=1e-3, solver="cg",
+                                       marshall=True),
+    "tfim1d_N10_alpha1_c256": dict(model=0, Lx=10, Ly=1, J=1.0, h=1.0, alpha=1, chains=256,
+                                   spc=200, shift=1e-4, solver="mixed", marshall=False),
+}
+DEFAULT_WORKLOAD = "heis2d_8x8_alpha2_c8192"
+W = WORKLOADS[DEFAULT_WORKLOAD]
+LX, LY, ALPHA, CHAINS, SHIFT = W["Lx"], W["Ly"], W["alpha"], W["chains"], W["shift"]
 
 
 def peaks():
@@ -170,6 +180,9 @@ def run_reference(args):
 # our arm
 # ----------------------------------------------------------------------------------------
 def run_ours(args):
+    global LX, LY, ALPHA, CHAINS, SHIFT
+    wl = WORKLOADS[args.workload]
+    LX, LY, ALPHA, CHAINS, SHIFT = wl["Lx"], wl["Ly"], wl["alpha"], wl["chains"], wl["shift"]
     import torch
     from paper_2108_03409_b300 import build as vbuild
     from paper_2108_03409_b300 import inputs, stats as vstats, vmc
@@ -181,18 +194,22 @@ def run_ours(args):
     torch.cuda.set_device(local)
     vbuild.build()
     prec = {"fp32": vmc.PREC_FP32, "bf16split": vmc.PREC_BF16SPLIT}[args.precision]
-    solver = {"fp64": vmc.SOLVER_CHOLESKY_FP64, "mixed": vmc.SOLVER_CHOLESKY_MIXED}[args.solver]
+    solver_name = args.solver or wl["solver"]
+    solver = {"fp64": vmc.SOLVER_CHOLESKY_FP64, "mixed": vmc.SOLVER_CHOLESKY_MIXED,
+              "tc": vmc.SOLVER_CHOLESKY_TC, "cg": vmc.SOLVER_CG}[solver_name]
     N, M = LX * LY, ALPHA * LX * LY
     P = N + M + N * M
     stream = torch.cuda.current_stream()
+    Ns = CHAINS * wl["spc"]
+    cg = solver == vmc.SOLVER_CG
     cfg = vmc.make_config(seed=1 + rank, n_chains=CHAINS, therm_sweeps=20, sweeps_per_sample=1,
-                          samples_per_chain=1, precision=prec, solver=solver, shift=SHIFT,
-                          cg_tol=1e-10, cg_maxit=50)
-    lat = vmc.make_lattice(vmc.MODEL_HEISENBERG, LX, LY, 1.0, 0.0, ALPHA)
+                          samples_per_chain=wl["spc"], precision=prec, solver=solver, shift=SHIFT,
+                          cg_tol=1e-6 if cg else 1e-10, cg_maxit=100 if cg else 50)
+    lat = vmc.make_lattice(wl["model"], LX, LY, wl["J"], wl["h"], ALPHA)
     ctx = vmc.vmc_init(cfg, [lat], stream.cuda_stream)
-    p0 = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(LX, LY))
+    p0 = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(LX, LY) if wl["marshall"] else None)
     vmc.vmc_set_params(ctx, 0, p0)
-    vmc.vmc_set_chains(ctx, 0, inputs.random_sz0_spins(CHAINS, N, seed=99 + rank))
+    vmc.vmc_set_chains(ctx, 0, inputs.initial_spins(wl["model"], CHAINS, N, seed=99 + rank))
 
     def barrier():
         if ws > 1:
@@ -235,18 +252,20 @@ def run_ours(args):
 
     # integrated autocorrelation time of E_loc at the final parameters (sampler only)
     T = 200
+    cs = min(CHAINS, 2048)
     el = torch.zeros((T * CHAINS, 2), dtype=torch.float32, device="cuda")
     vmc.vmc_sample(ctx, 0, 0, T, None, None, el)
-    e_series = el[:, 0].reshape(T, CHAINS).double().cpu().numpy()
-    tau = vstats.integrated_autocorr_time(e_series[:, :2048])
+    e_series = el[:, 0].reshape(T, CHAINS)[:, :cs].double().cpu().numpy()
+    del el
+    tau = vstats.integrated_autocorr_time(e_series)
 
     ms_samp = statistics.mean(s.ms_sample + s.ms_grad for s in st_list)
     ms_gram = statistics.mean(s.ms_gram for s in st_list)
-    eff = CHAINS / (ms_samp / 1e3) / (2 * tau)
+    eff = Ns / (ms_samp / 1e3) / (2 * tau)
     pk, pk_kind = peaks()
     # dominant kernel: the S contraction.  Algorithmic work of the Hermitian half of the
     # complex Gram S = Obar^H Obar: 4 P^2 Ns real flops (8 P^2 Ns for the full matrix).
-    alg_flops = 4.0 * P * P * CHAINS
+    alg_flops = 4.0 * P * P * Ns
     achieved = alg_flops / (ms_gram / 1e3) / 1e12
     if prec == vmc.PREC_BF16SPLIT:
         roof = {"bound": "tensor", "peak": pk.get("bf16_tflops_sustained", 1388.0),
@@ -266,9 +285,9 @@ def run_ours(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if prec == vmc.PREC_FP32 else "bf16x3-split/f32-accum",
            "data": "synthetic",
-           "config": {"workload": "heis2d_8x8_alpha2_c8192", "N": N, "M": M, "P": P,
-                      "chains": CHAINS, "Ns": CHAINS, "shift": SHIFT, "dt": DT,
-                      "precision": args.precision, "solver": args.solver,
+           "config": {"workload": args.workload, "N": N, "M": M, "P": P,
+                      "chains": CHAINS, "Ns": Ns, "shift": SHIFT, "dt": DT,
+                      "precision": args.precision, "solver": solver_name,
                       "l2": "working set (S 1.1 GB, X 0.55 GB) larger than L2; no flush",
                       "parallelism": f"replicas x{ws}"},
            "eff_samples_per_s": {"value": eff * ws, "unit": "samples/s", "tau_int_E": tau,
@@ -283,7 +302,10 @@ def run_ours(args):
                    "d2h_bytes_per_step": P * 16 + 4 * 8 * 0 + 64},
            "gpu_launches": launches,
            "clocks": clk.summary()}
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if cg:
+        out["roofline"] = None
+        out["note"] = "CG workload: per-iteration kernels reported in phases_ms; no dense S"
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == DEFAULT_WORKLOAD:
         out["cpu_baseline"] = cpu_baseline()
     vmc.vmc_destroy(ctx)
     if rank == 0:
@@ -298,8 +320,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16split"])
-    ap.add_argument("--solver", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="bf16split", choices=["fp32", "bf16split"])
+    ap.add_argument("--solver", default=None, choices=["mixed", "tc", "fp64", "cg"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -47,7 +47,11 @@ typedef enum {
 
 enum { VMC_MODEL_TFIM = 0, VMC_MODEL_HEISENBERG = 1 };
 enum { VMC_PREC_FP32 = 0, VMC_PREC_BF16SPLIT = 1 };
-enum { VMC_SOLVER_CHOLESKY_FP64 = 0, VMC_SOLVER_CG = 1, VMC_SOLVER_CHOLESKY_MIXED = 2 };
+/* Solvers of S~ x = F: FP64 Cholesky; matrix-free CG; FP32 Cholesky + FP64 iterative
+ * refinement; the same with the trailing (Schur) updates of 256-wide panels on the tensor
+ * cores (BF16 hi/lo split) + FP64 iterative refinement. */
+enum { VMC_SOLVER_CHOLESKY_FP64 = 0, VMC_SOLVER_CG = 1, VMC_SOLVER_CHOLESKY_MIXED = 2,
+       VMC_SOLVER_CHOLESKY_TC = 3 };
 enum { VMC_SHIFT_MULTIPLICATIVE = 0, VMC_SHIFT_ADDITIVE = 1 };
 
 /* One lattice (Hamiltonian + RBM size).
@@ -165,6 +169,16 @@ vmc_status vmc_qfm(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, in
  * the factorisation meets a non-positive pivot or the iteration does not converge. */
 vmc_status vmc_solve(vmc_ctx* ctx, int lattice, const double* S, const double* F, double* x,
                      int* iters, double* relres);
+
+/* Matrix-free conjugate gradient for S~ x = F (section "Diagonal shift": the shift works
+ * with iterative solvers) on the sample set `spins` (dev int8 [n][N], n <= Ns):
+ *   S~ v = (1/n) Obar^H (Obar v) + D v,  D = shift * diag(S) (multiplicative) or shift,
+ * with Obar v and Obar^H u evaluated from the RBM structure (O = [s | t | t (x) s]), never
+ * forming S.  x0 = 0; stops when ||r|| <= cg_tol ||F|| or after cg_maxit iterations.
+ * F, x: dev double [P][2].  iters / relres (host, may be NULL) report the finish
+ * (relres is the recursively updated residual).  Synchronises once per iteration. */
+vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                        const double* F, double* x, int* iters, double* relres);
 
 /* One full SR step (Algorithm 1, then the Euler update theta <- theta - dt x of
  * imaginary-time TDVP, Eq. stochastic_reconfiguration): sample Ns configurations, local

@@ -53,6 +53,7 @@ struct vmc_ctx {
   __nv_bfloat16* Xlo = nullptr;
   double2* S = nullptr;           // [Pmax][Pmax]
   SolveWork sw{};
+  CgWork cg{};
   unsigned* status = nullptr;
   unsigned long long* n_accept = nullptr;
   int64_t launches = 0;
@@ -169,9 +170,10 @@ vmc_status solve_core(vmc_ctx* ctx, LatticeState& L, const double2* S, const dou
                            &ctx->launches), "cholesky_fp64");
     CK(residual_fp64(S, F, x, c.shift, c.shift_mode, ctx->sw, ctx->st, &rel), "residual");
     ctx->launches += 2;
-  } else if (c.solver == VMC_SOLVER_CHOLESKY_MIXED) {
-    CK(solve_cholesky_mixed(S, F, x, c.shift, c.shift_mode, c.cg_tol, c.cg_maxit, ctx->sw,
-                            ctx->status, ctx->st, &ctx->launches, &it, &rel), "cholesky_mixed");
+  } else if (c.solver == VMC_SOLVER_CHOLESKY_MIXED || c.solver == VMC_SOLVER_CHOLESKY_TC) {
+    CK(solve_cholesky_mixed(S, F, x, c.shift, c.shift_mode, c.cg_tol, c.cg_maxit,
+                            c.solver == VMC_SOLVER_CHOLESKY_TC, ctx->sw, ctx->status, ctx->st,
+                            &ctx->launches, &it, &rel), "cholesky_mixed");
   } else {
     return fail(ctx, VMC_ERR_ARG, "solver not available for a dense S");
   }
@@ -179,7 +181,7 @@ vmc_status solve_core(vmc_ctx* ctx, LatticeState& L, const double2* S, const dou
   if (relres) *relres = rel;
   vmc_status s = check_status(ctx, "solve");
   if (s != VMC_OK) return s;
-  if (!(rel == rel) || (c.solver == VMC_SOLVER_CHOLESKY_MIXED && !(rel <= c.cg_tol)))
+  if (!(rel == rel) || (c.solver != VMC_SOLVER_CHOLESKY_FP64 && !(rel <= c.cg_tol)))
     return fail(ctx, VMC_ERR_NUMERIC, "iterative refinement did not reach the tolerance");
   return VMC_OK;
 }
@@ -196,7 +198,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
       cfg->therm_sweeps < 0 || cfg->sweep_len < 0)
     return VMC_ERR_ARG;
   if (cfg->precision != VMC_PREC_FP32 && cfg->precision != VMC_PREC_BF16SPLIT) return VMC_ERR_ARG;
-  if (cfg->solver < 0 || cfg->solver > 2 || (cfg->shift_mode != 0 && cfg->shift_mode != 1))
+  if (cfg->solver < 0 || cfg->solver > 3 || (cfg->shift_mode != 0 && cfg->shift_mode != 1))
     return VMC_ERR_ARG;
   if (!(cfg->shift >= 0.0)) return VMC_ERR_ARG;
   for (int l = 0; l < n_lattices; ++l) {
@@ -249,6 +251,21 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
       (e = dalloc(ctx, &ctx->x, ctx->Pmax)) || (e = dalloc(ctx, &ctx->status, 1)) ||
       (e = dalloc(ctx, &ctx->n_accept, 1)))
     return oom(e);
+  {
+    CgWork& w = ctx->cg;
+    const int64_t P = ctx->Pmax;
+    if ((e = dalloc(ctx, &w.r, P)) || (e = dalloc(ctx, &w.p, P)) || (e = dalloc(ctx, &w.q, P)) ||
+        (e = dalloc(ctx, &w.y, P)) || (e = dalloc(ctx, &w.z, P)) ||
+        (e = dalloc(ctx, &w.meanO_c, P)) || (e = dalloc(ctx, &w.D, P)) ||
+        (e = dalloc(ctx, &w.Minv, P)) || (e = dalloc(ctx, &w.t2, ctx->Mmax)) ||
+        (e = dalloc(ctx, &w.va, ctx->Nmax)) || (e = dalloc(ctx, &w.vb, ctx->Mmax)) ||
+        (e = dalloc(ctx, &w.V, (size_t)ctx->Nmax * ctx->Mmax)) || (e = dalloc(ctx, &w.u, Ns)) ||
+        (e = dalloc(ctx, &w.upart, (size_t)cg_partial_floats2(Ns, ctx->Mmax))) ||
+        (e = dalloc(ctx, &w.ustats, 8)) || (e = dalloc(ctx, &w.dpart, 256)) ||
+        (e = dalloc(ctx, &w.c2, 8)) || (e = dalloc(ctx, &w.sc, 8)))
+      return oom(e);
+    w.mpart = ctx->partial;
+  }
   if (ctx->dense) {
     const int64_t P = ctx->Pmax;
     ctx->rows_pad = (2 * P + 127) / 128 * 128;
@@ -259,15 +276,24 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &ctx->Xlo, xs)) || (e = dalloc(ctx, &ctx->S, (size_t)P * P)) ||
         (e = dalloc(ctx, &ctx->sw.r, P)) || (e = dalloc(ctx, &ctx->sw.c, P)) ||
         (e = dalloc(ctx, &ctx->sw.r32, P)) || (e = dalloc(ctx, &ctx->sw.y32, P)) ||
-        (e = dalloc(ctx, &ctx->sw.c32, P)) || (e = dalloc(ctx, &ctx->sw.scal, 8)))
+        (e = dalloc(ctx, &ctx->sw.c32, P)) || (e = dalloc(ctx, &ctx->sw.scal, 8)) ||
+        (e = dalloc(ctx, &ctx->sw.bar, 4)))
       return oom(e);
+    ctx->sw.Xhi = ctx->Xhi;
+    ctx->sw.Xlo = ctx->Xlo;
+    ctx->sw.x_elems = (int64_t)xs;
+    const size_t nsb = (size_t)((P + 255) / 256);
     if (cfg->solver == VMC_SOLVER_CHOLESKY_FP64) {
       if ((e = dalloc(ctx, &ctx->sw.A64, (size_t)P * P)) ||
-          (e = dalloc(ctx, &ctx->sw.D64, (size_t)nblk * 64 * 64)))
+          (e = dalloc(ctx, &ctx->sw.D64, (size_t)nblk * 64 * 64)) ||
+          (e = dalloc(ctx, &ctx->sw.T64f, nsb * 256 * 256)) ||
+          (e = dalloc(ctx, &ctx->sw.T64b, nsb * 256 * 256)))
         return oom(e);
     } else {
       if ((e = dalloc(ctx, &ctx->sw.A32, (size_t)P * P)) ||
-          (e = dalloc(ctx, &ctx->sw.D32, (size_t)nblk * 64 * 64)))
+          (e = dalloc(ctx, &ctx->sw.D32, (size_t)nblk * 64 * 64)) ||
+          (e = dalloc(ctx, &ctx->sw.T32f, nsb * 256 * 256)) ||
+          (e = dalloc(ctx, &ctx->sw.T32b, nsb * 256 * 256)))
         return oom(e);
     }
   }
@@ -458,10 +484,33 @@ vmc_status vmc_solve(vmc_ctx* ctx, int lattice, const double* S, const double* F
                     reinterpret_cast<double2*>(x), iters, relres);
 }
 
+vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, const double* F,
+                        double* x, int* iters, double* relres) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 1 || n > ctx->Ns || !spins || !F || !x) return fail(ctx, VMC_ERR_ARG, "bad arguments");
+  LatticeState& L = ctx->lats[lattice];
+  const vmc_config& c = ctx->cfg;
+  CK(launch_theta_tanh(rbm_of(L), spins, n, ctx->s_T, ctx->st), "theta_tanh");
+  CK(launch_moments(spins, ctx->s_T, nullptr, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
+                    nullptr, ctx->st), "moments");
+  ctx->launches += 3;
+  CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO, nullptr};
+  CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
+  int it = 0;
+  double rel = 0.0;
+  CK(cg_solve(pb, reinterpret_cast<const double2*>(F), reinterpret_cast<double2*>(x), c.cg_tol,
+              c.cg_maxit, ctx->cg, ctx->st, &ctx->launches, &it, &rel), "cg_solve");
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  if ((s = check_status(ctx, "cg_solve"))) return s;
+  if (!(rel == rel)) return fail(ctx, VMC_ERR_NUMERIC, "CG produced a non-finite residual");
+  return VMC_OK;
+}
+
 vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats) {
   vmc_status s = lattice_ok(ctx, lattice);
   if (s) return s;
-  if (!ctx->dense) return fail(ctx, VMC_ERR_STATE, "CG SR step is not available in this build");
   LatticeState& L = ctx->lats[lattice];
   const vmc_config& c = ctx->cfg;
   const int64_t Ns = ctx->Ns;
@@ -497,13 +546,30 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   CK(launch_estats(ctx->s_E, Ns, ctx->estats, ctx->status, ctx->st), "estats");
   ++ctx->launches;
   CK(cudaEventRecord(ctx->ev[2], ctx->st), "sr_step");
-  // 3. S (moments + centred X + Gram)
-  if ((s = qfm_core(ctx, L, ctx->s_spins, ctx->s_E, Ns, c.precision, ctx->S, true))) return s;
-  CK(cudaEventRecord(ctx->ev[3], ctx->st), "sr_step");
-  // 4. solve (synchronises)
   int iters = 0;
   double rel = 0.0;
-  if ((s = solve_core(ctx, L, ctx->S, ctx->F, ctx->x, &iters, &rel))) return s;
+  if (ctx->dense) {
+    // 3. S (moments + centred X + Gram)
+    if ((s = qfm_core(ctx, L, ctx->s_spins, ctx->s_E, Ns, c.precision, ctx->S, true))) return s;
+    CK(cudaEventRecord(ctx->ev[3], ctx->st), "sr_step");
+    // 4. solve (synchronises)
+    if ((s = solve_core(ctx, L, ctx->S, ctx->F, ctx->x, &iters, &rel))) return s;
+  } else {
+    // 3. <O>, F and diag(S) (S itself is never formed)
+    CK(launch_moments(ctx->s_spins, ctx->s_T, ctx->s_E, ctx->estats, Ns, L.N, L.M, ctx->partial,
+                      ctx->meanO, ctx->F, ctx->st), "moments");
+    ctx->launches += 2;
+    CgProblem pb{ctx->s_spins, ctx->s_T, Ns, L.N, L.M, ctx->meanO, nullptr};
+    CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
+    cudaEventRecord(ctx->ev[6], ctx->st);
+    cudaEventRecord(ctx->ev[7], ctx->st);
+    CK(cudaEventRecord(ctx->ev[3], ctx->st), "sr_step");
+    // 4. matrix-free CG (synchronises once per iteration)
+    CK(cg_solve(pb, ctx->F, ctx->x, c.cg_tol, c.cg_maxit, ctx->cg, ctx->st, &ctx->launches, &iters,
+                &rel), "cg_solve");
+    if ((s = check_status(ctx, "cg"))) return s;
+    if (!(rel == rel)) return fail(ctx, VMC_ERR_NUMERIC, "CG produced a non-finite residual");
+  }
   CK(cudaEventRecord(ctx->ev[4], ctx->st), "sr_step");
   // 5. Euler update of the FP64 master parameters, refresh the FP32 copies
   CK(launch_update(L.params, ctx->x, L.P, dt, ctx->st), "update");

@@ -140,8 +140,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 __global__ void __launch_bounds__(tc::THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-          int nk, int64_t P, double inv_n, double2* __restrict__ S, int mirror,
-          unsigned* status) {
+          int nk, int nt, int64_t P, double inv_n, double2* __restrict__ S, int mirror,
+          float2* __restrict__ A32, int64_t ldA, int64_t off, unsigned* status) {
   using namespace tc;
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
@@ -151,12 +151,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
-  // tile (bm, bn), bn <= bm, from the triangular block index
-  const int64_t t = blockIdx.x;
-  int bm = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(bm + 1) * (bm + 2) / 2 <= t) ++bm;
-  while ((int64_t)bm * (bm + 1) / 2 > t) --bm;
-  const int bn = (int)(t - (int64_t)bm * (bm + 1) / 2);
+  // tile (bm, bn), bn <= bm, grouped rasterisation (12 tile rows per group)
+  int bm, bn;
+  grouped_tri_tile(blockIdx.x, nt, 12, &bm, &bn);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -231,21 +228,54 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     for (int c0 = 0; c0 < BN; c0 += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      double re[16], im[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         // row 2k holds G[2k][2l], G[2k][2l+1]; row 2k+1 holds G[2k+1][2l], G[2k+1][2l+1]
         const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
         const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
         const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
-        const double re = even ? (double)mine0 + (double)oth1 : (double)oth0 + (double)mine1;
-        const double im = even ? (double)mine1 - (double)oth0 : (double)oth1 - (double)mine0;
-        const int64_t l = (int64_t)bn * (BN / 2) + (c0 >> 1) + q;
+        re[q] = even ? (double)mine0 + (double)oth1 : (double)oth0 + (double)mine1;
+        im[q] = even ? (double)mine1 - (double)oth0 : (double)oth1 - (double)mine0;
+      }
+      const int64_t l0 = (int64_t)bn * (BN / 2) + (c0 >> 1);
+      if (A32) {
+        // Schur-complement update of a Cholesky factor: rows of X are the real and
+        // imaginary parts of L's panel, so sum_m L_km conj(L_lm) = conj(fold);
+        // A[off+k][off+l] -= conj(fold) on l <= k (the diagonal stays real).  The even row
+        // updates the even q, the odd row the odd q; loads are issued before the stores.
+        if (k < P) {
+          float2* rowp = A32 + (off + k) * ldA + off + l0;
+          float2 cur[8];
+#pragma unroll
+          for (int h = 0; h < 8; ++h) {
+            const int q = 2 * h + (even ? 0 : 1);
+            const int64_t l = l0 + q;
+            if (l < P && (bm != bn || l <= k)) cur[h] = rowp[q];
+          }
+#pragma unroll
+          for (int h = 0; h < 8; ++h) {
+            const int q = 2 * h + (even ? 0 : 1);
+            const int64_t l = l0 + q;
+            if (l < P && (bm != bn || l <= k)) {
+              float2 a = cur[h];
+              a.x -= (float)re[q];
+              if (l != k) a.y += (float)im[q];
+              rowp[q] = a;
+            }
+          }
+        }
+      } else {
         // Off-diagonal tiles: the even row writes S_kl, the odd row its mirror.  In a
         // diagonal tile the accumulation order of (k,l) and (l,k) differs, so only l <= k
         // is taken and mirrored, which keeps S exactly Hermitian.
-        if (k < P && l < P && (bm != bn || l <= k)) {
-          if (even) S[k * P + l] = make_double2(re * inv_n, (l == k) ? 0.0 : im * inv_n);
-          else if (mirror && l != k) S[l * P + k] = make_double2(re * inv_n, -im * inv_n);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int64_t l = l0 + q;
+          if (k < P && l < P && (bm != bn || l <= k)) {
+            if (even) S[k * P + l] = make_double2(re[q] * inv_n, (l == k) ? 0.0 : im[q] * inv_n);
+            else if (mirror && l != k) S[l * P + k] = make_double2(re[q] * inv_n, -im[q] * inv_n);
+          }
         }
       }
     }
@@ -315,7 +345,29 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
   k_gram_tc<<<(unsigned)tiles, tc::THREADS, tc::SMEM_BYTES, st>>>(
-      mhi, mlo, (int)(ld / tc::BK), P, inv_n, S, mirror ? 1 : 0, status);
+      mhi, mlo, (int)(ld / tc::BK), (int)nt, P, inv_n, S, mirror ? 1 : 0, nullptr, 0, 0, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, int64_t rows_pad,
+                           int64_t K, int64_t n, float2* A32, int64_t ldA, int64_t off,
+                           unsigned* status, cudaStream_t st) {
+  if (rows_pad % tc::BM != 0 || K % tc::BK != 0 || K < tc::BK) return cudaErrorNotSupported;
+  CUtensorMap mhi, mlo;
+  cudaError_t e;
+  if ((e = make_map(&mhi, Xhi, rows_pad, K)) != cudaSuccess) return e;
+  if ((e = make_map(&mlo, Xlo, rows_pad, K)) != cudaSuccess) return e;
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t nt = rows_pad / tc::BM;
+  const int64_t tiles = nt * (nt + 1) / 2;
+  k_gram_tc<<<(unsigned)tiles, tc::THREADS, tc::SMEM_BYTES, st>>>(
+      mhi, mlo, (int)(K / tc::BK), (int)nt, n, 1.0, nullptr, 0, A32, ldA, off, status);
   return cudaGetLastError();
 }
 

@@ -76,8 +76,9 @@ __device__ __forceinline__ float2 warp_logpsi(const RbmDev& R, const int8_t* s, 
 }
 
 // sum over the warp's hidden slots of log[cosh(theta_k - d_k) / cosh(theta_k)], with
-// d_k = 2 s_i W_ki (+ 2 s_j W_kj for an exchange), as (log modulus, phase); the per-lane
-// partial product of four factors is turned into logs before the warp sum.
+// d_k = 2 s_i W_ki (+ 2 s_j W_kj for an exchange), as (log modulus, phase).  Each lane
+// multiplies its factors and takes one log at the end; the running product is folded into
+// the logs early only if it leaves [1e-15, 1e15] (checked every four factors).
 template <int MPL, bool PAIR>
 __device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
                                                  const float2 (&t)[MPL], int i, float si,
@@ -100,12 +101,17 @@ __device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
       }
       prod = cmul(prod, cosh_ratio(t[k], dr, di));
     }
-    if ((k & 3) == 3 || k == MPL - 1) {
-      lr += 0.5f * logf(fmaf(prod.x, prod.x, prod.y * prod.y));
-      li += atan2f(prod.y, prod.x);
-      prod = make_float2(1.f, 0.f);
+    if ((k & 3) == 3 && k != MPL - 1) {
+      const float m2 = fmaf(prod.x, prod.x, prod.y * prod.y);
+      if (m2 > 1e30f || m2 < 1e-30f) {
+        lr += 0.5f * logf(m2);
+        li += atan2f(prod.y, prod.x);
+        prod = make_float2(1.f, 0.f);
+      }
     }
   }
+  lr += 0.5f * logf(fmaf(prod.x, prod.x, prod.y * prod.y));
+  li += atan2f(prod.y, prod.x);
   return make_float2(warp_sum(lr), warp_sum(li));
 }
 
@@ -244,15 +250,49 @@ __global__ void k_ok_dense(const int8_t* __restrict__ spins, const float2* __res
 }
 
 // ---------------------------------------------------------------------------------------
-// a3/a4 + a6 (+ the t factors of a7): Metropolis sweeps with theta and t = tanh theta
-// cached in registers.  One warp per chain.  For a proposal s -> s' that changes theta by
-// -d_k (d_k = 2 s_i W_ki, plus 2 s_j W_kj for an exchange),
+// a3/a4 + a6 (+ the t factors of a7): Metropolis sweeps with t = tanh theta cached in
+// registers.  One warp per chain.  For a proposal s -> s' that changes theta by -d_k
+// (d_k = 2 s_i W_ki, plus 2 s_j W_kj for an exchange),
 //   psi(s')/psi(s) = exp(a-term) * prod_k [cosh d_k - t_k sinh d_k],
-// and the acceptance needs only its modulus squared.  Random numbers for 32 consecutive
-// steps are drawn in parallel (lane q draws step t0+q) and broadcast.  At every record
-// point theta is recomputed from the spins (no drift), and the sample's spins, log psi,
-// E_loc (fused, from the cached t) and t are written.
+// and the acceptance needs only its modulus squared.  On acceptance
+// t_k <- tanh(theta_k - d_k) = (t_k - tanh d_k) / (1 - t_k tanh d_k).  Random numbers for
+// 32 consecutive steps are drawn in parallel (lane q draws step t0+q) and broadcast.  At
+// every record point theta is recomputed from the spins (no drift), and the sample's
+// spins, log psi, E_loc (fused, from the cached t) and t are written.
 // ---------------------------------------------------------------------------------------
+template <int MPL>
+__device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, int lane,
+                                              float2 (&t)[MPL], bool want_logpsi) {
+  float lr = 0.f, li = 0.f;
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    const int hj = lane + 32 * k;
+    t[k] = make_float2(0.f, 0.f);
+    if (hj < R.M) {
+      float2 th = R.b[hj];
+      for (int i = 0; i < R.N; ++i) {
+        const float si = (float)s[i];
+        const float2 v = R.Wt[(int64_t)i * R.M + hj];
+        th.x = fmaf(si, v.x, th.x);
+        th.y = fmaf(si, v.y, th.y);
+      }
+      t[k] = tanh_c(th.x, th.y);
+      if (want_logpsi) {
+        const float2 lc = logcosh_c(th.x, th.y);
+        lr += lc.x;
+        li += lc.y;
+      }
+    }
+  }
+  if (!want_logpsi) return make_float2(0.f, 0.f);
+  for (int i = lane; i < R.N; i += 32) {
+    const float si = (float)s[i];
+    lr = fmaf(si, R.a[i].x, lr);
+    li = fmaf(si, R.a[i].y, li);
+  }
+  return make_float2(warp_sum(lr), warp_sum(li));
+}
+
 template <int MPL, bool HEIS>
 __global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
   extern __shared__ int8_t sm[];
@@ -267,10 +307,8 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
   for (int i = lane; i < N; i += 32) s[i] = A.chains[(int64_t)chain * N + i];
   __syncwarp();
 
-  float2 th[MPL], t[MPL];
-  warp_theta<MPL>(R, s, lane, th);
-#pragma unroll
-  for (int k = 0; k < MPL; ++k) t[k] = tanh_c(th[k].x, th[k].y);
+  float2 t[MPL];
+  warp_resync<MPL>(R, s, lane, t, false);
 
   const uint32_t K = HEIS ? (uint32_t)L.nb : (uint32_t)N;
   const int total = A.n_therm + A.n_samples * A.sweeps_per_sample;
@@ -298,27 +336,25 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
         }
         const float si = (float)s[i];
         const float two_re_da = HEIS ? -4.f * si * (R.a[i].x - R.a[j].x) : -4.f * si * R.a[i].x;
-        float dr[MPL], di[MPL];
         float lsum = 0.f, prod = 1.f;
 #pragma unroll
         for (int k = 0; k < MPL; ++k) {
           const int hj = lane + 32 * k;
-          dr[k] = 0.f;
-          di[k] = 0.f;
           if (hj < M) {
             const float2 wi = R.Wt[(int64_t)i * M + hj];
+            float dr, di;
             if (HEIS) {
               const float2 wj = R.Wt[(int64_t)j * M + hj];
-              dr[k] = 2.f * si * (wi.x - wj.x);
-              di[k] = 2.f * si * (wi.y - wj.y);
+              dr = 2.f * si * (wi.x - wj.x);
+              di = 2.f * si * (wi.y - wj.y);
             } else {
-              dr[k] = 2.f * si * wi.x;
-              di[k] = 2.f * si * wi.y;
+              dr = 2.f * si * wi.x;
+              di = 2.f * si * wi.y;
             }
-            const float2 r = cosh_ratio(t[k], dr[k], di[k]);
+            const float2 r = cosh_ratio(t[k], dr, di);
             prod *= fmaf(r.x, r.x, r.y * r.y);
           }
-          if ((k & 3) == 3 || k == MPL - 1) {
+          if ((k & 7) == 7 || k == MPL - 1) {
             lsum += logf(prod);
             prod = 1.f;
           }
@@ -327,10 +363,19 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
         if (logu < two_re_delta) {
 #pragma unroll
           for (int k = 0; k < MPL; ++k) {
-            if (lane + 32 * k < M) {
-              th[k].x -= dr[k];
-              th[k].y -= di[k];
-              t[k] = tanh_c(th[k].x, th[k].y);
+            const int hj = lane + 32 * k;
+            if (hj < M) {
+              const float2 wi = R.Wt[(int64_t)i * M + hj];
+              float dr, di;
+              if (HEIS) {
+                const float2 wj = R.Wt[(int64_t)j * M + hj];
+                dr = 2.f * si * (wi.x - wj.x);
+                di = 2.f * si * (wi.y - wj.y);
+              } else {
+                dr = 2.f * si * wi.x;
+                di = 2.f * si * wi.y;
+              }
+              t[k] = tanh_shift(t[k], dr, di);
             }
           }
           __syncwarp();
@@ -347,17 +392,16 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
     if (after > 0 && after % A.sweeps_per_sample == 0) {
       const int64_t rec = after / A.sweeps_per_sample - 1;
       const int64_t qs = rec * A.C + chain;
-      warp_theta<MPL>(R, s, lane, th);           // resynchronise the cache
+      const float2 lp = warp_resync<MPL>(R, s, lane, t, A.logpsi_out != nullptr);
+      if (A.t_out)
 #pragma unroll
-      for (int k = 0; k < MPL; ++k) {
-        t[k] = tanh_c(th[k].x, th[k].y);
-        const int hj = lane + 32 * k;
-        if (A.t_out && hj < M) A.t_out[qs * M + hj] = t[k];
-      }
+        for (int k = 0; k < MPL; ++k) {
+          const int hj = lane + 32 * k;
+          if (hj < M) A.t_out[qs * M + hj] = t[k];
+        }
       if (A.spins_out)
         for (int i = lane; i < N; i += 32) A.spins_out[qs * N + i] = s[i];
       if (A.logpsi_out) {
-        const float2 lp = warp_logpsi<MPL>(R, s, lane, th);
         if (lane == 0) A.logpsi_out[qs] = lp;
         bad |= !isfinite(lp.x) || !isfinite(lp.y);
       }

@@ -99,15 +99,25 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A,
     }
     if (tid == 0) a[c * (NB + 1) + c] = mk<C>((double)lcc, 0.0);
     __syncthreads();
-    const int m = kw - c - 1;
-    for (int e = tid; e < m * m; e += POTRF_THREADS) {
-      const int rr = c + 1 + e / m, cc = c + 1 + e % m;
-      if (cc > rr) continue;
-      const C lr = a[rr * (NB + 1) + c], lc = a[cc * (NB + 1) + c];
-      C v = a[rr * (NB + 1) + cc];
-      v.x -= lr.x * lc.x + lr.y * lc.y;       // v -= l_rc * conj(l_cc,c)
-      v.y -= lr.y * lc.x - lr.x * lc.y;
-      a[rr * (NB + 1) + cc] = v;
+    // trailing update: thread (ty, tx) owns rows ty + 16p and columns tx + 16q of the block
+    {
+      const int ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+      for (int pp = 0; pp < NB / 16; ++pp) {
+        const int rr = ty + 16 * pp;
+        if (rr <= c || rr >= kw) continue;
+        const C lr = a[rr * (NB + 1) + c];
+#pragma unroll
+        for (int qq = 0; qq < NB / 16; ++qq) {
+          const int cc = tx + 16 * qq;
+          if (cc <= c || cc > rr) continue;
+          const C lc = a[cc * (NB + 1) + c];
+          C v = a[rr * (NB + 1) + cc];
+          v.x -= lr.x * lc.x + lr.y * lc.y;       // v -= l_rc * conj(l_cc,c)
+          v.y -= lr.y * lc.x - lr.x * lc.y;
+          a[rr * (NB + 1) + cc] = v;
+        }
+      }
     }
     __syncthreads();
   }
@@ -116,8 +126,13 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A,
     const int r = e / kw, c = e % kw;
     if (c <= r) A[(k0 + r) * P + k0 + c] = a[r * (NB + 1) + c];
   }
-  // inverse of the lower-triangular block, row by row
-  if (tid < kw) inv[tid * (NB + 1) + tid] = mk<C>(1.0 / (double)a[tid * (NB + 1) + tid].x, 0.0);
+  // inverse of the lower-triangular block, row by row (in the factor's precision)
+  if (tid < kw) {
+    C d;
+    d.x = (R)1 / a[tid * (NB + 1) + tid].x;
+    d.y = (R)0;
+    inv[tid * (NB + 1) + tid] = d;
+  }
   __syncthreads();
   const int col = tid >> 2, part = tid & 3;
   for (int rr = 1; rr < kw; ++rr) {
@@ -129,8 +144,11 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A,
     s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
     s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
     if (col < rr && part == 0) {
-      const R lrr = a[rr * (NB + 1) + rr].x;
-      inv[rr * (NB + 1) + col] = mk<C>(-(double)s.x / (double)lrr, -(double)s.y / (double)lrr);
+      const R ilrr = inv[rr * (NB + 1) + rr].x;      // 1 / L[rr][rr]
+      C v;
+      v.x = -s.x * ilrr;
+      v.y = -s.y * ilrr;
+      inv[rr * (NB + 1) + col] = v;
     }
     __syncthreads();
   }
@@ -167,19 +185,30 @@ __global__ void __launch_bounds__(256) k_trsm_inv(C* __restrict__ A, int64_t P, 
   }
 }
 
-// Trailing update A[r][c] -= sum_m X[r][m] conj(X[c][m]) on lower 64x64 tiles.
+// Trailing update A[r][c] -= sum_m X[r][m] conj(X[c][m]) on lower 64x64 tiles, for columns
+// c < col_end (col_end >= P: the whole trailing matrix; otherwise a trapezoid of at most a
+// few tile columns, used inside a panel).
 template <typename C>
-__global__ void __launch_bounds__(256) k_herk(C* __restrict__ A, int64_t P, int64_t k0, int kw) {
+__global__ void __launch_bounds__(256) k_herk(C* __restrict__ A, int64_t P, int64_t k0, int kw,
+                                              int64_t col_end) {
   extern __shared__ unsigned char hsm[];
   C* Xr = reinterpret_cast<C*>(hsm);           // [NB (m)][NB+1 (row)]
   C* Xc = Xr + NB * (NB + 1);                  // [NB (m)][NB+1 (col)]
   const int64_t k1 = k0 + kw;
-  // lower-triangular tile enumeration
   const int64_t t = blockIdx.x;
-  int64_t tm = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
-  while (tm * (tm + 1) / 2 > t) --tm;
-  const int64_t tn = t - tm * (tm + 1) / 2;
+  int64_t tm, tn;
+  if (col_end >= P) {                        // lower-triangular tile enumeration
+    tm = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+    while (tm * (tm + 1) / 2 > t) --tm;
+    tn = t - tm * (tm + 1) / 2;
+  } else {                                   // trapezoid, column by column
+    const int64_t nt = (P - k1 + NB - 1) / NB;
+    int64_t u = t;
+    tn = 0;
+    while (u >= nt - tn) { u -= nt - tn; ++tn; }
+    tm = tn + u;
+  }
   const int64_t r0 = k1 + tm * NB, c0 = k1 + tn * NB;
   const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += 256) {
@@ -222,63 +251,206 @@ __global__ void __launch_bounds__(256) k_herk(C* __restrict__ A, int64_t P, int6
   }
 }
 
-// Forward step kb of L y = b: y_kb = Linv_kb b_kb (every block recomputes it; block 0
-// stores it), then b[r] -= sum_m L[r][k0+m] y_kb[m] for the rows below.
-template <typename C>
-__global__ void __launch_bounds__(256) k_fwd_step(const C* __restrict__ A,
-                                                  const C* __restrict__ Dinv, int64_t P,
-                                                  int64_t k0, int kw, C* __restrict__ b,
-                                                  C* __restrict__ y) {
-  __shared__ C yk[NB];
-  const int tid = threadIdx.x;
-  if (tid < kw) {
-    C s = mk<C>(0.0, 0.0);
-    for (int m = 0; m <= tid; ++m) cfma(s, Dinv[tid * NB + m], b[k0 + m]);
-    yk[tid] = s;
-    if (blockIdx.x == 0) y[k0 + tid] = s;
+// ---------------------------------------------------------------------------------------
+// Whole triangular solves in one cooperative launch: the block steps of the forward
+// (L y = b) and backward (L^H x = y) substitutions are separated by a grid barrier.  The
+// barrier is a counter plus a generation word in global memory; every wait is bounded
+// (iteration and clock limits) and an expired wait sets DEV_ERR_TIMEOUT and an abort word
+// that makes every block leave the loop.  The right-hand-side vectors are read and written
+// with L2-only accesses (ld/st.global.cg): rows move between blocks from step to step, so
+// an L1 copy from an earlier step could be stale.
+// ---------------------------------------------------------------------------------------
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  unsigned abort;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, unsigned* status) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = &bar->gen;
+    volatile unsigned* vab = &bar->abort;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      unsigned it = 0;
+      while (*vgen == g) {
+        if (*vab) { ok = 0; break; }
+        if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
+          atomicExch(&bar->abort, 1u);
+          flag_error(status, DEV_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
   }
   __syncthreads();
-  const int lane = tid & 31, warp = tid >> 5;
-  const int64_t first = k0 + kw;
-  for (int64_t row = first + (int64_t)blockIdx.x * 8 + warp; row < P; row += (int64_t)gridDim.x * 8) {
-    C s = mk<C>(0.0, 0.0);
-    for (int m = lane; m < kw; m += 32) cfma(s, A[row * P + k0 + m], yk[m]);
-    for (int o = 16; o > 0; o >>= 1) {
-      s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-      s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  return ok != 0;
+}
+
+// Steps of SB = 256 rows.  After the factorisation the inverse of every 256 x 256 diagonal
+// block is formed once (k_inv_sb); each block of the cooperative solve then applies it to
+// the step's right-hand side redundantly (a coalesced matrix-vector product) and updates
+// its share of the remaining rows; one grid barrier per step.
+constexpr int SB = 256;
+
+// Inverse of the diagonal block sb of L (rows/cols k0 .. k0+kw), one CTA per block, thread t
+// owns column t: forward substitution L_blk X = I with X[r][t] = (delta_rt - sum_{m<r}
+// L[r][m] X[m][t]) / L[r][r].  Stored twice: T[m][t] = Linv[t][m] (forward solve) and
+// Linv[m][t] (backward solve), both [nsb][SB][SB].
+template <typename C>
+__global__ void __launch_bounds__(SB) k_inv_sb(const C* __restrict__ A, int64_t P,
+                                              C* __restrict__ Tf, C* __restrict__ Tb) {
+  typedef typename RealOf<C>::T R;
+  const int64_t k0 = (int64_t)blockIdx.x * SB;
+  const int kw = (int)min((int64_t)SB, P - k0);
+  const int t = threadIdx.x;
+  C* tf = Tf + (int64_t)blockIdx.x * SB * SB;
+  C* tb = Tb + (int64_t)blockIdx.x * SB * SB;
+  // X column t, built row by row into tb[r][t] (coalesced across t)
+  for (int r = 0; r < SB; ++r) {
+    C v = mk<C>(0.0, 0.0);
+    if (r < kw && t < kw && t <= r) {
+      C acc = mk<C>(r == t ? 1.0 : 0.0, 0.0);
+      for (int m = t; m < r; ++m) {
+        const C l = A[(k0 + r) * P + k0 + m];          // same address in every thread
+        const C xm = tb[(int64_t)m * SB + t];
+        acc.x -= l.x * xm.x - l.y * xm.y;
+        acc.y -= l.x * xm.y + l.y * xm.x;
+      }
+      const R ild = (R)1 / A[(k0 + r) * P + k0 + r].x;
+      v.x = acc.x * ild;
+      v.y = acc.y * ild;
     }
-    if (lane == 0) {
-      C v = b[row];
-      v.x -= s.x;
-      v.y -= s.y;
-      b[row] = v;
+    tb[(int64_t)r * SB + t] = v;       // each thread reads back only its own column
+  }
+  for (int r = 0; r < SB; ++r) tf[(int64_t)t * SB + r] = tb[(int64_t)r * SB + t];
+}
+
+// y[t] = sum_m T[m][t] v[m] over the (zero-padded) 256 x 256 block, loads issued in
+// batches of 16 so that they overlap.
+template <typename C, bool CONJ>
+__device__ __forceinline__ C block_matvec(const C* __restrict__ T, const C* v, int tid) {
+  C s = mk<C>(0.0, 0.0);
+  for (int m0 = 0; m0 < SB; m0 += 16) {
+    C w[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) w[j] = T[(int64_t)(m0 + j) * SB + tid];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (CONJ) cfmac(s, v[m0 + j], w[j]);     // s += v * conj(T)
+      else cfma(s, w[j], v[m0 + j]);
     }
+  }
+  return s;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
+                                                  const C* __restrict__ Tf, int64_t P,
+                                                  C* __restrict__ b, C* __restrict__ y,
+                                                  GridBarrier* bar, unsigned* status) {
+  __shared__ C yk[SB];
+  __shared__ C bb[SB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t k0 = 0; k0 < P; k0 += SB) {
+    const int kw = (int)min((int64_t)SB, P - k0);
+    bb[tid] = (tid < kw) ? __ldcg(&b[k0 + tid]) : mk<C>(0.0, 0.0);
+    __syncthreads();
+    yk[tid] = block_matvec<C, false>(Tf + (k0 / SB) * SB * SB, bb, tid);   // T[m][t] = Linv[t][m]
+    __syncthreads();
+    if (blockIdx.x == 0 && tid < kw) __stcg(&y[k0 + tid], yk[tid]);
+    // rows below: four rows per warp, all 32 loads of a lane issued before the products
+    for (int64_t base = k0 + kw + ((int64_t)blockIdx.x * 8 + warp) * 4; base < P;
+         base += (int64_t)gridDim.x * 32) {
+      C v[4][8];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int m = lane + 32 * i;
+          const int64_t row = base + rr;
+          v[rr][i] = (row < P && m < kw) ? A[row * P + k0 + m] : mk<C>(0.0, 0.0);
+        }
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        C s = mk<C>(0.0, 0.0);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) cfma(s, v[rr][i], yk[lane + 32 * i]);
+        for (int o = 16; o > 0; o >>= 1) {
+          s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+          s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+        }
+        const int64_t row = base + rr;
+        if (lane == 0 && row < P) {
+          C t = __ldcg(&b[row]);
+          t.x -= s.x;
+          t.y -= s.y;
+          __stcg(&b[row], t);
+        }
+      }
+    }
+    if (!grid_sync(bar, gridDim.x, status)) return;
   }
 }
 
-// Backward step kb of L^H x = y: x_kb = Linv_kb^H c_kb, then c[r] -= sum_m conj(L[k0+m][r]) x_kb[m]
-// for the rows above.
 template <typename C>
-__global__ void __launch_bounds__(256) k_bwd_step(const C* __restrict__ A,
-                                                  const C* __restrict__ Dinv, int64_t P,
-                                                  int64_t k0, int kw, C* __restrict__ c,
-                                                  C* __restrict__ x) {
-  __shared__ C xk[NB];
-  const int tid = threadIdx.x;
-  if (tid < kw) {
-    C s = mk<C>(0.0, 0.0);
-    for (int m = tid; m < kw; ++m) cfmac(s, c[k0 + m], Dinv[m * NB + tid]);  // conj(Linv[m][tid]) c[m]
-    xk[tid] = s;
-    if (blockIdx.x == 0) x[k0 + tid] = s;
-  }
-  __syncthreads();
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + tid; r < k0; r += (int64_t)gridDim.x * blockDim.x) {
-    C s = mk<C>(0.0, 0.0);
-    for (int m = 0; m < kw; ++m) cfmac(s, xk[m], A[(k0 + m) * P + r]);
-    C v = c[r];
-    v.x -= s.x;
-    v.y -= s.y;
-    c[r] = v;
+__global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
+                                                  const C* __restrict__ Tb, int64_t P,
+                                                  C* __restrict__ c, C* __restrict__ x,
+                                                  GridBarrier* bar, unsigned* status) {
+  __shared__ C xk[SB];
+  __shared__ C cc[SB];
+  __shared__ C red[8][32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nsb = (P + SB - 1) / SB;
+  for (int64_t sb = nsb - 1; sb >= 0; --sb) {
+    const int64_t k0 = sb * SB;
+    const int kw = (int)min((int64_t)SB, P - k0);
+    cc[tid] = (tid < kw) ? __ldcg(&c[k0 + tid]) : mk<C>(0.0, 0.0);
+    __syncthreads();
+    xk[tid] = block_matvec<C, true>(Tb + sb * SB * SB, cc, tid);   // Linv[m][t], conjugated
+    __syncthreads();
+    if (blockIdx.x == 0 && tid < kw) __stcg(&x[k0 + tid], xk[tid]);
+    // rows above: chunks of 32 rows, warp w takes m in [32w, 32w+32), lanes take the rows
+    for (int64_t ch = blockIdx.x; ch * 32 < k0; ch += gridDim.x) {
+      const int64_t r = ch * 32 + lane;
+      C s = mk<C>(0.0, 0.0);
+      if (r < k0) {
+        C v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int m = warp * 32 + j;
+          v[j] = (m < kw) ? A[(k0 + m) * P + r] : mk<C>(0.0, 0.0);
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) cfmac(s, xk[warp * 32 + j], v[j]);
+      }
+      red[warp][lane] = s;
+      __syncthreads();
+      if (warp == 0 && r < k0) {
+        C tot = red[0][lane];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) { tot.x += red[w][lane].x; tot.y += red[w][lane].y; }
+        C t = __ldcg(&c[r]);
+        t.x -= tot.x;
+        t.y -= tot.y;
+        __stcg(&c[r], t);
+      }
+      __syncthreads();
+    }
+    if (!grid_sync(bar, gridDim.x, status)) return;
   }
 }
 
@@ -346,6 +518,26 @@ __global__ void k_update(double2* __restrict__ p, const double2* __restrict__ x,
   }
 }
 
+// Panel L[r0 + r][c0 + m] (0 <= r < n, 0 <= m < K) of the FP32 factor as real rows for the
+// tensor-core update: X[2r][m] = Re, X[2r+1][m] = Im, BF16 hi/lo pair, zero padded rows.
+__global__ void k_panel_to_x(const float2* __restrict__ A, int64_t P, int64_t r0, int64_t c0,
+                             int64_t n, int K, int64_t rows_pad, __nv_bfloat16* __restrict__ Xhi,
+                             __nv_bfloat16* __restrict__ Xlo) {
+  const int64_t total = (rows_pad / 2) * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / K;
+    const int m = (int)(e % K);
+    float2 v = make_float2(0.f, 0.f);
+    if (r < n) v = A[(r0 + r) * P + c0 + m];
+    const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
+    Xhi[(2 * r) * K + m] = hr;
+    Xhi[(2 * r + 1) * K + m] = hi;
+    Xlo[(2 * r) * K + m] = __float2bfloat16_rn(v.x - __bfloat162float(hr));
+    Xlo[(2 * r + 1) * K + m] = __float2bfloat16_rn(v.y - __bfloat162float(hi));
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
@@ -383,7 +575,7 @@ static cudaError_t factor(C* A, C* Dinv, int64_t P, unsigned* status, cudaStream
     if (rest > 0) {
       k_trsm_inv<C><<<(unsigned)((rest + NB - 1) / NB), 256, s2, st>>>(A, P, k0, kw, Dinv + kb * NB * NB);
       const int64_t nt = (rest + NB - 1) / NB;
-      k_herk<C><<<(unsigned)(nt * (nt + 1) / 2), 256, s2, st>>>(A, P, k0, kw);
+      k_herk<C><<<(unsigned)(nt * (nt + 1) / 2), 256, s2, st>>>(A, P, k0, kw, P);
       *launches += 2;
     }
     VMC_TRY(cudaGetLastError());
@@ -391,26 +583,101 @@ static cudaError_t factor(C* A, C* Dinv, int64_t P, unsigned* status, cudaStream
   return cudaSuccess;
 }
 
-// b is overwritten (workspace); the solution lands in x
+// Two-level factorisation: 256-wide panels factored by the SIMT kernels above (64-wide
+// diagonal blocks, updates restricted to the panel's columns), then the whole trailing
+// matrix receives the panel's Schur complement on the tensor cores (BF16 split, K = 256).
+static constexpr int NBO = 256;
+
+static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, unsigned* status,
+                             cudaStream_t st, int64_t* launches) {
+  VMC_TRY(set_smem_attrs<float2>());
+  const size_t s2 = 2 * NB * (NB + 1) * sizeof(float2);
+  for (int64_t p0 = 0; p0 < P; p0 += NBO) {
+    const int64_t pend = std::min<int64_t>(P, p0 + NBO);
+    for (int64_t k0 = p0; k0 < pend; k0 += NB) {
+      const int64_t kb = k0 / NB;
+      const int kw = (int)std::min<int64_t>(NB, P - k0);
+      k_potrf_diag<float2><<<1, POTRF_THREADS, s2, st>>>(A, P, k0, kw, Dinv + kb * NB * NB, status);
+      ++*launches;
+      const int64_t rest = P - k0 - kw;
+      if (rest > 0) {
+        k_trsm_inv<float2><<<(unsigned)((rest + NB - 1) / NB), 256, s2, st>>>(A, P, k0, kw, Dinv + kb * NB * NB);
+        ++*launches;
+        if (k0 + kw < pend) {
+          const int64_t nt = (rest + NB - 1) / NB;
+          const int64_t nct = (pend - k0 - kw + NB - 1) / NB;
+          const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
+          k_herk<float2><<<(unsigned)tiles, 256, s2, st>>>(A, P, k0, kw, pend);
+          ++*launches;
+        }
+      }
+      VMC_TRY(cudaGetLastError());
+    }
+    const int64_t n = P - pend;
+    if (n > 0) {
+      const int64_t rows_pad = (2 * n + 127) / 128 * 128;
+      if (rows_pad * NBO > w.x_elems) return cudaErrorInvalidValue;
+      const int K = (int)(pend - p0);
+      if (K != NBO) return cudaErrorInvalidValue;
+      const int64_t total = (rows_pad / 2) * K;
+      k_panel_to_x<<<grid_for(total, 256), 256, 0, st>>>(A, P, pend, p0, n, K, rows_pad, w.Xhi, w.Xlo);
+      VMC_TRY(cudaGetLastError());
+      VMC_TRY(launch_herk_tc(w.Xhi, w.Xlo, rows_pad, K, n, A, P, pend, status, st));
+      *launches += 2;
+    }
+  }
+  return cudaSuccess;
+}
+
+// b is overwritten (workspace); the solution lands in x.  One cooperative launch per
+// substitution (all blocks resident: the grid is sized from the occupancy query).
+template <typename C> static C* inv_fwd(SolveWork& w);
+template <> float2* inv_fwd<float2>(SolveWork& w) { return w.T32f; }
+template <> double2* inv_fwd<double2>(SolveWork& w) { return w.T64f; }
+template <typename C> static C* inv_bwd(SolveWork& w);
+template <> float2* inv_bwd<float2>(SolveWork& w) { return w.T32b; }
+template <> double2* inv_bwd<double2>(SolveWork& w) { return w.T64b; }
+
+// inverses of the 256-wide diagonal blocks of the factor (once per factorisation)
 template <typename C>
-static cudaError_t chol_solve(const C* A, const C* Dinv, int64_t P, C* b, C* y, C* x,
-                              cudaStream_t st, int64_t* launches) {
-  const int64_t nblk = (P + NB - 1) / NB;
-  for (int64_t kb = 0; kb < nblk; ++kb) {
-    const int64_t k0 = kb * NB;
-    const int kw = (int)std::min<int64_t>(NB, P - k0);
-    const int64_t rest = P - k0 - kw;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((rest + 7) / 8, 1184));
-    k_fwd_step<C><<<g, 256, 0, st>>>(A, Dinv + kb * NB * NB, P, k0, kw, b, y);
-    ++*launches;
+static cudaError_t invert_blocks(const C* A, int64_t P, SolveWork& w, cudaStream_t st,
+                                 int64_t* launches) {
+  const int64_t nsb = (P + SB - 1) / SB;
+  k_inv_sb<C><<<(unsigned)nsb, SB, 0, st>>>(A, P, inv_fwd<C>(w), inv_bwd<C>(w));
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <typename C>
+static cudaError_t chol_solve(const C* A, const C* Dinv_unused, int64_t P, C* b, C* y, C* x,
+                              SolveWork& w, unsigned* status, cudaStream_t st, int64_t* launches) {
+  (void)Dinv_unused;
+  const C* Dinv = inv_fwd<C>(w);   // forward kernel reads the transposed inverses
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    VMC_TRY(cudaGetDevice(&dev));
+    VMC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int pf = 0, pb = 0;
+    VMC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, k_fwd_coop<C>, 256, 0));
+    VMC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pb, k_bwd_coop<C>, 256, 0));
+    per_sm = std::min(std::min(pf, pb), 1);
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    grid = sms * per_sm;
   }
-  for (int64_t kb = nblk - 1; kb >= 0; --kb) {
-    const int64_t k0 = kb * NB;
-    const int kw = (int)std::min<int64_t>(NB, P - k0);
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((k0 + 255) / 256, 1184));
-    k_bwd_step<C><<<g, 256, 0, st>>>(A, Dinv + kb * NB * NB, P, k0, kw, y, x);
-    ++*launches;
+  GridBarrier* bar = reinterpret_cast<GridBarrier*>(w.bar);
+  VMC_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+  {
+    void* args[] = {(void*)&A, (void*)&Dinv, (void*)&P, (void*)&b, (void*)&y, (void*)&bar, (void*)&status};
+    VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_fwd_coop<C>, dim3(grid), dim3(256), args, 0, st));
   }
+  VMC_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+  {
+    const C* Dinvb = inv_bwd<C>(w);
+    void* args[] = {(void*)&A, (void*)&Dinvb, (void*)&P, (void*)&y, (void*)&x, (void*)&bar, (void*)&status};
+    VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_bwd_coop<C>, dim3(grid), dim3(256), args, 0, st));
+  }
+  *launches += 2;
   return cudaGetLastError();
 }
 
@@ -435,31 +702,45 @@ cudaError_t solve_cholesky_fp64(const double2* S, const double2* F, double2* x, 
   k_copy_shift<double2><<<grid_for(P * P, 256), 256, 0, st>>>(S, w.A64, P, nu, mode);
   ++*launches;
   VMC_TRY(factor<double2>(w.A64, w.D64, P, status, st, launches));
+  VMC_TRY(invert_blocks<double2>(w.A64, P, w, st, launches));
   VMC_TRY(cudaMemcpyAsync(w.c, F, P * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  return chol_solve<double2>(w.A64, w.D64, P, w.c, w.r, x, st, launches);
+  return chol_solve<double2>(w.A64, w.D64, P, w.c, w.r, x, w, status, st, launches);
 }
 
 cudaError_t solve_cholesky_mixed(const double2* S, const double2* F, double2* x, double nu,
-                                 int mode, double tol, int maxit, SolveWork& w,
+                                 int mode, double tol, int maxit, bool tc, SolveWork& w,
                                  unsigned* status, cudaStream_t st, int64_t* launches,
                                  int* iters, double* relres) {
   const int64_t P = w.P;
   k_copy_shift<float2><<<grid_for(P * P, 256), 256, 0, st>>>(S, w.A32, P, nu, mode);
   ++*launches;
-  VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
+  if (tc && P > NBO) VMC_TRY(factor_tc(w.A32, w.D32, P, w, status, st, launches));
+  else VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
+  VMC_TRY(invert_blocks<float2>(w.A32, P, w, st, launches));
   VMC_TRY(cudaMemsetAsync(x, 0, P * sizeof(double2), st));
   VMC_TRY(cudaMemcpyAsync(w.r, F, P * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  double rel = 1.0;
+  double rel = 1.0, prev = 1.0;
+  bool tc_factor = tc && P > NBO;
   int it = 0;
   for (; it < std::max(1, maxit); ++it) {
     k_to_f32<<<grid_for(P, 256, 1024), 256, 0, st>>>(w.r, w.r32, P);
-    VMC_TRY(chol_solve<float2>(w.A32, w.D32, P, w.r32, w.y32, w.c32, st, launches));
+    VMC_TRY(chol_solve<float2>(w.A32, w.D32, P, w.r32, w.y32, w.c32, w, status, st, launches));
     k_add_f32<<<grid_for(P, 256, 1024), 256, 0, st>>>(x, w.c32, P);
     *launches += 2;
     VMC_TRY(residual_fp64(S, F, x, nu, mode, w, st, &rel));
     *launches += 2;
     if (!(rel == rel)) break;      // NaN
     if (rel <= tol) { ++it; break; }
+    // The BF16-split factor contracts the error by ~cond(S~) * 2^-16 per iteration; if that
+    // is too slow, refactor in FP32 and keep refining from the current x.
+    if (tc_factor && it >= 1 && rel > 0.25 * prev) {
+      k_copy_shift<float2><<<grid_for(P * P, 256), 256, 0, st>>>(S, w.A32, P, nu, mode);
+      ++*launches;
+      VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
+      VMC_TRY(invert_blocks<float2>(w.A32, P, w, st, launches));
+      tc_factor = false;
+    }
+    prev = rel;
   }
   if (iters) *iters = it;
   if (relres) *relres = rel;      // the caller compares it with tol

@@ -242,23 +242,14 @@ cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* 
 // ---------------------------------------------------------------------------------------
 static constexpr int GB = 128, GK = 16, GPAD = 4;
 
-__device__ __forceinline__ void tri_index(int64_t t, int* bm, int* bn) {
-  // t enumerates (bm, bn) with bn <= bm: t = bm(bm+1)/2 + bn
-  int m = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(m + 1) * (m + 2) / 2 <= t) ++m;
-  while ((int64_t)m * (m + 1) / 2 > t) --m;
-  *bm = m;
-  *bn = (int)(t - (int64_t)m * (m + 1) / 2);
-}
-
 __global__ void __launch_bounds__(256) k_gram_f32(const float* __restrict__ X, int64_t ld,
-                                                  int64_t P, double inv_n,
+                                                  int nt, int64_t P, double inv_n,
                                                   double2* __restrict__ S, int mirror) {
   extern __shared__ float gsm[];
   float* As = gsm;                              // [2][GK][GB + GPAD]
   float* Bs = gsm + 2 * GK * (GB + GPAD);       // [2][GK][GB + GPAD]
   int bm, bn;
-  tri_index(blockIdx.x, &bm, &bn);
+  grouped_tri_tile(blockIdx.x, nt, 12, &bm, &bn);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const float* Ag = X + (int64_t)bm * GB * ld;
   const float* Bg = X + (int64_t)bn * GB * ld;
@@ -365,7 +356,7 @@ cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_gram_f32<<<(unsigned)tiles, 256, smem, st>>>(X, ld, P, inv_n, S, mirror ? 1 : 0);
+  k_gram_f32<<<(unsigned)tiles, 256, smem, st>>>(X, ld, (int)nt, P, inv_n, S, mirror ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -132,6 +132,54 @@ __device__ __forceinline__ float2 cosh_ratio(float2 t, float dr, float di) {
   return make_float2(ch.x - ts.x, ch.y - ts.y);
 }
 
+// complex division a / b
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+  const float inv = 1.0f / fmaf(b.x, b.x, b.y * b.y);
+  return make_float2(fmaf(a.x, b.x, a.y * b.y) * inv, fmaf(a.y, b.x, -a.x * b.y) * inv);
+}
+
+// tanh(theta - d) from t = tanh theta: (t - tanh d) / (1 - t tanh d)
+__device__ __forceinline__ float2 tanh_shift(float2 t, float dr, float di) {
+  float2 ch, sh;
+  cosh_sinh_c(dr, di, &ch, &sh);
+  const float2 td = cdiv(sh, ch);
+  const float2 num = make_float2(t.x - td.x, t.y - td.y);
+  const float2 tt = cmul(t, td);
+  return cdiv(num, make_float2(1.0f - tt.x, -tt.y));
+}
+
+// Lower-triangular tile t of an nt x nt tile grid (bn <= bm), rasterised in groups of
+// `group` tile rows and column-major inside a group, so that the tiles resident at the same
+// time share a few row blocks of both operands.
+__device__ __forceinline__ void grouped_tri_tile(int64_t t, int nt, int group, int* bm, int* bn) {
+  // group index: the largest g with tri(group*g) <= t, tri(m) = m(m+1)/2
+  int g = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5) / group;
+  auto tri = [](int64_t m) { return m * (m + 1) / 2; };
+  while (g > 0 && tri((int64_t)group * g) > t) --g;
+  while (tri((int64_t)group * (g + 1)) <= t && group * (g + 1) < nt) ++g;
+  const int r0 = group * g;
+  const int r1 = min(r0 + group, nt) - 1;
+  const int h = r1 - r0 + 1;
+  int64_t u = t - tri(r0);
+  if (u < (int64_t)r0 * h) {
+    *bn = (int)(u / h);
+    *bm = r0 + (int)(u % h);
+    return;
+  }
+  u -= (int64_t)r0 * h;
+  for (int c = r0; c <= r1; ++c) {
+    const int height = r1 - c + 1;
+    if (u < height) {
+      *bn = c;
+      *bm = c + (int)u;
+      return;
+    }
+    u -= height;
+  }
+  *bm = r1;
+  *bn = r1;
+}
+
 // warp reductions with xor butterflies: every lane ends with the same bits (each level
 // adds the same two operands in both partner lanes).
 __device__ __forceinline__ float warp_sum(float v) {

@@ -84,6 +84,13 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
                            bool mirror, unsigned* status, cudaStream_t st);
 
+// Schur-complement update of an FP32 complex Cholesky factor on the tensor cores:
+// A[off+k][off+l] -= sum_m L_km conj(L_lm) for 0 <= l <= k < n, with L's panel given as
+// real rows (row 2k = Re L_k., row 2k+1 = Im L_k.) split into BF16 hi/lo, K columns.
+cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, int64_t rows_pad,
+                           int64_t K, int64_t n, float2* A32, int64_t ldA, int64_t off,
+                           unsigned* status, cudaStream_t st);
+
 // ---- solve.cu -------------------------------------------------------------------------
 struct SolveWork {
   int64_t P;
@@ -97,20 +104,59 @@ struct SolveWork {
   float2* y32;     // [P]
   float2* c32;     // [P]
   double* scal;    // [8] device scalars
+  unsigned* bar;   // [4] grid barrier of the cooperative triangular solves
+  float2 *T32f, *T32b;    // [ceil(P/256)][256][256] inverses of the 256-wide diagonal blocks
+  double2 *T64f, *T64b;   //   (transposed for the forward solve; FP32 or FP64 solver)
+  __nv_bfloat16* Xhi;  // panel operands of the tensor-core Schur updates
+  __nv_bfloat16* Xlo;
+  int64_t x_elems;     // capacity of Xhi / Xlo
 };
 
 // Cholesky solve of (S + shift) x = F, FP64 throughout.
 cudaError_t solve_cholesky_fp64(const double2* S, const double2* F, double2* x, double nu,
                                 int mode, SolveWork& w, unsigned* status, cudaStream_t st,
                                 int64_t* launches);
-// FP32 Cholesky of the shifted matrix + FP64 iterative refinement.
+// FP32 Cholesky of the shifted matrix + FP64 iterative refinement; tc = trailing updates
+// of 256-wide panels on the tensor cores (BF16 split) instead of FP32 SIMT.
 cudaError_t solve_cholesky_mixed(const double2* S, const double2* F, double2* x, double nu,
-                                 int mode, double tol, int maxit, SolveWork& w,
+                                 int mode, double tol, int maxit, bool tc, SolveWork& w,
                                  unsigned* status, cudaStream_t st, int64_t* launches,
                                  int* iters, double* relres);
 // FP64 relative residual ||(S + shift) x - F|| / ||F|| (synchronises).
 cudaError_t residual_fp64(const double2* S, const double2* F, const double2* x, double nu,
                           int mode, SolveWork& w, cudaStream_t st, double* relres);
+
+// ---- cg.cu ----------------------------------------------------------------------------
+struct CgProblem {
+  const int8_t* spins;            // [n][N]
+  const float2* T;                // [n][M] tanh theta
+  int64_t n;
+  int N, M;
+  const double2* meanO;           // [P] <O>
+  const double2* meanO_conj_free; // set by cg_solve
+};
+struct CgWork {
+  double2 *r, *p, *q, *y, *z, *meanO_c;   // [P]
+  double* D;                          // [P] shift diagonal
+  double* Minv;                       // [P] inverse diagonal of S~ (preconditioner)
+  double* t2;                         // [M]
+  float2 *va, *vb, *V;                // FP32 copies of the CG direction
+  float2* u;                          // [n]
+  float2* upart;                      // [ceil(M/64)][n]
+  double* ustats;                     // [8]
+  double* mpart;                      // moments scratch
+  double2* dpart;                     // [256] dot partials
+  double2* c2;                        // [8] device complex scalars
+  double* sc;                         // [8] device real scalars
+};
+int64_t cg_partial_floats2(int64_t n, int M);
+// diag(S) and the conjugated means; T and meanO must describe the sample set
+cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cudaStream_t st,
+                       int64_t* launches);
+// CG on (1/n) Obar^H Obar + D from x0 = 0 until ||r|| <= tol ||F|| or maxit (synchronises
+// once per iteration to read the residual)
+cudaError_t cg_solve(const CgProblem& pb, const double2* F, double2* x, double tol, int maxit,
+                     CgWork& w, cudaStream_t st, int64_t* launches, int* iters, double* relres);
 
 // theta <- theta - dt * x, then refresh the FP32 copies
 cudaError_t launch_update(double2* params, const double2* x, int64_t P, double dt,

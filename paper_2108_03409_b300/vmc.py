@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libvmc.so")
 VMC_OK, VMC_ERR_ARG, VMC_ERR_CUDA, VMC_ERR_OOM, VMC_ERR_NUMERIC, VMC_ERR_TIMEOUT, VMC_ERR_STATE = range(7)
 MODEL_TFIM, MODEL_HEISENBERG = 0, 1
 PREC_FP32, PREC_BF16SPLIT = 0, 1
-SOLVER_CHOLESKY_FP64, SOLVER_CG, SOLVER_CHOLESKY_MIXED = 0, 1, 2
+SOLVER_CHOLESKY_FP64, SOLVER_CG, SOLVER_CHOLESKY_MIXED, SOLVER_CHOLESKY_TC = 0, 1, 2, 3
 SHIFT_MULTIPLICATIVE, SHIFT_ADDITIVE = 0, 1
 
 _STATUS_NAMES = {0: "VMC_OK", 1: "VMC_ERR_ARG", 2: "VMC_ERR_CUDA", 3: "VMC_ERR_OOM",
@@ -60,7 +60,7 @@ class vmc_sr_stats(ctypes.Structure):
 EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
             "vmc_set_chains", "vmc_get_chains", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
             "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
-            "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc"]
+            "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve"]
 
 _lib = None
 
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
         "vmc_num_samples": (i64, [P]),
         "vmc_num_params": (i64, [P, i32]),
         "vmc_force_noalloc": (i32, [P, P, P, i64, i32, i32, P, P, P]),
+        "vmc_cg_solve": (i32, [P, i32, P, i64, P, P, ctypes.POINTER(i32), ctypes.POINTER(f64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -209,6 +210,14 @@ def vmc_solve(ctx, lattice, S, F, x):
     rr = ctypes.c_double(0.0)
     _check(ctx, load().vmc_solve(ctx, lattice, _ptr(S), _ptr(F), _ptr(x), ctypes.byref(it),
                                  ctypes.byref(rr)))
+    return it.value, rr.value
+
+
+def vmc_cg_solve(ctx, lattice, spins, F, x):
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    _check(ctx, load().vmc_cg_solve(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(F), _ptr(x),
+                                    ctypes.byref(it), ctypes.byref(rr)))
     return it.value, rr.value
 
 

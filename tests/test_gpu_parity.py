@@ -264,7 +264,8 @@ def test_qfm_8x8_sampled_entries():
     assert np.array_equal(Sd[..., 0], Sd[..., 0].T) and np.array_equal(Sd[..., 1], -Sd[..., 1].T)
 
 
-@pytest.mark.parametrize("solver", [vmc.SOLVER_CHOLESKY_FP64, vmc.SOLVER_CHOLESKY_MIXED])
+@pytest.mark.parametrize("solver", [vmc.SOLVER_CHOLESKY_FP64, vmc.SOLVER_CHOLESKY_MIXED,
+                                    vmc.SOLVER_CHOLESKY_TC])
 @pytest.mark.parametrize("shape", [(T, 10, 1, 1, 1e-4, 0), (H, 4, 4, 2, 1e-3, 0), (T, 6, 6, 1, 1e-2, 1)],
                          ids=["P120", "P560", "P1332_additive"])
 def test_solve_matches_oracle(solver, shape):
@@ -279,7 +280,7 @@ def test_solve_matches_oracle(solver, shape):
     S, F, _ = oracle.sr_matrices(O, E)
     xref = oracle.cholesky_solve(oracle.shift(S, nu, mode), F)
     with context(lattice(model, Lx, Ly, 1.0, 1.0, alpha), n_chains=n, solver=solver, shift=nu,
-                 shift_mode=mode, cg_tol=1e-12, cg_maxit=30) as ctx:
+                 shift_mode=mode, cg_tol=1e-12, cg_maxit=60) as ctx:
         Sd = torch.from_numpy(S.view(np.float64).reshape(P, P, 2).copy()).cuda()
         Fd = torch.from_numpy(F.view(np.float64).reshape(P, 2).copy()).cuda()
         xd = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
@@ -314,7 +315,8 @@ def test_solve_reports_non_positive_pivot():
 
 @pytest.mark.parametrize("solver,precision", [(vmc.SOLVER_CHOLESKY_FP64, vmc.PREC_FP32),
                                               (vmc.SOLVER_CHOLESKY_MIXED, vmc.PREC_FP32),
-                                              (vmc.SOLVER_CHOLESKY_MIXED, vmc.PREC_BF16SPLIT)])
+                                              (vmc.SOLVER_CHOLESKY_MIXED, vmc.PREC_BF16SPLIT),
+                                              (vmc.SOLVER_CHOLESKY_TC, vmc.PREC_BF16SPLIT)])
 def test_sr_step_matches_oracle_pipeline(solver, precision):
     """One SR step.  The sample set is read back through vmc_sample on a twin context
     (the kernels are deterministic, and the sampler's agreement with the oracle's
@@ -354,3 +356,64 @@ def test_sr_step_matches_oracle_pipeline(solver, precision):
     assert res <= bound, (res, bound)
     assert 0.0 < st.acceptance < 1.0
     assert st.solver_relres <= 1e-10
+
+
+# --------------------------------------------------------------------------------------
+# matrix-free CG (a11)
+# --------------------------------------------------------------------------------------
+# The CG operator is applied in FP32 (u = Obar v and the F-type reduction with FP32
+# sub-sums of 128 samples), so the returned x solves a system within
+# CG_OPERATOR_REL * ||S~|| ||x|| of the oracle's FP64 one.
+CG_OPERATOR_REL = 128 * 2.0 ** -24 * 8
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("shape", [(T, 10, 1, 1.0, 1.0, 1, 2000), (H, 4, 4, 1.0, 0.0, 2, 1500),
+                                   (T, 6, 6, 1.0, 3.0, 2, 1100)], ids=["tfim10", "heis4x4", "tfim6x6"])
+def test_cg_solve_matches_oracle(shape, mode):
+    model, Lx, Ly, J, h, alpha, n = shape
+    N, M = Lx * Ly, alpha * Lx * Ly
+    P = N + M + N * M
+    nu = 1e-3 if mode == 0 else 1e-2
+    p = inputs.rbm_params(N, M, 0.1, seed=51, marshall=(Lx, Ly) if model == H else None)
+    s = inputs.initial_spins(model, n, N, seed=52)
+    with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=n, solver=vmc.SOLVER_CG, shift=nu,
+                 shift_mode=mode, cg_tol=1e-8, cg_maxit=2000) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        sd = to_dev_spins(s)
+        e = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_local_energy(ctx, 0, sd, e)
+        F = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        vmc.vmc_grad(ctx, 0, sd, e, None, F)
+        x = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        it, rel = vmc.vmc_cg_solve(ctx, 0, sd, F, x)
+        Fh, xh = cplx(F), cplx(x)
+    assert rel <= 1e-8 and 0 < it < 2000
+    O = oracle.ok(N, M, p, s)
+    S, _, _ = oracle.sr_matrices(O, np.zeros(n))
+    St = oracle.shift(S, nu, mode)
+    res = np.linalg.norm(St @ xh - Fh) / np.linalg.norm(Fh)
+    bound = 1e-8 + CG_OPERATOR_REL * np.linalg.norm(St, 2) * np.linalg.norm(xh) / np.linalg.norm(Fh)
+    assert res <= bound, (res, bound)
+    # the oracle's own matrix-free CG reaches the same solution
+    xo, ito, relo = oracle.cg_solve(O, Fh, nu, mode, tol=1e-12, maxit=5000)
+    assert np.linalg.norm(xh - xo) <= np.linalg.cond(St) * bound * np.linalg.norm(xo)
+
+
+def test_sr_step_cg_heisenberg_16x16():
+    """The 16x16 Heisenberg shape (N = 256, M = 512, P = 131 840) through the CG step,
+    with fewer chains than the benchmark: the step converges and the energy is physical
+    (Pauli units: E/N >= -3, the 2D antiferromagnet's ground state is about -2.68 per site)."""
+    Lx = Ly = 16
+    N, M = 256, 512
+    C = 2048
+    p = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(Lx, Ly))
+    with context(lattice(H, Lx, Ly, 1.0, 0.0, 2), n_chains=C, solver=vmc.SOLVER_CG, shift=1e-3,
+                 cg_tol=1e-6, cg_maxit=100, therm_sweeps=5) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vmc.vmc_set_chains(ctx, 0, inputs.random_sz0_spins(C, N, seed=3))
+        st = vmc.vmc_sr_step(ctx, 0, 0.02)
+        p1 = vmc.vmc_get_params(ctx, 0)
+    assert st.solver_relres <= 1e-6 and st.solver_iters <= 100
+    assert -3.0 <= st.e_mean_re / N <= 1.0
+    assert np.all(np.isfinite(p1)) and np.linalg.norm(p1 - p) > 0
