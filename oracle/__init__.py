@@ -22,6 +22,11 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   metropolis      -- pinned: chi-square of the histogram against exact |psi|^2
   philox4x64      -- pinned: numpy.random.Philox bit-for-bit
   tau_int         -- pinned: AR(1) closed form
+  made_forward    -- pinned: autoregressive property (flip tests), sum_s q(s) = 1 by
+                     enumeration, brute-force conditionals
+  made_grad       -- pinned: central finite differences of the loss
+  adam_step       -- pinned: closed form of the first two steps
+  made_sample     -- pinned: chi-square of the sample histogram against q
 """
 from __future__ import annotations
 
@@ -75,6 +80,11 @@ def _load():
             "orc_update": (i32, [i64, P, P, f64]),
             "orc_metropolis": (i32, [i32, i32, i32, i32, P, i64, P, u64, u64, u64, u64, i32, i32,
                                      P, P, P]),
+            "orc_made_nparams": (i64, [i32, i32]),
+            "orc_made_forward": (i32, [i32, i32, P, P, i64, P, P]),
+            "orc_made_grad": (i32, [i32, i32, P, P, i64, P, P]),
+            "orc_adam_step": (i32, [i64, P, P, P, P, i32, f64, f64, f64, f64]),
+            "orc_made_sample": (i32, [i32, i32, P, i64, u64, u64, u64, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -343,3 +353,51 @@ def tau_int_chains(series: np.ndarray, c: float = 5.0) -> float:
     """Average tau_int over chains; series is [T][C]."""
     series = np.asarray(series, dtype=np.float64)
     return float(np.mean([tau_int(series[:, k], c) for k in range(series.shape[1])]))
+
+
+# ----------------------------------------------------------------------------------------
+# MADE proposal
+# ----------------------------------------------------------------------------------------
+def made_nparams(N: int, H: int) -> int:
+    return int(_load().orc_made_nparams(N, H))
+
+
+def made_forward(N: int, H: int, params: np.ndarray, spins: np.ndarray, want_z: bool = False):
+    s = _spins(spins).reshape(-1, N)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    lq = np.zeros(s.shape[0])
+    z = np.zeros((s.shape[0], N)) if want_z else None
+    _check(_load().orc_made_forward(N, H, _ptr(p), _ptr(s), s.shape[0], _ptr(lq), _ptr(z)),
+           "made_forward")
+    return (lq, z) if want_z else lq
+
+
+def made_grad(N: int, H: int, params: np.ndarray, spins: np.ndarray):
+    s = _spins(spins).reshape(-1, N)
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    g = np.zeros_like(p)
+    L = ctypes.c_double(0.0)
+    _check(_load().orc_made_grad(N, H, _ptr(p), _ptr(s), s.shape[0], _ptr(g),
+                                 ctypes.addressof(L)), "made_grad")
+    return g, L.value
+
+
+def adam_step(theta, m, v, g, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    th = np.array(theta, dtype=np.float64, copy=True)
+    mm = np.array(m, dtype=np.float64, copy=True)
+    vv = np.array(v, dtype=np.float64, copy=True)
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    _check(_load().orc_adam_step(th.size, _ptr(th), _ptr(mm), _ptr(vv), _ptr(gg), int(t),
+                                 float(lr), float(b1), float(b2), float(eps)), "adam_step")
+    return th, mm, vv
+
+
+def made_sample(N: int, H: int, params: np.ndarray, n: int, seed: int, stream: int = 0,
+                round_: int = 0):
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    s = np.zeros((n, N), dtype=np.int8)
+    lq = np.zeros(n)
+    mm = np.zeros(n)
+    _check(_load().orc_made_sample(N, H, _ptr(p), n, int(seed), int(stream), int(round_),
+                                   _ptr(s), _ptr(lq), _ptr(mm)), "made_sample")
+    return s, lq, mm

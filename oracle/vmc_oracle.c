@@ -552,3 +552,195 @@ int orc_metropolis(int model, int Lx, int Ly, int M, const double* params, int64
   }
   return bad ? ORC_ERR_NUMERIC : ORC_OK;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Masked autoregressive MLP proposal (MADE; Germain, Gregor, Murray, Larochelle 2015),   */
+/* used as an independent Metropolis-Hastings proposal.  The paper's autoregressive      */
+/* factorisation p(s) = p1(s1) p2(s2|s1) ... ("Autoregressive neural quantum states")      */
+/* gives q(s) with exact sampling.                                                        */
+/*   degrees (1-based): input d = 1..N; hidden k of both layers m(k) = (k mod (N-1)) + 1   */
+/*   h1 = relu(W1 x + b1), W1[k][d] used iff m(k) >= d        (x_d = s_d)                 */
+/*   h2 = relu(W2 h1 + b2), W2[k2][k1] used iff m(k2) >= m(k1)                             */
+/*   z  = W3 h2 + b3,       W3[d][k2] used iff d > m(k2)                                   */
+/*   q(s) = prod_d sigma(s_d z_d),  log sigma(x) = -log(1 + e^-x)                          */
+/* parameters (doubles): W1[H][N] | b1[H] | W2[H][H] | b2[H] | W3[N][H] | b3[N].          */
+/* ------------------------------------------------------------------------------------ */
+static int made_deg(int k, int N) { return (N > 1) ? (k % (N - 1)) + 1 : 1; }
+
+static double log_sigmoid(double x) {
+  return (x >= 0.0) ? -log1p(exp(-x)) : x - log1p(exp(x));
+}
+
+int64_t orc_made_nparams(int N, int H) {
+  return (int64_t)H * N + H + (int64_t)H * H + H + (int64_t)N * H + N;
+}
+
+typedef struct { const double *W1, *b1, *W2, *b2, *W3, *b3; } made_view;
+
+static made_view made_split(const double* p, int N, int H) {
+  made_view v;
+  v.W1 = p;
+  v.b1 = v.W1 + (int64_t)H * N;
+  v.W2 = v.b1 + H;
+  v.b2 = v.W2 + (int64_t)H * H;
+  v.W3 = v.b2 + H;
+  v.b3 = v.W3 + (int64_t)N * H;
+  return v;
+}
+
+/* forward of one configuration; a1, a2 pre-activations [H], z logits [N]; returns log q */
+static double made_fwd1(const made_view* v, int N, int H, const int8_t* s, double* a1, double* a2,
+                        double* z) {
+  for (int k = 0; k < H; ++k) {
+    double acc = v->b1[k];
+    const int mk = made_deg(k, N);
+    for (int d = 1; d <= N; ++d)
+      if (mk >= d) acc += v->W1[(int64_t)k * N + (d - 1)] * (double)s[d - 1];
+    a1[k] = acc;
+  }
+  for (int k2 = 0; k2 < H; ++k2) {
+    double acc = v->b2[k2];
+    const int m2 = made_deg(k2, N);
+    for (int k1 = 0; k1 < H; ++k1)
+      if (m2 >= made_deg(k1, N) && a1[k1] > 0.0) acc += v->W2[(int64_t)k2 * H + k1] * a1[k1];
+    a2[k2] = acc;
+  }
+  double lq = 0.0;
+  for (int d = 1; d <= N; ++d) {
+    double acc = v->b3[d - 1];
+    for (int k2 = 0; k2 < H; ++k2)
+      if (d > made_deg(k2, N) && a2[k2] > 0.0) acc += v->W3[(int64_t)(d - 1) * H + k2] * a2[k2];
+    z[d - 1] = acc;
+    lq += log_sigmoid((double)s[d - 1] * acc);
+  }
+  return lq;
+}
+
+/* log q(s) and the logits for a batch: logq[n], z[n][N] (z may be NULL) */
+int orc_made_forward(int N, int H, const double* params, const int8_t* spins, int64_t n,
+                     double* logq, double* z) {
+  if (N < 2 || H < 1 || !params || (n > 0 && (!spins || !logq))) return ORC_ERR_ARG;
+  made_view v = made_split(params, N, H);
+#pragma omp parallel for schedule(static)
+  for (int64_t q = 0; q < n; ++q) {
+    double* a1 = (double*)malloc(sizeof(double) * (size_t)(2 * H + N));
+    double* a2 = a1 + H;
+    double* zz = a2 + H;
+    logq[q] = made_fwd1(&v, N, H, spins + q * N, a1, a2, zz);
+    if (z) memcpy(z + q * N, zz, sizeof(double) * (size_t)N);
+    free(a1);
+  }
+  return ORC_OK;
+}
+
+/* Gradient of the loss L = -(1/n) sum_q log q(s_q) (backpropagation through the masked
+   layers; ReLU derivative 1 for a > 0).  grad has the parameter layout; returns L. */
+int orc_made_grad(int N, int H, const double* params, const int8_t* spins, int64_t n,
+                  double* grad, double* loss) {
+  if (N < 2 || H < 1 || !params || !spins || !grad || n < 1) return ORC_ERR_ARG;
+  const int64_t np = orc_made_nparams(N, H);
+  made_view v = made_split(params, N, H);
+  memset(grad, 0, sizeof(double) * (size_t)np);
+  double* gW1 = grad;
+  double* gb1 = gW1 + (int64_t)H * N;
+  double* gW2 = gb1 + H;
+  double* gb2 = gW2 + (int64_t)H * H;
+  double* gW3 = gb2 + H;
+  double* gb3 = gW3 + (int64_t)N * H;
+  double* a1 = (double*)malloc(sizeof(double) * (size_t)(4 * H + 2 * N));
+  double* a2 = a1 + H;
+  double* z = a2 + H;
+  double* g3 = z + N;
+  double* g2 = g3 + N;
+  double* g1 = g2 + H;
+  double L = 0.0;
+  for (int64_t q = 0; q < n; ++q) {
+    const int8_t* s = spins + q * N;
+    L -= made_fwd1(&v, N, H, s, a1, a2, z);
+    /* d(-log sigma(s z))/dz = -s sigma(-s z) */
+    for (int d = 0; d < N; ++d) {
+      const double sd = (double)s[d];
+      g3[d] = -sd / (1.0 + exp(sd * z[d])) / (double)n;
+    }
+    for (int k2 = 0; k2 < H; ++k2) g2[k2] = 0.0;
+    for (int d = 1; d <= N; ++d) {
+      gb3[d - 1] += g3[d - 1];
+      for (int k2 = 0; k2 < H; ++k2) {
+        if (!(d > made_deg(k2, N))) continue;
+        const double h2 = a2[k2] > 0.0 ? a2[k2] : 0.0;
+        gW3[(int64_t)(d - 1) * H + k2] += g3[d - 1] * h2;
+        if (a2[k2] > 0.0) g2[k2] += v.W3[(int64_t)(d - 1) * H + k2] * g3[d - 1];
+      }
+    }
+    for (int k1 = 0; k1 < H; ++k1) g1[k1] = 0.0;
+    for (int k2 = 0; k2 < H; ++k2) {
+      gb2[k2] += g2[k2];
+      const int m2 = made_deg(k2, N);
+      for (int k1 = 0; k1 < H; ++k1) {
+        if (!(m2 >= made_deg(k1, N))) continue;
+        const double h1 = a1[k1] > 0.0 ? a1[k1] : 0.0;
+        gW2[(int64_t)k2 * H + k1] += g2[k2] * h1;
+        if (a1[k1] > 0.0) g1[k1] += v.W2[(int64_t)k2 * H + k1] * g2[k2];
+      }
+    }
+    for (int k1 = 0; k1 < H; ++k1) {
+      gb1[k1] += g1[k1];
+      const int m1 = made_deg(k1, N);
+      for (int d = 1; d <= N; ++d)
+        if (m1 >= d) gW1[(int64_t)k1 * N + (d - 1)] += g1[k1] * (double)s[d - 1];
+    }
+  }
+  free(a1);
+  if (loss) *loss = L / (double)n;
+  return ORC_OK;
+}
+
+/* One Adam step (Kingma & Ba 2014): m <- b1 m + (1-b1) g, v <- b2 v + (1-b2) g^2,
+   theta <- theta - lr (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps); t is 1-based. */
+int orc_adam_step(int64_t np, double* theta, double* m, double* v, const double* g, int t,
+                  double lr, double b1, double b2, double eps) {
+  if (np < 1 || !theta || !m || !v || !g || t < 1) return ORC_ERR_ARG;
+  const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+  for (int64_t k = 0; k < np; ++k) {
+    m[k] = b1 * m[k] + (1.0 - b1) * g[k];
+    v[k] = b2 * v[k] + (1.0 - b2) * g[k] * g[k];
+    theta[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
+  }
+  return ORC_OK;
+}
+
+/* Autoregressive sampling of n configurations from q: site d of sample c in round r uses
+   u = ((w[(d-1) mod 4] >> 40) + 1/2) / 2^24 from Philox4x64-10(ctr = {c, r, (d-1)/4, 2},
+   key = {seed, stream}), and s_d = +1 iff u < sigma(z_d).  spins[n][N], logq[n]. */
+int orc_made_sample(int N, int H, const double* params, int64_t n, uint64_t seed,
+                    uint64_t stream, uint64_t round, int8_t* spins, double* logq,
+                    double* min_margin) {
+  if (N < 2 || H < 1 || !params || !spins) return ORC_ERR_ARG;
+  made_view v = made_split(params, N, H);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < n; ++c) {
+    int8_t* s = spins + c * N;
+    double* a1 = (double*)malloc(sizeof(double) * (size_t)(2 * H + N));
+    double* a2 = a1 + H;
+    double* z = a2 + H;
+    double mm = INFINITY;
+    for (int d = 0; d < N; ++d) s[d] = 1;
+    for (int d = 1; d <= N; ++d) {
+      /* logits of site d from the sites already drawn (later sites do not enter) */
+      made_fwd1(&v, N, H, s, a1, a2, z);
+      uint64_t ctr[4] = {(uint64_t)c, round, (uint64_t)((d - 1) / 4), 2};
+      uint64_t key[2] = {seed, stream};
+      uint64_t w[4];
+      philox4x64_10(ctr, key, w);
+      const double u = ((double)(w[(d - 1) % 4] >> 40) + 0.5) * 0x1.0p-24;
+      const double p = 1.0 / (1.0 + exp(-z[d - 1]));
+      const double margin = fabs(u - p);
+      if (margin < mm) mm = margin;
+      s[d - 1] = (u < p) ? 1 : -1;
+    }
+    if (logq) logq[c] = made_fwd1(&v, N, H, s, a1, a2, z);
+    if (min_margin) min_margin[c] = mm;
+    free(a1);
+  }
+  return ORC_OK;
+}
