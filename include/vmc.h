@@ -79,6 +79,9 @@ typedef struct {
   int shift_mode;           /* VMC_SHIFT_*: (1+nu) S_kk (the paper's) or S_kk + nu             */
   int cg_maxit;             /* CG / refinement iteration cap                                   */
   double cg_tol;            /* relative residual target of the iterative solvers               */
+  int made_hidden;          /* width H of the learned proposal's two hidden layers (multiple   */
+                            /* of 32, <= 512); 0 = no learned proposal                         */
+  int made_batch;           /* training batch of the learned proposal (0 = 4096)               */
 } vmc_config;
 
 /* Statistics of one SR step (host struct filled by vmc_sr_step). */
@@ -185,6 +188,42 @@ vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
  * energies, log-derivatives, S and F, regularised solve, parameter update.  stats (host)
  * may be NULL.  Synchronises. */
 vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats);
+
+/* ---- learned proposal (masked autoregressive MLP; requires made_hidden > 0) -------------
+ * q(s) = prod_d sigma(s_d z_d), z = W3 relu(W2 relu(W1 s + b1) + b2) + b3 with MADE masks
+ * (Germain et al. 2015): hidden unit k has degree m(k) = (k mod (N-1)) + 1, W1[k][d] is used
+ * iff m(k) >= d, W2[k2][k1] iff m(k2) >= m(k1), W3[d][k2] iff d > m(k2) (d 1-based).  It builds
+ * on the paper's autoregressive factorisation (section "Autoregressive neural quantum
+ * states") and is used as an independent Metropolis-Hastings proposal.  Parameters are
+ * FP32 in the layout W1[H][N] | b1[H] | W2[H][H] | b2[H] | W3[N][H] | b3[N]. */
+vmc_status vmc_made_set_params(vmc_ctx* ctx, int lattice, const float* params_host);
+vmc_status vmc_made_get_params(vmc_ctx* ctx, int lattice, float* params_host);
+/* log q(s) for a batch: spins dev int8 [n][N], logq dev float [n]; n <= max(n_chains, batch). */
+vmc_status vmc_made_logq(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                         float* logq);
+/* Gradient (dev float, parameter layout) of L = -(1/n) sum log q(s) over the batch; loss (host)
+ * receives L.  Synchronises. */
+vmc_status vmc_made_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                         float* grad, double* loss);
+/* Train q on samples (dev int8 [n][N]) by Adam (beta = 0.9, 0.999, eps = 1e-8, learning rate
+ * lr) for `epochs` passes in consecutive batches of made_batch; loss (host) receives the mean
+ * -log q over the samples after training.  Synchronises. */
+vmc_status vmc_proposal_train(vmc_ctx* ctx, int lattice, const int8_t* samples, int64_t n,
+                              int epochs, double lr, double* loss);
+/* n exact draws from q (autoregressive): sample c of round r draws site d with
+ * u = ((w[(d-1) mod 4] >> 40) + 1/2) / 2^24, w = Philox4x64-10({c, r, (d-1)/4, 2},
+ * {seed, lattice}), s_d = +1 iff u < sigma(z_d).  spins dev int8 [n][N], logq dev float [n]
+ * (may be NULL). */
+vmc_status vmc_made_sample(vmc_ctx* ctx, int lattice, int64_t n, uint64_t round,
+                           int8_t* spins, float* logq);
+/* n_rounds rounds of independent Metropolis-Hastings on every chain: chain c draws s' from q
+ * (round counter of the lattice) and accepts iff ln u < 2 Re[log psi(s') - log psi(s)] +
+ * log q(s) - log q(s'), u from Philox4x64-10({c, r, 0, 3}, {seed, lattice}) word 1.  After each
+ * round the chain states (spins_out [n_rounds*C][N]) and their local energies (eloc_out
+ * [n_rounds*C][2]) are written (either may be NULL); acceptance (host) receives the
+ * accepted fraction.  Synchronises. */
+vmc_status vmc_sample_learned(vmc_ctx* ctx, int lattice, int n_rounds, int8_t* spins_out,
+                              float* eloc_out, double* acceptance);
 
 /* Number of kernel launches the library has issued on this context since it was created
  * (a counter kept by the host code). */

@@ -26,6 +26,18 @@ struct LatticeState {
   int8_t* chains = nullptr;    // [C][N]
   uint64_t sweep = 0;          // sweeps done by every chain
   bool thermalized = false;
+  // learned proposal (MADE)
+  float* made = nullptr;       // FP32 parameters, canonical layout
+  float *made_m = nullptr, *made_v = nullptr, *made_g = nullptr;
+  float *W1t = nullptr, *W2t = nullptr, *W3t = nullptr;
+  int made_t = 0;              // Adam step counter
+  uint64_t made_round = 0;     // proposal rounds drawn (Philox counter)
+  float2* chain_lp = nullptr;  // cached log psi of the chains
+  float* chain_lq = nullptr;   // cached log q of the chains
+  int8_t* prop = nullptr;      // proposals [C][N]
+  float* prop_lq = nullptr;
+  float2* prop_lp = nullptr;
+  bool chain_cache = false;
 };
 
 }  // namespace
@@ -54,6 +66,8 @@ struct vmc_ctx {
   double2* S = nullptr;           // [Pmax][Pmax]
   SolveWork sw{};
   CgWork cg{};
+  MadeWork mw{};
+  int64_t made_cap = 0;           // rows of the MADE batch workspaces
   unsigned* status = nullptr;
   unsigned long long* n_accept = nullptr;
   int64_t launches = 0;
@@ -110,6 +124,10 @@ vmc_status check_status(vmc_ctx* ctx, const char* where) {
     return fail(ctx, VMC_ERR_NUMERIC, std::string(where) + ": non-finite value or non-positive pivot");
   }
   return VMC_OK;
+}
+
+MadeDev made_of(vmc_ctx* ctx, LatticeState& L) {
+  return made_view(L.made, L.W1t, L.W2t, L.W3t, L.N, ctx->cfg.made_hidden);
 }
 
 vmc_status lattice_ok(vmc_ctx* ctx, int lattice) {
@@ -201,6 +219,9 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
   if (cfg->solver < 0 || cfg->solver > 3 || (cfg->shift_mode != 0 && cfg->shift_mode != 1))
     return VMC_ERR_ARG;
   if (!(cfg->shift >= 0.0)) return VMC_ERR_ARG;
+  if (cfg->made_hidden < 0 || cfg->made_hidden > 512 || cfg->made_hidden % 32 != 0 ||
+      cfg->made_batch < 0)
+    return VMC_ERR_ARG;
   for (int l = 0; l < n_lattices; ++l) {
     const vmc_lattice& L = lattices[l];
     const int N = L.Lx * L.Ly;
@@ -241,6 +262,32 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
     std::vector<int8_t> up((size_t)cfg->n_chains * L.N, 1);
     cudaMemcpy(L.chains, up.data(), up.size(), cudaMemcpyHostToDevice);
     launch_param_prep(L.params, L.N, L.M, L.a, L.b, L.Wt, ctx->st);
+    if (cfg->made_hidden > 0) {
+      const int H = cfg->made_hidden;
+      const int64_t np = made_nparams(L.N, H);
+      const size_t C = (size_t)cfg->n_chains;
+      if ((e = dalloc(ctx, &L.made, np)) || (e = dalloc(ctx, &L.made_m, np)) ||
+          (e = dalloc(ctx, &L.made_v, np)) || (e = dalloc(ctx, &L.made_g, np)) ||
+          (e = dalloc(ctx, &L.W1t, (size_t)H * L.N)) || (e = dalloc(ctx, &L.W2t, (size_t)H * H)) ||
+          (e = dalloc(ctx, &L.W3t, (size_t)H * L.N)) || (e = dalloc(ctx, &L.chain_lp, C)) ||
+          (e = dalloc(ctx, &L.chain_lq, C)) || (e = dalloc(ctx, &L.prop, C * L.N)) ||
+          (e = dalloc(ctx, &L.prop_lq, C)) || (e = dalloc(ctx, &L.prop_lp, C)))
+        return oom(e);
+      cudaMemset(L.made, 0, np * sizeof(float));
+      cudaMemset(L.made_m, 0, np * sizeof(float));
+      cudaMemset(L.made_v, 0, np * sizeof(float));
+      launch_made_transpose(made_view(L.made, L.W1t, L.W2t, L.W3t, L.N, H), ctx->st);
+    }
+  }
+  if (cfg->made_hidden > 0) {
+    const int H = cfg->made_hidden;
+    const int64_t B = std::max<int64_t>(cfg->made_batch > 0 ? cfg->made_batch : 4096, cfg->n_chains);
+    ctx->made_cap = B;
+    if ((e = dalloc(ctx, &ctx->mw.logq, B)) || (e = dalloc(ctx, &ctx->mw.H1, (size_t)B * H)) ||
+        (e = dalloc(ctx, &ctx->mw.H2, (size_t)B * H)) || (e = dalloc(ctx, &ctx->mw.G1, (size_t)B * H)) ||
+        (e = dalloc(ctx, &ctx->mw.G2, (size_t)B * H)) ||
+        (e = dalloc(ctx, &ctx->mw.G3, (size_t)B * ctx->Nmax)))
+      return oom(e);
   }
   const int64_t Ns = ctx->Ns;
   if ((e = dalloc(ctx, &ctx->s_spins, (size_t)Ns * ctx->Nmax)) ||
@@ -336,6 +383,7 @@ vmc_status vmc_set_params(vmc_ctx* ctx, int lattice, const double* params_host) 
      "set_params");
   if ((s = refresh_fp32(ctx, L))) return s;
   CK(cudaStreamSynchronize(ctx->st), "set_params");
+  L.chain_cache = false;
   return VMC_OK;
 }
 
@@ -362,6 +410,7 @@ vmc_status vmc_set_chains(vmc_ctx* ctx, int lattice, const int8_t* spins_host) {
   CK(cudaStreamSynchronize(ctx->st), "set_chains");
   L.sweep = 0;
   L.thermalized = false;
+  L.chain_cache = false;
   return VMC_OK;
 }
 
@@ -573,6 +622,7 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   CK(cudaEventRecord(ctx->ev[4], ctx->st), "sr_step");
   // 5. Euler update of the FP64 master parameters, refresh the FP32 copies
   CK(launch_update(L.params, ctx->x, L.P, dt, ctx->st), "update");
+  L.chain_cache = false;
   ++ctx->launches;
   if ((s = refresh_fp32(ctx, L))) return s;
   CK(cudaEventRecord(ctx->ev[5], ctx->st), "sr_step");
@@ -600,6 +650,157 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
     cudaEventElapsedTime(&stats->ms_gram, ctx->ev[6], ctx->ev[7]);
     stats->launches = ctx->launches - launches0;
   }
+  return VMC_OK;
+}
+
+
+static vmc_status made_ok(vmc_ctx* ctx, int lattice) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (ctx->cfg.made_hidden <= 0) return fail(ctx, VMC_ERR_STATE, "context has no learned proposal (made_hidden = 0)");
+  return VMC_OK;
+}
+
+vmc_status vmc_made_set_params(vmc_ctx* ctx, int lattice, const float* params_host) {
+  vmc_status s = made_ok(ctx, lattice);
+  if (s) return s;
+  if (!params_host) return fail(ctx, VMC_ERR_ARG, "params_host is NULL");
+  LatticeState& L = ctx->lats[lattice];
+  const int64_t np = made_nparams(L.N, ctx->cfg.made_hidden);
+  CK(cudaMemcpyAsync(L.made, params_host, np * sizeof(float), cudaMemcpyHostToDevice, ctx->st), "made_set_params");
+  CK(cudaMemsetAsync(L.made_m, 0, np * sizeof(float), ctx->st), "made_set_params");
+  CK(cudaMemsetAsync(L.made_v, 0, np * sizeof(float), ctx->st), "made_set_params");
+  CK(launch_made_transpose(made_of(ctx, L), ctx->st), "made_transpose");
+  ++ctx->launches;
+  L.made_t = 0;
+  L.chain_cache = false;
+  CK(cudaStreamSynchronize(ctx->st), "made_set_params");
+  return VMC_OK;
+}
+
+vmc_status vmc_made_get_params(vmc_ctx* ctx, int lattice, float* params_host) {
+  vmc_status s = made_ok(ctx, lattice);
+  if (s) return s;
+  if (!params_host) return fail(ctx, VMC_ERR_ARG, "params_host is NULL");
+  LatticeState& L = ctx->lats[lattice];
+  const int64_t np = made_nparams(L.N, ctx->cfg.made_hidden);
+  CK(cudaMemcpyAsync(params_host, L.made, np * sizeof(float), cudaMemcpyDeviceToHost, ctx->st), "made_get_params");
+  CK(cudaStreamSynchronize(ctx->st), "made_get_params");
+  return VMC_OK;
+}
+
+vmc_status vmc_made_logq(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* logq) {
+  vmc_status s = made_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!spins || !logq))) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_made_logq(made_of(ctx, L), spins, n, logq, ctx->st), "made_logq");
+  ++ctx->launches;
+  return VMC_OK;
+}
+
+static double mean_neg(const float* d_logq, int64_t n, vmc_ctx* ctx) {
+  std::vector<float> h((size_t)n);
+  cudaMemcpyAsync(h.data(), d_logq, n * sizeof(float), cudaMemcpyDeviceToHost, ctx->st);
+  cudaStreamSynchronize(ctx->st);
+  double acc = 0.0;
+  for (float v : h) acc -= (double)v;
+  return acc / (double)n;
+}
+
+vmc_status vmc_made_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* grad,
+                         double* loss) {
+  vmc_status s = made_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 1 || n > ctx->made_cap || !spins || !grad) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_made_grad(made_of(ctx, L), spins, n, ctx->mw, grad, ctx->st), "made_grad");
+  ctx->launches += 7;
+  const double l = mean_neg(ctx->mw.logq, n, ctx);
+  if (loss) *loss = l;
+  return check_status(ctx, "made_grad");
+}
+
+vmc_status vmc_proposal_train(vmc_ctx* ctx, int lattice, const int8_t* samples, int64_t n,
+                              int epochs, double lr, double* loss) {
+  vmc_status s = made_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 1 || epochs < 0 || !samples || !(lr > 0.0)) return fail(ctx, VMC_ERR_ARG, "bad training arguments");
+  LatticeState& L = ctx->lats[lattice];
+  const int64_t B = std::min<int64_t>(ctx->cfg.made_batch > 0 ? ctx->cfg.made_batch : 4096, ctx->made_cap);
+  const int64_t np = made_nparams(L.N, ctx->cfg.made_hidden);
+  MadeDev D = made_of(ctx, L);
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int64_t b0 = 0; b0 < n; b0 += B) {
+      const int64_t nb = std::min<int64_t>(B, n - b0);
+      CK(launch_made_grad(D, samples + b0 * L.N, nb, ctx->mw, L.made_g, ctx->st), "made_grad");
+      CK(launch_adam(L.made, L.made_m, L.made_v, L.made_g, np, ++L.made_t, (float)lr, ctx->st), "adam");
+      CK(launch_made_transpose(D, ctx->st), "made_transpose");
+      ctx->launches += 9;
+    }
+  }
+  L.chain_cache = false;
+  if (loss) {
+    double acc = 0.0;
+    for (int64_t b0 = 0; b0 < n; b0 += B) {
+      const int64_t nb = std::min<int64_t>(B, n - b0);
+      CK(launch_made_logq(D, samples + b0 * L.N, nb, ctx->mw.logq, ctx->st), "made_logq");
+      ++ctx->launches;
+      acc += mean_neg(ctx->mw.logq, nb, ctx) * (double)nb;
+    }
+    *loss = acc / (double)n;
+  }
+  return check_status(ctx, "proposal_train");
+}
+
+vmc_status vmc_made_sample(vmc_ctx* ctx, int lattice, int64_t n, uint64_t round, int8_t* spins,
+                           float* logq) {
+  vmc_status s = made_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && !spins)) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_made_sample(made_of(ctx, L), n, ctx->cfg.seed, (uint64_t)lattice, round, spins, logq,
+                        ctx->st), "made_sample");
+  ++ctx->launches;
+  return VMC_OK;
+}
+
+vmc_status vmc_sample_learned(vmc_ctx* ctx, int lattice, int n_rounds, int8_t* spins_out,
+                              float* eloc_out, double* acceptance) {
+  vmc_status s = made_ok(ctx, lattice);
+  if (s) return s;
+  if (n_rounds < 0) return fail(ctx, VMC_ERR_ARG, "negative round count");
+  LatticeState& L = ctx->lats[lattice];
+  const int64_t C = ctx->cfg.n_chains;
+  MadeDev D = made_of(ctx, L);
+  if (!L.chain_cache) {
+    CK(launch_logpsi(rbm_of(L), L.chains, C, L.chain_lp, ctx->status, ctx->st), "logpsi");
+    CK(launch_made_logq(D, L.chains, C, L.chain_lq, ctx->st), "made_logq");
+    ctx->launches += 2;
+    L.chain_cache = true;
+  }
+  CK(cudaMemsetAsync(ctx->n_accept, 0, sizeof(unsigned long long), ctx->st), "sample_learned");
+  for (int r = 0; r < n_rounds; ++r) {
+    const uint64_t round = L.made_round++;
+    CK(launch_made_sample(D, C, ctx->cfg.seed, (uint64_t)lattice, round, L.prop, L.prop_lq, ctx->st),
+       "made_sample");
+    CK(launch_logpsi(rbm_of(L), L.prop, C, L.prop_lp, ctx->status, ctx->st), "logpsi");
+    CK(launch_made_mh(C, L.N, L.prop, L.prop_lp, L.prop_lq, L.chains, L.chain_lp, L.chain_lq,
+                      ctx->cfg.seed, (uint64_t)lattice, round, ctx->n_accept, ctx->st), "made_mh");
+    ctx->launches += 3;
+    if (spins_out)
+      CK(cudaMemcpyAsync(spins_out + (int64_t)r * C * L.N, L.chains, (size_t)C * L.N,
+                         cudaMemcpyDeviceToDevice, ctx->st), "sample_learned");
+    if (eloc_out) {
+      CK(launch_eloc(rbm_of(L), lat_of(L), L.chains, C,
+                     reinterpret_cast<float2*>(eloc_out) + (int64_t)r * C, ctx->status, ctx->st), "eloc");
+      ++ctx->launches;
+    }
+  }
+  unsigned long long acc = 0;
+  CK(cudaMemcpyAsync(&acc, ctx->n_accept, sizeof(acc), cudaMemcpyDeviceToHost, ctx->st), "sample_learned");
+  if ((s = check_status(ctx, "sample_learned"))) return s;
+  if (acceptance) *acceptance = (n_rounds > 0) ? (double)acc / ((double)C * n_rounds) : 0.0;
   return VMC_OK;
 }
 

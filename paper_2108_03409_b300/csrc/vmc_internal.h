@@ -158,6 +158,34 @@ cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cuda
 cudaError_t cg_solve(const CgProblem& pb, const double2* F, double2* x, double tol, int maxit,
                      CgWork& w, cudaStream_t st, int64_t* launches, int* iters, double* relres);
 
+// ---- made.cu ---------------------------------------------------------------------------
+struct MadeDev {
+  int N, H;
+  const float *W1, *b1, *W2, *b2, *W3, *b3;   // canonical layout (views into theta)
+  const float *W1t, *W2t, *W3t;               // transposed copies
+};
+struct MadeWork {                             // batch workspaces, rows <= capacity
+  float* logq;                                // [B]
+  float *H1, *H2, *G1, *G2;                   // [B][H]
+  float* G3;                                  // [B][N]
+};
+int64_t made_nparams(int N, int H);
+MadeDev made_view(float* theta, float* W1t, float* W2t, float* W3t, int N, int H);
+cudaError_t launch_made_transpose(const MadeDev& D, cudaStream_t st);
+cudaError_t launch_made_logq(const MadeDev& D, const int8_t* spins, int64_t n, float* logq,
+                             cudaStream_t st);
+// gradient of -(1/n) sum log q over the batch into grad (canonical layout); w.logq holds log q
+cudaError_t launch_made_grad(const MadeDev& D, const int8_t* spins, int64_t n, MadeWork& w,
+                             float* grad, cudaStream_t st);
+cudaError_t launch_adam(float* th, float* m, float* v, const float* g, int64_t np, int t, float lr,
+                        cudaStream_t st);
+cudaError_t launch_made_sample(const MadeDev& D, int64_t n, uint64_t seed, uint64_t stream,
+                               uint64_t round, int8_t* spins, float* logq, cudaStream_t st);
+cudaError_t launch_made_mh(int64_t C, int N, const int8_t* prop, const float2* prop_lp,
+                           const float* prop_lq, int8_t* chains, float2* chain_lp,
+                           float* chain_lq, uint64_t seed, uint64_t stream, uint64_t round,
+                           unsigned long long* accepts, cudaStream_t st);
+
 // theta <- theta - dt * x, then refresh the FP32 copies
 cudaError_t launch_update(double2* params, const double2* x, int64_t P, double dt,
                           cudaStream_t st);

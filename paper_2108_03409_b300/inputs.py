@@ -48,6 +48,17 @@ def rbm_params(N: int, M: int, sigma: float, seed: int,
     return p
 
 
+def made_params(N: int, H: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Initial parameters of the learned proposal, float32, layout W1[H][N] | b1[H] |
+    W2[H][H] | b2[H] | W3[N][H] | b3[N]: weights N(0, scale^2 / fan_in), biases zero."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0.0, scale / np.sqrt(N), (H, N))
+    W2 = rng.normal(0.0, scale / np.sqrt(H), (H, H))
+    W3 = rng.normal(0.0, scale / np.sqrt(H), (N, H))
+    return np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3.ravel(),
+                           np.zeros(N)]).astype(np.float32)
+
+
 def random_spins(C: int, N: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return (1 - 2 * rng.integers(0, 2, size=(C, N))).astype(np.int8)

@@ -40,7 +40,8 @@ class vmc_config(ctypes.Structure):
                 ("therm_sweeps", ctypes.c_int), ("sweeps_per_sample", ctypes.c_int),
                 ("samples_per_chain", ctypes.c_int), ("precision", ctypes.c_int),
                 ("solver", ctypes.c_int), ("shift", ctypes.c_double), ("shift_mode", ctypes.c_int),
-                ("cg_maxit", ctypes.c_int), ("cg_tol", ctypes.c_double)]
+                ("cg_maxit", ctypes.c_int), ("cg_tol", ctypes.c_double),
+                ("made_hidden", ctypes.c_int), ("made_batch", ctypes.c_int)]
 
 
 class vmc_sr_stats(ctypes.Structure):
@@ -60,7 +61,9 @@ class vmc_sr_stats(ctypes.Structure):
 EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
             "vmc_set_chains", "vmc_get_chains", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
             "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
-            "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve"]
+            "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve",
+            "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
+            "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned"]
 
 _lib = None
 
@@ -96,6 +99,13 @@ def load(path: str = LIB_PATH):
         "vmc_num_params": (i64, [P, i32]),
         "vmc_force_noalloc": (i32, [P, P, P, i64, i32, i32, P, P, P]),
         "vmc_cg_solve": (i32, [P, i32, P, i64, P, P, ctypes.POINTER(i32), ctypes.POINTER(f64)]),
+        "vmc_made_set_params": (i32, [P, i32, P]),
+        "vmc_made_get_params": (i32, [P, i32, P]),
+        "vmc_made_logq": (i32, [P, i32, P, i64, P]),
+        "vmc_made_grad": (i32, [P, i32, P, i64, P, ctypes.POINTER(f64)]),
+        "vmc_proposal_train": (i32, [P, i32, P, i64, i32, f64, ctypes.POINTER(f64)]),
+        "vmc_made_sample": (i32, [P, i32, i64, ctypes.c_uint64, P, P]),
+        "vmc_sample_learned": (i32, [P, i32, i32, P, P, ctypes.POINTER(f64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -124,9 +134,10 @@ def _check(ctx, status: int):
 def make_config(seed=1, n_chains=256, sweep_len=0, therm_sweeps=20, sweeps_per_sample=1,
                 samples_per_chain=1, precision=PREC_FP32, solver=SOLVER_CHOLESKY_FP64,
                 shift=1e-4, shift_mode=SHIFT_MULTIPLICATIVE, cg_maxit=100,
-                cg_tol=1e-10) -> vmc_config:
+                cg_tol=1e-10, made_hidden=0, made_batch=0) -> vmc_config:
     return vmc_config(seed, n_chains, sweep_len, therm_sweeps, sweeps_per_sample,
-                      samples_per_chain, precision, solver, shift, shift_mode, cg_maxit, cg_tol)
+                      samples_per_chain, precision, solver, shift, shift_mode, cg_maxit, cg_tol,
+                      made_hidden, made_batch)
 
 
 def make_lattice(model, Lx, Ly=1, J=1.0, h=0.0, alpha=1) -> vmc_lattice:
@@ -245,3 +256,49 @@ def vmc_force_noalloc(spins, tanh_theta, eloc, N, M, F_out, meanO_out=None, stre
                                   _ptr(F_out), _ptr(meanO_out), ctypes.c_void_p(stream or None))
     if st != VMC_OK:
         raise VmcError(st, "vmc_force_noalloc failed")
+
+
+# --------------------------------------------------------------------------------------
+# learned proposal
+# --------------------------------------------------------------------------------------
+def vmc_made_set_params(ctx, lattice, params_host):
+    import numpy as np
+    p = np.ascontiguousarray(params_host, dtype=np.float32)
+    _check(ctx, load().vmc_made_set_params(ctx, lattice, p.ctypes.data))
+
+
+def vmc_made_get_params(ctx, lattice, n_params):
+    import numpy as np
+    out = np.zeros(n_params, dtype=np.float32)
+    _check(ctx, load().vmc_made_get_params(ctx, lattice, out.ctypes.data))
+    return out
+
+
+def vmc_made_logq(ctx, lattice, spins, out):
+    _check(ctx, load().vmc_made_logq(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(out)))
+
+
+def vmc_made_grad(ctx, lattice, spins, grad_out):
+    loss = ctypes.c_double(0.0)
+    _check(ctx, load().vmc_made_grad(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(grad_out),
+                                     ctypes.byref(loss)))
+    return loss.value
+
+
+def vmc_proposal_train(ctx, lattice, samples, epochs, lr=1e-3):
+    loss = ctypes.c_double(0.0)
+    _check(ctx, load().vmc_proposal_train(ctx, lattice, _ptr(samples), samples.shape[0],
+                                          int(epochs), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def vmc_made_sample(ctx, lattice, n, round_, spins_out, logq_out=None):
+    _check(ctx, load().vmc_made_sample(ctx, lattice, int(n), int(round_), _ptr(spins_out),
+                                       _ptr(logq_out)))
+
+
+def vmc_sample_learned(ctx, lattice, n_rounds, spins_out=None, eloc_out=None):
+    acc = ctypes.c_double(0.0)
+    _check(ctx, load().vmc_sample_learned(ctx, lattice, int(n_rounds), _ptr(spins_out),
+                                          _ptr(eloc_out), ctypes.byref(acc)))
+    return acc.value
