@@ -21,7 +21,6 @@ import argparse
 import json
 import os
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -46,6 +45,9 @@ WORKLOADS = {
     "tfim1d_N10_alpha1_c256": dict(model=0, Lx=10, Ly=1, J=1.0, h=1.0, alpha=1, chains=256,
                                    spc=200, shift=1e-4, solver="mixed", marshall=False),
 }
+# batched sampling of many independent lattices (one sweep + a record per chain per step)
+BATCHED = {"tfim2d_batched48_alpha2_c1024": dict(sizes=[4] * 16 + [6] * 16 + [8] * 16, alpha=2,
+                                                 chains=1024, h_lo=2.0, h_hi=4.0, h_seed=7)}
 DEFAULT_WORKLOAD = "heis2d_8x8_alpha2_c8192"
 W = WORKLOADS[DEFAULT_WORKLOAD]
 LX, LY, ALPHA, CHAINS, SHIFT = W["Lx"], W["Ly"], W["alpha"], W["chains"], W["shift"]
@@ -62,52 +64,71 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """SM clocks, power and clock-event (throttle) reasons, read through NVML every 20 ms
+    during the timed region (one reading on entry and one on exit, so that even a short
+    region has samples).  Reads only; changes no setting."""
+    BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+            "sw_power_cap": 0x4}
 
     def __init__(self, index: int):
         self.index = index
         self.rows = []
-        self.proc = None
+        self.h = None
+        self.stop = threading.Event()
+
+    def _handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(self.index).uuid)
+            return pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+        except Exception:
+            return pynvml.nvmlDeviceGetHandleByIndex(self.index)
+
+    def _sample(self):
+        import pynvml
+        sm = pynvml.nvmlDeviceGetClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+        mx = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+        try:
+            r = pynvml.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+        except Exception:
+            r = pynvml.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
+        self.rows.append((float(sm), float(mx), int(r)))
+
+    def _loop(self):
+        while not self.stop.wait(0.02):
+            try:
+                self._sample()
+            except Exception:
+                return
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
+            self.h = self._handle()
+            self._sample()
+            self.t = threading.Thread(target=self._loop, daemon=True)
             self.t.start()
         except Exception:
-            self.proc = None
+            self.h = None
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) >= 9:
-                self.rows.append(parts)
-
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
+        if self.h is not None:
+            self.stop.set()
+            self.t.join(timeout=1)
             try:
-                self.proc.wait(timeout=5)
+                self._sample()
             except Exception:
-                self.proc.kill()
+                pass
 
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows for k in range(4)
-                          if r[5 + k].lower().startswith("active")})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+        reasons = sorted({k for (_, _, r) in self.rows for k, bit in self.BITS.items() if r & bit})
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                "sm_max_mhz": max(r[1] for r in self.rows), "reasons": reasons,
+                "samples": len(self.rows), "source": "NVML, 20 ms"}
 
 
 def dist_env():
@@ -314,6 +335,137 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batched(args):
+    """48 TFIM lattices of uneven size: one persistent launch (autotuned, CUDA graph) per
+    step against 48 per-lattice launches of the same sweeps.  A step is one sweep of every
+    chain of every lattice plus the record (spins and fused E_loc) of each chain."""
+    import torch
+    from paper_2108_03409_b300 import build as vbuild
+    from paper_2108_03409_b300 import inputs, vmc
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    vbuild.build()
+    wl = BATCHED[args.workload]
+    C, alpha = wl["chains"], wl["alpha"]
+    hs = inputs.uniform_fields(len(wl["sizes"]), wl["h_lo"], wl["h_hi"], wl["h_seed"])
+    lats = [vmc.make_lattice(vmc.MODEL_TFIM, L, L, 1.0, float(h), alpha)
+            for L, h in zip(wl["sizes"], hs)]
+    Ns_ = [L * L for L in wl["sizes"]]
+    stream = torch.cuda.current_stream()
+    cfg = vmc.make_config(seed=1 + rank, n_chains=C, solver=vmc.SOLVER_CG)
+    ctx = vmc.vmc_init(cfg, lats, stream.cuda_stream)
+    for l, N in enumerate(Ns_):
+        vmc.vmc_set_params(ctx, l, inputs.rbm_params(N, alpha * N, 0.01, seed=1234 + l))
+        vmc.vmc_set_chains(ctx, l, inputs.random_spins(C, N, seed=99 + 1000 * rank + l))
+    n_lat, tot = len(Ns_), sum(Ns_)
+    spins = torch.zeros(C * tot, dtype=torch.int8, device="cuda")
+    eloc = torch.zeros((n_lat * C, 2), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    outs = []
+    off = 0
+    for N in Ns_:
+        outs.append(spins[off:off + C * N].view(C, N))
+        off += C * N
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    vmc.vmc_sample_all(ctx, 20, 0, None, None, False)       # thermalise (and autotune)
+    for _ in range(args.warmup):
+        vmc.vmc_sample_all(ctx, 0, 1, spins, eloc, True)
+        for l in range(n_lat):
+            vmc.vmc_sample(ctx, l, 0, 1, outs[l], None, eloc[l * C:(l + 1) * C])
+    barrier()
+
+    def timed(fn):
+        evs = []
+        for _ in range(args.steps):
+            flush.zero_()               # L2 flushed between timed iterations
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        barrier()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    launches0 = vmc.vmc_kernel_launches(ctx)
+    with ClockSampler(local) as clk:
+        ms_b = timed(lambda: vmc.vmc_sample_all(ctx, 0, 1, spins, eloc, True))
+    launches = vmc.vmc_kernel_launches(ctx) - launches0
+
+    def per_lattice():
+        for l in range(n_lat):
+            vmc.vmc_sample(ctx, l, 0, 1, outs[l], None, eloc[l * C:(l + 1) * C])
+    ms_p = timed(per_lattice)
+    ms_ng = timed(lambda: vmc.vmc_sample_all(ctx, 0, 1, spins, eloc, False))
+    ms_t = torch.tensor([ms_b, ms_p, ms_ng], device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_b, ms_p, ms_ng = (float(x) for x in ms_t.tolist())
+    samples = n_lat * C
+    value = ws * samples * args.steps / (ms_b / 1e3)
+
+    # e2e: the chains in from pinned host memory and the records out, every step
+    host_in = [torch.from_numpy(vmc.vmc_get_chains(ctx, l, C, N)).pin_memory()
+               for l, N in enumerate(Ns_)]
+    host_s = torch.empty(C * tot, dtype=torch.int8).pin_memory()
+    host_e = torch.empty((n_lat * C, 2), dtype=torch.float32).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for l in range(n_lat):
+            vmc.load().vmc_set_chains(ctx, l, host_in[l].data_ptr())
+        vmc.vmc_sample_all(ctx, 0, 1, spins, eloc, True)
+        host_s.copy_(spins)
+        host_e.copy_(eloc)
+    barrier()
+    e2e = ws * samples * args.steps / (time.perf_counter() - t0)
+
+    # ALU roofline of the persistent sweep kernel: per proposed flip and hidden unit the
+    # ratio cosh(theta - d)/cosh(theta) = cosh d - tanh(theta) sinh d and its squared
+    # modulus take 22 FP32 operations (18 arithmetic, 4 elementary functions counted once), so one
+    # step does 22 * sum_l C * N_l * M_l flops of the acceptance test.
+    flops = 22.0 * sum(C * N * alpha * N for N in Ns_)
+    pk, pk_kind = peaks()
+    fp32_peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    achieved = flops / (ms_b / args.steps / 1e3) / 1e12
+    out = {"metric": METRIC, "value": value, "unit": "samples/s (incl. E_loc)", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "lattices": "16 x 4x4, 16 x 6x6, 16 x 8x8 TFIM",
+                      "alpha": alpha, "chains_per_lattice": C, "h": "U[2,4] seed 7",
+                      "l2": "flushed (256 MB write) before every timed step",
+                      "parallelism": f"replicas x{ws}"},
+           "per_lattice_launches": {"value": ws * samples * args.steps / (ms_p / 1e3),
+                                    "ms_per_step": ms_p / args.steps},
+           "batched_no_graph": {"value": ws * samples * args.steps / (ms_ng / 1e3),
+                                "ms_per_step": ms_ng / args.steps},
+           "speedup_vs_per_lattice": ms_p / ms_b,
+           "autotuned_warps_per_block": vmc.vmc_autotuned_warps_per_block(ctx),
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                        "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                        "kernel": "sample_batched",
+                        "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock",
+                        "algorithmic": "22 flops per proposed flip per hidden unit"},
+           "e2e": {"value": e2e, "unit": "samples/s (incl. E_loc)",
+                   "h2d_bytes_per_step": C * tot, "d2h_bytes_per_step": C * tot + n_lat * C * 8},
+           "gpu_launches": launches,
+           "clocks": clk.summary()}
+    vmc.vmc_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,11 +474,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16split", choices=["fp32", "bf16split"])
     ap.add_argument("--solver", default=None, choices=["mixed", "tc", "fp64", "cg"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS) + sorted(BATCHED))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in BATCHED:
+        run_batched(args)
     else:
         run_ours(args)
 

@@ -225,6 +225,21 @@ vmc_status vmc_made_sample(vmc_ctx* ctx, int lattice, int64_t n, uint64_t round,
 vmc_status vmc_sample_learned(vmc_ctx* ctx, int lattice, int n_rounds, int8_t* spins_out,
                               float* eloc_out, double* acceptance);
 
+/* Every chain of every lattice in one persistent launch (batched sampling of many
+ * independent lattices of uneven size): warps take (lattice, chain) work items from an
+ * atomic counter, the most expensive lattices first, and run the same sweeps, records and
+ * Philox streams as vmc_sample does per lattice (n_therm sweeps, then n_samples records).
+ * Outputs (dev, may be NULL): spins_out holds lattice l's samples [n_samples][n_chains][N_l]
+ * starting at byte n_samples * n_chains * (N_0 + ... + N_{l-1}); eloc_out is
+ * [n_lattices][n_samples * n_chains][2].  The first call autotunes the warps per block of the
+ * persistent grid (timed on one sweep; chains restored).  use_graph = 1 captures the launch
+ * into a CUDA graph and replays it while (n_therm, n_samples, spins_out, eloc_out) stay the
+ * same.  ms (host, may be NULL) receives the device time of the call.  Synchronises. */
+vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spins_out,
+                          float* eloc_out, int use_graph, double* ms);
+/* Warps per block chosen by the autotuner (0 before the first vmc_sample_all). */
+int vmc_autotuned_warps_per_block(const vmc_ctx* ctx);
+
 /* Number of kernel launches the library has issued on this context since it was created
  * (a counter kept by the host code). */
 int64_t vmc_kernel_launches(const vmc_ctx* ctx);

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points of libvmc (declared in include/vmc.h): context
 // life cycle, parameter and chain transfer, and the steps of Algorithm 1 (sample,
 // evaluate, gradients, local energies, S and F, solve) followed by the Euler update.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -68,6 +69,20 @@ struct vmc_ctx {
   CgWork cg{};
   MadeWork mw{};
   int64_t made_cap = 0;           // rows of the MADE batch workspaces
+  // batched sampler
+  SampleArgs* d_bargs = nullptr;  // [n_lattices] device descriptors
+  int* d_order = nullptr;         // heavy-first lattice order
+  unsigned* d_counter = nullptr;  // work-queue counter
+  int8_t* chain_backup = nullptr; // chains of all lattices (autotuning runs restore them)
+  int tuned_wpb = 0, tuned_grid = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_st = nullptr;  // private stream the graph is captured on (the context's
+                                  // own stream may be the legacy default stream)
+  int g_therm = -1, g_samples = -1;  // arguments the captured graph was made for
+  std::vector<uint64_t> g_sweep;      // sweep counters the device descriptors hold
+  int8_t* g_spins = nullptr;
+  float* g_eloc = nullptr;
   unsigned* status = nullptr;
   unsigned long long* n_accept = nullptr;
   int64_t launches = 0;
@@ -279,6 +294,14 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
       launch_made_transpose(made_view(L.made, L.W1t, L.W2t, L.W3t, L.N, H), ctx->st);
     }
   }
+  {
+    size_t chain_bytes = 0;
+    for (auto& L : ctx->lats) chain_bytes += (size_t)cfg->n_chains * L.N;
+    if ((e = dalloc(ctx, &ctx->d_bargs, ctx->lats.size())) ||
+        (e = dalloc(ctx, &ctx->d_order, ctx->lats.size())) || (e = dalloc(ctx, &ctx->d_counter, 1)) ||
+        (e = dalloc(ctx, &ctx->chain_backup, chain_bytes)))
+      return oom(e);
+  }
   if (cfg->made_hidden > 0) {
     const int H = cfg->made_hidden;
     const int64_t B = std::max<int64_t>(cfg->made_batch > 0 ? cfg->made_batch : 4096, cfg->n_chains);
@@ -359,6 +382,9 @@ void vmc_destroy(vmc_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
   else cudaDeviceSynchronize();
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+  if (ctx->graph) cudaGraphDestroy(ctx->graph);
+  if (ctx->cap_st) cudaStreamDestroy(ctx->cap_st);
   for (void* p : ctx->allocs) cudaFree(p);
   for (auto& ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
@@ -803,5 +829,153 @@ vmc_status vmc_sample_learned(vmc_ctx* ctx, int lattice, int n_rounds, int8_t* s
   if (acceptance) *acceptance = (n_rounds > 0) ? (double)acc / ((double)C * n_rounds) : 0.0;
   return VMC_OK;
 }
+
+
+static vmc_status batched_upload(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spins_out,
+                                 float* eloc_out) {
+  const int nl = (int)ctx->lats.size();
+  const int C = ctx->cfg.n_chains;
+  std::vector<SampleArgs> args((size_t)nl);
+  int64_t off = 0;
+  for (int l = 0; l < nl; ++l) {
+    LatticeState& L = ctx->lats[l];
+    SampleArgs& A = args[(size_t)l];
+    A = SampleArgs{};
+    A.rbm = rbm_of(L);
+    A.lat = lat_of(L);
+    A.chains = L.chains;
+    A.C = C;
+    A.L = ctx->cfg.sweep_len > 0 ? ctx->cfg.sweep_len : L.N;
+    A.seed = ctx->cfg.seed;
+    A.stream = (uint64_t)l;
+    A.sweep0 = L.sweep;
+    A.n_therm = n_therm;
+    A.n_samples = n_samples;
+    A.sweeps_per_sample = ctx->cfg.sweeps_per_sample;
+    A.spins_out = spins_out ? spins_out + off : nullptr;
+    A.eloc_out = eloc_out ? reinterpret_cast<float2*>(eloc_out) + (int64_t)l * n_samples * C : nullptr;
+    A.n_accept = ctx->n_accept;
+    A.status = ctx->status;
+    off += (int64_t)n_samples * C * L.N;
+  }
+  // heavy lattices first (work per chain ~ N * M)
+  std::vector<int> order((size_t)nl);
+  for (int l = 0; l < nl; ++l) order[(size_t)l] = l;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return (int64_t)ctx->lats[x].N * ctx->lats[x].M > (int64_t)ctx->lats[y].N * ctx->lats[y].M;
+  });
+  CK(cudaMemcpyAsync(ctx->d_bargs, args.data(), sizeof(SampleArgs) * nl, cudaMemcpyHostToDevice, ctx->st), "sample_all");
+  CK(cudaMemcpyAsync(ctx->d_order, order.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, ctx->st), "sample_all");
+  CK(cudaStreamSynchronize(ctx->st), "sample_all");
+  return VMC_OK;
+}
+
+// Autotuner: warps per block of the persistent launch, timed on one sweep of every chain
+// (chains saved before and restored after; sweep counters untouched).
+static vmc_status batched_tune(vmc_ctx* ctx) {
+  ctx->g_therm = -1;
+  const int nl = (int)ctx->lats.size();
+  const int C = ctx->cfg.n_chains;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev), "tune");
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "tune");
+  vmc_status s;
+  if ((s = batched_upload(ctx, 1, 0, nullptr, nullptr))) return s;
+  size_t off = 0;
+  for (auto& L : ctx->lats) {
+    CK(cudaMemcpyAsync(ctx->chain_backup + off, L.chains, (size_t)C * L.N, cudaMemcpyDeviceToDevice, ctx->st), "tune");
+    off += (size_t)C * L.N;
+  }
+  float best = 1e30f;
+  const int cand[3] = {2, 4, 8};
+  for (int wpb : cand) {
+    const int per_sm = batched_blocks_per_sm(ctx->Mmax, wpb, ctx->Nmax);
+    if (per_sm < 1) continue;
+    const int grid = sms * per_sm;
+    CK(cudaEventRecord(ctx->ev[0], ctx->st), "tune");
+    CK(launch_sample_batched(ctx->d_bargs, ctx->d_order, nl, C, ctx->Nmax, ctx->Mmax, ctx->d_counter,
+                             wpb, grid, 0, ctx->d_bargs, ctx->st), "tune");
+    CK(cudaEventRecord(ctx->ev[1], ctx->st), "tune");
+    CK(cudaEventSynchronize(ctx->ev[1]), "tune");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    ctx->launches += 2;
+    if (ms < best) { best = ms; ctx->tuned_wpb = wpb; ctx->tuned_grid = grid; }
+    off = 0;
+    for (auto& L : ctx->lats) {
+      CK(cudaMemcpyAsync(L.chains, ctx->chain_backup + off, (size_t)C * L.N, cudaMemcpyDeviceToDevice, ctx->st), "tune");
+      off += (size_t)C * L.N;
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->st), "tune");
+  if (ctx->tuned_wpb == 0) return fail(ctx, VMC_ERR_CUDA, "no launch configuration fits");
+  return check_status(ctx, "tune");
+}
+
+vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spins_out,
+                          float* eloc_out, int use_graph, double* ms) {
+  if (!ctx) return VMC_ERR_ARG;
+  if (n_therm < 0 || n_samples < 0) return fail(ctx, VMC_ERR_ARG, "negative sweep count");
+  vmc_status s;
+  if (ctx->tuned_wpb == 0 && (s = batched_tune(ctx))) return s;
+  const int nl = (int)ctx->lats.size();
+  const int C = ctx->cfg.n_chains;
+  const uint64_t adv = (uint64_t)n_therm + (uint64_t)n_samples * ctx->cfg.sweeps_per_sample;
+  // a replay is valid only while the device descriptors still describe this call: same
+  // arguments, and no per-lattice sampling or chain reset moved a sweep counter since
+  bool same = ctx->graph_exec && ctx->g_therm == n_therm && ctx->g_samples == n_samples &&
+              ctx->g_spins == spins_out && ctx->g_eloc == eloc_out && ctx->g_sweep.size() == ctx->lats.size();
+  for (size_t l = 0; same && l < ctx->lats.size(); ++l) same = ctx->g_sweep[l] == ctx->lats[l].sweep;
+  CK(cudaEventRecord(ctx->ev[0], ctx->st), "sample_all");
+  if (use_graph && same) {
+    CK(cudaGraphLaunch(ctx->graph_exec, ctx->st), "sample_all");
+    ctx->launches += 2;
+  } else {
+    if ((s = batched_upload(ctx, n_therm, n_samples, spins_out, eloc_out))) return s;
+    if (use_graph) {
+      if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+      if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+      if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking), "capture");
+      CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal), "capture");
+      cudaError_t e = launch_sample_batched(ctx->d_bargs, ctx->d_order, nl, C, ctx->Nmax, ctx->Mmax,
+                                            ctx->d_counter, ctx->tuned_wpb, ctx->tuned_grid, adv,
+                                            ctx->d_bargs, ctx->cap_st);
+      cudaGraph_t g = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(ctx->cap_st, &g);
+      if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(ctx, e, "capture"); }
+      CK(e2, "capture");
+      ctx->graph = g;
+      CK(cudaGraphInstantiate(&ctx->graph_exec, g, 0), "instantiate");
+      ctx->g_therm = n_therm;
+      ctx->g_samples = n_samples;
+      ctx->g_spins = spins_out;
+      ctx->g_eloc = eloc_out;
+      CK(cudaGraphLaunch(ctx->graph_exec, ctx->st), "sample_all");
+    } else {
+      ctx->g_therm = -1;  // the descriptors no longer match the captured graph
+      CK(launch_sample_batched(ctx->d_bargs, ctx->d_order, nl, C, ctx->Nmax, ctx->Mmax, ctx->d_counter,
+                               ctx->tuned_wpb, ctx->tuned_grid, adv, ctx->d_bargs, ctx->st), "sample_all");
+    }
+    ctx->launches += 2;
+  }
+  CK(cudaEventRecord(ctx->ev[1], ctx->st), "sample_all");
+  ctx->g_sweep.resize(ctx->lats.size());
+  for (size_t l = 0; l < ctx->lats.size(); ++l) {
+    LatticeState& L = ctx->lats[l];
+    L.sweep += adv;
+    ctx->g_sweep[l] = L.sweep;
+    if (n_therm > 0) L.thermalized = true;
+    L.chain_cache = false;
+  }
+  if ((s = check_status(ctx, "sample_all"))) return s;
+  if (ms) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, ctx->ev[0], ctx->ev[1]);
+    *ms = t;
+  }
+  return VMC_OK;
+}
+
+int vmc_autotuned_warps_per_block(const vmc_ctx* ctx) { return ctx ? ctx->tuned_wpb : 0; }
 
 }  // extern "C"

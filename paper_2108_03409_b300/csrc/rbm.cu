@@ -293,17 +293,12 @@ __device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, 
   return make_float2(warp_sum(lr), warp_sum(li));
 }
 
+// All sweeps of one chain (the whole warp); s is the warp's shared-memory spin buffer.
 template <int MPL, bool HEIS>
-__global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
-  extern __shared__ int8_t sm[];
+__device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
   const RbmDev& R = A.rbm;
   const LatDev& L = A.lat;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int chain = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (chain >= A.C) return;
   const int N = R.N, M = R.M;
-  const int Npad = (N + 15) & ~15;
-  int8_t* s = sm + wib * Npad;
   for (int i = lane; i < N; i += 32) s[i] = A.chains[(int64_t)chain * N + i];
   __syncwarp();
 
@@ -420,6 +415,49 @@ __global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
   }
 }
 
+template <int MPL, bool HEIS>
+__global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
+  extern __shared__ int8_t sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int chain = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (chain >= A.C) return;
+  const int Npad = (A.rbm.N + 15) & ~15;
+  run_chain<MPL, HEIS>(A, chain, sm + wib * Npad, lane);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched persistent sampler: many lattices (uneven N, M) in one launch.  Work items are
+// (lattice, chain) pairs, ordered by the host so that the most expensive lattices come
+// first; every warp takes the next item from an atomic counter until the list is done.
+// The per-lattice arguments live in device memory (their sweep counters are advanced on
+// the device after each call, so a captured graph can be replayed as is).
+// ---------------------------------------------------------------------------------------
+template <int MPL>
+__global__ void k_sample_batched(const SampleArgs* __restrict__ args, const int* __restrict__ order,
+                                 int n_lat, int C, int npad_max, unsigned* counter) {
+  extern __shared__ int8_t sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int8_t* s = sm + wib * npad_max;
+  const unsigned total = (unsigned)n_lat * (unsigned)C;
+  while (true) {
+    unsigned item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1u);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    const int l = order[item / (unsigned)C];
+    const int chain = (int)(item % (unsigned)C);
+    const SampleArgs& A = args[l];
+    if (A.lat.model == 1) run_chain<MPL, true>(A, chain, s, lane);
+    else run_chain<MPL, false>(A, chain, s, lane);
+    __syncwarp();
+  }
+}
+
+__global__ void k_advance_sweeps(SampleArgs* args, int n_lat, uint64_t by) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < n_lat) args[l].sweep0 += by;
+}
+
 // ---------------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------------
@@ -484,6 +522,38 @@ cudaError_t launch_ok_dense(const int8_t* spins, const float2* T, int64_t n, int
   int blocks = (int)std::min<int64_t>((total + 255) / 256, 65536);
   k_ok_dense<<<blocks, 256, 0, st>>>(spins, T, n, N, M, O);
   return cudaGetLastError();
+}
+
+cudaError_t launch_sample_batched(const SampleArgs* d_args, const int* d_order, int n_lat, int C,
+                                  int Nmax, int Mmax, unsigned* counter, int warps_per_block,
+                                  int grid, uint64_t advance, SampleArgs* d_args_mut,
+                                  cudaStream_t st) {
+  const int npad = (Nmax + 15) & ~15;
+  const size_t smem = (size_t)warps_per_block * npad;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  VMC_DISPATCH_MPL(Mmax, k_sample_batched<MPL><<<grid, 32 * warps_per_block, smem, st>>>(
+                             d_args, d_order, n_lat, C, npad, counter));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (advance) {
+    k_advance_sweeps<<<(n_lat + 127) / 128, 128, 0, st>>>(d_args_mut, n_lat, advance);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+int batched_blocks_per_sm(int Mmax, int warps_per_block, int Nmax) {
+  int n = 0;
+  const size_t smem = (size_t)warps_per_block * ((Nmax + 15) & ~15);
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (pick_mpl(Mmax)) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sample_batched<1>, 32 * warps_per_block, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sample_batched<2>, 32 * warps_per_block, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sample_batched<4>, 32 * warps_per_block, smem); break;
+    case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sample_batched<8>, 32 * warps_per_block, smem); break;
+    case 16: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sample_batched<16>, 32 * warps_per_block, smem); break;
+  }
+  return (e == cudaSuccess) ? n : 0;
 }
 
 cudaError_t launch_sample(const SampleArgs& A, cudaStream_t st) {

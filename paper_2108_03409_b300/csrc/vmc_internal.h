@@ -50,6 +50,13 @@ cudaError_t launch_theta_tanh(const RbmDev& R, const int8_t* spins, int64_t n, f
 cudaError_t launch_ok_dense(const int8_t* spins, const float2* T, int64_t n, int N, int M,
                             float2* O, cudaStream_t st);
 cudaError_t launch_sample(const SampleArgs& A, cudaStream_t st);
+// every chain of n_lat lattices in one persistent launch (work list `order`, heavy first);
+// the sweep counters in d_args_mut advance by `advance` afterwards (on the device)
+cudaError_t launch_sample_batched(const SampleArgs* d_args, const int* d_order, int n_lat, int C,
+                                  int Nmax, int Mmax, unsigned* counter, int warps_per_block,
+                                  int grid, uint64_t advance, SampleArgs* d_args_mut,
+                                  cudaStream_t st);
+int batched_blocks_per_sm(int Mmax, int warps_per_block, int Nmax);
 
 // ---- sr.cu ----------------------------------------------------------------------------
 // Energy statistics in FP64: out[0..3] = <E>.re, <E>.im, <|E-<E>|^2>, sqrt(var/n).

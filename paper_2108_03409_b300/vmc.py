@@ -63,7 +63,8 @@ EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_
             "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
             "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve",
             "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
-            "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned"]
+            "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned", "vmc_sample_all",
+            "vmc_autotuned_warps_per_block"]
 
 _lib = None
 
@@ -106,6 +107,8 @@ def load(path: str = LIB_PATH):
         "vmc_proposal_train": (i32, [P, i32, P, i64, i32, f64, ctypes.POINTER(f64)]),
         "vmc_made_sample": (i32, [P, i32, i64, ctypes.c_uint64, P, P]),
         "vmc_sample_learned": (i32, [P, i32, i32, P, P, ctypes.POINTER(f64)]),
+        "vmc_sample_all": (i32, [P, i32, i32, P, P, i32, ctypes.POINTER(f64)]),
+        "vmc_autotuned_warps_per_block": (i32, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -302,3 +305,14 @@ def vmc_sample_learned(ctx, lattice, n_rounds, spins_out=None, eloc_out=None):
     _check(ctx, load().vmc_sample_learned(ctx, lattice, int(n_rounds), _ptr(spins_out),
                                           _ptr(eloc_out), ctypes.byref(acc)))
     return acc.value
+
+
+def vmc_sample_all(ctx, n_therm, n_samples, spins_out=None, eloc_out=None, use_graph=True):
+    ms = ctypes.c_double(0.0)
+    _check(ctx, load().vmc_sample_all(ctx, int(n_therm), int(n_samples), _ptr(spins_out),
+                                      _ptr(eloc_out), 1 if use_graph else 0, ctypes.byref(ms)))
+    return ms.value
+
+
+def vmc_autotuned_warps_per_block(ctx) -> int:
+    return int(load().vmc_autotuned_warps_per_block(ctx))

@@ -1,0 +1,163 @@
+"""Batched sampling of many independent lattices of uneven size in one persistent launch
+(vmc_sample_all): same Philox streams and sweeps as per-lattice vmc_sample, so the records
+must agree with it and with the oracle's Metropolis trajectories."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_03409_b300 import inputs, vmc
+
+from gpu_helpers import cplx, eloc_tolerance
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+T, H = inputs.MODEL_TFIM, inputs.MODEL_HEIS
+
+# (model, Lx, Ly, J, h, alpha): uneven sizes, both models, Lx != Ly, M from 10 to 72
+LATS = [
+    (T, 10, 1, 1.0, 1.0, 1),
+    (T, 4, 4, 1.0, 3.0, 2),
+    (T, 3, 5, 1.0, 2.5, 1),
+    (H, 4, 4, 1.0, 0.0, 1),
+    (T, 6, 6, 1.0, 3.0, 2),
+    (T, 2, 2, 1.0, 2.0, 3),
+]
+C = 96
+SEED = 2024
+
+
+def _setup(ctx):
+    ps, ss = [], []
+    for l, (model, Lx, Ly, J, h, alpha) in enumerate(LATS):
+        N, M = Lx * Ly, alpha * Lx * Ly
+        p = inputs.rbm_params(N, M, 0.1, seed=100 + l,
+                              marshall=(Lx, Ly) if model == H else None)
+        s0 = inputs.initial_spins(model, C, N, seed=200 + l)
+        vmc.vmc_set_params(ctx, l, p)
+        vmc.vmc_set_chains(ctx, l, s0)
+        ps.append(p)
+        ss.append(s0)
+    return ps, ss
+
+
+def _ctx():
+    lats = [vmc.make_lattice(*L) for L in LATS]
+    return vmc.vmc_init(vmc.make_config(seed=SEED, n_chains=C, solver=vmc.SOLVER_CG), lats)
+
+
+def _sizes():
+    return [Lx * Ly for (_, Lx, Ly, _, _, _) in LATS]
+
+
+def _split(flat, n_samples):
+    out, off = [], 0
+    for N in _sizes():
+        k = n_samples * C * N
+        out.append(flat[off:off + k].reshape(n_samples, C, N))
+        off += k
+    return out
+
+
+def _per_lattice(ctx, n_therm, n_samples):
+    sp, el = [], []
+    for l, N in enumerate(_sizes()):
+        o = torch.zeros((n_samples * C, N), dtype=torch.int8, device="cuda")
+        e = torch.zeros((n_samples * C, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_sample(ctx, l, n_therm, n_samples, o, None, e)
+        sp.append(o.cpu().numpy().reshape(n_samples, C, N))
+        el.append(cplx(e).reshape(n_samples, C))
+    return sp, el
+
+
+def _batched(ctx, n_therm, n_samples, spins, eloc, use_graph):
+    vmc.vmc_sample_all(ctx, n_therm, n_samples, spins, eloc, use_graph)
+    sp = _split(spins.cpu().numpy(), n_samples)
+    el = cplx(eloc).reshape(len(LATS), n_samples, C)
+    return sp, el
+
+
+def test_batched_equals_per_lattice_and_graph_replay():
+    """Three batched calls (plain launch, graph capture, graph replay) against the same
+    sequence of per-lattice calls: identical spins and E_loc, identical final chains."""
+    a, b = _ctx(), _ctx()
+    try:
+        _setup(a)
+        _setup(b)
+        tot = sum(_sizes())
+        calls = [(3, 2, False), (0, 2, True), (0, 2, True)]
+        bufs = {}
+        for k, (nt, ns, g) in enumerate(calls):
+            ref_s, ref_e = _per_lattice(a, nt, ns)
+            key = (nt, ns)
+            if key not in bufs:   # the replay needs the same output buffers
+                bufs[key] = (torch.zeros(ns * C * tot, dtype=torch.int8, device="cuda"),
+                             torch.zeros((len(LATS) * ns * C, 2), dtype=torch.float32, device="cuda"))
+            got_s, got_e = _batched(b, nt, ns, *bufs[key], g)
+            for l in range(len(LATS)):
+                assert np.array_equal(got_s[l], ref_s[l]), (k, l)
+                np.testing.assert_allclose(got_e[l], ref_e[l], rtol=1e-6, atol=1e-5)
+        for l, N in enumerate(_sizes()):
+            assert np.array_equal(vmc.vmc_get_chains(a, l, C, N), vmc.vmc_get_chains(b, l, C, N))
+        assert vmc.vmc_autotuned_warps_per_block(b) in (2, 4, 8)
+    finally:
+        vmc.vmc_destroy(a)
+        vmc.vmc_destroy(b)
+
+
+def test_batched_matches_oracle_trajectories():
+    """Each lattice's records follow the oracle's Metropolis chain on Philox stream = lattice
+    index (chains that met a decision within 1e-4 of the threshold may part), and the fused
+    E_loc matches the oracle's."""
+    ctx = _ctx()
+    try:
+        ps, ss = _setup(ctx)
+        n_therm, n_samples = 2, 3
+        tot = sum(_sizes())
+        spins = torch.zeros(n_samples * C * tot, dtype=torch.int8, device="cuda")
+        eloc = torch.zeros((len(LATS) * n_samples * C, 2), dtype=torch.float32, device="cuda")
+        got_s, got_e = _batched(ctx, n_therm, n_samples, spins, eloc, True)
+    finally:
+        vmc.vmc_destroy(ctx)
+    for l, (model, Lx, Ly, J, h, alpha) in enumerate(LATS):
+        N, M = Lx * Ly, alpha * Lx * Ly
+        _, rec, margin, _ = oracle.metropolis(model, Lx, Ly, M, ps[l], ss[l], seed=SEED,
+                                              stream=l, n_sweeps=n_therm + n_samples,
+                                              record=True)
+        same = np.all(got_s[l] == rec[n_therm:], axis=(0, 2))
+        assert np.all(margin[~same] < 1e-4) and same.mean() >= 0.97, (l, np.sum(~same))
+        flat = got_s[l].reshape(-1, N)
+        ref = oracle.eloc(model, Lx, Ly, J, h, M, ps[l], flat)
+        tol = eloc_tolerance(model, Lx, Ly, J, h, M, ps[l], flat)
+        assert np.all(np.abs(got_e[l].reshape(-1) - ref) <= tol), l
+        if model == H:
+            assert np.all(got_s[l].sum(axis=2) == 0)
+
+
+def test_graph_not_replayed_after_per_lattice_sampling():
+    """A per-lattice call between two batched calls moves that lattice's sweep counter: the
+    second batched call must re-upload (not replay stale descriptors), so it still agrees
+    with per-lattice sampling."""
+    a, b = _ctx(), _ctx()
+    try:
+        _setup(a)
+        _setup(b)
+        tot = sum(_sizes())
+        spins = torch.zeros(C * tot, dtype=torch.int8, device="cuda")
+        eloc = torch.zeros((len(LATS) * C, 2), dtype=torch.float32, device="cuda")
+        for ctx in (a, b):
+            o = torch.zeros((C, _sizes()[2]), dtype=torch.int8, device="cuda")
+            vmc.vmc_sample(ctx, 2, 0, 1, o)
+        _per_lattice(a, 0, 1)
+        _batched(b, 0, 1, spins, eloc, True)
+        o = torch.zeros((C, _sizes()[2]), dtype=torch.int8, device="cuda")
+        vmc.vmc_sample(a, 2, 0, 1, o)
+        vmc.vmc_sample(b, 2, 0, 1, o)
+        ref_s, _ = _per_lattice(a, 0, 1)
+        got_s, _ = _batched(b, 0, 1, spins, eloc, True)
+        for l in range(len(LATS)):
+            assert np.array_equal(got_s[l], ref_s[l]), l
+    finally:
+        vmc.vmc_destroy(a)
+        vmc.vmc_destroy(b)
