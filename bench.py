@@ -21,6 +21,7 @@ import argparse
 import json
 import os
 import statistics
+import subprocess
 import sys
 import threading
 import time
@@ -48,6 +49,11 @@ WORKLOADS = {
 # batched sampling of many independent lattices (one sweep + a record per chain per step)
 BATCHED = {"tfim2d_batched48_alpha2_c1024": dict(sizes=[4] * 16 + [6] * 16 + [8] * 16, alpha=2,
                                                  chains=1024, h_lo=2.0, h_hi=4.0, h_seed=7)}
+# learned independent proposal against single-flip moves on a near-critical TFIM
+LEARNED = {"tfim2d_12x12_h3.04_alpha2_c16384_made256": dict(L=12, h=3.04, alpha=2, chains=16384,
+                                                            hidden=256, sr_steps=200,
+                                                            train_records=16, epochs=10,
+                                                            lr=1e-3, tau_rounds=200)}
 DEFAULT_WORKLOAD = "heis2d_8x8_alpha2_c8192"
 W = WORKLOADS[DEFAULT_WORKLOAD]
 LX, LY, ALPHA, CHAINS, SHIFT = W["Lx"], W["Ly"], W["alpha"], W["chains"], W["shift"]
@@ -64,71 +70,131 @@ def peaks():
 
 
 class ClockSampler:
-    """SM clocks, power and clock-event (throttle) reasons, read through NVML every 20 ms
-    during the timed region (one reading on entry and one on exit, so that even a short
-    region has samples).  Reads only; changes no setting."""
+    """SM clocks and clock-event (throttle) reasons during the timed region: NVML polled
+    every 20 ms when the Python binding is importable, else nvidia-smi every 100 ms.  One
+    reading is taken on entry and one on exit, so that even a short region has samples.
+    Reads only; changes no setting."""
     BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
             "sw_power_cap": 0x4}
+    SMI_Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
-        self.rows = []
-        self.h = None
+        self.rows = []          # (sm MHz, max sm MHz, set of active reasons)
         self.stop = threading.Event()
+        self.err = None
+        self.mode = None
 
-    def _handle(self):
+    # ---- NVML ----
+    def _nvml_handle(self):
         import pynvml
         pynvml.nvmlInit()
+        import torch
+        pr = torch.cuda.get_device_properties(self.index)
         try:
-            import torch
-            uuid = str(torch.cuda.get_device_properties(self.index).uuid)
-            return pynvml.nvmlDeviceGetHandleByUUID(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+            bus = f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+            return pynvml.nvmlDeviceGetHandleByPciBusId(bus)
         except Exception:
-            return pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            if pynvml.nvmlDeviceGetCount() == 1:
+                return pynvml.nvmlDeviceGetHandleByIndex(0)
+            raise
 
-    def _sample(self):
+    def _nvml_sample(self):
         import pynvml
         sm = pynvml.nvmlDeviceGetClockInfo(self.h, pynvml.NVML_CLOCK_SM)
         mx = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+        r = int(pynvml.nvmlDeviceGetCurrentClocksEventReasons(self.h))
+        self.rows.append((float(sm), float(mx), {k for k, bit in self.BITS.items() if r & bit}))
+
+    # ---- nvidia-smi ----
+    def _smi_target(self):
+        import torch
+        pr = torch.cuda.get_device_properties(self.index)
+        return f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+
+    def _smi_parse(self, line):
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 6:
+            return
         try:
-            r = pynvml.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-        except Exception:
-            r = pynvml.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
-        self.rows.append((float(sm), float(mx), int(r)))
+            sm, mx = float(parts[0]), float(parts[1])
+        except ValueError:
+            return
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        act = {names[k] for k in range(4) if parts[2 + k].lower().startswith("active")}
+        self.rows.append((sm, mx, act))
+
+    def _smi_once(self):
+        out = subprocess.run(["nvidia-smi", "-i", self.target, f"--query-gpu={self.SMI_Q}",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=10)
+        for line in out.stdout.splitlines():
+            self._smi_parse(line)
+
+    def _smi_read(self):
+        for line in self.proc.stdout:
+            self._smi_parse(line)
+
+    def __enter__(self):
+        try:
+            self.h = self._nvml_handle()
+            self._nvml_sample()
+            self.mode = "NVML, 20 ms"
+            self.t = threading.Thread(target=self._loop, daemon=True)
+            self.t.start()
+            return self
+        except Exception as e:
+            self.err = f"NVML: {type(e).__name__}: {e}"
+        try:
+            self.target = self._smi_target()
+            self._smi_once()
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.target, f"--query-gpu={self.SMI_Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._smi_read, daemon=True)
+            self.t.start()
+            self.mode = "nvidia-smi, 100 ms"
+        except Exception as e:
+            self.err = (self.err or "") + f"; nvidia-smi: {type(e).__name__}: {e}"
+        return self
 
     def _loop(self):
         while not self.stop.wait(0.02):
             try:
-                self._sample()
+                self._nvml_sample()
             except Exception:
                 return
 
-    def __enter__(self):
-        try:
-            self.h = self._handle()
-            self._sample()
-            self.t = threading.Thread(target=self._loop, daemon=True)
-            self.t.start()
-        except Exception:
-            self.h = None
-        return self
-
     def __exit__(self, *a):
-        if self.h is not None:
+        if self.mode and self.mode.startswith("NVML"):
             self.stop.set()
             self.t.join(timeout=1)
             try:
-                self._sample()
+                self._nvml_sample()
             except Exception:
                 pass
+        elif self.mode:
+            try:
+                self._smi_once()
+            except Exception:
+                pass
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
 
     def summary(self):
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
-        reasons = sorted({k for (_, _, r) in self.rows for k, bit in self.BITS.items() if r & bit})
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"],
+                    "error": self.err}
+        reasons = sorted(set().union(*(r[2] for r in self.rows)))
         return {"sm_mhz": statistics.median(r[0] for r in self.rows),
                 "sm_max_mhz": max(r[1] for r in self.rows), "reasons": reasons,
-                "samples": len(self.rows), "source": "NVML, 20 ms"}
+                "samples": len(self.rows), "source": self.mode}
 
 
 def dist_env():
@@ -466,6 +532,126 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+def run_learned(args):
+    """Learned proposal: the RBM is first optimised by plain SR steps (matrix-free CG), the
+    MADE proposal is trained on 2^18 samples of the local chains, then both samplers run from
+    the same state.  A step is one round on every chain (a learned proposal + accept, or one
+    single-flip sweep) with the E_loc record; tau_int(E) comes from a longer run of each."""
+    import torch
+    from paper_2108_03409_b300 import build as vbuild
+    from paper_2108_03409_b300 import inputs, stats as vstats, vmc
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    vbuild.build()
+    wl = LEARNED[args.workload]
+    L, C, H = wl["L"], wl["chains"], wl["hidden"]
+    N, M = L * L, wl["alpha"] * L * L
+    stream = torch.cuda.current_stream()
+    cfg = vmc.make_config(seed=1 + rank, n_chains=C, therm_sweeps=20, solver=vmc.SOLVER_CG,
+                          shift=1e-3, cg_maxit=100, cg_tol=1e-6, made_hidden=H, made_batch=4096)
+    ctx = vmc.vmc_init(cfg, [vmc.make_lattice(vmc.MODEL_TFIM, L, L, 1.0, wl["h"], wl["alpha"])],
+                       stream.cuda_stream)
+    vmc.vmc_set_params(ctx, 0, inputs.rbm_params(N, M, 0.01, seed=1234))
+    vmc.vmc_set_chains(ctx, 0, inputs.random_spins(C, N, seed=99 + rank))
+    t0 = time.perf_counter()
+    for _ in range(wl["sr_steps"]):
+        st = vmc.vmc_sr_step(ctx, 0, DT)
+    t_sr = time.perf_counter() - t0
+    e_sr = st.e_mean_re / N
+    # training set: 2^18 samples of the local chains (one sweep apart)
+    R = wl["train_records"]
+    train = torch.zeros((R * C, N), dtype=torch.int8, device="cuda")
+    vmc.vmc_sample(ctx, 0, 0, R, train)
+    vmc.vmc_made_set_params(ctx, 0, inputs.made_params(N, H, seed=5))
+    t0 = time.perf_counter()
+    loss = vmc.vmc_proposal_train(ctx, 0, train, epochs=wl["epochs"], lr=wl["lr"])
+    t_train = time.perf_counter() - t0
+    del train
+    chains0 = vmc.vmc_get_chains(ctx, 0, C, N)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    el1 = torch.zeros((C, 2), dtype=torch.float32, device="cuda")
+
+    def timed(fn, steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        barrier()
+        return a.elapsed_time(b)
+
+    local_round = lambda: vmc.vmc_sample(ctx, 0, 0, 1, None, None, el1)
+    learned_round = lambda: vmc.vmc_sample_learned(ctx, 0, 1, None, el1)
+    for _ in range(args.warmup):
+        local_round()
+        learned_round()
+    barrier()
+    launches0 = vmc.vmc_kernel_launches(ctx)
+    with ClockSampler(local) as clk:
+        ms_lrn = timed(learned_round, args.steps)
+    launches = vmc.vmc_kernel_launches(ctx) - launches0
+    ms_loc = timed(local_round, args.steps)
+
+    # tau_int(E), <E> +- err and acceptance of both samplers from the same start
+    T = wl["tau_rounds"]
+    res = {}
+    for name in ("local", "learned"):
+        vmc.vmc_set_chains(ctx, 0, chains0)
+        el = torch.zeros((T * C, 2), dtype=torch.float32, device="cuda")
+        if name == "local":
+            vmc.vmc_sample(ctx, 0, 0, T, None, None, el)
+            acc = None
+        else:
+            acc = vmc.vmc_sample_learned(ctx, 0, T, None, el)
+        e = el[:, 0].double().reshape(T, C).cpu().numpy()
+        del el
+        tau = vstats.integrated_autocorr_time(e[:, :4096])
+        err = float(np.sqrt(e.var() / e.size * 2 * tau))
+        res[name] = {"tau_int_E": tau, "e_per_site": float(e.mean()) / N, "err_per_site": err / N,
+                     "acceptance": acc}
+    t_loc = ms_loc / args.steps / 1e3
+    t_lrn = ms_lrn / args.steps / 1e3
+    eff_loc = ws * C / t_loc / (2 * res["local"]["tau_int_E"])
+    eff_lrn = ws * C / t_lrn / (2 * res["learned"]["tau_int_E"])
+    res["local"].update({"samples_per_s": ws * C / t_loc, "eff_samples_per_s": eff_loc,
+                         "ms_per_round": t_loc * 1e3})
+    res["learned"].update({"samples_per_s": ws * C / t_lrn, "eff_samples_per_s": eff_lrn,
+                           "ms_per_round": t_lrn * 1e3})
+    dE = abs(res["learned"]["e_per_site"] - res["local"]["e_per_site"])
+    comb = float(np.hypot(res["learned"]["err_per_site"], res["local"]["err_per_site"]))
+    out = {"metric": METRIC, "value": eff_lrn, "unit": "effective samples/s (incl. E_loc)",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_lrn * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32 (MADE f32 weights)", "data": "synthetic",
+           "config": {"workload": args.workload, "N": N, "M": M, "h": wl["h"], "chains": C,
+                      "made_hidden": H, "sr_steps_checkpoint": wl["sr_steps"],
+                      "train_samples": R * C, "epochs": wl["epochs"],
+                      "l2": "chains + weights fit L2; no flush (sampler rounds)",
+                      "parallelism": f"replicas x{ws}"},
+           "samplers": res, "speedup_eff_vs_local": eff_lrn / eff_loc,
+           "equal_accuracy": {"dE_per_site": dE, "combined_err_per_site": comb,
+                              "ok": bool(dE <= 1e-4 and dE <= 3 * comb)},
+           "checkpoint": {"e_per_site": e_sr, "s": t_sr}, "train": {"loss": loss, "s": t_train},
+           "roofline": None,
+           "note": "sampler comparison; rooflines of the sweep and Gram kernels are in the "
+                   "default workload's line",
+           "gpu_launches": launches, "clocks": clk.summary()}
+    vmc.vmc_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -475,13 +661,15 @@ def main():
     ap.add_argument("--precision", default="bf16split", choices=["fp32", "bf16split"])
     ap.add_argument("--solver", default=None, choices=["mixed", "tc", "fp64", "cg"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=sorted(WORKLOADS) + sorted(BATCHED))
+                    choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(LEARNED))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload in BATCHED:
         run_batched(args)
+    elif args.workload in LEARNED:
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -505,6 +505,7 @@ vmc_status vmc_sample(vmc_ctx* ctx, int lattice, int n_therm, int n_samples, int
   ++ctx->launches;
   L.sweep += (uint64_t)n_therm + (uint64_t)n_samples * ctx->cfg.sweeps_per_sample;
   if (n_therm > 0) L.thermalized = true;
+  L.chain_cache = false;          // the chains moved: cached log psi / log q are stale
   return VMC_OK;
 }
 

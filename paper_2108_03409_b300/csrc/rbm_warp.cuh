@@ -1,0 +1,333 @@
+// rbm_warp.cuh -- warp-level building blocks of the complex-RBM kernels (shared by the
+// evaluation, sampling and batched-sampling translation units).  One warp owns one
+// configuration (or one chain); hidden unit j = lane + 32*k lives in register slot k of
+// that lane.
+#pragma once
+
+#include "vmc_device.cuh"
+#include "vmc_internal.h"
+
+namespace vmc {
+
+static constexpr unsigned FULL = 0xffffffffu;
+
+// theta_j = b_j + sum_i W_ji s_i for the warp's hidden slots, from spins in shared memory.
+template <int MPL>
+__device__ __forceinline__ void warp_theta(const RbmDev& R, const int8_t* s, int lane,
+                                           float2 (&th)[MPL]) {
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    int hj = lane + 32 * k;
+    th[k] = (hj < R.M) ? R.b[hj] : make_float2(0.f, 0.f);
+  }
+  for (int i = 0; i < R.N; ++i) {
+    const float si = (float)s[i];
+    const float2* w = R.Wt + (int64_t)i * R.M;
+#pragma unroll
+    for (int k = 0; k < MPL; ++k) {
+      int hj = lane + 32 * k;
+      if (hj < R.M) {
+        float2 v = w[hj];
+        th[k].x = fmaf(si, v.x, th[k].x);
+        th[k].y = fmaf(si, v.y, th[k].y);
+      }
+    }
+  }
+}
+
+// log psi = sum_i a_i s_i + sum_j log cosh theta_j (all lanes return the same value).
+template <int MPL>
+__device__ __forceinline__ float2 warp_logpsi(const RbmDev& R, const int8_t* s, int lane,
+                                              const float2 (&th)[MPL]) {
+  float re = 0.f, im = 0.f;
+  for (int i = lane; i < R.N; i += 32) {
+    float si = (float)s[i];
+    re = fmaf(si, R.a[i].x, re);
+    im = fmaf(si, R.a[i].y, im);
+  }
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    if (lane + 32 * k < R.M) {
+      float2 lc = logcosh_c(th[k].x, th[k].y);
+      re += lc.x;
+      im += lc.y;
+    }
+  }
+  return make_float2(warp_sum(re), warp_sum(im));
+}
+
+// sum over the warp's hidden slots of log[cosh(theta_k - d_k) / cosh(theta_k)], with
+// d_k = 2 s_i W_ki (+ 2 s_j W_kj for an exchange), as (log modulus, phase).  Each lane
+// multiplies its factors and takes one log at the end; the running product is folded into
+// the logs early only if it leaves [1e-15, 1e15] (checked every four factors).
+template <int MPL, bool PAIR>
+__device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
+                                                 const float2 (&t)[MPL], int i, float si,
+                                                 int j) {
+  float lr = 0.f, li = 0.f;
+  float2 prod = make_float2(1.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    int hj = lane + 32 * k;
+    if (hj < R.M) {
+      float2 wi = R.Wt[(int64_t)i * R.M + hj];
+      float dr, di;
+      if (PAIR) {
+        float2 wj = R.Wt[(int64_t)j * R.M + hj];
+        dr = 2.f * si * (wi.x - wj.x);
+        di = 2.f * si * (wi.y - wj.y);
+      } else {
+        dr = 2.f * si * wi.x;
+        di = 2.f * si * wi.y;
+      }
+      prod = cmul(prod, cosh_ratio(t[k], dr, di));
+    }
+    if ((k & 3) == 3 && k != MPL - 1) {
+      const float m2 = fmaf(prod.x, prod.x, prod.y * prod.y);
+      if (m2 > 1e30f || m2 < 1e-30f) {
+        lr += 0.5f * logf(m2);
+        li += atan2f(prod.y, prod.x);
+        prod = make_float2(1.f, 0.f);
+      }
+    }
+  }
+  lr += 0.5f * logf(fmaf(prod.x, prod.x, prod.y * prod.y));
+  li += atan2f(prod.y, prod.x);
+  return make_float2(warp_sum(lr), warp_sum(li));
+}
+
+// E_loc(s) = sum_s' H_ss' psi(s')/psi(s) from the cached t = tanh theta(s) (Eq. Oloc).
+template <int MPL>
+__device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, int lane,
+                            const float2 (&t)[MPL]) {
+  // diagonal: sum over bonds of s_i s_j (exact small integers)
+  float zz = 0.f;
+  for (int b = lane; b < L.nb; b += 32) {
+    int i, j;
+    bond_ends(L.Lx, L.Ly, b, &i, &j);
+    zz += (float)(s[i] * s[j]);
+  }
+  zz = warp_sum(zz);
+  float2 e;
+  if (L.model == 0) {
+    e = make_float2(-L.J * zz, 0.f);
+    for (int i = 0; i < R.N; ++i) {           // -h X_i: flip site i
+      float si = (float)s[i];
+      float2 lg = warp_log_ratio<MPL, false>(R, lane, t, i, si, 0);
+      float2 ai = R.a[i];
+      float lx = lg.x - 2.f * si * ai.x, ly = lg.y - 2.f * si * ai.y;
+      float mag = expf(lx), sn, cs;
+      sincosf(ly, &sn, &cs);
+      e.x = fmaf(-L.h, mag * cs, e.x);
+      e.y = fmaf(-L.h, mag * sn, e.y);
+    }
+  } else {
+    e = make_float2(L.J * zz, 0.f);
+    for (int b = 0; b < L.nb; ++b) {          // J(XX+YY): swap an anti-parallel pair, 2J
+      int i, j;
+      bond_ends(L.Lx, L.Ly, b, &i, &j);
+      if (s[i] == s[j]) continue;
+      float si = (float)s[i];
+      float2 lg = warp_log_ratio<MPL, true>(R, lane, t, i, si, j);
+      float2 ai = R.a[i], aj = R.a[j];
+      float lx = lg.x - 2.f * si * (ai.x - aj.x), ly = lg.y - 2.f * si * (ai.y - aj.y);
+      float mag = expf(lx), sn, cs;
+      sincosf(ly, &sn, &cs);
+      e.x = fmaf(2.f * L.J, mag * cs, e.x);
+      e.y = fmaf(2.f * L.J, mag * sn, e.y);
+    }
+  }
+  return e;
+}
+
+// ---------------------------------------------------------------------------------------
+// a3/a4 + a6 (+ the t factors of a7): Metropolis sweeps with t = tanh theta cached in
+// registers.  One warp per chain.  For a proposal s -> s' that changes theta by -d_k
+// (d_k = 2 s_i W_ki, plus 2 s_j W_kj for an exchange),
+//   psi(s')/psi(s) = exp(a-term) * prod_k [cosh d_k - t_k sinh d_k],
+// and the acceptance needs only its modulus squared.  On acceptance
+// t_k <- tanh(theta_k - d_k) = (t_k - tanh d_k) / (1 - t_k tanh d_k).  Random numbers for
+// 32 consecutive steps are drawn in parallel (lane q draws step t0+q) and broadcast.  At
+// every record point theta is recomputed from the spins (no drift), and the sample's
+// spins, log psi, E_loc (fused, from the cached t) and t are written.
+// ---------------------------------------------------------------------------------------
+template <int MPL>
+__device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, int lane,
+                                              float2 (&t)[MPL], bool want_logpsi) {
+  float lr = 0.f, li = 0.f;
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    const int hj = lane + 32 * k;
+    t[k] = make_float2(0.f, 0.f);
+    if (hj < R.M) {
+      float2 th = R.b[hj];
+      for (int i = 0; i < R.N; ++i) {
+        const float si = (float)s[i];
+        const float2 v = R.Wt[(int64_t)i * R.M + hj];
+        th.x = fmaf(si, v.x, th.x);
+        th.y = fmaf(si, v.y, th.y);
+      }
+      t[k] = tanh_c(th.x, th.y);
+      if (want_logpsi) {
+        const float2 lc = logcosh_c(th.x, th.y);
+        lr += lc.x;
+        li += lc.y;
+      }
+    }
+  }
+  if (!want_logpsi) return make_float2(0.f, 0.f);
+  for (int i = lane; i < R.N; i += 32) {
+    const float si = (float)s[i];
+    lr = fmaf(si, R.a[i].x, lr);
+    li = fmaf(si, R.a[i].y, li);
+  }
+  return make_float2(warp_sum(lr), warp_sum(li));
+}
+
+// All sweeps of one chain (the whole warp); s is the warp's shared-memory spin buffer.
+template <int MPL, bool HEIS>
+__device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
+  const RbmDev& R = A.rbm;
+  const LatDev& L = A.lat;
+  const int N = R.N, M = R.M;
+  for (int i = lane; i < N; i += 32) s[i] = A.chains[(int64_t)chain * N + i];
+  __syncwarp();
+
+  float2 t[MPL];
+  warp_resync<MPL>(R, s, lane, t, false);
+
+  const uint32_t K = HEIS ? (uint32_t)L.nb : (uint32_t)N;
+  const int total = A.n_therm + A.n_samples * A.sweeps_per_sample;
+  unsigned long long n_acc = 0;
+  bool bad = false;
+
+  for (int sw = 0; sw < total; ++sw) {
+    const uint64_t sweep_id = A.sweep0 + (uint64_t)sw;
+    for (int t0 = 0; t0 < A.L; t0 += 32) {
+      uint32_t my_idx = 0;
+      float my_logu = 0.f;
+      if (t0 + lane < A.L) {
+        u64x4 w = philox4x64_10((uint64_t)chain, sweep_id, (uint64_t)(t0 + lane), 0ull,
+                                A.seed, A.stream);
+        mh_draw(w, K, &my_idx, &my_logu);
+      }
+      const int nstep = min(32, A.L - t0);
+      for (int q = 0; q < nstep; ++q) {
+        const int idx = (int)__shfl_sync(FULL, my_idx, q);
+        const float logu = __shfl_sync(FULL, my_logu, q);
+        int i = idx, j = 0;
+        if (HEIS) {
+          bond_ends(L.Lx, L.Ly, idx, &i, &j);
+          if (s[i] == s[j]) continue;             // parallel pair: rejected no-op
+        }
+        const float si = (float)s[i];
+        const float two_re_da = HEIS ? -4.f * si * (R.a[i].x - R.a[j].x) : -4.f * si * R.a[i].x;
+        float lsum = 0.f, prod = 1.f;
+#pragma unroll
+        for (int k = 0; k < MPL; ++k) {
+          const int hj = lane + 32 * k;
+          if (hj < M) {
+            const float2 wi = R.Wt[(int64_t)i * M + hj];
+            float dr, di;
+            if (HEIS) {
+              const float2 wj = R.Wt[(int64_t)j * M + hj];
+              dr = 2.f * si * (wi.x - wj.x);
+              di = 2.f * si * (wi.y - wj.y);
+            } else {
+              dr = 2.f * si * wi.x;
+              di = 2.f * si * wi.y;
+            }
+            const float2 r = cosh_ratio(t[k], dr, di);
+            prod *= fmaf(r.x, r.x, r.y * r.y);
+          }
+          if ((k & 7) == 7 || k == MPL - 1) {
+            lsum += logf(prod);
+            prod = 1.f;
+          }
+        }
+        const float two_re_delta = warp_sum(lsum) + two_re_da;
+        if (logu < two_re_delta) {
+#pragma unroll
+          for (int k = 0; k < MPL; ++k) {
+            const int hj = lane + 32 * k;
+            if (hj < M) {
+              const float2 wi = R.Wt[(int64_t)i * M + hj];
+              float dr, di;
+              if (HEIS) {
+                const float2 wj = R.Wt[(int64_t)j * M + hj];
+                dr = 2.f * si * (wi.x - wj.x);
+                di = 2.f * si * (wi.y - wj.y);
+              } else {
+                dr = 2.f * si * wi.x;
+                di = 2.f * si * wi.y;
+              }
+              t[k] = tanh_shift(t[k], dr, di);
+            }
+          }
+          __syncwarp();
+          if (lane == 0) {
+            s[i] = (int8_t)(-s[i]);
+            if (HEIS) s[j] = (int8_t)(-s[j]);
+          }
+          __syncwarp();
+          ++n_acc;
+        }
+      }
+    }
+    const int after = sw + 1 - A.n_therm;
+    if (after > 0 && after % A.sweeps_per_sample == 0) {
+      const int64_t rec = after / A.sweeps_per_sample - 1;
+      const int64_t qs = rec * A.C + chain;
+      const float2 lp = warp_resync<MPL>(R, s, lane, t, A.logpsi_out != nullptr);
+      if (A.t_out)
+#pragma unroll
+        for (int k = 0; k < MPL; ++k) {
+          const int hj = lane + 32 * k;
+          if (hj < M) A.t_out[qs * M + hj] = t[k];
+        }
+      if (A.spins_out)
+        for (int i = lane; i < N; i += 32) A.spins_out[qs * N + i] = s[i];
+      if (A.logpsi_out) {
+        if (lane == 0) A.logpsi_out[qs] = lp;
+        bad |= !isfinite(lp.x) || !isfinite(lp.y);
+      }
+      if (A.eloc_out) {
+        const float2 e = warp_eloc<MPL>(R, L, s, lane, t);
+        if (lane == 0) A.eloc_out[qs] = e;
+        bad |= !isfinite(e.x) || !isfinite(e.y);
+      }
+    }
+  }
+  __syncwarp();
+  for (int i = lane; i < N; i += 32) A.chains[(int64_t)chain * N + i] = s[i];
+  if (lane == 0) {
+    if (A.n_accept) atomicAdd(A.n_accept, n_acc);
+    if (bad) flag_error(A.status, DEV_ERR_NUMERIC);
+  }
+}
+
+// hidden slots per lane: ceil(M / 32) rounded up to one of the instantiated widths
+// (at most a third of the lanes' slots idle, e.g. M = 288 -> 10 slots of 32)
+static inline int pick_mpl(int M) {
+  const int m = (M + 31) / 32;
+  static const int widths[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
+  for (int w : widths)
+    if (w >= m) return w;
+  return 0;
+}
+
+#define VMC_MPL_CASE(V, ...) case V: { constexpr int MPL = V; __VA_ARGS__; } break;
+#define VMC_DISPATCH_MPL(M, ...)                                                        \
+  switch (pick_mpl(M)) {                                                                \
+    VMC_MPL_CASE(1, __VA_ARGS__) VMC_MPL_CASE(2, __VA_ARGS__) VMC_MPL_CASE(3, __VA_ARGS__) \
+    VMC_MPL_CASE(4, __VA_ARGS__) VMC_MPL_CASE(5, __VA_ARGS__) VMC_MPL_CASE(6, __VA_ARGS__) \
+    VMC_MPL_CASE(8, __VA_ARGS__) VMC_MPL_CASE(10, __VA_ARGS__)                          \
+    VMC_MPL_CASE(12, __VA_ARGS__) VMC_MPL_CASE(16, __VA_ARGS__)                         \
+    default: return cudaErrorInvalidValue;                                              \
+  }
+
+static constexpr int kWarps = 4;
+
+static inline size_t spin_smem(int N) { return (size_t)kWarps * ((N + 15) & ~15); }
+
+}  // namespace vmc

@@ -1,0 +1,25 @@
+// sample_tfim.cu -- Metropolis sampler kernel for the transverse-field Ising model (single flips);
+// one warp per chain (the sweep itself is run_chain in rbm_warp.cuh).
+#include "rbm_warp.cuh"
+
+namespace vmc {
+
+template <int MPL, bool HEIS>
+__global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
+  extern __shared__ int8_t sm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int chain = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (chain >= A.C) return;
+  const int Npad = (A.rbm.N + 15) & ~15;
+  run_chain<MPL, HEIS>(A, chain, sm + wib * Npad, lane);
+}
+
+cudaError_t launch_sample_tfim(const SampleArgs& A, cudaStream_t st) {
+  if (A.C <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((A.C + kWarps - 1) / kWarps);
+  const size_t smem = spin_smem(A.rbm.N);
+  VMC_DISPATCH_MPL(A.rbm.M, k_sample<MPL, false><<<grid, 32 * kWarps, smem, st>>>(A));
+  return cudaGetLastError();
+}
+
+}  // namespace vmc
