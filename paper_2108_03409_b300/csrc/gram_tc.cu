@@ -1,18 +1,24 @@
-// gram_tc.cu -- S = <O^H O>^c (Eq. qfm) on the 5th-generation tensor cores.
+// gram_tc.cu -- S = <O^H O>^c (Eq. qfm) and the Schur-complement updates of the Cholesky
+// factorisation on the 5th-generation tensor cores.
 //
 // The centred log-derivatives are stored as real rows X (row 2k = Re Obar_k, row 2k+1 =
 // Im Obar_k, samples contiguous), split into BF16 pairs X = hi + lo.  The real Gram
 // G = X X^T is accumulated in FP32 in tensor memory as hi.hi^T + hi.lo^T + lo.hi^T (the
-// lo.lo^T term is 2^-16 below the others), one 128 x 128 tile of G per CTA, lower tiles
-// only.  The epilogue folds each 2x2 block of G into one complex entry of S:
+// lo.lo^T term is 2^-16 below the others), one 128 x 128 tile of G at a time, lower tiles
+// only.  The epilogue folds each 2x2 block of G into one complex entry:
 //   S_kl = (G[2k][2l] + G[2k+1][2l+1] + i (G[2k][2l+1] - G[2k+1][2l])) / n.
 //
-// Data movement: TMA (cp.async.bulk.tensor, 128-byte swizzle, no multicast) into a
-// 3-stage shared-memory ring guarded by mbarriers; one thread issues tcgen05.mma
-// (kind::f16, BF16 inputs, FP32 accumulator, M = N = 128, K = 16); tcgen05.commit frees
-// ring stages and signals the epilogue; tcgen05.ld reads the accumulator back.  Every
-// mbarrier wait is bounded (iteration and clock limits); on expiry the kernel records
-// DEV_ERR_TIMEOUT, skips the remaining work, frees its tensor memory and returns.
+// The kernel is persistent (one CTA per SM walks the tile list) and warp-specialised:
+// warp 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage ring,
+// warp 1 issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate, 128 x 128 x 16) into one
+// of two TMEM accumulators, and warps 2-5 drain the other accumulator with tcgen05.ld, so
+// the epilogue of one tile overlaps the loads and products of the next.  Ring stages and
+// accumulators are handed over through mbarriers (tcgen05.commit arrives on them).  Every
+// wait is bounded (iteration and clock limits); on expiry the kernel records
+// DEV_ERR_TIMEOUT, every role leaves its loop, copies and products in flight are waited for
+// (bounded), the tensor memory is freed and the kernel returns.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -27,9 +33,13 @@ constexpr int BM = 128, BN = 128, BK = 64;      // tile; BK = one 128-byte swizz
 constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * BK * 2;         // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;     // A_hi, A_lo, B_hi, B_lo
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int THREADS = 128;
-constexpr int TMEM_COLS = 128;
+constexpr int STG_LD = 66;                      // staging row stride (float2) of the Schur epilogue
+constexpr int STG_BYTES = 64 * STG_LD * 8;
+constexpr int NUM_BARS = 2 * STAGES + 5;        // full, empty, acc full x2, acc empty x2, final
+constexpr int SMEM_BYTES = 1024 /*align*/ + STAGES * STAGE_BYTES + STG_BYTES + 256;
+constexpr int THREADS = 192;                    // TMA warp, MMA warp, 4 epilogue warps
+constexpr int TMEM_COLS = 256;                  // two 128-column accumulators
+static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -42,6 +52,14 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
@@ -140,28 +158,34 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 __global__ void __launch_bounds__(tc::THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
-          int nk, int nt, int64_t P, double inv_n, double2* __restrict__ S, int mirror,
-          float2* __restrict__ A32, int64_t ldA, int64_t off, unsigned* status) {
+          int nk, int nt, int64_t tiles, int64_t P, double inv_n, double2* __restrict__ S,
+          int mirror, float2* __restrict__ A32, int64_t ldA, int64_t off, unsigned* status) {
   using namespace tc;
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
                                              ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars[0..STAGES): full, bars[STAGES..2 STAGES): empty, bars[2 STAGES]: accumulator done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  float2* stg = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + STG_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* accf = bars + 2 * STAGES;
+  uint64_t* acce = bars + 2 * STAGES + 2;
+  uint64_t* fin = bars + 2 * STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NUM_BARS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-
-  // tile (bm, bn), bn <= bm, grouped rasterisation (12 tile rows per group)
-  int bm, bn;
-  grouped_tri_tile(blockIdx.x, nt, 12, &bm, &bn);
+  // the epilogue leader's verdict per tile, in two slots by tile parity: a slot is rewritten
+  // two tiles later, after every epilogue thread has passed the barrier that follows its read
+  volatile int* epi_go = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2 * STAGES + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < NUM_BARS; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    mbar_init(smem_u32(&acce[0]), 4);
+    mbar_init(smem_u32(&acce[1]), 4);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                  ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -171,110 +195,150 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (kb >= STAGES && !mbar_wait(smem_u32(&bars[STAGES + s]), ((kb / STAGES) + 1) & 1, abort_flag))
-        break;
-      uint8_t* st = smem + s * STAGE_BYTES;
-      const uint32_t full = smem_u32(&bars[s]);
-      mbar_expect_tx(full, STAGE_BYTES);
-      tma_load_2d(smem_u32(st + 0 * TILE_BYTES), &map_hi, kb * BK, bm * BM, full);
-      tma_load_2d(smem_u32(st + 1 * TILE_BYTES), &map_lo, kb * BK, bm * BM, full);
-      tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &map_hi, kb * BK, bn * BN, full);
-      tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &map_lo, kb * BK, bn * BN, full);
-      issued = kb + 1;
-    }
-    if (*abort_flag) {
-      // let the copies already in flight land before the CTA exits (bounded)
-      volatile int dummy = 0;
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-        mbar_wait(smem_u32(&bars[kb % STAGES]), (kb / STAGES) & 1, &dummy);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(smem_u32(&bars[s]), (kb / STAGES) & 1, abort_flag)) break;
-      fence_after();
-      uint8_t* st = smem + s * STAGE_BYTES;
-      const uint64_t ah = smem_desc_sw128(smem_u32(st + 0 * TILE_BYTES));
-      const uint64_t al = smem_desc_sw128(smem_u32(st + 1 * TILE_BYTES));
-      const uint64_t bh = smem_desc_sw128(smem_u32(st + 2 * TILE_BYTES));
-      const uint64_t bl = smem_desc_sw128(smem_u32(st + 3 * TILE_BYTES));
-#pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t off = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
-        mma_bf16(tmem, ah + off, bh + off, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_bf16(tmem, ah + off, bl + off, idesc, 1u);
-        mma_bf16(tmem, al + off, bh + off, idesc, 1u);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int64_t g = 0;                                  // k-blocks issued so far
+      for (int64_t t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x) {
+        int bm, bn;
+        grouped_tri_tile(t, nt, 12, &bm, &bn);
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % STAGES);
+          const int64_t j = g / STAGES;
+          if (j > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((j - 1) & 1), abort_flag)) break;
+          uint8_t* st = smem + s * STAGE_BYTES;
+          const uint32_t fb = smem_u32(&full[s]);
+          mbar_expect_tx(fb, STAGE_BYTES);
+          tma_load_2d(smem_u32(st + 0 * TILE_BYTES), &map_hi, kb * BK, bm * BM, fb);
+          tma_load_2d(smem_u32(st + 1 * TILE_BYTES), &map_lo, kb * BK, bm * BM, fb);
+          tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &map_hi, kb * BK, bn * BN, fb);
+          tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &map_lo, kb * BK, bn * BN, fb);
+        }
       }
-      mma_commit(smem_u32(&bars[STAGES + s]));    // frees the stage when these MMAs finish
-    }
-    mma_commit(smem_u32(&bars[2 * STAGES]));      // accumulator complete
-  }
-  __syncwarp();
-
-  // ---------------- epilogue: all 4 warps, TMEM lane = tile row ----------------
-  const bool ok = mbar_wait(smem_u32(&bars[2 * STAGES]), 0, abort_flag) && !*abort_flag;
-  fence_after();
-  if (ok) {
-    const int r = warp * 32 + lane;                // tile row held by this thread
-    const bool even = (r & 1) == 0;
-    const int64_t k = (int64_t)bm * (BM / 2) + (r >> 1);
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      double re[16], im[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        // row 2k holds G[2k][2l], G[2k][2l+1]; row 2k+1 holds G[2k+1][2l], G[2k+1][2l+1]
-        const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
-        const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
-        const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
-        re[q] = even ? (double)mine0 + (double)oth1 : (double)oth0 + (double)mine1;
-        im[q] = even ? (double)mine1 - (double)oth0 : (double)oth1 - (double)mine0;
+      if (*abort_flag) {
+        // let the copies in flight land before the CTA exits (bounded)
+        volatile int dummy = 0;
+        for (int64_t h = (g > STAGES ? g - STAGES : 0); h < g; ++h)
+          mbar_wait(smem_u32(&full[h % STAGES]), (uint32_t)((h / STAGES) & 1), &dummy);
       }
-      const int64_t l0 = (int64_t)bn * (BN / 2) + (c0 >> 1);
-      if (A32) {
-        // Schur-complement update of a Cholesky factor: rows of X are the real and
-        // imaginary parts of L's panel, so sum_m L_km conj(L_lm) = conj(fold);
-        // A[off+k][off+l] -= conj(fold) on l <= k (the diagonal stays real).  The even row
-        // updates the even q, the odd row the odd q; loads are issued before the stores.
-        if (k < P) {
-          float2* rowp = A32 + (off + k) * ldA + off + l0;
-          float2 cur[8];
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+      int64_t g = 0;
+      int i = 0;
+      bool issued_any = false;
+      for (int64_t t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x, ++i) {
+        const int acc = i & 1, u = i >> 1;
+        if (u > 0 && !mbar_wait(smem_u32(&acce[acc]), (uint32_t)((u - 1) & 1), abort_flag)) break;
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % STAGES);
+          if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((g / STAGES) & 1), abort_flag)) { ok = false; break; }
+          fence_after();
+          uint8_t* st = smem + s * STAGE_BYTES;
+          const uint64_t ah = smem_desc_sw128(smem_u32(st + 0 * TILE_BYTES));
+          const uint64_t al = smem_desc_sw128(smem_u32(st + 1 * TILE_BYTES));
+          const uint64_t bh = smem_desc_sw128(smem_u32(st + 2 * TILE_BYTES));
+          const uint64_t bl = smem_desc_sw128(smem_u32(st + 3 * TILE_BYTES));
 #pragma unroll
-          for (int h = 0; h < 8; ++h) {
-            const int q = 2 * h + (even ? 0 : 1);
-            const int64_t l = l0 + q;
-            if (l < P && (bm != bn || l <= k)) cur[h] = rowp[q];
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
+            mma_bf16(d, ah + o, bh + o, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(d, ah + o, bl + o, idesc, 1u);
+            mma_bf16(d, al + o, bh + o, idesc, 1u);
           }
+          issued_any = true;
+          mma_commit(smem_u32(&empty[s]));            // frees the stage when these finish
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&accf[acc]));              // accumulator complete
+      }
+      if (*abort_flag && issued_any) {
+        // products in flight must finish before the tensor memory is freed (bounded)
+        volatile int dummy = 0;
+        mma_commit(smem_u32(fin));
+        mbar_wait(smem_u32(fin), 0, &dummy);
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2-5; TMEM lane quadrant = warp % 4 ----------------
+    const int qd = warp & 3;
+    const int r = qd * 32 + lane;                    // tile row held by this thread
+    const int et = (warp - 2) * 32 + lane;           // 0..127 within the epilogue group
+    const bool even = (r & 1) == 0;
+    int i = 0;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+      const int acc = i & 1, u = i >> 1;
+      if (et == 0)
+        epi_go[i & 1] = mbar_wait(smem_u32(&accf[acc]), (uint32_t)(u & 1), abort_flag) && !*abort_flag;
+      named_bar_sync(1, 128);                        // the leader's verdict is uniform
+      if (!epi_go[i & 1]) break;
+      fence_after();
+      int bm, bn;
+      grouped_tri_tile(t, nt, 12, &bm, &bn);
+      const int64_t k = (int64_t)bm * (BM / 2) + (r >> 1);
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(acc * BN + c0), v);
+        const int64_t l0 = (int64_t)bn * (BN / 2) + (c0 >> 1);
+        if (A32) {
+          // Schur update: stage the fold (FP32) of this row pair; the even row keeps the
+          // even q, the odd row the odd q.
 #pragma unroll
-          for (int h = 0; h < 8; ++h) {
-            const int q = 2 * h + (even ? 0 : 1);
+          for (int q = 0; q < 16; ++q) {
+            const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
+            const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
+            const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
+            if ((q & 1) == (even ? 0 : 1)) {
+              const float re = even ? mine0 + oth1 : oth0 + mine1;
+              const float im = even ? mine1 - oth0 : oth1 - mine0;
+              stg[(r >> 1) * STG_LD + (c0 >> 1) + q] = make_float2(re, im);
+            }
+          }
+        } else {
+          // row 2k holds G[2k][2l], G[2k][2l+1]; row 2k+1 holds G[2k+1][2l], G[2k+1][2l+1].
+          // Off-diagonal tiles: the even row writes S_kl, the odd row its mirror.  In a
+          // diagonal tile the accumulation order of (k,l) and (l,k) differs, so only l <= k
+          // is taken and mirrored, which keeps S exactly Hermitian.
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
+            const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
+            const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
+            const double re = even ? (double)mine0 + (double)oth1 : (double)oth0 + (double)mine1;
+            const double im = even ? (double)mine1 - (double)oth0 : (double)oth1 - (double)mine0;
             const int64_t l = l0 + q;
-            if (l < P && (bm != bn || l <= k)) {
-              float2 a = cur[h];
-              a.x -= (float)re[q];
-              if (l != k) a.y += (float)im[q];
-              rowp[q] = a;
+            if (k < P && l < P && (bm != bn || l <= k)) {
+              if (even) S[k * P + l] = make_double2(re * inv_n, (l == k) ? 0.0 : im * inv_n);
+              else if (mirror && l != k) S[l * P + k] = make_double2(re * inv_n, -im * inv_n);
             }
           }
         }
-      } else {
-        // Off-diagonal tiles: the even row writes S_kl, the odd row its mirror.  In a
-        // diagonal tile the accumulation order of (k,l) and (l,k) differs, so only l <= k
-        // is taken and mirrored, which keeps S exactly Hermitian.
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int64_t l = l0 + q;
-          if (k < P && l < P && (bm != bn || l <= k)) {
-            if (even) S[k * P + l] = make_double2(re[q] * inv_n, (l == k) ? 0.0 : im[q] * inv_n);
-            else if (mirror && l != k) S[l * P + k] = make_double2(re[q] * inv_n, -im[q] * inv_n);
+      }
+      // the accumulator may be overwritten once every warp's loads have completed
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acce[acc]));
+      if (A32) {
+        named_bar_sync(1, 128);                      // staging complete
+        // A[off+k][off+l] -= conj(fold) on l <= k, coalesced along rows; the diagonal
+        // stays real.  (The next tile's writes to the staging buffer come after the next
+        // named barrier, which every thread reaches only after this loop.)
+        const int64_t kb0 = (int64_t)bm * (BM / 2), lb0 = (int64_t)bn * (BN / 2);
+        for (int e = et; e < 64 * 64; e += 128) {
+          const int rr = e >> 6, cc = e & 63;
+          const int64_t kk = kb0 + rr, ll = lb0 + cc;
+          if (kk < P && ll < P && (bm != bn || ll <= kk)) {
+            float2* ap = A32 + (off + kk) * ldA + off + ll;
+            const float2 f = stg[rr * STG_LD + cc];
+            float2 a = *ap;
+            a.x -= f.x;
+            if (ll != kk) a.y += f.y;
+            *ap = a;
           }
         }
       }
@@ -282,7 +346,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS) : "memory");
@@ -325,6 +389,18 @@ static cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// one CTA per SM (the kernel's shared memory allows no second one), at most one per tile
+static unsigned persistent_grid(int64_t tiles) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, sms));
+}
+
 cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
                            bool mirror, unsigned* status, cudaStream_t st) {
@@ -344,8 +420,9 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
   }
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
-  k_gram_tc<<<(unsigned)tiles, tc::THREADS, tc::SMEM_BYTES, st>>>(
-      mhi, mlo, (int)(ld / tc::BK), (int)nt, P, inv_n, S, mirror ? 1 : 0, nullptr, 0, 0, status);
+  k_gram_tc<<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
+      mhi, mlo, (int)(ld / tc::BK), (int)nt, tiles, P, inv_n, S, mirror ? 1 : 0, nullptr, 0, 0,
+      status);
   return cudaGetLastError();
 }
 
@@ -366,8 +443,8 @@ cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, i
   }
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
-  k_gram_tc<<<(unsigned)tiles, tc::THREADS, tc::SMEM_BYTES, st>>>(
-      mhi, mlo, (int)(K / tc::BK), (int)nt, n, 1.0, nullptr, 0, A32, ldA, off, status);
+  k_gram_tc<<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
+      mhi, mlo, (int)(K / tc::BK), (int)nt, tiles, n, 1.0, nullptr, 0, A32, ldA, off, status);
   return cudaGetLastError();
 }
 
