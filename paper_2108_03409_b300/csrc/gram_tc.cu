@@ -273,13 +273,26 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     int i = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
       const int acc = i & 1, u = i >> 1;
+      int bm, bn;
+      grouped_tri_tile(t, nt, 12, &bm, &bn);
+      // Schur mode: fetch this thread's 32 entries of the factor's tile now, so that their
+      // memory latency overlaps the wait for the products (no stores intervene).
+      float2 cur[32];
+      if (A32) {
+        const int64_t kb0 = (int64_t)bm * (BM / 2), lb0 = (int64_t)bn * (BN / 2);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int e = et + 128 * j, rr = e >> 6, cc = e & 63;
+          const int64_t kk = kb0 + rr, ll = lb0 + cc;
+          cur[j] = (kk < P && ll < P && (bm != bn || ll <= kk)) ? A32[(off + kk) * ldA + off + ll]
+                                                              : make_float2(0.f, 0.f);
+        }
+      }
       if (et == 0)
         epi_go[i & 1] = mbar_wait(smem_u32(&accf[acc]), (uint32_t)(u & 1), abort_flag) && !*abort_flag;
       named_bar_sync(1, 128);                        // the leader's verdict is uniform
       if (!epi_go[i & 1]) break;
       fence_after();
-      int bm, bn;
-      grouped_tri_tile(t, nt, 12, &bm, &bn);
       const int64_t k = (int64_t)bm * (BM / 2) + (r >> 1);
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
@@ -329,16 +342,16 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
         // stays real.  (The next tile's writes to the staging buffer come after the next
         // named barrier, which every thread reaches only after this loop.)
         const int64_t kb0 = (int64_t)bm * (BM / 2), lb0 = (int64_t)bn * (BN / 2);
-        for (int e = et; e < 64 * 64; e += 128) {
-          const int rr = e >> 6, cc = e & 63;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int e = et + 128 * j, rr = e >> 6, cc = e & 63;
           const int64_t kk = kb0 + rr, ll = lb0 + cc;
           if (kk < P && ll < P && (bm != bn || ll <= kk)) {
-            float2* ap = A32 + (off + kk) * ldA + off + ll;
             const float2 f = stg[rr * STG_LD + cc];
-            float2 a = *ap;
+            float2 a = cur[j];
             a.x -= f.x;
             if (ll != kk) a.y += f.y;
-            *ap = a;
+            A32[(off + kk) * ldA + off + ll] = a;
           }
         }
       }

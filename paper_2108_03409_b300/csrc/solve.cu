@@ -61,11 +61,14 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
   }
 }
 
-// Factor the diagonal block (rows/cols k0..k0+kw) in shared memory and store its inverse.
-// 256 threads: column c is scaled, then the trailing lower triangle (r, cc), c < cc <= r,
-// is updated with all threads striding over it; the inverse is built row by row
-// (Linv[rr][c] = -sum_{m=c}^{rr-1} L[rr][m] Linv[m][c] / L[rr][rr]) with four threads per
-// column sharing the sum.
+// Factor the diagonal block (rows/cols k0..k0+kw) and store its inverse.  256 threads;
+// thread (tx, ty) = (tid / 16, tid % 16) keeps entries (ty + 16p, tx + 16q), p, q < 4, of
+// the block in registers.  Step c of the right-looking factorisation: the half-warp that
+// owns column c takes the pivot from its diagonal owner by a shuffle, scales the column and
+// publishes it in shared memory (double-buffered), then one block barrier, then every
+// thread applies the rank-1 update to its own entries.  The inverse Linv (L Linv = I) is
+// built the same way row by row: row m of Linv = (row m of the running right-hand side) /
+// L_mm is published by its owners, then the rows below subtract L_rm times it.
 constexpr int POTRF_THREADS = 256;
 
 template <typename C>
@@ -75,113 +78,178 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A,
                                                               unsigned* status) {
   typedef typename RealOf<C>::T R;
   extern __shared__ unsigned char psm[];
-  C* a = reinterpret_cast<C*>(psm);           // [NB][NB+1]
-  C* inv = a + NB * (NB + 1);                 // [NB][NB+1]
+  C* a = reinterpret_cast<C*>(psm);           // [NB][NB+1]: L after the factorisation
+  C* buf = a + NB * (NB + 1);                 // [2][NB]: published column / row
   const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
-    const int r = e / NB, c = e % NB;
-    a[r * (NB + 1) + c] = (r < kw && c <= r) ? A[(k0 + r) * P + k0 + c] : mk<C>(0.0, 0.0);
-    inv[r * (NB + 1) + c] = mk<C>(0.0, 0.0);
-  }
-  __syncthreads();
-  bool bad = false;
-  for (int c = 0; c < kw; ++c) {
-    R d = a[c * (NB + 1) + c].x;
-    if (!(d > (R)0) || !isfinite(d)) { bad = true; d = (R)1; }
-    const R lcc = sqrt(d);
-    const R ilcc = (R)1 / lcc;
-    __syncthreads();                          // everyone has read the pivot
-    for (int r = c + 1 + tid; r < kw; r += POTRF_THREADS) {
-      C v = a[r * (NB + 1) + c];
-      v.x *= ilcc;
-      v.y *= ilcc;
-      a[r * (NB + 1) + c] = v;
+  const int tx = tid >> 4, ty = tid & 15, warp = tid >> 5;
+  C v[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 16 * p, c = tx + 16 * q;
+      v[p][q] = (r < kw && c <= r) ? A[(k0 + r) * P + k0 + c] : mk<C>(0.0, 0.0);
     }
-    if (tid == 0) a[c * (NB + 1) + c] = mk<C>((double)lcc, 0.0);
-    __syncthreads();
-    // trailing update: thread (ty, tx) owns rows ty + 16p and columns tx + 16q of the block
-    {
-      const int ty = tid >> 4, tx = tid & 15;
+  bool bad = false;
+  int pb = 0;
 #pragma unroll
-      for (int pp = 0; pp < NB / 16; ++pp) {
-        const int rr = ty + 16 * pp;
-        if (rr <= c || rr >= kw) continue;
-        const C lr = a[rr * (NB + 1) + c];
+  for (int q = 0; q < 4; ++q) {
+    for (int cl = 0; cl < 16; ++cl) {
+      const int c = 16 * q + cl;
+      if (c >= kw) break;
+      if (warp == (cl >> 1)) {                       // the warp holding column c
+        R d = __shfl_sync(0xffffffffu, v[q][q].x, ((cl & 1) << 4) | cl);
+        if (tx == cl) {
+          if (!(d > (R)0) || !isfinite(d)) { bad = true; d = (R)1; }
+          const R lcc = sqrt(d), il = (R)1 / lcc;
 #pragma unroll
-        for (int qq = 0; qq < NB / 16; ++qq) {
-          const int cc = tx + 16 * qq;
-          if (cc <= c || cc > rr) continue;
-          const C lc = a[cc * (NB + 1) + c];
-          C v = a[rr * (NB + 1) + cc];
-          v.x -= lr.x * lc.x + lr.y * lc.y;       // v -= l_rc * conj(l_cc,c)
-          v.y -= lr.y * lc.x - lr.x * lc.y;
-          a[rr * (NB + 1) + cc] = v;
+          for (int p = 0; p < 4; ++p) {
+            const int r = ty + 16 * p;
+            if (r > c) {
+              v[p][q].x *= il;
+              v[p][q].y *= il;
+              buf[pb * NB + r] = v[p][q];
+            } else if (r == c) {
+              v[p][q] = mk<C>((double)lcc, 0.0);
+            }
+          }
         }
       }
+      __syncthreads();
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int r = ty + 16 * p;
+        if (r > c && r < kw) {
+          const C lr = buf[pb * NB + r];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const int cc = tx + 16 * qq;
+            if (cc > c && cc <= r) {
+              const C lc = buf[pb * NB + cc];
+              v[p][qq].x -= lr.x * lc.x + lr.y * lc.y;       // v -= l_rc * conj(l_cc,c)
+              v[p][qq].y -= lr.y * lc.x - lr.x * lc.y;
+            }
+          }
+        }
+      }
+      pb ^= 1;
     }
-    __syncthreads();
   }
-  if (bad && tid == 0) flag_error(status, DEV_ERR_NUMERIC);
+  if (bad) flag_error(status, DEV_ERR_NUMERIC);
+  // L to shared memory (for the inverse) and back to A
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 16 * p, c = tx + 16 * q;
+      a[r * (NB + 1) + c] = (r < kw && c <= r) ? v[p][q] : mk<C>(0.0, 0.0);
+    }
+  __syncthreads();
   for (int e = tid; e < kw * kw; e += POTRF_THREADS) {
     const int r = e / kw, c = e % kw;
     if (c <= r) A[(k0 + r) * P + k0 + c] = a[r * (NB + 1) + c];
   }
-  // inverse of the lower-triangular block, row by row (in the factor's precision)
-  if (tid < kw) {
-    C d;
-    d.x = (R)1 / a[tid * (NB + 1) + tid].x;
-    d.y = (R)0;
-    inv[tid * (NB + 1) + tid] = d;
-  }
-  __syncthreads();
-  const int col = tid >> 2, part = tid & 3;
-  for (int rr = 1; rr < kw; ++rr) {
-    C s = mk<C>(0.0, 0.0);
-    if (col < rr)
-      for (int mm = col + part; mm < rr; mm += 4) cfma(s, a[rr * (NB + 1) + mm], inv[mm * (NB + 1) + col]);
-    s.x += __shfl_xor_sync(0xffffffffu, s.x, 1);
-    s.y += __shfl_xor_sync(0xffffffffu, s.y, 1);
-    s.x += __shfl_xor_sync(0xffffffffu, s.x, 2);
-    s.y += __shfl_xor_sync(0xffffffffu, s.y, 2);
-    if (col < rr && part == 0) {
-      const R ilrr = inv[rr * (NB + 1) + rr].x;      // 1 / L[rr][rr]
-      C v;
-      v.x = -s.x * ilrr;
-      v.y = -s.y * ilrr;
-      inv[rr * (NB + 1) + col] = v;
+  // inverse: running right-hand side X (starts as I), same register ownership
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      v[p][q] = mk<C>((ty + 16 * p == tx + 16 * q) ? 1.0 : 0.0, 0.0);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    for (int ml = 0; ml < 16; ++ml) {
+      const int m = 16 * p + ml;
+      if (m >= kw) break;
+      if (ty == ml) {                               // owners of row m publish Linv[m][.]
+        const R il = (R)1 / a[m * (NB + 1) + m].x;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = tx + 16 * q;
+          if (c <= m) {
+            v[p][q].x *= il;
+            v[p][q].y *= il;
+            buf[pb * NB + c] = v[p][q];
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int pp = 0; pp < 4; ++pp) {
+        const int r = ty + 16 * pp;
+        if (r > m && r < kw) {
+          const C lrm = a[r * (NB + 1) + m];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = tx + 16 * q;
+            if (c <= m) {
+              const C xm = buf[pb * NB + c];
+              v[pp][q].x -= lrm.x * xm.x - lrm.y * xm.y;     // v -= L_rm * Linv[m][c]
+              v[pp][q].y -= lrm.x * xm.y + lrm.y * xm.x;
+            }
+          }
+        }
+      }
+      pb ^= 1;
     }
-    __syncthreads();
   }
+  __syncthreads();                                  // a is reused as the staging buffer
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = ty + 16 * p, c = tx + 16 * q;
+      a[r * (NB + 1) + c] = (r < kw && c <= r) ? v[p][q] : mk<C>(0.0, 0.0);
+    }
+  __syncthreads();
   for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
     const int r = e / NB, c = e % NB;
-    Dinv[e] = (r < kw && c < kw) ? inv[r * (NB + 1) + c] : mk<C>(0.0, 0.0);
+    Dinv[e] = a[r * (NB + 1) + c];
   }
 }
 
-// Panel: X = B L_kk^{-H}, X[r][c] = sum_{m<=c} B[r][m] conj(Linv[c][m]) for the rows
-// below the diagonal block; 64 rows per block, written over the panel of A.
+// Panel: X = B L_kk^{-H}, X[r][c] = sum_m B[r][m] conj(Linv[c][m]) (Linv is zero above its
+// diagonal) for the rows below the diagonal block; 64 rows per block, written over the
+// panel of A.  Thread (ty, tx) accumulates the 4 x 4 outputs (ty + 16a, tx + 16b).
 template <typename C>
 __global__ void __launch_bounds__(256) k_trsm_inv(C* __restrict__ A, int64_t P, int64_t k0,
                                                   int kw, const C* __restrict__ Dinv) {
   extern __shared__ unsigned char tsm[];
-  C* B = reinterpret_cast<C*>(tsm);            // [NB][NB+1]
-  C* Li = B + NB * (NB + 1);                   // [NB][NB+1]
+  C* Bt = reinterpret_cast<C*>(tsm);           // [NB (m)][NB+1 (r)]
+  C* Lt = Bt + NB * (NB + 1);                  // [NB (m)][NB+1 (c)]
   const int64_t r0 = k0 + kw + (int64_t)blockIdx.x * NB;
   const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += 256) {
-    const int rr = e / NB, c = e % NB;
-    Li[rr * (NB + 1) + c] = Dinv[e];
+    const int rr = e / NB, m = e % NB;
     const int64_t row = r0 + rr;
-    B[rr * (NB + 1) + c] = (row < P && c < kw) ? A[row * P + k0 + c] : mk<C>(0.0, 0.0);
+    Bt[m * (NB + 1) + rr] = (row < P && m < kw) ? A[row * P + k0 + m] : mk<C>(0.0, 0.0);
+    Lt[m * (NB + 1) + rr] = Dinv[e];             // e = c * NB + m with c = rr
   }
   __syncthreads();
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int rr = e / NB, c = e % NB;
-    const int64_t row = r0 + rr;
-    if (row >= P || c >= kw) continue;
-    C s = mk<C>(0.0, 0.0);
-    for (int m = 0; m <= c; ++m) cfmac(s, B[rr * (NB + 1) + m], Li[c * (NB + 1) + m]);
-    A[row * P + k0 + c] = s;
+  const int tx = tid & 15, ty = tid >> 4;
+  C acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<C>(0.0, 0.0);
+  for (int m = 0; m < kw; ++m) {
+    C br[4], lc[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) br[i] = Bt[m * (NB + 1) + ty + 16 * i];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) lc[j] = Lt[m * (NB + 1) + tx + 16 * j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cfmac(acc[i][j], br[i], lc[j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t row = r0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = tx + 16 * j;
+      if (row < P && c < kw) A[row * P + k0 + c] = acc[i][j];
+    }
   }
 }
 
@@ -542,12 +610,15 @@ __global__ void k_panel_to_x(const float2* __restrict__ A, int64_t P, int64_t r0
 // host side
 // ---------------------------------------------------------------------------------------
 template <typename C>
+static constexpr size_t potrf_smem() { return (size_t)(NB * (NB + 1) + 2 * NB) * sizeof(C); }
+
+template <typename C>
 static cudaError_t set_smem_attrs() {
   static bool done = false;
   if (done) return cudaSuccess;
   const int s2 = 2 * NB * (NB + 1) * (int)sizeof(C);
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_potrf_diag<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_potrf_diag<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, potrf_smem<C>())) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_trsm_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_herk<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2)) != cudaSuccess) return e;
   done = true;
@@ -569,7 +640,7 @@ static cudaError_t factor(C* A, C* Dinv, int64_t P, unsigned* status, cudaStream
   for (int64_t kb = 0; kb < nblk; ++kb) {
     const int64_t k0 = kb * NB;
     const int kw = (int)std::min<int64_t>(NB, P - k0);
-    k_potrf_diag<C><<<1, POTRF_THREADS, s2, st>>>(A, P, k0, kw, Dinv + kb * NB * NB, status);
+    k_potrf_diag<C><<<1, POTRF_THREADS, potrf_smem<C>(), st>>>(A, P, k0, kw, Dinv + kb * NB * NB, status);
     ++*launches;
     const int64_t rest = P - k0 - kw;
     if (rest > 0) {
@@ -597,7 +668,7 @@ static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, u
     for (int64_t k0 = p0; k0 < pend; k0 += NB) {
       const int64_t kb = k0 / NB;
       const int kw = (int)std::min<int64_t>(NB, P - k0);
-      k_potrf_diag<float2><<<1, POTRF_THREADS, s2, st>>>(A, P, k0, kw, Dinv + kb * NB * NB, status);
+      k_potrf_diag<float2><<<1, POTRF_THREADS, potrf_smem<float2>(), st>>>(A, P, k0, kw, Dinv + kb * NB * NB, status);
       ++*launches;
       const int64_t rest = P - k0 - kw;
       if (rest > 0) {
