@@ -158,9 +158,11 @@ vmc_status refresh_fp32(vmc_ctx* ctx, LatticeState& L) {
   return VMC_OK;
 }
 
-// S of a sample set with T = tanh theta already in ctx->s_T; E may be null.
+// S of a sample set with T = tanh theta already in ctx->s_T; E may be null.  S_out (FP64)
+// may be null when `fused` (tensor-core Gram only): the Gram then writes the mixed solvers'
+// inputs (ctx->sw.S2 and the shifted lower triangle in ctx->sw.A32) directly.
 vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const float2* E,
-                    int64_t n, int precision, double2* S_out, bool mirror) {
+                    int64_t n, int precision, double2* S_out, bool mirror, bool fused = false) {
   CK(launch_moments(spins, ctx->s_T, E, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
                     E ? ctx->F : nullptr, ctx->st), "moments");
   ctx->launches += 2;
@@ -175,7 +177,8 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
     ++ctx->launches;
     cudaEventRecord(ctx->ev[6], ctx->st);
     cudaError_t e = launch_gram_tc(ctx->Xhi, ctx->Xlo, rows_pad, ld, L.P, inv_n, S_out, mirror,
-                                   ctx->status, ctx->st);
+                                   fused ? ctx->sw.S2 : nullptr, fused ? ctx->sw.A32 : nullptr,
+                                   ctx->cfg.shift, ctx->cfg.shift_mode, ctx->status, ctx->st);
     cudaEventRecord(ctx->ev[7], ctx->st);
     if (e == cudaErrorNotSupported) return fail(ctx, VMC_ERR_ARG, "tensor-core Gram: shape not supported");
     CK(e, "gram_tc");
@@ -192,6 +195,7 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
   return VMC_OK;
 }
 
+// S (FP64) may be null for the mixed solvers when the Gram already wrote their inputs.
 vmc_status solve_core(vmc_ctx* ctx, LatticeState& L, const double2* S, const double2* F,
                       double2* x, int* iters, double* relres) {
   ctx->sw.P = L.P;
@@ -204,7 +208,11 @@ vmc_status solve_core(vmc_ctx* ctx, LatticeState& L, const double2* S, const dou
     CK(residual_fp64(S, F, x, c.shift, c.shift_mode, ctx->sw, ctx->st, &rel), "residual");
     ctx->launches += 2;
   } else if (c.solver == VMC_SOLVER_CHOLESKY_MIXED || c.solver == VMC_SOLVER_CHOLESKY_TC) {
-    CK(solve_cholesky_mixed(S, F, x, c.shift, c.shift_mode, c.cg_tol, c.cg_maxit,
+    if (S) {
+      CK(split_shift(S, c.shift, c.shift_mode, ctx->sw, ctx->st), "split_shift");
+      ++ctx->launches;
+    }
+    CK(solve_cholesky_mixed(F, x, c.shift, c.shift_mode, c.cg_tol, c.cg_maxit,
                             c.solver == VMC_SOLVER_CHOLESKY_TC, ctx->sw, ctx->status, ctx->st,
                             &ctx->launches, &it, &rel), "cholesky_mixed");
   } else {
@@ -363,7 +371,8 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
       if ((e = dalloc(ctx, &ctx->sw.A32, (size_t)P * P)) ||
           (e = dalloc(ctx, &ctx->sw.D32, (size_t)nblk * 64 * 64)) ||
           (e = dalloc(ctx, &ctx->sw.T32f, nsb * 256 * 256)) ||
-          (e = dalloc(ctx, &ctx->sw.T32b, nsb * 256 * 256)))
+          (e = dalloc(ctx, &ctx->sw.T32b, nsb * 256 * 256)) ||
+          (e = dalloc(ctx, &ctx->sw.S2, (size_t)P * P)) || (e = dalloc(ctx, &ctx->sw.x2, P)))
         return oom(e);
     }
   }
@@ -625,11 +634,17 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   int iters = 0;
   double rel = 0.0;
   if (ctx->dense) {
-    // 3. S (moments + centred X + Gram)
-    if ((s = qfm_core(ctx, L, ctx->s_spins, ctx->s_E, Ns, c.precision, ctx->S, true))) return s;
+    // 3. S (moments + centred X + Gram); with the tensor-core Gram and a mixed solver the
+    //    Gram writes the solver's inputs directly
+    const bool fused = c.precision == VMC_PREC_BF16SPLIT &&
+                       (c.solver == VMC_SOLVER_CHOLESKY_MIXED || c.solver == VMC_SOLVER_CHOLESKY_TC);
+    ctx->sw.P = L.P;
+    if ((s = qfm_core(ctx, L, ctx->s_spins, ctx->s_E, Ns, c.precision, fused ? nullptr : ctx->S,
+                      true, fused)))
+      return s;
     CK(cudaEventRecord(ctx->ev[3], ctx->st), "sr_step");
     // 4. solve (synchronises)
-    if ((s = solve_core(ctx, L, ctx->S, ctx->F, ctx->x, &iters, &rel))) return s;
+    if ((s = solve_core(ctx, L, fused ? nullptr : ctx->S, ctx->F, ctx->x, &iters, &rel))) return s;
   } else {
     // 3. <O>, F and diag(S) (S itself is never formed)
     CK(launch_moments(ctx->s_spins, ctx->s_T, ctx->s_E, ctx->estats, Ns, L.N, L.M, ctx->partial,

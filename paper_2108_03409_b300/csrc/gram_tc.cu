@@ -159,7 +159,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 __global__ void __launch_bounds__(tc::THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
           int nk, int nt, int64_t tiles, int64_t P, double inv_n, double2* __restrict__ S,
-          int mirror, float2* __restrict__ A32, int64_t ldA, int64_t off, unsigned* status) {
+          float4* __restrict__ S2, float2* __restrict__ Af, double nu, int shift_mode, int mirror,
+          float2* __restrict__ A32, int64_t ldA, int64_t off, unsigned* status) {
   using namespace tc;
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
@@ -326,8 +327,25 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             const double im = even ? (double)mine1 - (double)oth0 : (double)oth1 - (double)mine0;
             const int64_t l = l0 + q;
             if (k < P && l < P && (bm != bn || l <= k)) {
-              if (even) S[k * P + l] = make_double2(re * inv_n, (l == k) ? 0.0 : im * inv_n);
-              else if (mirror && l != k) S[l * P + k] = make_double2(re * inv_n, -im * inv_n);
+              const double vr = re * inv_n, vi = (l == k) ? 0.0 : im * inv_n;
+              if (even) {
+                if (S) S[k * P + l] = make_double2(vr, vi);
+                if (S2 || Af) {
+                  const float hr = (float)vr, hi = (float)vi;
+                  if (S2) S2[k * P + l] = make_float4(hr, hi, (float)(vr - (double)hr), (float)(vi - (double)hi));
+                  if (Af) {
+                    // the factor's input: lower triangle with the diagonal shift
+                    const float d = (l == k) ? (float)(shift_mode == 0 ? vr * (1.0 + nu) : vr + nu) : hr;
+                    Af[k * P + l] = make_float2(d, hi);
+                  }
+                }
+              } else if (mirror && l != k) {
+                if (S) S[l * P + k] = make_double2(vr, -vi);
+                if (S2) {
+                  const float hr = (float)vr, hi = (float)(-vi);
+                  S2[l * P + k] = make_float4(hr, hi, (float)(vr - (double)hr), (float)(-vi - (double)hi));
+                }
+              }
             }
           }
         }
@@ -416,7 +434,8 @@ static unsigned persistent_grid(int64_t tiles) {
 
 cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
-                           bool mirror, unsigned* status, cudaStream_t st) {
+                           bool mirror, float4* S2, float2* Af, double nu, int shift_mode,
+                           unsigned* status, cudaStream_t st) {
   if (rows_pad % tc::BM != 0 || ld % tc::BK != 0 || ld < tc::BK) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(Xhi) | reinterpret_cast<uintptr_t>(Xlo)) & 15)
     return cudaErrorNotSupported;
@@ -434,8 +453,8 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
   k_gram_tc<<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
-      mhi, mlo, (int)(ld / tc::BK), (int)nt, tiles, P, inv_n, S, mirror ? 1 : 0, nullptr, 0, 0,
-      status);
+      mhi, mlo, (int)(ld / tc::BK), (int)nt, tiles, P, inv_n, S, S2, Af, nu, shift_mode,
+      mirror ? 1 : 0, nullptr, 0, 0, status);
   return cudaGetLastError();
 }
 
@@ -457,7 +476,8 @@ cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, i
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
   k_gram_tc<<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
-      mhi, mlo, (int)(K / tc::BK), (int)nt, tiles, n, 1.0, nullptr, 0, A32, ldA, off, status);
+      mhi, mlo, (int)(K / tc::BK), (int)nt, tiles, n, 1.0, nullptr, nullptr, nullptr, 0.0, 0, 0,
+      A32, ldA, off, status);
   return cudaGetLastError();
 }
 

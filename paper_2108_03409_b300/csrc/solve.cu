@@ -373,37 +373,110 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, un
 // its share of the remaining rows; one grid barrier per step.
 constexpr int SB = 256;
 
-// Inverse of the diagonal block sb of L (rows/cols k0 .. k0+kw), one CTA per block, thread t
-// owns column t: forward substitution L_blk X = I with X[r][t] = (delta_rt - sum_{m<r}
-// L[r][m] X[m][t]) / L[r][r].  Stored twice: T[m][t] = Linv[t][m] (forward solve) and
-// Linv[m][t] (backward solve), both [nsb][SB][SB].
+// Inverse of each 256 x 256 diagonal block of L, assembled from the inverses D_i of its
+// four 64 x 64 diagonal blocks (left by the factorisation) by block forward substitution:
+//   X_jj = D_j,   X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj   (i > j, 64 x 64 blocks),
+// one CTA per 256-block doing its 64 x 64 complex products in shared memory (4 x 4
+// register tiles).  Stored twice: Tb[r][c] = Linv[r][c] (backward solve) and
+// Tf[c][r] = Linv[r][c] (forward solve), both [nsb][SB][SB].
 template <typename C>
-__global__ void __launch_bounds__(SB) k_inv_sb(const C* __restrict__ A, int64_t P,
-                                              C* __restrict__ Tf, C* __restrict__ Tb) {
-  typedef typename RealOf<C>::T R;
-  const int64_t k0 = (int64_t)blockIdx.x * SB;
-  const int kw = (int)min((int64_t)SB, P - k0);
-  const int t = threadIdx.x;
-  C* tf = Tf + (int64_t)blockIdx.x * SB * SB;
-  C* tb = Tb + (int64_t)blockIdx.x * SB * SB;
-  // X column t, built row by row into tb[r][t] (coalesced across t)
-  for (int r = 0; r < SB; ++r) {
-    C v = mk<C>(0.0, 0.0);
-    if (r < kw && t < kw && t <= r) {
-      C acc = mk<C>(r == t ? 1.0 : 0.0, 0.0);
-      for (int m = t; m < r; ++m) {
-        const C l = A[(k0 + r) * P + k0 + m];          // same address in every thread
-        const C xm = tb[(int64_t)m * SB + t];
-        acc.x -= l.x * xm.x - l.y * xm.y;
-        acc.y -= l.x * xm.y + l.y * xm.x;
-      }
-      const R ild = (R)1 / A[(k0 + r) * P + k0 + r].x;
-      v.x = acc.x * ild;
-      v.y = acc.y * ild;
-    }
-    tb[(int64_t)r * SB + t] = v;       // each thread reads back only its own column
+__device__ void tile_load(C* sm_t, const C* __restrict__ g, int64_t ld, int rows, int cols,
+                          bool transpose) {
+  // sm_t[m][r] (transpose) or sm_t[r][m], 64 x 65 padded; entries outside rows x cols are 0
+  for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+    const int r = e / NB, m = e % NB;
+    const C v = (r < rows && m < cols) ? g[(int64_t)r * ld + m] : mk<C>(0.0, 0.0);
+    if (transpose) sm_t[m * (NB + 1) + r] = v;
+    else sm_t[r * (NB + 1) + m] = v;
   }
-  for (int r = 0; r < SB; ++r) tf[(int64_t)t * SB + r] = tb[(int64_t)r * SB + t];
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t P,
+                                               const C* __restrict__ Dinv, C* __restrict__ Tf,
+                                               C* __restrict__ Tb) {
+  extern __shared__ unsigned char ism[];
+  C* At = reinterpret_cast<C*>(ism);          // left operand, transposed: At[m][r]
+  C* Bs = At + NB * (NB + 1);                 // right operand: Bs[m][c]
+  const int sb = blockIdx.x;
+  const int64_t k0 = (int64_t)sb * SB;
+  const int kw = (int)min((int64_t)SB, P - k0);
+  const int nblk = (kw + NB - 1) / NB;
+  C* tb = Tb + (int64_t)sb * SB * SB;
+  C* tf = Tf + (int64_t)sb * SB * SB;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // diagonal blocks and zeros elsewhere
+  for (int e = tid; e < SB * SB; e += 256) {
+    const int r = e / SB, c = e % SB, i = r / NB, j = c / NB;
+    tb[e] = (i == j && i < nblk) ? Dinv[((int64_t)(k0 / NB) + i) * NB * NB + (r % NB) * NB + (c % NB)]
+                                 : mk<C>(0.0, 0.0);
+  }
+  __syncthreads();
+  auto rows_of = [&](int i) { return min(NB, kw - NB * i); };
+  for (int j = 0; j < nblk; ++j) {
+    for (int i = j + 1; i < nblk; ++i) {
+      C acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = mk<C>(0.0, 0.0);
+      // T = sum_k L_ik X_kj
+      for (int k = j; k < i; ++k) {
+        tile_load(At, A + (k0 + NB * i) * P + k0 + NB * k, P, rows_of(i), rows_of(k), true);
+        tile_load(Bs, tb + (int64_t)(NB * k) * SB + NB * j, SB, rows_of(k), rows_of(j), false);
+        __syncthreads();
+        for (int m = 0; m < NB; ++m) {
+          C ar[4], bc[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) ar[a] = At[m * (NB + 1) + ty + 16 * a];
+#pragma unroll
+          for (int b = 0; b < 4; ++b) bc[b] = Bs[m * (NB + 1) + tx + 16 * b];
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) cfma(acc[a][b], ar[a], bc[b]);
+        }
+        __syncthreads();
+      }
+      // X_ij = -D_i T
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) Bs[(ty + 16 * a) * (NB + 1) + tx + 16 * b] = acc[a][b];
+      tile_load(At, Dinv + ((int64_t)(k0 / NB) + i) * NB * NB, NB, NB, NB, true);
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = mk<C>(0.0, 0.0);
+      for (int m = 0; m < NB; ++m) {
+        C ar[4], bc[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) ar[a] = At[m * (NB + 1) + ty + 16 * a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) bc[b] = Bs[m * (NB + 1) + tx + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) cfma(acc[a][b], ar[a], bc[b]);
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int r = ty + 16 * a, c = tx + 16 * b;
+          C v = acc[a][b];
+          v.x = -v.x;
+          v.y = -v.y;
+          if (r < rows_of(i) && c < rows_of(j)) tb[(int64_t)(NB * i + r) * SB + NB * j + c] = v;
+        }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < SB * SB; e += 256) {
+    const int r = e / SB, c = e % SB;
+    tf[(int64_t)c * SB + r] = tb[e];
+  }
 }
 
 // y[t] = sum_m T[m][t] v[m] over the (zero-padded) 256 x 256 block, loads issued in
@@ -607,6 +680,122 @@ __global__ void k_panel_to_x(const float2* __restrict__ A, int64_t P, int64_t r0
 }
 
 // ---------------------------------------------------------------------------------------
+// Residuals of the mixed solvers in compensated FP32 arithmetic.  S and x are held as
+// FP32 hi/lo pairs (S = S_hi + S_lo to ~2^-48); each row's sum of S_hi x_hi products is
+// accumulated error-free (Dekker's product by fma, Knuth's two-sum) into a (sum,
+// correction) pair, the hi.lo and lo.hi terms (2^-24 smaller) into the correction.  This
+// keeps the refinement at FP64-level accuracy on the FP32 pipe (FP64 throughput on this
+// part is ~1/60 of FP32).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum_acc(float& s, float& c, float p) {
+  const float t = s + p;
+  const float bb = t - s;
+  c += (s - (t - bb)) + (p - bb);
+  s = t;
+}
+
+__global__ void k_split_x(const double2* __restrict__ x, float4* __restrict__ x2, int64_t P) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = x[k];
+    const float hr = (float)v.x, hi = (float)v.y;
+    x2[k] = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+  }
+}
+
+// S (FP64) -> S2 (hi/lo pairs, every entry) and A32 (lower triangle, shifted diagonal)
+__global__ void k_split_shift(const double2* __restrict__ S, float4* __restrict__ S2,
+                              float2* __restrict__ A, int64_t P, double nu, int mode) {
+  const int64_t total = P * P;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 v = S[e];
+    const float hr = (float)v.x, hi = (float)v.y;
+    S2[e] = make_float4(hr, hi, (float)(v.x - (double)hr), (float)(v.y - (double)hi));
+    const int64_t r = e / P, c = e - r * P;
+    if (c <= r) {
+      const float d = (r == c) ? (float)(mode == 0 ? v.x * (1.0 + nu) : v.x + nu) : hr;
+      A[e] = make_float2(d, hi);
+    }
+  }
+}
+
+// A32 (lower, shifted) again from S2, for a refactorisation
+__global__ void k_s2_to_a32(const float4* __restrict__ S2, float2* __restrict__ A, int64_t P,
+                            double nu, int mode) {
+  const int64_t total = P * P;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / P, c = e - r * P;
+    if (c > r) continue;
+    const float4 v = S2[e];
+    float d = v.x;
+    if (r == c) {
+      const double s = (double)v.x + (double)v.z;
+      d = (float)(mode == 0 ? s * (1.0 + nu) : s + nu);
+    }
+    A[e] = make_float2(d, v.y);
+  }
+}
+
+// r = F - (S + shift) x, one block per row; acc[0] += ||r||^2
+__global__ void __launch_bounds__(256) k_resid_df(const float4* __restrict__ S2,
+                                                  const float4* __restrict__ x2,
+                                                  const double2* __restrict__ x,
+                                                  const double2* __restrict__ F, int64_t P,
+                                                  double nu, int mode, double2* __restrict__ r,
+                                                  double* acc) {
+  __shared__ double red[2][8];
+  const int64_t row = blockIdx.x;
+  const float4* srow = S2 + row * P;
+  float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+  for (int64_t c = threadIdx.x; c < P; c += blockDim.x) {
+    const float4 a = srow[c];      // hi.re, hi.im, lo.re, lo.im
+    const float4 v = x2[c];
+    const float p1 = a.x * v.x, e1 = fmaf(a.x, v.x, -p1);
+    const float p2 = -(a.y * v.y), e2 = fmaf(-a.y, v.y, -p2);
+    const float p3 = a.x * v.y, e3 = fmaf(a.x, v.y, -p3);
+    const float p4 = a.y * v.x, e4 = fmaf(a.y, v.x, -p4);
+    float tr = e1 + e2;
+    tr = fmaf(a.x, v.z, tr);
+    tr = fmaf(-a.y, v.w, tr);
+    tr = fmaf(a.z, v.x, tr);
+    tr = fmaf(-a.w, v.y, tr);
+    float ti = e3 + e4;
+    ti = fmaf(a.x, v.w, ti);
+    ti = fmaf(a.y, v.z, ti);
+    ti = fmaf(a.z, v.y, ti);
+    ti = fmaf(a.w, v.x, ti);
+    two_sum_acc(sr, cr, p1);
+    two_sum_acc(sr, cr, p2);
+    cr += tr;
+    two_sum_acc(si, ci, p3);
+    two_sum_acc(si, ci, p4);
+    ci += ti;
+  }
+  double dr = (double)sr + (double)cr, di = (double)si + (double)ci;
+  dr = warp_sum_d(dr);
+  di = warp_sum_d(di);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { red[0][w] = dr; red[1][w] = di; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0, ti = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { tr += red[0][k]; ti += red[1][k]; }
+    const float4 d = srow[row];
+    const double skk = (double)d.x + (double)d.z;
+    const double2 v = x[row];
+    const double extra = (mode == 0) ? nu * skk : nu;   // shift acts on the diagonal only
+    tr += extra * v.x;
+    ti += extra * v.y;
+    const double2 f = F[row];
+    const double2 res = make_double2(f.x - tr, f.y - ti);
+    r[row] = res;
+    atomicAdd(acc, res.x * res.x + res.y * res.y);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
 template <typename C>
@@ -620,6 +809,7 @@ static cudaError_t set_smem_attrs() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_potrf_diag<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, potrf_smem<C>())) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_trsm_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_inv_sb<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_herk<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, s2)) != cudaSuccess) return e;
   done = true;
   return cudaSuccess;
@@ -709,12 +899,18 @@ template <typename C> static C* inv_bwd(SolveWork& w);
 template <> float2* inv_bwd<float2>(SolveWork& w) { return w.T32b; }
 template <> double2* inv_bwd<double2>(SolveWork& w) { return w.T64b; }
 
+template <typename C> static const C* dinv_of(SolveWork& w);
+template <> const float2* dinv_of<float2>(SolveWork& w) { return w.D32; }
+template <> const double2* dinv_of<double2>(SolveWork& w) { return w.D64; }
+
 // inverses of the 256-wide diagonal blocks of the factor (once per factorisation)
 template <typename C>
 static cudaError_t invert_blocks(const C* A, int64_t P, SolveWork& w, cudaStream_t st,
                                  int64_t* launches) {
   const int64_t nsb = (P + SB - 1) / SB;
-  k_inv_sb<C><<<(unsigned)nsb, SB, 0, st>>>(A, P, inv_fwd<C>(w), inv_bwd<C>(w));
+  const C* Dinv = dinv_of<C>(w);
+  k_inv_sb<C><<<(unsigned)nsb, 256, 2 * NB * (NB + 1) * sizeof(C), st>>>(A, P, Dinv, inv_fwd<C>(w),
+                                                                           inv_bwd<C>(w));
   ++*launches;
   return cudaGetLastError();
 }
@@ -778,13 +974,31 @@ cudaError_t solve_cholesky_fp64(const double2* S, const double2* F, double2* x, 
   return chol_solve<double2>(w.A64, w.D64, P, w.c, w.r, x, w, status, st, launches);
 }
 
-cudaError_t solve_cholesky_mixed(const double2* S, const double2* F, double2* x, double nu,
-                                 int mode, double tol, int maxit, bool tc, SolveWork& w,
-                                 unsigned* status, cudaStream_t st, int64_t* launches,
-                                 int* iters, double* relres) {
+cudaError_t split_shift(const double2* S, double nu, int mode, SolveWork& w, cudaStream_t st) {
+  k_split_shift<<<grid_for(w.P * w.P, 256), 256, 0, st>>>(S, w.S2, w.A32, w.P, nu, mode);
+  return cudaGetLastError();
+}
+
+static cudaError_t residual_df(const double2* F, const double2* x, double nu, int mode,
+                               SolveWork& w, cudaStream_t st, double* relres) {
   const int64_t P = w.P;
-  k_copy_shift<float2><<<grid_for(P * P, 256), 256, 0, st>>>(S, w.A32, P, nu, mode);
-  ++*launches;
+  VMC_TRY(cudaMemsetAsync(w.scal, 0, 2 * sizeof(double), st));
+  k_split_x<<<grid_for(P, 256, 1024), 256, 0, st>>>(x, w.x2, P);
+  k_resid_df<<<(unsigned)P, 256, 0, st>>>(w.S2, w.x2, x, F, P, nu, mode, w.r, w.scal);
+  k_norm2<<<grid_for(P, 256, 1024), 256, 0, st>>>(F, P, w.scal + 1);
+  VMC_TRY(cudaGetLastError());
+  double h[2];
+  VMC_TRY(cudaMemcpyAsync(h, w.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VMC_TRY(cudaStreamSynchronize(st));
+  *relres = (h[1] > 0) ? sqrt(h[0] / h[1]) : 0.0;
+  return cudaSuccess;
+}
+
+cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mode, double tol,
+                                 int maxit, bool tc, SolveWork& w, unsigned* status,
+                                 cudaStream_t st, int64_t* launches, int* iters,
+                                 double* relres) {
+  const int64_t P = w.P;
   if (tc && P > NBO) VMC_TRY(factor_tc(w.A32, w.D32, P, w, status, st, launches));
   else VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
   VMC_TRY(invert_blocks<float2>(w.A32, P, w, st, launches));
@@ -798,14 +1012,14 @@ cudaError_t solve_cholesky_mixed(const double2* S, const double2* F, double2* x,
     VMC_TRY(chol_solve<float2>(w.A32, w.D32, P, w.r32, w.y32, w.c32, w, status, st, launches));
     k_add_f32<<<grid_for(P, 256, 1024), 256, 0, st>>>(x, w.c32, P);
     *launches += 2;
-    VMC_TRY(residual_fp64(S, F, x, nu, mode, w, st, &rel));
-    *launches += 2;
+    VMC_TRY(residual_df(F, x, nu, mode, w, st, &rel));
+    *launches += 3;
     if (!(rel == rel)) break;      // NaN
     if (rel <= tol) { ++it; break; }
     // The BF16-split factor contracts the error by ~cond(S~) * 2^-16 per iteration; if that
     // is too slow, refactor in FP32 and keep refining from the current x.
     if (tc_factor && it >= 1 && rel > 0.25 * prev) {
-      k_copy_shift<float2><<<grid_for(P * P, 256), 256, 0, st>>>(S, w.A32, P, nu, mode);
+      k_s2_to_a32<<<grid_for(P * P, 256), 256, 0, st>>>(w.S2, w.A32, P, nu, mode);
       ++*launches;
       VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
       VMC_TRY(invert_blocks<float2>(w.A32, P, w, st, launches));

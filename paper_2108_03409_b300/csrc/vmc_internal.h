@@ -87,9 +87,13 @@ cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_
 
 // Same contraction on the tensor cores (tcgen05, BF16 hi/lo split, FP32 accumulation
 // in TMEM).  Returns cudaErrorNotSupported when the shapes are not supported.
+// Optional outputs besides S (FP64, may be null): S2 = S as FP32 hi/lo pairs {hi.re,
+// hi.im, lo.re, lo.im} (full matrix with the mirror), and Af = the FP32 input of the
+// Cholesky factorisation (lower triangle, diagonal shifted by nu in shift_mode).
 cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
-                           bool mirror, unsigned* status, cudaStream_t st);
+                           bool mirror, float4* S2, float2* Af, double nu, int shift_mode,
+                           unsigned* status, cudaStream_t st);
 
 // Schur-complement update of an FP32 complex Cholesky factor on the tensor cores:
 // A[off+k][off+l] -= sum_m L_km conj(L_lm) for 0 <= l <= k < n, with L's panel given as
@@ -117,18 +121,25 @@ struct SolveWork {
   __nv_bfloat16* Xhi;  // panel operands of the tensor-core Schur updates
   __nv_bfloat16* Xlo;
   int64_t x_elems;     // capacity of Xhi / Xlo
+  float4* S2;          // [P][P] S as FP32 hi/lo pairs (mixed solvers' residual)
+  float4* x2;          // [P] iterate as FP32 hi/lo pairs
 };
 
 // Cholesky solve of (S + shift) x = F, FP64 throughout.
 cudaError_t solve_cholesky_fp64(const double2* S, const double2* F, double2* x, double nu,
                                 int mode, SolveWork& w, unsigned* status, cudaStream_t st,
                                 int64_t* launches);
-// FP32 Cholesky of the shifted matrix + FP64 iterative refinement; tc = trailing updates
-// of 256-wide panels on the tensor cores (BF16 split) instead of FP32 SIMT.
-cudaError_t solve_cholesky_mixed(const double2* S, const double2* F, double2* x, double nu,
-                                 int mode, double tol, int maxit, bool tc, SolveWork& w,
-                                 unsigned* status, cudaStream_t st, int64_t* launches,
-                                 int* iters, double* relres);
+// Mixed solvers' inputs from an FP64 S: w.S2 (hi/lo pairs, full) and w.A32 (lower
+// triangle + shift).  The tensor-core Gram writes both directly instead.
+cudaError_t split_shift(const double2* S, double nu, int mode, SolveWork& w, cudaStream_t st);
+// FP32 Cholesky of w.A32 + iterative refinement with residuals F - (S + shift) x formed from
+// w.S2 in compensated FP32 arithmetic (hi/lo pairs, error-free products and sums);
+// tc = trailing updates of 256-wide panels on the tensor cores (BF16 split) instead of
+// FP32 SIMT.
+cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mode, double tol,
+                                 int maxit, bool tc, SolveWork& w, unsigned* status,
+                                 cudaStream_t st, int64_t* launches, int* iters,
+                                 double* relres);
 // FP64 relative residual ||(S + shift) x - F|| / ||F|| (synchronises).
 cudaError_t residual_fp64(const double2* S, const double2* F, const double2* x, double nu,
                           int mode, SolveWork& w, cudaStream_t st, double* relres);
