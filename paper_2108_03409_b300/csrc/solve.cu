@@ -479,17 +479,19 @@ __global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t
   }
 }
 
-// y[t] = sum_m T[m][t] v[m] over the (zero-padded) 256 x 256 block, loads issued in
-// batches of 16 so that they overlap.
+// y[t] = sum_m T[m][t] v[m] over the (zero-padded) 256 x 256 block.  Loads go out in four
+// groups of 64 per thread (a group's loads are all issued before its products), so a step
+// waits for four L2 round trips instead of one per element.
 template <typename C, bool CONJ>
 __device__ __forceinline__ C block_matvec(const C* __restrict__ T, const C* v, int tid) {
   C s = mk<C>(0.0, 0.0);
-  for (int m0 = 0; m0 < SB; m0 += 16) {
-    C w[16];
+#pragma unroll 1
+  for (int m0 = 0; m0 < SB; m0 += 64) {
+    C w[64];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) w[j] = T[(int64_t)(m0 + j) * SB + tid];
+    for (int j = 0; j < 64; ++j) w[j] = __ldg(&T[(int64_t)(m0 + j) * SB + tid]);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < 64; ++j) {
       if (CONJ) cfmac(s, v[m0 + j], w[j]);     // s += v * conj(T)
       else cfma(s, w[j], v[m0 + j]);
     }
