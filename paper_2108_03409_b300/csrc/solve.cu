@@ -61,15 +61,18 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
   }
 }
 
-// Factor the diagonal block (rows/cols k0..k0+kw) and store its inverse.  256 threads;
-// thread (tx, ty) = (tid / 16, tid % 16) keeps entries (ty + 16p, tx + 16q), p, q < 4, of
-// the block in registers.  Step c of the right-looking factorisation: the half-warp that
-// owns column c takes the pivot from its diagonal owner by a shuffle, scales the column and
-// publishes it in shared memory (double-buffered), then one block barrier, then every
-// thread applies the rank-1 update to its own entries.  The inverse Linv (L Linv = I) is
-// built the same way row by row: row m of Linv = (row m of the running right-hand side) /
-// L_mm is published by its owners, then the rows below subtract L_rm times it.
+// Factor the 64 x 64 diagonal block (rows/cols k0..k0+kw) and store its inverse; one CTA
+// of 256 threads, the block in shared memory (identity padding beyond kw, masked on output).
+//  * Factorisation in four 16-column panels.  Within a panel thread (col, rg) keeps rows
+//    c0 + rg + 16i of panel column col in registers; step c: the half-warp owning column c
+//    takes the pivot from its diagonal lane by a shuffle, scales and publishes the column
+//    (double-buffered), one barrier, then every later column of the panel applies its
+//    rank-1 update.  After the panel the trailing triangle gets one rank-16 update.
+//  * Inverse: the four 16 x 16 diagonal blocks are inverted at once (forward substitution
+//    on the identity, one 64-thread group each, named barriers), then the off-diagonal
+//    16-blocks by levels, X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj (D_i = diagonal inverse).
 constexpr int POTRF_THREADS = 256;
+constexpr int PLD = NB + 1;
 
 template <typename C>
 __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A, int64_t P,
@@ -78,132 +81,171 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A,
                                                               unsigned* status) {
   typedef typename RealOf<C>::T R;
   extern __shared__ unsigned char psm[];
-  C* a = reinterpret_cast<C*>(psm);           // [NB][NB+1]: L after the factorisation
-  C* buf = a + NB * (NB + 1);                 // [2][NB]: published column / row
+  C* a = reinterpret_cast<C*>(psm);           // [64][PLD]: A -> L
+  C* li = a + NB * PLD;                       // [64][PLD]: Linv
+  C* tt = li + NB * PLD;                      // [64][PLD]: products of the inverse
+  C* cb = tt + NB * PLD;                      // [2][64]: published column / row
   const int tid = threadIdx.x;
-  const int tx = tid >> 4, ty = tid & 15, warp = tid >> 5;
-  C v[4][4];
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = ty + 16 * p, c = tx + 16 * q;
-      v[p][q] = (r < kw && c <= r) ? A[(k0 + r) * P + k0 + c] : mk<C>(0.0, 0.0);
+  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
+    const int r = e >> 6, c = e & 63;
+    C v = mk<C>(0.0, 0.0);
+    if (r < kw && c < kw) {
+      if (c <= r) v = A[(k0 + r) * P + k0 + c];
+    } else if (r == c) {
+      v = mk<C>(1.0, 0.0);
     }
+    a[r * PLD + c] = v;
+    li[r * PLD + c] = mk<C>(0.0, 0.0);
+  }
+  __syncthreads();
   bool bad = false;
+  const int col = tid >> 4, rg = tid & 15;
   int pb = 0;
+  for (int pp = 0; pp < 4; ++pp) {
+    const int c0 = 16 * pp;
+    C e[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+    for (int i = 0; i < 4; ++i) {
+      const int r = c0 + rg + 16 * i;
+      e[i] = (r < NB) ? a[r * PLD + c0 + col] : mk<C>(0.0, 0.0);
+    }
     for (int cl = 0; cl < 16; ++cl) {
-      const int c = 16 * q + cl;
-      if (c >= kw) break;
-      if (warp == (cl >> 1)) {                       // the warp holding column c
-        R d = __shfl_sync(0xffffffffu, v[q][q].x, ((cl & 1) << 4) | cl);
-        if (tx == cl) {
+      const int c = c0 + cl;
+      if ((tid >> 5) == (cl >> 1)) {                 // the warp holding column c's owners
+        R d = __shfl_sync(0xffffffffu, e[0].x, ((cl & 1) << 4) | cl);
+        if (col == cl) {
           if (!(d > (R)0) || !isfinite(d)) { bad = true; d = (R)1; }
-          const R lcc = sqrt(d), il = (R)1 / lcc;
+          const R l = sqrt(d), il = (R)1 / l;
 #pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const int r = ty + 16 * p;
-            if (r > c) {
-              v[p][q].x *= il;
-              v[p][q].y *= il;
-              buf[pb * NB + r] = v[p][q];
+          for (int i = 0; i < 4; ++i) {
+            const int r = c0 + rg + 16 * i;
+            if (r > c && r < NB) {
+              e[i].x *= il;
+              e[i].y *= il;
+              cb[pb * NB + r] = e[i];
             } else if (r == c) {
-              v[p][q] = mk<C>((double)lcc, 0.0);
+              e[i] = mk<C>((double)l, 0.0);
             }
           }
         }
       }
       __syncthreads();
+      if (col > cl) {
+        const C lc = cb[pb * NB + c0 + col];          // L[c0+col][c]
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int r = c0 + rg + 16 * i;
+          if (r >= c0 + col && r < NB) {
+            const C lr = cb[pb * NB + r];
+            e[i].x -= lr.x * lc.x + lr.y * lc.y;       // e -= L[r][c] conj(L[c0+col][c])
+            e[i].y -= lr.y * lc.x - lr.x * lc.y;
+          }
+        }
+      }
+      pb ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = c0 + rg + 16 * i;
+      if (r < NB) a[r * PLD + c0 + col] = e[i];
+    }
+    __syncthreads();
+    if (pp < 3) {
+      // trailing rank-16 update of rows/cols >= c0 + 16 (lower triangle)
+      const int t0 = c0 + 16;
+      const int ty = tid & 15, tx = tid >> 4;
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const int r = ty + 16 * p;
-        if (r > c && r < kw) {
-          const C lr = buf[pb * NB + r];
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            const int cc = tx + 16 * qq;
-            if (cc > c && cc <= r) {
-              const C lc = buf[pb * NB + cc];
-              v[p][qq].x -= lr.x * lc.x + lr.y * lc.y;       // v -= l_rc * conj(l_cc,c)
-              v[p][qq].y -= lr.y * lc.x - lr.x * lc.y;
-            }
-          }
-        }
-      }
-      pb ^= 1;
-    }
-  }
-  if (bad) flag_error(status, DEV_ERR_NUMERIC);
-  // L to shared memory (for the inverse) and back to A
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = ty + 16 * p, c = tx + 16 * q;
-      a[r * (NB + 1) + c] = (r < kw && c <= r) ? v[p][q] : mk<C>(0.0, 0.0);
-    }
-  __syncthreads();
-  for (int e = tid; e < kw * kw; e += POTRF_THREADS) {
-    const int r = e / kw, c = e % kw;
-    if (c <= r) A[(k0 + r) * P + k0 + c] = a[r * (NB + 1) + c];
-  }
-  // inverse: running right-hand side X (starts as I), same register ownership
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      v[p][q] = mk<C>((ty + 16 * p == tx + 16 * q) ? 1.0 : 0.0, 0.0);
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    for (int ml = 0; ml < 16; ++ml) {
-      const int m = 16 * p + ml;
-      if (m >= kw) break;
-      if (ty == ml) {                               // owners of row m publish Linv[m][.]
-        const R il = (R)1 / a[m * (NB + 1) + m].x;
+        if (r < t0) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int c = tx + 16 * q;
-          if (c <= m) {
-            v[p][q].x *= il;
-            v[p][q].y *= il;
-            buf[pb * NB + c] = v[p][q];
-          }
+          const int cc = tx + 16 * q;
+          if (cc < t0 || cc > r) continue;
+          C acc = mk<C>(0.0, 0.0);
+#pragma unroll
+          for (int m = 0; m < 16; ++m) cfmac(acc, a[r * PLD + c0 + m], a[cc * PLD + c0 + m]);
+          a[r * PLD + cc].x -= acc.x;
+          a[r * PLD + cc].y -= acc.y;
         }
       }
       __syncthreads();
+    }
+  }
+  if (bad) flag_error(status, DEV_ERR_NUMERIC);
+  // ---- inverse: 16 x 16 diagonal blocks, one 64-thread group each ----
+  {
+    const int g = tid >> 6, gt = tid & 63, rr = gt >> 2, cq = gt & 3;
+    const int b0 = 16 * g;
+    C x[4];
 #pragma unroll
-      for (int pp = 0; pp < 4; ++pp) {
-        const int r = ty + 16 * pp;
-        if (r > m && r < kw) {
-          const C lrm = a[r * (NB + 1) + m];
+    for (int j = 0; j < 4; ++j) x[j] = mk<C>((cq + 4 * j == rr) ? 1.0 : 0.0, 0.0);
+    C* rb = cb;                                    // group g uses entries [16g, 16g + 16)
+    int q2 = 0;
+    for (int m = 0; m < 16; ++m) {
+      if (rr == m) {
+        const R il = (R)1 / a[(b0 + m) * PLD + b0 + m].x;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int c = tx + 16 * q;
-            if (c <= m) {
-              const C xm = buf[pb * NB + c];
-              v[pp][q].x -= lrm.x * xm.x - lrm.y * xm.y;     // v -= L_rm * Linv[m][c]
-              v[pp][q].y -= lrm.x * xm.y + lrm.y * xm.x;
-            }
+        for (int j = 0; j < 4; ++j) {
+          const int c = cq + 4 * j;
+          if (c <= m) {
+            x[j].x *= il;
+            x[j].y *= il;
+            rb[q2 * NB + b0 + c] = x[j];
           }
         }
       }
-      pb ^= 1;
+      asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory");
+      if (rr > m) {
+        const C lrm = a[(b0 + rr) * PLD + b0 + m];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = cq + 4 * j;
+          if (c <= m) {
+            const C xm = rb[q2 * NB + b0 + c];
+            x[j].x -= lrm.x * xm.x - lrm.y * xm.y;      // x -= L[rr][m] Linv[m][c]
+            x[j].y -= lrm.x * xm.y + lrm.y * xm.x;
+          }
+        }
+      }
+      q2 ^= 1;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = cq + 4 * j;
+      if (c <= rr) li[(b0 + rr) * PLD + b0 + c] = x[j];
     }
   }
-  __syncthreads();                                  // a is reused as the staging buffer
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = ty + 16 * p, c = tx + 16 * q;
-      a[r * (NB + 1) + c] = (r < kw && c <= r) ? v[p][q] : mk<C>(0.0, 0.0);
-    }
   __syncthreads();
+  // ---- off-diagonal 16-blocks by levels d = i - j ----
+  for (int d = 1; d < 4; ++d) {
+    const int nb = 4 - d;                          // blocks (j + d, j), j < nb
+    // T_ij = sum_{k=j}^{i-1} L_ik X_kj, into tt at block (i, j)
+    for (int e = tid; e < nb * 256; e += POTRF_THREADS) {
+      const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
+      C acc = mk<C>(0.0, 0.0);
+      for (int k = j; k < i; ++k)
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+          cfma(acc, a[(16 * i + r) * PLD + 16 * k + m], li[(16 * k + m) * PLD + 16 * j + c]);
+      tt[(16 * i + r) * PLD + 16 * j + c] = acc;
+    }
+    __syncthreads();
+    // X_ij = -D_i T_ij
+    for (int e = tid; e < nb * 256; e += POTRF_THREADS) {
+      const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
+      C acc = mk<C>(0.0, 0.0);
+#pragma unroll
+      for (int m = 0; m < 16; ++m)
+        cfma(acc, li[(16 * i + r) * PLD + 16 * i + m], tt[(16 * i + m) * PLD + 16 * j + c]);
+      li[(16 * i + r) * PLD + 16 * j + c] = mk<C>(-(double)acc.x, -(double)acc.y);
+    }
+    __syncthreads();
+  }
   for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
-    const int r = e / NB, c = e % NB;
-    Dinv[e] = a[r * (NB + 1) + c];
+    const int r = e >> 6, c = e & 63;
+    if (r < kw && c <= r) A[(k0 + r) * P + k0 + c] = a[r * PLD + c];
+    Dinv[e] = (r < kw && c < kw && c <= r) ? li[r * PLD + c] : mk<C>(0.0, 0.0);
   }
 }
 
@@ -801,7 +843,7 @@ __global__ void __launch_bounds__(256) k_resid_df(const float4* __restrict__ S2,
 // host side
 // ---------------------------------------------------------------------------------------
 template <typename C>
-static constexpr size_t potrf_smem() { return (size_t)(NB * (NB + 1) + 2 * NB) * sizeof(C); }
+static constexpr size_t potrf_smem() { return (size_t)(3 * NB * (NB + 1) + 2 * NB) * sizeof(C); }
 
 template <typename C>
 static cudaError_t set_smem_attrs() {
