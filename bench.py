@@ -364,8 +364,11 @@ def run_ours(args):
         roof = {"bound": "alu", "peak": fp32_peak,
                 "peak_kind": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock"}
     achieved = alg_flops / (ms_gram / 1e3) / 1e12
+    # DRAM bytes (read + write) of one S-Gram launch, from the ncu capture summarised in
+    # profiles/gram_tc_heis8x8_full.md (this workload, this kernel)
+    traffic = 7.56e9 if (prec == vmc.PREC_BF16SPLIT and args.workload == DEFAULT_WORKLOAD) else None
     roofline = {"bound": roof["bound"], "achieved": achieved, "peak": roof["peak"],
-                "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": traffic,
                 "kernel": "gram_tc" if prec == vmc.PREC_BF16SPLIT else "gram_f32",
                 "peak_source": roof["peak_kind"], "algorithmic": alg_text,
                 "ms_per_launch": ms_gram}
