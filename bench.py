@@ -364,8 +364,8 @@ def run_ours(args):
         roof = {"bound": "alu", "peak": fp32_peak,
                 "peak_kind": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock"}
     achieved = alg_flops / (ms_gram / 1e3) / 1e12
-    # DRAM bytes (read + write) of one S-Gram launch, from the ncu capture summarised in
-    # profiles/gram_tc_heis8x8_full.md (this workload, this kernel)
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one S-Gram launch of
+    # this kernel on this workload, from an ncu capture of the same command
     traffic = 7.56e9 if (prec == vmc.PREC_BF16SPLIT and args.workload == DEFAULT_WORKLOAD) else None
     roofline = {"bound": roof["bound"], "achieved": achieved, "peak": roof["peak"],
                 "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": traffic,
