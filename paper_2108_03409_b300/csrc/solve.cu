@@ -74,13 +74,12 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
 constexpr int POTRF_THREADS = 256;
 constexpr int PLD = NB + 1;
 
+// (Global loads bypass L1 (ld.global.cg): inside the cooperative panel kernel the block
+// may have been written by other CTAs since this SM last cached it.)
 template <typename C>
-__global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A, int64_t P,
-                                                              int64_t k0, int kw,
-                                                              C* __restrict__ Dinv,
-                                                              unsigned* status) {
+__device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
+                           C* __restrict__ Dinv, unsigned* status, unsigned char* psm) {
   typedef typename RealOf<C>::T R;
-  extern __shared__ unsigned char psm[];
   C* a = reinterpret_cast<C*>(psm);           // [64][PLD]: A -> L
   C* li = a + NB * PLD;                       // [64][PLD]: Linv
   C* tt = li + NB * PLD;                      // [64][PLD]: products of the inverse
@@ -90,7 +89,7 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A,
     const int r = e >> 6, c = e & 63;
     C v = mk<C>(0.0, 0.0);
     if (r < kw && c < kw) {
-      if (c <= r) v = A[(k0 + r) * P + k0 + c];
+      if (c <= r) v = __ldcg(&A[(k0 + r) * P + k0 + c]);
     } else if (r == c) {
       v = mk<C>(1.0, 0.0);
     }
@@ -249,22 +248,29 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A,
   }
 }
 
+template <typename C>
+__global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A, int64_t P,
+                                                              int64_t k0, int kw,
+                                                              C* __restrict__ Dinv,
+                                                              unsigned* status) {
+  extern __shared__ unsigned char psm[];
+  potrf_body<C>(A, P, k0, kw, Dinv, status, psm);
+}
+
 // Panel: X = B L_kk^{-H}, X[r][c] = sum_m B[r][m] conj(Linv[c][m]) (Linv is zero above its
 // diagonal) for the rows below the diagonal block; 64 rows per block, written over the
 // panel of A.  Thread (ty, tx) accumulates the 4 x 4 outputs (ty + 16a, tx + 16b).
 template <typename C>
-__global__ void __launch_bounds__(256) k_trsm_inv(C* __restrict__ A, int64_t P, int64_t k0,
-                                                  int kw, const C* __restrict__ Dinv) {
-  extern __shared__ unsigned char tsm[];
+__device__ void trsm_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
+                          const C* __restrict__ Dinv, int64_t r0, unsigned char* tsm) {
   C* Bt = reinterpret_cast<C*>(tsm);           // [NB (m)][NB+1 (r)]
   C* Lt = Bt + NB * (NB + 1);                  // [NB (m)][NB+1 (c)]
-  const int64_t r0 = k0 + kw + (int64_t)blockIdx.x * NB;
   const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += 256) {
     const int rr = e / NB, m = e % NB;
     const int64_t row = r0 + rr;
-    Bt[m * (NB + 1) + rr] = (row < P && m < kw) ? A[row * P + k0 + m] : mk<C>(0.0, 0.0);
-    Lt[m * (NB + 1) + rr] = Dinv[e];             // e = c * NB + m with c = rr
+    Bt[m * (NB + 1) + rr] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : mk<C>(0.0, 0.0);
+    Lt[m * (NB + 1) + rr] = __ldcg(&Dinv[e]);    // e = c * NB + m with c = rr
   }
   __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
@@ -295,40 +301,39 @@ __global__ void __launch_bounds__(256) k_trsm_inv(C* __restrict__ A, int64_t P, 
   }
 }
 
-// Trailing update A[r][c] -= sum_m X[r][m] conj(X[c][m]) on lower 64x64 tiles, for columns
-// c < col_end (col_end >= P: the whole trailing matrix; otherwise a trapezoid of at most a
-// few tile columns, used inside a panel).
 template <typename C>
-__global__ void __launch_bounds__(256) k_herk(C* __restrict__ A, int64_t P, int64_t k0, int kw,
-                                              int64_t col_end) {
-  extern __shared__ unsigned char hsm[];
+__global__ void __launch_bounds__(256) k_trsm_inv(C* __restrict__ A, int64_t P, int64_t k0,
+                                                  int kw, const C* __restrict__ Dinv) {
+  extern __shared__ unsigned char tsm[];
+  trsm_body<C>(A, P, k0, kw, Dinv, k0 + kw + (int64_t)blockIdx.x * NB, tsm);
+}
+
+// Trailing update of one lower 64x64 tile (rows r0.., columns c0..):
+// A[r][c] -= sum_m X[r][m] conj(X[c][m]) for c <= r, X = the panel A[.][k0 .. k0+kw).
+// The tile's current values are fetched before the products so that their latency
+// overlaps the arithmetic.
+template <typename C>
+__device__ void herk_tile_body(C* __restrict__ A, int64_t P, int64_t k0, int kw, int64_t r0,
+                               int64_t c0, unsigned char* hsm) {
   C* Xr = reinterpret_cast<C*>(hsm);           // [NB (m)][NB+1 (row)]
   C* Xc = Xr + NB * (NB + 1);                  // [NB (m)][NB+1 (col)]
-  const int64_t k1 = k0 + kw;
-  const int64_t t = blockIdx.x;
-  int64_t tm, tn;
-  if (col_end >= P) {                        // lower-triangular tile enumeration
-    tm = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
-    while (tm * (tm + 1) / 2 > t) --tm;
-    tn = t - tm * (tm + 1) / 2;
-  } else {                                   // trapezoid, column by column
-    const int64_t nt = (P - k1 + NB - 1) / NB;
-    int64_t u = t;
-    tn = 0;
-    while (u >= nt - tn) { u -= nt - tn; ++tn; }
-    tm = tn + u;
-  }
-  const int64_t r0 = k1 + tm * NB, c0 = k1 + tn * NB;
   const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += 256) {
     const int rr = e / NB, m = e % NB;
     const int64_t row = r0 + rr, col = c0 + rr;
-    Xr[m * (NB + 1) + rr] = (row < P && m < kw) ? A[row * P + k0 + m] : mk<C>(0.0, 0.0);
-    Xc[m * (NB + 1) + rr] = (col < P && m < kw) ? A[col * P + k0 + m] : mk<C>(0.0, 0.0);
+    Xr[m * (NB + 1) + rr] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : mk<C>(0.0, 0.0);
+    Xc[m * (NB + 1) + rr] = (col < P && m < kw) ? __ldcg(&A[col * P + k0 + m]) : mk<C>(0.0, 0.0);
   }
-  __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
+  C cur[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int64_t row = r0 + ty + 16 * a, col = c0 + tx + 16 * b;
+      cur[a][b] = (row < P && col < P && col <= row) ? __ldcg(&A[row * P + col]) : mk<C>(0.0, 0.0);
+    }
+  __syncthreads();
   C acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -352,13 +357,42 @@ __global__ void __launch_bounds__(256) k_herk(C* __restrict__ A, int64_t P, int6
     for (int b = 0; b < 4; ++b) {
       const int64_t col = c0 + tx + 16 * b;
       if (row < P && col < P && col <= row) {
-        C v = A[row * P + col];
+        C v = cur[a][b];
         v.x -= acc[a][b].x;
         v.y -= acc[a][b].y;
         A[row * P + col] = v;
       }
     }
   }
+}
+
+// tile t of the trapezoid below k1 = k0 + kw restricted to nct tile columns, column by
+// column (column tn holds tiles tm = tn .. nt-1)
+__device__ __forceinline__ void trapezoid_tile(int64_t t, int64_t nt, int64_t* tm, int64_t* tn) {
+  int64_t u = t, c = 0;
+  while (u >= nt - c) { u -= nt - c; ++c; }
+  *tn = c;
+  *tm = c + u;
+}
+
+// Trailing update on lower 64x64 tiles for columns c < col_end (col_end >= P: the whole
+// trailing matrix; otherwise a trapezoid of a few tile columns, used inside a panel).
+template <typename C>
+__global__ void __launch_bounds__(256) k_herk(C* __restrict__ A, int64_t P, int64_t k0, int kw,
+                                              int64_t col_end) {
+  extern __shared__ unsigned char hsm[];
+  const int64_t k1 = k0 + kw;
+  const int64_t t = blockIdx.x;
+  int64_t tm, tn;
+  if (col_end >= P) {                        // lower-triangular tile enumeration
+    tm = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((tm + 1) * (tm + 2) / 2 <= t) ++tm;
+    while (tm * (tm + 1) / 2 > t) --tm;
+    tn = t - tm * (tm + 1) / 2;
+  } else {
+    trapezoid_tile(t, (P - k1 + NB - 1) / NB, &tm, &tn);
+  }
+  herk_tile_body<C>(A, P, k0, kw, k1 + tm * NB, k1 + tn * NB, hsm);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -407,6 +441,63 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, un
   }
   __syncthreads();
   return ok != 0;
+}
+
+// ---------------------------------------------------------------------------------------
+// Factorisation of one 256-wide panel (columns p0 .. pend, all rows below) in a single
+// cooperative launch.  Per 64-column block k: the panel rows below the block are solved
+// against its inverse (trsm, rows spread over the CTAs), grid barrier, then the rest of
+// the panel receives the block's update (herk tiles over the CTAs) while CTA 0 updates the
+// next diagonal tile first and factors it at once (look-ahead), grid barrier.  The panel's
+// first diagonal block is factored before the loop.
+// ---------------------------------------------------------------------------------------
+constexpr size_t PANEL_SMEM = (size_t)(3 * NB * (NB + 1) + 2 * NB) * sizeof(float2);
+
+__global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int64_t P,
+                                                    int64_t p0, int64_t pend,
+                                                    float2* __restrict__ Dinv,
+                                                    GridBarrier* bar, unsigned* status) {
+  extern __shared__ unsigned char csm[];
+  const unsigned G = gridDim.x, b = blockIdx.x;
+  if (b == 0) potrf_body<float2>(A, P, p0, (int)min((int64_t)NB, P - p0), Dinv + (p0 / NB) * NB * NB, status, csm);
+  if (!grid_sync(bar, G, status)) return;
+  for (int64_t k0 = p0; k0 < pend; k0 += NB) {
+    const int kw = (int)min((int64_t)NB, P - k0);
+    const int64_t k1 = k0 + kw, rest = P - k1;
+    if (rest <= 0) break;
+    const float2* Di = Dinv + (k0 / NB) * NB * NB;
+    const int64_t nrb = (rest + NB - 1) / NB;
+    for (int64_t rb = b; rb < nrb; rb += G) {
+      trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm);
+      __syncthreads();
+    }
+    if (!grid_sync(bar, G, status)) return;
+    if (k1 >= pend) break;                         // last block of the panel
+    const int64_t nt = nrb, nct = (pend - k1 + NB - 1) / NB;
+    const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
+    if (b == 0) {
+      // the next diagonal tile (tile 0), then its factorisation; CTA 0 takes no other tile
+      // unless it is alone
+      herk_tile_body<float2>(A, P, k0, kw, k1, k1, csm);
+      __syncthreads();
+      if (G == 1)
+        for (int64_t t = 1; t < tiles; ++t) {
+          int64_t tm, tn;
+          trapezoid_tile(t, nt, &tm, &tn);
+          herk_tile_body<float2>(A, P, k0, kw, k1 + tm * NB, k1 + tn * NB, csm);
+          __syncthreads();
+        }
+      potrf_body<float2>(A, P, k1, (int)min((int64_t)NB, P - k1), Dinv + (k1 / NB) * NB * NB, status, csm);
+    } else {
+      for (int64_t t = b; t < tiles; t += G - 1) {
+        int64_t tm, tn;
+        trapezoid_tile(t, nt, &tm, &tn);
+        herk_tile_body<float2>(A, P, k0, kw, k1 + tm * NB, k1 + tn * NB, csm);
+        __syncthreads();
+      }
+    }
+    if (!grid_sync(bar, G, status)) return;
+  }
 }
 
 // Steps of SB = 256 rows.  After the factorisation the inverse of every 256 x 256 diagonal
@@ -521,41 +612,85 @@ __global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t
   }
 }
 
-// y[t] = sum_m T[m][t] v[m] over the (zero-padded) 256 x 256 block.  Loads go out in four
-// groups of 64 per thread (a group's loads are all issued before its products), so a step
-// waits for four L2 round trips instead of one per element.
+// The step's diagonal-block product y_k = T v_k (T = the block's inverse, 256 x 256) is
+// split over the first MV CTAs: CTA j computes outputs [32j, 32j + 32) (warp w sums the
+// inputs [32w, 32w + 32), one output per lane, then a shared-memory reduction), stores them
+// to `out` (L2) and counts itself into the step's flag; every CTA then waits (bounded) for
+// the flag to reach MV and reads y_k from L2.  Without the split every CTA would re-read
+// the whole 512 KB block from L2 in every step.
+constexpr int MV = 8;
+
 template <typename C, bool CONJ>
-__device__ __forceinline__ C block_matvec(const C* __restrict__ T, const C* v, int tid) {
-  C s = mk<C>(0.0, 0.0);
-#pragma unroll 1
-  for (int m0 = 0; m0 < SB; m0 += 64) {
-    C w[64];
+__device__ bool split_block_matvec(const C* __restrict__ T, const C* __restrict__ v, int kw,
+                                   C* out, unsigned* flag, GridBarrier* bar, unsigned* status,
+                                   C* vv, C* red, C* yk) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ int ok;
+  if (blockIdx.x < MV) {
+    vv[tid] = (tid < kw) ? __ldcg(&v[tid]) : mk<C>(0.0, 0.0);
+    __syncthreads();
+    const int t = 32 * blockIdx.x + lane;
+    C w[32];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) w[j] = __ldg(&T[(int64_t)(m0 + j) * SB + tid]);
+    for (int j = 0; j < 32; ++j) w[j] = __ldg(&T[(int64_t)(32 * warp + j) * SB + t]);
+    C sacc = mk<C>(0.0, 0.0);
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
-      if (CONJ) cfmac(s, v[m0 + j], w[j]);     // s += v * conj(T)
-      else cfma(s, w[j], v[m0 + j]);
+    for (int j = 0; j < 32; ++j) {
+      if (CONJ) cfmac(sacc, vv[32 * warp + j], w[j]);   // s += v * conj(T)
+      else cfma(sacc, w[j], vv[32 * warp + j]);
     }
+    red[warp * 32 + lane] = sacc;
+    __syncthreads();
+    if (warp == 0) {
+      C tot = red[lane];
+#pragma unroll
+      for (int q = 1; q < 8; ++q) { tot.x += red[q * 32 + lane].x; tot.y += red[q * 32 + lane].y; }
+      if (t < kw) __stcg(&out[t], tot);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(flag, 1u);
   }
-  return s;
+  if (tid == 0) {
+    ok = 1;
+    volatile unsigned* vf = flag;
+    volatile unsigned* vab = &bar->abort;
+    const long long t0 = clock64();
+    unsigned it = 0;
+    while (*vf < (unsigned)MV) {
+      if (*vab) { ok = 0; break; }
+      if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
+        atomicExch(&bar->abort, 1u);
+        flag_error(status, DEV_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  if (!ok) return false;
+  yk[tid] = (tid < kw) ? __ldcg(&out[tid]) : mk<C>(0.0, 0.0);
+  __syncthreads();
+  return true;
 }
 
 template <typename C>
 __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
                                                   const C* __restrict__ Tf, int64_t P,
                                                   C* __restrict__ b, C* __restrict__ y,
-                                                  GridBarrier* bar, unsigned* status) {
+                                                  GridBarrier* bar, unsigned* flags,
+                                                  unsigned* status) {
   __shared__ C yk[SB];
-  __shared__ C bb[SB];
+  __shared__ C vv[SB];
+  __shared__ C red[SB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int64_t k0 = 0; k0 < P; k0 += SB) {
     const int kw = (int)min((int64_t)SB, P - k0);
-    bb[tid] = (tid < kw) ? __ldcg(&b[k0 + tid]) : mk<C>(0.0, 0.0);
-    __syncthreads();
-    yk[tid] = block_matvec<C, false>(Tf + (k0 / SB) * SB * SB, bb, tid);   // T[m][t] = Linv[t][m]
-    __syncthreads();
-    if (blockIdx.x == 0 && tid < kw) __stcg(&y[k0 + tid], yk[tid]);
+    // y_k = Linv_kk b_k (T[m][t] = Linv[t][m]), published in y itself
+    if (!split_block_matvec<C, false>(Tf + (k0 / SB) * SB * SB, b + k0, kw, y + k0,
+                                      flags + k0 / SB, bar, status, vv, red, yk))
+      return;
     // rows below: four rows per warp, all 32 loads of a lane issued before the products
     for (int64_t base = k0 + kw + ((int64_t)blockIdx.x * 8 + warp) * 4; base < P;
          base += (int64_t)gridDim.x * 32) {
@@ -594,20 +729,20 @@ template <typename C>
 __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
                                                   const C* __restrict__ Tb, int64_t P,
                                                   C* __restrict__ c, C* __restrict__ x,
-                                                  GridBarrier* bar, unsigned* status) {
+                                                  GridBarrier* bar, unsigned* flags,
+                                                  unsigned* status) {
   __shared__ C xk[SB];
-  __shared__ C cc[SB];
-  __shared__ C red[8][32];
+  __shared__ C vv[SB];
+  __shared__ C red[SB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t nsb = (P + SB - 1) / SB;
   for (int64_t sb = nsb - 1; sb >= 0; --sb) {
     const int64_t k0 = sb * SB;
     const int kw = (int)min((int64_t)SB, P - k0);
-    cc[tid] = (tid < kw) ? __ldcg(&c[k0 + tid]) : mk<C>(0.0, 0.0);
-    __syncthreads();
-    xk[tid] = block_matvec<C, true>(Tb + sb * SB * SB, cc, tid);   // Linv[m][t], conjugated
-    __syncthreads();
-    if (blockIdx.x == 0 && tid < kw) __stcg(&x[k0 + tid], xk[tid]);
+    // x_k = Linv_kk^H c_k (Linv[m][t], conjugated), published in x itself
+    if (!split_block_matvec<C, true>(Tb + sb * SB * SB, c + k0, kw, x + k0, flags + sb, bar,
+                                     status, vv, red, xk))
+      return;
     // rows above: chunks of 32 rows, warp w takes m in [32w, 32w+32), lanes take the rows
     for (int64_t ch = blockIdx.x; ch * 32 < k0; ch += gridDim.x) {
       const int64_t r = ch * 32 + lane;
@@ -622,12 +757,12 @@ __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
 #pragma unroll
         for (int j = 0; j < 32; ++j) cfmac(s, xk[warp * 32 + j], v[j]);
       }
-      red[warp][lane] = s;
+      red[warp * 32 + lane] = s;
       __syncthreads();
       if (warp == 0 && r < k0) {
-        C tot = red[0][lane];
+        C tot = red[lane];
 #pragma unroll
-        for (int w = 1; w < 8; ++w) { tot.x += red[w][lane].x; tot.y += red[w][lane].y; }
+        for (int w = 1; w < 8; ++w) { tot.x += red[w * 32 + lane].x; tot.y += red[w * 32 + lane].y; }
         C t = __ldcg(&c[r]);
         t.x -= tot.x;
         t.y -= tot.y;
@@ -895,29 +1030,27 @@ static constexpr int NBO = 256;
 
 static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, unsigned* status,
                              cudaStream_t st, int64_t* launches) {
-  VMC_TRY(set_smem_attrs<float2>());
-  const size_t s2 = 2 * NB * (NB + 1) * sizeof(float2);
+  VMC_TRY(set_smem_attrs<float2>());               // k_inv_sb and the refactorisation fallback
+  static int grid = 0;
+  if (grid == 0) {
+    VMC_TRY(cudaFuncSetAttribute(k_panel_coop, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PANEL_SMEM));
+    int dev = 0, sms = 0, per_sm = 0;
+    VMC_TRY(cudaGetDevice(&dev));
+    VMC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    VMC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_coop, 256, PANEL_SMEM));
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    grid = sms;                                     // one CTA per SM
+  }
+  GridBarrier* bar = reinterpret_cast<GridBarrier*>(w.bar);
   for (int64_t p0 = 0; p0 < P; p0 += NBO) {
     const int64_t pend = std::min<int64_t>(P, p0 + NBO);
-    for (int64_t k0 = p0; k0 < pend; k0 += NB) {
-      const int64_t kb = k0 / NB;
-      const int kw = (int)std::min<int64_t>(NB, P - k0);
-      k_potrf_diag<float2><<<1, POTRF_THREADS, potrf_smem<float2>(), st>>>(A, P, k0, kw, Dinv + kb * NB * NB, status);
-      ++*launches;
-      const int64_t rest = P - k0 - kw;
-      if (rest > 0) {
-        k_trsm_inv<float2><<<(unsigned)((rest + NB - 1) / NB), 256, s2, st>>>(A, P, k0, kw, Dinv + kb * NB * NB);
-        ++*launches;
-        if (k0 + kw < pend) {
-          const int64_t nt = (rest + NB - 1) / NB;
-          const int64_t nct = (pend - k0 - kw + NB - 1) / NB;
-          const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
-          k_herk<float2><<<(unsigned)tiles, 256, s2, st>>>(A, P, k0, kw, pend);
-          ++*launches;
-        }
-      }
-      VMC_TRY(cudaGetLastError());
-    }
+    VMC_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+    void* args[] = {(void*)&A, (void*)&P, (void*)&p0, (void*)&pend, (void*)&Dinv, (void*)&bar,
+                    (void*)&status};
+    VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3(grid), dim3(256), args,
+                                        PANEL_SMEM, st));
+    ++*launches;
     const int64_t n = P - pend;
     if (n > 0) {
       const int64_t rows_pad = (2 * n + 127) / 128 * 128;
@@ -976,16 +1109,21 @@ static cudaError_t chol_solve(const C* A, const C* Dinv_unused, int64_t P, C* b,
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     grid = sms * per_sm;
   }
+  // w.bar: the grid barrier (4 words) followed by one flag per 256-row step
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(w.bar);
-  VMC_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+  unsigned* flags = w.bar + 4;
+  const size_t bar_bytes = (4 + (size_t)((P + SB - 1) / SB)) * sizeof(unsigned);
+  VMC_TRY(cudaMemsetAsync(w.bar, 0, bar_bytes, st));
   {
-    void* args[] = {(void*)&A, (void*)&Dinv, (void*)&P, (void*)&b, (void*)&y, (void*)&bar, (void*)&status};
+    void* args[] = {(void*)&A, (void*)&Dinv, (void*)&P, (void*)&b, (void*)&y, (void*)&bar,
+                    (void*)&flags, (void*)&status};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_fwd_coop<C>, dim3(grid), dim3(256), args, 0, st));
   }
-  VMC_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+  VMC_TRY(cudaMemsetAsync(w.bar, 0, bar_bytes, st));
   {
     const C* Dinvb = inv_bwd<C>(w);
-    void* args[] = {(void*)&A, (void*)&Dinvb, (void*)&P, (void*)&y, (void*)&x, (void*)&bar, (void*)&status};
+    void* args[] = {(void*)&A, (void*)&Dinvb, (void*)&P, (void*)&y, (void*)&x, (void*)&bar,
+                    (void*)&flags, (void*)&status};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_bwd_coop<C>, dim3(grid), dim3(256), args, 0, st));
   }
   *launches += 2;
