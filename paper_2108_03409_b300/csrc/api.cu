@@ -355,7 +355,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &ctx->sw.r, P)) || (e = dalloc(ctx, &ctx->sw.c, P)) ||
         (e = dalloc(ctx, &ctx->sw.r32, P)) || (e = dalloc(ctx, &ctx->sw.y32, P)) ||
         (e = dalloc(ctx, &ctx->sw.c32, P)) || (e = dalloc(ctx, &ctx->sw.scal, 8)) ||
-        (e = dalloc(ctx, &ctx->sw.bar, 4 + (size_t)((P + 255) / 256))))
+        (e = dalloc(ctx, &ctx->sw.bar, 4 + 9 * (size_t)((P + 255) / 256))))
       return oom(e);
     ctx->sw.Xhi = ctx->Xhi;
     ctx->sw.Xlo = ctx->Xlo;

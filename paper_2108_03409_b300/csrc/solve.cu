@@ -612,116 +612,164 @@ __global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t
   }
 }
 
-// The step's diagonal-block product y_k = T v_k (T = the block's inverse, 256 x 256) is
-// split over the first MV CTAs: CTA j computes outputs [32j, 32j + 32) (warp w sums the
-// inputs [32w, 32w + 32), one output per lane, then a shared-memory reduction), stores them
-// to `out` (L2) and counts itself into the step's flag; every CTA then waits (bounded) for
-// the flag to reach MV and reads y_k from L2.  Without the split every CTA would re-read
-// the whole 512 KB block from L2 in every step.
-constexpr int MV = 8;
+// ---------------------------------------------------------------------------------------
+// Triangular solves as a dataflow over 32-row slices, one cooperative launch each.  The
+// right-hand side is cut into slices (j, s) = rows 256 j + 32 s .. + 31 of 256-row block j;
+// each slice has a fixed owner CTA (slice index mod grid) and a counter of the block
+// updates applied to it.  Forward step k (L y = b):
+//   * the owners of block k's eight slices wait until every slice of block k has received
+//     its k updates, then each computes its 32 entries of y_k = Linv_kk b_k (Linv_kk from
+//     the precomputed 256 x 256 inverses), stores them and counts into flag[k];
+//   * the owner of every slice of a later block waits for flag[k] = 8, subtracts
+//     L[rows][block k] y_k from its rows and increments the slice's counter.
+// The backward solve (L^H x = y) runs the same scheme from the last block to the first with
+// x_k = Linv_kk^H c_k and the rows above.  There is no grid-wide barrier: a step's
+// critical path is the eight-CTA product and one flag.  Every wait is bounded (iteration
+// and clock limits); an expired wait sets DEV_ERR_TIMEOUT and the abort word, which every
+// other wait also checks.  Right-hand sides go through L2 only (ld/st.global.cg).
+// ---------------------------------------------------------------------------------------
+constexpr int TS = 32;                          // slice rows
+constexpr int SPB = SB / TS;                    // slices per 256-row block
 
-template <typename C, bool CONJ>
-__device__ bool split_block_matvec(const C* __restrict__ T, const C* __restrict__ v, int kw,
-                                   C* out, unsigned* flag, GridBarrier* bar, unsigned* status,
-                                   C* vv, C* red, C* yk) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  __shared__ int ok;
-  if (blockIdx.x < MV) {
-    vv[tid] = (tid < kw) ? __ldcg(&v[tid]) : mk<C>(0.0, 0.0);
-    __syncthreads();
-    const int t = 32 * blockIdx.x + lane;
-    C w[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) w[j] = __ldg(&T[(int64_t)(32 * warp + j) * SB + t]);
-    C sacc = mk<C>(0.0, 0.0);
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (CONJ) cfmac(sacc, vv[32 * warp + j], w[j]);   // s += v * conj(T)
-      else cfma(sacc, w[j], vv[32 * warp + j]);
+__device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned target,
+                                              unsigned* abort_word, unsigned* status) {
+  volatile const unsigned* vw = word;
+  volatile unsigned* vab = abort_word;
+  const long long t0 = clock64();
+  unsigned it = 0;
+  while (*vw < target) {
+    if (*vab) return false;
+    if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
+      atomicExch(abort_word, 1u);
+      flag_error(status, DEV_ERR_TIMEOUT);
+      return false;
     }
-    red[warp * 32 + lane] = sacc;
-    __syncthreads();
-    if (warp == 0) {
-      C tot = red[lane];
-#pragma unroll
-      for (int q = 1; q < 8; ++q) { tot.x += red[q * 32 + lane].x; tot.y += red[q * 32 + lane].y; }
-      if (t < kw) __stcg(&out[t], tot);
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) atomicAdd(flag, 1u);
   }
-  if (tid == 0) {
-    ok = 1;
-    volatile unsigned* vf = flag;
-    volatile unsigned* vab = &bar->abort;
-    const long long t0 = clock64();
-    unsigned it = 0;
-    while (*vf < (unsigned)MV) {
-      if (*vab) { ok = 0; break; }
-      if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
-        atomicExch(&bar->abort, 1u);
-        flag_error(status, DEV_ERR_TIMEOUT);
-        ok = 0;
-        break;
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  if (!ok) return false;
-  yk[tid] = (tid < kw) ? __ldcg(&out[tid]) : mk<C>(0.0, 0.0);
-  __syncthreads();
   return true;
 }
 
+// CTA-wide: thread 0 waits, the verdict is shared; a fence makes the awaited data visible.
+// Barriers on both sides keep the shared verdict from being overwritten by the next call
+// before every thread has read it.
+__device__ __forceinline__ bool cta_wait(const unsigned* word, unsigned target,
+                                         unsigned* abort_word, unsigned* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = wait_at_least(word, target, abort_word, status) ? 1 : 0;
+    __threadfence();
+  }
+  __syncthreads();
+  const bool r = ok != 0;
+  __syncthreads();
+  return r;
+}
+
+// this CTA's 32 entries [32 s, 32 s + 32) of y = T^(op) v for the 256 x 256 block T
+// (T[m][t]; CONJ: conj(T)); v in shared memory; result to out (L2)
+template <typename C, bool CONJ>
+__device__ __forceinline__ void slice_matvec(const C* __restrict__ T, const C* vv, int s, int kw,
+                                             C* out, C* red) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = TS * s + lane;
+  C w[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) w[j] = __ldg(&T[(int64_t)(32 * warp + j) * SB + t]);
+  C acc = mk<C>(0.0, 0.0);
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (CONJ) cfmac(acc, vv[32 * warp + j], w[j]);
+    else cfma(acc, w[j], vv[32 * warp + j]);
+  }
+  red[warp * 32 + lane] = acc;
+  __syncthreads();
+  if (warp == 0) {
+    C tot = red[lane];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) { tot.x += red[q * 32 + lane].x; tot.y += red[q * 32 + lane].y; }
+    if (t < kw) __stcg(&out[t], tot);
+  }
+  __threadfence();
+  __syncthreads();
+}
+
+// bar: [0] abort word; flags[nsb]; counters[nsb * SPB]
 template <typename C>
 __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
                                                   const C* __restrict__ Tf, int64_t P,
                                                   C* __restrict__ b, C* __restrict__ y,
-                                                  GridBarrier* bar, unsigned* flags,
-                                                  unsigned* status) {
-  __shared__ C yk[SB];
+                                                  unsigned* sync, unsigned* status) {
   __shared__ C vv[SB];
   __shared__ C red[SB];
+  __shared__ C yk[SB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int64_t k0 = 0; k0 < P; k0 += SB) {
+  const int nsb = (int)((P + SB - 1) / SB);
+  const int G = gridDim.x, me = blockIdx.x;
+  unsigned* abort_word = sync;
+  unsigned* flags = sync + 1;
+  unsigned* cnt = flags + nsb;
+  const int nslices = nsb * SPB;
+  for (int k = 0; k < nsb; ++k) {
+    const int64_t k0 = (int64_t)k * SB;
     const int kw = (int)min((int64_t)SB, P - k0);
-    // y_k = Linv_kk b_k (T[m][t] = Linv[t][m]), published in y itself
-    if (!split_block_matvec<C, false>(Tf + (k0 / SB) * SB * SB, b + k0, kw, y + k0,
-                                      flags + k0 / SB, bar, status, vv, red, yk))
-      return;
-    // rows below: four rows per warp, all 32 loads of a lane issued before the products
-    for (int64_t base = k0 + kw + ((int64_t)blockIdx.x * 8 + warp) * 4; base < P;
-         base += (int64_t)gridDim.x * 32) {
+    // 1. owners of block k's slices: y_k
+    for (int s = 0; s < SPB; ++s) {
+      const int q = k * SPB + s;
+      if (q % G != me) continue;
+      for (int s2 = 0; s2 < SPB && k0 + (int64_t)s2 * TS < P; ++s2)
+        if (!cta_wait(&cnt[k * SPB + s2], (unsigned)k, abort_word, status)) return;
+      vv[tid] = (tid < kw) ? __ldcg(&b[k0 + tid]) : mk<C>(0.0, 0.0);
+      __syncthreads();
+      slice_matvec<C, false>(Tf + (int64_t)k * SB * SB, vv, s, kw, y + k0, red);
+      if (tid == 0) atomicAdd(&flags[k], 1u);
+    }
+    // 2. owners of later slices: b_rows -= L[rows][block k] y_k
+    bool have_y = false;
+    for (int q = me; q < nslices; q += G) {
+      const int j = q / SPB, s = q % SPB;
+      if (j <= k) continue;
+      const int64_t r0 = (int64_t)j * SB + (int64_t)s * TS;
+      if (r0 >= P) continue;
+      if (!have_y) {
+        if (!cta_wait(&flags[k], (unsigned)SPB, abort_word, status)) return;
+        yk[tid] = (tid < kw) ? __ldcg(&y[k0 + tid]) : mk<C>(0.0, 0.0);
+        __syncthreads();
+        have_y = true;
+      }
+      // four rows per warp, lanes over the 256 columns (8 each)
       C v[4][8];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int m = lane + 32 * i;
-          const int64_t row = base + rr;
+          const int64_t row = r0 + warp * 4 + rr;
           v[rr][i] = (row < P && m < kw) ? A[row * P + k0 + m] : mk<C>(0.0, 0.0);
         }
+      C cur = mk<C>(0.0, 0.0);
+      if (lane < 4 && r0 + warp * 4 + lane < P) cur = __ldcg(&b[r0 + warp * 4 + lane]);
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
-        C s = mk<C>(0.0, 0.0);
+        C sacc = mk<C>(0.0, 0.0);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) cfma(s, v[rr][i], yk[lane + 32 * i]);
+        for (int i = 0; i < 8; ++i) cfma(sacc, v[rr][i], yk[lane + 32 * i]);
         for (int o = 16; o > 0; o >>= 1) {
-          s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-          s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+          sacc.x += __shfl_xor_sync(0xffffffffu, sacc.x, o);
+          sacc.y += __shfl_xor_sync(0xffffffffu, sacc.y, o);
         }
-        const int64_t row = base + rr;
-        if (lane == 0 && row < P) {
-          C t = __ldcg(&b[row]);
-          t.x -= s.x;
-          t.y -= s.y;
+        const int64_t row = r0 + warp * 4 + rr;
+        if (lane == rr && row < P) {
+          C t = cur;
+          t.x -= sacc.x;
+          t.y -= sacc.y;
           __stcg(&b[row], t);
         }
       }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(&cnt[q], 1u);
     }
-    if (!grid_sync(bar, gridDim.x, status)) return;
+    if (have_y) __syncthreads();                   // yk is rewritten at the next step
   }
 }
 
@@ -729,48 +777,71 @@ template <typename C>
 __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
                                                   const C* __restrict__ Tb, int64_t P,
                                                   C* __restrict__ c, C* __restrict__ x,
-                                                  GridBarrier* bar, unsigned* flags,
-                                                  unsigned* status) {
-  __shared__ C xk[SB];
+                                                  unsigned* sync, unsigned* status) {
   __shared__ C vv[SB];
   __shared__ C red[SB];
+  __shared__ C xk[SB];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t nsb = (P + SB - 1) / SB;
-  for (int64_t sb = nsb - 1; sb >= 0; --sb) {
-    const int64_t k0 = sb * SB;
+  const int nsb = (int)((P + SB - 1) / SB);
+  const int G = gridDim.x, me = blockIdx.x;
+  unsigned* abort_word = sync;
+  unsigned* flags = sync + 1;
+  unsigned* cnt = flags + nsb;
+  const int nslices = nsb * SPB;
+  for (int k = nsb - 1; k >= 0; --k) {
+    const int64_t k0 = (int64_t)k * SB;
     const int kw = (int)min((int64_t)SB, P - k0);
-    // x_k = Linv_kk^H c_k (Linv[m][t], conjugated), published in x itself
-    if (!split_block_matvec<C, true>(Tb + sb * SB * SB, c + k0, kw, x + k0, flags + sb, bar,
-                                     status, vv, red, xk))
-      return;
-    // rows above: chunks of 32 rows, warp w takes m in [32w, 32w+32), lanes take the rows
-    for (int64_t ch = blockIdx.x; ch * 32 < k0; ch += gridDim.x) {
-      const int64_t r = ch * 32 + lane;
-      C s = mk<C>(0.0, 0.0);
-      if (r < k0) {
-        C v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int m = warp * 32 + j;
-          v[j] = (m < kw) ? A[(k0 + m) * P + r] : mk<C>(0.0, 0.0);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) cfmac(s, xk[warp * 32 + j], v[j]);
-      }
-      red[warp * 32 + lane] = s;
+    const unsigned need = (unsigned)(nsb - 1 - k);
+    for (int s = 0; s < SPB; ++s) {
+      const int q = k * SPB + s;
+      if (q % G != me) continue;
+      for (int s2 = 0; s2 < SPB && k0 + (int64_t)s2 * TS < P; ++s2)
+        if (!cta_wait(&cnt[k * SPB + s2], need, abort_word, status)) return;
+      vv[tid] = (tid < kw) ? __ldcg(&c[k0 + tid]) : mk<C>(0.0, 0.0);
       __syncthreads();
-      if (warp == 0 && r < k0) {
+      slice_matvec<C, true>(Tb + (int64_t)k * SB * SB, vv, s, kw, x + k0, red);
+      if (tid == 0) atomicAdd(&flags[k], 1u);
+    }
+    // owners of earlier slices: c_rows -= L[block k][rows]^H x_k; lanes over the 32 rows,
+    // warp w over the columns [32 w, 32 w + 32) of block k, shared-memory reduction
+    bool have_x = false;
+    for (int q = me; q < nslices; q += G) {
+      const int j = q / SPB, s = q % SPB;
+      if (j >= k) continue;
+      const int64_t r0 = (int64_t)j * SB + (int64_t)s * TS;
+      if (!have_x) {
+        if (!cta_wait(&flags[k], (unsigned)SPB, abort_word, status)) return;
+        xk[tid] = (tid < kw) ? __ldcg(&x[k0 + tid]) : mk<C>(0.0, 0.0);
+        __syncthreads();
+        have_x = true;
+      }
+      const int64_t r = r0 + lane;                 // r < k0 <= P
+      C v[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) {
+        const int m = warp * 32 + jj;
+        v[jj] = (m < kw) ? A[(k0 + m) * P + r] : mk<C>(0.0, 0.0);
+      }
+      const C cur = (warp == 0) ? __ldcg(&c[r]) : mk<C>(0.0, 0.0);
+      C sacc = mk<C>(0.0, 0.0);
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) cfmac(sacc, xk[warp * 32 + jj], v[jj]);
+      red[warp * 32 + lane] = sacc;
+      __syncthreads();
+      if (warp == 0) {
         C tot = red[lane];
 #pragma unroll
         for (int w = 1; w < 8; ++w) { tot.x += red[w * 32 + lane].x; tot.y += red[w * 32 + lane].y; }
-        C t = __ldcg(&c[r]);
+        C t = cur;
         t.x -= tot.x;
         t.y -= tot.y;
         __stcg(&c[r], t);
       }
+      __threadfence();
       __syncthreads();
+      if (tid == 0) atomicAdd(&cnt[q], 1u);
     }
-    if (!grid_sync(bar, gridDim.x, status)) return;
+    if (have_x) __syncthreads();
   }
 }
 
@@ -1109,21 +1180,21 @@ static cudaError_t chol_solve(const C* A, const C* Dinv_unused, int64_t P, C* b,
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     grid = sms * per_sm;
   }
-  // w.bar: the grid barrier (4 words) followed by one flag per 256-row step
-  GridBarrier* bar = reinterpret_cast<GridBarrier*>(w.bar);
-  unsigned* flags = w.bar + 4;
-  const size_t bar_bytes = (4 + (size_t)((P + SB - 1) / SB)) * sizeof(unsigned);
-  VMC_TRY(cudaMemsetAsync(w.bar, 0, bar_bytes, st));
+  // w.bar: abort word, one flag per 256-row block, one counter per 32-row slice
+  unsigned* sync = w.bar;
+  const int64_t nsb = (P + SB - 1) / SB;
+  const size_t sync_bytes = (1 + nsb + nsb * SPB) * sizeof(unsigned);
+  VMC_TRY(cudaMemsetAsync(sync, 0, sync_bytes, st));
   {
-    void* args[] = {(void*)&A, (void*)&Dinv, (void*)&P, (void*)&b, (void*)&y, (void*)&bar,
-                    (void*)&flags, (void*)&status};
+    void* args[] = {(void*)&A, (void*)&Dinv, (void*)&P, (void*)&b, (void*)&y, (void*)&sync,
+                    (void*)&status};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_fwd_coop<C>, dim3(grid), dim3(256), args, 0, st));
   }
-  VMC_TRY(cudaMemsetAsync(w.bar, 0, bar_bytes, st));
+  VMC_TRY(cudaMemsetAsync(sync, 0, sync_bytes, st));
   {
     const C* Dinvb = inv_bwd<C>(w);
-    void* args[] = {(void*)&A, (void*)&Dinvb, (void*)&P, (void*)&y, (void*)&x, (void*)&bar,
-                    (void*)&flags, (void*)&status};
+    void* args[] = {(void*)&A, (void*)&Dinvb, (void*)&P, (void*)&y, (void*)&x, (void*)&sync,
+                    (void*)&status};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_bwd_coop<C>, dim3(grid), dim3(256), args, 0, st));
   }
   *launches += 2;
