@@ -25,6 +25,48 @@ __global__ void k_param_prep(const double2* __restrict__ p, int N, int M, float2
   }
 }
 
+// Move tables (see RbmDev): D from the FP64 W, complex cosh, sinh and tanh in FP64, rounded
+// once to FP32.
+__global__ void k_move_tables(const double2* __restrict__ p, int N, int M, int model, int Lx,
+                              int Ly, float4* __restrict__ mcs, float2* __restrict__ mth) {
+  const int moves = model == 1 ? num_bonds(Lx, Ly) : N;
+  const int64_t total = (int64_t)moves * M;
+  const double2* W = p + N + M;                  // W[k][i] at k * N + i
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e / M), k = (int)(e % M);
+    double dx, dy;
+    if (model == 1) {
+      int i, j;
+      bond_ends(Lx, Ly, q, &i, &j);
+      const double2 wi = W[(int64_t)k * N + i], wj = W[(int64_t)k * N + j];
+      dx = 2.0 * (wi.x - wj.x);
+      dy = 2.0 * (wi.y - wj.y);
+    } else {
+      const double2 w = W[(int64_t)k * N + q];
+      dx = 2.0 * w.x;
+      dy = 2.0 * w.y;
+    }
+    double sy, cy;
+    sincos(dy, &sy, &cy);
+    const double chx = cosh(dx), shx = sinh(dx);
+    const double cr = chx * cy, ci = shx * sy;   // cosh(dx + i dy)
+    const double sr = shx * cy, si = chx * sy;   // sinh(dx + i dy)
+    const double den = cr * cr + ci * ci;
+    mcs[e] = make_float4((float)cr, (float)ci, (float)sr, (float)si);
+    mth[e] = make_float2((float)((sr * cr + si * ci) / den), (float)((si * cr - sr * ci) / den));
+  }
+}
+
+cudaError_t launch_move_tables(const double2* p, int N, int M, int model, int Lx, int Ly,
+                               float4* mcs, float2* mth, cudaStream_t st) {
+  const int moves = model == 1 ? num_bonds(Lx, Ly) : N;
+  const int64_t total = (int64_t)moves * M;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
+  k_move_tables<<<blocks, 256, 0, st>>>(p, N, M, model, Lx, Ly, mcs, mth);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------
 // batch kernels: one warp per configuration
 // ---------------------------------------------------------------------------------------

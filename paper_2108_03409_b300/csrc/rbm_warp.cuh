@@ -56,32 +56,36 @@ __device__ __forceinline__ float2 warp_logpsi(const RbmDev& R, const int8_t* s, 
   return make_float2(warp_sum(re), warp_sum(im));
 }
 
-// sum over the warp's hidden slots of log[cosh(theta_k - d_k) / cosh(theta_k)], with
-// d_k = 2 s_i W_ki (+ 2 s_j W_kj for an exchange), as (log modulus, phase).  Each lane
-// multiplies its factors and takes one log at the end; the running product is folded into
-// the logs early only if it leaves [1e-15, 1e15] (checked every four factors).
-template <int MPL, bool PAIR>
+// A move q (a site flip, or a bond exchange of anti-parallel spins) with s_i the spin of
+// its first site shifts theta_k by -s_i D_qk (D from the move tables):
+//   cosh(theta - s_i D) / cosh(theta) = cosh D - s_i t sinh D          (t = tanh theta)
+//   tanh(theta - s_i D) = (t - s_i tanh D) / (1 - s_i t tanh D)
+__device__ __forceinline__ float2 move_ratio(float2 t, float4 cs, float si) {
+  const float2 ts = cmul(t, make_float2(cs.z, cs.w));
+  return make_float2(fmaf(-si, ts.x, cs.x), fmaf(-si, ts.y, cs.y));
+}
+
+__device__ __forceinline__ float2 move_tanh_shift(float2 t, float2 th, float si) {
+  const float2 td = make_float2(si * th.x, si * th.y);
+  const float2 num = make_float2(t.x - td.x, t.y - td.y);
+  const float2 tt = cmul(t, td);
+  return cdiv(num, make_float2(1.0f - tt.x, -tt.y));
+}
+
+// sum over the warp's hidden slots of log[cosh(theta_k - s_i D_qk) / cosh(theta_k)] for
+// move q, as (log modulus, phase).  Each lane multiplies its factors and takes one log at
+// the end; the running product is folded into the logs early only if it leaves
+// [1e-15, 1e15] (checked every four factors).
+template <int MPL>
 __device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
-                                                 const float2 (&t)[MPL], int i, float si,
-                                                 int j) {
+                                                 const float2 (&t)[MPL], int q, float si) {
   float lr = 0.f, li = 0.f;
   float2 prod = make_float2(1.f, 0.f);
+  const float4* row = R.mcs + (int64_t)q * R.M;
 #pragma unroll
   for (int k = 0; k < MPL; ++k) {
     int hj = lane + 32 * k;
-    if (hj < R.M) {
-      float2 wi = R.Wt[(int64_t)i * R.M + hj];
-      float dr, di;
-      if (PAIR) {
-        float2 wj = R.Wt[(int64_t)j * R.M + hj];
-        dr = 2.f * si * (wi.x - wj.x);
-        di = 2.f * si * (wi.y - wj.y);
-      } else {
-        dr = 2.f * si * wi.x;
-        di = 2.f * si * wi.y;
-      }
-      prod = cmul(prod, cosh_ratio(t[k], dr, di));
-    }
+    if (hj < R.M) prod = cmul(prod, move_ratio(t[k], row[hj], si));
     if ((k & 3) == 3 && k != MPL - 1) {
       const float m2 = fmaf(prod.x, prod.x, prod.y * prod.y);
       if (m2 > 1e30f || m2 < 1e-30f) {
@@ -113,7 +117,7 @@ __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, i
     e = make_float2(-L.J * zz, 0.f);
     for (int i = 0; i < R.N; ++i) {           // -h X_i: flip site i
       float si = (float)s[i];
-      float2 lg = warp_log_ratio<MPL, false>(R, lane, t, i, si, 0);
+      float2 lg = warp_log_ratio<MPL>(R, lane, t, i, si);
       float2 ai = R.a[i];
       float lx = lg.x - 2.f * si * ai.x, ly = lg.y - 2.f * si * ai.y;
       float mag = expf(lx), sn, cs;
@@ -128,7 +132,7 @@ __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, i
       bond_ends(L.Lx, L.Ly, b, &i, &j);
       if (s[i] == s[j]) continue;
       float si = (float)s[i];
-      float2 lg = warp_log_ratio<MPL, true>(R, lane, t, i, si, j);
+      float2 lg = warp_log_ratio<MPL>(R, lane, t, b, si);
       float2 ai = R.a[i], aj = R.a[j];
       float lx = lg.x - 2.f * si * (ai.x - aj.x), ly = lg.y - 2.f * si * (ai.y - aj.y);
       float mag = expf(lx), sn, cs;
@@ -222,22 +226,13 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
         }
         const float si = (float)s[i];
         const float two_re_da = HEIS ? -4.f * si * (R.a[i].x - R.a[j].x) : -4.f * si * R.a[i].x;
+        const int64_t qrow = (int64_t)idx * M;     // move index: the bond, or the site
         float lsum = 0.f, prod = 1.f;
 #pragma unroll
         for (int k = 0; k < MPL; ++k) {
           const int hj = lane + 32 * k;
           if (hj < M) {
-            const float2 wi = R.Wt[(int64_t)i * M + hj];
-            float dr, di;
-            if (HEIS) {
-              const float2 wj = R.Wt[(int64_t)j * M + hj];
-              dr = 2.f * si * (wi.x - wj.x);
-              di = 2.f * si * (wi.y - wj.y);
-            } else {
-              dr = 2.f * si * wi.x;
-              di = 2.f * si * wi.y;
-            }
-            const float2 r = cosh_ratio(t[k], dr, di);
+            const float2 r = move_ratio(t[k], R.mcs[qrow + hj], si);
             prod *= fmaf(r.x, r.x, r.y * r.y);
           }
           if ((k & 7) == 7 || k == MPL - 1) {
@@ -250,19 +245,7 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
 #pragma unroll
           for (int k = 0; k < MPL; ++k) {
             const int hj = lane + 32 * k;
-            if (hj < M) {
-              const float2 wi = R.Wt[(int64_t)i * M + hj];
-              float dr, di;
-              if (HEIS) {
-                const float2 wj = R.Wt[(int64_t)j * M + hj];
-                dr = 2.f * si * (wi.x - wj.x);
-                di = 2.f * si * (wi.y - wj.y);
-              } else {
-                dr = 2.f * si * wi.x;
-                di = 2.f * si * wi.y;
-              }
-              t[k] = tanh_shift(t[k], dr, di);
-            }
+            if (hj < M) t[k] = move_tanh_shift(t[k], R.mth[qrow + hj], si);
           }
           __syncwarp();
           if (lane == 0) {

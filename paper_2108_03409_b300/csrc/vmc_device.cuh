@@ -101,51 +101,10 @@ __device__ __forceinline__ float2 tanh_c(float x, float y) {
   return make_float2(sh / d, s / d);
 }
 
-// cosh and sinh of a complex argument d = x + iy:
-//   cosh d = cosh x cos y + i sinh x sin y,   sinh d = sinh x cos y + i cosh x sin y.
-// For |x|, |y| < 1/2 the four real functions come from their Taylor series (through the
-// x^8 / x^9 terms: truncation below 3e-10), which keeps full FP32 relative accuracy for the
-// small arguments the RBM updates produce; larger arguments use the accurate libm calls.
-__device__ __forceinline__ void cosh_sinh_c(float x, float y, float2* ch, float2* sh) {
-  float chx, shx, cy, sy;
-  if (fabsf(x) < 0.5f && fabsf(y) < 0.5f) {
-    const float x2 = x * x, y2 = y * y;
-    chx = 1.0f + x2 * fmaf(x2, fmaf(x2, fmaf(x2, 2.4801587e-05f, 1.3888889e-03f), 4.1666668e-02f), 0.5f);
-    shx = fmaf(x * x2, fmaf(x2, fmaf(x2, fmaf(x2, 2.7557319e-06f, 1.9841270e-04f), 8.3333333e-03f), 1.6666667e-01f), x);
-    cy = 1.0f - y2 * fmaf(y2, fmaf(y2, fmaf(y2, -2.4801587e-05f, 1.3888889e-03f), -4.1666668e-02f), 0.5f);
-    sy = fmaf(y * y2, fmaf(y2, fmaf(y2, fmaf(y2, 2.7557319e-06f, -1.9841270e-04f), 8.3333333e-03f), -1.6666667e-01f), y);
-  } else {
-    chx = coshf(x);
-    shx = sinhf(x);
-    sincosf(y, &sy, &cy);
-  }
-  *ch = make_float2(chx * cy, shx * sy);
-  *sh = make_float2(shx * cy, chx * sy);
-}
-
-// cosh(theta - d) / cosh(theta) = cosh d - tanh(theta) sinh d   (t = tanh theta cached);
-// finite for every theta, including |Re theta| large where t -> +-1.
-__device__ __forceinline__ float2 cosh_ratio(float2 t, float dr, float di) {
-  float2 ch, sh;
-  cosh_sinh_c(dr, di, &ch, &sh);
-  float2 ts = cmul(t, sh);
-  return make_float2(ch.x - ts.x, ch.y - ts.y);
-}
-
 // complex division a / b
 __device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
   const float inv = 1.0f / fmaf(b.x, b.x, b.y * b.y);
   return make_float2(fmaf(a.x, b.x, a.y * b.y) * inv, fmaf(a.y, b.x, -a.x * b.y) * inv);
-}
-
-// tanh(theta - d) from t = tanh theta: (t - tanh d) / (1 - t tanh d)
-__device__ __forceinline__ float2 tanh_shift(float2 t, float dr, float di) {
-  float2 ch, sh;
-  cosh_sinh_c(dr, di, &ch, &sh);
-  const float2 td = cdiv(sh, ch);
-  const float2 num = make_float2(t.x - td.x, t.y - td.y);
-  const float2 tt = cmul(t, td);
-  return cdiv(num, make_float2(1.0f - tt.x, -tt.y));
 }
 
 // Lower-triangular tile t of an nt x nt tile grid (bn <= bm), rasterised in groups of
