@@ -60,6 +60,7 @@ struct vmc_ctx {
   double* estats = nullptr;       // [4]
   double* partial = nullptr;      // moments scratch
   double2* meanO = nullptr;       // [Pmax]
+  float4* mean2 = nullptr;        // [Pmax] <O> as FP32 hi/lo pairs
   double2* F = nullptr;           // [Pmax]
   double2* x = nullptr;           // [Pmax]
   int64_t rows_pad = 0, ld = 0;
@@ -179,9 +180,9 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
   if (rows_pad > ctx->rows_pad || ld > ctx->ld) return fail(ctx, VMC_ERR_ARG, "S workspace too small");
   const double inv_n = 1.0 / (double)n;
   if (precision == VMC_PREC_BF16SPLIT) {
-    CK(launch_build_x(spins, ctx->s_T, ctx->meanO, n, L.N, L.M, rows_pad, ld, nullptr, ctx->Xhi,
+    CK(launch_build_x(spins, ctx->s_T, ctx->meanO, ctx->mean2, n, L.N, L.M, rows_pad, ld, nullptr, ctx->Xhi,
                       ctx->Xlo, ctx->st), "build_x");
-    ++ctx->launches;
+    ctx->launches += 2;
     cudaEventRecord(ctx->ev[6], ctx->st);
     cudaError_t e = launch_gram_tc(ctx->Xhi, ctx->Xlo, rows_pad, ld, L.P, inv_n, S_out, mirror,
                                    fused ? ctx->sw.S2 : nullptr, fused ? ctx->sw.A32 : nullptr,
@@ -191,9 +192,9 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
     CK(e, "gram_tc");
     ++ctx->launches;
   } else {
-    CK(launch_build_x(spins, ctx->s_T, ctx->meanO, n, L.N, L.M, rows_pad, ld, ctx->X32, nullptr,
+    CK(launch_build_x(spins, ctx->s_T, ctx->meanO, ctx->mean2, n, L.N, L.M, rows_pad, ld, ctx->X32, nullptr,
                       nullptr, ctx->st), "build_x");
-    ++ctx->launches;
+    ctx->launches += 2;
     cudaEventRecord(ctx->ev[6], ctx->st);
     CK(launch_gram_f32(ctx->X32, rows_pad, ld, L.P, inv_n, S_out, mirror, ctx->st), "gram_f32");
     cudaEventRecord(ctx->ev[7], ctx->st);
@@ -335,7 +336,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
       (e = dalloc(ctx, &ctx->s_T, (size_t)Ns * ctx->Mmax)) || (e = dalloc(ctx, &ctx->s_E, Ns)) ||
       (e = dalloc(ctx, &ctx->estats, 8)) ||
       (e = dalloc(ctx, &ctx->partial, (size_t)moments_partial_doubles(Ns, ctx->Nmax, ctx->Mmax))) ||
-      (e = dalloc(ctx, &ctx->meanO, ctx->Pmax)) || (e = dalloc(ctx, &ctx->F, ctx->Pmax)) ||
+      (e = dalloc(ctx, &ctx->meanO, ctx->Pmax)) || (e = dalloc(ctx, &ctx->mean2, ctx->Pmax)) || (e = dalloc(ctx, &ctx->F, ctx->Pmax)) ||
       (e = dalloc(ctx, &ctx->x, ctx->Pmax)) || (e = dalloc(ctx, &ctx->status, 1)) ||
       (e = dalloc(ctx, &ctx->n_accept, 1)))
     return oom(e);

@@ -1,6 +1,8 @@
 // sr.cu -- reductions of the SR/TDVP equation (Eq. qfm, Eq. force_vector):
 // energy statistics, <O>, F, the centred log-derivative matrix and the FP32 Gram that
 // gives S = <O^H O> - <O^H><O>.
+#include <cstring>
+
 #include "vmc_device.cuh"
 #include "vmc_internal.h"
 
@@ -183,55 +185,112 @@ cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E
 }
 
 // ---------------------------------------------------------------------------------------
-// X = centred log-derivatives, transposed, real/imag rows interleaved, zero padded
+// X = centred log-derivatives, transposed, real/imag rows interleaved, zero padded.
+// One warp per (32 samples, hidden unit j); lane = sample.  The warp reads t_qj once and
+// its sample's spins once (16-byte loads) and writes the rows of parameter b_j, of
+// W_j1 .. W_jN and, for j < N, of a_j, 32 consecutive samples per store.  The mean is
+// subtracted in FP32 as a hi/lo pair (o - m_hi - m_lo), which keeps the FP64 mean's
+// accuracy in the centred value.
 // ---------------------------------------------------------------------------------------
+struct XOut {
+  float* X32;
+  __nv_bfloat16* Xhi;
+  __nv_bfloat16* Xlo;
+  int64_t ld;
+};
+
+__device__ __forceinline__ void put_x(const XOut& o, int64_t k, int64_t q, float vr, float vi) {
+  const int64_t r0 = (2 * k) * o.ld + q, r1 = r0 + o.ld;
+  if (o.X32) {
+    o.X32[r0] = vr;
+    o.X32[r1] = vi;
+  }
+  if (o.Xhi) {
+    const __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
+    o.Xhi[r0] = hr;
+    o.Xhi[r1] = hi;
+    o.Xlo[r0] = __float2bfloat16_rn(vr - __bfloat162float(hr));
+    o.Xlo[r1] = __float2bfloat16_rn(vi - __bfloat162float(hi));
+  }
+}
+
+// m = {Re hi, Im hi, Re lo, Im lo} of the FP64 mean
+__device__ __forceinline__ float2 centre(float ox, float oy, float4 m) {
+  return make_float2((ox - m.x) - m.z, (oy - m.y) - m.w);
+}
+
+__global__ void k_split_mean(const double2* __restrict__ meanO, int64_t P, float4* __restrict__ m2) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 m = meanO[k];
+    const float hx = (float)m.x, hy = (float)m.y;
+    m2[k] = make_float4(hx, hy, (float)(m.x - (double)hx), (float)(m.y - (double)hy));
+  }
+}
+
+constexpr int BX_NMAX = 1024;
+
 __global__ void __launch_bounds__(256) k_build_x(const int8_t* __restrict__ spins,
                                                  const float2* __restrict__ T,
-                                                 const double2* __restrict__ meanO, int64_t n,
-                                                 int N, int M, int64_t rows_pad, int64_t ld,
-                                                 float* __restrict__ X32,
-                                                 __nv_bfloat16* __restrict__ Xhi,
-                                                 __nv_bfloat16* __restrict__ Xlo) {
-  const int64_t P = (int64_t)N + M + (int64_t)N * M;
-  const int64_t q = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  const int64_t k = (int64_t)blockIdx.y * 8 + threadIdx.y;
-  if (q >= ld || 2 * k >= rows_pad) return;
-  float vr = 0.f, vi = 0.f;
-  if (k < P && q < n) {
-    float2 o;
-    if (k < N) o = make_float2((float)spins[q * N + k], 0.f);
-    else if (k < N + M) o = T[q * M + (k - N)];
-    else {
-      const int64_t r = k - N - M;
-      const int j = (int)(r / N), i = (int)(r % N);
-      const float si = (float)spins[q * N + i];
-      const float2 t = T[q * M + j];
-      o = make_float2(si * t.x, si * t.y);
+                                                 const float4* __restrict__ meanO, int64_t n,
+                                                 int N, int M, int64_t rows_pad, bool vec16,
+                                                 XOut o) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
+  const int64_t q = (int64_t)blockIdx.x * 32 + lane;
+  if (j >= M || q >= o.ld) return;
+  const bool live = q < n;
+  const float2 t = live ? T[q * M + j] : make_float2(0.f, 0.f);
+  // b_j
+  {
+    const int64_t k = N + j;
+    float2 v = live ? centre(t.x, t.y, meanO[k]) : make_float2(0.f, 0.f);
+    put_x(o, k, q, v.x, v.y);
+  }
+  // a_j (the first N warps of the j range)
+  if (j < N) {
+    const float sj = live ? (float)spins[q * N + j] : 0.f;
+    float2 v = live ? centre(sj, 0.f, meanO[j]) : make_float2(0.f, 0.f);
+    put_x(o, j, q, v.x, v.y);
+  }
+  // W_ji, i = 0 .. N-1 (rows N + M + j N + i)
+  const int64_t kb = (int64_t)N + M + (int64_t)j * N;
+  const int8_t* sq = spins + q * N;
+  for (int i0 = 0; i0 < N; i0 += 16) {
+    int8_t sv[16];
+    if (live && vec16) {
+      const int4 w = *reinterpret_cast<const int4*>(sq + i0);
+      memcpy(sv, &w, 16);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) sv[u] = (live && i0 + u < N) ? sq[i0 + u] : (int8_t)0;
     }
-    const double2 m = meanO[k];
-    vr = (float)((double)o.x - m.x);
-    vi = (float)((double)o.y - m.y);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int i = i0 + u;
+      if (i >= N) break;
+      const float si = (float)sv[u];
+      float2 v = live ? centre(si * t.x, si * t.y, meanO[kb + i]) : make_float2(0.f, 0.f);
+      put_x(o, kb + i, q, v.x, v.y);
+    }
   }
-  const int64_t r0 = (2 * k) * ld + q, r1 = (2 * k + 1) * ld + q;
-  if (X32) {
-    X32[r0] = vr;
-    X32[r1] = vi;
-  }
-  if (Xhi) {
-    __nv_bfloat16 hr = __float2bfloat16_rn(vr), hi = __float2bfloat16_rn(vi);
-    Xhi[r0] = hr;
-    Xhi[r1] = hi;
-    Xlo[r0] = __float2bfloat16_rn(vr - __bfloat162float(hr));
-    Xlo[r1] = __float2bfloat16_rn(vi - __bfloat162float(hi));
+  // zero padding rows 2P .. rows_pad (written by the j = 0 warps)
+  if (j == 0) {
+    const int64_t P = (int64_t)N + M + (int64_t)N * M;
+    for (int64_t k = P; 2 * k < rows_pad; ++k) put_x(o, k, q, 0.f, 0.f);
   }
 }
 
 cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* meanO,
-                           int64_t n, int N, int M, int64_t rows_pad, int64_t ld, float* X32,
-                           __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, cudaStream_t st) {
-  dim3 block(32, 8);
-  dim3 grid((unsigned)((ld + 31) / 32), (unsigned)((rows_pad / 2 + 7) / 8));
-  k_build_x<<<grid, block, 0, st>>>(spins, T, meanO, n, N, M, rows_pad, ld, X32, Xhi, Xlo);
+                           float4* mean2, int64_t n, int N, int M, int64_t rows_pad, int64_t ld,
+                           float* X32, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, cudaStream_t st) {
+  if (N > BX_NMAX) return cudaErrorInvalidValue;
+  const int64_t P = (int64_t)N + M + (int64_t)N * M;
+  k_split_mean<<<(unsigned)std::min<int64_t>((P + 255) / 256, 1024), 256, 0, st>>>(meanO, P, mean2);
+  dim3 grid((unsigned)((ld + 31) / 32), (unsigned)((M + 7) / 8));
+  XOut o{X32, Xhi, Xlo, ld};
+  const bool vec16 = (N % 16) == 0 && (reinterpret_cast<uintptr_t>(spins) & 15) == 0;
+  k_build_x<<<grid, 256, 0, st>>>(spins, T, mean2, n, N, M, rows_pad, vec16, o);
   return cudaGetLastError();
 }
 

@@ -83,9 +83,10 @@ cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E
 // Centred log-derivatives, transposed and split into real rows:
 //   X[2k][q] = Re(O_qk - <O_k>), X[2k+1][q] = Im(...), zero padded to [rows_pad][ld].
 // FP32 (X32) and/or the BF16 pair hi = bf16(x), lo = bf16(x - hi).
+// mean2 [P] is a workspace (the mean as FP32 hi/lo pairs).
 cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* meanO,
-                           int64_t n, int N, int M, int64_t rows_pad, int64_t ld, float* X32,
-                           __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, cudaStream_t st);
+                           float4* mean2, int64_t n, int N, int M, int64_t rows_pad, int64_t ld,
+                           float* X32, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, cudaStream_t st);
 
 // S_kl = (1/n) sum_q conj(Xc_qk) Xc_ql from the real row Gram G = X X^T (FP32 SIMT):
 //   S = (G_{2k,2l} + G_{2k+1,2l+1}) + i (G_{2k,2l+1} - G_{2k+1,2l}), written as double2
