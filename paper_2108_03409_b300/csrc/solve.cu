@@ -85,16 +85,22 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
   C* tt = li + NB * PLD;                      // [64][PLD]: products of the inverse
   C* cb = tt + NB * PLD;                      // [2][64]: published column / row
   const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
-    const int r = e >> 6, c = e & 63;
-    C v = mk<C>(0.0, 0.0);
-    if (r < kw && c < kw) {
-      if (c <= r) v = __ldcg(&A[(k0 + r) * P + k0 + c]);
-    } else if (r == c) {
-      v = mk<C>(1.0, 0.0);
+  {
+    // all of a thread's loads are issued before any shared-memory store
+    constexpr int PER = NB * NB / POTRF_THREADS;
+    C v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + POTRF_THREADS * u, r = e >> 6, c = e & 63;
+      v[u] = (r < kw && c <= r) ? __ldcg(&A[(k0 + r) * P + k0 + c])
+                                : mk<C>((r == c && r >= kw) ? 1.0 : 0.0, 0.0);
     }
-    a[r * PLD + c] = v;
-    li[r * PLD + c] = mk<C>(0.0, 0.0);
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + POTRF_THREADS * u, r = e >> 6, c = e & 63;
+      a[r * PLD + c] = v[u];
+      li[r * PLD + c] = mk<C>(0.0, 0.0);
+    }
   }
   __syncthreads();
   bool bad = false;
@@ -266,11 +272,22 @@ __device__ void trsm_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
   C* Bt = reinterpret_cast<C*>(tsm);           // [NB (m)][NB+1 (r)]
   C* Lt = Bt + NB * (NB + 1);                  // [NB (m)][NB+1 (c)]
   const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int rr = e / NB, m = e % NB;
-    const int64_t row = r0 + rr;
-    Bt[m * (NB + 1) + rr] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : mk<C>(0.0, 0.0);
-    Lt[m * (NB + 1) + rr] = __ldcg(&Dinv[e]);    // e = c * NB + m with c = rr
+  {
+    constexpr int PER = NB * NB / 256;
+    C bv[PER], lv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u, rr = e / NB, m = e % NB;
+      const int64_t row = r0 + rr;
+      bv[u] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : mk<C>(0.0, 0.0);
+      lv[u] = __ldcg(&Dinv[e]);                  // e = c * NB + m with c = rr
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u, rr = e / NB, m = e % NB;
+      Bt[m * (NB + 1) + rr] = bv[u];
+      Lt[m * (NB + 1) + rr] = lv[u];
+    }
   }
   __syncthreads();
   const int tx = tid & 15, ty = tid >> 4;
@@ -318,11 +335,22 @@ __device__ void herk_tile_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
   C* Xr = reinterpret_cast<C*>(hsm);           // [NB (m)][NB+1 (row)]
   C* Xc = Xr + NB * (NB + 1);                  // [NB (m)][NB+1 (col)]
   const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += 256) {
-    const int rr = e / NB, m = e % NB;
-    const int64_t row = r0 + rr, col = c0 + rr;
-    Xr[m * (NB + 1) + rr] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : mk<C>(0.0, 0.0);
-    Xc[m * (NB + 1) + rr] = (col < P && m < kw) ? __ldcg(&A[col * P + k0 + m]) : mk<C>(0.0, 0.0);
+  {
+    constexpr int PER = NB * NB / 256;
+    C rv[PER], cv[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u, rr = e / NB, m = e % NB;
+      const int64_t row = r0 + rr, col = c0 + rr;
+      rv[u] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : mk<C>(0.0, 0.0);
+      cv[u] = (col < P && m < kw) ? __ldcg(&A[col * P + k0 + m]) : mk<C>(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = tid + 256 * u, rr = e / NB, m = e % NB;
+      Xr[m * (NB + 1) + rr] = rv[u];
+      Xc[m * (NB + 1) + rr] = cv[u];
+    }
   }
   const int tx = tid & 15, ty = tid >> 4;
   C cur[4][4];
