@@ -269,8 +269,163 @@ static cudaError_t cdot(const double2* a, const double2* b, int64_t P, CgWork& w
 }
 
 // q = S~ p
+// ---------------------------------------------------------------------------------------
+// Tensor-core operator.  Per step: Sb = spins as BF16 [q][i] (A of the Obar v product) and
+// Bs = [spins^T ; ones] [i][q] (B of the Obar^H u product); per CG iteration: the direction's
+// W block as hi/lo real-row planes, and A2 = [conj(t_qj)(u_q - <u>) rows 2j / 2j+1 ; (u_q -
+// <u>) rows 2M / 2M+1] as hi/lo planes [row][q].  Zero padding everywhere the products
+// read (K padding must be finite: 0 x garbage could be NaN).
+// ---------------------------------------------------------------------------------------
+static inline int64_t pad_to(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+__global__ void k_build_sb(const int8_t* __restrict__ spins, int64_t n, int N, int64_t rows,
+                           int64_t K, __nv_bfloat16* __restrict__ Sb) {
+  const int64_t total = rows * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / K;
+    const int i = (int)(e - q * K);
+    Sb[e] = __float2bfloat16_rn((q < n && i < N) ? (float)spins[q * N + i] : 0.f);
+  }
+}
+
+// Bs[i][q] (32 x 32 tiles through shared memory)
+__global__ void k_build_bs(const int8_t* __restrict__ spins, int64_t n, int N, int64_t rows,
+                           int64_t K, __nv_bfloat16* __restrict__ Bs) {
+  __shared__ float tile[32][33];
+  const int64_t q0 = (int64_t)blockIdx.x * 32;
+  const int i0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t q = q0 + r;
+    const int i = i0 + tx;
+    float v = 0.f;
+    if (q < n) v = (i < N) ? (float)spins[q * N + i] : (i == N ? 1.f : 0.f);
+    tile[r][tx] = v;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = i0 + r;
+    const int64_t q = q0 + tx;
+    if (i < rows && q < K) Bs[(int64_t)i * K + q] = __float2bfloat16_rn(tile[tx][r]);
+  }
+}
+
+__global__ void k_build_vplanes(const float2* __restrict__ V, int N, int M, int64_t rows,
+                                int64_t K, __nv_bfloat16* __restrict__ Vhi,
+                                __nv_bfloat16* __restrict__ Vlo) {
+  const int64_t total = rows * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / K;
+    const int i = (int)(e - r * K);
+    const int j = (int)(r >> 1);
+    float v = 0.f;
+    if (j < M && i < N) {
+      const float2 z = V[(int64_t)j * N + i];
+      v = (r & 1) ? z.y : z.x;
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    Vhi[e] = h;
+    Vlo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+// A2 rows [2j, 2j+1] = conj(t_qj) u'_q, rows [2M, 2M+1] = u'_q, u' = u - mean(u)
+__global__ void k_build_a2(const float2* __restrict__ T, const float2* __restrict__ u,
+                           const double* __restrict__ ustats, int64_t n, int M, int64_t rows,
+                           int64_t K, __nv_bfloat16* __restrict__ Ahi,
+                           __nv_bfloat16* __restrict__ Alo) {
+  __shared__ float2 tile[32][33];
+  const int64_t q0 = (int64_t)blockIdx.x * 32;
+  const int j0 = blockIdx.y * 32;                 // complex row index (j or M for u')
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const float mr = (float)ustats[0], mi = (float)ustats[1];
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t q = q0 + r;
+    const int j = j0 + tx;
+    float2 w = make_float2(0.f, 0.f);
+    if (q < n) {
+      const float2 uq = u[q];
+      const float ur = uq.x - mr, ui = uq.y - mi;
+      if (j < M) {
+        const float2 t = T[q * M + j];
+        w = make_float2(t.x * ur + t.y * ui, t.x * ui - t.y * ur);   // conj(t) u'
+      } else if (j == M) {
+        w = make_float2(ur, ui);
+      }
+    }
+    tile[r][tx] = w;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r;
+    const int64_t q = q0 + tx;
+    if (2 * (int64_t)j + 1 < rows && q < K) {
+      const float2 w = tile[tx][r];
+      const __nv_bfloat16 hr = __float2bfloat16_rn(w.x), hi = __float2bfloat16_rn(w.y);
+      Ahi[(2 * (int64_t)j) * K + q] = hr;
+      Ahi[(2 * (int64_t)j + 1) * K + q] = hi;
+      Alo[(2 * (int64_t)j) * K + q] = __float2bfloat16_rn(w.x - __bfloat162float(hr));
+      Alo[(2 * (int64_t)j + 1) * K + q] = __float2bfloat16_rn(w.y - __bfloat162float(hi));
+    }
+  }
+}
+
+// y_k = (1/n) sum_q conj(Obar_qk) u_q from the K-chunk partials G[kc][row][col] (FP64 sum):
+// a_i: rows 2M/2M+1, col i; b_j: rows 2j/2j+1, col N; W_ji: rows 2j/2j+1, col i
+__global__ void k_reduce_y(const float* __restrict__ part, int nkc, int64_t a_rows,
+                           int64_t b_rows, int N, int M, int64_t n, double2* __restrict__ y) {
+  const int64_t P = (int64_t)N + M + (int64_t)N * M;
+  const double inv = 1.0 / (double)n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t row, col;
+    if (k < N) { row = 2 * (int64_t)M; col = k; }
+    else if (k < N + M) { row = 2 * (k - N); col = N; }
+    else { const int64_t r = k - N - M; row = 2 * (r / N); col = r % N; }
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < nkc; ++c) {
+      const float* g = part + (int64_t)c * a_rows * b_rows;
+      re += (double)g[row * b_rows + col];
+      im += (double)g[(row + 1) * b_rows + col];
+    }
+    y[k] = make_double2(re * inv, im * inv);
+  }
+}
+
+static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, double2* q,
+                              cudaStream_t st, int64_t* launches) {
+  const int N = pb.N, M = pb.M;
+  const int64_t n = pb.n, P = (int64_t)N + M + (int64_t)N * M;
+  const int64_t kN = pad_to(N, 64), s_rows = pad_to(n, 128), v_rows = pad_to(2 * (int64_t)M, 128);
+  const int64_t ldK = pad_to(n, 64), a_rows = pad_to(2 * (int64_t)M + 2, 128),
+                b_rows = pad_to((int64_t)N + 1, 128);
+  const int nkc = (int)((ldK / 64 + CG_KB_PER_CHUNK - 1) / CG_KB_PER_CHUNK);
+  if (v_rows * kN > w.cap_v || a_rows * ldK > w.cap_a || nkc * a_rows * b_rows > w.cap_part2)
+    return cudaErrorInvalidValue;
+  k_split_v<<<g1d(P), 256, 0, st>>>(p, N, M, w.va, w.vb, w.V);
+  k_build_vplanes<<<g1d(v_rows * kN), 256, 0, st>>>(w.V, N, M, v_rows, kN, w.Vhi, w.Vlo);
+  VMC_TRY(cdot(pb.meanO_conj_free, p, P, w, w.c2, st));   // c = sum_k <O_k> p_k (no conj)
+  VMC_TRY(launch_cg_ov_tc(w.Sb, s_rows, kN, w.Vhi, w.Vlo, v_rows, pb.T, w.vb, M, n, w.upart,
+                          pb.status, st));
+  const int mtiles = (int)(v_rows / 128);
+  k_vs_finish<<<g1d(n), 256, 0, st>>>(w.upart, mtiles, pb.spins, w.va,
+                                      reinterpret_cast<const double*>(w.c2), n, N, w.u);
+  VMC_TRY(launch_estats(w.u, n, w.ustats, nullptr, st));
+  dim3 ga((unsigned)(ldK / 32), (unsigned)((a_rows / 2 + 31) / 32));
+  k_build_a2<<<ga, 256, 0, st>>>(pb.T, w.u, w.ustats, n, M, a_rows, ldK, w.Ahi, w.Alo);
+  VMC_TRY(launch_cg_ohu_tc(w.Ahi, w.Alo, a_rows, w.Bs, b_rows, ldK, CG_KB_PER_CHUNK, w.part2,
+                           pb.status, st));
+  k_reduce_y<<<g1d(P), 256, 0, st>>>(w.part2, nkc, a_rows, b_rows, N, M, n, w.y);
+  k_add_diag<<<g1d(P), 256, 0, st>>>(w.y, w.D, p, P, q);
+  *launches += 12;
+  return cudaGetLastError();
+}
+
 static cudaError_t apply_s(const CgProblem& pb, CgWork& w, const double2* p, double2* q,
                            cudaStream_t st, int64_t* launches) {
+  if (pb.tc) return apply_s_tc(pb, w, p, q, st, launches);
   const int N = pb.N, M = pb.M;
   const int64_t n = pb.n, P = (int64_t)N + M + (int64_t)N * M;
   k_split_v<<<g1d(P), 256, 0, st>>>(p, N, M, w.va, w.vb, w.V);
@@ -300,6 +455,15 @@ cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cuda
   // <O> with conjugation undone so that cdot(conj(a), p) gives sum <O_k> p_k
   k_conj_copy<<<g1d(P), 256, 0, st>>>(pb.meanO, P, w.meanO_c);
   *launches += 3;
+  if (pb.tc) {
+    const int64_t kN = pad_to(pb.N, 64), s_rows = pad_to(pb.n, 128), ldK = pad_to(pb.n, 64);
+    const int64_t b_rows = pad_to((int64_t)pb.N + 1, 128);
+    if (s_rows * kN > w.cap_sb || b_rows * ldK > w.cap_bs) return cudaErrorInvalidValue;
+    k_build_sb<<<g1d(s_rows * kN), 256, 0, st>>>(pb.spins, pb.n, pb.N, s_rows, kN, w.Sb);
+    dim3 gb((unsigned)(ldK / 32), (unsigned)(b_rows / 32));
+    k_build_bs<<<gb, 256, 0, st>>>(pb.spins, pb.n, pb.N, b_rows, ldK, w.Bs);
+    *launches += 2;
+  }
   return cudaGetLastError();
 }
 

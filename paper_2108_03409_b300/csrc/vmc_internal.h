@@ -153,6 +153,18 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
 cudaError_t residual_fp64(const double2* S, const double2* F, const double2* x, double nu,
                           int mode, SolveWork& w, cudaStream_t st, double* relres);
 
+// CG operator products on the tensor cores (gram_tc.cu):
+//   Ov:  part[n tile][q] = sum_{j in tile} t_qj (v_b,j + sum_i s_qi V_ji), Sb = spins as BF16
+//        [s_rows][K], V planes [v_rows][K] (rows 2j / 2j+1 = Re / Im of V_j)
+//   OhU: out[kc][a_rows][b_rows] = chunk kc of A B^T, A = hi/lo planes [a_rows][K], B exact
+cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, int64_t s_rows, int64_t K,
+                            const __nv_bfloat16* Vhi, const __nv_bfloat16* Vlo, int64_t v_rows,
+                            const float2* T, const float2* vb, int M, int64_t n, float2* part,
+                            unsigned* status, cudaStream_t st);
+cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int64_t a_rows,
+                             const __nv_bfloat16* Bs, int64_t b_rows, int64_t K,
+                             int kb_per_chunk, float* out, unsigned* status, cudaStream_t st);
+
 // ---- cg.cu ----------------------------------------------------------------------------
 struct CgProblem {
   const int8_t* spins;            // [n][N]
@@ -161,6 +173,8 @@ struct CgProblem {
   int N, M;
   const double2* meanO;           // [P] <O>
   const double2* meanO_conj_free; // set by cg_solve
+  bool tc;                        // operator products on the tensor cores (BF16 split)
+  unsigned* status;
 };
 struct CgWork {
   double2 *r, *p, *q, *y, *z, *meanO_c;   // [P]
@@ -175,7 +189,12 @@ struct CgWork {
   double2* dpart;                     // [256] dot partials
   double2* c2;                        // [8] device complex scalars
   double* sc;                         // [8] device real scalars
+  // tensor-core operator (capacities in elements; null when not allocated)
+  __nv_bfloat16 *Sb, *Bs, *Vhi, *Vlo, *Ahi, *Alo;
+  float* part2;
+  int64_t cap_sb, cap_bs, cap_v, cap_a, cap_part2;
 };
+constexpr int CG_KB_PER_CHUNK = 32;   // K chunk (blocks of 64 samples) of the Obar^H u product
 int64_t cg_partial_floats2(int64_t n, int M);
 // diag(S) and the conjugated means; T and meanO must describe the sample set
 cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cudaStream_t st,

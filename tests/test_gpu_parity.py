@@ -365,20 +365,26 @@ def test_sr_step_matches_oracle_pipeline(solver, precision):
 # sub-sums of 128 samples), so the returned x solves a system within
 # CG_OPERATOR_REL * ||S~|| ||x|| of the oracle's FP64 one.
 CG_OPERATOR_REL = 128 * 2.0 ** -24 * 8
+# On the tensor cores the direction's W block and conj(t) u' are BF16 hi/lo pairs (~2^-17
+# relative each, lo.lo dropped: 4 * 2^-16 as for S) and the Obar^H u sums accumulate in FP32
+# over K chunks of 2048 samples (worst case 2048 * 2^-24) before the FP64 sum of the chunks.
+CG_OPERATOR_REL_TC = 4 * 2.0 ** -16 + 2048 * 2.0 ** -24
 
 
+@pytest.mark.parametrize("precision", [vmc.PREC_FP32, vmc.PREC_BF16SPLIT], ids=["simt", "tc"])
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("shape", [(T, 10, 1, 1.0, 1.0, 1, 2000), (H, 4, 4, 1.0, 0.0, 2, 1500),
                                    (T, 6, 6, 1.0, 3.0, 2, 1100)], ids=["tfim10", "heis4x4", "tfim6x6"])
-def test_cg_solve_matches_oracle(shape, mode):
+def test_cg_solve_matches_oracle(shape, mode, precision):
     model, Lx, Ly, J, h, alpha, n = shape
+    op_rel = CG_OPERATOR_REL if precision == vmc.PREC_FP32 else CG_OPERATOR_REL_TC
     N, M = Lx * Ly, alpha * Lx * Ly
     P = N + M + N * M
     nu = 1e-3 if mode == 0 else 1e-2
     p = inputs.rbm_params(N, M, 0.1, seed=51, marshall=(Lx, Ly) if model == H else None)
     s = inputs.initial_spins(model, n, N, seed=52)
     with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=n, solver=vmc.SOLVER_CG, shift=nu,
-                 shift_mode=mode, cg_tol=1e-8, cg_maxit=2000) as ctx:
+                 shift_mode=mode, cg_tol=1e-8, cg_maxit=2000, precision=precision) as ctx:
         vmc.vmc_set_params(ctx, 0, p)
         sd = to_dev_spins(s)
         e = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
@@ -393,14 +399,15 @@ def test_cg_solve_matches_oracle(shape, mode):
     S, _, _ = oracle.sr_matrices(O, np.zeros(n))
     St = oracle.shift(S, nu, mode)
     res = np.linalg.norm(St @ xh - Fh) / np.linalg.norm(Fh)
-    bound = 1e-8 + CG_OPERATOR_REL * np.linalg.norm(St, 2) * np.linalg.norm(xh) / np.linalg.norm(Fh)
+    bound = 1e-8 + op_rel * np.linalg.norm(St, 2) * np.linalg.norm(xh) / np.linalg.norm(Fh)
     assert res <= bound, (res, bound)
     # the oracle's own matrix-free CG reaches the same solution
     xo, ito, relo = oracle.cg_solve(O, Fh, nu, mode, tol=1e-12, maxit=5000)
     assert np.linalg.norm(xh - xo) <= np.linalg.cond(St) * bound * np.linalg.norm(xo)
 
 
-def test_sr_step_cg_heisenberg_16x16():
+@pytest.mark.parametrize("precision", [vmc.PREC_FP32, vmc.PREC_BF16SPLIT], ids=["simt", "tc"])
+def test_sr_step_cg_heisenberg_16x16(precision):
     """The 16x16 Heisenberg shape (N = 256, M = 512, P = 131 840) through the CG step,
     with fewer chains than the benchmark: the step converges and the energy is physical
     (Pauli units: E/N >= -3, the 2D antiferromagnet's ground state is about -2.68 per site)."""
@@ -409,7 +416,7 @@ def test_sr_step_cg_heisenberg_16x16():
     C = 2048
     p = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(Lx, Ly))
     with context(lattice(H, Lx, Ly, 1.0, 0.0, 2), n_chains=C, solver=vmc.SOLVER_CG, shift=1e-3,
-                 cg_tol=1e-6, cg_maxit=100, therm_sweeps=5) as ctx:
+                 cg_tol=1e-6, cg_maxit=100, therm_sweeps=5, precision=precision) as ctx:
         vmc.vmc_set_params(ctx, 0, p)
         vmc.vmc_set_chains(ctx, 0, inputs.random_sz0_spins(C, N, seed=3))
         st = vmc.vmc_sr_step(ctx, 0, 0.02)
