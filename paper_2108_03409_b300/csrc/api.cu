@@ -349,7 +349,8 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &w.Minv, P)) || (e = dalloc(ctx, &w.t2, ctx->Mmax)) ||
         (e = dalloc(ctx, &w.va, ctx->Nmax)) || (e = dalloc(ctx, &w.vb, ctx->Mmax)) ||
         (e = dalloc(ctx, &w.V, (size_t)ctx->Nmax * ctx->Mmax)) || (e = dalloc(ctx, &w.u, Ns)) ||
-        (e = dalloc(ctx, &w.upart, (size_t)cg_partial_floats2(Ns, ctx->Mmax))) ||
+        (e = dalloc(ctx, &w.upart, (size_t)std::max<int64_t>(cg_partial_floats2(Ns, ctx->Mmax),
+                                                              ((2 * (int64_t)ctx->Mmax + 2 + 127) / 128) * Ns))) ||
         (e = dalloc(ctx, &w.ustats, 8)) || (e = dalloc(ctx, &w.dpart, 256)) ||
         (e = dalloc(ctx, &w.c2, 8)) || (e = dalloc(ctx, &w.sc, 8)))
       return oom(e);
@@ -362,7 +363,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
       const int64_t nkc = (ldK / 64 + CG_KB_PER_CHUNK - 1) / CG_KB_PER_CHUNK;
       w.cap_sb = pad(Ns, 128) * kN;
       w.cap_bs = b_rows * ldK;
-      w.cap_v = pad(2 * (int64_t)ctx->Mmax, 128) * kN;
+      w.cap_v = pad(2 * (int64_t)ctx->Mmax + 2, 128) * kN;
       w.cap_a = a_rows * ldK;
       w.cap_part2 = nkc * a_rows * b_rows;
       if ((e = dalloc(ctx, &w.Sb, (size_t)w.cap_sb)) || (e = dalloc(ctx, &w.Bs, (size_t)w.cap_bs)) ||
@@ -370,8 +371,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
           (e = dalloc(ctx, &w.Ahi, (size_t)w.cap_a)) || (e = dalloc(ctx, &w.Alo, (size_t)w.cap_a)) ||
           (e = dalloc(ctx, &w.part2, (size_t)w.cap_part2)))
         return oom(e);
-      const int64_t up_need = (pad(2 * (int64_t)ctx->Mmax, 128) / 128) * Ns;
-      if (up_need > cg_partial_floats2(Ns, ctx->Mmax)) return oom(cudaErrorMemoryAllocation);
+
     }
   }
   if (ctx->dense) {

@@ -147,11 +147,61 @@ __global__ void __launch_bounds__(256) k_cdot_partial(const double2* __restrict_
   }
 }
 
+// one warp: lane l adds partials l, l + 32, ...; then a fixed-order warp reduction
 __global__ void k_cdot_final(const double2* __restrict__ partial, int nb, double2* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
+  double tr = 0, ti = 0;
+  for (int k = threadIdx.x; k < nb; k += 32) { tr += partial[k].x; ti += partial[k].y; }
+  tr = warp_sum_d(tr);
+  ti = warp_sum_d(ti);
+  if (threadIdx.x == 0) *out = make_double2(tr, ti);
+}
+
+// mean of a complex FP32 vector in FP64: block partials, then one warp (fixed order)
+__global__ void __launch_bounds__(256) k_mean_partial(const float2* __restrict__ u, int64_t n,
+                                                      double2* __restrict__ partial) {
+  __shared__ double red[2][8];
+  double sr = 0, si = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = u[k];
+    sr += v.x;
+    si += v.y;
+  }
+  sr = warp_sum_d(sr);
+  si = warp_sum_d(si);
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sr; red[1][threadIdx.x >> 5] = si; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double tr = 0, ti = 0;
-    for (int k = 0; k < nb; ++k) { tr += partial[k].x; ti += partial[k].y; }
-    *out = make_double2(tr, ti);
+    for (int w = 0; w < 8; ++w) { tr += red[0][w]; ti += red[1][w]; }
+    partial[blockIdx.x] = make_double2(tr, ti);
+  }
+}
+
+__global__ void k_mean_final(const double2* __restrict__ partial, int nb, int64_t n,
+                             double* __restrict__ out) {
+  double tr = 0, ti = 0;
+  for (int k = threadIdx.x; k < nb; k += 32) { tr += partial[k].x; ti += partial[k].y; }
+  tr = warp_sum_d(tr);
+  ti = warp_sum_d(ti);
+  if (threadIdx.x == 0) {
+    out[0] = tr / (double)n;
+    out[1] = ti / (double)n;
+  }
+}
+
+// u_q = sum over the tiles' partials - c (the a block came through the product)
+__global__ void k_vs_finish_tc(const float2* __restrict__ part, int mtiles,
+                               const double* __restrict__ c, int64_t n, float2* __restrict__ u) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    float ur = 0.f, ui = 0.f;
+    for (int m = 0; m < mtiles; ++m) {
+      const float2 p = part[(int64_t)m * n + q];
+      ur += p.x;
+      ui += p.y;
+    }
+    u[q] = make_float2(ur - (float)c[0], ui - (float)c[1]);
   }
 }
 
@@ -311,9 +361,10 @@ __global__ void k_build_bs(const int8_t* __restrict__ spins, int64_t n, int N, i
   }
 }
 
-__global__ void k_build_vplanes(const float2* __restrict__ V, int N, int M, int64_t rows,
-                                int64_t K, __nv_bfloat16* __restrict__ Vhi,
-                                __nv_bfloat16* __restrict__ Vlo) {
+// rows 2j / 2j+1: Re / Im of V_j (j < M); rows 2M / 2M+1: Re / Im of v_a
+__global__ void k_build_vplanes(const float2* __restrict__ V, const float2* __restrict__ va,
+                                int N, int M, int64_t rows, int64_t K,
+                                __nv_bfloat16* __restrict__ Vhi, __nv_bfloat16* __restrict__ Vlo) {
   const int64_t total = rows * K;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -321,8 +372,8 @@ __global__ void k_build_vplanes(const float2* __restrict__ V, int N, int M, int6
     const int i = (int)(e - r * K);
     const int j = (int)(r >> 1);
     float v = 0.f;
-    if (j < M && i < N) {
-      const float2 z = V[(int64_t)j * N + i];
+    if (j <= M && i < N) {
+      const float2 z = (j < M) ? V[(int64_t)j * N + i] : va[i];
       v = (r & 1) ? z.y : z.x;
     }
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
@@ -398,21 +449,25 @@ static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, 
                               cudaStream_t st, int64_t* launches) {
   const int N = pb.N, M = pb.M;
   const int64_t n = pb.n, P = (int64_t)N + M + (int64_t)N * M;
-  const int64_t kN = pad_to(N, 64), s_rows = pad_to(n, 128), v_rows = pad_to(2 * (int64_t)M, 128);
+  const int64_t kN = pad_to(N, 64), s_rows = pad_to(n, 128), v_rows = pad_to(2 * (int64_t)M + 2, 128);
   const int64_t ldK = pad_to(n, 64), a_rows = pad_to(2 * (int64_t)M + 2, 128),
                 b_rows = pad_to((int64_t)N + 1, 128);
   const int nkc = (int)((ldK / 64 + CG_KB_PER_CHUNK - 1) / CG_KB_PER_CHUNK);
   if (v_rows * kN > w.cap_v || a_rows * ldK > w.cap_a || nkc * a_rows * b_rows > w.cap_part2)
     return cudaErrorInvalidValue;
   k_split_v<<<g1d(P), 256, 0, st>>>(p, N, M, w.va, w.vb, w.V);
-  k_build_vplanes<<<g1d(v_rows * kN), 256, 0, st>>>(w.V, N, M, v_rows, kN, w.Vhi, w.Vlo);
+  k_build_vplanes<<<g1d(v_rows * kN), 256, 0, st>>>(w.V, w.va, N, M, v_rows, kN, w.Vhi, w.Vlo);
   VMC_TRY(cdot(pb.meanO_conj_free, p, P, w, w.c2, st));   // c = sum_k <O_k> p_k (no conj)
   VMC_TRY(launch_cg_ov_tc(w.Sb, s_rows, kN, w.Vhi, w.Vlo, v_rows, pb.T, w.vb, M, n, w.upart,
                           pb.status, st));
   const int mtiles = (int)(v_rows / 128);
-  k_vs_finish<<<g1d(n), 256, 0, st>>>(w.upart, mtiles, pb.spins, w.va,
-                                      reinterpret_cast<const double*>(w.c2), n, N, w.u);
-  VMC_TRY(launch_estats(w.u, n, w.ustats, nullptr, st));
+  k_vs_finish_tc<<<g1d(n), 256, 0, st>>>(w.upart, mtiles, reinterpret_cast<const double*>(w.c2),
+                                         n, w.u);
+  {
+    const int nb = (int)std::min<int64_t>(RED_BLOCKS, (n + 1023) / 1024);
+    k_mean_partial<<<nb, 256, 0, st>>>(w.u, n, w.dpart);
+    k_mean_final<<<1, 32, 0, st>>>(w.dpart, nb, n, w.ustats);
+  }
   dim3 ga((unsigned)(ldK / 32), (unsigned)((a_rows / 2 + 31) / 32));
   k_build_a2<<<ga, 256, 0, st>>>(pb.T, w.u, w.ustats, n, M, a_rows, ldK, w.Ahi, w.Alo);
   VMC_TRY(launch_cg_ohu_tc(w.Ahi, w.Alo, a_rows, w.Bs, b_rows, ldK, CG_KB_PER_CHUNK, w.part2,
