@@ -44,7 +44,8 @@ WORKLOADS = {
                                        chains=65536, spc=1, shift=1e-3, solver="cg",
                                        marshall=True),
     "tfim1d_N10_alpha1_c256": dict(model=0, Lx=10, Ly=1, J=1.0, h=1.0, alpha=1, chains=256,
-                                   spc=200, shift=1e-4, solver="mixed", marshall=False),
+                                   spc=200, shift=1e-4, solver="mixed", marshall=False,
+                                   precision="fp32"),
 }
 # batched sampling of many independent lattices (one sweep + a record per chain per step)
 BATCHED = {"tfim2d_batched48_alpha2_c1024": dict(sizes=[4] * 16 + [6] * 16 + [8] * 16, alpha=2,
@@ -280,7 +281,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     vbuild.build()
-    prec = {"fp32": vmc.PREC_FP32, "bf16split": vmc.PREC_BF16SPLIT}[args.precision]
+    prec_name = args.precision or wl.get("precision", "bf16split")
+    prec = {"fp32": vmc.PREC_FP32, "bf16split": vmc.PREC_BF16SPLIT}[prec_name]
     solver_name = args.solver or wl["solver"]
     solver = {"fp64": vmc.SOLVER_CHOLESKY_FP64, "mixed": vmc.SOLVER_CHOLESKY_MIXED,
               "tc": vmc.SOLVER_CHOLESKY_TC, "cg": vmc.SOLVER_CG}[solver_name]
@@ -382,7 +384,7 @@ def run_ours(args):
            "data": "synthetic",
            "config": {"workload": args.workload, "N": N, "M": M, "P": P,
                       "chains": CHAINS, "Ns": Ns, "shift": SHIFT, "dt": DT,
-                      "precision": args.precision, "solver": solver_name,
+                      "precision": prec_name, "solver": solver_name,
                       "l2": "working set (S 1.1 GB, X 0.55 GB) larger than L2; no flush",
                       "parallelism": f"replicas x{ws}"},
            "eff_samples_per_s": {"value": eff * ws, "unit": "samples/s", "tau_int_E": tau,
@@ -666,7 +668,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16split", choices=["fp32", "bf16split"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16split"],
+                    help="default: the workload's (bf16split, fp32 for the 1D chain)")
     ap.add_argument("--solver", default=None, choices=["mixed", "tc", "fp64", "cg"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(LEARNED))

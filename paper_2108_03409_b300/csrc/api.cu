@@ -68,6 +68,8 @@ struct vmc_ctx {
   __nv_bfloat16* Xhi = nullptr;
   __nv_bfloat16* Xlo = nullptr;
   double2* S = nullptr;           // [Pmax][Pmax]
+  float2* gpart = nullptr;        // split-K partials of the Gram (small P)
+  int64_t gpart_cap = 0;
   SolveWork sw{};
   CgWork cg{};
   MadeWork mw{};
@@ -89,6 +91,7 @@ struct vmc_ctx {
   unsigned* status = nullptr;
   unsigned long long* n_accept = nullptr;
   int64_t launches = 0;
+  int64_t psd_retries = 0;        // SR steps whose S was re-formed with the fourth product
   std::vector<void*> allocs;
   cudaEvent_t ev[8] = {};
   std::string err;
@@ -170,7 +173,8 @@ vmc_status refresh_fp32(vmc_ctx* ctx, LatticeState& L) {
 // may be null when `fused` (tensor-core Gram only): the Gram then writes the mixed solvers'
 // inputs (ctx->sw.S2 and the shifted lower triangle in ctx->sw.A32) directly.
 vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const float2* E,
-                    int64_t n, int precision, double2* S_out, bool mirror, bool fused = false) {
+                    int64_t n, int precision, double2* S_out, bool mirror, bool fused = false,
+                    bool lolo = false) {
   CK(launch_moments(spins, ctx->s_T, E, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
                     E ? ctx->F : nullptr, ctx->st), "moments");
   ctx->launches += 2;
@@ -186,7 +190,8 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
     cudaEventRecord(ctx->ev[6], ctx->st);
     cudaError_t e = launch_gram_tc(ctx->Xhi, ctx->Xlo, rows_pad, ld, L.P, inv_n, S_out, mirror,
                                    fused ? ctx->sw.S2 : nullptr, fused ? ctx->sw.A32 : nullptr,
-                                   ctx->cfg.shift, ctx->cfg.shift_mode, ctx->status, ctx->st);
+                                   ctx->cfg.shift, ctx->cfg.shift_mode, lolo, ctx->gpart,
+                                   ctx->gpart_cap, ctx->status, ctx->st);
     cudaEventRecord(ctx->ev[7], ctx->st);
     if (e == cudaErrorNotSupported) return fail(ctx, VMC_ERR_ARG, "tensor-core Gram: shape not supported");
     CK(e, "gram_tc");
@@ -196,7 +201,8 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
                       nullptr, ctx->st), "build_x");
     ctx->launches += 2;
     cudaEventRecord(ctx->ev[6], ctx->st);
-    CK(launch_gram_f32(ctx->X32, rows_pad, ld, L.P, inv_n, S_out, mirror, ctx->st), "gram_f32");
+    CK(launch_gram_f32(ctx->X32, rows_pad, ld, L.P, inv_n, S_out, mirror, ctx->gpart,
+                       ctx->gpart_cap, ctx->st), "gram_f32");
     cudaEventRecord(ctx->ev[7], ctx->st);
     ++ctx->launches;
   }
@@ -387,6 +393,9 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &ctx->sw.c32, P)) || (e = dalloc(ctx, &ctx->sw.scal, 8)) ||
         (e = dalloc(ctx, &ctx->sw.bar, 4 + 9 * (size_t)((P + 255) / 256))))
       return oom(e);
+    // split-K Gram partials: up to 8M complex FP32 (64 MB), used only when P is small
+    ctx->gpart_cap = std::min<int64_t>((int64_t)1 << 23, P * P * 64);
+    if ((e = dalloc(ctx, &ctx->gpart, (size_t)ctx->gpart_cap))) return oom(e);
     ctx->sw.Xhi = ctx->Xhi;
     ctx->sw.Xlo = ctx->Xlo;
     ctx->sw.x_elems = (int64_t)xs;
@@ -402,7 +411,8 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
           (e = dalloc(ctx, &ctx->sw.D32, (size_t)nblk * 64 * 64)) ||
           (e = dalloc(ctx, &ctx->sw.T32f, nsb * 256 * 256)) ||
           (e = dalloc(ctx, &ctx->sw.T32b, nsb * 256 * 256)) ||
-          (e = dalloc(ctx, &ctx->sw.S2, (size_t)P * P)) || (e = dalloc(ctx, &ctx->sw.x2, P)))
+          (e = dalloc(ctx, &ctx->sw.S2, (size_t)P * P)) || (e = dalloc(ctx, &ctx->sw.x2, P)) ||
+          (e = dalloc(ctx, &ctx->sw.dsc, P)))
         return oom(e);
     }
   }
@@ -674,8 +684,18 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
                       true, fused)))
       return s;
     CK(cudaEventRecord(ctx->ev[3], ctx->st), "sr_step");
-    // 4. solve (synchronises)
-    if ((s = solve_core(ctx, L, fused ? nullptr : ctx->S, ctx->F, ctx->x, &iters, &rel))) return s;
+    // 4. solve (synchronises).  The three-product BF16 split can leave S indefinite by up
+    //    to the dropped lo.lo^T term; if the shifted matrix then has a non-positive pivot,
+    //    S is formed again with the fourth product (PSD) and the solve repeated once.
+    s = solve_core(ctx, L, fused ? nullptr : ctx->S, ctx->F, ctx->x, &iters, &rel);
+    if (s == VMC_ERR_NUMERIC && c.precision == VMC_PREC_BF16SPLIT) {
+      if ((s = qfm_core(ctx, L, ctx->s_spins, ctx->s_E, Ns, c.precision, fused ? nullptr : ctx->S,
+                        true, fused, true)))
+        return s;
+      ++ctx->psd_retries;
+      s = solve_core(ctx, L, fused ? nullptr : ctx->S, ctx->F, ctx->x, &iters, &rel);
+    }
+    if (s) return s;
   } else {
     // 3. <O>, F and diag(S) (S itself is never formed)
     CK(launch_moments(ctx->s_spins, ctx->s_T, ctx->s_E, ctx->estats, Ns, L.N, L.M, ctx->partial,

@@ -156,11 +156,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 }  // namespace tc
 
+template <bool LOLO>
 __global__ void __launch_bounds__(tc::THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
           int nk, int nt, int64_t tiles, int64_t P, double inv_n, double2* __restrict__ S,
           float4* __restrict__ S2, float2* __restrict__ Af, double nu, int shift_mode, int mirror,
-          float2* __restrict__ A32, int64_t ldA, int64_t off, unsigned* status) {
+          float2* __restrict__ A32, int64_t ldA, int64_t off, int kchunks, int nkpc,
+          float2* __restrict__ part, unsigned* status) {
   using namespace tc;
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
@@ -200,10 +202,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     if (lane == 0) {
       // ---------------- TMA producer ----------------
       int64_t g = 0;                                  // k-blocks issued so far
-      for (int64_t t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x) {
+      for (int64_t t = blockIdx.x; t < tiles * kchunks && !*abort_flag; t += gridDim.x) {
         int bm, bn;
-        grouped_tri_tile(t, nt, 12, &bm, &bn);
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        grouped_tri_tile(t % tiles, nt, 12, &bm, &bn);
+        const int kbeg = (int)(t / tiles) * nkpc, kend = min(nk, kbeg + nkpc);
+        for (int kb = kbeg; kb < kend; ++kb, ++g) {
           const int s = (int)(g % STAGES);
           const int64_t j = g / STAGES;
           if (j > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((j - 1) & 1), abort_flag)) break;
@@ -230,13 +233,14 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       int64_t g = 0;
       int i = 0;
       bool issued_any = false;
-      for (int64_t t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x, ++i) {
+      for (int64_t t = blockIdx.x; t < tiles * kchunks && !*abort_flag; t += gridDim.x, ++i) {
         const int acc = i & 1, u = i >> 1;
         if (u > 0 && !mbar_wait(smem_u32(&acce[acc]), (uint32_t)((u - 1) & 1), abort_flag)) break;
         fence_after();
         const uint32_t d = tmem + (uint32_t)(acc * BN);
         bool ok = true;
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int kbeg = (int)(t / tiles) * nkpc, kend = min(nk, kbeg + nkpc);
+        for (int kb = kbeg; kb < kend; ++kb, ++g) {
           const int s = (int)(g % STAGES);
           if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((g / STAGES) & 1), abort_flag)) { ok = false; break; }
           fence_after();
@@ -248,9 +252,10 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
-            mma_bf16(d, ah + o, bh + o, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            mma_bf16(d, ah + o, bh + o, idesc, (kb > kbeg || kk > 0) ? 1u : 0u);
             mma_bf16(d, ah + o, bl + o, idesc, 1u);
             mma_bf16(d, al + o, bh + o, idesc, 1u);
+            if (LOLO) mma_bf16(d, al + o, bl + o, idesc, 1u);   // (hi+lo)(hi+lo)^T: PSD
           }
           issued_any = true;
           mma_commit(smem_u32(&empty[s]));            // frees the stage when these finish
@@ -272,10 +277,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     const int et = (warp - 2) * 32 + lane;           // 0..127 within the epilogue group
     const bool even = (r & 1) == 0;
     int i = 0;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+    for (int64_t t = blockIdx.x; t < tiles * kchunks; t += gridDim.x, ++i) {
       const int acc = i & 1, u = i >> 1;
       int bm, bn;
-      grouped_tri_tile(t, nt, 12, &bm, &bn);
+      grouped_tri_tile(t % tiles, nt, 12, &bm, &bn);
+      const int kc = (int)(t / tiles);
       // Schur mode: fetch this thread's 32 entries of the factor's tile now, so that their
       // memory latency overlaps the wait for the products (no stores intervene).
       float2 cur[32];
@@ -312,6 +318,18 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
               const float im = even ? mine1 - oth0 : oth1 - mine0;
               stg[(r >> 1) * STG_LD + (c0 >> 1) + q] = make_float2(re, im);
             }
+          }
+        } else if (part) {
+          // split over K: this chunk's fold (FP32, unnormalised) for l <= k; the chunks
+          // are summed in FP64 afterwards
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
+            const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
+            const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
+            const int64_t l = l0 + q;
+            if (even && k < P && l < P && (bm != bn || l <= k))
+              part[((int64_t)kc * P + k) * P + l] = make_float2(mine0 + oth1, mine1 - oth0);
           }
         } else {
           // row 2k holds G[2k][2l], G[2k][2l+1]; row 2k+1 holds G[2k+1][2l], G[2k+1][2l+1].
@@ -609,7 +627,8 @@ static unsigned persistent_grid(int64_t tiles) {
 cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
                            bool mirror, float4* S2, float2* Af, double nu, int shift_mode,
-                           unsigned* status, cudaStream_t st) {
+                           bool lolo, float2* part, int64_t part_cap, unsigned* status,
+                           cudaStream_t st) {
   if (rows_pad % tc::BM != 0 || ld % tc::BK != 0 || ld < tc::BK) return cudaErrorNotSupported;
   if ((reinterpret_cast<uintptr_t>(Xhi) | reinterpret_cast<uintptr_t>(Xlo)) & 15)
     return cudaErrorNotSupported;
@@ -619,17 +638,28 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
   if ((e = make_map(&mlo, Xlo, rows_pad, ld)) != cudaSuccess) return e;
   static bool attr = false;
   if (!attr) {
-    e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
-  k_gram_tc<<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
-      mhi, mlo, (int)(ld / tc::BK), (int)nt, tiles, P, inv_n, S, S2, Af, nu, shift_mode,
-      mirror ? 1 : 0, nullptr, 0, 0, status);
-  return cudaGetLastError();
+  const int nkb = (int)(ld / tc::BK);
+  int kchunks = gram_kchunks(tiles, nkb, P, part_cap);
+  const int nkpc = (nkb + kchunks - 1) / kchunks;
+  kchunks = (nkb + nkpc - 1) / nkpc;                 // no empty chunk
+  auto kern = lolo ? k_gram_tc<true> : k_gram_tc<false>;
+  kern<<<persistent_grid(tiles * kchunks), tc::THREADS, tc::SMEM_BYTES, st>>>(
+      mhi, mlo, nkb, (int)nt, tiles, P, inv_n, S, S2, Af, nu, shift_mode, mirror ? 1 : 0,
+      nullptr, 0, 0, kchunks, nkpc, kchunks > 1 ? part : nullptr, status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (kchunks > 1)
+    return launch_gram_reduce(part, kchunks, P, inv_n, S, S2, Af, nu, shift_mode, mirror, st);
+  return cudaSuccess;
 }
 
 cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, int64_t rows_pad,
@@ -642,16 +672,19 @@ cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, i
   if ((e = make_map(&mlo, Xlo, rows_pad, K)) != cudaSuccess) return e;
   static bool attr = false;
   if (!attr) {
-    e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
-  k_gram_tc<<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
+  k_gram_tc<false><<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
       mhi, mlo, (int)(K / tc::BK), (int)nt, tiles, n, 1.0, nullptr, nullptr, nullptr, 0.0, 0, 0,
-      A32, ldA, off, status);
+      A32, ldA, off, 1, (int)(K / tc::BK), nullptr, status);
   return cudaGetLastError();
 }
 

@@ -918,15 +918,48 @@ __global__ void k_norm2(const double2* __restrict__ v, int64_t P, double* acc) {
   if ((threadIdx.x & 31) == 0) atomicAdd(acc, s);
 }
 
-__global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ b, int64_t P) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
-    b[k] = make_float2((float)a[k].x, (float)a[k].y);
+// b = D a (D the equilibration scales, or 1 when dsc is null)
+__global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ b, int64_t P,
+                         const float* __restrict__ dsc) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    const double d = dsc ? (double)dsc[k] : 1.0;
+    b[k] = make_float2((float)(a[k].x * d), (float)(a[k].y * d));
+  }
 }
 
-__global__ void k_add_f32(double2* __restrict__ x, const float2* __restrict__ c, int64_t P) {
+// x += D c
+__global__ void k_add_f32(double2* __restrict__ x, const float2* __restrict__ c, int64_t P,
+                          const float* __restrict__ dsc) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-    x[k].x += (double)c[k].x;
-    x[k].y += (double)c[k].y;
+    const double d = dsc ? (double)dsc[k] : 1.0;
+    x[k].x += (double)c[k].x * d;
+    x[k].y += (double)c[k].y * d;
+  }
+}
+
+// Jacobi equilibration of the factor's input: d_k = 1 / sqrt(A_kk), A_rc <- d_r A_rc d_c on
+// the lower triangle (unit diagonal).  The FP32 factorisation of S~ with its diagonal
+// spread over orders of magnitude (Var s_i ~ 1 against |t_j|^2 << 1) keeps positive pivots
+// and contracts the refinement faster on the scaled matrix; corrections are mapped back
+// with D (S~ c = r  <=>  (D S~ D)(D^-1 c) = D r).
+__global__ void k_eq_scales(const float2* __restrict__ A, int64_t P, float* __restrict__ dsc) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    const float d = A[k * P + k].x;
+    dsc[k] = (d > 0.f && isfinite(d)) ? rsqrtf(d) : 1.f;
+  }
+}
+
+__global__ void k_equilibrate(float2* __restrict__ A, int64_t P, const float* __restrict__ dsc) {
+  const int64_t total = P * P;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / P, c = e - r * P;
+    if (c > r) continue;
+    const float s = dsc[r] * dsc[c];
+    float2 v = A[e];
+    v.x *= s;
+    v.y *= s;
+    A[e] = v;
   }
 }
 
@@ -1280,6 +1313,9 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
                                  cudaStream_t st, int64_t* launches, int* iters,
                                  double* relres) {
   const int64_t P = w.P;
+  k_eq_scales<<<grid_for(P, 256, 1024), 256, 0, st>>>(w.A32, P, w.dsc);
+  k_equilibrate<<<grid_for(P * P, 256), 256, 0, st>>>(w.A32, P, w.dsc);
+  *launches += 2;
   if (tc && P > NBO) VMC_TRY(factor_tc(w.A32, w.D32, P, w, status, st, launches));
   else VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
   VMC_TRY(invert_blocks<float2>(w.A32, P, w, st, launches));
@@ -1289,9 +1325,9 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
   bool tc_factor = tc && P > NBO;
   int it = 0;
   for (; it < std::max(1, maxit); ++it) {
-    k_to_f32<<<grid_for(P, 256, 1024), 256, 0, st>>>(w.r, w.r32, P);
+    k_to_f32<<<grid_for(P, 256, 1024), 256, 0, st>>>(w.r, w.r32, P, w.dsc);
     VMC_TRY(chol_solve<float2>(w.A32, w.D32, P, w.r32, w.y32, w.c32, w, status, st, launches));
-    k_add_f32<<<grid_for(P, 256, 1024), 256, 0, st>>>(x, w.c32, P);
+    k_add_f32<<<grid_for(P, 256, 1024), 256, 0, st>>>(x, w.c32, P, w.dsc);
     *launches += 2;
     VMC_TRY(residual_df(F, x, nu, mode, w, st, &rel));
     *launches += 3;
@@ -1301,7 +1337,8 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
     // is too slow, refactor in FP32 and keep refining from the current x.
     if (tc_factor && it >= 1 && rel > 0.25 * prev) {
       k_s2_to_a32<<<grid_for(P * P, 256), 256, 0, st>>>(w.S2, w.A32, P, nu, mode);
-      ++*launches;
+      k_equilibrate<<<grid_for(P * P, 256), 256, 0, st>>>(w.A32, P, w.dsc);
+      *launches += 2;
       VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
       VMC_TRY(invert_blocks<float2>(w.A32, P, w, st, launches));
       tc_factor = false;

@@ -303,7 +303,8 @@ static constexpr int GB = 128, GK = 16, GPAD = 4;
 
 __global__ void __launch_bounds__(256) k_gram_f32(const float* __restrict__ X, int64_t ld,
                                                   int nt, int64_t P, double inv_n,
-                                                  double2* __restrict__ S, int mirror) {
+                                                  double2* __restrict__ S, int mirror,
+                                                  int ktpc, float2* __restrict__ part) {
   extern __shared__ float gsm[];
   float* As = gsm;                              // [2][GK][GB + GPAD]
   float* Bs = gsm + 2 * GK * (GB + GPAD);       // [2][GK][GB + GPAD]
@@ -312,7 +313,11 @@ __global__ void __launch_bounds__(256) k_gram_f32(const float* __restrict__ X, i
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const float* Ag = X + (int64_t)bm * GB * ld;
   const float* Bg = X + (int64_t)bn * GB * ld;
-  const int ktiles = (int)(ld / GK);
+  // K range of this block (blockIdx.y = sample chunk of ktpc GK-blocks)
+  const int kt_begin = blockIdx.y * ktpc;
+  const int ktiles = min((int)(ld / GK), kt_begin + ktpc) - kt_begin;
+  Ag += (int64_t)kt_begin * GK;
+  Bg += (int64_t)kt_begin * GK;
 
   float acc[8][8];
 #pragma unroll
@@ -394,6 +399,11 @@ __global__ void __launch_bounds__(256) k_gram_f32(const float* __restrict__ X, i
     if (k >= P || l >= P) continue;
     const float g00 = Cs[(2 * r) * (GB + 1) + 2 * c], g11 = Cs[(2 * r + 1) * (GB + 1) + 2 * c + 1];
     const float g01 = Cs[(2 * r) * (GB + 1) + 2 * c + 1], g10 = Cs[(2 * r + 1) * (GB + 1) + 2 * c];
+    if (part) {
+      if (bm != bn || l <= k)
+        part[((int64_t)blockIdx.y * P + k) * P + l] = make_float2(g00 + g11, g01 - g10);
+      continue;
+    }
     const double re = ((double)g00 + (double)g11) * inv_n;
     const double im = ((double)g01 - (double)g10) * inv_n;
     S[k * P + l] = make_double2(re, im);
@@ -401,8 +411,62 @@ __global__ void __launch_bounds__(256) k_gram_f32(const float* __restrict__ X, i
   }
 }
 
+int gram_kchunks(int64_t tiles, int nkb, int64_t P, int64_t part_cap) {
+  if (!part_cap || tiles >= 296) return 1;          // two waves of 148 SMs from tiles alone
+  int64_t kc = std::min<int64_t>((296 + tiles - 1) / tiles, nkb / 16);
+  kc = std::min<int64_t>(kc, part_cap / std::max<int64_t>(1, P * P));
+  return (int)std::max<int64_t>(1, kc);
+}
+
+// S_kl = (1/n) sum over chunks (FP64) of the FP32 chunk folds, l <= k; mirrors as usual
+__global__ void k_gram_reduce(const float2* __restrict__ part, int kchunks, int64_t P,
+                              double inv_n, double2* __restrict__ S, float4* __restrict__ S2,
+                              float2* __restrict__ Af, double nu, int shift_mode, int mirror) {
+  const int64_t total = P * P;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = e / P, l = e - k * P;
+    if (l > k) continue;
+    double re = 0.0, im = 0.0;
+    for (int c = 0; c < kchunks; ++c) {
+      const float2 v = part[(int64_t)c * total + e];
+      re += (double)v.x;
+      im += (double)v.y;
+    }
+    const double vr = re * inv_n, vi = (l == k) ? 0.0 : im * inv_n;
+    if (S) {
+      S[e] = make_double2(vr, vi);
+      if (mirror && l != k) S[l * P + k] = make_double2(vr, -vi);
+    }
+    if (S2 || Af) {
+      const float hr = (float)vr, hi = (float)vi;
+      if (S2) {
+        S2[e] = make_float4(hr, hi, (float)(vr - (double)hr), (float)(vi - (double)hi));
+        if (mirror && l != k) {
+          const float mhi = (float)(-vi);
+          S2[l * P + k] = make_float4(hr, mhi, (float)(vr - (double)hr), (float)(-vi - (double)mhi));
+        }
+      }
+      if (Af) {
+        const float d = (l == k) ? (float)(shift_mode == 0 ? vr * (1.0 + nu) : vr + nu) : hr;
+        Af[e] = make_float2(d, hi);
+      }
+    }
+  }
+}
+
+cudaError_t launch_gram_reduce(const float2* part, int kchunks, int64_t P, double inv_n,
+                               double2* S, float4* S2, float2* Af, double nu, int shift_mode,
+                               bool mirror, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((P * P + 255) / 256, 4096);
+  k_gram_reduce<<<blocks, 256, 0, st>>>(part, kchunks, P, inv_n, S, S2, Af, nu, shift_mode,
+                                        mirror ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_t P,
-                            double inv_n, double2* S, bool mirror, cudaStream_t st) {
+                            double inv_n, double2* S, bool mirror, float2* part,
+                            int64_t part_cap, cudaStream_t st) {
   if (rows_pad % GB != 0 || ld % GK != 0) return cudaErrorInvalidValue;
   const int64_t nt = rows_pad / GB;
   const int64_t tiles = nt * (nt + 1) / 2;
@@ -415,8 +479,16 @@ cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_gram_f32<<<(unsigned)tiles, 256, smem, st>>>(X, ld, (int)nt, P, inv_n, S, mirror ? 1 : 0);
-  return cudaGetLastError();
+  const int nkb = (int)(ld / 64);                    // chunk sizes in the 64-sample blocks
+  int kchunks = gram_kchunks(tiles, nkb, P, part_cap);
+  const int ktpc = ((nkb + kchunks - 1) / kchunks) * (64 / GK);
+  kchunks = (int)((ld / GK + ktpc - 1) / ktpc);
+  dim3 grid((unsigned)tiles, (unsigned)kchunks);
+  k_gram_f32<<<grid, 256, smem, st>>>(X, ld, (int)nt, P, inv_n, S, mirror ? 1 : 0, ktpc,
+                                      kchunks > 1 ? part : nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || kchunks == 1) return e;
+  return launch_gram_reduce(part, kchunks, P, inv_n, S, nullptr, nullptr, 0.0, 0, mirror, st);
 }
 
 }  // namespace vmc

@@ -92,17 +92,31 @@ cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* 
 //   S = (G_{2k,2l} + G_{2k+1,2l+1}) + i (G_{2k,2l+1} - G_{2k+1,2l}), written as double2
 //   [P][P]; mirror = also write the upper triangle.
 cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_t P,
-                            double inv_n, double2* S, bool mirror, cudaStream_t st);
+                            double inv_n, double2* S, bool mirror, float2* part,
+                            int64_t part_cap, cudaStream_t st);
 
 // Same contraction on the tensor cores (tcgen05, BF16 hi/lo split, FP32 accumulation
 // in TMEM).  Returns cudaErrorNotSupported when the shapes are not supported.
 // Optional outputs besides S (FP64, may be null): S2 = S as FP32 hi/lo pairs {hi.re,
 // hi.im, lo.re, lo.im} (full matrix with the mirror), and Af = the FP32 input of the
 // Cholesky factorisation (lower triangle, diagonal shifted by nu in shift_mode).
+// lolo adds the fourth product lo.lo^T: S is then exactly the Gram of the BF16-rounded X
+// (positive semi-definite up to FP32 accumulation), which the three-product split (lo.lo^T
+// dropped, a PSD term) is not.
+// part [part_cap float2] is a workspace: when the tiles alone cannot fill the GPU (small P)
+// the sample range is split into chunks whose FP32 partial folds are summed in FP64.
 cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
                            bool mirror, float4* S2, float2* Af, double nu, int shift_mode,
-                           unsigned* status, cudaStream_t st);
+                           bool lolo, float2* part, int64_t part_cap, unsigned* status,
+                           cudaStream_t st);
+// split-K support shared by both Gram kernels: number of sample chunks for `tiles` lower
+// tiles over nkb blocks of samples (>= 16 blocks a chunk, P*P*chunks <= part_cap), and the
+// FP64 sum of the chunk partials part[c][k][l] (l <= k) into S / S2 / Af
+int gram_kchunks(int64_t tiles, int nkb, int64_t P, int64_t part_cap);
+cudaError_t launch_gram_reduce(const float2* part, int kchunks, int64_t P, double inv_n,
+                               double2* S, float4* S2, float2* Af, double nu, int shift_mode,
+                               bool mirror, cudaStream_t st);
 
 // Schur-complement update of an FP32 complex Cholesky factor on the tensor cores:
 // A[off+k][off+l] -= sum_m L_km conj(L_lm) for 0 <= l <= k < n, with L's panel given as
@@ -131,6 +145,7 @@ struct SolveWork {
   __nv_bfloat16* Xlo;
   int64_t x_elems;     // capacity of Xhi / Xlo
   float4* S2;          // [P][P] S as FP32 hi/lo pairs (mixed solvers' residual)
+  float* dsc;          // [P] equilibration scales of the mixed solvers' factor
   float4* x2;          // [P] iterate as FP32 hi/lo pairs
 };
 

@@ -424,3 +424,28 @@ def test_sr_step_cg_heisenberg_16x16(precision):
     assert st.solver_relres <= 1e-6 and st.solver_iters <= 100
     assert -3.0 <= st.e_mean_re / N <= 1.0
     assert np.all(np.isfinite(p1)) and np.linalg.norm(p1 - p) > 0
+
+
+def test_sr_step_bf16_split_recovers_from_indefinite_s():
+    """1D TFIM N = 10 near the uniform state with a 1e-4 relative shift: the three-product
+    BF16 split can make the shifted S indefinite (its error is minus the PSD lo.lo^T term);
+    the step then re-forms S with the fourth product and solves.  (The two updates are not
+    compared entry by entry: S~ has a condition number near 1e8 here, so the FP32 and BF16
+    roundings of S move the solution far along its near-null directions.)"""
+    N, M, C, spc = 10, 10, 256, 200
+    p = inputs.rbm_params(N, M, 0.01, seed=1234)
+    s0 = inputs.random_spins(C, N, seed=99)
+    out = {}
+    for prec in (vmc.PREC_FP32, vmc.PREC_BF16SPLIT):
+        with context(lattice(T, N, 1, 1.0, 1.0, 1), n_chains=C, samples_per_chain=spc,
+                     solver=vmc.SOLVER_CHOLESKY_MIXED, shift=1e-4, precision=prec, seed=1) as ctx:
+            vmc.vmc_set_params(ctx, 0, p)
+            vmc.vmc_set_chains(ctx, 0, s0)
+            st = vmc.vmc_sr_step(ctx, 0, 0.02)
+            out[prec] = (st, vmc.vmc_get_params(ctx, 0))
+    for prec, (st, p1) in out.items():
+        assert st.solver_relres <= 1e-10 and np.all(np.isfinite(p1))
+    # same samples (same seed, same sampler), so the energies agree exactly
+    assert out[vmc.PREC_FP32][0].e_mean_re == out[vmc.PREC_BF16SPLIT][0].e_mean_re
+    for prec in out:
+        assert np.linalg.norm(out[prec][1] - p) > 0
