@@ -472,7 +472,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, un
 }
 
 // ---------------------------------------------------------------------------------------
-// Factorisation of one 256-wide panel (columns p0 .. pend, all rows below) in a single
+// Factorisation of one 512-wide panel (columns p0 .. pend, all rows below) in a single
 // cooperative launch.  Per 64-column block k: the panel rows below the block are solved
 // against its inverse (trsm, rows spread over the CTAs), grid barrier, then the rest of
 // the panel receives the block's update (herk tiles over the CTAs) while CTA 0 updates the
@@ -1155,10 +1155,10 @@ static cudaError_t factor(C* A, C* Dinv, int64_t P, unsigned* status, cudaStream
   return cudaSuccess;
 }
 
-// Two-level factorisation: 256-wide panels factored by the SIMT kernels above (64-wide
+// Two-level factorisation: 512-wide panels factored by the cooperative panel kernel (64-wide
 // diagonal blocks, updates restricted to the panel's columns), then the whole trailing
 // matrix receives the panel's Schur complement on the tensor cores (BF16 split, K = 256).
-static constexpr int NBO = 256;
+static constexpr int NBO = 512;
 
 static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, unsigned* status,
                              cudaStream_t st, int64_t* launches) {

@@ -158,7 +158,7 @@ cudaError_t solve_cholesky_fp64(const double2* S, const double2* F, double2* x, 
 cudaError_t split_shift(const double2* S, double nu, int mode, SolveWork& w, cudaStream_t st);
 // FP32 Cholesky of w.A32 + iterative refinement with residuals F - (S + shift) x formed from
 // w.S2 in compensated FP32 arithmetic (hi/lo pairs, error-free products and sums);
-// tc = trailing updates of 256-wide panels on the tensor cores (BF16 split) instead of
+// tc = trailing updates of 512-wide panels on the tensor cores (BF16 split) instead of
 // FP32 SIMT.
 cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mode, double tol,
                                  int maxit, bool tc, SolveWork& w, unsigned* status,
