@@ -1157,7 +1157,7 @@ static cudaError_t factor(C* A, C* Dinv, int64_t P, unsigned* status, cudaStream
 
 // Two-level factorisation: 512-wide panels factored by the cooperative panel kernel (64-wide
 // diagonal blocks, updates restricted to the panel's columns), then the whole trailing
-// matrix receives the panel's Schur complement on the tensor cores (BF16 split, K = 256).
+// matrix receives the panel's Schur complement on the tensor cores (BF16 split, K = 512).
 static constexpr int NBO = 512;
 
 static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, unsigned* status,
