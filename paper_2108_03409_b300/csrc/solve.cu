@@ -74,6 +74,18 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
 constexpr int POTRF_THREADS = 256;
 constexpr int PLD = NB + 1;
 
+// Pivot root: l = sqrt(d), il = 1 / l.  In FP32 from the hardware reciprocal square root
+// (the factor only preconditions the FP64-accurate refinement, and l il = 1 to rounding);
+// in FP64 correctly rounded.
+__device__ __forceinline__ void pivot_root(float d, float* l, float* il) {
+  *il = rsqrtf(d);
+  *l = d * *il;
+}
+__device__ __forceinline__ void pivot_root(double d, double* l, double* il) {
+  *l = sqrt(d);
+  *il = 1.0 / *l;
+}
+
 // (Global loads bypass L1 (ld.global.cg): inside the cooperative panel kernel the block
 // may have been written by other CTAs since this SM last cached it.)
 template <typename C>
@@ -84,6 +96,7 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
   C* li = a + NB * PLD;                       // [64][PLD]: Linv
   C* tt = li + NB * PLD;                      // [64][PLD]: products of the inverse
   C* cb = tt + NB * PLD;                      // [2][64]: published column / row
+  R* dg = reinterpret_cast<R*>(cb + 2 * NB);  // [64]: 1 / L_cc
   const int tid = threadIdx.x;
   {
     // all of a thread's loads are issued before any shared-memory store
@@ -120,7 +133,9 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
         R d = __shfl_sync(0xffffffffu, e[0].x, ((cl & 1) << 4) | cl);
         if (col == cl) {
           if (!(d > (R)0) || !isfinite(d)) { bad = true; d = (R)1; }
-          const R l = sqrt(d), il = (R)1 / l;
+          R l, il;
+          pivot_root(d, &l, &il);
+          if (rg == cl) dg[c] = il;                  // 1 / L_cc for the inverse
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int r = c0 + rg + 16 * i;
@@ -189,7 +204,7 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
     int q2 = 0;
     for (int m = 0; m < 16; ++m) {
       if (rr == m) {
-        const R il = (R)1 / a[(b0 + m) * PLD + b0 + m].x;
+        const R il = dg[b0 + m];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int c = cq + 4 * j;
@@ -479,7 +494,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, un
 // next diagonal tile first and factors it at once (look-ahead), grid barrier.  The panel's
 // first diagonal block is factored before the loop.
 // ---------------------------------------------------------------------------------------
-constexpr size_t PANEL_SMEM = (size_t)(3 * NB * (NB + 1) + 2 * NB) * sizeof(float2);
+constexpr size_t PANEL_SMEM = (size_t)(3 * NB * (NB + 1) + 3 * NB) * sizeof(float2);
 
 __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int64_t P,
                                                     int64_t p0, int64_t pend,
@@ -1110,7 +1125,7 @@ __global__ void __launch_bounds__(256) k_resid_df(const float4* __restrict__ S2,
 // host side
 // ---------------------------------------------------------------------------------------
 template <typename C>
-static constexpr size_t potrf_smem() { return (size_t)(3 * NB * (NB + 1) + 2 * NB) * sizeof(C); }
+static constexpr size_t potrf_smem() { return (size_t)(3 * NB * (NB + 1) + 3 * NB) * sizeof(C); }
 
 template <typename C>
 static cudaError_t set_smem_attrs() {
