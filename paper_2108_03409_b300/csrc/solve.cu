@@ -488,13 +488,19 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, un
 
 // ---------------------------------------------------------------------------------------
 // Factorisation of one 512-wide panel (columns p0 .. pend, all rows below) in a single
-// cooperative launch.  Per 64-column block k: the panel rows below the block are solved
-// against its inverse (trsm, rows spread over the CTAs), grid barrier, then the rest of
-// the panel receives the block's update (herk tiles over the CTAs) while CTA 0 updates the
-// next diagonal tile first and factors it at once (look-ahead), grid barrier.  The panel's
-// first diagonal block is factored before the loop.
+// cooperative launch.  Per 64-column block k (k1 = the next block):
+//   * CTA 0 solves the row block k1 against the block inverse, counts it done, updates the
+//     diagonal tile (k1, k1) and factors it (look-ahead: the critical path is one row block,
+//     one tile and one diagonal factorisation);
+//   * the other CTAs solve the remaining row blocks, count them done, wait (bounded) until
+//     every row block of step k is solved, and apply block k's update to the rest of the
+//     panel (all trapezoid tiles but the diagonal one);
+//   * one grid barrier ends the step.
+// The panel's first diagonal block is factored before the loop.  sync: the grid barrier
+// (3 words) followed by one counter per step, zeroed before the launch.
 // ---------------------------------------------------------------------------------------
 constexpr size_t PANEL_SMEM = (size_t)(3 * NB * (NB + 1) + 3 * NB) * sizeof(float2);
+constexpr int PANEL_MAX_STEPS = 32;                // 64-column blocks per panel (>= NBO / 64)
 
 __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int64_t P,
                                                     int64_t p0, int64_t pend,
@@ -502,36 +508,80 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
                                                     GridBarrier* bar, unsigned* status) {
   extern __shared__ unsigned char csm[];
   const unsigned G = gridDim.x, b = blockIdx.x;
+  unsigned* done = reinterpret_cast<unsigned*>(bar) + 4;
   if (b == 0) potrf_body<float2>(A, P, p0, (int)min((int64_t)NB, P - p0), Dinv + (p0 / NB) * NB * NB, status, csm);
   if (!grid_sync(bar, G, status)) return;
-  for (int64_t k0 = p0; k0 < pend; k0 += NB) {
+  int step = 0;
+  for (int64_t k0 = p0; k0 < pend; k0 += NB, ++step) {
     const int kw = (int)min((int64_t)NB, P - k0);
     const int64_t k1 = k0 + kw, rest = P - k1;
     if (rest <= 0) break;
     const float2* Di = Dinv + (k0 / NB) * NB * NB;
     const int64_t nrb = (rest + NB - 1) / NB;
-    for (int64_t rb = b; rb < nrb; rb += G) {
-      trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm);
-      __syncthreads();
-    }
-    if (!grid_sync(bar, G, status)) return;
-    if (k1 >= pend) break;                         // last block of the panel
-    const int64_t nt = nrb, nct = (pend - k1 + NB - 1) / NB;
-    const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
+    const bool last = k1 >= pend;                  // no update inside the panel after this
     if (b == 0) {
-      // the next diagonal tile (tile 0), then its factorisation; CTA 0 takes no other tile
-      // unless it is alone
-      herk_tile_body<float2>(A, P, k0, kw, k1, k1, csm);
+      trsm_body<float2>(A, P, k0, kw, Di, k1, csm);
       __syncthreads();
       if (G == 1)
+        for (int64_t rb = 1; rb < nrb; ++rb) {
+          trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm);
+          __syncthreads();
+        }
+      if (last) break;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(&done[step], 1u);
+      herk_tile_body<float2>(A, P, k0, kw, k1, k1, csm);
+      __syncthreads();
+      if (G == 1) {
+        const int64_t nt = nrb, nct = (pend - k1 + NB - 1) / NB;
+        const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
         for (int64_t t = 1; t < tiles; ++t) {
           int64_t tm, tn;
           trapezoid_tile(t, nt, &tm, &tn);
           herk_tile_body<float2>(A, P, k0, kw, k1 + tm * NB, k1 + tn * NB, csm);
           __syncthreads();
         }
+      }
       potrf_body<float2>(A, P, k1, (int)min((int64_t)NB, P - k1), Dinv + (k1 / NB) * NB * NB, status, csm);
     } else {
+      unsigned mine = 0;
+      for (int64_t rb = b; rb < nrb; rb += G - 1) {
+        trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm);
+        __syncthreads();
+        ++mine;
+      }
+      if (last) break;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0 && mine) atomicAdd(&done[step], mine);
+      // every row block of this step solved (CTA 0's included) before the panel update
+      {
+        __shared__ int ok;
+        if (threadIdx.x == 0) {
+          ok = 1;
+          volatile unsigned* vd = &done[step];
+          volatile unsigned* vab = &bar->abort;
+          const long long t0 = clock64();
+          unsigned it = 0;
+          while (*vd < (unsigned)nrb) {
+            if (*vab) { ok = 0; break; }
+            if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
+              atomicExch(&bar->abort, 1u);
+              flag_error(status, DEV_ERR_TIMEOUT);
+              ok = 0;
+              break;
+            }
+          }
+          __threadfence();
+        }
+        __syncthreads();
+        const bool go = ok != 0;
+        __syncthreads();
+        if (!go) return;
+      }
+      const int64_t nt = nrb, nct = (pend - k1 + NB - 1) / NB;
+      const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
       for (int64_t t = b; t < tiles; t += G - 1) {
         int64_t tm, tn;
         trapezoid_tile(t, nt, &tm, &tn);
@@ -1174,6 +1224,7 @@ static cudaError_t factor(C* A, C* Dinv, int64_t P, unsigned* status, cudaStream
 // diagonal blocks, updates restricted to the panel's columns), then the whole trailing
 // matrix receives the panel's Schur complement on the tensor cores (BF16 split, K = 512).
 static constexpr int NBO = 512;
+static_assert(NBO / NB <= PANEL_MAX_STEPS, "panel step counters");
 
 static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, unsigned* status,
                              cudaStream_t st, int64_t* launches) {
@@ -1192,7 +1243,7 @@ static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, u
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(w.bar);
   for (int64_t p0 = 0; p0 < P; p0 += NBO) {
     const int64_t pend = std::min<int64_t>(P, p0 + NBO);
-    VMC_TRY(cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st));
+    VMC_TRY(cudaMemsetAsync(bar, 0, (4 + PANEL_MAX_STEPS) * sizeof(unsigned), st));
     void* args[] = {(void*)&A, (void*)&P, (void*)&p0, (void*)&pend, (void*)&Dinv, (void*)&bar,
                     (void*)&status};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3(grid), dim3(256), args,
