@@ -95,8 +95,8 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
   C* a = reinterpret_cast<C*>(psm);           // [64][PLD]: A -> L
   C* li = a + NB * PLD;                       // [64][PLD]: Linv
   C* tt = li + NB * PLD;                      // [64][PLD]: products of the inverse
-  C* cb = tt + NB * PLD;                      // [2][64]: published column / row
-  R* dg = reinterpret_cast<R*>(cb + 2 * NB);  // [64]: 1 / L_cc
+  C* cb = tt + NB * PLD;                      // [2][2][64]: published column pair / row
+  R* dg = reinterpret_cast<R*>(cb + 4 * NB);  // [64]: 1 / L_cc
   const int tid = threadIdx.x;
   {
     // all of a thread's loads are issued before any shared-memory store
@@ -127,38 +127,86 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
       const int r = c0 + rg + 16 * i;
       e[i] = (r < NB) ? a[r * PLD + c0 + col] : mk<C>(0.0, 0.0);
     }
-    for (int cl = 0; cl < 16; ++cl) {
+    // columns in pairs (c, c+1): both owner half-warps are in warp cl/2, which resolves the
+    // 2x2 pivot block by shuffles; one barrier, then a rank-2 update of the later columns
+    for (int cl = 0; cl < 16; cl += 2) {
       const int c = c0 + cl;
-      if ((tid >> 5) == (cl >> 1)) {                 // the warp holding column c's owners
-        R d = __shfl_sync(0xffffffffu, e[0].x, ((cl & 1) << 4) | cl);
+      C* cbA = cb + pb * 2 * NB;                     // column c
+      C* cbB = cbA + NB;                             // column c + 1
+      if ((tid >> 5) == (cl >> 1)) {
+        const int lane = tid & 31;
+        R d0 = __shfl_sync(0xffffffffu, e[0].x, cl);            // (c, c): half 0, rg = cl
+        if (!(d0 > (R)0) || !isfinite(d0)) { bad |= (col == cl); d0 = (R)1; }
+        R l0, il0;
+        pivot_root(d0, &l0, &il0);
         if (col == cl) {
-          if (!(d > (R)0) || !isfinite(d)) { bad = true; d = (R)1; }
-          R l, il;
-          pivot_root(d, &l, &il);
-          if (rg == cl) dg[c] = il;                  // 1 / L_cc for the inverse
+          if (rg == cl) dg[c] = il0;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const int r = c0 + rg + 16 * i;
             if (r > c && r < NB) {
-              e[i].x *= il;
-              e[i].y *= il;
-              cb[pb * NB + r] = e[i];
+              e[i].x *= il0;
+              e[i].y *= il0;
             } else if (r == c) {
-              e[i] = mk<C>((double)l, 0.0);
+              e[i] = mk<C>((double)l0, 0.0);
             }
+          }
+        }
+        // column c+1: subtract L[r][c] conj(L[c+1][c]) (L[r][c] from the partner lane)
+        C lcol[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          lcol[i].x = __shfl_sync(0xffffffffu, e[i].x, lane & 15);
+          lcol[i].y = __shfl_sync(0xffffffffu, e[i].y, lane & 15);
+        }
+        const R wr = __shfl_sync(0xffffffffu, e[0].x, cl + 1);  // L[c+1][c]: half 0, rg = cl+1
+        const R wi = __shfl_sync(0xffffffffu, e[0].y, cl + 1);
+        if (col == cl + 1) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = c0 + rg + 16 * i;
+            if (r > c && r < NB) {
+              e[i].x -= lcol[i].x * wr + lcol[i].y * wi;
+              e[i].y -= lcol[i].y * wr - lcol[i].x * wi;
+            }
+          }
+        }
+        R d1 = __shfl_sync(0xffffffffu, e[0].x, 16 + cl + 1);   // (c+1, c+1): half 1
+        if (!(d1 > (R)0) || !isfinite(d1)) { bad |= (col == cl + 1); d1 = (R)1; }
+        R l1, il1;
+        pivot_root(d1, &l1, &il1);
+        if (col == cl + 1) {
+          if (rg == cl + 1) dg[c + 1] = il1;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = c0 + rg + 16 * i;
+            if (r > c + 1 && r < NB) {
+              e[i].x *= il1;
+              e[i].y *= il1;
+              cbB[r] = e[i];
+            } else if (r == c + 1) {
+              e[i] = mk<C>((double)l1, 0.0);
+            }
+          }
+        }
+        if (col == cl) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = c0 + rg + 16 * i;
+            if (r > c && r < NB) cbA[r] = e[i];
           }
         }
       }
       __syncthreads();
-      if (col > cl) {
-        const C lc = cb[pb * NB + c0 + col];          // L[c0+col][c]
+      if (col > cl + 1) {
+        const C la = cbA[c0 + col], lb = cbB[c0 + col];         // L[c0+col][c], [c+1]
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int r = c0 + rg + 16 * i;
           if (r >= c0 + col && r < NB) {
-            const C lr = cb[pb * NB + r];
-            e[i].x -= lr.x * lc.x + lr.y * lc.y;       // e -= L[r][c] conj(L[c0+col][c])
-            e[i].y -= lr.y * lc.x - lr.x * lc.y;
+            const C ra = cbA[r], rb = cbB[r];
+            e[i].x -= ra.x * la.x + ra.y * la.y + rb.x * lb.x + rb.y * lb.y;
+            e[i].y -= ra.y * la.x - ra.x * la.y + rb.y * lb.x - rb.x * lb.y;
           }
         }
       }
@@ -499,7 +547,7 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, un
 // The panel's first diagonal block is factored before the loop.  sync: the grid barrier
 // (3 words) followed by one counter per step, zeroed before the launch.
 // ---------------------------------------------------------------------------------------
-constexpr size_t PANEL_SMEM = (size_t)(3 * NB * (NB + 1) + 3 * NB) * sizeof(float2);
+constexpr size_t PANEL_SMEM = (size_t)(3 * NB * (NB + 1) + 5 * NB) * sizeof(float2);
 constexpr int PANEL_MAX_STEPS = 32;                // 64-column blocks per panel (>= NBO / 64)
 
 __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int64_t P,
@@ -1175,7 +1223,7 @@ __global__ void __launch_bounds__(256) k_resid_df(const float4* __restrict__ S2,
 // host side
 // ---------------------------------------------------------------------------------------
 template <typename C>
-static constexpr size_t potrf_smem() { return (size_t)(3 * NB * (NB + 1) + 3 * NB) * sizeof(C); }
+static constexpr size_t potrf_smem() { return (size_t)(3 * NB * (NB + 1) + 5 * NB) * sizeof(C); }
 
 template <typename C>
 static cudaError_t set_smem_attrs() {
