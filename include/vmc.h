@@ -240,6 +240,26 @@ vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spin
 /* Warps per block chosen by the autotuner (0 before the first vmc_sample_all). */
 int vmc_autotuned_warps_per_block(const vmc_ctx* ctx);
 
+/* Checkpoint / resume.  vmc_get_state writes everything the method's trajectory depends on
+ * into a host buffer: per lattice the FP64 parameters, the chains, the sweep counter (the
+ * Philox counter of the local moves), the thermalised flag and, with a learned proposal,
+ * its parameters, Adam moments, step and round counters (the seed is part of vmc_config).
+ * With buf == NULL it only stores the required size in *len; otherwise *len (in: the
+ * buffer's size) receives the bytes written.  vmc_set_state restores a state into a context
+ * created with the same configuration and lattices (checked: VMC_ERR_ARG otherwise, the
+ * context untouched); the continuation is then identical to the original's.  Both
+ * synchronise. */
+vmc_status vmc_get_state(vmc_ctx* ctx, void* buf, size_t* len);
+vmc_status vmc_set_state(vmc_ctx* ctx, const void* buf, size_t len);
+
+/* Failure-path self-test (no GPU fault): which = 0 runs the cooperative kernels' bounded
+ * flag wait on a word that nothing sets, which = 1 the tensor-core kernels' bounded mbarrier
+ * wait on a barrier that nothing arrives at.  Each gives up after about 2e9 SM clock cycles
+ * (about a second), records the expiry in the context's status word and returns: the call
+ * returns VMC_ERR_TIMEOUT (the designed outcome) and the context stays usable.  Allocates a
+ * two-word scratch; synchronises. */
+vmc_status vmc_selftest_wait_timeout(vmc_ctx* ctx, int which);
+
 /* Number of kernel launches the library has issued on this context since it was created
  * (a counter kept by the host code). */
 int64_t vmc_kernel_launches(const vmc_ctx* ctx);

@@ -1046,4 +1046,134 @@ vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spin
 
 int vmc_autotuned_warps_per_block(const vmc_ctx* ctx) { return ctx ? ctx->tuned_wpb : 0; }
 
+
+// ---- checkpoint / resume ------------------------------------------------------------------
+namespace {
+constexpr uint64_t kStateMagic = 0x3130315354434d56ull;   // "VMCSTO01" (little endian)
+
+struct StateHeader {
+  uint64_t magic;
+  uint64_t bytes;                 // whole buffer
+  int32_t n_lattices, n_chains, made_hidden, reserved;
+};
+
+struct LatticeRecord {
+  int32_t N, M, model, thermalized;
+  int64_t P;
+  uint64_t sweep, made_round;
+  int32_t made_t, reserved;
+};
+
+size_t state_bytes(const vmc_ctx* ctx) {
+  size_t b = sizeof(StateHeader);
+  for (const auto& L : ctx->lats) {
+    b += sizeof(LatticeRecord) + (size_t)L.P * sizeof(double2) + (size_t)ctx->cfg.n_chains * L.N;
+    if (ctx->cfg.made_hidden > 0) b += 3 * (size_t)made_nparams(L.N, ctx->cfg.made_hidden) * sizeof(float);
+  }
+  return b;
+}
+}  // namespace
+
+vmc_status vmc_get_state(vmc_ctx* ctx, void* buf, size_t* len) {
+  if (!ctx || !len) return VMC_ERR_ARG;
+  const size_t need = state_bytes(ctx);
+  if (!buf) {
+    *len = need;
+    return VMC_OK;
+  }
+  if (*len < need) return fail(ctx, VMC_ERR_ARG, "state buffer too small");
+  uint8_t* p = static_cast<uint8_t*>(buf);
+  StateHeader h{kStateMagic, need, (int32_t)ctx->lats.size(), ctx->cfg.n_chains,
+                ctx->cfg.made_hidden, 0};
+  memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  for (auto& L : ctx->lats) {
+    LatticeRecord r{L.N, L.M, L.lat.model, L.thermalized ? 1 : 0, L.P, L.sweep, L.made_round,
+                    L.made_t, 0};
+    memcpy(p, &r, sizeof(r));
+    p += sizeof(r);
+    CK(cudaMemcpyAsync(p, L.params, (size_t)L.P * sizeof(double2), cudaMemcpyDeviceToHost, ctx->st), "get_state");
+    p += (size_t)L.P * sizeof(double2);
+    CK(cudaMemcpyAsync(p, L.chains, (size_t)ctx->cfg.n_chains * L.N, cudaMemcpyDeviceToHost, ctx->st), "get_state");
+    p += (size_t)ctx->cfg.n_chains * L.N;
+    if (ctx->cfg.made_hidden > 0) {
+      const size_t nb = (size_t)made_nparams(L.N, ctx->cfg.made_hidden) * sizeof(float);
+      const float* src[3] = {L.made, L.made_m, L.made_v};
+      for (const float* q : src) {
+        CK(cudaMemcpyAsync(p, q, nb, cudaMemcpyDeviceToHost, ctx->st), "get_state");
+        p += nb;
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(ctx->st), "get_state");
+  *len = need;
+  return VMC_OK;
+}
+
+vmc_status vmc_set_state(vmc_ctx* ctx, const void* buf, size_t len) {
+  if (!ctx || !buf) return VMC_ERR_ARG;
+  if (len < sizeof(StateHeader)) return fail(ctx, VMC_ERR_ARG, "state buffer too small");
+  const uint8_t* p = static_cast<const uint8_t*>(buf);
+  StateHeader h;
+  memcpy(&h, p, sizeof(h));
+  p += sizeof(h);
+  if (h.magic != kStateMagic) return fail(ctx, VMC_ERR_ARG, "not a vmc state");
+  if (h.bytes != state_bytes(ctx) || len < h.bytes || h.n_lattices != (int32_t)ctx->lats.size() ||
+      h.n_chains != ctx->cfg.n_chains || h.made_hidden != ctx->cfg.made_hidden)
+    return fail(ctx, VMC_ERR_ARG, "state does not match this context's configuration");
+  // validate every record before touching the context
+  {
+    const uint8_t* q = p;
+    for (auto& L : ctx->lats) {
+      LatticeRecord r;
+      memcpy(&r, q, sizeof(r));
+      if (r.N != L.N || r.M != L.M || r.model != L.lat.model || r.P != L.P)
+        return fail(ctx, VMC_ERR_ARG, "state does not match this context's lattices");
+      q += sizeof(r) + (size_t)L.P * sizeof(double2) + (size_t)ctx->cfg.n_chains * L.N;
+      if (ctx->cfg.made_hidden > 0) q += 3 * (size_t)made_nparams(L.N, ctx->cfg.made_hidden) * sizeof(float);
+    }
+  }
+  for (auto& L : ctx->lats) {
+    LatticeRecord r;
+    memcpy(&r, p, sizeof(r));
+    p += sizeof(r);
+    CK(cudaMemcpyAsync(L.params, p, (size_t)L.P * sizeof(double2), cudaMemcpyHostToDevice, ctx->st), "set_state");
+    p += (size_t)L.P * sizeof(double2);
+    CK(cudaMemcpyAsync(L.chains, p, (size_t)ctx->cfg.n_chains * L.N, cudaMemcpyHostToDevice, ctx->st), "set_state");
+    p += (size_t)ctx->cfg.n_chains * L.N;
+    L.sweep = r.sweep;
+    L.thermalized = r.thermalized != 0;
+    L.chain_cache = false;
+    vmc_status s;
+    if ((s = refresh_fp32(ctx, L))) return s;
+    if (ctx->cfg.made_hidden > 0) {
+      const size_t nb = (size_t)made_nparams(L.N, ctx->cfg.made_hidden) * sizeof(float);
+      float* dst[3] = {L.made, L.made_m, L.made_v};
+      for (float* q : dst) {
+        CK(cudaMemcpyAsync(q, p, nb, cudaMemcpyHostToDevice, ctx->st), "set_state");
+        p += nb;
+      }
+      CK(launch_made_transpose(made_of(ctx, L), ctx->st), "made_transpose");
+      ++ctx->launches;
+      L.made_t = r.made_t;
+      L.made_round = r.made_round;
+    }
+  }
+  ctx->g_therm = -1;                                  // batched descriptors are stale
+  CK(cudaStreamSynchronize(ctx->st), "set_state");
+  return VMC_OK;
+}
+
+vmc_status vmc_selftest_wait_timeout(vmc_ctx* ctx, int which) {
+  if (!ctx || which < 0 || which > 1) return VMC_ERR_ARG;
+  unsigned* word = nullptr;
+  CK(cudaMalloc(&word, 2 * sizeof(unsigned)), "selftest");
+  cudaError_t e = which == 0 ? launch_selftest_flag_wait(word, ctx->status, ctx->st)
+                             : launch_selftest_mbar_wait(ctx->status, ctx->st);
+  ++ctx->launches;
+  vmc_status s = (e == cudaSuccess) ? check_status(ctx, "selftest") : cuda_fail(ctx, e, "selftest");
+  cudaFree(word);
+  return s;
+}
+
 }  // extern "C"

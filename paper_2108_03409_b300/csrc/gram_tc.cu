@@ -577,6 +577,28 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ C
   if (threadIdx.x == 0 && *abort_flag) flag_error(status, DEV_ERR_TIMEOUT);
 }
 
+// Failure-path self-test: the tensor-core kernels' bounded mbarrier wait on a barrier that
+// nothing arrives at must give up, set the abort flag and report DEV_ERR_TIMEOUT.
+__global__ void k_selftest_mbar_wait(unsigned* status) {
+  using namespace tc;
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(smem_u32(&bar), 0, &abort_flag)) flag_error(status, DEV_ERR_TIMEOUT);
+  }
+}
+
+cudaError_t launch_selftest_mbar_wait(unsigned* status, cudaStream_t st) {
+  k_selftest_mbar_wait<<<1, 32, 0, st>>>(status);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------

@@ -1219,6 +1219,19 @@ __global__ void __launch_bounds__(256) k_resid_df(const float4* __restrict__ S2,
   }
 }
 
+// Failure-path self-test: the cooperative kernels' bounded flag wait on a word that nothing
+// sets (word[0] = 0, word[1] = the abort word) must give up, set DEV_ERR_TIMEOUT and return.
+__global__ void k_selftest_flag_wait(unsigned* word, unsigned* status) {
+  if (threadIdx.x == 0) wait_at_least(word, 1u, word + 1, status);
+}
+
+cudaError_t launch_selftest_flag_wait(unsigned* word2, unsigned* status, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(word2, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  k_selftest_flag_wait<<<1, 32, 0, st>>>(word2, status);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------

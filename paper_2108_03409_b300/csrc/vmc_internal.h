@@ -180,6 +180,10 @@ cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo,
                              const __nv_bfloat16* Bs, int64_t b_rows, int64_t K,
                              int kb_per_chunk, float* out, unsigned* status, cudaStream_t st);
 
+// failure-path self-tests of the bounded waits (a flag / an mbarrier that nothing sets)
+cudaError_t launch_selftest_flag_wait(unsigned* word2, unsigned* status, cudaStream_t st);
+cudaError_t launch_selftest_mbar_wait(unsigned* status, cudaStream_t st);
+
 // ---- cg.cu ----------------------------------------------------------------------------
 struct CgProblem {
   const int8_t* spins;            // [n][N]

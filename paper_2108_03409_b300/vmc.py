@@ -64,7 +64,7 @@ EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_
             "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve",
             "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
             "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned", "vmc_sample_all",
-            "vmc_autotuned_warps_per_block"]
+            "vmc_autotuned_warps_per_block", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout"]
 
 _lib = None
 
@@ -109,6 +109,9 @@ def load(path: str = LIB_PATH):
         "vmc_sample_learned": (i32, [P, i32, i32, P, P, ctypes.POINTER(f64)]),
         "vmc_sample_all": (i32, [P, i32, i32, P, P, i32, ctypes.POINTER(f64)]),
         "vmc_autotuned_warps_per_block": (i32, [P]),
+        "vmc_get_state": (i32, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
+        "vmc_set_state": (i32, [P, P, ctypes.c_size_t]),
+        "vmc_selftest_wait_timeout": (i32, [P, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -316,3 +319,22 @@ def vmc_sample_all(ctx, n_therm, n_samples, spins_out=None, eloc_out=None, use_g
 
 def vmc_autotuned_warps_per_block(ctx) -> int:
     return int(load().vmc_autotuned_warps_per_block(ctx))
+
+
+def vmc_get_state(ctx) -> bytes:
+    """Checkpoint of the context (parameters, chains, RNG counters, learned proposal)."""
+    n = ctypes.c_size_t(0)
+    _check(ctx, load().vmc_get_state(ctx, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(ctx, load().vmc_get_state(ctx, buf, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def vmc_set_state(ctx, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(ctx, load().vmc_set_state(ctx, buf, len(state)))
+
+
+def vmc_selftest_wait_timeout(ctx, which: int) -> int:
+    """Run a bounded wait that nothing satisfies; returns the status (VMC_ERR_TIMEOUT expected)."""
+    return int(load().vmc_selftest_wait_timeout(ctx, int(which)))
