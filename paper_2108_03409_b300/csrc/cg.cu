@@ -425,24 +425,31 @@ __global__ void k_build_a2(const float2* __restrict__ T, const float2* __restric
 
 // y_k = (1/n) sum_q conj(Obar_qk) u_q from the K-chunk partials G[kc][row][col] (FP64 sum):
 // a_i: rows 2M/2M+1, col i; b_j: rows 2j/2j+1, col N; W_ji: rows 2j/2j+1, col i
-__global__ void k_reduce_y(const float* __restrict__ part, int nkc, int64_t a_rows,
-                           int64_t b_rows, int N, int M, int64_t n, double2* __restrict__ y) {
+// four threads per entry (chunks c = q, q + 4, ...), then a fixed-order shuffle sum
+__global__ void __launch_bounds__(256) k_reduce_y(const float* __restrict__ part, int nkc,
+                                                  int64_t a_rows, int64_t b_rows, int N, int M,
+                                                  int64_t n, double2* __restrict__ y) {
   const int64_t P = (int64_t)N + M + (int64_t)N * M;
   const double inv = 1.0 / (double)n;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
-       k += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t k = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
+  const int q = threadIdx.x & 3;
+  double re = 0.0, im = 0.0;
+  if (k < P) {
     int64_t row, col;
     if (k < N) { row = 2 * (int64_t)M; col = k; }
     else if (k < N + M) { row = 2 * (k - N); col = N; }
     else { const int64_t r = k - N - M; row = 2 * (r / N); col = r % N; }
-    double re = 0.0, im = 0.0;
-    for (int c = 0; c < nkc; ++c) {
+    for (int c = q; c < nkc; c += 4) {
       const float* g = part + (int64_t)c * a_rows * b_rows;
       re += (double)g[row * b_rows + col];
       im += (double)g[(row + 1) * b_rows + col];
     }
-    y[k] = make_double2(re * inv, im * inv);
   }
+  re += __shfl_xor_sync(0xffffffffu, re, 1);
+  im += __shfl_xor_sync(0xffffffffu, im, 1);
+  re += __shfl_xor_sync(0xffffffffu, re, 2);
+  im += __shfl_xor_sync(0xffffffffu, im, 2);
+  if (k < P && q == 0) y[k] = make_double2(re * inv, im * inv);
 }
 
 static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, double2* q,
@@ -472,7 +479,7 @@ static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, 
   k_build_a2<<<ga, 256, 0, st>>>(pb.T, w.u, w.ustats, n, M, a_rows, ldK, w.Ahi, w.Alo);
   VMC_TRY(launch_cg_ohu_tc(w.Ahi, w.Alo, a_rows, w.Bs, b_rows, ldK, CG_KB_PER_CHUNK, w.part2,
                            pb.status, st));
-  k_reduce_y<<<g1d(P), 256, 0, st>>>(w.part2, nkc, a_rows, b_rows, N, M, n, w.y);
+  k_reduce_y<<<(unsigned)((P + 63) / 64), 256, 0, st>>>(w.part2, nkc, a_rows, b_rows, N, M, n, w.y);
   k_add_diag<<<g1d(P), 256, 0, st>>>(w.y, w.D, p, P, q);
   *launches += 12;
   return cudaGetLastError();

@@ -429,8 +429,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ C
   using namespace tc;
   constexpr int NPL = (SPLIT_A ? 2 : 1) + (SPLIT_B ? 2 : 1);
   constexpr int SBYTES = NPL * TILE_BYTES;
-  // EPI_OV has K = N (a few blocks): two stages, so that two CTAs fit on an SM
-  constexpr int NST = (EPI == EPI_OV) ? 2 : ((NPL == 4) ? 3 : 4);
+  // two stages, so that two CTAs share an SM (EPI_OV has K = N, a few blocks; EPI_STORE
+  // overlaps one CTA's epilogue with the other's loads)
+  constexpr int NST = (NPL == 4) ? 3 : 2;
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
                                              ~uintptr_t(1023));
@@ -442,6 +443,26 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ C
   const int kb0 = kc * kb_per_chunk, kb1 = min(nkb, kb0 + kb_per_chunk);
   const int nk = kb1 - kb0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // EPI_OV: this thread's row of t for the tile's 64 hidden units is loaded now, so that
+  // the loads overlap the main loop (t does not depend on the products)
+  float2 tp[EPI == EPI_OV ? 64 : 1];
+  if (EPI == EPI_OV) {
+    const int64_t m = (int64_t)bm * BM + threadIdx.x;
+    const int jb = bn * (BN / 2);
+    if (m < n && (M & 1) == 0 && jb + 64 <= M) {
+      const float4* tq = reinterpret_cast<const float4*>(T + m * M + jb);
+#pragma unroll
+      for (int h = 0; h < 32; ++h) {
+        const float4 f = tq[h];
+        tp[2 * h] = make_float2(f.x, f.y);
+        tp[2 * h + 1] = make_float2(f.z, f.w);
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < 64; ++h)
+        tp[h] = (m < n && jb + h < M) ? T[m * M + jb + h] : make_float2(0.f, 0.f);
+    }
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2 * NST + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
     *abort_flag = 0;
@@ -527,32 +548,21 @@ k_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ C
     } else {
       // rows 2M, 2M+1 of B carry v_a: the pseudo-unit j = M adds sum_i s_qi v_a,i as is
       float ar = 0.f, ai = 0.f;
+#pragma unroll
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
         const int jb = bn * (BN / 2) + (c0 >> 1);
         if (m < n && jb < M) {
-          float2 t[16];
-          if ((M & 1) == 0 && jb + 16 <= M) {
-            const float4* tp = reinterpret_cast<const float4*>(T + m * M + jb);
-#pragma unroll
-            for (int h = 0; h < 8; ++h) {
-              const float4 f = tp[h];
-              t[2 * h] = make_float2(f.x, f.y);
-              t[2 * h + 1] = make_float2(f.z, f.w);
-            }
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < 16; ++jj) t[jj] = (jb + jj < M) ? T[m * M + jb + jj] : make_float2(0.f, 0.f);
-          }
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
             const int j = jb + jj;
+            const float2 t = tp[(c0 >> 1) + jj];
             if (j < M) {
               const float2 b = vb[j];
               const float zr = v[2 * jj] + b.x, zi = v[2 * jj + 1] + b.y;
-              ar = fmaf(t[jj].x, zr, fmaf(-t[jj].y, zi, ar));
-              ai = fmaf(t[jj].x, zi, fmaf(t[jj].y, zr, ai));
+              ar = fmaf(t.x, zr, fmaf(-t.y, zi, ar));
+              ai = fmaf(t.x, zi, fmaf(t.y, zr, ai));
             } else if (j == M) {
               ar += v[2 * jj];
               ai += v[2 * jj + 1];
@@ -721,7 +731,7 @@ static cudaError_t gemm_launch(const CUtensorMap& ahi, const CUtensorMap& alo,
                                int64_t out_ld, const float2* T, const float2* vb, int M,
                                int64_t n, float2* part, unsigned* status, cudaStream_t st) {
   constexpr int NPL = (SA ? 2 : 1) + (SB ? 2 : 1);
-  constexpr int NST = (EPI == tc::EPI_OV) ? 2 : ((NPL == 4) ? 3 : 4);
+  constexpr int NST = (NPL == 4) ? 3 : 2;
   constexpr int smem = 1024 + NST * NPL * tc::TILE_BYTES + 256;
   static bool attr = false;
   if (!attr) {

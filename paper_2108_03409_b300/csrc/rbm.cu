@@ -25,27 +25,26 @@ __global__ void k_param_prep(const double2* __restrict__ p, int N, int M, float2
   }
 }
 
-// Move tables (see RbmDev): D from the FP64 W, complex cosh, sinh and tanh in FP64, rounded
-// once to FP32.
-__global__ void k_move_tables(const double2* __restrict__ p, int N, int M, int model, int Lx,
-                              int Ly, float4* __restrict__ mcs, float2* __restrict__ mth) {
-  const int moves = model == 1 ? num_bonds(Lx, Ly) : N;
-  const int64_t total = (int64_t)moves * M;
+// Move tables (see RbmDev), one block per move: D from the FP64 W, tanh D and log cosh D in
+// FP64, the tanh rounded once to FP32 and the log cosh summed over k in FP64 first.
+//   log cosh z = z' - ln 2 + log(1 + exp(-2 z')),  z' = z or -z with Re z' >= 0,
+// which stays finite for any |Re D|.
+__global__ void __launch_bounds__(128) k_move_tables(const double2* __restrict__ p, int N, int M,
+                                                     int model, int Lx, int Ly,
+                                                     float2* __restrict__ mth,
+                                                     float2* __restrict__ mlc) {
+  const int q = blockIdx.x;
   const double2* W = p + N + M;                  // W[k][i] at k * N + i
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(e / M), k = (int)(e % M);
-    double dx, dy;
-    if (model == 1) {
-      int i, j;
-      bond_ends(Lx, Ly, q, &i, &j);
-      const double2 wi = W[(int64_t)k * N + i], wj = W[(int64_t)k * N + j];
-      dx = 2.0 * (wi.x - wj.x);
-      dy = 2.0 * (wi.y - wj.y);
-    } else {
-      const double2 w = W[(int64_t)k * N + q];
-      dx = 2.0 * w.x;
-      dy = 2.0 * w.y;
+  int i = q, j = -1;
+  if (model == 1) bond_ends(Lx, Ly, q, &i, &j);
+  double lre = 0.0, lim = 0.0;
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    const double2 wi = W[(int64_t)k * N + i];
+    double dx = 2.0 * wi.x, dy = 2.0 * wi.y;
+    if (j >= 0) {
+      const double2 wj = W[(int64_t)k * N + j];
+      dx -= 2.0 * wj.x;
+      dy -= 2.0 * wj.y;
     }
     double sy, cy;
     sincos(dy, &sy, &cy);
@@ -53,17 +52,38 @@ __global__ void k_move_tables(const double2* __restrict__ p, int N, int M, int m
     const double cr = chx * cy, ci = shx * sy;   // cosh(dx + i dy)
     const double sr = shx * cy, si = chx * sy;   // sinh(dx + i dy)
     const double den = cr * cr + ci * ci;
-    mcs[e] = make_float4((float)cr, (float)ci, (float)sr, (float)si);
-    mth[e] = make_float2((float)((sr * cr + si * ci) / den), (float)((si * cr - sr * ci) / den));
+    mth[(int64_t)q * M + k] =
+        make_float2((float)((sr * cr + si * ci) / den), (float)((si * cr - sr * ci) / den));
+    const double zx = dx >= 0.0 ? dx : -dx, zy = dx >= 0.0 ? dy : -dy;
+    const double e = exp(-2.0 * zx);
+    double s2, c2;
+    sincos(-2.0 * zy, &s2, &c2);
+    const double wr = 1.0 + e * c2, wim = e * s2;
+    lre += zx - 0.69314718055994530942 + 0.5 * log(wr * wr + wim * wim);
+    lim += zy + atan2(wim, wr);
+  }
+  __shared__ double red[2][4];
+  for (int o = 16; o > 0; o >>= 1) {
+    lre += __shfl_xor_sync(0xffffffffu, lre, o);
+    lim += __shfl_xor_sync(0xffffffffu, lim, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = lre;
+    red[1][threadIdx.x >> 5] = lim;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double re = red[0][0] + red[0][1] + red[0][2] + red[0][3];
+    const double im = red[1][0] + red[1][1] + red[1][2] + red[1][3];
+    const double twopi = 6.28318530717958647692;
+    mlc[q] = make_float2((float)re, (float)(im - twopi * rint(im / twopi)));
   }
 }
 
 cudaError_t launch_move_tables(const double2* p, int N, int M, int model, int Lx, int Ly,
-                               float4* mcs, float2* mth, cudaStream_t st) {
+                               float2* mth, float2* mlc, cudaStream_t st) {
   const int moves = model == 1 ? num_bonds(Lx, Ly) : N;
-  const int64_t total = (int64_t)moves * M;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
-  k_move_tables<<<blocks, 256, 0, st>>>(p, N, M, model, Lx, Ly, mcs, mth);
+  k_move_tables<<<moves, 128, 0, st>>>(p, N, M, model, Lx, Ly, mth, mlc);
   return cudaGetLastError();
 }
 

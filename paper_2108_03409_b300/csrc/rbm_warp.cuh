@@ -58,11 +58,13 @@ __device__ __forceinline__ float2 warp_logpsi(const RbmDev& R, const int8_t* s, 
 
 // A move q (a site flip, or a bond exchange of anti-parallel spins) with s_i the spin of
 // its first site shifts theta_k by -s_i D_qk (D from the move tables):
-//   cosh(theta - s_i D) / cosh(theta) = cosh D - s_i t sinh D          (t = tanh theta)
+//   cosh(theta - s_i D) / cosh(theta) = cosh D (1 - s_i t tanh D)      (t = tanh theta)
 //   tanh(theta - s_i D) = (t - s_i tanh D) / (1 - s_i t tanh D)
-__device__ __forceinline__ float2 move_ratio(float2 t, float4 cs, float si) {
-  const float2 ts = cmul(t, make_float2(cs.z, cs.w));
-  return make_float2(fmaf(-si, ts.x, cs.x), fmaf(-si, ts.y, cs.y));
+// so a proposal reads one complex number per hidden unit (tanh D_qk) and adds the move's
+// precomputed sum_k log cosh D_qk once.
+__device__ __forceinline__ float2 move_factor(float2 t, float2 th, float si) {
+  const float2 p = cmul(t, th);
+  return make_float2(fmaf(-si, p.x, 1.f), -si * p.y);
 }
 
 __device__ __forceinline__ float2 move_tanh_shift(float2 t, float2 th, float si) {
@@ -81,11 +83,11 @@ __device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
                                                  const float2 (&t)[MPL], int q, float si) {
   float lr = 0.f, li = 0.f;
   float2 prod = make_float2(1.f, 0.f);
-  const float4* row = R.mcs + (int64_t)q * R.M;
+  const float2* row = R.mth + (int64_t)q * R.M;
 #pragma unroll
   for (int k = 0; k < MPL; ++k) {
     int hj = lane + 32 * k;
-    if (hj < R.M) prod = cmul(prod, move_ratio(t[k], row[hj], si));
+    if (hj < R.M) prod = cmul(prod, move_factor(t[k], row[hj], si));
     if ((k & 3) == 3 && k != MPL - 1) {
       const float m2 = fmaf(prod.x, prod.x, prod.y * prod.y);
       if (m2 > 1e30f || m2 < 1e-30f) {
@@ -97,7 +99,8 @@ __device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
   }
   lr += 0.5f * logf(fmaf(prod.x, prod.x, prod.y * prod.y));
   li += atan2f(prod.y, prod.x);
-  return make_float2(warp_sum(lr), warp_sum(li));
+  const float2 c = R.mlc[q];
+  return make_float2(warp_sum(lr) + c.x, warp_sum(li) + c.y);
 }
 
 // E_loc(s) = sum_s' H_ss' psi(s')/psi(s) from the cached t = tanh theta(s) (Eq. Oloc).
@@ -148,13 +151,18 @@ __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, i
 // a3/a4 + a6 (+ the t factors of a7): Metropolis sweeps with t = tanh theta cached in
 // registers.  One warp per chain.  For a proposal s -> s' that changes theta by -d_k
 // (d_k = 2 s_i W_ki, plus 2 s_j W_kj for an exchange),
-//   psi(s')/psi(s) = exp(a-term) * prod_k [cosh d_k - t_k sinh d_k],
+//   psi(s')/psi(s) = exp(a-term) * prod_k cosh d_k * prod_k [1 - t_k tanh d_k],
 // and the acceptance needs only its modulus squared.  On acceptance
 // t_k <- tanh(theta_k - d_k) = (t_k - tanh d_k) / (1 - t_k tanh d_k).  Random numbers for
 // 32 consecutive steps are drawn in parallel (lane q draws step t0+q) and broadcast.  At
-// every record point theta is recomputed from the spins (no drift), and the sample's
-// spins, log psi, E_loc (fused, from the cached t) and t are written.
+// record points the sample's spins, log psi, E_loc (fused, from the cached t) and t are
+// written.  theta is recomputed from the spins (which removes the rounding drift of the
+// t updates) at the start, at a record point where log psi is wanted, and at a record
+// point after kResyncAccepts accepted moves since the last recomputation (each update
+// adds a few units in the last place to t, so the drift stays near 1e-6 relative).
 // ---------------------------------------------------------------------------------------
+static constexpr int kResyncAccepts = 128;
+
 template <int MPL>
 __device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, int lane,
                                               float2 (&t)[MPL], bool want_logpsi) {
@@ -203,6 +211,7 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
   const uint32_t K = HEIS ? (uint32_t)L.nb : (uint32_t)N;
   const int total = A.n_therm + A.n_samples * A.sweeps_per_sample;
   unsigned long long n_acc = 0;
+  int since_resync = 0;
   bool bad = false;
 
   for (int sw = 0; sw < total; ++sw) {
@@ -232,7 +241,7 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
         for (int k = 0; k < MPL; ++k) {
           const int hj = lane + 32 * k;
           if (hj < M) {
-            const float2 r = move_ratio(t[k], R.mcs[qrow + hj], si);
+            const float2 r = move_factor(t[k], R.mth[qrow + hj], si);
             prod *= fmaf(r.x, r.x, r.y * r.y);
           }
           if ((k & 7) == 7 || k == MPL - 1) {
@@ -240,7 +249,7 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
             prod = 1.f;
           }
         }
-        const float two_re_delta = warp_sum(lsum) + two_re_da;
+        const float two_re_delta = warp_sum(lsum) + 2.f * R.mlc[idx].x + two_re_da;
         if (logu < two_re_delta) {
 #pragma unroll
           for (int k = 0; k < MPL; ++k) {
@@ -254,6 +263,7 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
           }
           __syncwarp();
           ++n_acc;
+          ++since_resync;
         }
       }
     }
@@ -261,7 +271,11 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
     if (after > 0 && after % A.sweeps_per_sample == 0) {
       const int64_t rec = after / A.sweeps_per_sample - 1;
       const int64_t qs = rec * A.C + chain;
-      const float2 lp = warp_resync<MPL>(R, s, lane, t, A.logpsi_out != nullptr);
+      float2 lp = make_float2(0.f, 0.f);
+      if (A.logpsi_out || since_resync >= kResyncAccepts) {
+        lp = warp_resync<MPL>(R, s, lane, t, A.logpsi_out != nullptr);
+        since_resync = 0;
+      }
       if (A.t_out)
 #pragma unroll
         for (int k = 0; k < MPL; ++k) {

@@ -15,10 +15,11 @@ struct RbmDev {
   const float2* b;    // [M]
   const float2* Wt;   // [N][M]  (W transposed)
   // move tables: for move q (site q of a TFIM flip, bond q of a Heisenberg exchange) with
-  // D_qk = 2 W_kq (flip) or 2 (W_ki - W_kj) (bond (i, j)): mcs[q][k] = {cosh D, sinh D},
-  // mth[q][k] = tanh D.  A move with s_i changes theta_k by -s_i D_qk.
-  const float4* mcs;  // [moves][M]
+  // D_qk = 2 W_kq (flip) or 2 (W_ki - W_kj) (bond (i, j)): mth[q][k] = tanh D_qk and
+  // mlc[q] = sum_k log cosh D_qk (real part, and imaginary part reduced to (-pi, pi]).  A
+  // move with s_i changes theta_k by -s_i D_qk.
   const float2* mth;  // [moves][M]
+  const float2* mlc;  // [moves]
 };
 
 struct LatDev {
@@ -46,7 +47,7 @@ struct SampleArgs {
 // ---- rbm.cu -------------------------------------------------------------------------
 // move tables of the lattice's model from the FP64 parameters (computed in FP64)
 cudaError_t launch_move_tables(const double2* p, int N, int M, int model, int Lx, int Ly,
-                               float4* mcs, float2* mth, cudaStream_t st);
+                               float2* mth, float2* mlc, cudaStream_t st);
 cudaError_t launch_param_prep(const double2* p, int N, int M, float2* a, float2* b, float2* Wt,
                               cudaStream_t st);
 cudaError_t launch_logpsi(const RbmDev& R, const int8_t* spins, int64_t n, float2* out,
