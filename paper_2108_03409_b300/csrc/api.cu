@@ -355,29 +355,28 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &w.Minv, P)) || (e = dalloc(ctx, &w.t2, ctx->Mmax)) ||
         (e = dalloc(ctx, &w.va, ctx->Nmax)) || (e = dalloc(ctx, &w.vb, ctx->Mmax)) ||
         (e = dalloc(ctx, &w.V, (size_t)ctx->Nmax * ctx->Mmax)) || (e = dalloc(ctx, &w.u, Ns)) ||
-        (e = dalloc(ctx, &w.upart, (size_t)std::max<int64_t>(cg_partial_floats2(Ns, ctx->Mmax),
-                                                              ((2 * (int64_t)ctx->Mmax + 2 + 127) / 128) * Ns))) ||
+        (e = dalloc(ctx, &w.upart, (size_t)cg_partial_floats2(Ns, ctx->Mmax))) ||
         (e = dalloc(ctx, &w.ustats, 8)) || (e = dalloc(ctx, &w.dpart, 256)) ||
         (e = dalloc(ctx, &w.c2, 8)) || (e = dalloc(ctx, &w.sc, 8)))
       return oom(e);
     w.mpart = ctx->partial;
     if (!ctx->dense && cfg->precision == VMC_PREC_BF16SPLIT) {
       // operator products on the tensor cores: operand planes sized for the largest lattice
-      auto pad = [](int64_t x, int64_t m) { return (x + m - 1) / m * m; };
-      const int64_t kN = pad(ctx->Nmax, 64), ldK = pad(Ns, 64);
-      const int64_t a_rows = pad(2 * (int64_t)ctx->Mmax + 2, 128), b_rows = pad((int64_t)ctx->Nmax + 1, 128);
-      const int64_t nkc = (ldK / 64 + CG_KB_PER_CHUNK - 1) / CG_KB_PER_CHUNK;
-      w.cap_sb = pad(Ns, 128) * kN;
-      w.cap_bs = b_rows * ldK;
-      w.cap_v = pad(2 * (int64_t)ctx->Mmax + 2, 128) * kN;
-      w.cap_a = a_rows * ldK;
-      w.cap_part2 = nkc * a_rows * b_rows;
+      // (every lattice's shape is bounded by the largest N, M; the OhU grid by the SMs)
+      const CgTcShape sh = cg_tc_shape(ctx->Nmax, ctx->Mmax, Ns);
+      const int64_t sms = persistent_grid(1 << 20);
+      w.cap_sb = sh.s_rows * sh.kN;
+      w.cap_bs = sh.b_rows * sh.ldK;
+      w.cap_v = sh.v_rows * sh.kN;
+      w.cap_part2 = sms * 128 * 256;
+      w.cap_yb = sms * ctx->Mmax;
+      w.cap_ov = sms;
       if ((e = dalloc(ctx, &w.Sb, (size_t)w.cap_sb)) || (e = dalloc(ctx, &w.Bs, (size_t)w.cap_bs)) ||
           (e = dalloc(ctx, &w.Vhi, (size_t)w.cap_v)) || (e = dalloc(ctx, &w.Vlo, (size_t)w.cap_v)) ||
-          (e = dalloc(ctx, &w.Ahi, (size_t)w.cap_a)) || (e = dalloc(ctx, &w.Alo, (size_t)w.cap_a)) ||
-          (e = dalloc(ctx, &w.part2, (size_t)w.cap_part2)))
+          (e = dalloc(ctx, &w.part2, (size_t)w.cap_part2)) ||
+          (e = dalloc(ctx, &w.ybpart, (size_t)w.cap_yb)) ||
+          (e = dalloc(ctx, &w.ovpart, (size_t)w.cap_ov)))
         return oom(e);
-
     }
   }
   if (ctx->dense) {
@@ -620,8 +619,8 @@ vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
   CK(launch_moments(spins, ctx->s_T, nullptr, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
                     nullptr, ctx->st), "moments");
   ctx->launches += 3;
-  CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO, nullptr, ctx->cg.Sb != nullptr,
-               ctx->status};
+  CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO, nullptr,
+               ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, n).ok, ctx->status};
   CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
   int it = 0;
   double rel = 0.0;
@@ -701,8 +700,8 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
     CK(launch_moments(ctx->s_spins, ctx->s_T, ctx->s_E, ctx->estats, Ns, L.N, L.M, ctx->partial,
                       ctx->meanO, ctx->F, ctx->st), "moments");
     ctx->launches += 2;
-    CgProblem pb{ctx->s_spins, ctx->s_T, Ns, L.N, L.M, ctx->meanO, nullptr, ctx->cg.Sb != nullptr,
-                 ctx->status};
+    CgProblem pb{ctx->s_spins, ctx->s_T, Ns, L.N, L.M, ctx->meanO, nullptr,
+                 ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, Ns).ok, ctx->status};
     CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
     cudaEventRecord(ctx->ev[6], ctx->st);
     cudaEventRecord(ctx->ev[7], ctx->st);

@@ -190,21 +190,6 @@ __global__ void k_mean_final(const double2* __restrict__ partial, int nb, int64_
   }
 }
 
-// u_q = sum over the tiles' partials - c (the a block came through the product)
-__global__ void k_vs_finish_tc(const float2* __restrict__ part, int mtiles,
-                               const double* __restrict__ c, int64_t n, float2* __restrict__ u) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    float ur = 0.f, ui = 0.f;
-    for (int m = 0; m < mtiles; ++m) {
-      const float2 p = part[(int64_t)m * n + q];
-      ur += p.x;
-      ui += p.y;
-    }
-    u[q] = make_float2(ur - (float)c[0], ui - (float)c[1]);
-  }
-}
-
 // diag(S) in closed form (s_i^2 = 1); t2[j] = <|t_j|^2>.  D = shift part, Minv = 1/diag(S~).
 __global__ void k_diag_s(const double2* __restrict__ meanO, const double* __restrict__ t2, int N,
                          int M, double nu, int mode, double* __restrict__ D,
@@ -320,14 +305,11 @@ static cudaError_t cdot(const double2* a, const double2* b, int64_t P, CgWork& w
 
 // q = S~ p
 // ---------------------------------------------------------------------------------------
-// Tensor-core operator.  Per step: Sb = spins as BF16 [q][i] (A of the Obar v product) and
-// Bs = [spins^T ; ones] [i][q] (B of the Obar^H u product); per CG iteration: the direction's
-// W block as hi/lo real-row planes, and A2 = [conj(t_qj)(u_q - <u>) rows 2j / 2j+1 ; (u_q -
-// <u>) rows 2M / 2M+1] as hi/lo planes [row][q].  Zero padding everywhere the products
-// read (K padding must be finite: 0 x garbage could be NaN).
+// Tensor-core operator (products in cg_tc.cu).  Per step: Sb = spins as BF16 [q][i] (A of
+// the Obar v product) and Bs = spins^T [i][q] (B of the Obar^H u product); per CG
+// iteration: the direction's W block and v_a as hi/lo real-row planes.  Zero padding
+// everywhere the products read (K padding must be finite: 0 x garbage could be NaN).
 // ---------------------------------------------------------------------------------------
-static inline int64_t pad_to(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
-
 __global__ void k_build_sb(const int8_t* __restrict__ spins, int64_t n, int N, int64_t rows,
                            int64_t K, __nv_bfloat16* __restrict__ Sb) {
   const int64_t total = rows * K;
@@ -349,9 +331,7 @@ __global__ void k_build_bs(const int8_t* __restrict__ spins, int64_t n, int N, i
   for (int r = ty; r < 32; r += 8) {
     const int64_t q = q0 + r;
     const int i = i0 + tx;
-    float v = 0.f;
-    if (q < n) v = (i < N) ? (float)spins[q * N + i] : (i == N ? 1.f : 0.f);
-    tile[r][tx] = v;
+    tile[r][tx] = (q < n && i < N) ? (float)spins[q * N + i] : 0.f;
   }
   __syncthreads();
   for (int r = ty; r < 32; r += 8) {
@@ -382,106 +362,73 @@ __global__ void k_build_vplanes(const float2* __restrict__ V, const float2* __re
   }
 }
 
-// A2 rows [2j, 2j+1] = conj(t_qj) u'_q, rows [2M, 2M+1] = u'_q, u' = u - mean(u)
-__global__ void k_build_a2(const float2* __restrict__ T, const float2* __restrict__ u,
-                           const double* __restrict__ ustats, int64_t n, int M, int64_t rows,
-                           int64_t K, __nv_bfloat16* __restrict__ Ahi,
-                           __nv_bfloat16* __restrict__ Alo) {
-  __shared__ float2 tile[32][33];
-  const int64_t q0 = (int64_t)blockIdx.x * 32;
-  const int j0 = blockIdx.y * 32;                 // complex row index (j or M for u')
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const float mr = (float)ustats[0], mi = (float)ustats[1];
-  for (int r = ty; r < 32; r += 8) {
-    const int64_t q = q0 + r;
-    const int j = j0 + tx;
-    float2 w = make_float2(0.f, 0.f);
-    if (q < n) {
-      const float2 uq = u[q];
-      const float ur = uq.x - mr, ui = uq.y - mi;
-      if (j < M) {
-        const float2 t = T[q * M + j];
-        w = make_float2(t.x * ur + t.y * ui, t.x * ui - t.y * ur);   // conj(t) u'
-      } else if (j == M) {
-        w = make_float2(ur, ui);
-      }
-    }
-    tile[r][tx] = w;
-  }
-  __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int j = j0 + r;
-    const int64_t q = q0 + tx;
-    if (2 * (int64_t)j + 1 < rows && q < K) {
-      const float2 w = tile[tx][r];
-      const __nv_bfloat16 hr = __float2bfloat16_rn(w.x), hi = __float2bfloat16_rn(w.y);
-      Ahi[(2 * (int64_t)j) * K + q] = hr;
-      Ahi[(2 * (int64_t)j + 1) * K + q] = hi;
-      Alo[(2 * (int64_t)j) * K + q] = __float2bfloat16_rn(w.x - __bfloat162float(hr));
-      Alo[(2 * (int64_t)j + 1) * K + q] = __float2bfloat16_rn(w.y - __bfloat162float(hi));
-    }
-  }
-}
-
-// y_k = (1/n) sum_q conj(Obar_qk) u_q from the K-chunk partials G[kc][row][col] (FP64 sum):
-// a_i: rows 2M/2M+1, col i; b_j: rows 2j/2j+1, col N; W_ji: rows 2j/2j+1, col i
-// four threads per entry (chunks c = q, q + 4, ...), then a fixed-order shuffle sum
-__global__ void __launch_bounds__(256) k_reduce_y(const float* __restrict__ part, int nkc,
-                                                  int64_t a_rows, int64_t b_rows, int N, int M,
-                                                  int64_t n, double2* __restrict__ y) {
+// q_k = y_k + D_k p_k with y_k = (1/n) sum_q conj(Obar_qk) w_q from the K-chunk partials
+// (FP64 sum over chunks): a_i: out rows 2M / 2M+1, column i; b_j: ybpart[.][j]; W_ji: out
+// rows 2j / 2j+1, column i.  Four threads per entry (chunks c = l, l + 4, ...), then a
+// fixed-order shuffle sum.
+__global__ void __launch_bounds__(256) k_cg_reduce_tc(const float* __restrict__ out,
+                                                      const float2* __restrict__ ybpart,
+                                                      int kchunks, int64_t a_rows, int ncols,
+                                                      int N, int M, int64_t n,
+                                                      const double* __restrict__ D,
+                                                      const double2* __restrict__ p,
+                                                      double2* __restrict__ q) {
   const int64_t P = (int64_t)N + M + (int64_t)N * M;
   const double inv = 1.0 / (double)n;
   const int64_t k = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
-  const int q = threadIdx.x & 3;
+  const int l = threadIdx.x & 3;
   double re = 0.0, im = 0.0;
   if (k < P) {
-    int64_t row, col;
-    if (k < N) { row = 2 * (int64_t)M; col = k; }
-    else if (k < N + M) { row = 2 * (k - N); col = N; }
-    else { const int64_t r = k - N - M; row = 2 * (r / N); col = r % N; }
-    for (int c = q; c < nkc; c += 4) {
-      const float* g = part + (int64_t)c * a_rows * b_rows;
-      re += (double)g[row * b_rows + col];
-      im += (double)g[(row + 1) * b_rows + col];
+    if (k >= N && k < N + M) {
+      for (int c = l; c < kchunks; c += 4) {
+        const float2 v = ybpart[(int64_t)c * M + (k - N)];
+        re += (double)v.x;
+        im += (double)v.y;
+      }
+    } else {
+      int64_t row, col;
+      if (k < N) { row = 2 * (int64_t)M; col = k; }
+      else { const int64_t r = k - N - M; row = 2 * (r / N); col = r % N; }
+      for (int c = l; c < kchunks; c += 4) {
+        const float* g = out + (int64_t)c * a_rows * ncols;
+        re += (double)g[row * ncols + col];
+        im += (double)g[(row + 1) * ncols + col];
+      }
     }
   }
   re += __shfl_xor_sync(0xffffffffu, re, 1);
   im += __shfl_xor_sync(0xffffffffu, im, 1);
   re += __shfl_xor_sync(0xffffffffu, re, 2);
   im += __shfl_xor_sync(0xffffffffu, im, 2);
-  if (k < P && q == 0) y[k] = make_double2(re * inv, im * inv);
+  if (k < P && l == 0) {
+    const double2 pk = p[k];
+    q[k] = make_double2(re * inv + D[k] * pk.x, im * inv + D[k] * pk.y);
+  }
 }
 
 static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, double2* q,
                               cudaStream_t st, int64_t* launches) {
   const int N = pb.N, M = pb.M;
   const int64_t n = pb.n, P = (int64_t)N + M + (int64_t)N * M;
-  const int64_t kN = pad_to(N, 64), s_rows = pad_to(n, 128), v_rows = pad_to(2 * (int64_t)M + 2, 128);
-  const int64_t ldK = pad_to(n, 64), a_rows = pad_to(2 * (int64_t)M + 2, 128),
-                b_rows = pad_to((int64_t)N + 1, 128);
-  const int nkc = (int)((ldK / 64 + CG_KB_PER_CHUNK - 1) / CG_KB_PER_CHUNK);
-  if (v_rows * kN > w.cap_v || a_rows * ldK > w.cap_a || nkc * a_rows * b_rows > w.cap_part2)
+  const CgTcShape sh = cg_tc_shape(N, M, n);
+  if (!sh.ok || sh.v_rows * sh.kN > w.cap_v ||
+      (int64_t)sh.kchunks * sh.mtiles * 128 * sh.nbt * 128 > w.cap_part2 ||
+      (int64_t)sh.kchunks * M > w.cap_yb)
     return cudaErrorInvalidValue;
   k_split_v<<<g1d(P), 256, 0, st>>>(p, N, M, w.va, w.vb, w.V);
-  k_build_vplanes<<<g1d(v_rows * kN), 256, 0, st>>>(w.V, w.va, N, M, v_rows, kN, w.Vhi, w.Vlo);
+  k_build_vplanes<<<g1d(sh.v_rows * sh.kN), 256, 0, st>>>(w.V, w.va, N, M, sh.v_rows, sh.kN,
+                                                          w.Vhi, w.Vlo);
   VMC_TRY(cdot(pb.meanO_conj_free, p, P, w, w.c2, st));   // c = sum_k <O_k> p_k (no conj)
-  VMC_TRY(launch_cg_ov_tc(w.Sb, s_rows, kN, w.Vhi, w.Vlo, v_rows, pb.T, w.vb, M, n, w.upart,
-                          pb.status, st));
-  const int mtiles = (int)(v_rows / 128);
-  k_vs_finish_tc<<<g1d(n), 256, 0, st>>>(w.upart, mtiles, reinterpret_cast<const double*>(w.c2),
-                                         n, w.u);
-  {
-    const int nb = (int)std::min<int64_t>(RED_BLOCKS, (n + 1023) / 1024);
-    k_mean_partial<<<nb, 256, 0, st>>>(w.u, n, w.dpart);
-    k_mean_final<<<1, 32, 0, st>>>(w.dpart, nb, n, w.ustats);
-  }
-  dim3 ga((unsigned)(ldK / 32), (unsigned)((a_rows / 2 + 31) / 32));
-  k_build_a2<<<ga, 256, 0, st>>>(pb.T, w.u, w.ustats, n, M, a_rows, ldK, w.Ahi, w.Alo);
-  VMC_TRY(launch_cg_ohu_tc(w.Ahi, w.Alo, a_rows, w.Bs, b_rows, ldK, CG_KB_PER_CHUNK, w.part2,
+  int nup = 0;
+  VMC_TRY(launch_cg_ov_tc(w.Sb, w.Vhi, w.Vlo, sh, pb.T, w.vb, reinterpret_cast<const double*>(w.c2),
+                          M, n, w.u, w.ovpart, &nup, pb.status, st));
+  if (nup > w.cap_ov) return cudaErrorInvalidValue;
+  VMC_TRY(launch_cg_ohu_tc(w.Bs, sh, pb.T, w.u, w.ovpart, nup, M, n, w.part2, w.ybpart,
                            pb.status, st));
-  k_reduce_y<<<(unsigned)((P + 63) / 64), 256, 0, st>>>(w.part2, nkc, a_rows, b_rows, N, M, n, w.y);
-  k_add_diag<<<g1d(P), 256, 0, st>>>(w.y, w.D, p, P, q);
-  *launches += 12;
+  k_cg_reduce_tc<<<(unsigned)((P + 63) / 64), 256, 0, st>>>(w.part2, w.ybpart, sh.kchunks,
+                                                            (int64_t)sh.mtiles * 128, sh.nbt * 128,
+                                                            N, M, n, w.D, p, q);
+  *launches += 7;
   return cudaGetLastError();
 }
 
@@ -518,12 +465,13 @@ cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cuda
   k_conj_copy<<<g1d(P), 256, 0, st>>>(pb.meanO, P, w.meanO_c);
   *launches += 3;
   if (pb.tc) {
-    const int64_t kN = pad_to(pb.N, 64), s_rows = pad_to(pb.n, 128), ldK = pad_to(pb.n, 64);
-    const int64_t b_rows = pad_to((int64_t)pb.N + 1, 128);
-    if (s_rows * kN > w.cap_sb || b_rows * ldK > w.cap_bs) return cudaErrorInvalidValue;
-    k_build_sb<<<g1d(s_rows * kN), 256, 0, st>>>(pb.spins, pb.n, pb.N, s_rows, kN, w.Sb);
-    dim3 gb((unsigned)(ldK / 32), (unsigned)(b_rows / 32));
-    k_build_bs<<<gb, 256, 0, st>>>(pb.spins, pb.n, pb.N, b_rows, ldK, w.Bs);
+    const CgTcShape sh = cg_tc_shape(pb.N, pb.M, pb.n);
+    if (!sh.ok || sh.s_rows * sh.kN > w.cap_sb || sh.b_rows * sh.ldK > w.cap_bs)
+      return cudaErrorInvalidValue;
+    k_build_sb<<<g1d(sh.s_rows * sh.kN), 256, 0, st>>>(pb.spins, pb.n, pb.N, sh.s_rows, sh.kN,
+                                                       w.Sb);
+    dim3 gb((unsigned)(sh.ldK / 32), (unsigned)(sh.b_rows / 32));
+    k_build_bs<<<gb, 256, 0, st>>>(pb.spins, pb.n, pb.N, sh.b_rows, sh.ldK, w.Bs);
     *launches += 2;
   }
   return cudaGetLastError();

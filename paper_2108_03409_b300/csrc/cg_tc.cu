@@ -1,0 +1,650 @@
+// cg_tc.cu -- the two sample-sum products of the matrix-free S~ v on the 5th-generation
+// tensor cores (CG on the shifted S, section "Diagonal shift"; S itself is never formed).
+//
+// For a CG direction v = [v_a | v_b | V] (V the W block as an M x N matrix):
+//   Ov:  u_q = sum_j t_qj (v_b,j + Z_qj) + Z_q,M - c,      Z = S_b V^T,  c = <O> . v
+//        S_b = spins as BF16 (exact), V as real rows 2j / 2j+1 = Re / Im V_j plus rows
+//        2M / 2M+1 = Re / Im v_a, each row a BF16 hi/lo pair: Z = S_b V_hi^T + S_b V_lo^T.
+//   OhU: w_q = u_q - mean(u);  y_W[j][i] = sum_q conj(t_qj) w_q s_qi,  y_a[i] = sum_q w_q s_qi,
+//        y_b[j] = sum_q conj(t_qj) w_q.  The product A B^T has A rows 2j / 2j+1 = Re / Im of
+//        conj(t_qj) w_q and rows 2M / 2M+1 = Re / Im w_q (as BF16 hi/lo pairs, samples q
+//        along K) and B = spins^T; A is never stored: warps of the kernel form each 128 x 64
+//        tile from t and u in shared memory (128-byte swizzled, as TMA would write it), so
+//        t is read from HBM once per product.
+//
+// Both kernels are warp-specialised (warp 0: TMA, warp 1: tcgen05.mma issue, warps 2-9:
+// epilogue or operand formation), hand stages over through mbarriers, and bound every wait:
+// on expiry the kernel records DEV_ERR_TIMEOUT, the roles leave their loops, copies and
+// products in flight are waited for (bounded), the tensor memory is freed and the kernel
+// returns.
+#include <algorithm>
+
+#include "tc_ptx.cuh"
+#include "vmc_device.cuh"
+#include "vmc_internal.h"
+
+namespace vmc {
+
+namespace cgtc {
+constexpr int TILE = 128 * 64 * 2;              // 128 rows x 64 BF16 (one swizzle row each)
+constexpr int THREADS = 64 + 32 * 8;            // TMA warp, MMA warp, eight worker warps
+constexpr int WORKER_WARPS = 8;
+constexpr int TAIL = 1024;                      // barriers and small shared scalars
+// Ov: a work item is 256 samples (two 128-row sub-tiles sharing every V stage); K = N <= 256
+constexpr int OV_MAX_NKB = 4;
+constexpr int OV_STAGES = 3;
+constexpr int OV_A_BYTES = OV_MAX_NKB * 2 * TILE;
+constexpr int OV_STAGE_BYTES = 2 * TILE;        // V hi, V lo (128 rows each)
+constexpr int OV_SMEM = 1024 + OV_A_BYTES + OV_STAGES * OV_STAGE_BYTES + TAIL;
+constexpr int OV_TMEM_COLS = 512;               // two buffers x two sub-tiles x 128 columns
+// OhU: A hi, A lo (formed in place), B = spins^T (up to 256 rows)
+constexpr int OH_STAGES = 3;
+constexpr int OH_STAGE_BYTES = 4 * TILE;
+constexpr int OH_SMEM = 1024 + OH_STAGES * OH_STAGE_BYTES + TAIL;
+static_assert(OV_SMEM <= 232448 && OH_SMEM <= 232448, "shared memory budget");
+
+__device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
+  return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// one lane waits, the warp shares the verdict (tcgen05.ld needs the whole warp)
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int lane) {
+  int ok = 0;
+  if (lane == 0) ok = tc::mbar_wait(bar, parity, abort_flag) && !*abort_flag;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+}  // namespace cgtc
+
+// ---------------------------------------------------------------------------------------
+// Ov.  Persistent: CTA b takes items b, b + grid, ...  Per item the two spin sub-tiles stay
+// in shared memory (one slot per 64-wide K block, refilled for the next item as soon as the
+// item's last product on that block completes) while the V tiles stream through a 3-stage
+// ring; each 128-column tile of Z (64 hidden units, re/im interleaved) accumulates in one
+// of two TMEM buffers, so the epilogue of one column tile overlaps the products of the
+// next.  Epilogue warp e (2..9) owns TMEM lane quadrant e % 4 of sub-tile (e - 2) / 4: one
+// sample per thread, whose row of t it loads from HBM (32 hidden units ahead of use).
+// upart[b] = FP64 sum of u over the samples CTA b wrote.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(cgtc::THREADS, 1)
+k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUtensorMap map_vhi,
+        const __grid_constant__ CUtensorMap map_vlo, int nkb, int nct, int64_t items,
+        const float2* __restrict__ T, const float2* __restrict__ vb, const double* __restrict__ c,
+        int M, int64_t n, float2* __restrict__ u, double2* __restrict__ upart,
+        unsigned* status) {
+  using namespace tc;
+  using namespace cgtc;
+  extern __shared__ uint8_t gsm_raw[];
+  uint8_t* smem = align1024(gsm_raw);
+  uint8_t* Abuf = smem;                                   // [kb][sub] tiles
+  uint8_t* Bbuf = smem + OV_A_BYTES;                      // [stage][hi, lo]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bbuf + OV_STAGES * OV_STAGE_BYTES);
+  uint64_t* full = bars;                                  // [3] V stage landed
+  uint64_t* empty = bars + 3;                             // [3] V stage consumed
+  uint64_t* afull = bars + 6;                             // [4] spin slot landed
+  uint64_t* aempty = bars + 10;                           // [4] spin slot consumed
+  uint64_t* accf = bars + 14;                             // [2] accumulator complete
+  uint64_t* acce = bars + 16;                             // [2] accumulator drained
+  uint64_t* fin = bars + 18;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 19);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  double2* red = reinterpret_cast<double2*>(bars + 20);   // [8]
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 19; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    mbar_init(smem_u32(&acce[0]), WORKER_WARPS);
+    mbar_init(smem_u32(&acce[1]), WORKER_WARPS);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(OV_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int64_t g = 0;                                      // V stages issued
+      int last_it = -1, last_kb = -1;                     // the last spin slot load issued
+      bool ok = true;
+      int it = 0;
+      for (int64_t w = blockIdx.x; w < items && ok && !*abort_flag; w += gridDim.x, ++it) {
+        for (int kb = 0; kb < nkb && ok; ++kb) {
+          if (it > 0 && !mbar_wait(smem_u32(&aempty[kb]), (uint32_t)((it - 1) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(&afull[kb]);
+          mbar_expect_tx(fb, 2 * TILE);
+          tma_load_2d(smem_u32(Abuf + (2 * kb) * TILE), &map_s, kb * 64, (int)(w * 256), fb);
+          tma_load_2d(smem_u32(Abuf + (2 * kb + 1) * TILE), &map_s, kb * 64, (int)(w * 256 + 128), fb);
+          last_it = it;
+          last_kb = kb;
+        }
+        for (int ct = 0; ct < nct && ok; ++ct)
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            const int s = (int)(g % OV_STAGES);
+            if (g >= OV_STAGES &&
+                !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((g / OV_STAGES) - 1) & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            uint8_t* st = Bbuf + s * OV_STAGE_BYTES;
+            const uint32_t fb = smem_u32(&full[s]);
+            mbar_expect_tx(fb, 2 * TILE);
+            tma_load_2d(smem_u32(st), &map_vhi, kb * 64, ct * 128, fb);
+            tma_load_2d(smem_u32(st + TILE), &map_vlo, kb * 64, ct * 128, fb);
+          }
+      }
+      if (*abort_flag) {
+        // copies in flight land before the CTA exits (bounded)
+        volatile int dummy = 0;
+        for (int64_t h = (g > OV_STAGES ? g - OV_STAGES : 0); h < g; ++h)
+          mbar_wait(smem_u32(&full[h % OV_STAGES]), (uint32_t)((h / OV_STAGES) & 1), &dummy);
+        for (int kb = 0; kb < nkb; ++kb) {
+          const int cnt = (kb <= last_kb) ? last_it + 1 : last_it;   // loads into slot kb
+          if (cnt > 0) mbar_wait(smem_u32(&afull[kb]), (uint32_t)((cnt - 1) & 1), &dummy);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      constexpr uint32_t idesc = idesc_bf16_f32(128, 128);
+      int64_t g = 0, cc = 0;
+      bool ok = true, any = false;
+      int it = 0;
+      for (int64_t w = blockIdx.x; w < items && ok && !*abort_flag; w += gridDim.x, ++it) {
+        for (int ct = 0; ct < nct && ok; ++ct, ++cc) {
+          const int b = (int)(cc & 1);
+          if (cc >= 2 && !mbar_wait(smem_u32(&acce[b]), (uint32_t)(((cc >> 1) - 1) & 1), abort_flag)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t d0 = tmem + (uint32_t)(b * 256), d1 = d0 + 128u;
+          for (int kb = 0; kb < nkb; ++kb, ++g) {
+            if (ct == 0 && !mbar_wait(smem_u32(&afull[kb]), (uint32_t)(it & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            const int s = (int)(g % OV_STAGES);
+            if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((g / OV_STAGES) & 1), abort_flag)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint64_t a0 = smem_desc_sw128(smem_u32(Abuf + (2 * kb) * TILE));
+            const uint64_t a1 = smem_desc_sw128(smem_u32(Abuf + (2 * kb + 1) * TILE));
+            const uint64_t bh = smem_desc_sw128(smem_u32(Bbuf + s * OV_STAGE_BYTES));
+            const uint64_t bl = smem_desc_sw128(smem_u32(Bbuf + s * OV_STAGE_BYTES + TILE));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
+              const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+              mma_bf16(d0, a0 + o, bh + o, idesc, acc);
+              mma_bf16(d0, a0 + o, bl + o, idesc, 1u);
+              mma_bf16(d1, a1 + o, bh + o, idesc, acc);
+              mma_bf16(d1, a1 + o, bl + o, idesc, 1u);
+            }
+            any = true;
+            mma_commit(smem_u32(&empty[s]));
+            if (ct == nct - 1) mma_commit(smem_u32(&aempty[kb]));   // slot free for the next item
+          }
+          if (!ok) break;
+          mma_commit(smem_u32(&accf[b]));
+        }
+      }
+      if (*abort_flag && any) {
+        volatile int dummy = 0;
+        mma_commit(smem_u32(fin));
+        mbar_wait(smem_u32(fin), 0, &dummy);
+      }
+    }
+  } else {
+    // ---------------- epilogue: u_q for one sample per thread ----------------
+    const int ew = warp - 2;
+    const int qd = warp & 3, sub = ew >> 2;
+    const int r = qd * 32 + lane;
+    const bool vec = (M & 1) == 0;
+    const float cre = (float)c[0], cim = (float)c[1];
+    // The thread's work is a sequence of quarters g = 0, 1, ...: quarter g covers hidden
+    // units 16 (g % 4) .. + 15 of column tile (g / 4) % nct of the CTA's item g / (4 nct).
+    // Its 16 values of t are loaded two quarters ahead into one of three rotating buffers.
+    const int64_t my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    const int64_t nq = my_items * nct * 4;
+    auto load_t = [&](int64_t g, float4 (&dst)[8]) {
+      if (g >= nq) return;
+      const int64_t w = blockIdx.x + (g / (4 * nct)) * gridDim.x;
+      const int64_t m = w * 256 + sub * 128 + r;
+      const int j0 = (int)((g >> 2) % nct) * 64 + (int)(g & 3) * 16;
+      if (m < n && vec && j0 + 16 <= M) {
+        const float4* src = reinterpret_cast<const float4*>(T + m * M + j0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dst[k] = src[k];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int j = j0 + 2 * k;
+          const float2 x = (m < n && j < M) ? T[m * M + j] : make_float2(0.f, 0.f);
+          const float2 y = (m < n && j + 1 < M) ? T[m * M + j + 1] : make_float2(0.f, 0.f);
+          dst[k] = make_float4(x.x, x.y, y.x, y.y);
+        }
+      }
+    };
+    double usr = 0.0, usi = 0.0;
+    float ar = 0.f, ai = 0.f;
+    bool ok = true;
+    // quarter g from buffer cur; quarter g + 2 into buffer ahead (the one quarter g - 1 used)
+    auto step = [&](int64_t g, const float4 (&cur)[8], float4 (&ahead)[8]) {
+      if (!ok || g >= nq) return;
+      load_t(g + 2, ahead);
+      const int64_t cc = g >> 2;                  // column tiles so far
+      const int b = (int)(cc & 1), qtr = (int)(g & 3), ct = (int)(cc % nct);
+      if (qtr == 0) {
+        if (!warp_wait(smem_u32(&accf[b]), (uint32_t)((cc >> 1) & 1), abort_flag, lane)) {
+          ok = false;
+          return;
+        }
+        fence_after();
+      }
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * 256 + sub * 128 + qtr * 32), v);
+      const int jb = ct * 64 + qtr * 16;
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) {
+        const int j = jb + jj;
+        const float4 t4 = cur[jj >> 1];
+        const float tr = (jj & 1) ? t4.z : t4.x, ti = (jj & 1) ? t4.w : t4.y;
+        if (j < M) {
+          const float2 bj = vb[j];
+          const float zr = v[2 * jj] + bj.x, zi = v[2 * jj + 1] + bj.y;
+          ar = fmaf(tr, zr, fmaf(-ti, zi, ar));
+          ai = fmaf(tr, zi, fmaf(ti, zr, ai));
+        } else if (j == M) {                       // rows 2M / 2M+1: sum_i s_qi v_a,i as is
+          ar += v[2 * jj];
+          ai += v[2 * jj + 1];
+        }
+      }
+      if (qtr == 3) {
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
+        if (ct == nct - 1) {                       // the item's last column tile: u is complete
+          const int64_t w = blockIdx.x + (g / (4 * nct)) * gridDim.x;
+          const int64_t m = w * 256 + sub * 128 + r;
+          if (m < n) {
+            const float ur = ar - cre, ui = ai - cim;
+            u[m] = make_float2(ur, ui);
+            usr += (double)ur;
+            usi += (double)ui;
+          }
+          ar = 0.f;
+          ai = 0.f;
+        }
+      }
+    };
+    float4 ta[8], tb[8], tc3[8];
+    load_t(0, ta);
+    load_t(1, tb);
+    for (int64_t g = 0; g < nq && ok; g += 3) {
+      step(g, ta, tc3);
+      step(g + 1, tb, ta);
+      step(g + 2, tc3, tb);
+    }
+    usr = warp_sum_d(usr);
+    usi = warp_sum_d(usi);
+    if (lane == 0) red[ew] = make_double2(usr, usi);
+    named_bar_sync(1, 32 * WORKER_WARPS);
+    if (ew == 0 && lane == 0) {
+      double sr = 0.0, si = 0.0;
+      for (int k = 0; k < WORKER_WARPS; ++k) {
+        sr += red[k].x;
+        si += red[k].y;
+      }
+      upart[blockIdx.x] = make_double2(sr, si);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(OV_TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) flag_error(status, DEV_ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------------------
+// OhU.  CTA (mt, kc): rows [128 mt, 128 mt + 128) of A (hidden units 64 mt ..), K blocks
+// [kc nkpc, ...) of the samples.  Worker thread (jp, kq) forms rows 4jp .. 4jp+3 of the
+// tile (Re / Im of units j0 = 64 mt + 2 jp and j0 + 1) for the eight samples 8 kq .. 8 kq + 7
+// of each 64-sample block: one 16-byte hi and one lo chunk per row, written at the swizzled
+// position (lanes of a warp cover all eight chunk positions of a row group, so the stores
+// are conflict-free); the next block's t and u are loaded before this block is formed.
+// The same threads keep y_b's FP32 partial sums and, at the end, drain the accumulator.
+// out[kc][128 mt + r][col] = the chunk's FP32 partial of A B^T; ybpart[kc][j] likewise.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(cgtc::THREADS, 1)
+k_cg_ohu(const __grid_constant__ CUtensorMap map_b, int nbt, int nkb, int nkpc, int mtiles,
+         const float2* __restrict__ T, const float2* __restrict__ u,
+         const double2* __restrict__ upart, int nup, int M, int64_t n, float* __restrict__ out,
+         float2* __restrict__ ybpart, unsigned* status) {
+  using namespace tc;
+  using namespace cgtc;
+  extern __shared__ uint8_t gsm_raw[];
+  uint8_t* smem = align1024(gsm_raw);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OH_STAGES * OH_STAGE_BYTES);
+  uint64_t* fullb = bars;                                 // [3] B landed
+  uint64_t* fulla = bars + 3;                             // [3] A formed (8 warps)
+  uint64_t* empty = bars + 6;                             // [3] stage consumed
+  uint64_t* accf = bars + 9;
+  uint64_t* fin = bars + 10;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float2* mean = reinterpret_cast<float2*>(bars + 12);
+
+  const int mt = (int)(blockIdx.x % mtiles), kc = (int)(blockIdx.x / mtiles);
+  const int kb0 = kc * nkpc, nk = min(nkb, kb0 + nkpc) - kb0;
+  const int ncols = nbt * 128;
+  const uint32_t tmem_cols = (uint32_t)ncols;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 11; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < OH_STAGES; ++s) mbar_init(smem_u32(&fulla[s]), WORKER_WARPS);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(tmem_cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (B = spins^T) ----------------
+      int g = 0;
+      for (; g < nk; ++g) {
+        const int s = g % OH_STAGES;
+        if (g >= OH_STAGES &&
+            !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((g / OH_STAGES) - 1) & 1), abort_flag))
+          break;
+        uint8_t* st = smem + s * OH_STAGE_BYTES + 2 * TILE;
+        const uint32_t fb = smem_u32(&fullb[s]);
+        mbar_expect_tx(fb, (uint32_t)(nbt * TILE));
+        for (int bt = 0; bt < nbt; ++bt)
+          tma_load_2d(smem_u32(st + bt * TILE), &map_b, (kb0 + g) * 64, bt * 128, fb);
+      }
+      if (*abort_flag) {
+        volatile int dummy = 0;
+        for (int h = (g > OH_STAGES ? g - OH_STAGES : 0); h < g; ++h)
+          mbar_wait(smem_u32(&fullb[h % OH_STAGES]), (uint32_t)((h / OH_STAGES) & 1), &dummy);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t idesc = idesc_bf16_f32(128, ncols);
+      bool any = false, ok = true;
+      for (int g = 0; g < nk; ++g) {
+        const int s = g % OH_STAGES;
+        const uint32_t par = (uint32_t)((g / OH_STAGES) & 1);
+        if (!mbar_wait(smem_u32(&fullb[s]), par, abort_flag) ||
+            !mbar_wait(smem_u32(&fulla[s]), par, abort_flag)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        uint8_t* st = smem + s * OH_STAGE_BYTES;
+        const uint64_t ah = smem_desc_sw128(smem_u32(st));
+        const uint64_t al = smem_desc_sw128(smem_u32(st + TILE));
+        const uint64_t bd = smem_desc_sw128(smem_u32(st + 2 * TILE));
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t o = (uint64_t)(kk * 32) >> 4;
+          mma_bf16(tmem, ah + o, bd + o, idesc, (g > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16(tmem, al + o, bd + o, idesc, 1u);
+        }
+        any = true;
+        mma_commit(smem_u32(&empty[s]));
+      }
+      if (ok && any) mma_commit(smem_u32(accf));
+      if (*abort_flag && any) {
+        volatile int dummy = 0;
+        mma_commit(smem_u32(fin));
+        mbar_wait(smem_u32(fin), 0, &dummy);
+      }
+    }
+  } else {
+    // ---------------- operand formation, y_b partials, then the accumulator ----------------
+    const int ew = warp - 2, et = ew * 32 + lane;
+    const int kq = et & 7, jp = et >> 3;                  // lanes: 4 unit pairs x 8 chunks
+    const int j0 = mt * 64 + 2 * jp, j1 = j0 + 1;
+    if (ew == 0) {
+      // mean(u) from the Ov CTAs' FP64 partials (fixed order)
+      double sr = 0.0, si = 0.0;
+      for (int k = lane; k < nup; k += 32) {
+        sr += upart[k].x;
+        si += upart[k].y;
+      }
+      sr = warp_sum_d(sr);
+      si = warp_sum_d(si);
+      if (lane == 0) *mean = make_float2((float)(sr / (double)n), (float)(si / (double)n));
+    }
+    named_bar_sync(1, 32 * WORKER_WARPS);
+    const float mr = mean->x, mi = mean->y;
+    const bool pair_vec = (M & 1) == 0 && j1 < M;
+    auto load_blk = [&](int g, float4 (&tq)[8], float2 (&uq)[8]) {
+      const int64_t q0 = (int64_t)(kb0 + g) * 64 + 8 * kq;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        const int64_t q = q0 + kk;
+        uq[kk] = (q < n) ? u[q] : make_float2(0.f, 0.f);
+        if (q < n && pair_vec) {
+          tq[kk] = *reinterpret_cast<const float4*>(T + q * M + j0);
+        } else {
+          const float2 x = (q < n && j0 < M) ? T[q * M + j0] : make_float2(0.f, 0.f);
+          const float2 y = (q < n && j1 < M) ? T[q * M + j1] : make_float2(0.f, 0.f);
+          tq[kk] = make_float4(x.x, x.y, y.x, y.y);
+        }
+      }
+    };
+    float y0r = 0.f, y0i = 0.f, y1r = 0.f, y1i = 0.f;
+    float4 tn[8];
+    float2 un[8];
+    if (nk > 0) load_blk(0, tn, un);
+    bool ok = true;
+    for (int g = 0; g < nk; ++g) {
+      float4 tq[8];
+      float2 uq[8];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        tq[kk] = tn[kk];
+        uq[kk] = un[kk];
+      }
+      if (g + 1 < nk) load_blk(g + 1, tn, un);
+      const int s = g % OH_STAGES;
+      if (g >= OH_STAGES &&
+          !warp_wait(smem_u32(&empty[s]), (uint32_t)(((g / OH_STAGES) - 1) & 1), abort_flag, lane)) {
+        ok = false;
+        break;
+      }
+      const int64_t q0 = (int64_t)(kb0 + g) * 64 + 8 * kq;
+      uint32_t hi[4][4], lo[4][4];                         // [row][pair of samples]
+#pragma unroll
+      for (int kp = 0; kp < 4; ++kp) {
+        float a[2][4];                                     // [sample][row]
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int kk = 2 * kp + e;
+          const bool valid = q0 + kk < n;
+          const float wr = valid ? uq[kk].x - mr : 0.f, wi = valid ? uq[kk].y - mi : 0.f;
+          const float4 t = tq[kk];
+          float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
+          if (j0 < M) {                                    // conj(t) w
+            a0r = fmaf(t.x, wr, t.y * wi);
+            a0i = fmaf(t.x, wi, -t.y * wr);
+          } else if (j0 == M) {
+            a0r = wr;
+            a0i = wi;
+          }
+          if (j1 < M) {
+            a1r = fmaf(t.z, wr, t.w * wi);
+            a1i = fmaf(t.z, wi, -t.w * wr);
+          } else if (j1 == M) {
+            a1r = wr;
+            a1i = wi;
+          }
+          y0r += (j0 < M) ? a0r : 0.f;
+          y0i += (j0 < M) ? a0i : 0.f;
+          y1r += (j1 < M) ? a1r : 0.f;
+          y1i += (j1 < M) ? a1i : 0.f;
+          a[e][0] = a0r;
+          a[e][1] = a0i;
+          a[e][2] = a1r;
+          a[e][3] = a1i;
+        }
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+          const float x0 = a[0][rr], x1 = a[1][rr];
+          const float h0 = __bfloat162float(__float2bfloat16_rn(x0));
+          const float h1 = __bfloat162float(__float2bfloat16_rn(x1));
+          hi[rr][kp] = pack_bf16(h0, h1);
+          lo[rr][kp] = pack_bf16(x0 - h0, x1 - h1);
+        }
+      }
+      uint8_t* st = smem + s * OH_STAGE_BYTES;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const uint32_t off = sw128_offset(4 * jp + rr, kq);
+        *reinterpret_cast<uint4*>(st + off) = make_uint4(hi[rr][0], hi[rr][1], hi[rr][2], hi[rr][3]);
+        *reinterpret_cast<uint4*>(st + TILE + off) =
+            make_uint4(lo[rr][0], lo[rr][1], lo[rr][2], lo[rr][3]);
+      }
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&fulla[s]));
+    }
+    // y_b: sum over the eight chunk lanes of each unit pair (lane bits 0-2), fixed order
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      y0r += __shfl_xor_sync(0xffffffffu, y0r, o);
+      y0i += __shfl_xor_sync(0xffffffffu, y0i, o);
+      y1r += __shfl_xor_sync(0xffffffffu, y1r, o);
+      y1i += __shfl_xor_sync(0xffffffffu, y1i, o);
+    }
+    if (ok && kq == 0) {
+      if (j0 < M) ybpart[(int64_t)kc * M + j0] = make_float2(y0r, y0i);
+      if (j1 < M) ybpart[(int64_t)kc * M + j1] = make_float2(y1r, y1i);
+    }
+    // the accumulator: quadrant warp % 4, column half (warp - 2) / 4
+    if (ok && nk > 0 && warp_wait(smem_u32(accf), 0u, abort_flag, lane)) {
+      fence_after();
+      const int qd = warp & 3, half = ew >> 2;
+      const int r = qd * 32 + lane;
+      float* orow = out + ((int64_t)kc * mtiles * 128 + (int64_t)mt * 128 + r) * ncols;
+      for (int c0 = half * (ncols / 2); c0 < (half + 1) * (ncols / 2); c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int k = 0; k < 32; k += 4)
+          *reinterpret_cast<float4*>(orow + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(tmem_cols) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) flag_error(status, DEV_ERR_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------------------
+CgTcShape cg_tc_shape(int N, int M, int64_t n) {
+  CgTcShape sh{};
+  sh.kN = (N + 63) / 64 * 64;
+  sh.s_rows = (n + 255) / 256 * 256;
+  sh.v_rows = (2 * (int64_t)M + 2 + 127) / 128 * 128;
+  sh.ldK = (n + 63) / 64 * 64;
+  sh.b_rows = (N + 127) / 128 * 128;
+  sh.nbt = (N + 127) / 128;
+  sh.mtiles = (int)sh.v_rows / 128;
+  const int nkb = (int)(sh.ldK / 64);
+  const int sms = (int)persistent_grid(1 << 20);
+  int kch = std::max(1, std::min(nkb, sms / sh.mtiles));
+  sh.nkpc = (nkb + kch - 1) / kch;
+  sh.kchunks = (nkb + sh.nkpc - 1) / sh.nkpc;               // no empty chunk
+  sh.ok = N >= 1 && sh.kN <= 64 * cgtc::OV_MAX_NKB && sh.nbt <= 2;
+  return sh;
+}
+
+cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
+                            const __nv_bfloat16* Vlo, const CgTcShape& sh, const float2* T,
+                            const float2* vb, const double* c, int M, int64_t n, float2* u,
+                            double2* upart, int* nup, unsigned* status, cudaStream_t st) {
+  if (!sh.ok) return cudaErrorNotSupported;
+  CUtensorMap ms, mvh, mvl;
+  cudaError_t e;
+  if ((e = make_map(&ms, Sb, sh.s_rows, sh.kN)) != cudaSuccess) return e;
+  if ((e = make_map(&mvh, Vhi, sh.v_rows, sh.kN)) != cudaSuccess) return e;
+  if ((e = make_map(&mvl, Vlo, sh.v_rows, sh.kN)) != cudaSuccess) return e;
+  static bool attr = false;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(k_cg_ov, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  cgtc::OV_SMEM)) != cudaSuccess)
+      return e;
+    attr = true;
+  }
+  const int64_t items = sh.s_rows / 256;
+  const unsigned grid = persistent_grid(items);
+  k_cg_ov<<<grid, cgtc::THREADS, cgtc::OV_SMEM, st>>>(ms, mvh, mvl, (int)(sh.kN / 64),
+                                                      (int)(sh.v_rows / 128), items, T, vb, c, M,
+                                                      n, u, upart, status);
+  *nup = (int)grid;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const float2* T,
+                             const float2* u, const double2* upart, int nup, int M, int64_t n,
+                             float* out, float2* ybpart, unsigned* status, cudaStream_t st) {
+  if (!sh.ok) return cudaErrorNotSupported;
+  CUtensorMap mb;
+  cudaError_t e;
+  if ((e = make_map(&mb, Bs, sh.b_rows, sh.ldK)) != cudaSuccess) return e;
+  static bool attr = false;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(k_cg_ohu, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  cgtc::OH_SMEM)) != cudaSuccess)
+      return e;
+    attr = true;
+  }
+  const unsigned grid = (unsigned)(sh.mtiles * sh.kchunks);
+  k_cg_ohu<<<grid, cgtc::THREADS, cgtc::OH_SMEM, st>>>(mb, sh.nbt, (int)(sh.ldK / 64), sh.nkpc,
+                                                       sh.mtiles, T, u, upart, nup, M, n, out,
+                                                       ybpart, status);
+  return cudaGetLastError();
+}
+
+}  // namespace vmc

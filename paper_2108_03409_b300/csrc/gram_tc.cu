@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "tc_ptx.cuh"
 #include "vmc_device.cuh"
 #include "vmc_internal.h"
 
@@ -40,119 +41,6 @@ constexpr int SMEM_BYTES = 1024 /*align*/ + STAGES * STAGE_BYTES + STG_BYTES + 2
 constexpr int THREADS = 192;                    // TMA warp, MMA warp, 4 epilogue warps
 constexpr int TMEM_COLS = 256;                  // two 128-column accumulators
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void named_bar_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait: gives up after 2^24 polls or ~2e9 SM cycles, whichever comes first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-  const long long t0 = clock64();
-  for (uint32_t it = 0; it < (1u << 24); ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 255u) == 255u) {
-      if (*abort_flag) return false;
-      if (clock64() - t0 > 2000000000ll) break;
-    }
-  }
-  *abort_flag = 1;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major operand tile written by TMA with 128-byte
-// swizzle: rows of 128 bytes, 8-row swizzle atoms 1024 bytes apart (stride byte offset),
-// descriptor version 1, layout type 2 (128-byte swizzle).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)(1) << 16;                     // leading byte offset (unused for this layout)
-  d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;                       // version
-  d |= (uint64_t)2 << 61;                       // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-      ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
-}
 
 }  // namespace tc
 
@@ -403,190 +291,6 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   if (threadIdx.x == 0 && *abort_flag) flag_error(status, DEV_ERR_TIMEOUT);
 }
 
-// ---------------------------------------------------------------------------------------
-// General product D = A B^T on the tensor cores for the matrix-free CG operator: A (rows m)
-// and B (rows n) are K-major BF16 planes; an operand given as a hi/lo pair contributes both
-// planes (A_hi B + A_lo B, or A B_hi + A B_lo; spins are exact in BF16 and need one plane).
-// One CTA per (m tile, n tile, K chunk), 128 threads: lane 0 of warp 0 issues the TMA loads
-// into a ring of stages, lane 0 of warp 1 the MMAs; all four warps drain the accumulator.
-//   EPI_STORE: the FP32 tile goes to out[kc][m][n] (row stride out_ld; partial per K chunk).
-//   EPI_OV:    A = spins [q][i], B = the CG direction's W block as real rows (2j: Re V_j,
-//              2j+1: Im V_j); row q of the tile holds Z_qj = sum_i s_qi V_ji for the tile's
-//              64 hidden units and the epilogue reduces sum_j t_qj (v_b,j + Z_qj) into
-//              part[n tile][q].
-// ---------------------------------------------------------------------------------------
-namespace tc {
-constexpr int EPI_STORE = 0, EPI_OV = 1;
-}
-
-template <bool SPLIT_A, bool SPLIT_B, int EPI>
-__global__ void __launch_bounds__(128, 1)
-k_gemm_tc(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
-          const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
-          int kb_per_chunk, int nkb, float* __restrict__ out, int64_t out_rows, int64_t out_ld,
-          const float2* __restrict__ T, const float2* __restrict__ vb, int M, int64_t n,
-          float2* __restrict__ part, unsigned* status) {
-  using namespace tc;
-  constexpr int NPL = (SPLIT_A ? 2 : 1) + (SPLIT_B ? 2 : 1);
-  constexpr int SBYTES = NPL * TILE_BYTES;
-  // two stages, so that two CTAs share an SM (EPI_OV has K = N, a few blocks; EPI_STORE
-  // overlaps one CTA's epilogue with the other's loads)
-  constexpr int NST = (NPL == 4) ? 3 : 2;
-  extern __shared__ uint8_t gsm_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
-                                             ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + NST * SBYTES);
-  // bars[0..NST): full, bars[NST..2 NST): empty, bars[2 NST]: accumulator done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 1);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  const int bm = blockIdx.x, bn = blockIdx.y, kc = blockIdx.z;
-  const int kb0 = kc * kb_per_chunk, kb1 = min(nkb, kb0 + kb_per_chunk);
-  const int nk = kb1 - kb0;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // EPI_OV: this thread's row of t for the tile's 64 hidden units is loaded now, so that
-  // the loads overlap the main loop (t does not depend on the products)
-  float2 tp[EPI == EPI_OV ? 64 : 1];
-  if (EPI == EPI_OV) {
-    const int64_t m = (int64_t)bm * BM + threadIdx.x;
-    const int jb = bn * (BN / 2);
-    if (m < n && (M & 1) == 0 && jb + 64 <= M) {
-      const float4* tq = reinterpret_cast<const float4*>(T + m * M + jb);
-#pragma unroll
-      for (int h = 0; h < 32; ++h) {
-        const float4 f = tq[h];
-        tp[2 * h] = make_float2(f.x, f.y);
-        tp[2 * h + 1] = make_float2(f.z, f.w);
-      }
-    } else {
-#pragma unroll
-      for (int h = 0; h < 64; ++h)
-        tp[h] = (m < n && jb + h < M) ? T[m * M + jb + h] : make_float2(0.f, 0.f);
-    }
-  }
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < 2 * NST + 1; ++s) mbar_init(smem_u32(&bars[s]), 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(128) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = *tmem_slot;
-  if (warp == 0 && lane == 0) {
-    int issued = 0;
-    for (int k = 0; k < nk; ++k) {
-      const int s = k % NST;
-      if (k >= NST && !mbar_wait(smem_u32(&bars[NST + s]), ((k / NST) + 1) & 1, abort_flag)) break;
-      uint8_t* st = smem + s * SBYTES;
-      const uint32_t full = smem_u32(&bars[s]);
-      const int x = (kb0 + k) * BK;
-      mbar_expect_tx(full, SBYTES);
-      int pl = 0;
-      tma_load_2d(smem_u32(st + (pl++) * TILE_BYTES), &map_ahi, x, bm * BM, full);
-      if (SPLIT_A) tma_load_2d(smem_u32(st + (pl++) * TILE_BYTES), &map_alo, x, bm * BM, full);
-      tma_load_2d(smem_u32(st + (pl++) * TILE_BYTES), &map_bhi, x, bn * BN, full);
-      if (SPLIT_B) tma_load_2d(smem_u32(st + (pl++) * TILE_BYTES), &map_blo, x, bn * BN, full);
-      issued = k + 1;
-    }
-    if (*abort_flag) {
-      volatile int dummy = 0;
-      for (int k = (issued > NST ? issued - NST : 0); k < issued; ++k)
-        mbar_wait(smem_u32(&bars[k % NST]), (k / NST) & 1, &dummy);
-    }
-  } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
-    bool any = false;
-    for (int k = 0; k < nk; ++k) {
-      const int s = k % NST;
-      if (!mbar_wait(smem_u32(&bars[s]), (k / NST) & 1, abort_flag)) break;
-      fence_after();
-      uint8_t* st = smem + s * SBYTES;
-      int pl = 0;
-      const uint64_t ah = smem_desc_sw128(smem_u32(st + (pl++) * TILE_BYTES));
-      const uint64_t al = SPLIT_A ? smem_desc_sw128(smem_u32(st + (pl++) * TILE_BYTES)) : 0;
-      const uint64_t bh = smem_desc_sw128(smem_u32(st + (pl++) * TILE_BYTES));
-      const uint64_t bl = SPLIT_B ? smem_desc_sw128(smem_u32(st + (pl++) * TILE_BYTES)) : 0;
-#pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint64_t o = (uint64_t)(kk * 32) >> 4;
-        mma_bf16(tmem, ah + o, bh + o, idesc, (k > 0 || kk > 0) ? 1u : 0u);
-        if (SPLIT_B) mma_bf16(tmem, ah + o, bl + o, idesc, 1u);
-        if (SPLIT_A) mma_bf16(tmem, al + o, bh + o, idesc, 1u);
-      }
-      any = true;
-      mma_commit(smem_u32(&bars[NST + s]));
-    }
-    if (any) {
-      mma_commit(smem_u32(&bars[2 * NST]));
-      if (*abort_flag) {                            // products in flight finish before TMEM is freed
-        volatile int dummy = 0;
-        mbar_wait(smem_u32(&bars[2 * NST]), 0, &dummy);
-      }
-    }
-  }
-  __syncwarp();
-  const bool ok = nk > 0 && mbar_wait(smem_u32(&bars[2 * NST]), 0, abort_flag) && !*abort_flag;
-  fence_after();
-  if (ok) {
-    const int r = warp * 32 + lane;
-    const int64_t m = (int64_t)bm * BM + r;
-    if (EPI == EPI_STORE) {
-      float* orow = out + ((int64_t)kc * out_rows + m) * out_ld + (int64_t)bn * BN;
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        if (m < out_rows)
-#pragma unroll
-          for (int q = 0; q < 32; q += 4)
-            *reinterpret_cast<float4*>(orow + c0 + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
-      }
-    } else {
-      // rows 2M, 2M+1 of B carry v_a: the pseudo-unit j = M adds sum_i s_qi v_a,i as is
-      float ar = 0.f, ai = 0.f;
-#pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-        const int jb = bn * (BN / 2) + (c0 >> 1);
-        if (m < n && jb < M) {
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = jb + jj;
-            const float2 t = tp[(c0 >> 1) + jj];
-            if (j < M) {
-              const float2 b = vb[j];
-              const float zr = v[2 * jj] + b.x, zi = v[2 * jj + 1] + b.y;
-              ar = fmaf(t.x, zr, fmaf(-t.y, zi, ar));
-              ai = fmaf(t.x, zi, fmaf(t.y, zr, ai));
-            } else if (j == M) {
-              ar += v[2 * jj];
-              ai += v[2 * jj + 1];
-            }
-          }
-        } else if (m < n && jb <= M && M < jb + 16) {
-          const int jj = M - jb;
-          ar += v[2 * jj];
-          ai += v[2 * jj + 1];
-        }
-      }
-      if (m < n) part[(int64_t)bn * n + m] = make_float2(ar, ai);
-    }
-  }
-  fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
-                 : "memory");
-  }
-  if (threadIdx.x == 0 && *abort_flag) flag_error(status, DEV_ERR_TIMEOUT);
-}
-
 // Failure-path self-test: the tensor-core kernels' bounded mbarrier wait on a barrier that
 // nothing arrives at must give up, set the abort flag and report DEV_ERR_TIMEOUT.
 __global__ void k_selftest_mbar_wait(unsigned* status) {
@@ -628,8 +332,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-static cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows,
-                            int64_t ld) {
+cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t ld) {
   PFN_cuTensorMapEncodeTiled_v12000 encode = encode_tiled();
   if (!encode) return cudaErrorNotSupported;
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
@@ -644,8 +347,8 @@ static cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// one CTA per SM (the kernel's shared memory allows no second one), at most one per tile
-static unsigned persistent_grid(int64_t tiles) {
+// one CTA per SM (the kernels' shared memory allows no second one), at most one per tile
+unsigned persistent_grid(int64_t tiles) {
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -718,64 +421,6 @@ cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, i
       mhi, mlo, (int)(K / tc::BK), (int)nt, tiles, n, 1.0, nullptr, nullptr, nullptr, 0.0, 0, 0,
       A32, ldA, off, 1, (int)(K / tc::BK), nullptr, status);
   return cudaGetLastError();
-}
-
-// D = A B^T with A planes [a_rows][K] and B planes [b_rows][K] (BF16, K-major, ld = K);
-// a_rows, b_rows multiples of 128, K a multiple of 64 (zero padded).  split_a / split_b say
-// whether the operand has a lo plane.  EPI_STORE: out [kchunks][a_rows][b_rows] FP32 with
-// K cut into chunks of kb_per_chunk blocks of 64.  EPI_OV: see the kernel.
-template <bool SA, bool SB, int EPI>
-static cudaError_t gemm_launch(const CUtensorMap& ahi, const CUtensorMap& alo,
-                               const CUtensorMap& bhi, const CUtensorMap& blo, dim3 grid,
-                               int kb_per_chunk, int nkb, float* out, int64_t out_rows,
-                               int64_t out_ld, const float2* T, const float2* vb, int M,
-                               int64_t n, float2* part, unsigned* status, cudaStream_t st) {
-  constexpr int NPL = (SA ? 2 : 1) + (SB ? 2 : 1);
-  constexpr int NST = (NPL == 4) ? 3 : 2;
-  constexpr int smem = 1024 + NST * NPL * tc::TILE_BYTES + 256;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<SA, SB, EPI>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  k_gemm_tc<SA, SB, EPI><<<grid, 128, smem, st>>>(ahi, alo, bhi, blo, kb_per_chunk, nkb, out,
-                                                  out_rows, out_ld, T, vb, M, n, part, status);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, int64_t s_rows, int64_t K,
-                            const __nv_bfloat16* Vhi, const __nv_bfloat16* Vlo, int64_t v_rows,
-                            const float2* T, const float2* vb, int M, int64_t n, float2* part,
-                            unsigned* status, cudaStream_t st) {
-  if (s_rows % tc::BM || v_rows % tc::BN || K % tc::BK || K < tc::BK) return cudaErrorNotSupported;
-  CUtensorMap ma, mbh, mbl;
-  cudaError_t e;
-  if ((e = make_map(&ma, Sb, s_rows, K)) != cudaSuccess) return e;
-  if ((e = make_map(&mbh, Vhi, v_rows, K)) != cudaSuccess) return e;
-  if ((e = make_map(&mbl, Vlo, v_rows, K)) != cudaSuccess) return e;
-  const int nkb = (int)(K / tc::BK);
-  dim3 grid((unsigned)(s_rows / tc::BM), (unsigned)(v_rows / tc::BN), 1);
-  return gemm_launch<false, true, tc::EPI_OV>(ma, ma, mbh, mbl, grid, nkb, nkb, nullptr, 0, 0, T,
-                                              vb, M, n, part, status, st);
-}
-
-cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int64_t a_rows,
-                             const __nv_bfloat16* Bs, int64_t b_rows, int64_t K,
-                             int kb_per_chunk, float* out, unsigned* status, cudaStream_t st) {
-  if (a_rows % tc::BM || b_rows % tc::BN || K % tc::BK || K < tc::BK) return cudaErrorNotSupported;
-  CUtensorMap mah, mal, mb;
-  cudaError_t e;
-  if ((e = make_map(&mah, Ahi, a_rows, K)) != cudaSuccess) return e;
-  if ((e = make_map(&mal, Alo, a_rows, K)) != cudaSuccess) return e;
-  if ((e = make_map(&mb, Bs, b_rows, K)) != cudaSuccess) return e;
-  const int nkb = (int)(K / tc::BK);
-  const int kc = (nkb + kb_per_chunk - 1) / kb_per_chunk;
-  dim3 grid((unsigned)(a_rows / tc::BM), (unsigned)(b_rows / tc::BN), (unsigned)kc);
-  return gemm_launch<true, false, tc::EPI_STORE>(mah, mal, mb, mb, grid, kb_per_chunk, nkb, out,
-                                                 a_rows, b_rows, nullptr, nullptr, 0, 0, nullptr,
-                                                 status, st);
 }
 
 }  // namespace vmc

@@ -169,17 +169,30 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
 cudaError_t residual_fp64(const double2* S, const double2* F, const double2* x, double nu,
                           int mode, SolveWork& w, cudaStream_t st, double* relres);
 
-// CG operator products on the tensor cores (gram_tc.cu):
-//   Ov:  part[n tile][q] = sum_{j in tile} t_qj (v_b,j + sum_i s_qi V_ji), Sb = spins as BF16
-//        [s_rows][K], V planes [v_rows][K] (rows 2j / 2j+1 = Re / Im of V_j)
-//   OhU: out[kc][a_rows][b_rows] = chunk kc of A B^T, A = hi/lo planes [a_rows][K], B exact
-cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, int64_t s_rows, int64_t K,
-                            const __nv_bfloat16* Vhi, const __nv_bfloat16* Vlo, int64_t v_rows,
-                            const float2* T, const float2* vb, int M, int64_t n, float2* part,
-                            unsigned* status, cudaStream_t st);
-cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Ahi, const __nv_bfloat16* Alo, int64_t a_rows,
-                             const __nv_bfloat16* Bs, int64_t b_rows, int64_t K,
-                             int kb_per_chunk, float* out, unsigned* status, cudaStream_t st);
+// min(tiles, number of SMs), at least 1: the grid of the persistent tensor-core kernels
+unsigned persistent_grid(int64_t tiles);
+
+// CG operator products on the tensor cores (cg_tc.cu).  Shapes for N <= 256:
+//   Sb [s_rows][kN] spins as BF16 (s_rows = n padded to 256), V planes [v_rows][kN] (rows
+//   2j / 2j+1 = Re / Im V_j, 2M / 2M+1 = Re / Im v_a), Bs [b_rows][ldK] = spins^T;
+//   out [kchunks][mtiles * 128][nbt * 128] and ybpart [kchunks][M] are the OhU partials.
+struct CgTcShape {
+  int64_t kN, s_rows, v_rows, ldK, b_rows;
+  int nbt, mtiles, nkpc, kchunks;
+  bool ok;
+};
+CgTcShape cg_tc_shape(int N, int M, int64_t n);
+// u_q = sum_j t_qj (v_b,j + (Sb V^T)_qj) + (Sb V^T)_q,M - c; upart[b] = FP64 sum of u over
+// CTA b's samples, *nup = number of CTAs
+cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
+                            const __nv_bfloat16* Vlo, const CgTcShape& sh, const float2* T,
+                            const float2* vb, const double* c, int M, int64_t n, float2* u,
+                            double2* upart, int* nup, unsigned* status, cudaStream_t st);
+// chunk partials of sum_q A_rq s_qi with A rows 2j / 2j+1 = Re / Im conj(t_qj) w_q, rows
+// 2M / 2M+1 = Re / Im w_q, w = u - mean(u) (mean from upart), and of sum_q conj(t_qj) w_q
+cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const float2* T,
+                             const float2* u, const double2* upart, int nup, int M, int64_t n,
+                             float* out, float2* ybpart, unsigned* status, cudaStream_t st);
 
 // failure-path self-tests of the bounded waits (a flag / an mbarrier that nothing sets)
 cudaError_t launch_selftest_flag_wait(unsigned* word2, unsigned* status, cudaStream_t st);
@@ -210,11 +223,12 @@ struct CgWork {
   double2* c2;                        // [8] device complex scalars
   double* sc;                         // [8] device real scalars
   // tensor-core operator (capacities in elements; null when not allocated)
-  __nv_bfloat16 *Sb, *Bs, *Vhi, *Vlo, *Ahi, *Alo;
-  float* part2;
-  int64_t cap_sb, cap_bs, cap_v, cap_a, cap_part2;
+  __nv_bfloat16 *Sb, *Bs, *Vhi, *Vlo;
+  float* part2;                       // OhU chunk partials
+  float2* ybpart;                     // [kchunks][M]
+  double2* ovpart;                    // [grid] FP64 sums of u per Ov CTA
+  int64_t cap_sb, cap_bs, cap_v, cap_part2, cap_yb, cap_ov;
 };
-constexpr int CG_KB_PER_CHUNK = 32;   // K chunk (blocks of 64 samples) of the Obar^H u product
 int64_t cg_partial_floats2(int64_t n, int M);
 // diag(S) and the conjugated means; T and meanO must describe the sample set
 cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cudaStream_t st,
