@@ -183,6 +183,13 @@ vmc_status vmc_solve(vmc_ctx* ctx, int lattice, const double* S, const double* F
 vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
                         const double* F, double* x, int* iters, double* relres);
 
+/* One application y = S~ v of the operator vmc_cg_solve iterates with (same sample set
+ * conventions, same arithmetic: the tensor-core products for VMC_PREC_BF16SPLIT contexts
+ * with N <= 256, FP32 SIMT products otherwise).  v, y: dev double [P][2], v read only.
+ * Only for contexts created for the CG solver. */
+vmc_status vmc_sr_apply(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                        const double* v, double* y);
+
 /* One full SR step (Algorithm 1, then the Euler update theta <- theta - dt x of
  * imaginary-time TDVP, Eq. stochastic_reconfiguration): sample Ns configurations, local
  * energies, log-derivatives, S and F, regularised solve, parameter update.  stats (host)

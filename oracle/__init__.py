@@ -18,6 +18,7 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   sr_matrices     -- pinned: exact-energy finite-difference gradient (F), fidelity
                      expansion (S), Hermitian PSD, Sz = 0 null mode
   cholesky_solve  -- pinned: residual and numpy.linalg.solve
+  sr_apply        -- pinned: equals shift(sr_matrices S) v formed densely
   cg_solve        -- pinned: agrees with the dense solve, residual
   metropolis      -- pinned: chi-square of the histogram against exact |psi|^2
   philox4x64      -- pinned: numpy.random.Philox bit-for-bit
@@ -77,6 +78,7 @@ def _load():
             "orc_shift": (i32, [i64, P, f64, i32]),
             "orc_cholesky_solve": (i32, [i64, P, P, P]),
             "orc_cg_solve": (i32, [i64, i64, P, P, f64, i32, f64, i32, P, P, P]),
+            "orc_sr_apply": (i32, [i64, i64, P, f64, i32, P, P]),
             "orc_update": (i32, [i64, P, P, f64]),
             "orc_metropolis": (i32, [i32, i32, i32, i32, P, i64, P, u64, u64, u64, u64, i32, i32,
                                      P, P, P]),
@@ -243,6 +245,17 @@ def cholesky_solve(S: np.ndarray, F: np.ndarray) -> np.ndarray:
                                       _ptr(F.view(np.float64)), _ptr(x.view(np.float64))),
            "cholesky_solve")
     return x
+
+
+def sr_apply(O: np.ndarray, v: np.ndarray, nu: float, mode: int = 0) -> np.ndarray:
+    """S~ v = (1/Ns) Obar^H (Obar v) + D v without forming S (D = nu diag(S), or nu)."""
+    O = np.ascontiguousarray(O, dtype=np.complex128)
+    v = np.ascontiguousarray(v, dtype=np.complex128)
+    Ns, P = O.shape
+    y = np.zeros(P, dtype=np.complex128)
+    _check(_load().orc_sr_apply(Ns, P, _ptr(O.view(np.float64)), float(nu), int(mode),
+                                _ptr(v.view(np.float64)), _ptr(y.view(np.float64))), "sr_apply")
+    return y
 
 
 def cg_solve(O: np.ndarray, F: np.ndarray, nu: float, mode: int = 0, tol: float = 1e-10,

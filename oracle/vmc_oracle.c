@@ -404,11 +404,58 @@ int orc_cholesky_solve(int64_t P, const double* S, const double* F, double* x) {
 }
 
 /* ------------------------------------------------------------------------------------ */
-/* Matrix-free conjugate gradient for S~ x = F with                                       */
+/* The shifted Fisher matrix applied without storing it (Carleo & Troyer CG, "Diagonal    */
+/* shift" subsection):                                                                    */
 /*   S~ v = (1/Ns) Obar^H (Obar v) + D v,   Obar = O - <O>,  D = nu diag(S) (mode 0)     */
-/*   or D = nu (mode 1),                                                                  */
-/* which is the shifted Fisher matrix applied without storing it (Carleo & Troyer CG,     */
-/* "Diagonal shift" subsection).  Plain CG, FP64, x0 = 0; stops when ||r|| <= tol ||F||.  */
+/*   or D = nu (mode 1).                                                                  */
+/* sr_operator_setup forms <O> and D; sr_operator_apply forms q = S~ p (u: Ns scratch).   */
+/* ------------------------------------------------------------------------------------ */
+static void sr_operator_setup(int64_t Ns, int64_t P, const cd* o, double nu, int mode, cd* mo,
+                              double* diag) {
+  for (int64_t k = 0; k < P; ++k) {
+    cd acc = 0.0;
+    for (int64_t n = 0; n < Ns; ++n) acc += o[n * P + k];
+    mo[k] = acc / (double)Ns;
+  }
+  for (int64_t k = 0; k < P; ++k) {
+    double acc = 0.0;
+    for (int64_t n = 0; n < Ns; ++n) { cd d = o[n * P + k] - mo[k]; acc += creal(d * conj(d)); }
+    diag[k] = (mode == 0) ? nu * acc / (double)Ns : nu;
+  }
+}
+
+static void sr_operator_apply(int64_t Ns, int64_t P, const cd* o, const cd* mo,
+                              const double* diag, const cd* p, cd* u, cd* q) {
+#pragma omp parallel for schedule(static)
+  for (int64_t n = 0; n < Ns; ++n) {
+    cd acc = 0.0;
+    for (int64_t k = 0; k < P; ++k) acc += (o[n * P + k] - mo[k]) * p[k];
+    u[n] = acc;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < P; ++k) {
+    cd acc = 0.0;
+    for (int64_t n = 0; n < Ns; ++n) acc += conj(o[n * P + k] - mo[k]) * u[n];
+    q[k] = acc / (double)Ns + diag[k] * p[k];
+  }
+}
+
+/* y = S~ v once.  O[Ns][P][2], v[P][2] in; y[P][2] out.                                 */
+int orc_sr_apply(int64_t Ns, int64_t P, const double* O, double nu, int mode, const double* v,
+                 double* y) {
+  if (Ns < 1 || P < 1 || !O || !v || !y) return ORC_ERR_ARG;
+  cd* mo = (cd*)calloc((size_t)P, sizeof(cd));
+  double* diag = (double*)calloc((size_t)P, sizeof(double));
+  cd* u = (cd*)malloc(sizeof(cd) * (size_t)Ns);
+  sr_operator_setup(Ns, P, (const cd*)O, nu, mode, mo, diag);
+  sr_operator_apply(Ns, P, (const cd*)O, mo, diag, (const cd*)v, u, (cd*)y);
+  free(mo); free(diag); free(u);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Matrix-free conjugate gradient for S~ x = F with the operator above.  Plain CG, FP64,  */
+/* x0 = 0; stops when ||r|| <= tol ||F||.                                                 */
 /* O[Ns][P][2], F[P][2] in; x[P][2] out; *iters and *relres report the finish.           */
 /* ------------------------------------------------------------------------------------ */
 int orc_cg_solve(int64_t Ns, int64_t P, const double* O, const double* F, double nu, int mode,
@@ -423,35 +470,14 @@ int orc_cg_solve(int64_t Ns, int64_t P, const double* O, const double* F, double
   cd* p = (cd*)malloc(sizeof(cd) * (size_t)P);
   cd* q = (cd*)malloc(sizeof(cd) * (size_t)P);
   cd* u = (cd*)malloc(sizeof(cd) * (size_t)Ns);
-  for (int64_t k = 0; k < P; ++k) {
-    cd acc = 0.0;
-    for (int64_t n = 0; n < Ns; ++n) acc += o[n * P + k];
-    mo[k] = acc / (double)Ns;
-  }
-  for (int64_t k = 0; k < P; ++k) {
-    double acc = 0.0;
-    for (int64_t n = 0; n < Ns; ++n) { cd d = o[n * P + k] - mo[k]; acc += creal(d * conj(d)); }
-    diag[k] = (mode == 0) ? nu * acc / (double)Ns : nu;
-  }
+  sr_operator_setup(Ns, P, o, nu, mode, mo, diag);
   double fn = 0.0;
   for (int64_t k = 0; k < P; ++k) { xo[k] = 0.0; r[k] = f[k]; p[k] = f[k]; fn += creal(f[k] * conj(f[k])); }
   fn = sqrt(fn);
   double rr = fn * fn;
   int it = 0;
   while (it < maxit && sqrt(rr) > tol * fn) {
-    /* q = S~ p */
-#pragma omp parallel for schedule(static)
-    for (int64_t n = 0; n < Ns; ++n) {
-      cd acc = 0.0;
-      for (int64_t k = 0; k < P; ++k) acc += (o[n * P + k] - mo[k]) * p[k];
-      u[n] = acc;
-    }
-#pragma omp parallel for schedule(static)
-    for (int64_t k = 0; k < P; ++k) {
-      cd acc = 0.0;
-      for (int64_t n = 0; n < Ns; ++n) acc += conj(o[n * P + k] - mo[k]) * u[n];
-      q[k] = acc / (double)Ns + diag[k] * p[k];
-    }
+    sr_operator_apply(Ns, P, o, mo, diag, p, u, q);   /* q = S~ p */
     cd pq = 0.0;
     for (int64_t k = 0; k < P; ++k) pq += conj(p[k]) * q[k];
     double alpha = rr / creal(pq);

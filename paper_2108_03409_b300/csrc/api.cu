@@ -354,12 +354,15 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &w.meanO_c, P)) || (e = dalloc(ctx, &w.D, P)) ||
         (e = dalloc(ctx, &w.Minv, P)) || (e = dalloc(ctx, &w.t2, ctx->Mmax)) ||
         (e = dalloc(ctx, &w.va, ctx->Nmax)) || (e = dalloc(ctx, &w.vb, ctx->Mmax)) ||
-        (e = dalloc(ctx, &w.V, (size_t)ctx->Nmax * ctx->Mmax)) || (e = dalloc(ctx, &w.u, Ns)) ||
+        (e = dalloc(ctx, &w.V, (size_t)ctx->Nmax * ctx->Mmax)) || (e = dalloc(ctx, &w.u, (Ns + 255) / 256 * 256)) ||
         (e = dalloc(ctx, &w.upart, (size_t)cg_partial_floats2(Ns, ctx->Mmax))) ||
         (e = dalloc(ctx, &w.ustats, 8)) || (e = dalloc(ctx, &w.dpart, 256)) ||
         (e = dalloc(ctx, &w.c2, 8)) || (e = dalloc(ctx, &w.sc, 8)))
       return oom(e);
     w.mpart = ctx->partial;
+    // u stays finite beyond the sample count (the OhU kernel reads whole 64-sample blocks)
+    if ((e = cudaMemset(w.u, 0, sizeof(float2) * (size_t)((Ns + 255) / 256 * 256))) != cudaSuccess)
+      return oom(e);
     if (!ctx->dense && cfg->precision == VMC_PREC_BF16SPLIT) {
       // operator products on the tensor cores: operand planes sized for the largest lattice
       // (every lattice's shape is bounded by the largest N, M; the OhU grid by the SMs)
@@ -631,6 +634,27 @@ vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
   if ((s = check_status(ctx, "cg_solve"))) return s;
   if (!(rel == rel)) return fail(ctx, VMC_ERR_NUMERIC, "CG produced a non-finite residual");
   return VMC_OK;
+}
+
+vmc_status vmc_sr_apply(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                        const double* v, double* y) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 1 || n > ctx->Ns || !spins || !v || !y) return fail(ctx, VMC_ERR_ARG, "bad arguments");
+  if (ctx->dense) return fail(ctx, VMC_ERR_STATE, "context was created for a dense solver");
+  LatticeState& L = ctx->lats[lattice];
+  const vmc_config& c = ctx->cfg;
+  CK(launch_theta_tanh(rbm_of(L), spins, n, ctx->s_T, ctx->st), "theta_tanh");
+  CK(launch_moments(spins, ctx->s_T, nullptr, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
+                    nullptr, ctx->st), "moments");
+  ctx->launches += 3;
+  CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO, nullptr,
+               ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, n).ok, ctx->status};
+  CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
+  CK(cg_apply(pb, ctx->cg, reinterpret_cast<const double2*>(v), reinterpret_cast<double2*>(y),
+              ctx->st, &ctx->launches), "cg_apply");
+  CK(cudaStreamSynchronize(ctx->st), "cg_apply");
+  return check_status(ctx, "cg_apply");
 }
 
 vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats) {

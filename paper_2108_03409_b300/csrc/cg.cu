@@ -477,6 +477,13 @@ cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cuda
   return cudaGetLastError();
 }
 
+cudaError_t cg_apply(const CgProblem& pb_in, CgWork& w, const double2* v, double2* y,
+                     cudaStream_t st, int64_t* launches) {
+  CgProblem pb = pb_in;
+  pb.meanO_conj_free = w.meanO_c;
+  return apply_s(pb, w, v, y, st, launches);
+}
+
 cudaError_t cg_solve(const CgProblem& pb_in, const double2* F, double2* x, double tol, int maxit,
                      CgWork& w, cudaStream_t st, int64_t* launches, int* iters, double* relres) {
   CgProblem pb = pb_in;

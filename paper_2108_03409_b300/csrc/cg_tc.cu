@@ -37,10 +37,15 @@ constexpr int OV_A_BYTES = OV_MAX_NKB * 2 * TILE;
 constexpr int OV_STAGE_BYTES = 2 * TILE;        // V hi, V lo (128 rows each)
 constexpr int OV_SMEM = 1024 + OV_A_BYTES + OV_STAGES * OV_STAGE_BYTES + TAIL;
 constexpr int OV_TMEM_COLS = 512;               // two buffers x two sub-tiles x 128 columns
-// OhU: A hi, A lo (formed in place), B = spins^T (up to 256 rows)
-constexpr int OH_STAGES = 3;
-constexpr int OH_STAGE_BYTES = 4 * TILE;
+// OhU: per stage B = spins^T (up to 256 rows) and the block's 64 values of u in shared
+// memory; A (hi, lo) in tensor memory
+constexpr int OH_STAGES = 4;
+constexpr int OH_B_BYTES = 2 * TILE;
+constexpr int OH_U_BYTES = 64 * 8;
+constexpr int OH_STAGE_BYTES = OH_B_BYTES + 1024;         // stages stay 1024-byte aligned
 constexpr int OH_SMEM = 1024 + OH_STAGES * OH_STAGE_BYTES + TAIL;
+constexpr int OH_TMEM_COLS = 512;                         // accumulator + 4 A stages
+static_assert(256 + OH_STAGES * 64 <= OH_TMEM_COLS, "tensor memory budget");
 static_assert(OV_SMEM <= 232448 && OH_SMEM <= 232448, "shared memory budget");
 
 __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
@@ -55,9 +60,13 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<const uint32_t*>(&h);
+// two FP32 values as packed BF16 pairs x = hi + lo (hi = RN(x), lo = RN(x - hi))
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 }  // namespace cgtc
 
@@ -73,7 +82,8 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(cgtc::THREADS, 1)
 k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUtensorMap map_vhi,
-        const __grid_constant__ CUtensorMap map_vlo, int nkb, int nct, int64_t items,
+        const __grid_constant__ CUtensorMap map_vlo, const __grid_constant__ CUtensorMap map_t,
+        int prefetch_t, int nkb, int nct, int64_t items,
         const float2* __restrict__ T, const float2* __restrict__ vb, const double* __restrict__ c,
         int M, int64_t n, float2* __restrict__ u, double2* __restrict__ upart,
         unsigned* status) {
@@ -133,7 +143,10 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
           last_it = it;
           last_kb = kb;
         }
-        for (int ct = 0; ct < nct && ok; ++ct)
+        for (int ct = 0; ct < nct && ok; ++ct) {
+          // t of this column tile's 256 samples into L2: the epilogue reads it one or two
+          // column tiles from now
+          if (prefetch_t) tma_prefetch_2d(&map_t, ct * 64, (int)(w * 256));
           for (int kb = 0; kb < nkb; ++kb, ++g) {
             const int s = (int)(g % OV_STAGES);
             if (g >= OV_STAGES &&
@@ -147,6 +160,7 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
             tma_load_2d(smem_u32(st), &map_vhi, kb * 64, ct * 128, fb);
             tma_load_2d(smem_u32(st + TILE), &map_vlo, kb * 64, ct * 128, fb);
           }
+        }
       }
       if (*abort_flag) {
         // copies in flight land before the CTA exits (bounded)
@@ -220,71 +234,98 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
     const int r = qd * 32 + lane;
     const bool vec = (M & 1) == 0;
     const float cre = (float)c[0], cim = (float)c[1];
-    // The thread's work is a sequence of quarters g = 0, 1, ...: quarter g covers hidden
-    // units 16 (g % 4) .. + 15 of column tile (g / 4) % nct of the CTA's item g / (4 nct).
-    // Its 16 values of t are loaded two quarters ahead into one of three rotating buffers.
-    const int64_t my_items = (items - blockIdx.x + gridDim.x - 1) / gridDim.x;
-    const int64_t nq = my_items * nct * 4;
-    auto load_t = [&](int64_t g, float4 (&dst)[8]) {
-      if (g >= nq) return;
-      const int64_t w = blockIdx.x + (g / (4 * nct)) * gridDim.x;
-      const int64_t m = w * 256 + sub * 128 + r;
-      const int j0 = (int)((g >> 2) % nct) * 64 + (int)(g & 3) * 16;
+    // The thread's work is a sequence of quarters: quarter (item w, column tile ct, qtr)
+    // covers hidden units 64 ct + 16 qtr .. + 15 of the thread's sample in item w.  A
+    // quarter's t is loaded two quarters ahead into one of three rotating buffers; two
+    // cursors (the quarter in use, the quarter being loaded) advance without divisions.
+    struct Cursor {
+      int64_t w;
+      int ct, qtr;
+    };
+    auto advance = [&](Cursor& k) {
+      if (++k.qtr == 4) {
+        k.qtr = 0;
+        if (++k.ct == nct) {
+          k.ct = 0;
+          k.w += gridDim.x;
+        }
+      }
+    };
+    auto load_t = [&](const Cursor& k, float4 (&dst)[8]) {
+      if (k.w >= items) return;
+      const int64_t m = k.w * 256 + sub * 128 + r;
+      const int j0 = k.ct * 64 + k.qtr * 16;
       if (m < n && vec && j0 + 16 <= M) {
         const float4* src = reinterpret_cast<const float4*>(T + m * M + j0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) dst[k] = src[k];
+        for (int k2 = 0; k2 < 8; ++k2) dst[k2] = src[k2];
       } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int j = j0 + 2 * k;
+        for (int k2 = 0; k2 < 8; ++k2) {
+          const int j = j0 + 2 * k2;
           const float2 x = (m < n && j < M) ? T[m * M + j] : make_float2(0.f, 0.f);
           const float2 y = (m < n && j + 1 < M) ? T[m * M + j + 1] : make_float2(0.f, 0.f);
-          dst[k] = make_float4(x.x, x.y, y.x, y.y);
+          dst[k2] = make_float4(x.x, x.y, y.x, y.y);
         }
       }
     };
     double usr = 0.0, usi = 0.0;
     float ar = 0.f, ai = 0.f;
     bool ok = true;
-    // quarter g from buffer cur; quarter g + 2 into buffer ahead (the one quarter g - 1 used)
-    auto step = [&](int64_t g, const float4 (&cur)[8], float4 (&ahead)[8]) {
-      if (!ok || g >= nq) return;
-      load_t(g + 2, ahead);
-      const int64_t cc = g >> 2;                  // column tiles so far
-      const int b = (int)(cc & 1), qtr = (int)(g & 3), ct = (int)(cc % nct);
-      if (qtr == 0) {
+    int64_t cc = 0;                                 // column tiles completed
+    Cursor use{(int64_t)blockIdx.x, 0, 0}, ahead = use;
+    auto step = [&](const float4 (&cur)[8], float4 (&nxt)[8]) {
+      if (!ok || use.w >= items) return;
+      load_t(ahead, nxt);
+      advance(ahead);
+      const int b = (int)(cc & 1);
+      if (use.qtr == 0) {
         if (!warp_wait(smem_u32(&accf[b]), (uint32_t)((cc >> 1) & 1), abort_flag, lane)) {
           ok = false;
           return;
         }
         fence_after();
       }
+      const int jb = use.ct * 64 + use.qtr * 16;
       float v[32];
-      tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * 256 + sub * 128 + qtr * 32), v);
-      const int jb = ct * 64 + qtr * 16;
+      tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * 256 + sub * 128 + use.qtr * 32), v);
+      if (jb + 16 <= M) {
+        const float4* vb4 = reinterpret_cast<const float4*>(vb + jb);
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        const int j = jb + jj;
-        const float4 t4 = cur[jj >> 1];
-        const float tr = (jj & 1) ? t4.z : t4.x, ti = (jj & 1) ? t4.w : t4.y;
-        if (j < M) {
-          const float2 bj = vb[j];
-          const float zr = v[2 * jj] + bj.x, zi = v[2 * jj + 1] + bj.y;
-          ar = fmaf(tr, zr, fmaf(-ti, zi, ar));
-          ai = fmaf(tr, zi, fmaf(ti, zr, ai));
-        } else if (j == M) {                       // rows 2M / 2M+1: sum_i s_qi v_a,i as is
-          ar += v[2 * jj];
-          ai += v[2 * jj + 1];
+        for (int h = 0; h < 8; ++h) {              // hidden units jb + 2h, jb + 2h + 1
+          const float4 bb = vb4[h], tt = cur[h];
+          float zr = v[4 * h] + bb.x, zi = v[4 * h + 1] + bb.y;
+          ar = fmaf(tt.x, zr, fmaf(-tt.y, zi, ar));
+          ai = fmaf(tt.x, zi, fmaf(tt.y, zr, ai));
+          zr = v[4 * h + 2] + bb.z;
+          zi = v[4 * h + 3] + bb.w;
+          ar = fmaf(tt.z, zr, fmaf(-tt.w, zi, ar));
+          ai = fmaf(tt.z, zi, fmaf(tt.w, zr, ai));
+        }
+      } else {
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) {
+          const int j = jb + jj;
+          const float4 t4 = cur[jj >> 1];
+          const float tr = (jj & 1) ? t4.z : t4.x, ti = (jj & 1) ? t4.w : t4.y;
+          if (j < M) {
+            const float2 bj = vb[j];
+            const float zr = v[2 * jj] + bj.x, zi = v[2 * jj + 1] + bj.y;
+            ar = fmaf(tr, zr, fmaf(-ti, zi, ar));
+            ai = fmaf(tr, zi, fmaf(ti, zr, ai));
+          } else if (j == M) {                     // rows 2M / 2M+1: sum_i s_qi v_a,i as is
+            ar += v[2 * jj];
+            ai += v[2 * jj + 1];
+          }
         }
       }
-      if (qtr == 3) {
+      if (use.qtr == 3) {
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
-        if (ct == nct - 1) {                       // the item's last column tile: u is complete
-          const int64_t w = blockIdx.x + (g / (4 * nct)) * gridDim.x;
-          const int64_t m = w * 256 + sub * 128 + r;
+        ++cc;
+        if (use.ct == nct - 1) {                   // the item's last column tile: u is complete
+          const int64_t m = use.w * 256 + sub * 128 + r;
           if (m < n) {
             const float ur = ar - cre, ui = ai - cim;
             u[m] = make_float2(ur, ui);
@@ -295,14 +336,17 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
           ai = 0.f;
         }
       }
+      advance(use);
     };
     float4 ta[8], tb[8], tc3[8];
-    load_t(0, ta);
-    load_t(1, tb);
-    for (int64_t g = 0; g < nq && ok; g += 3) {
-      step(g, ta, tc3);
-      step(g + 1, tb, ta);
-      step(g + 2, tc3, tb);
+    load_t(ahead, ta);
+    advance(ahead);
+    load_t(ahead, tb);
+    advance(ahead);
+    while (ok && use.w < items) {
+      step(ta, tc3);
+      step(tb, ta);
+      step(tc3, tb);
     }
     usr = warp_sum_d(usr);
     usi = warp_sum_d(usi);
@@ -329,47 +373,50 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
 
 // ---------------------------------------------------------------------------------------
 // OhU.  CTA (mt, kc): rows [128 mt, 128 mt + 128) of A (hidden units 64 mt ..), K blocks
-// [kc nkpc, ...) of the samples.  Worker thread (jp, kq) forms rows 4jp .. 4jp+3 of the
-// tile (Re / Im of units j0 = 64 mt + 2 jp and j0 + 1) for the eight samples 8 kq .. 8 kq + 7
-// of each 64-sample block: one 16-byte hi and one lo chunk per row, written at the swizzled
-// position (lanes of a warp cover all eight chunk positions of a row group, so the stores
-// are conflict-free); the next block's t and u are loaded before this block is formed.
-// The same threads keep y_b's FP32 partial sums and, at the end, drain the accumulator.
+// [kc nkpc, ...) of the samples.  A is formed in tensor memory, never in shared memory:
+// worker thread r (lane r of its warp's TMEM quadrant) owns row 2j + c of the tile and, for
+// its half of each 64-sample block, loads t_qj of 32 samples (the warp's lanes cover 16
+// consecutive units, so each load instruction reads 128 contiguous bytes of one sample's
+// row), forms component c of conj(t_qj) w_q as a BF16 hi/lo pair and stores the packed
+// pairs into the block's TMEM stage (tcgen05.st); the MMA takes A from TMEM and B =
+// spins^T from shared memory.  w_q = u_q - mean(u) arrives in shared memory beside each B
+// stage (1-D bulk copy of u).  The same threads keep y_b's FP32 partial sums and finally
+// drain the accumulator.  TMEM: accumulator columns [0, 256); A stage s at columns
+// 256 + 64 s (32 hi, then 32 lo; column m holds samples 2m, 2m + 1 of the block).
 // out[kc][128 mt + r][col] = the chunk's FP32 partial of A B^T; ybpart[kc][j] likewise.
 // ---------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(cgtc::THREADS, 1)
-k_cg_ohu(const __grid_constant__ CUtensorMap map_b, int nbt, int nkb, int nkpc, int mtiles,
-         const float2* __restrict__ T, const float2* __restrict__ u,
-         const double2* __restrict__ upart, int nup, int M, int64_t n, float* __restrict__ out,
-         float2* __restrict__ ybpart, unsigned* status) {
+k_cg_ohu(const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_t,
+         int prefetch_t, int nbt, int nkb, int nkpc, int mtiles, const float2* __restrict__ T,
+         const float2* __restrict__ u, const double2* __restrict__ upart, int nup, int M,
+         int64_t n, float* __restrict__ out, float2* __restrict__ ybpart, unsigned* status) {
   using namespace tc;
   using namespace cgtc;
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = align1024(gsm_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OH_STAGES * OH_STAGE_BYTES);
-  uint64_t* fullb = bars;                                 // [3] B landed
-  uint64_t* fulla = bars + 3;                             // [3] A formed (8 warps)
-  uint64_t* empty = bars + 6;                             // [3] stage consumed
-  uint64_t* accf = bars + 9;
-  uint64_t* fin = bars + 10;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
+  uint64_t* fullb = bars;                                 // [4] B and u landed
+  uint64_t* fulla = bars + OH_STAGES;                     // [4] A formed (8 warps)
+  uint64_t* empty = bars + 2 * OH_STAGES;                 // [4] stage consumed
+  uint64_t* accf = bars + 3 * OH_STAGES;
+  uint64_t* fin = accf + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float2* mean = reinterpret_cast<float2*>(bars + 12);
+  float2* mean = reinterpret_cast<float2*>(fin + 2);
 
   const int mt = (int)(blockIdx.x % mtiles), kc = (int)(blockIdx.x / mtiles);
   const int kb0 = kc * nkpc, nk = min(nkb, kb0 + nkpc) - kb0;
   const int ncols = nbt * 128;
-  const uint32_t tmem_cols = (uint32_t)ncols;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 11; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s < 3 * OH_STAGES + 2; ++s) mbar_init(smem_u32(&bars[s]), 1);
     for (int s = 0; s < OH_STAGES; ++s) mbar_init(smem_u32(&fulla[s]), WORKER_WARPS);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(tmem_cols) : "memory");
+                 ::"r"(smem_u32(tmem_slot)), "r"(OH_TMEM_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   fence_before();
@@ -379,18 +426,23 @@ k_cg_ohu(const __grid_constant__ CUtensorMap map_b, int nbt, int nkb, int nkpc, 
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer (B = spins^T) ----------------
+      // ---------------- TMA producer (B = spins^T and u; t of later blocks into L2) ----------
+      constexpr int PF = 4;                               // blocks of t prefetched ahead
+      if (prefetch_t)
+        for (int h = 0; h < PF && h < nk; ++h) tma_prefetch_2d(&map_t, mt * 64, (kb0 + h) * 64);
       int g = 0;
       for (; g < nk; ++g) {
+        if (prefetch_t && g + PF < nk) tma_prefetch_2d(&map_t, mt * 64, (kb0 + g + PF) * 64);
         const int s = g % OH_STAGES;
         if (g >= OH_STAGES &&
             !mbar_wait(smem_u32(&empty[s]), (uint32_t)(((g / OH_STAGES) - 1) & 1), abort_flag))
           break;
-        uint8_t* st = smem + s * OH_STAGE_BYTES + 2 * TILE;
+        uint8_t* st = smem + s * OH_STAGE_BYTES;
         const uint32_t fb = smem_u32(&fullb[s]);
-        mbar_expect_tx(fb, (uint32_t)(nbt * TILE));
+        mbar_expect_tx(fb, (uint32_t)(nbt * TILE + OH_U_BYTES));
         for (int bt = 0; bt < nbt; ++bt)
           tma_load_2d(smem_u32(st + bt * TILE), &map_b, (kb0 + g) * 64, bt * 128, fb);
+        bulk_load(smem_u32(st + OH_B_BYTES), u + (int64_t)(kb0 + g) * 64, OH_U_BYTES, fb);
       }
       if (*abort_flag) {
         volatile int dummy = 0;
@@ -412,15 +464,13 @@ k_cg_ohu(const __grid_constant__ CUtensorMap map_b, int nbt, int nkb, int nkpc, 
           break;
         }
         fence_after();
-        uint8_t* st = smem + s * OH_STAGE_BYTES;
-        const uint64_t ah = smem_desc_sw128(smem_u32(st));
-        const uint64_t al = smem_desc_sw128(smem_u32(st + TILE));
-        const uint64_t bd = smem_desc_sw128(smem_u32(st + 2 * TILE));
+        const uint32_t ah = tmem + (uint32_t)(256 + 64 * s), al = ah + 32u;
+        const uint64_t bd = smem_desc_sw128(smem_u32(smem + s * OH_STAGE_BYTES));
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t o = (uint64_t)(kk * 32) >> 4;
-          mma_bf16(tmem, ah + o, bd + o, idesc, (g > 0 || kk > 0) ? 1u : 0u);
-          mma_bf16(tmem, al + o, bd + o, idesc, 1u);
+          const uint64_t o = (uint64_t)(kk * 32) >> 4;    // 16 BF16 along K
+          mma_bf16_ts(tmem, ah + 8u * kk, bd + o, idesc, (g > 0 || kk > 0) ? 1u : 0u);
+          mma_bf16_ts(tmem, al + 8u * kk, bd + o, idesc, 1u);
         }
         any = true;
         mma_commit(smem_u32(&empty[s]));
@@ -433,10 +483,18 @@ k_cg_ohu(const __grid_constant__ CUtensorMap map_b, int nbt, int nkb, int nkpc, 
       }
     }
   } else {
-    // ---------------- operand formation, y_b partials, then the accumulator ----------------
-    const int ew = warp - 2, et = ew * 32 + lane;
-    const int kq = et & 7, jp = et >> 3;                  // lanes: 4 unit pairs x 8 chunks
-    const int j0 = mt * 64 + 2 * jp, j1 = j0 + 1;
+    // ---------------- A in TMEM, y_b partials, then the accumulator ----------------
+    // TMEM lane L of the tile holds row (j, c) with j = 64 mt + 8 (L / 16) + L % 8 and
+    // c = (L / 8) % 2 (the row order of A is free: D follows it).  Worker warp e writes
+    // lanes 32 (e % 4) + 16 ((e - 2) / 4) .. + 15 with the 16x256b shape: thread t owns unit
+    // jl = t / 4 of the warp's eight, both components (lanes jl and jl + 8), and samples
+    // 16 k + 4 (t % 4) .. + 3 (k = 0..3) of each 64-sample block.
+    const int ew = warp - 2;
+    const int qd = warp & 3, hsel = ew >> 2;
+    const int jl = lane >> 2, cq = lane & 3;
+    const int j = mt * 64 + 8 * (2 * qd + hsel) + jl;
+    const bool jv = j < M, jw = j == M;
+    const uint32_t st_base = (uint32_t)(32 * qd + 16 * hsel) << 16;
     if (ew == 0) {
       // mean(u) from the Ov CTAs' FP64 partials (fixed order)
       double sr = 0.0, si = 0.0;
@@ -450,119 +508,94 @@ k_cg_ohu(const __grid_constant__ CUtensorMap map_b, int nbt, int nkb, int nkpc, 
     }
     named_bar_sync(1, 32 * WORKER_WARPS);
     const float mr = mean->x, mi = mean->y;
-    const bool pair_vec = (M & 1) == 0 && j1 < M;
-    auto load_blk = [&](int g, float4 (&tq)[8], float2 (&uq)[8]) {
-      const int64_t q0 = (int64_t)(kb0 + g) * 64 + 8 * kq;
+    // t of this thread's 16 samples of block g (rows 2M / 2M+1 carry w itself: t = 1;
+    // samples q >= n get t = 0, and u there is finite: zeroed once, only finite values)
+    const int64_t ldT = M;
+    auto load_blk = [&](int g, float2 (&dst)[16]) {
+      if (g >= nk) return;
+      const int64_t qb = (int64_t)(kb0 + g) * 64 + 4 * cq;
+      if (jv && qb + 52 < n) {
+        const float2* tp = T + qb * ldT + j;
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        const int64_t q = q0 + kk;
-        uq[kk] = (q < n) ? u[q] : make_float2(0.f, 0.f);
-        if (q < n && pair_vec) {
-          tq[kk] = *reinterpret_cast<const float4*>(T + q * M + j0);
-        } else {
-          const float2 x = (q < n && j0 < M) ? T[q * M + j0] : make_float2(0.f, 0.f);
-          const float2 y = (q < n && j1 < M) ? T[q * M + j1] : make_float2(0.f, 0.f);
-          tq[kk] = make_float4(x.x, x.y, y.x, y.y);
-        }
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) dst[4 * k + i] = tp[(16 * k + i) * ldT];
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int64_t q = qb + 16 * k + i;
+            const bool q_ok = q < n;
+            dst[4 * k + i] = (jv && q_ok) ? T[q * ldT + j]
+                                          : make_float2((jw && q_ok) ? 1.f : 0.f, 0.f);
+          }
       }
     };
-    float y0r = 0.f, y0i = 0.f, y1r = 0.f, y1i = 0.f;
-    float4 tn[8];
-    float2 un[8];
-    if (nk > 0) load_blk(0, tn, un);
+    float ybr = 0.f, ybi = 0.f;
     bool ok = true;
+    float2 tn[16];
+    load_blk(0, tn);
     for (int g = 0; g < nk; ++g) {
-      float4 tq[8];
-      float2 uq[8];
+      float2 tq[16];
 #pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        tq[kk] = tn[kk];
-        uq[kk] = un[kk];
-      }
-      if (g + 1 < nk) load_blk(g + 1, tn, un);
+      for (int k = 0; k < 16; ++k) tq[k] = tn[k];
+      load_blk(g + 1, tn);
       const int s = g % OH_STAGES;
-      if (g >= OH_STAGES &&
-          !warp_wait(smem_u32(&empty[s]), (uint32_t)(((g / OH_STAGES) - 1) & 1), abort_flag, lane)) {
+      // B and u of block g landed, which also means the MMA is done with A stage s
+      if (!warp_wait(smem_u32(&fullb[s]), (uint32_t)((g / OH_STAGES) & 1), abort_flag, lane)) {
         ok = false;
         break;
       }
-      const int64_t q0 = (int64_t)(kb0 + g) * 64 + 8 * kq;
-      uint32_t hi[4][4], lo[4][4];                         // [row][pair of samples]
+      fence_after();
+      const float4* us = reinterpret_cast<const float4*>(smem + s * OH_STAGE_BYTES + OH_B_BYTES);
+      uint32_t hi[16], lo[16];
 #pragma unroll
-      for (int kp = 0; kp < 4; ++kp) {
-        float a[2][4];                                     // [sample][row]
+      for (int k = 0; k < 4; ++k) {
+        float ar[4], ai[4];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int kk = 2 * kp + e;
-          const bool valid = q0 + kk < n;
-          const float wr = valid ? uq[kk].x - mr : 0.f, wi = valid ? uq[kk].y - mi : 0.f;
-          const float4 t = tq[kk];
-          float a0r = 0.f, a0i = 0.f, a1r = 0.f, a1i = 0.f;
-          if (j0 < M) {                                    // conj(t) w
-            a0r = fmaf(t.x, wr, t.y * wi);
-            a0i = fmaf(t.x, wi, -t.y * wr);
-          } else if (j0 == M) {
-            a0r = wr;
-            a0i = wi;
+        for (int i2 = 0; i2 < 2; ++i2) {
+          const float4 uq = us[8 * k + 2 * cq + i2];       // samples 16k + 4cq + 2 i2, + 1
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int i = 2 * i2 + e;
+            const float wr = (e ? uq.z : uq.x) - mr, wi = (e ? uq.w : uq.y) - mi;
+            const float2 t = tq[4 * k + i];
+            ar[i] = fmaf(t.x, wr, t.y * wi);                 // conj(t) w
+            ai[i] = fmaf(t.x, wi, -t.y * wr);
+            ybr += ar[i];
+            ybi += ai[i];
           }
-          if (j1 < M) {
-            a1r = fmaf(t.z, wr, t.w * wi);
-            a1i = fmaf(t.z, wi, -t.w * wr);
-          } else if (j1 == M) {
-            a1r = wr;
-            a1i = wi;
-          }
-          y0r += (j0 < M) ? a0r : 0.f;
-          y0i += (j0 < M) ? a0i : 0.f;
-          y1r += (j1 < M) ? a1r : 0.f;
-          y1i += (j1 < M) ? a1i : 0.f;
-          a[e][0] = a0r;
-          a[e][1] = a0i;
-          a[e][2] = a1r;
-          a[e][3] = a1i;
         }
-#pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-          const float x0 = a[0][rr], x1 = a[1][rr];
-          const float h0 = __bfloat162float(__float2bfloat16_rn(x0));
-          const float h1 = __bfloat162float(__float2bfloat16_rn(x1));
-          hi[rr][kp] = pack_bf16(h0, h1);
-          lo[rr][kp] = pack_bf16(x0 - h0, x1 - h1);
-        }
+        split_pair(ar[0], ar[1], hi[4 * k], lo[4 * k]);
+        split_pair(ar[2], ar[3], hi[4 * k + 1], lo[4 * k + 1]);
+        split_pair(ai[0], ai[1], hi[4 * k + 2], lo[4 * k + 2]);
+        split_pair(ai[2], ai[3], hi[4 * k + 3], lo[4 * k + 3]);
       }
-      uint8_t* st = smem + s * OH_STAGE_BYTES;
-#pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-        const uint32_t off = sw128_offset(4 * jp + rr, kq);
-        *reinterpret_cast<uint4*>(st + off) = make_uint4(hi[rr][0], hi[rr][1], hi[rr][2], hi[rr][3]);
-        *reinterpret_cast<uint4*>(st + TILE + off) =
-            make_uint4(lo[rr][0], lo[rr][1], lo[rr][2], lo[rr][3]);
-      }
-      fence_proxy_async_smem();
+      const uint32_t col = (uint32_t)(256 + 64 * s);
+      tmem_st16x256b_x4(tmem + st_base + col, hi);
+      tmem_st16x256b_x4(tmem + st_base + col + 32u, lo);
+      tmem_wait_st();
+      fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&fulla[s]));
     }
-    // y_b: sum over the eight chunk lanes of each unit pair (lane bits 0-2), fixed order
+    // y_b: the four sample groups of each unit (lane bits 0-1), one FP32 partial per chunk
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-      y0r += __shfl_xor_sync(0xffffffffu, y0r, o);
-      y0i += __shfl_xor_sync(0xffffffffu, y0i, o);
-      y1r += __shfl_xor_sync(0xffffffffu, y1r, o);
-      y1i += __shfl_xor_sync(0xffffffffu, y1i, o);
+    for (int o = 1; o < 4; o <<= 1) {
+      ybr += __shfl_xor_sync(0xffffffffu, ybr, o);
+      ybi += __shfl_xor_sync(0xffffffffu, ybi, o);
     }
-    if (ok && kq == 0) {
-      if (j0 < M) ybpart[(int64_t)kc * M + j0] = make_float2(y0r, y0i);
-      if (j1 < M) ybpart[(int64_t)kc * M + j1] = make_float2(y1r, y1i);
-    }
-    // the accumulator: quadrant warp % 4, column half (warp - 2) / 4
+    if (ok && cq == 0 && jv) ybpart[(int64_t)kc * M + j] = make_float2(ybr, ybi);
+    // the accumulator: quadrant qd, column half hsel; D lane L holds row (j(L), c(L))
     if (ok && nk > 0 && warp_wait(smem_u32(accf), 0u, abort_flag, lane)) {
       fence_after();
-      const int qd = warp & 3, half = ew >> 2;
-      const int r = qd * 32 + lane;
-      float* orow = out + ((int64_t)kc * mtiles * 128 + (int64_t)mt * 128 + r) * ncols;
-      for (int c0 = half * (ncols / 2); c0 < (half + 1) * (ncols / 2); c0 += 32) {
+      const int L = 32 * qd + lane;
+      const int arow = 2 * (8 * (L >> 4) + (L & 7)) + ((L >> 3) & 1);
+      float* orow = out + ((int64_t)kc * mtiles * 128 + (int64_t)mt * 128 + arow) * ncols;
+      for (int c0 = hsel * (ncols / 2); c0 < (hsel + 1) * (ncols / 2); c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)c0, v);
 #pragma unroll
         for (int k = 0; k < 32; k += 4)
           *reinterpret_cast<float4*>(orow + c0 + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
@@ -574,7 +607,7 @@ k_cg_ohu(const __grid_constant__ CUtensorMap map_b, int nbt, int nkb, int nkpc, 
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(tmem_cols) : "memory");
+                 "r"(OH_TMEM_COLS) : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag) flag_error(status, DEV_ERR_TIMEOUT);
 }
@@ -605,8 +638,12 @@ cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
                             const float2* vb, const double* c, int M, int64_t n, float2* u,
                             double2* upart, int* nup, unsigned* status, cudaStream_t st) {
   if (!sh.ok) return cudaErrorNotSupported;
-  CUtensorMap ms, mvh, mvl;
+  CUtensorMap ms, mvh, mvl, mt;
   cudaError_t e;
+  // L2 prefetch boxes of t (8-byte elements): 64 hidden units x 256 samples; the rows of an
+  // odd M are not 16-byte aligned, so those shapes go without
+  const int pf = (M % 2 == 0) && make_map_c64(&mt, T, n, M, 64, 256) == cudaSuccess;
+  if (!pf) mt = CUtensorMap{};
   if ((e = make_map(&ms, Sb, sh.s_rows, sh.kN)) != cudaSuccess) return e;
   if ((e = make_map(&mvh, Vhi, sh.v_rows, sh.kN)) != cudaSuccess) return e;
   if ((e = make_map(&mvl, Vlo, sh.v_rows, sh.kN)) != cudaSuccess) return e;
@@ -619,7 +656,7 @@ cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
   }
   const int64_t items = sh.s_rows / 256;
   const unsigned grid = persistent_grid(items);
-  k_cg_ov<<<grid, cgtc::THREADS, cgtc::OV_SMEM, st>>>(ms, mvh, mvl, (int)(sh.kN / 64),
+  k_cg_ov<<<grid, cgtc::THREADS, cgtc::OV_SMEM, st>>>(ms, mvh, mvl, mt, pf, (int)(sh.kN / 64),
                                                       (int)(sh.v_rows / 128), items, T, vb, c, M,
                                                       n, u, upart, status);
   *nup = (int)grid;
@@ -630,9 +667,12 @@ cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const
                              const float2* u, const double2* upart, int nup, int M, int64_t n,
                              float* out, float2* ybpart, unsigned* status, cudaStream_t st) {
   if (!sh.ok) return cudaErrorNotSupported;
-  CUtensorMap mb;
+  CUtensorMap mb, mt;
   cudaError_t e;
   if ((e = make_map(&mb, Bs, sh.b_rows, sh.ldK)) != cudaSuccess) return e;
+  // L2 prefetch boxes of t: 64 hidden units x 64 samples (none for an odd M)
+  const int pf = (M % 2 == 0) && make_map_c64(&mt, T, n, M, 64, 64) == cudaSuccess;
+  if (!pf) mt = CUtensorMap{};
   static bool attr = false;
   if (!attr) {
     if ((e = cudaFuncSetAttribute(k_cg_ohu, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -641,7 +681,7 @@ cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const
     attr = true;
   }
   const unsigned grid = (unsigned)(sh.mtiles * sh.kchunks);
-  k_cg_ohu<<<grid, cgtc::THREADS, cgtc::OH_SMEM, st>>>(mb, sh.nbt, (int)(sh.ldK / 64), sh.nkpc,
+  k_cg_ohu<<<grid, cgtc::THREADS, cgtc::OH_SMEM, st>>>(mb, mt, pf, sh.nbt, (int)(sh.ldK / 64), sh.nkpc,
                                                        sh.mtiles, T, u, upart, nup, M, n, out,
                                                        ybpart, status);
   return cudaGetLastError();

@@ -215,7 +215,7 @@ struct CgWork {
   double* Minv;                       // [P] inverse diagonal of S~ (preconditioner)
   double* t2;                         // [M]
   float2 *va, *vb, *V;                // FP32 copies of the CG direction
-  float2* u;                          // [n]
+  float2* u;                          // [n padded to 256] (the OhU kernel copies 64-sample blocks)
   float2* upart;                      // [ceil(M/64)][n]
   double* ustats;                     // [8]
   double* mpart;                      // moments scratch
@@ -233,6 +233,9 @@ int64_t cg_partial_floats2(int64_t n, int M);
 // diag(S) and the conjugated means; T and meanO must describe the sample set
 cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cudaStream_t st,
                        int64_t* launches);
+// y = S~ v once (after cg_prepare on the same problem)
+cudaError_t cg_apply(const CgProblem& pb, CgWork& w, const double2* v, double2* y,
+                     cudaStream_t st, int64_t* launches);
 // CG on (1/n) Obar^H Obar + D from x0 = 0 until ||r|| <= tol ||F|| or maxit (synchronises
 // once per iteration to read the residual)
 cudaError_t cg_solve(const CgProblem& pb, const double2* F, double2* x, double tol, int maxit,

@@ -61,7 +61,7 @@ class vmc_sr_stats(ctypes.Structure):
 EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
             "vmc_set_chains", "vmc_get_chains", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
             "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
-            "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve",
+            "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve", "vmc_sr_apply",
             "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
             "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned", "vmc_sample_all",
             "vmc_autotuned_warps_per_block", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout"]
@@ -100,6 +100,7 @@ def load(path: str = LIB_PATH):
         "vmc_num_params": (i64, [P, i32]),
         "vmc_force_noalloc": (i32, [P, P, P, i64, i32, i32, P, P, P]),
         "vmc_cg_solve": (i32, [P, i32, P, i64, P, P, ctypes.POINTER(i32), ctypes.POINTER(f64)]),
+        "vmc_sr_apply": (i32, [P, i32, P, i64, P, P]),
         "vmc_made_set_params": (i32, [P, i32, P]),
         "vmc_made_get_params": (i32, [P, i32, P]),
         "vmc_made_logq": (i32, [P, i32, P, i64, P]),
@@ -236,6 +237,11 @@ def vmc_cg_solve(ctx, lattice, spins, F, x):
     _check(ctx, load().vmc_cg_solve(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(F), _ptr(x),
                                     ctypes.byref(it), ctypes.byref(rr)))
     return it.value, rr.value
+
+
+def vmc_sr_apply(ctx, lattice, spins, v, y):
+    """y = S~ v (the CG operator) for the sample set spins (dev int8 [n][N])."""
+    _check(ctx, load().vmc_sr_apply(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(v), _ptr(y)))
 
 
 def vmc_sr_step(ctx, lattice, dt) -> vmc_sr_stats:

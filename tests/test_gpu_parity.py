@@ -406,6 +406,62 @@ def test_cg_solve_matches_oracle(shape, mode, precision):
     assert np.linalg.norm(xh - xo) <= np.linalg.cond(St) * bound * np.linalg.norm(xo)
 
 
+# (model, Lx, Ly, alpha, n): shapes that exercise every tiling path of the tensor-core
+# operator: more 256-sample items than SMs with many K chunks (4x4), N > 128 (two 128-row
+# spin tiles, three 64-wide K blocks, three column / row tiles of 128), a ragged sample count
+# with three column tiles (8x8), an odd M (unpaired hidden units).
+APPLY_SHAPES = [(T, 4, 4, 2, 40000), (T, 130, 1, 1, 1024), (H, 8, 8, 2, 3000), (T, 9, 1, 1, 777)]
+
+
+@pytest.mark.parametrize("precision", [vmc.PREC_FP32, vmc.PREC_BF16SPLIT], ids=["simt", "tc"])
+@pytest.mark.parametrize("shape", APPLY_SHAPES, ids=["items", "n130", "heis8x8", "oddM"])
+def test_sr_apply_matches_oracle(shape, precision):
+    """One application y = S~ v of the CG operator against the oracle's, entry by entry, on
+    samples away from the nodes of psi (|cosh theta_j| >= 0.1).  Bound, to first order:
+      the products see each O_qk and v_l with relative error e (BF16 split: 4 * 2^-16;
+      FP32: 2^-24) plus FP32 accumulation over at most K terms -> rel * b_k with
+      b_k = (1/n) sum_q |O_qk| (sum_l |O_ql| |v_l| + |<O>.v|);
+      t = tanh theta is formed in FP32 from an FP32 theta (N + 1 terms), whose rounding
+      enters t amplified by 1/|cosh theta|^2 -> dO, propagated through both products."""
+    model, Lx, Ly, alpha, n0 = shape
+    N, M = Lx * Ly, alpha * Lx * Ly
+    P = N + M + N * M
+    nu = 1e-3
+    p = inputs.rbm_params(N, M, 0.1, seed=61, marshall=(Lx, Ly) if model == H else None)
+    s = inputs.initial_spins(model, n0, N, seed=62)
+    s = s[well_conditioned(p, s, N, M, cut=0.1)]
+    n = len(s)
+    assert n >= 0.5 * n0
+    rng = np.random.default_rng(63)
+    v = rng.normal(size=P) + 1j * rng.normal(size=P)
+    with context(lattice(model, Lx, Ly, 1.0, 2.0, alpha), n_chains=n0, solver=vmc.SOLVER_CG,
+                 shift=nu, precision=precision) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vd = torch.from_numpy(np.stack([v.real, v.imag], axis=1).copy()).cuda()
+        yd = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        vmc.vmc_sr_apply(ctx, 0, to_dev_spins(s), vd, yd)
+        y = cplx(yd)
+    O = oracle.ok(N, M, p, s)
+    ref = oracle.sr_apply(O, v, nu, 0)
+    aO = np.abs(O)
+    inner = aO @ np.abs(v) + abs(O.mean(axis=0) @ v)
+    rel = (4 * 2.0 ** -16 if precision == vmc.PREC_BF16SPLIT else 2.0 ** -24) \
+        + (max(N, M) + 4096) * 2.0 ** -24
+    bound = rel * (aO.T @ inner) / n
+    # FP32 theta and tanh: |dt_qj| <= (N + 1) 2^-24 (|b_j| + sum_i |W_ji|) / |cosh theta|^2
+    #                                 + 4 * 2^-24 |t_qj|
+    b, W = p[N:N + M], p[N + M:].reshape(M, N)
+    theta = b[None, :] + s.astype(np.float64) @ W.T
+    dth = (N + 1) * 2.0 ** -24 * (np.abs(b) + np.abs(W).sum(axis=1))
+    dt = dth[None, :] / np.abs(np.cosh(theta)) ** 2 + 4 * 2.0 ** -24 * np.abs(np.tanh(theta))
+    dO = np.concatenate([np.zeros((n, N)), dt, np.repeat(dt, N, axis=1)], axis=1)
+    du = dO @ np.abs(v)
+    bound += (dO.T @ inner + aO.T @ du) / n
+    err = np.abs(y - ref)
+    assert np.all(err <= bound), (np.max(err / bound), np.argmax(err / bound))
+    assert np.linalg.norm(y - ref) <= 1e-3 * np.linalg.norm(ref)
+
+
 @pytest.mark.parametrize("precision", [vmc.PREC_FP32, vmc.PREC_BF16SPLIT], ids=["simt", "tc"])
 def test_sr_step_cg_heisenberg_16x16(precision):
     """The 16x16 Heisenberg shape (N = 256, M = 512, P = 131 840) through the CG step,

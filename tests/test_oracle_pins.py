@@ -321,6 +321,22 @@ def test_cholesky_rejects_indefinite():
 
 
 @pytest.mark.parametrize("mode", [0, 1])
+def test_sr_apply_matches_dense_shifted_s(mode):
+    """The matrix-free operator equals the dense shifted S (formed by the separately pinned
+    sr_matrices) times v, and v^H S~ v is real and positive."""
+    rng = np.random.default_rng(17)
+    Ns, P = 60, 25
+    O = rng.normal(size=(Ns, P)) + 1j * rng.normal(size=(Ns, P)) + 0.7   # non-zero mean
+    v = rng.normal(size=P) + 1j * rng.normal(size=P)
+    S, _, _ = oracle.sr_matrices(O, np.zeros(Ns))
+    y = oracle.sr_apply(O, v, 1e-2, mode)
+    yd = oracle.shift(S, 1e-2, mode) @ v
+    assert np.linalg.norm(y - yd) <= 1e-12 * np.linalg.norm(yd)
+    q = np.vdot(v, y)
+    assert q.real > 0 and abs(q.imag) <= 1e-12 * abs(q)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
 def test_cg_matches_dense_solve(mode):
     rng = np.random.default_rng(5)
     Ns, P = 50, 30
