@@ -341,7 +341,10 @@ __global__ void k_build_bs(const int8_t* __restrict__ spins, int64_t n, int N, i
   }
 }
 
-// rows 2j / 2j+1: Re / Im of V_j (j < M); rows 2M / 2M+1: Re / Im of v_a
+// Re / Im of V_j (j < M) and of v_a (the pseudo-unit j = M), rows in the order the
+// product's epilogue reads them: within each block of 32 rows (16 units), row
+// 8k + 2 cq + c holds component c of unit 4 cq + k, so that the 16x256b TMEM load gives a
+// thread four consecutive units.
 __global__ void k_build_vplanes(const float2* __restrict__ V, const float2* __restrict__ va,
                                 int N, int M, int64_t rows, int64_t K,
                                 __nv_bfloat16* __restrict__ Vhi, __nv_bfloat16* __restrict__ Vlo) {
@@ -350,7 +353,8 @@ __global__ void k_build_vplanes(const float2* __restrict__ V, const float2* __re
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = e / K;
     const int i = (int)(e - r * K);
-    const int j = (int)(r >> 1);
+    const int rho = (int)(r & 31);
+    const int j = (int)(r >> 5) * 16 + 4 * ((rho & 7) >> 1) + (rho >> 3);
     float v = 0.f;
     if (j <= M && i < N) {
       const float2 z = (j < M) ? V[(int64_t)j * N + i] : va[i];

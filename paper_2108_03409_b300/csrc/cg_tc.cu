@@ -228,16 +228,20 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
       }
     }
   } else {
-    // ---------------- epilogue: u_q for one sample per thread ----------------
+    // ---------------- epilogue: u_q ----------------
+    // Warp e owns TMEM lane quadrant e % 4 of sample sub-tile (e - 2) / 4 and reads it with
+    // the 16x256b shape, two 16-lane halves hh per quarter (16 units = 32 columns): thread t
+    // gets samples 16 hh + t/4 and 16 hh + t/4 + 8 of the quadrant and units 4 (t%4) .. + 3
+    // of the quarter (the V rows are ordered for this), so its t and v_b come in 16-byte
+    // loads; the four threads of a sample sum their parts at the end of the item.
     const int ew = warp - 2;
     const int qd = warp & 3, sub = ew >> 2;
-    const int r = qd * 32 + lane;
+    const int cq = lane & 3, sl = lane >> 2;
     const bool vec = (M & 1) == 0;
     const float cre = (float)c[0], cim = (float)c[1];
-    // The thread's work is a sequence of quarters: quarter (item w, column tile ct, qtr)
-    // covers hidden units 64 ct + 16 qtr .. + 15 of the thread's sample in item w.  A
-    // quarter's t is loaded two quarters ahead into one of three rotating buffers; two
-    // cursors (the quarter in use, the quarter being loaded) advance without divisions.
+    // quarter (item w, column tile ct, qtr): units jb = 64 ct + 16 qtr ..; a quarter's t
+    // (4 samples x 4 units per thread) is loaded two quarters ahead into one of three
+    // rotating buffers; two cursors advance without divisions
     struct Cursor {
       int64_t w;
       int ct, qtr;
@@ -251,26 +255,33 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
         }
       }
     };
+    // dst[2 (2 hh + e) + p]: units j0 + 2p, j0 + 2p + 1 of sample 16 hh + sl + 8 e
     auto load_t = [&](const Cursor& k, float4 (&dst)[8]) {
       if (k.w >= items) return;
-      const int64_t m = k.w * 256 + sub * 128 + r;
-      const int j0 = k.ct * 64 + k.qtr * 16;
-      if (m < n && vec && j0 + 16 <= M) {
-        const float4* src = reinterpret_cast<const float4*>(T + m * M + j0);
+      const int j0 = k.ct * 64 + k.qtr * 16 + 4 * cq;
+      const int64_t mb = k.w * 256 + sub * 128 + qd * 32 + sl;
 #pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) dst[k2] = src[k2];
-      } else {
+      for (int se = 0; se < 4; ++se) {
+        const int64_t m = mb + 16 * (se >> 1) + 8 * (se & 1);
+        if (m < n && vec && j0 + 4 <= M) {
+          const float4* src = reinterpret_cast<const float4*>(T + m * M + j0);
+          dst[2 * se] = src[0];
+          dst[2 * se + 1] = src[1];
+        } else {
 #pragma unroll
-        for (int k2 = 0; k2 < 8; ++k2) {
-          const int j = j0 + 2 * k2;
-          const float2 x = (m < n && j < M) ? T[m * M + j] : make_float2(0.f, 0.f);
-          const float2 y = (m < n && j + 1 < M) ? T[m * M + j + 1] : make_float2(0.f, 0.f);
-          dst[k2] = make_float4(x.x, x.y, y.x, y.y);
+          for (int p = 0; p < 2; ++p) {
+            const int j = j0 + 2 * p;
+            const float2 x = (m < n && j < M) ? T[m * M + j] : make_float2(0.f, 0.f);
+            const float2 y = (m < n && j + 1 < M) ? T[m * M + j + 1] : make_float2(0.f, 0.f);
+            dst[2 * se + p] = make_float4(x.x, x.y, y.x, y.y);
+          }
         }
       }
     };
     double usr = 0.0, usi = 0.0;
-    float ar = 0.f, ai = 0.f;
+    float acc[4][2];                                // [sample 2 hh + e][re, im]
+#pragma unroll
+    for (int se = 0; se < 4; ++se) acc[se][0] = acc[se][1] = 0.f;
     bool ok = true;
     int64_t cc = 0;                                 // column tiles completed
     Cursor use{(int64_t)blockIdx.x, 0, 0}, ahead = use;
@@ -286,36 +297,41 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
         }
         fence_after();
       }
-      const int jb = use.ct * 64 + use.qtr * 16;
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(b * 256 + sub * 128 + use.qtr * 32), v);
-      if (jb + 16 <= M) {
-        const float4* vb4 = reinterpret_cast<const float4*>(vb + jb);
-#pragma unroll
-        for (int h = 0; h < 8; ++h) {              // hidden units jb + 2h, jb + 2h + 1
-          const float4 bb = vb4[h], tt = cur[h];
-          float zr = v[4 * h] + bb.x, zi = v[4 * h + 1] + bb.y;
-          ar = fmaf(tt.x, zr, fmaf(-tt.y, zi, ar));
-          ai = fmaf(tt.x, zi, fmaf(tt.y, zr, ai));
-          zr = v[4 * h + 2] + bb.z;
-          zi = v[4 * h + 3] + bb.w;
-          ar = fmaf(tt.z, zr, fmaf(-tt.w, zi, ar));
-          ai = fmaf(tt.z, zi, fmaf(tt.w, zr, ai));
-        }
+      const int j0 = use.ct * 64 + use.qtr * 16 + 4 * cq;
+      float2 bv[4];
+      if (j0 + 4 <= M) {
+        const float4* vb4 = reinterpret_cast<const float4*>(vb + j0);
+        const float4 x = vb4[0], y = vb4[1];
+        bv[0] = make_float2(x.x, x.y);
+        bv[1] = make_float2(x.z, x.w);
+        bv[2] = make_float2(y.x, y.y);
+        bv[3] = make_float2(y.z, y.w);
       } else {
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) {
-          const int j = jb + jj;
-          const float4 t4 = cur[jj >> 1];
-          const float tr = (jj & 1) ? t4.z : t4.x, ti = (jj & 1) ? t4.w : t4.y;
-          if (j < M) {
-            const float2 bj = vb[j];
-            const float zr = v[2 * jj] + bj.x, zi = v[2 * jj + 1] + bj.y;
-            ar = fmaf(tr, zr, fmaf(-ti, zi, ar));
-            ai = fmaf(tr, zi, fmaf(ti, zr, ai));
-          } else if (j == M) {                     // rows 2M / 2M+1: sum_i s_qi v_a,i as is
-            ar += v[2 * jj];
-            ai += v[2 * jj + 1];
+        for (int k = 0; k < 4; ++k) bv[k] = (j0 + k < M) ? vb[j0 + k] : make_float2(0.f, 0.f);
+      }
+      const bool interior = j0 + 4 <= M;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float v[16];
+        tmem_ld16x256b_x4(tmem + ((uint32_t)(32 * qd + 16 * hh) << 16) +
+                              (uint32_t)(b * 256 + sub * 128 + use.qtr * 32), v);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int se = 2 * hh + e;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float4 t4 = cur[2 * se + (k >> 1)];
+            const float tr = (k & 1) ? t4.z : t4.x, ti = (k & 1) ? t4.w : t4.y;
+            const float zr0 = v[4 * k + 2 * e], zi0 = v[4 * k + 2 * e + 1];
+            if (interior || j0 + k < M) {
+              const float zr = zr0 + bv[k].x, zi = zi0 + bv[k].y;
+              acc[se][0] = fmaf(tr, zr, fmaf(-ti, zi, acc[se][0]));
+              acc[se][1] = fmaf(tr, zi, fmaf(ti, zr, acc[se][1]));
+            } else if (j0 + k == M) {             // v_a rows: sum_i s_qi v_a,i as is
+              acc[se][0] += zr0;
+              acc[se][1] += zi0;
+            }
           }
         }
       }
@@ -325,15 +341,22 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
         if (lane == 0) mbar_arrive(smem_u32(&acce[b]));
         ++cc;
         if (use.ct == nct - 1) {                   // the item's last column tile: u is complete
-          const int64_t m = use.w * 256 + sub * 128 + r;
-          if (m < n) {
-            const float ur = ar - cre, ui = ai - cim;
-            u[m] = make_float2(ur, ui);
-            usr += (double)ur;
-            usi += (double)ui;
+#pragma unroll
+          for (int se = 0; se < 4; ++se) {
+            float xr = acc[se][0], xi = acc[se][1];
+            xr += __shfl_xor_sync(0xffffffffu, xr, 1);
+            xi += __shfl_xor_sync(0xffffffffu, xi, 1);
+            xr += __shfl_xor_sync(0xffffffffu, xr, 2);
+            xi += __shfl_xor_sync(0xffffffffu, xi, 2);
+            const int64_t m = use.w * 256 + sub * 128 + qd * 32 + 16 * (se >> 1) + 8 * (se & 1) + sl;
+            if (cq == 0 && m < n) {
+              const float ur = xr - cre, ui = xi - cim;
+              u[m] = make_float2(ur, ui);
+              usr += (double)ur;
+              usi += (double)ui;
+            }
+            acc[se][0] = acc[se][1] = 0.f;
           }
-          ar = 0.f;
-          ai = 0.f;
         }
       }
       advance(use);

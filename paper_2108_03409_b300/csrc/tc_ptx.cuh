@@ -156,6 +156,21 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
       : "memory");
 }
 
+// Load counterpart of tmem_st16x256b_x4 (same register-to-(lane, column) layout).
+__device__ __forceinline__ void tmem_ld16x256b_x4(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
+}
+
 // 16 lanes x 256 bits, repeated over 4 x 8 columns (warp-collective, 16x256b shape):
 // thread t holds, for repetition k, v[4k] at (lane t/4, column 8k + 2(t%4)), v[4k+1] at
 // (lane t/4, column 8k + 2(t%4) + 1), v[4k+2] and v[4k+3] at lane t/4 + 8, same columns.
