@@ -351,13 +351,13 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
     const int64_t P = ctx->Pmax;
     if ((e = dalloc(ctx, &w.r, P)) || (e = dalloc(ctx, &w.p, P)) || (e = dalloc(ctx, &w.q, P)) ||
         (e = dalloc(ctx, &w.y, P)) || (e = dalloc(ctx, &w.z, P)) ||
-        (e = dalloc(ctx, &w.meanO_c, P)) || (e = dalloc(ctx, &w.D, P)) ||
+        (e = dalloc(ctx, &w.D, P)) ||
         (e = dalloc(ctx, &w.Minv, P)) || (e = dalloc(ctx, &w.t2, ctx->Mmax)) ||
-        (e = dalloc(ctx, &w.va, ctx->Nmax)) || (e = dalloc(ctx, &w.vb, ctx->Mmax)) ||
+        (e = dalloc(ctx, &w.va, ctx->Nmax)) || (e = dalloc(ctx, &w.vb, ctx->Mmax + 128)) ||
         (e = dalloc(ctx, &w.V, (size_t)ctx->Nmax * ctx->Mmax)) || (e = dalloc(ctx, &w.u, (Ns + 255) / 256 * 256)) ||
         (e = dalloc(ctx, &w.upart, (size_t)cg_partial_floats2(Ns, ctx->Mmax))) ||
-        (e = dalloc(ctx, &w.ustats, 8)) || (e = dalloc(ctx, &w.dpart, 256)) ||
-        (e = dalloc(ctx, &w.c2, 8)) || (e = dalloc(ctx, &w.sc, 8)))
+        (e = dalloc(ctx, &w.ustats, 8)) || (e = dalloc(ctx, &w.vpart, CG_VPART_DOUBLES)) ||
+        (e = dalloc(ctx, &w.sc, 8)) || (e = dalloc(ctx, &w.flag, 4)))
       return oom(e);
     w.mpart = ctx->partial;
     // u stays finite beyond the sample count (the OhU kernel reads whole 64-sample blocks)
@@ -622,7 +622,7 @@ vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
   CK(launch_moments(spins, ctx->s_T, nullptr, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
                     nullptr, ctx->st), "moments");
   ctx->launches += 3;
-  CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO, nullptr,
+  CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO,
                ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, n).ok, ctx->status};
   CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
   int it = 0;
@@ -648,7 +648,7 @@ vmc_status vmc_sr_apply(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
   CK(launch_moments(spins, ctx->s_T, nullptr, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
                     nullptr, ctx->st), "moments");
   ctx->launches += 3;
-  CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO, nullptr,
+  CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO,
                ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, n).ok, ctx->status};
   CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
   CK(cg_apply(pb, ctx->cg, reinterpret_cast<const double2*>(v), reinterpret_cast<double2*>(y),
@@ -724,7 +724,7 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
     CK(launch_moments(ctx->s_spins, ctx->s_T, ctx->s_E, ctx->estats, Ns, L.N, L.M, ctx->partial,
                       ctx->meanO, ctx->F, ctx->st), "moments");
     ctx->launches += 2;
-    CgProblem pb{ctx->s_spins, ctx->s_T, Ns, L.N, L.M, ctx->meanO, nullptr,
+    CgProblem pb{ctx->s_spins, ctx->s_T, Ns, L.N, L.M, ctx->meanO,
                  ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, Ns).ok, ctx->status};
     CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
     cudaEventRecord(ctx->ev[6], ctx->st);

@@ -122,74 +122,6 @@ __global__ void k_vs_finish(const float2* __restrict__ part, int mtiles, const i
   }
 }
 
-// FP64 helpers -------------------------------------------------------------------------
-constexpr int RED_BLOCKS = 256;
-
-// partial[b] = sum over the block's slice of conj(a_k) b_k (complex), two-stage reduction
-__global__ void __launch_bounds__(256) k_cdot_partial(const double2* __restrict__ a,
-                                                      const double2* __restrict__ b, int64_t P,
-                                                      double2* __restrict__ partial) {
-  __shared__ double red[2][8];
-  double sr = 0, si = 0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-    const double2 x = a[k], y = b[k];
-    sr += x.x * y.x + x.y * y.y;
-    si += x.x * y.y - x.y * y.x;
-  }
-  sr = warp_sum_d(sr);
-  si = warp_sum_d(si);
-  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sr; red[1][threadIdx.x >> 5] = si; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tr = 0, ti = 0;
-    for (int w = 0; w < 8; ++w) { tr += red[0][w]; ti += red[1][w]; }
-    partial[blockIdx.x] = make_double2(tr, ti);
-  }
-}
-
-// one warp: lane l adds partials l, l + 32, ...; then a fixed-order warp reduction
-__global__ void k_cdot_final(const double2* __restrict__ partial, int nb, double2* __restrict__ out) {
-  double tr = 0, ti = 0;
-  for (int k = threadIdx.x; k < nb; k += 32) { tr += partial[k].x; ti += partial[k].y; }
-  tr = warp_sum_d(tr);
-  ti = warp_sum_d(ti);
-  if (threadIdx.x == 0) *out = make_double2(tr, ti);
-}
-
-// mean of a complex FP32 vector in FP64: block partials, then one warp (fixed order)
-__global__ void __launch_bounds__(256) k_mean_partial(const float2* __restrict__ u, int64_t n,
-                                                      double2* __restrict__ partial) {
-  __shared__ double red[2][8];
-  double sr = 0, si = 0;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = u[k];
-    sr += v.x;
-    si += v.y;
-  }
-  sr = warp_sum_d(sr);
-  si = warp_sum_d(si);
-  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sr; red[1][threadIdx.x >> 5] = si; }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tr = 0, ti = 0;
-    for (int w = 0; w < 8; ++w) { tr += red[0][w]; ti += red[1][w]; }
-    partial[blockIdx.x] = make_double2(tr, ti);
-  }
-}
-
-__global__ void k_mean_final(const double2* __restrict__ partial, int nb, int64_t n,
-                             double* __restrict__ out) {
-  double tr = 0, ti = 0;
-  for (int k = threadIdx.x; k < nb; k += 32) { tr += partial[k].x; ti += partial[k].y; }
-  tr = warp_sum_d(tr);
-  ti = warp_sum_d(ti);
-  if (threadIdx.x == 0) {
-    out[0] = tr / (double)n;
-    out[1] = ti / (double)n;
-  }
-}
-
 // diag(S) in closed form (s_i^2 = 1); t2[j] = <|t_j|^2>.  D = shift part, Minv = 1/diag(S~).
 __global__ void k_diag_s(const double2* __restrict__ meanO, const double* __restrict__ t2, int N,
                          int M, double nu, int mode, double* __restrict__ D,
@@ -205,13 +137,6 @@ __global__ void k_diag_s(const double2* __restrict__ meanO, const double* __rest
     const double dd = v + D[k];
     Minv[k] = (dd > 0.0) ? 1.0 / dd : 1.0;
   }
-}
-
-// z = Minv r
-__global__ void k_prec(const double* __restrict__ Minv, const double2* __restrict__ r, int64_t P,
-                       double2* __restrict__ z) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
-    z[k] = make_double2(Minv[k] * r[k].x, Minv[k] * r[k].y);
 }
 
 // t2[j] = (1/n) sum_q |t_qj|^2 in FP64
@@ -233,58 +158,6 @@ __global__ void k_t2(const float2* __restrict__ T, int64_t n, int M, double* __r
   }
 }
 
-// split p into FP32 pieces for the product: va [N], vb [M], V [M][N] (row-major as in p)
-__global__ void k_split_v(const double2* __restrict__ p, int N, int M, float2* __restrict__ va,
-                          float2* __restrict__ vb, float2* __restrict__ V) {
-  const int64_t P = (int64_t)N + M + (int64_t)N * M;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-    const float2 f = make_float2((float)p[k].x, (float)p[k].y);
-    if (k < N) va[k] = f;
-    else if (k < N + M) vb[k - N] = f;
-    else V[k - N - M] = f;
-  }
-}
-
-// q = y + D p
-__global__ void k_add_diag(const double2* __restrict__ y, const double* __restrict__ D,
-                           const double2* __restrict__ p, int64_t P, double2* __restrict__ q) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
-    q[k] = make_double2(y[k].x + D[k] * p[k].x, y[k].y + D[k] * p[k].y);
-}
-
-// x += alpha p; r -= alpha q
-__global__ void k_cg_xr(double2* __restrict__ x, double2* __restrict__ r, const double2* __restrict__ p,
-                        const double2* __restrict__ q, int64_t P, const double* __restrict__ alpha) {
-  const double al = *alpha;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
-    x[k].x += al * p[k].x;
-    x[k].y += al * p[k].y;
-    r[k].x -= al * q[k].x;
-    r[k].y -= al * q[k].y;
-  }
-}
-
-// p = r + beta p
-__global__ void k_cg_p(double2* __restrict__ p, const double2* __restrict__ r, int64_t P,
-                       const double* __restrict__ beta) {
-  const double be = *beta;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
-    p[k] = make_double2(r[k].x + be * p[k].x, r[k].y + be * p[k].y);
-}
-
-// scalars: sc[0] = r.z, sc[1] = p.q (re), sc[2] = alpha, sc[3] = beta, sc[4] = new r.z,
-// sc[5] = |r|^2
-__global__ void k_cg_alpha(double* sc, const double2* pq) {
-  sc[1] = pq->x;
-  sc[2] = (pq->x != 0.0) ? sc[0] / pq->x : 0.0;
-}
-__global__ void k_cg_beta(double* sc, const double2* rz_new, const double2* rr) {
-  sc[4] = rz_new->x;
-  sc[3] = (sc[0] != 0.0) ? sc[4] / sc[0] : 0.0;
-  sc[0] = sc[4];
-  sc[5] = rr->x;
-}
-
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------
@@ -295,13 +168,6 @@ static int g1d(int64_t n, int cap = 4096) {
 }
 
 int64_t cg_partial_floats2(int64_t n, int M) { return ((M + VS_J - 1) / VS_J) * n; }
-
-static cudaError_t cdot(const double2* a, const double2* b, int64_t P, CgWork& w, double2* out,
-                        cudaStream_t st) {
-  k_cdot_partial<<<RED_BLOCKS, 256, 0, st>>>(a, b, P, w.dpart);
-  k_cdot_final<<<1, 32, 0, st>>>(w.dpart, RED_BLOCKS, out);
-  return cudaGetLastError();
-}
 
 // q = S~ p
 // ---------------------------------------------------------------------------------------
@@ -344,10 +210,13 @@ __global__ void k_build_bs(const int8_t* __restrict__ spins, int64_t n, int N, i
 // Re / Im of V_j (j < M) and of v_a (the pseudo-unit j = M), rows in the order the
 // product's epilogue reads them: within each block of 32 rows (16 units), row
 // 8k + 2 cq + c holds component c of unit 4 cq + k, so that the 16x256b TMEM load gives a
-// thread four consecutive units.
-__global__ void k_build_vplanes(const float2* __restrict__ V, const float2* __restrict__ va,
-                                int N, int M, int64_t rows, int64_t K,
-                                __nv_bfloat16* __restrict__ Vhi, __nv_bfloat16* __restrict__ Vlo) {
+// thread four consecutive units.  Read from the FP64 direction p (rounded to FP32, then
+// split); vb = v_b in FP32 for the epilogue.
+__global__ void k_build_vplanes(const double2* __restrict__ p, int N, int M, int64_t rows,
+                                int64_t K, __nv_bfloat16* __restrict__ Vhi,
+                                __nv_bfloat16* __restrict__ Vlo, float2* __restrict__ vb,
+                                const int* __restrict__ done) {
+  if (*done) return;
   const int64_t total = rows * K;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -357,34 +226,251 @@ __global__ void k_build_vplanes(const float2* __restrict__ V, const float2* __re
     const int j = (int)(r >> 5) * 16 + 4 * ((rho & 7) >> 1) + (rho >> 3);
     float v = 0.f;
     if (j <= M && i < N) {
-      const float2 z = (j < M) ? V[(int64_t)j * N + i] : va[i];
-      v = (r & 1) ? z.y : z.x;
+      const double2 z = (j < M) ? p[N + M + (int64_t)j * N + i] : p[i];
+      v = (float)((rho & 1) ? z.y : z.x);
     }
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     Vhi[e] = h;
     Vlo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    if (e < M) vb[e] = make_float2((float)p[N + e].x, (float)p[N + e].y);
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// CG vector kernels.  Every reduction is a fixed-order FP64 sum: each of CG_VB blocks
+// writes one partial, and whoever needs the total sums the CG_VB partials in a fixed order
+// (lane l takes l, l + 32, ..., then the warp tree).  Partial buffers (doubles):
+//   PQ   Re p^H q                     written by the operator's last kernel
+//   RZ   Re r^H z, two buffers by iteration parity (the update writes one, reads the other)
+//   RR   |r|^2, two buffers by iteration parity
+//   CR/CI  sum_k <O_k> p_k (no conjugation): the centring constant of Obar p
+// Scalars sc: [0] |F|^2, [1] |r|^2 of the latest check, [2..3] c = <O> . p.
+// Flags: [0] done (converged or non-finite), [1] iterations performed.
+// ---------------------------------------------------------------------------------------
+constexpr int CG_VB = 256;             // blocks of the vector kernels
+constexpr int CG_RB = 1024;            // blocks of the chunk reduction (its p.q partials)
+constexpr int OFF_PQ = 0, OFF_RZ = 1024, OFF_RR = 1536, OFF_CR = 2048, OFF_CI = 2304;
+static_assert(OFF_CI + CG_VB <= CG_VPART_DOUBLES, "CG partial buffer");
+
+// sum of NP partials, lane l taking l, l + 32, ... (all loads issued before the adds)
+template <int NP>
+__device__ __forceinline__ double sum_partials(const double* part, int lane) {
+  double v[NP / 32];
+#pragma unroll
+  for (int k = 0; k < NP / 32; ++k) v[k] = part[lane + 32 * k];
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < NP / 32; ++k) s += v[k];
+  return warp_sum_d(s);
+}
+
+// block sum of one value per thread (up to 256 threads) into part[blockIdx.x]
+__device__ __forceinline__ void block_partial(double v, double* part, double* red) {
+  v = warp_sum_d(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+  __syncthreads();
+}
+
+// x = 0, r = F, z = Minv r, p = z; partials of r.z (parity slot 1), |r|^2 (slot 1), <O>.p
+__global__ void __launch_bounds__(256) k_cg_init(const double2* __restrict__ F,
+                                                 const double* __restrict__ Minv,
+                                                 const double2* __restrict__ meanO, int64_t P,
+                                                 double2* __restrict__ x, double2* __restrict__ r,
+                                                 double2* __restrict__ z, double2* __restrict__ p,
+                                                 double* __restrict__ vpart) {
+  __shared__ double red[8];
+  double rz = 0.0, rr = 0.0, cr = 0.0, ci = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 f = F[k];
+    const double2 zk = make_double2(Minv[k] * f.x, Minv[k] * f.y);
+    x[k] = make_double2(0.0, 0.0);
+    r[k] = f;
+    z[k] = zk;
+    p[k] = zk;
+    rz += f.x * zk.x + f.y * zk.y;
+    rr += f.x * f.x + f.y * f.y;
+    const double2 m = meanO[k];
+    cr += m.x * zk.x - m.y * zk.y;
+    ci += m.x * zk.y + m.y * zk.x;
+  }
+  block_partial(rz, vpart + OFF_RZ + CG_VB, red);
+  block_partial(rr, vpart + OFF_RR + CG_VB, red);
+  block_partial(cr, vpart + OFF_CR, red);
+  block_partial(ci, vpart + OFF_CI, red);
+}
+
+// start of iteration `it` (one warp): |r|^2 and c from the partials of the previous
+// update / direction kernels; sets done once |r|^2 <= tol2 |F|^2 (or non-finite), else
+// counts the iteration (if `count`).  Nothing changes once done is set, so sc[1] keeps the
+// residual at which the iteration stopped.
+__global__ void k_cg_check(const double* __restrict__ vpart, int it, double tol2, double* sc,
+                           int* flag, int first, int count) {
+  if (flag[0]) return;
+  const int lane = threadIdx.x;
+  const int prev = (it & 1) ^ 1;
+  const double rr = sum_partials<CG_VB>(vpart + OFF_RR + prev * CG_VB, lane);
+  const double cr = sum_partials<CG_VB>(vpart + OFF_CR, lane);
+  const double ci = sum_partials<CG_VB>(vpart + OFF_CI, lane);
+  if (lane == 0) {
+    if (first) sc[0] = rr;
+    sc[1] = rr;
+    sc[2] = cr;
+    sc[3] = ci;
+    const double f2 = first ? rr : sc[0];
+    if (!(rr > tol2 * f2) || !(rr == rr)) flag[0] = 1;
+    else if (count) flag[1] += 1;
+  }
+}
+
+// alpha = r.z / p.q; x += alpha p; r -= alpha q; z = Minv r; partials of r.z and |r|^2
+__global__ void __launch_bounds__(256) k_cg_update(double2* __restrict__ x, double2* __restrict__ r,
+                                                   double2* __restrict__ z,
+                                                   const double2* __restrict__ p,
+                                                   const double2* __restrict__ q,
+                                                   const double* __restrict__ Minv, int64_t P,
+                                                   double* __restrict__ vpart, int it,
+                                                   const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[8];
+  __shared__ double alpha_s;
+  const int par = it & 1;
+  if (threadIdx.x < 32) {
+    const double rz = sum_partials<CG_VB>(vpart + OFF_RZ + (par ^ 1) * CG_VB, threadIdx.x);
+    const double pq = sum_partials<CG_RB>(vpart + OFF_PQ, threadIdx.x);
+    if (threadIdx.x == 0) alpha_s = (pq != 0.0) ? rz / pq : 0.0;
+  }
+  __syncthreads();
+  const double al = alpha_s;
+  double rz = 0.0, rr = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 pk = p[k], qk = q[k];
+    double2 xk = x[k], rk = r[k];
+    xk.x += al * pk.x;
+    xk.y += al * pk.y;
+    rk.x -= al * qk.x;
+    rk.y -= al * qk.y;
+    x[k] = xk;
+    r[k] = rk;
+    const double2 zk = make_double2(Minv[k] * rk.x, Minv[k] * rk.y);
+    z[k] = zk;
+    rz += rk.x * zk.x + rk.y * zk.y;
+    rr += rk.x * rk.x + rk.y * rk.y;
+  }
+  block_partial(rz, vpart + OFF_RZ + par * CG_VB, red);
+  block_partial(rr, vpart + OFF_RR + par * CG_VB, red);
+}
+
+// beta = r.z (new) / r.z (old); p = z + beta p; partials of <O>.p for the next operator
+__global__ void __launch_bounds__(256) k_cg_dir(double2* __restrict__ p,
+                                                const double2* __restrict__ z,
+                                                const double2* __restrict__ meanO, int64_t P,
+                                                double* __restrict__ vpart, int it,
+                                                const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[8];
+  __shared__ double beta_s;
+  const int par = it & 1;
+  if (threadIdx.x < 32) {
+    const double rz_new = sum_partials<CG_VB>(vpart + OFF_RZ + par * CG_VB, threadIdx.x);
+    const double rz_old = sum_partials<CG_VB>(vpart + OFF_RZ + (par ^ 1) * CG_VB, threadIdx.x);
+    if (threadIdx.x == 0) beta_s = (rz_old != 0.0) ? rz_new / rz_old : 0.0;
+  }
+  __syncthreads();
+  const double be = beta_s;
+  double cr = 0.0, ci = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 zk = z[k], pk = p[k];
+    const double2 pn = make_double2(zk.x + be * pk.x, zk.y + be * pk.y);
+    p[k] = pn;
+    const double2 m = meanO[k];
+    cr += m.x * pn.x - m.y * pn.y;
+    ci += m.x * pn.y + m.y * pn.x;
+  }
+  block_partial(cr, vpart + OFF_CR, red);
+  block_partial(ci, vpart + OFF_CI, red);
+}
+
+// partials of <O>.v for one application of the operator to v
+__global__ void __launch_bounds__(256) k_cg_cpart(const double2* __restrict__ v,
+                                                  const double2* __restrict__ meanO, int64_t P,
+                                                  double* __restrict__ vpart) {
+  __shared__ double red[8];
+  double cr = 0.0, ci = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 m = meanO[k], pk = v[k];
+    cr += m.x * pk.x - m.y * pk.y;
+    ci += m.x * pk.y + m.y * pk.x;
+  }
+  block_partial(cr, vpart + OFF_CR, red);
+  block_partial(ci, vpart + OFF_CI, red);
+}
+
+// SIMT operator: FP32 copies of the direction
+__global__ void k_split_v(const double2* __restrict__ p, int N, int M, float2* __restrict__ va,
+                          float2* __restrict__ vb, float2* __restrict__ V,
+                          const int* __restrict__ done) {
+  if (*done) return;
+  const int64_t P = (int64_t)N + M + (int64_t)N * M;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    const float2 f = make_float2((float)p[k].x, (float)p[k].y);
+    if (k < N) va[k] = f;
+    else if (k < N + M) vb[k - N] = f;
+    else V[k - N - M] = f;
+  }
+}
+
+// q = y + D p, with partials of Re p^H q
+__global__ void __launch_bounds__(256) k_add_diag(const double2* __restrict__ y,
+                                                  const double* __restrict__ D,
+                                                  const double2* __restrict__ p, int64_t P,
+                                                  double2* __restrict__ q,
+                                                  double* __restrict__ vpart,
+                                                  const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[8];
+  double pq = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 pk = p[k];
+    const double2 qk = make_double2(y[k].x + D[k] * pk.x, y[k].y + D[k] * pk.y);
+    q[k] = qk;
+    pq += pk.x * qk.x + pk.y * qk.y;
+  }
+  block_partial(pq, vpart + OFF_PQ, red);
+}
+
 // q_k = y_k + D_k p_k with y_k = (1/n) sum_q conj(Obar_qk) w_q from the K-chunk partials
-// (FP64 sum over chunks): a_i: out rows 2M / 2M+1, column i; b_j: ybpart[.][j]; W_ji: out
-// rows 2j / 2j+1, column i.  Four threads per entry (chunks c = l, l + 4, ...), then a
-// fixed-order shuffle sum.
-__global__ void __launch_bounds__(256) k_cg_reduce_tc(const float* __restrict__ out,
+// (FP64 sum over chunks in order): a_i: out rows 2M / 2M+1, column i; b_j: ybpart[.][j];
+// W_ji: out rows 2j / 2j+1, column i.  Partials of Re p^H q.
+__global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ out,
                                                       const float2* __restrict__ ybpart,
                                                       int kchunks, int64_t a_rows, int ncols,
                                                       int N, int M, int64_t n,
                                                       const double* __restrict__ D,
                                                       const double2* __restrict__ p,
-                                                      double2* __restrict__ q) {
+                                                      double2* __restrict__ q,
+                                                      double* __restrict__ vpart,
+                                                      const int* __restrict__ done) {
+  if (*done) return;
+  __shared__ double red[8];
   const int64_t P = (int64_t)N + M + (int64_t)N * M;
   const double inv = 1.0 / (double)n;
-  const int64_t k = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
-  const int l = threadIdx.x & 3;
-  double re = 0.0, im = 0.0;
-  if (k < P) {
+  double pq = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
     if (k >= N && k < N + M) {
-      for (int c = l; c < kchunks; c += 4) {
+#pragma unroll 8
+      for (int c = 0; c < kchunks; ++c) {
         const float2 v = ybpart[(int64_t)c * M + (k - N)];
         re += (double)v.x;
         im += (double)v.y;
@@ -392,22 +478,21 @@ __global__ void __launch_bounds__(256) k_cg_reduce_tc(const float* __restrict__ 
     } else {
       int64_t row, col;
       if (k < N) { row = 2 * (int64_t)M; col = k; }
-      else { const int64_t r = k - N - M; row = 2 * (r / N); col = r % N; }
-      for (int c = l; c < kchunks; c += 4) {
-        const float* g = out + (int64_t)c * a_rows * ncols;
-        re += (double)g[row * ncols + col];
-        im += (double)g[(row + 1) * ncols + col];
+      else { const int64_t rr = k - N - M; row = 2 * (rr / N); col = rr % N; }
+      const float* g = out + row * ncols + col;
+      const int64_t cs = a_rows * ncols;
+#pragma unroll 8
+      for (int c = 0; c < kchunks; ++c) {
+        re += (double)g[(int64_t)c * cs];
+        im += (double)g[(int64_t)c * cs + ncols];
       }
     }
-  }
-  re += __shfl_xor_sync(0xffffffffu, re, 1);
-  im += __shfl_xor_sync(0xffffffffu, im, 1);
-  re += __shfl_xor_sync(0xffffffffu, re, 2);
-  im += __shfl_xor_sync(0xffffffffu, im, 2);
-  if (k < P && l == 0) {
     const double2 pk = p[k];
-    q[k] = make_double2(re * inv + D[k] * pk.x, im * inv + D[k] * pk.y);
+    const double2 qk = make_double2(re * inv + D[k] * pk.x, im * inv + D[k] * pk.y);
+    q[k] = qk;
+    pq += pk.x * qk.x + pk.y * qk.y;
   }
+  block_partial(pq, vpart + OFF_PQ, red);
 }
 
 static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, double2* q,
@@ -419,45 +504,36 @@ static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, 
       (int64_t)sh.kchunks * sh.mtiles * 128 * sh.nbt * 128 > w.cap_part2 ||
       (int64_t)sh.kchunks * M > w.cap_yb)
     return cudaErrorInvalidValue;
-  k_split_v<<<g1d(P), 256, 0, st>>>(p, N, M, w.va, w.vb, w.V);
-  k_build_vplanes<<<g1d(sh.v_rows * sh.kN), 256, 0, st>>>(w.V, w.va, N, M, sh.v_rows, sh.kN,
-                                                          w.Vhi, w.Vlo);
-  VMC_TRY(cdot(pb.meanO_conj_free, p, P, w, w.c2, st));   // c = sum_k <O_k> p_k (no conj)
+  k_build_vplanes<<<g1d(sh.v_rows * sh.kN), 256, 0, st>>>(p, N, M, sh.v_rows, sh.kN, w.Vhi,
+                                                          w.Vlo, w.vb, w.flag);
   int nup = 0;
-  VMC_TRY(launch_cg_ov_tc(w.Sb, w.Vhi, w.Vlo, sh, pb.T, w.vb, reinterpret_cast<const double*>(w.c2),
-                          M, n, w.u, w.ovpart, &nup, pb.status, st));
+  VMC_TRY(launch_cg_ov_tc(w.Sb, w.Vhi, w.Vlo, sh, pb.T, w.vb, w.sc + 2, M, n, w.u, w.ovpart,
+                          &nup, w.flag, pb.status, st));
   if (nup > w.cap_ov) return cudaErrorInvalidValue;
-  VMC_TRY(launch_cg_ohu_tc(w.Bs, sh, pb.T, w.u, w.ovpart, nup, M, n, w.part2, w.ybpart,
+  VMC_TRY(launch_cg_ohu_tc(w.Bs, sh, pb.T, w.u, w.ovpart, nup, M, n, w.part2, w.ybpart, w.flag,
                            pb.status, st));
-  k_cg_reduce_tc<<<(unsigned)((P + 63) / 64), 256, 0, st>>>(w.part2, w.ybpart, sh.kchunks,
-                                                            (int64_t)sh.mtiles * 128, sh.nbt * 128,
-                                                            N, M, n, w.D, p, q);
-  *launches += 7;
+  k_cg_reduce_tc<<<CG_RB, 128, 0, st>>>(w.part2, w.ybpart, sh.kchunks, (int64_t)sh.mtiles * 128,
+                                        sh.nbt * 128, N, M, n, w.D, p, q, w.vpart, w.flag);
+  *launches += 4;
   return cudaGetLastError();
 }
 
+// q = S~ p with the centring constant c = <O>.p already in w.sc[2..3]
 static cudaError_t apply_s(const CgProblem& pb, CgWork& w, const double2* p, double2* q,
                            cudaStream_t st, int64_t* launches) {
   if (pb.tc) return apply_s_tc(pb, w, p, q, st, launches);
   const int N = pb.N, M = pb.M;
   const int64_t n = pb.n, P = (int64_t)N + M + (int64_t)N * M;
-  k_split_v<<<g1d(P), 256, 0, st>>>(p, N, M, w.va, w.vb, w.V);
-  VMC_TRY(cdot(pb.meanO_conj_free, p, P, w, w.c2, st));   // c = sum_k <O_k> p_k (no conj)
+  k_split_v<<<g1d(P), 256, 0, st>>>(p, N, M, w.va, w.vb, w.V, w.flag);
   const int mtiles = (M + VS_J - 1) / VS_J;
   dim3 grid((unsigned)((n + VS_Q - 1) / VS_Q), (unsigned)mtiles);
   k_vs_partial<<<grid, 256, 0, st>>>(w.V, w.vb, pb.spins, pb.T, n, N, M, w.upart);
-  k_vs_finish<<<g1d(n), 256, 0, st>>>(w.upart, mtiles, pb.spins, w.va,
-                                      reinterpret_cast<const double*>(w.c2), n, N, w.u);
+  k_vs_finish<<<g1d(n), 256, 0, st>>>(w.upart, mtiles, pb.spins, w.va, w.sc + 2, n, N, w.u);
   VMC_TRY(launch_estats(w.u, n, w.ustats, nullptr, st));
   VMC_TRY(launch_moments(pb.spins, pb.T, w.u, w.ustats, n, N, M, w.mpart, nullptr, w.y, st));
-  k_add_diag<<<g1d(P), 256, 0, st>>>(w.y, w.D, p, P, q);
-  *launches += 11;
+  k_add_diag<<<CG_RB, 256, 0, st>>>(w.y, w.D, p, P, q, w.vpart, w.flag);
+  *launches += 8;
   return cudaGetLastError();
-}
-
-__global__ void k_conj_copy(const double2* __restrict__ a, int64_t P, double2* __restrict__ b) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P; k += (int64_t)gridDim.x * blockDim.x)
-    b[k] = make_double2(a[k].x, -a[k].y);
 }
 
 cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cudaStream_t st,
@@ -465,9 +541,7 @@ cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cuda
   const int64_t P = (int64_t)pb.N + pb.M + (int64_t)pb.N * pb.M;
   k_t2<<<pb.M, 256, 0, st>>>(pb.T, pb.n, pb.M, w.t2);
   k_diag_s<<<g1d(P), 256, 0, st>>>(pb.meanO, w.t2, pb.N, pb.M, nu, mode, w.D, w.Minv);
-  // <O> with conjugation undone so that cdot(conj(a), p) gives sum <O_k> p_k
-  k_conj_copy<<<g1d(P), 256, 0, st>>>(pb.meanO, P, w.meanO_c);
-  *launches += 3;
+  *launches += 2;
   if (pb.tc) {
     const CgTcShape sh = cg_tc_shape(pb.N, pb.M, pb.n);
     if (!sh.ok || sh.s_rows * sh.kN > w.cap_sb || sh.b_rows * sh.ldK > w.cap_bs)
@@ -481,52 +555,51 @@ cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cuda
   return cudaGetLastError();
 }
 
-cudaError_t cg_apply(const CgProblem& pb_in, CgWork& w, const double2* v, double2* y,
+cudaError_t cg_apply(const CgProblem& pb, CgWork& w, const double2* v, double2* y,
                      cudaStream_t st, int64_t* launches) {
-  CgProblem pb = pb_in;
-  pb.meanO_conj_free = w.meanO_c;
+  const int64_t P = (int64_t)pb.N + pb.M + (int64_t)pb.N * pb.M;
+  VMC_TRY(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), st));
+  k_cg_cpart<<<CG_VB, 256, 0, st>>>(v, pb.meanO, P, w.vpart);
+  // the check kernel publishes c (its |r|^2 and done outputs are not used here)
+  k_cg_check<<<1, 32, 0, st>>>(w.vpart, 0, 0.0, w.sc, w.flag + 2, 1, 0);
+  *launches += 2;
   return apply_s(pb, w, v, y, st, launches);
 }
 
-cudaError_t cg_solve(const CgProblem& pb_in, const double2* F, double2* x, double tol, int maxit,
+// Host loop: the iterations are enqueued without waiting; every CG_SYNC_EVERY iterations
+// the host reads the done flag.  Iterations enqueued after convergence find done set and
+// return at once, so the result equals that of a check after every iteration.
+constexpr int CG_SYNC_EVERY = 4;
+
+cudaError_t cg_solve(const CgProblem& pb, const double2* F, double2* x, double tol, int maxit,
                      CgWork& w, cudaStream_t st, int64_t* launches, int* iters, double* relres) {
-  CgProblem pb = pb_in;
-  pb.meanO_conj_free = w.meanO_c;
   const int64_t P = (int64_t)pb.N + pb.M + (int64_t)pb.N * pb.M;
-  VMC_TRY(cudaMemsetAsync(x, 0, P * sizeof(double2), st));
-  VMC_TRY(cudaMemsetAsync(w.sc, 0, 8 * sizeof(double), st));
-  VMC_TRY(cudaMemcpyAsync(w.r, F, P * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  k_prec<<<g1d(P), 256, 0, st>>>(w.Minv, w.r, P, w.z);
-  VMC_TRY(cudaMemcpyAsync(w.p, w.z, P * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-  VMC_TRY(cdot(w.r, w.z, P, w, w.c2 + 1, st));
-  VMC_TRY(cdot(w.r, w.r, P, w, w.c2 + 4, st));
-  k_cg_beta<<<1, 1, 0, st>>>(w.sc, w.c2 + 1, w.c2 + 4);     // sc[0] = r.z, sc[5] = |F|^2
-  *launches += 6;
-  double h[8];
-  VMC_TRY(cudaMemcpyAsync(h, w.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  VMC_TRY(cudaStreamSynchronize(st));
-  const double f2 = h[5];
-  double rr = f2;
-  int it = 0;
-  while (it < maxit && rr > tol * tol * f2) {
+  const double tol2 = tol * tol;
+  VMC_TRY(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), st));
+  k_cg_init<<<CG_VB, 256, 0, st>>>(F, w.Minv, pb.meanO, P, x, w.r, w.z, w.p, w.vpart);
+  *launches += 1;
+  int h_flag[4] = {0, 0, 0, 0};
+  for (int it = 0; it < maxit; ++it) {
+    k_cg_check<<<1, 32, 0, st>>>(w.vpart, it, tol2, w.sc, w.flag, it == 0, 1);
     VMC_TRY(apply_s(pb, w, w.p, w.q, st, launches));
-    VMC_TRY(cdot(w.p, w.q, P, w, w.c2 + 2, st));
-    k_cg_alpha<<<1, 1, 0, st>>>(w.sc, w.c2 + 2);
-    k_cg_xr<<<g1d(P), 256, 0, st>>>(x, w.r, w.p, w.q, P, w.sc + 2);
-    k_prec<<<g1d(P), 256, 0, st>>>(w.Minv, w.r, P, w.z);
-    VMC_TRY(cdot(w.r, w.z, P, w, w.c2 + 3, st));
-    VMC_TRY(cdot(w.r, w.r, P, w, w.c2 + 5, st));
-    k_cg_beta<<<1, 1, 0, st>>>(w.sc, w.c2 + 3, w.c2 + 5);
-    k_cg_p<<<g1d(P), 256, 0, st>>>(w.p, w.z, P, w.sc + 3);
-    *launches += 12;
-    VMC_TRY(cudaMemcpyAsync(h, w.sc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    VMC_TRY(cudaStreamSynchronize(st));
-    rr = h[5];
-    ++it;
-    if (!(rr == rr)) break;
+    k_cg_update<<<CG_VB, 256, 0, st>>>(x, w.r, w.z, w.p, w.q, w.Minv, P, w.vpart, it, w.flag);
+    k_cg_dir<<<CG_VB, 256, 0, st>>>(w.p, w.z, pb.meanO, P, w.vpart, it, w.flag);
+    *launches += 3;
+    if ((it + 1) % CG_SYNC_EVERY == 0 && it + 1 < maxit) {
+      VMC_TRY(cudaMemcpyAsync(h_flag, w.flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+      VMC_TRY(cudaStreamSynchronize(st));
+      if (h_flag[0]) break;
+    }
   }
-  if (iters) *iters = it;
-  if (relres) *relres = (f2 > 0) ? sqrt(rr / f2) : 0.0;
+  // the residual of the final state when maxit ended the loop (a no-op once done is set)
+  k_cg_check<<<1, 32, 0, st>>>(w.vpart, maxit, tol2, w.sc, w.flag, maxit == 0, 0);
+  *launches += 1;
+  double h_sc[4];
+  VMC_TRY(cudaMemcpyAsync(h_sc, w.sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VMC_TRY(cudaMemcpyAsync(h_flag, w.flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  VMC_TRY(cudaStreamSynchronize(st));
+  if (iters) *iters = h_flag[1];
+  if (relres) *relres = (h_sc[0] > 0) ? sqrt(h_sc[1] / h_sc[0]) : 0.0;
   return cudaGetLastError();
 }
 

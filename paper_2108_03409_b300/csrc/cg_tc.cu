@@ -29,6 +29,8 @@ namespace cgtc {
 constexpr int TILE = 128 * 64 * 2;              // 128 rows x 64 BF16 (one swizzle row each)
 constexpr int THREADS = 64 + 32 * 8;            // TMA warp, MMA warp, eight worker warps
 constexpr int WORKER_WARPS = 8;
+constexpr int OV_EPI_WARPS = 16;                // Ov: four warps per TMEM lane quadrant
+constexpr int OV_THREADS = 64 + 32 * OV_EPI_WARPS;
 constexpr int TAIL = 1024;                      // barriers and small shared scalars
 // Ov: a work item is 256 samples (two 128-row sub-tiles sharing every V stage); K = N <= 256
 constexpr int OV_MAX_NKB = 4;
@@ -80,15 +82,16 @@ __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uin
 // sample per thread, whose row of t it loads from HBM (32 hidden units ahead of use).
 // upart[b] = FP64 sum of u over the samples CTA b wrote.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(cgtc::THREADS, 1)
+__global__ void __launch_bounds__(cgtc::OV_THREADS, 1)
 k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUtensorMap map_vhi,
         const __grid_constant__ CUtensorMap map_vlo, const __grid_constant__ CUtensorMap map_t,
         int prefetch_t, int nkb, int nct, int64_t items,
         const float2* __restrict__ T, const float2* __restrict__ vb, const double* __restrict__ c,
         int M, int64_t n, float2* __restrict__ u, double2* __restrict__ upart,
-        unsigned* status) {
+        const int* __restrict__ done, unsigned* status) {
   using namespace tc;
   using namespace cgtc;
+  if (*done) return;                                      // the CG iteration has converged
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = align1024(gsm_raw);
   uint8_t* Abuf = smem;                                   // [kb][sub] tiles
@@ -103,13 +106,13 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
   uint64_t* fin = bars + 18;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 19);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  double2* red = reinterpret_cast<double2*>(bars + 20);   // [8]
+  double2* red = reinterpret_cast<double2*>(bars + 20);   // [16]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < 19; ++s) mbar_init(smem_u32(&bars[s]), 1);
-    mbar_init(smem_u32(&acce[0]), WORKER_WARPS);
-    mbar_init(smem_u32(&acce[1]), WORKER_WARPS);
+    mbar_init(smem_u32(&acce[0]), OV_EPI_WARPS);
+    mbar_init(smem_u32(&acce[1]), OV_EPI_WARPS);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -229,18 +232,20 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
     }
   } else {
     // ---------------- epilogue: u_q ----------------
-    // Warp e owns TMEM lane quadrant e % 4 of sample sub-tile (e - 2) / 4 and reads it with
-    // the 16x256b shape, two 16-lane halves hh per quarter (16 units = 32 columns): thread t
-    // gets samples 16 hh + t/4 and 16 hh + t/4 + 8 of the quadrant and units 4 (t%4) .. + 3
-    // of the quarter (the V rows are ordered for this), so its t and v_b come in 16-byte
-    // loads; the four threads of a sample sum their parts at the end of the item.
+    // Sixteen warps, four per TMEM lane quadrant (warp % 4): warp e reads lanes
+    // 32 (e % 4) + 16 hh .. + 15 of sample sub-tile sub, (sub, hh) = ((e - 2) / 8, (e - 2) / 4 % 2),
+    // with the 16x256b shape, one quarter (16 units = 32 columns) at a time: thread t gets
+    // samples t/4 and t/4 + 8 of those 16 lanes and units 4 (t%4) .. + 3 of the quarter (the
+    // V rows are ordered for this), so its t and v_b come in 16-byte loads; the four threads
+    // of a sample sum their parts at the end of the item.
     const int ew = warp - 2;
-    const int qd = warp & 3, sub = ew >> 2;
+    const int qd = warp & 3, sub = ew >> 3, hh = (ew >> 2) & 1;
     const int cq = lane & 3, sl = lane >> 2;
     const bool vec = (M & 1) == 0;
     const float cre = (float)c[0], cim = (float)c[1];
+    const int row0 = sub * 128 + qd * 32 + 16 * hh + sl;    // sample of lane t/4 in the item
     // quarter (item w, column tile ct, qtr): units jb = 64 ct + 16 qtr ..; a quarter's t
-    // (4 samples x 4 units per thread) is loaded two quarters ahead into one of three
+    // (2 samples x 4 units per thread) is loaded two quarters ahead into one of three
     // rotating buffers; two cursors advance without divisions
     struct Cursor {
       int64_t w;
@@ -255,37 +260,34 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
         }
       }
     };
-    // dst[2 (2 hh + e) + p]: units j0 + 2p, j0 + 2p + 1 of sample 16 hh + sl + 8 e
-    auto load_t = [&](const Cursor& k, float4 (&dst)[8]) {
+    // dst[2 e + p]: units j0 + 2p, j0 + 2p + 1 of sample row0 + 8 e
+    auto load_t = [&](const Cursor& k, float4 (&dst)[4]) {
       if (k.w >= items) return;
       const int j0 = k.ct * 64 + k.qtr * 16 + 4 * cq;
-      const int64_t mb = k.w * 256 + sub * 128 + qd * 32 + sl;
 #pragma unroll
-      for (int se = 0; se < 4; ++se) {
-        const int64_t m = mb + 16 * (se >> 1) + 8 * (se & 1);
+      for (int e = 0; e < 2; ++e) {
+        const int64_t m = k.w * 256 + row0 + 8 * e;
         if (m < n && vec && j0 + 4 <= M) {
           const float4* src = reinterpret_cast<const float4*>(T + m * M + j0);
-          dst[2 * se] = src[0];
-          dst[2 * se + 1] = src[1];
+          dst[2 * e] = src[0];
+          dst[2 * e + 1] = src[1];
         } else {
 #pragma unroll
           for (int p = 0; p < 2; ++p) {
             const int j = j0 + 2 * p;
             const float2 x = (m < n && j < M) ? T[m * M + j] : make_float2(0.f, 0.f);
             const float2 y = (m < n && j + 1 < M) ? T[m * M + j + 1] : make_float2(0.f, 0.f);
-            dst[2 * se + p] = make_float4(x.x, x.y, y.x, y.y);
+            dst[2 * e + p] = make_float4(x.x, x.y, y.x, y.y);
           }
         }
       }
     };
     double usr = 0.0, usi = 0.0;
-    float acc[4][2];                                // [sample 2 hh + e][re, im]
-#pragma unroll
-    for (int se = 0; se < 4; ++se) acc[se][0] = acc[se][1] = 0.f;
+    float acc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};    // [sample e][re, im]
     bool ok = true;
     int64_t cc = 0;                                 // column tiles completed
     Cursor use{(int64_t)blockIdx.x, 0, 0}, ahead = use;
-    auto step = [&](const float4 (&cur)[8], float4 (&nxt)[8]) {
+    auto step = [&](const float4 (&cur)[4], float4 (&nxt)[4]) {
       if (!ok || use.w >= items) return;
       load_t(ahead, nxt);
       advance(ahead);
@@ -311,27 +313,23 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
         for (int k = 0; k < 4; ++k) bv[k] = (j0 + k < M) ? vb[j0 + k] : make_float2(0.f, 0.f);
       }
       const bool interior = j0 + 4 <= M;
+      float v[16];
+      tmem_ld16x256b_x4(tmem + ((uint32_t)(32 * qd + 16 * hh) << 16) +
+                            (uint32_t)(b * 256 + sub * 128 + use.qtr * 32), v);
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        float v[16];
-        tmem_ld16x256b_x4(tmem + ((uint32_t)(32 * qd + 16 * hh) << 16) +
-                              (uint32_t)(b * 256 + sub * 128 + use.qtr * 32), v);
+      for (int e = 0; e < 2; ++e) {
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int se = 2 * hh + e;
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const float4 t4 = cur[2 * se + (k >> 1)];
-            const float tr = (k & 1) ? t4.z : t4.x, ti = (k & 1) ? t4.w : t4.y;
-            const float zr0 = v[4 * k + 2 * e], zi0 = v[4 * k + 2 * e + 1];
-            if (interior || j0 + k < M) {
-              const float zr = zr0 + bv[k].x, zi = zi0 + bv[k].y;
-              acc[se][0] = fmaf(tr, zr, fmaf(-ti, zi, acc[se][0]));
-              acc[se][1] = fmaf(tr, zi, fmaf(ti, zr, acc[se][1]));
-            } else if (j0 + k == M) {             // v_a rows: sum_i s_qi v_a,i as is
-              acc[se][0] += zr0;
-              acc[se][1] += zi0;
-            }
+        for (int k = 0; k < 4; ++k) {
+          const float4 t4 = cur[2 * e + (k >> 1)];
+          const float tr = (k & 1) ? t4.z : t4.x, ti = (k & 1) ? t4.w : t4.y;
+          const float zr0 = v[4 * k + 2 * e], zi0 = v[4 * k + 2 * e + 1];
+          if (interior || j0 + k < M) {
+            const float zr = zr0 + bv[k].x, zi = zi0 + bv[k].y;
+            acc[e][0] = fmaf(tr, zr, fmaf(-ti, zi, acc[e][0]));
+            acc[e][1] = fmaf(tr, zi, fmaf(ti, zr, acc[e][1]));
+          } else if (j0 + k == M) {               // v_a rows: sum_i s_qi v_a,i as is
+            acc[e][0] += zr0;
+            acc[e][1] += zi0;
           }
         }
       }
@@ -342,26 +340,26 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
         ++cc;
         if (use.ct == nct - 1) {                   // the item's last column tile: u is complete
 #pragma unroll
-          for (int se = 0; se < 4; ++se) {
-            float xr = acc[se][0], xi = acc[se][1];
+          for (int e = 0; e < 2; ++e) {
+            float xr = acc[e][0], xi = acc[e][1];
             xr += __shfl_xor_sync(0xffffffffu, xr, 1);
             xi += __shfl_xor_sync(0xffffffffu, xi, 1);
             xr += __shfl_xor_sync(0xffffffffu, xr, 2);
             xi += __shfl_xor_sync(0xffffffffu, xi, 2);
-            const int64_t m = use.w * 256 + sub * 128 + qd * 32 + 16 * (se >> 1) + 8 * (se & 1) + sl;
+            const int64_t m = use.w * 256 + row0 + 8 * e;
             if (cq == 0 && m < n) {
               const float ur = xr - cre, ui = xi - cim;
               u[m] = make_float2(ur, ui);
               usr += (double)ur;
               usi += (double)ui;
             }
-            acc[se][0] = acc[se][1] = 0.f;
+            acc[e][0] = acc[e][1] = 0.f;
           }
         }
       }
       advance(use);
     };
-    float4 ta[8], tb[8], tc3[8];
+    float4 ta[4], tb[4], tc3[4];
     load_t(ahead, ta);
     advance(ahead);
     load_t(ahead, tb);
@@ -374,10 +372,10 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
     usr = warp_sum_d(usr);
     usi = warp_sum_d(usi);
     if (lane == 0) red[ew] = make_double2(usr, usi);
-    named_bar_sync(1, 32 * WORKER_WARPS);
+    named_bar_sync(1, 32 * OV_EPI_WARPS);
     if (ew == 0 && lane == 0) {
       double sr = 0.0, si = 0.0;
-      for (int k = 0; k < WORKER_WARPS; ++k) {
+      for (int k = 0; k < OV_EPI_WARPS; ++k) {
         sr += red[k].x;
         si += red[k].y;
       }
@@ -412,9 +410,11 @@ __global__ void __launch_bounds__(cgtc::THREADS, 1)
 k_cg_ohu(const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_t,
          int prefetch_t, int nbt, int nkb, int nkpc, int mtiles, const float2* __restrict__ T,
          const float2* __restrict__ u, const double2* __restrict__ upart, int nup, int M,
-         int64_t n, float* __restrict__ out, float2* __restrict__ ybpart, unsigned* status) {
+         int64_t n, float* __restrict__ out, float2* __restrict__ ybpart,
+         const int* __restrict__ done, unsigned* status) {
   using namespace tc;
   using namespace cgtc;
+  if (*done) return;                                      // the CG iteration has converged
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = align1024(gsm_raw);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + OH_STAGES * OH_STAGE_BYTES);
@@ -659,7 +659,8 @@ CgTcShape cg_tc_shape(int N, int M, int64_t n) {
 cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
                             const __nv_bfloat16* Vlo, const CgTcShape& sh, const float2* T,
                             const float2* vb, const double* c, int M, int64_t n, float2* u,
-                            double2* upart, int* nup, unsigned* status, cudaStream_t st) {
+                            double2* upart, int* nup, const int* done, unsigned* status,
+                            cudaStream_t st) {
   if (!sh.ok) return cudaErrorNotSupported;
   CUtensorMap ms, mvh, mvl, mt;
   cudaError_t e;
@@ -679,16 +680,17 @@ cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
   }
   const int64_t items = sh.s_rows / 256;
   const unsigned grid = persistent_grid(items);
-  k_cg_ov<<<grid, cgtc::THREADS, cgtc::OV_SMEM, st>>>(ms, mvh, mvl, mt, pf, (int)(sh.kN / 64),
+  k_cg_ov<<<grid, cgtc::OV_THREADS, cgtc::OV_SMEM, st>>>(ms, mvh, mvl, mt, pf, (int)(sh.kN / 64),
                                                       (int)(sh.v_rows / 128), items, T, vb, c, M,
-                                                      n, u, upart, status);
+                                                      n, u, upart, done, status);
   *nup = (int)grid;
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const float2* T,
                              const float2* u, const double2* upart, int nup, int M, int64_t n,
-                             float* out, float2* ybpart, unsigned* status, cudaStream_t st) {
+                             float* out, float2* ybpart, const int* done, unsigned* status,
+                             cudaStream_t st) {
   if (!sh.ok) return cudaErrorNotSupported;
   CUtensorMap mb, mt;
   cudaError_t e;
@@ -706,7 +708,7 @@ cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const
   const unsigned grid = (unsigned)(sh.mtiles * sh.kchunks);
   k_cg_ohu<<<grid, cgtc::THREADS, cgtc::OH_SMEM, st>>>(mb, mt, pf, sh.nbt, (int)(sh.ldK / 64), sh.nkpc,
                                                        sh.mtiles, T, u, upart, nup, M, n, out,
-                                                       ybpart, status);
+                                                       ybpart, done, status);
   return cudaGetLastError();
 }
 

@@ -171,6 +171,33 @@ __device__ __forceinline__ void tmem_ld16x256b_x4(uint32_t taddr, float (&v)[16]
   for (int k = 0; k < 16; ++k) v[k] = __uint_as_float(r[k]);
 }
 
+// tmem_ld16x256b_x4 without the wait: two loads, then tmem_wait_ld2 on both register sets.
+// The values are valid only after the wait.
+__device__ __forceinline__ void tmem_ld16x256b_x4_nowait(uint32_t taddr, float (&v)[16]) {
+  uint32_t* r = reinterpret_cast<uint32_t*>(v);
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// The wait for two outstanding 16-register loads; the registers are operands so that no
+// use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld2(float (&a)[16], float (&b)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(a[0]), "+f"(a[1]), "+f"(a[2]), "+f"(a[3]), "+f"(a[4]), "+f"(a[5]),
+                 "+f"(a[6]), "+f"(a[7]), "+f"(a[8]), "+f"(a[9]), "+f"(a[10]), "+f"(a[11]),
+                 "+f"(a[12]), "+f"(a[13]), "+f"(a[14]), "+f"(a[15]), "+f"(b[0]), "+f"(b[1]),
+                 "+f"(b[2]), "+f"(b[3]), "+f"(b[4]), "+f"(b[5]), "+f"(b[6]), "+f"(b[7]),
+                 "+f"(b[8]), "+f"(b[9]), "+f"(b[10]), "+f"(b[11]), "+f"(b[12]), "+f"(b[13]),
+                 "+f"(b[14]), "+f"(b[15])
+               :
+               : "memory");
+}
+
 // 16 lanes x 256 bits, repeated over 4 x 8 columns (warp-collective, 16x256b shape):
 // thread t holds, for repetition k, v[4k] at (lane t/4, column 8k + 2(t%4)), v[4k+1] at
 // (lane t/4, column 8k + 2(t%4) + 1), v[4k+2] and v[4k+3] at lane t/4 + 8, same columns.

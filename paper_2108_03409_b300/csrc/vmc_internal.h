@@ -187,12 +187,14 @@ CgTcShape cg_tc_shape(int N, int M, int64_t n);
 cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
                             const __nv_bfloat16* Vlo, const CgTcShape& sh, const float2* T,
                             const float2* vb, const double* c, int M, int64_t n, float2* u,
-                            double2* upart, int* nup, unsigned* status, cudaStream_t st);
+                            double2* upart, int* nup, const int* done, unsigned* status,
+                            cudaStream_t st);
 // chunk partials of sum_q A_rq s_qi with A rows 2j / 2j+1 = Re / Im conj(t_qj) w_q, rows
 // 2M / 2M+1 = Re / Im w_q, w = u - mean(u) (mean from upart), and of sum_q conj(t_qj) w_q
 cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const float2* T,
                              const float2* u, const double2* upart, int nup, int M, int64_t n,
-                             float* out, float2* ybpart, unsigned* status, cudaStream_t st);
+                             float* out, float2* ybpart, const int* done, unsigned* status,
+                             cudaStream_t st);
 
 // failure-path self-tests of the bounded waits (a flag / an mbarrier that nothing sets)
 cudaError_t launch_selftest_flag_wait(unsigned* word2, unsigned* status, cudaStream_t st);
@@ -205,23 +207,24 @@ struct CgProblem {
   int64_t n;
   int N, M;
   const double2* meanO;           // [P] <O>
-  const double2* meanO_conj_free; // set by cg_solve
   bool tc;                        // operator products on the tensor cores (BF16 split)
   unsigned* status;
 };
+constexpr int CG_VPART_DOUBLES = 2560;
 struct CgWork {
-  double2 *r, *p, *q, *y, *z, *meanO_c;   // [P]
+  double2 *r, *p, *q, *y, *z;         // [P]
   double* D;                          // [P] shift diagonal
   double* Minv;                       // [P] inverse diagonal of S~ (preconditioner)
   double* t2;                         // [M]
-  float2 *va, *vb, *V;                // FP32 copies of the CG direction
+  float2 *va, *vb, *V;                // FP32 copies of the CG direction (vb: M + 128, the
+                                      // tensor-core product copies 64-unit blocks)
   float2* u;                          // [n padded to 256] (the OhU kernel copies 64-sample blocks)
   float2* upart;                      // [ceil(M/64)][n]
   double* ustats;                     // [8]
   double* mpart;                      // moments scratch
-  double2* dpart;                     // [256] dot partials
-  double2* c2;                        // [8] device complex scalars
-  double* sc;                         // [8] device real scalars
+  double* vpart;                      // [CG_VPART_DOUBLES] FP64 block partials of the CG sums
+  double* sc;                         // [8] device scalars (|F|^2, |r|^2, <O>.p)
+  int* flag;                          // [4] done, iterations performed
   // tensor-core operator (capacities in elements; null when not allocated)
   __nv_bfloat16 *Sb, *Bs, *Vhi, *Vlo;
   float* part2;                       // OhU chunk partials
