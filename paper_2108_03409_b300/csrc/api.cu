@@ -339,7 +339,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
   }
   const int64_t Ns = ctx->Ns;
   if ((e = dalloc(ctx, &ctx->s_spins, (size_t)Ns * ctx->Nmax)) ||
-      (e = dalloc(ctx, &ctx->s_T, (size_t)Ns * ctx->Mmax)) || (e = dalloc(ctx, &ctx->s_E, Ns)) ||
+      (e = dalloc(ctx, &ctx->s_T, (size_t)Ns * ctx->Mmax)) || (e = dalloc(ctx, &ctx->s_E, (Ns + 255) / 256 * 256)) ||
       (e = dalloc(ctx, &ctx->estats, 8)) ||
       (e = dalloc(ctx, &ctx->partial, (size_t)moments_partial_doubles(Ns, ctx->Nmax, ctx->Mmax))) ||
       (e = dalloc(ctx, &ctx->meanO, ctx->Pmax)) || (e = dalloc(ctx, &ctx->mean2, ctx->Pmax)) || (e = dalloc(ctx, &ctx->F, ctx->Pmax)) ||
@@ -357,11 +357,18 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &w.V, (size_t)ctx->Nmax * ctx->Mmax)) || (e = dalloc(ctx, &w.u, (Ns + 255) / 256 * 256)) ||
         (e = dalloc(ctx, &w.upart, (size_t)cg_partial_floats2(Ns, ctx->Mmax))) ||
         (e = dalloc(ctx, &w.ustats, 8)) || (e = dalloc(ctx, &w.vpart, CG_VPART_DOUBLES)) ||
-        (e = dalloc(ctx, &w.sc, 8)) || (e = dalloc(ctx, &w.flag, 4)))
+        (e = dalloc(ctx, &w.sc, 8)) || (e = dalloc(ctx, &w.flag, 8)) ||
+        (e = dalloc(ctx, &w.ones, (Ns + 255) / 256 * 256)) || (e = dalloc(ctx, &w.zero2, 2)))
       return oom(e);
     w.mpart = ctx->partial;
-    // u stays finite beyond the sample count (the OhU kernel reads whole 64-sample blocks)
-    if ((e = cudaMemset(w.u, 0, sizeof(float2) * (size_t)((Ns + 255) / 256 * 256))) != cudaSuccess)
+    // u and E stay finite beyond the sample count (the O^H u kernel reads whole 64-sample
+    // blocks); the flags' upper half, the zero mean and the ones are constants
+    const size_t npad = (size_t)((Ns + 255) / 256 * 256);
+    if ((e = cudaMemset(w.u, 0, sizeof(float2) * npad)) != cudaSuccess ||
+        (e = cudaMemset(ctx->s_E, 0, sizeof(float2) * npad)) != cudaSuccess ||
+        (e = cudaMemset(w.flag, 0, 8 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(w.zero2, 0, 2 * sizeof(double))) != cudaSuccess ||
+        (e = fill_ones(w.ones, (int64_t)npad)) != cudaSuccess)
       return oom(e);
     if (!ctx->dense && cfg->precision == VMC_PREC_BF16SPLIT) {
       // operator products on the tensor cores: operand planes sized for the largest lattice
@@ -720,13 +727,20 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
     }
     if (s) return s;
   } else {
-    // 3. <O>, F and diag(S) (S itself is never formed)
-    CK(launch_moments(ctx->s_spins, ctx->s_T, ctx->s_E, ctx->estats, Ns, L.N, L.M, ctx->partial,
-                      ctx->meanO, ctx->F, ctx->st), "moments");
-    ctx->launches += 2;
+    // 3. <O>, F and diag(S) (S itself is never formed); on the tensor-core path <O> and F
+    //    come from the same O^H u product the CG uses
     CgProblem pb{ctx->s_spins, ctx->s_T, Ns, L.N, L.M, ctx->meanO,
                  ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, Ns).ok, ctx->status};
-    CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
+    if (pb.tc) {
+      CK(cg_moments_tc(pb, ctx->s_E, ctx->estats, ctx->meanO, ctx->F, ctx->cg, ctx->st,
+                       &ctx->launches), "moments");
+    } else {
+      CK(launch_moments(ctx->s_spins, ctx->s_T, ctx->s_E, ctx->estats, Ns, L.N, L.M, ctx->partial,
+                        ctx->meanO, ctx->F, ctx->st), "moments");
+      ctx->launches += 2;
+    }
+    CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches, pb.tc),
+       "cg_prepare");
     cudaEventRecord(ctx->ev[6], ctx->st);
     cudaEventRecord(ctx->ev[7], ctx->st);
     CK(cudaEventRecord(ctx->ev[3], ctx->st), "sr_step");

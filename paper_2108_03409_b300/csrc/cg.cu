@@ -450,7 +450,8 @@ __global__ void __launch_bounds__(256) k_add_diag(const double2* __restrict__ y,
 
 // q_k = y_k + D_k p_k with y_k = (1/n) sum_q conj(Obar_qk) w_q from the K-chunk partials
 // (FP64 sum over chunks in order): a_i: out rows 2M / 2M+1, column i; b_j: ybpart[.][j];
-// W_ji: out rows 2j / 2j+1, column i.  Partials of Re p^H q.
+// W_ji: out rows 2j / 2j+1, column i.  Partials of Re p^H q.  Without D: q = y (conjugated
+// if conj_out), no partials.
 __global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ out,
                                                       const float2* __restrict__ ybpart,
                                                       int kchunks, int64_t a_rows, int ncols,
@@ -459,7 +460,8 @@ __global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ 
                                                       const double2* __restrict__ p,
                                                       double2* __restrict__ q,
                                                       double* __restrict__ vpart,
-                                                      const int* __restrict__ done) {
+                                                      const int* __restrict__ done,
+                                                      int conj_out) {
   if (*done) return;
   __shared__ double red[8];
   const int64_t P = (int64_t)N + M + (int64_t)N * M;
@@ -487,12 +489,16 @@ __global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ 
         im += (double)g[(int64_t)c * cs + ncols];
       }
     }
-    const double2 pk = p[k];
-    const double2 qk = make_double2(re * inv + D[k] * pk.x, im * inv + D[k] * pk.y);
-    q[k] = qk;
-    pq += pk.x * qk.x + pk.y * qk.y;
+    if (D) {
+      const double2 pk = p[k];
+      const double2 qk = make_double2(re * inv + D[k] * pk.x, im * inv + D[k] * pk.y);
+      q[k] = qk;
+      pq += pk.x * qk.x + pk.y * qk.y;
+    } else {
+      q[k] = make_double2(re * inv, conj_out ? -im * inv : im * inv);
+    }
   }
-  block_partial(pq, vpart + OFF_PQ, red);
+  if (D) block_partial(pq, vpart + OFF_PQ, red);
 }
 
 static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, double2* q,
@@ -510,10 +516,10 @@ static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, 
   VMC_TRY(launch_cg_ov_tc(w.Sb, w.Vhi, w.Vlo, sh, pb.T, w.vb, w.sc + 2, M, n, w.u, w.ovpart,
                           &nup, w.flag, pb.status, st));
   if (nup > w.cap_ov) return cudaErrorInvalidValue;
-  VMC_TRY(launch_cg_ohu_tc(w.Bs, sh, pb.T, w.u, w.ovpart, nup, M, n, w.part2, w.ybpart, w.flag,
-                           pb.status, st));
+  VMC_TRY(launch_cg_ohu_tc(w.Bs, sh, pb.T, w.u, w.ovpart, nup, nullptr, M, n, w.part2, w.ybpart,
+                           w.flag, pb.status, st));
   k_cg_reduce_tc<<<CG_RB, 128, 0, st>>>(w.part2, w.ybpart, sh.kchunks, (int64_t)sh.mtiles * 128,
-                                        sh.nbt * 128, N, M, n, w.D, p, q, w.vpart, w.flag);
+                                        sh.nbt * 128, N, M, n, w.D, p, q, w.vpart, w.flag, 0);
   *launches += 4;
   return cudaGetLastError();
 }
@@ -536,22 +542,65 @@ static cudaError_t apply_s(const CgProblem& pb, CgWork& w, const double2* p, dou
   return cudaGetLastError();
 }
 
+__global__ void k_fill_ones(float2* __restrict__ a, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    a[k] = make_float2(1.f, 0.f);
+}
+
+cudaError_t fill_ones(float2* a, int64_t n) {
+  k_fill_ones<<<g1d(n), 256>>>(a, n);
+  return cudaGetLastError();
+}
+
+// the spin operands of the tensor-core products (Sb [q][i] and Bs = Sb^T), once per sample set
+static cudaError_t build_spin_operands(const CgProblem& pb, CgWork& w, cudaStream_t st,
+                                       int64_t* launches) {
+  const CgTcShape sh = cg_tc_shape(pb.N, pb.M, pb.n);
+  if (!sh.ok || sh.s_rows * sh.kN > w.cap_sb || sh.b_rows * sh.ldK > w.cap_bs)
+    return cudaErrorInvalidValue;
+  k_build_sb<<<g1d(sh.s_rows * sh.kN), 256, 0, st>>>(pb.spins, pb.n, pb.N, sh.s_rows, sh.kN, w.Sb);
+  dim3 gb((unsigned)(sh.ldK / 32), (unsigned)(sh.b_rows / 32));
+  k_build_bs<<<gb, 256, 0, st>>>(pb.spins, pb.n, pb.N, sh.b_rows, sh.ldK, w.Bs);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t cg_moments_tc(const CgProblem& pb, const float2* E, const double* estats,
+                          double2* meanO, double2* F, CgWork& w, cudaStream_t st,
+                          int64_t* launches) {
+  VMC_TRY(build_spin_operands(pb, w, st, launches));
+  const int N = pb.N, M = pb.M;
+  const int64_t n = pb.n, P = (int64_t)N + M + (int64_t)N * M;
+  const CgTcShape sh = cg_tc_shape(N, M, n);
+  if ((int64_t)sh.kchunks * sh.mtiles * 128 * sh.nbt * 128 > w.cap_part2 ||
+      (int64_t)sh.kchunks * M > w.cap_yb)
+    return cudaErrorInvalidValue;
+  const int* zero = w.flag + 4;
+  // F_k = (1/n) sum_q conj(O_qk) (E_q - <E>)
+  VMC_TRY(launch_cg_ohu_tc(w.Bs, sh, pb.T, E, nullptr, 0, estats, M, n, w.part2, w.ybpart, zero,
+                           pb.status, st));
+  k_cg_reduce_tc<<<CG_RB, 128, 0, st>>>(w.part2, w.ybpart, sh.kchunks, (int64_t)sh.mtiles * 128,
+                                        sh.nbt * 128, N, M, n, nullptr, nullptr, F, nullptr, zero, 0);
+  // <O_k> = conj((1/n) sum_q conj(O_qk) 1)
+  VMC_TRY(launch_cg_ohu_tc(w.Bs, sh, pb.T, w.ones, nullptr, 0, w.zero2, M, n, w.part2, w.ybpart,
+                           zero, pb.status, st));
+  k_cg_reduce_tc<<<CG_RB, 128, 0, st>>>(w.part2, w.ybpart, sh.kchunks, (int64_t)sh.mtiles * 128,
+                                        sh.nbt * 128, N, M, n, nullptr, nullptr, meanO, nullptr, zero,
+                                        1);
+  *launches += 4;
+  (void)P;
+  return cudaGetLastError();
+}
+
 cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cudaStream_t st,
-                       int64_t* launches) {
+                       int64_t* launches, bool operands_ready) {
   const int64_t P = (int64_t)pb.N + pb.M + (int64_t)pb.N * pb.M;
   k_t2<<<pb.M, 256, 0, st>>>(pb.T, pb.n, pb.M, w.t2);
   k_diag_s<<<g1d(P), 256, 0, st>>>(pb.meanO, w.t2, pb.N, pb.M, nu, mode, w.D, w.Minv);
   *launches += 2;
-  if (pb.tc) {
-    const CgTcShape sh = cg_tc_shape(pb.N, pb.M, pb.n);
-    if (!sh.ok || sh.s_rows * sh.kN > w.cap_sb || sh.b_rows * sh.ldK > w.cap_bs)
-      return cudaErrorInvalidValue;
-    k_build_sb<<<g1d(sh.s_rows * sh.kN), 256, 0, st>>>(pb.spins, pb.n, pb.N, sh.s_rows, sh.kN,
-                                                       w.Sb);
-    dim3 gb((unsigned)(sh.ldK / 32), (unsigned)(sh.b_rows / 32));
-    k_build_bs<<<gb, 256, 0, st>>>(pb.spins, pb.n, pb.N, sh.b_rows, sh.ldK, w.Bs);
-    *launches += 2;
-  }
+  // the spin operands, unless cg_moments_tc just built them for this sample set
+  if (pb.tc && !operands_ready) VMC_TRY(build_spin_operands(pb, w, st, launches));
   return cudaGetLastError();
 }
 

@@ -409,9 +409,9 @@ k_cg_ov(const __grid_constant__ CUtensorMap map_s, const __grid_constant__ CUten
 __global__ void __launch_bounds__(cgtc::THREADS, 1)
 k_cg_ohu(const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUtensorMap map_t,
          int prefetch_t, int nbt, int nkb, int nkpc, int mtiles, const float2* __restrict__ T,
-         const float2* __restrict__ u, const double2* __restrict__ upart, int nup, int M,
-         int64_t n, float* __restrict__ out, float2* __restrict__ ybpart,
-         const int* __restrict__ done, unsigned* status) {
+         const float2* __restrict__ u, const double2* __restrict__ upart, int nup,
+         const double* __restrict__ mean_in, int M, int64_t n, float* __restrict__ out,
+         float2* __restrict__ ybpart, const int* __restrict__ done, unsigned* status) {
   using namespace tc;
   using namespace cgtc;
   if (*done) return;                                      // the CG iteration has converged
@@ -519,7 +519,7 @@ k_cg_ohu(const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUte
     const bool jv = j < M, jw = j == M;
     const uint32_t st_base = (uint32_t)(32 * qd + 16 * hsel) << 16;
     if (ew == 0) {
-      // mean(u) from the Ov CTAs' FP64 partials (fixed order)
+      // mean(u): given, or from the Ov CTAs' FP64 partials (fixed order)
       double sr = 0.0, si = 0.0;
       for (int k = lane; k < nup; k += 32) {
         sr += upart[k].x;
@@ -527,7 +527,9 @@ k_cg_ohu(const __grid_constant__ CUtensorMap map_b, const __grid_constant__ CUte
       }
       sr = warp_sum_d(sr);
       si = warp_sum_d(si);
-      if (lane == 0) *mean = make_float2((float)(sr / (double)n), (float)(si / (double)n));
+      if (lane == 0)
+        *mean = mean_in ? make_float2((float)mean_in[0], (float)mean_in[1])
+                        : make_float2((float)(sr / (double)n), (float)(si / (double)n));
     }
     named_bar_sync(1, 32 * WORKER_WARPS);
     const float mr = mean->x, mi = mean->y;
@@ -688,9 +690,9 @@ cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
 }
 
 cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const float2* T,
-                             const float2* u, const double2* upart, int nup, int M, int64_t n,
-                             float* out, float2* ybpart, const int* done, unsigned* status,
-                             cudaStream_t st) {
+                             const float2* u, const double2* upart, int nup, const double* mean,
+                             int M, int64_t n, float* out, float2* ybpart, const int* done,
+                             unsigned* status, cudaStream_t st) {
   if (!sh.ok) return cudaErrorNotSupported;
   CUtensorMap mb, mt;
   cudaError_t e;
@@ -707,7 +709,7 @@ cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const
   }
   const unsigned grid = (unsigned)(sh.mtiles * sh.kchunks);
   k_cg_ohu<<<grid, cgtc::THREADS, cgtc::OH_SMEM, st>>>(mb, mt, pf, sh.nbt, (int)(sh.ldK / 64), sh.nkpc,
-                                                       sh.mtiles, T, u, upart, nup, M, n, out,
+                                                       sh.mtiles, T, u, upart, nup, mean, M, n, out,
                                                        ybpart, done, status);
   return cudaGetLastError();
 }

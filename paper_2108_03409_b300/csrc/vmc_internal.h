@@ -190,11 +190,13 @@ cudaError_t launch_cg_ov_tc(const __nv_bfloat16* Sb, const __nv_bfloat16* Vhi,
                             double2* upart, int* nup, const int* done, unsigned* status,
                             cudaStream_t st);
 // chunk partials of sum_q A_rq s_qi with A rows 2j / 2j+1 = Re / Im conj(t_qj) w_q, rows
-// 2M / 2M+1 = Re / Im w_q, w = u - mean(u) (mean from upart), and of sum_q conj(t_qj) w_q
+// 2M / 2M+1 = Re / Im w_q, w = u - mean (mean: the two doubles at `mean` if not null, else
+// the sum of the nup FP64 partials in upart over n), and of sum_q conj(t_qj) w_q.  u is read
+// in whole 64-sample blocks (the buffer must be padded to a multiple of 64, finite).
 cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const float2* T,
-                             const float2* u, const double2* upart, int nup, int M, int64_t n,
-                             float* out, float2* ybpart, const int* done, unsigned* status,
-                             cudaStream_t st);
+                             const float2* u, const double2* upart, int nup, const double* mean,
+                             int M, int64_t n, float* out, float2* ybpart, const int* done,
+                             unsigned* status, cudaStream_t st);
 
 // failure-path self-tests of the bounded waits (a flag / an mbarrier that nothing sets)
 cudaError_t launch_selftest_flag_wait(unsigned* word2, unsigned* status, cudaStream_t st);
@@ -224,7 +226,9 @@ struct CgWork {
   double* mpart;                      // moments scratch
   double* vpart;                      // [CG_VPART_DOUBLES] FP64 block partials of the CG sums
   double* sc;                         // [8] device scalars (|F|^2, |r|^2, <O>.p)
-  int* flag;                          // [4] done, iterations performed
+  int* flag;                          // [8] done, iterations performed; [4..7] stay zero
+  float2* ones;                       // [n padded to 256] of (1, 0) (the <O> product's u)
+  double* zero2;                      // [2] zeros (its mean)
   // tensor-core operator (capacities in elements; null when not allocated)
   __nv_bfloat16 *Sb, *Bs, *Vhi, *Vlo;
   float* part2;                       // OhU chunk partials
@@ -235,7 +239,15 @@ struct CgWork {
 int64_t cg_partial_floats2(int64_t n, int M);
 // diag(S) and the conjugated means; T and meanO must describe the sample set
 cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cudaStream_t st,
-                       int64_t* launches);
+                       int64_t* launches, bool operands_ready = false);
+// <O> and F = <O^* (E - <E>)> (Eq. force_vector) with the tensor-core O^H u product
+// (BF16 hi/lo operand, FP32 sums within K chunks, FP64 across); builds the spin operands
+// the CG products use.  estats: FP64 <E> (re, im).  E: [n padded to 64] finite.
+cudaError_t cg_moments_tc(const CgProblem& pb, const float2* E, const double* estats,
+                          double2* meanO, double2* F, CgWork& w, cudaStream_t st,
+                          int64_t* launches);
+// a[k] = (1, 0) for k < n (default stream; the context's initialisation synchronises)
+cudaError_t fill_ones(float2* a, int64_t n);
 // y = S~ v once (after cg_prepare on the same problem)
 cudaError_t cg_apply(const CgProblem& pb, CgWork& w, const double2* v, double2* y,
                      cudaStream_t st, int64_t* launches);

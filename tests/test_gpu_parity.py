@@ -316,7 +316,9 @@ def test_solve_reports_non_positive_pivot():
 @pytest.mark.parametrize("solver,precision", [(vmc.SOLVER_CHOLESKY_FP64, vmc.PREC_FP32),
                                               (vmc.SOLVER_CHOLESKY_MIXED, vmc.PREC_FP32),
                                               (vmc.SOLVER_CHOLESKY_MIXED, vmc.PREC_BF16SPLIT),
-                                              (vmc.SOLVER_CHOLESKY_TC, vmc.PREC_BF16SPLIT)])
+                                              (vmc.SOLVER_CHOLESKY_TC, vmc.PREC_BF16SPLIT),
+                                              (vmc.SOLVER_CG, vmc.PREC_FP32),
+                                              (vmc.SOLVER_CG, vmc.PREC_BF16SPLIT)])
 def test_sr_step_matches_oracle_pipeline(solver, precision):
     """One SR step.  The sample set is read back through vmc_sample on a twin context
     (the kernels are deterministic, and the sampler's agreement with the oracle's
@@ -329,7 +331,7 @@ def test_sr_step_matches_oracle_pipeline(solver, precision):
     p = inputs.rbm_params(N, M, 0.01, seed=1234)
     s0 = inputs.random_spins(C, N, seed=99)
     kw = dict(n_chains=C, samples_per_chain=spc, therm_sweeps=therm, seed=seed, solver=solver,
-              precision=precision, shift=nu, cg_tol=1e-10, cg_maxit=50)
+              precision=precision, shift=nu, cg_tol=1e-10, cg_maxit=1000)
     with context(lattice(model, Lx, Ly, J, h, alpha), **kw) as twin:
         vmc.vmc_set_params(twin, 0, p)
         vmc.vmc_set_chains(twin, 0, s0)
