@@ -353,6 +353,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &w.y, P)) || (e = dalloc(ctx, &w.z, P)) ||
         (e = dalloc(ctx, &w.D, P)) ||
         (e = dalloc(ctx, &w.Minv, P)) || (e = dalloc(ctx, &w.t2, ctx->Mmax)) ||
+        (e = dalloc(ctx, &w.t2part, (size_t)CG_T2_BLOCKS * ctx->Mmax)) ||
         (e = dalloc(ctx, &w.va, ctx->Nmax)) || (e = dalloc(ctx, &w.vb, ctx->Mmax + 128)) ||
         (e = dalloc(ctx, &w.V, (size_t)ctx->Nmax * ctx->Mmax)) || (e = dalloc(ctx, &w.u, (Ns + 255) / 256 * 256)) ||
         (e = dalloc(ctx, &w.upart, (size_t)cg_partial_floats2(Ns, ctx->Mmax))) ||
@@ -692,6 +693,12 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   A.t_out = ctx->s_T;
   A.n_accept = ctx->n_accept;
   A.status = ctx->status;
+  // theta of the chains' spins as one tiled product (bit-identical to the sampler's own
+  // per-chain formation, which would read W once per chain).  It goes into the t buffer: a
+  // chain reads its row before it writes its first record there.
+  CK(launch_theta_gemm(A.rbm, L.chains, c.n_chains, ctx->s_T, ctx->st), "theta");
+  ++ctx->launches;
+  A.theta_in = ctx->s_T;
   CK(launch_sample(A, ctx->st), "sample");
   ++ctx->launches;
   const uint64_t steps = (uint64_t)(A.n_therm + A.n_samples * A.sweeps_per_sample) * (uint64_t)A.L;

@@ -139,22 +139,27 @@ __global__ void k_diag_s(const double2* __restrict__ meanO, const double* __rest
   }
 }
 
-// t2[j] = (1/n) sum_q |t_qj|^2 in FP64
-__global__ void k_t2(const float2* __restrict__ T, int64_t n, int M, double* __restrict__ t2) {
-  const int j = blockIdx.x;
-  __shared__ double red[8];
-  double s = 0;
-  for (int64_t q = threadIdx.x; q < n; q += blockDim.x) {
-    const float2 t = T[q * M + j];
-    s += (double)t.x * t.x + (double)t.y * t.y;
+// t2[j] = (1/n) sum_q |t_qj|^2 in FP64: block b sums rows b, b + T2_BLOCKS, ... (threads
+// along j, coalesced), then one thread per j adds the T2_BLOCKS partials in order
+constexpr int T2_BLOCKS = 256;
+__global__ void __launch_bounds__(256) k_t2_partial(const float2* __restrict__ T, int64_t n,
+                                                    int M, double* __restrict__ part) {
+  for (int j = threadIdx.x; j < M; j += blockDim.x) {
+    double s = 0.0;
+    for (int64_t q = blockIdx.x; q < n; q += gridDim.x) {
+      const float2 t = T[q * M + j];
+      s += (double)t.x * t.x + (double)t.y * t.y;
+    }
+    part[(int64_t)blockIdx.x * M + j] = s;
   }
-  s = warp_sum_d(s);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-    t2[j] = tot / (double)n;
+}
+
+__global__ void k_t2_final(const double* __restrict__ part, int nb, int64_t n, int M,
+                           double* __restrict__ t2) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * M + j];
+    t2[j] = s / (double)n;
   }
 }
 
@@ -596,9 +601,11 @@ cudaError_t cg_moments_tc(const CgProblem& pb, const float2* E, const double* es
 cudaError_t cg_prepare(const CgProblem& pb, CgWork& w, double nu, int mode, cudaStream_t st,
                        int64_t* launches, bool operands_ready) {
   const int64_t P = (int64_t)pb.N + pb.M + (int64_t)pb.N * pb.M;
-  k_t2<<<pb.M, 256, 0, st>>>(pb.T, pb.n, pb.M, w.t2);
+  static_assert(T2_BLOCKS == CG_T2_BLOCKS, "t2 partial buffer");
+  k_t2_partial<<<T2_BLOCKS, 256, 0, st>>>(pb.T, pb.n, pb.M, w.t2part);
+  k_t2_final<<<(pb.M + 255) / 256, 256, 0, st>>>(w.t2part, T2_BLOCKS, pb.n, pb.M, w.t2);
   k_diag_s<<<g1d(P), 256, 0, st>>>(pb.meanO, w.t2, pb.N, pb.M, nu, mode, w.D, w.Minv);
-  *launches += 2;
+  *launches += 3;
   // the spin operands, unless cg_moments_tc just built them for this sample set
   if (pb.tc && !operands_ready) VMC_TRY(build_spin_operands(pb, w, st, launches));
   return cudaGetLastError();

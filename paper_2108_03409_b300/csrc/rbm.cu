@@ -177,6 +177,70 @@ __global__ void k_ok_dense(const int8_t* __restrict__ spins, const float2* __res
   }
 }
 
+// theta for a batch of configurations: 64 configurations x 64 hidden units per block,
+// K (the sites) in slices of 32 through shared memory; thread (tq, tj) owns configurations
+// tq + 16 a and units tj + 16 b (a, b < 4) and runs each entry's chain of fused
+// multiply-adds over i in increasing order, starting from b_j.
+constexpr int TG_Q = 64, TG_J = 64, TG_K = 32;
+__global__ void __launch_bounds__(256) k_theta_gemm(const float2* __restrict__ b,
+                                                    const float2* __restrict__ Wt, int N, int M,
+                                                    const int8_t* __restrict__ spins, int64_t C,
+                                                    float2* __restrict__ theta) {
+  __shared__ float2 Ws[TG_K][TG_J + 1];
+  __shared__ float Ss[TG_Q][TG_K + 1];
+  const int tid = threadIdx.x, tq = tid & 15, tj = tid >> 4;
+  const int64_t q0 = (int64_t)blockIdx.x * TG_Q;
+  const int j0 = blockIdx.y * TG_J;
+  float2 acc[4][4];
+#pragma unroll
+  for (int bb = 0; bb < 4; ++bb) {
+    const int j = j0 + tj + 16 * bb;
+    const float2 bj = (j < M) ? b[j] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[a][bb] = bj;
+  }
+  for (int k0 = 0; k0 < N; k0 += TG_K) {
+    for (int e = tid; e < TG_K * TG_J; e += 256) {
+      const int kk = e / TG_J, jj = e % TG_J;
+      const int i = k0 + kk, j = j0 + jj;
+      Ws[kk][jj] = (i < N && j < M) ? Wt[(int64_t)i * M + j] : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < TG_Q * TG_K; e += 256) {
+      const int qq = e / TG_K, kk = e % TG_K;
+      const int64_t q = q0 + qq;
+      const int i = k0 + kk;
+      Ss[qq][kk] = (q < C && i < N) ? (float)spins[q * N + i] : 0.f;
+    }
+    __syncthreads();
+    const int kn = min(TG_K, N - k0);
+    for (int kk = 0; kk < kn; ++kk) {
+      float sv[4];
+      float2 wv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) sv[a] = Ss[tq + 16 * a][kk];
+#pragma unroll
+      for (int bb = 0; bb < 4; ++bb) wv[bb] = Ws[kk][tj + 16 * bb];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 4; ++bb) {
+          acc[a][bb].x = fmaf(sv[a], wv[bb].x, acc[a][bb].x);
+          acc[a][bb].y = fmaf(sv[a], wv[bb].y, acc[a][bb].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int64_t q = q0 + tq + 16 * a;
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) {
+      const int j = j0 + tj + 16 * bb;
+      if (q < C && j < M) theta[q * M + j] = acc[a][bb];
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------------------
@@ -209,6 +273,14 @@ cudaError_t launch_theta_tanh(const RbmDev& R, const int8_t* spins, int64_t n, f
   if (n <= 0) return cudaSuccess;
   unsigned grid = (unsigned)((n + kWarps - 1) / kWarps);
   VMC_DISPATCH_MPL(R.M, k_theta_tanh<MPL><<<grid, 32 * kWarps, spin_smem(R.N), st>>>(R, spins, n, T));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_theta_gemm(const RbmDev& R, const int8_t* spins, int64_t C, float2* theta,
+                              cudaStream_t st) {
+  if (C <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((C + TG_Q - 1) / TG_Q), (unsigned)((R.M + TG_J - 1) / TG_J));
+  k_theta_gemm<<<grid, 256, 0, st>>>(R.b, R.Wt, R.N, R.M, spins, C, theta);
   return cudaGetLastError();
 }
 

@@ -206,7 +206,19 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
   __syncwarp();
 
   float2 t[MPL];
-  warp_resync<MPL>(R, s, lane, t, false);
+  if (A.theta_in) {
+#pragma unroll
+    for (int k = 0; k < MPL; ++k) {
+      const int hj = lane + 32 * k;
+      t[k] = make_float2(0.f, 0.f);
+      if (hj < M) {
+        const float2 th = A.theta_in[(int64_t)chain * M + hj];
+        t[k] = tanh_c(th.x, th.y);
+      }
+    }
+  } else {
+    warp_resync<MPL>(R, s, lane, t, false);
+  }
 
   const uint32_t K = HEIS ? (uint32_t)L.nb : (uint32_t)N;
   const int total = A.n_therm + A.n_samples * A.sweeps_per_sample;

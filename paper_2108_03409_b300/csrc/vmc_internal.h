@@ -40,6 +40,8 @@ struct SampleArgs {
   float2* logpsi_out;             // [n_samples*C] or null
   float2* eloc_out;               // [n_samples*C] or null
   float2* t_out;                  // [n_samples*C][M] or null
+  const float2* theta_in;         // [C][M] theta of the chains' current spins, or null
+                                  // (then the kernel forms theta = b + W s itself)
   unsigned long long* n_accept;
   unsigned* status;
 };
@@ -55,6 +57,11 @@ cudaError_t launch_logpsi(const RbmDev& R, const int8_t* spins, int64_t n, float
 cudaError_t launch_eloc(const RbmDev& R, const LatDev& L, const int8_t* spins, int64_t n,
                         float2* out, unsigned* status, cudaStream_t st);
 cudaError_t launch_theta_tanh(const RbmDev& R, const int8_t* spins, int64_t n, float2* T,
+                              cudaStream_t st);
+// theta[c][j] = b_j + sum_i W_ji s_ci for C configurations, as a tiled FP32 product with,
+// per entry, the same fused multiply-adds in the same order (i = 0 .. N-1 from b_j) as the
+// sampler's own per-chain formation, so the results are bit-identical to it
+cudaError_t launch_theta_gemm(const RbmDev& R, const int8_t* spins, int64_t C, float2* theta,
                               cudaStream_t st);
 cudaError_t launch_ok_dense(const int8_t* spins, const float2* T, int64_t n, int N, int M,
                             float2* O, cudaStream_t st);
@@ -213,11 +220,13 @@ struct CgProblem {
   unsigned* status;
 };
 constexpr int CG_VPART_DOUBLES = 2560;
+constexpr int CG_T2_BLOCKS = 256;
 struct CgWork {
   double2 *r, *p, *q, *y, *z;         // [P]
   double* D;                          // [P] shift diagonal
   double* Minv;                       // [P] inverse diagonal of S~ (preconditioner)
   double* t2;                         // [M]
+  double* t2part;                     // [CG_T2_BLOCKS][M] partial sums of |t|^2
   float2 *va, *vb, *V;                // FP32 copies of the CG direction (vb: M + 128, the
                                       // tensor-core product copies 64-unit blocks)
   float2* u;                          // [n padded to 256] (the OhU kernel copies 64-sample blocks)
