@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ 
 static cudaError_t apply_s_tc(const CgProblem& pb, CgWork& w, const double2* p, double2* q,
                               cudaStream_t st, int64_t* launches) {
   const int N = pb.N, M = pb.M;
-  const int64_t n = pb.n, P = (int64_t)N + M + (int64_t)N * M;
+  const int64_t n = pb.n;
   const CgTcShape sh = cg_tc_shape(N, M, n);
   if (!sh.ok || sh.v_rows * sh.kN > w.cap_v ||
       (int64_t)sh.kchunks * sh.mtiles * 128 * sh.nbt * 128 > w.cap_part2 ||
