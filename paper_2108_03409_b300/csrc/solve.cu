@@ -807,15 +807,21 @@ __device__ __forceinline__ bool cta_wait(const unsigned* word, unsigned target,
 }
 
 // this CTA's 32 entries [32 s, 32 s + 32) of y = T^(op) v for the 256 x 256 block T
-// (T[m][t]; CONJ: conj(T)); v in shared memory; result to out (L2)
+// (T[m][t]; CONJ: conj(T)); v in shared memory; result to out (L2).  The block's entries
+// are loaded first (slice_load, before the waits: T is read-only during the solve).
+template <typename C>
+__device__ __forceinline__ void slice_load(const C* __restrict__ T, int s, C (&w)[32]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = TS * s + lane;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) w[j] = __ldg(&T[(int64_t)(32 * warp + j) * SB + t]);
+}
+
 template <typename C, bool CONJ>
-__device__ __forceinline__ void slice_matvec(const C* __restrict__ T, const C* vv, int s, int kw,
+__device__ __forceinline__ void slice_matvec(const C (&w)[32], const C* vv, int s, int kw,
                                              C* out, C* red) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int t = TS * s + lane;
-  C w[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) w[j] = __ldg(&T[(int64_t)(32 * warp + j) * SB + t]);
   C acc = mk<C>(0.0, 0.0);
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
@@ -857,11 +863,13 @@ __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
     for (int s = 0; s < SPB; ++s) {
       const int q = k * SPB + s;
       if (q % G != me) continue;
+      C w[32];
+      slice_load<C>(Tf + (int64_t)k * SB * SB, s, w);
       for (int s2 = 0; s2 < SPB && k0 + (int64_t)s2 * TS < P; ++s2)
         if (!cta_wait(&cnt[k * SPB + s2], (unsigned)k, abort_word, status)) return;
       vv[tid] = (tid < kw) ? __ldcg(&b[k0 + tid]) : mk<C>(0.0, 0.0);
       __syncthreads();
-      slice_matvec<C, false>(Tf + (int64_t)k * SB * SB, vv, s, kw, y + k0, red);
+      slice_matvec<C, false>(w, vv, s, kw, y + k0, red);
       if (tid == 0) atomicAdd(&flags[k], 1u);
     }
     // 2. owners of later slices: b_rows -= L[rows][block k] y_k
@@ -871,13 +879,8 @@ __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
       if (j <= k) continue;
       const int64_t r0 = (int64_t)j * SB + (int64_t)s * TS;
       if (r0 >= P) continue;
-      if (!have_y) {
-        if (!cta_wait(&flags[k], (unsigned)SPB, abort_word, status)) return;
-        yk[tid] = (tid < kw) ? __ldcg(&y[k0 + tid]) : mk<C>(0.0, 0.0);
-        __syncthreads();
-        have_y = true;
-      }
-      // four rows per warp, lanes over the 256 columns (8 each)
+      // four rows per warp, lanes over the 256 columns (8 each); L and the slice's own
+      // rows of b (written only by this CTA) are loaded before the wait for y_k
       C v[4][8];
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr)
@@ -889,6 +892,12 @@ __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
         }
       C cur = mk<C>(0.0, 0.0);
       if (lane < 4 && r0 + warp * 4 + lane < P) cur = __ldcg(&b[r0 + warp * 4 + lane]);
+      if (!have_y) {
+        if (!cta_wait(&flags[k], (unsigned)SPB, abort_word, status)) return;
+        yk[tid] = (tid < kw) ? __ldcg(&y[k0 + tid]) : mk<C>(0.0, 0.0);
+        __syncthreads();
+        have_y = true;
+      }
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         C sacc = mk<C>(0.0, 0.0);
@@ -936,11 +945,13 @@ __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
     for (int s = 0; s < SPB; ++s) {
       const int q = k * SPB + s;
       if (q % G != me) continue;
+      C w[32];
+      slice_load<C>(Tb + (int64_t)k * SB * SB, s, w);
       for (int s2 = 0; s2 < SPB && k0 + (int64_t)s2 * TS < P; ++s2)
         if (!cta_wait(&cnt[k * SPB + s2], need, abort_word, status)) return;
       vv[tid] = (tid < kw) ? __ldcg(&c[k0 + tid]) : mk<C>(0.0, 0.0);
       __syncthreads();
-      slice_matvec<C, true>(Tb + (int64_t)k * SB * SB, vv, s, kw, x + k0, red);
+      slice_matvec<C, true>(w, vv, s, kw, x + k0, red);
       if (tid == 0) atomicAdd(&flags[k], 1u);
     }
     // owners of earlier slices: c_rows -= L[block k][rows]^H x_k; lanes over the 32 rows,
@@ -950,20 +961,20 @@ __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
       const int j = q / SPB, s = q % SPB;
       if (j >= k) continue;
       const int64_t r0 = (int64_t)j * SB + (int64_t)s * TS;
-      if (!have_x) {
-        if (!cta_wait(&flags[k], (unsigned)SPB, abort_word, status)) return;
-        xk[tid] = (tid < kw) ? __ldcg(&x[k0 + tid]) : mk<C>(0.0, 0.0);
-        __syncthreads();
-        have_x = true;
-      }
       const int64_t r = r0 + lane;                 // r < k0 <= P
-      C v[32];
+      C v[32];                                     // loaded before the wait for x_k
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) {
         const int m = warp * 32 + jj;
         v[jj] = (m < kw) ? A[(k0 + m) * P + r] : mk<C>(0.0, 0.0);
       }
       const C cur = (warp == 0) ? __ldcg(&c[r]) : mk<C>(0.0, 0.0);
+      if (!have_x) {
+        if (!cta_wait(&flags[k], (unsigned)SPB, abort_word, status)) return;
+        xk[tid] = (tid < kw) ? __ldcg(&x[k0 + tid]) : mk<C>(0.0, 0.0);
+        __syncthreads();
+        have_x = true;
+      }
       C sacc = mk<C>(0.0, 0.0);
 #pragma unroll
       for (int jj = 0; jj < 32; ++jj) cfmac(sacc, xk[warp * 32 + jj], v[jj]);
