@@ -534,21 +534,153 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, un
   return ok != 0;
 }
 
+// Bounded waits on a counter in global memory: iteration and clock limits; an expired wait
+// sets DEV_ERR_TIMEOUT and the abort word, which every other wait also checks.
+__device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned target,
+                                              unsigned* abort_word, unsigned* status) {
+  volatile const unsigned* vw = word;
+  volatile unsigned* vab = abort_word;
+  const long long t0 = clock64();
+  unsigned it = 0;
+  while (*vw < target) {
+    if (*vab) return false;
+    if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
+      atomicExch(abort_word, 1u);
+      flag_error(status, DEV_ERR_TIMEOUT);
+      return false;
+    }
+  }
+  return true;
+}
+
+// CTA-wide: thread 0 waits, the verdict is shared; a fence makes the awaited data visible.
+// Barriers on both sides keep the shared verdict from being overwritten by the next call
+// before every thread has read it.
+__device__ __forceinline__ bool cta_wait(const unsigned* word, unsigned target,
+                                         unsigned* abort_word, unsigned* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = wait_at_least(word, target, abort_word, status) ? 1 : 0;
+    __threadfence();
+  }
+  __syncthreads();
+  const bool r = ok != 0;
+  __syncthreads();
+  return r;
+}
+
 // ---------------------------------------------------------------------------------------
 // Factorisation of one 512-wide panel (columns p0 .. pend, all rows below) in a single
 // cooperative launch.  Per 64-column block k (k1 = the next block):
-//   * CTA 0 solves the row block k1 against the block inverse, counts it done, updates the
-//     diagonal tile (k1, k1) and factors it (look-ahead: the critical path is one row block,
-//     one tile and one diagonal factorisation);
+//   * the chain CTAs 0..3 solve the row block k1 against the block inverse in 16-row slabs,
+//     count them done, wait (bounded) for all four, update their 16-row slabs of the
+//     diagonal tile (k1, k1) and count again; CTA 0 waits for the four and factors the
+//     tile (look-ahead: the critical path is one slab solve, one slab update and one
+//     diagonal factorisation);
 //   * the other CTAs solve the remaining row blocks, count them done, wait (bounded) until
 //     every row block of step k is solved, and apply block k's update to the rest of the
 //     panel (all trapezoid tiles but the diagonal one);
 //   * one grid barrier ends the step.
+// With fewer than 8 CTAs, CTA 0 alone does the chain's work on whole 64-row blocks.
 // The panel's first diagonal block is factored before the loop.  sync: the grid barrier
-// (3 words) followed by one counter per step, zeroed before the launch.
+// (3 words, then a spare), then per step the row-block counter, the slab-solve counter and
+// the slab-update counter, zeroed before the launch.
 // ---------------------------------------------------------------------------------------
+// 16 rows r0 .. r0 + 15 of X = B L_kk^{-H} (as trsm_body); thread (row ry, columns tx + 16 b)
+__device__ void trsm_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw,
+                          const float2* __restrict__ Dinv, int64_t r0, unsigned char* sm) {
+  float2* Bt = reinterpret_cast<float2*>(sm);    // [NB (m)][17 (row)]
+  float2* Lt = Bt + NB * 17;                     // [NB (m)][NB + 1 (c)]
+  const int tid = threadIdx.x;
+  {
+    float2 bv[4], lv[16];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, rr = e / NB, m = e % NB;
+      const int64_t row = r0 + rr;
+      bv[u] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) lv[u] = __ldcg(&Dinv[tid + 256 * u]);   // e = c * NB + m
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + 256 * u, rr = e / NB, m = e % NB;
+      Bt[m * 17 + rr] = bv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * u, c = e / NB, m = e % NB;
+      Lt[m * (NB + 1) + c] = lv[u];
+    }
+  }
+  __syncthreads();
+  const int ry = tid >> 4, tx = tid & 15;
+  float2 acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int m = 0; m < kw; ++m) {
+    const float2 br = Bt[m * 17 + ry];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cfmac(acc[q], br, Lt[m * (NB + 1) + tx + 16 * q]);
+  }
+  const int64_t row = r0 + ry;
+  if (row < P)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = tx + 16 * q;
+      if (c < kw) A[row * P + k0 + c] = acc[q];
+    }
+}
+
+// Rows k1 + 16 sl .. + 15 of the diagonal tile (k1, k1), lower part:
+// A[r][c] -= sum_m X[r][m] conj(X[c][m]) for c <= r (as herk_tile_body), X = A[.][k0 .. k0+kw)
+__device__ void herk_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw, int64_t k1,
+                          int sl, unsigned char* sm) {
+  float2* Xc = reinterpret_cast<float2*>(sm);    // [NB (m)][NB + 1 (tile row)]
+  const int tid = threadIdx.x;
+  const int nr = 16 * sl + 16;                   // tile rows 0 .. nr - 1 are needed
+  const int ry = tid >> 4, tx = tid & 15;
+  const int64_t r = k1 + 16 * sl + ry;
+  float2 cur[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t c = k1 + tx + 16 * q;
+    cur[q] = (q <= sl && r < P && c <= r) ? __ldcg(&A[r * P + c]) : make_float2(0.f, 0.f);
+  }
+  for (int e = tid; e < nr * NB; e += 256) {
+    const int rr = e / NB, m = e % NB;
+    const int64_t row = k1 + rr;
+    Xc[m * (NB + 1) + rr] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 acc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int m = 0; m < kw; ++m) {
+    const float2 xr = Xc[m * (NB + 1) + 16 * sl + ry];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (q <= sl) cfmac(acc[q], xr, Xc[m * (NB + 1) + tx + 16 * q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int64_t c = k1 + tx + 16 * q;
+    if (q <= sl && r < P && c <= r) {
+      float2 v = cur[q];
+      v.x -= acc[q].x;
+      v.y -= acc[q].y;
+      A[r * P + c] = v;
+    }
+  }
+}
+
 constexpr size_t PANEL_SMEM = (size_t)(3 * NB * (NB + 1) + 5 * NB) * sizeof(float2);
 constexpr int PANEL_MAX_STEPS = 32;                // 64-column blocks per panel (>= NBO / 64)
+// grid barrier + spare, then three counters per step; the context allocates at least 128
+// words for the solve's sync buffer
+constexpr int PANEL_SYNC_WORDS = 4 + 3 * PANEL_MAX_STEPS;
+static_assert(PANEL_SYNC_WORDS <= 128, "panel sync words");
 
 __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int64_t P,
                                                     int64_t p0, int64_t pend,
@@ -556,7 +688,10 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
                                                     GridBarrier* bar, unsigned* status) {
   extern __shared__ unsigned char csm[];
   const unsigned G = gridDim.x, b = blockIdx.x;
+  const unsigned NC = (G >= 8) ? 4u : 1u;        // chain CTAs
   unsigned* done = reinterpret_cast<unsigned*>(bar) + 4;
+  unsigned* xdone = done + PANEL_MAX_STEPS;
+  unsigned* hdone = xdone + PANEL_MAX_STEPS;
   if (b == 0) potrf_body<float2>(A, P, p0, (int)min((int64_t)NB, P - p0), Dinv + (p0 / NB) * NB * NB, status, csm);
   if (!grid_sync(bar, G, status)) return;
   int step = 0;
@@ -567,7 +702,25 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
     const float2* Di = Dinv + (k0 / NB) * NB * NB;
     const int64_t nrb = (rest + NB - 1) / NB;
     const bool last = k1 >= pend;                  // no update inside the panel after this
-    if (b == 0) {
+    if (b < NC && NC > 1) {
+      trsm_slab(A, P, k0, kw, Di, k1 + 16 * (int64_t)b, csm);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        atomicAdd(&done[step], 1u);
+        atomicAdd(&xdone[step], 1u);
+      }
+      if (last) break;
+      if (!cta_wait(&xdone[step], NC, &bar->abort, status)) return;
+      herk_slab(A, P, k0, kw, k1, (int)b, csm);
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) atomicAdd(&hdone[step], 1u);
+      if (b == 0) {
+        if (!cta_wait(&hdone[step], NC, &bar->abort, status)) return;
+        potrf_body<float2>(A, P, k1, (int)min((int64_t)NB, P - k1), Dinv + (k1 / NB) * NB * NB, status, csm);
+      }
+    } else if (b == 0) {
       trsm_body<float2>(A, P, k0, kw, Di, k1, csm);
       __syncthreads();
       if (G == 1)
@@ -592,9 +745,11 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
         }
       }
       potrf_body<float2>(A, P, k1, (int)min((int64_t)NB, P - k1), Dinv + (k1 / NB) * NB * NB, status, csm);
-    } else {
+    } else if (b >= NC) {
+      // row blocks 1 .. nrb-1 and trapezoid tiles 1 .. over the CTAs NC .. G-1
+      const unsigned W = G - NC, me = b - NC;
       unsigned mine = 0;
-      for (int64_t rb = b; rb < nrb; rb += G - 1) {
+      for (int64_t rb = 1 + me; rb < nrb; rb += W) {
         trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm);
         __syncthreads();
         ++mine;
@@ -603,34 +758,11 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0 && mine) atomicAdd(&done[step], mine);
-      // every row block of this step solved (CTA 0's included) before the panel update
-      {
-        __shared__ int ok;
-        if (threadIdx.x == 0) {
-          ok = 1;
-          volatile unsigned* vd = &done[step];
-          volatile unsigned* vab = &bar->abort;
-          const long long t0 = clock64();
-          unsigned it = 0;
-          while (*vd < (unsigned)nrb) {
-            if (*vab) { ok = 0; break; }
-            if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
-              atomicExch(&bar->abort, 1u);
-              flag_error(status, DEV_ERR_TIMEOUT);
-              ok = 0;
-              break;
-            }
-          }
-          __threadfence();
-        }
-        __syncthreads();
-        const bool go = ok != 0;
-        __syncthreads();
-        if (!go) return;
-      }
+      // every row block of this step solved (the chain CTAs' slabs count one each)
+      if (!cta_wait(&done[step], (unsigned)(nrb - 1) + NC, &bar->abort, status)) return;
       const int64_t nt = nrb, nct = (pend - k1 + NB - 1) / NB;
       const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
-      for (int64_t t = b; t < tiles; t += G - 1) {
+      for (int64_t t = 1 + me; t < tiles; t += W) {
         int64_t tm, tn;
         trapezoid_tile(t, nt, &tm, &tn);
         herk_tile_body<float2>(A, P, k0, kw, k1 + tm * NB, k1 + tn * NB, csm);
@@ -771,40 +903,6 @@ __global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t
 // ---------------------------------------------------------------------------------------
 constexpr int TS = 32;                          // slice rows
 constexpr int SPB = SB / TS;                    // slices per 256-row block
-
-__device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned target,
-                                              unsigned* abort_word, unsigned* status) {
-  volatile const unsigned* vw = word;
-  volatile unsigned* vab = abort_word;
-  const long long t0 = clock64();
-  unsigned it = 0;
-  while (*vw < target) {
-    if (*vab) return false;
-    if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
-      atomicExch(abort_word, 1u);
-      flag_error(status, DEV_ERR_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-
-// CTA-wide: thread 0 waits, the verdict is shared; a fence makes the awaited data visible.
-// Barriers on both sides keep the shared verdict from being overwritten by the next call
-// before every thread has read it.
-__device__ __forceinline__ bool cta_wait(const unsigned* word, unsigned target,
-                                         unsigned* abort_word, unsigned* status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = wait_at_least(word, target, abort_word, status) ? 1 : 0;
-    __threadfence();
-  }
-  __syncthreads();
-  const bool r = ok != 0;
-  __syncthreads();
-  return r;
-}
 
 // this CTA's 32 entries [32 s, 32 s + 32) of y = T^(op) v for the 256 x 256 block T
 // (T[m][t]; CONJ: conj(T)); v in shared memory; result to out (L2).  The block's entries
@@ -1315,7 +1413,7 @@ static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, u
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(w.bar);
   for (int64_t p0 = 0; p0 < P; p0 += NBO) {
     const int64_t pend = std::min<int64_t>(P, p0 + NBO);
-    VMC_TRY(cudaMemsetAsync(bar, 0, (4 + PANEL_MAX_STEPS) * sizeof(unsigned), st));
+    VMC_TRY(cudaMemsetAsync(bar, 0, PANEL_SYNC_WORDS * sizeof(unsigned), st));
     void* args[] = {(void*)&A, (void*)&P, (void*)&p0, (void*)&pend, (void*)&Dinv, (void*)&bar,
                     (void*)&status};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3(grid), dim3(256), args,
