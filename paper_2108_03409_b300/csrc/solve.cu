@@ -904,6 +904,19 @@ __global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t
 constexpr int TS = 32;                          // slice rows
 constexpr int SPB = SB / TS;                    // slices per 256-row block
 
+// CTA-wide wait until words[0 .. n) all reach target: thread i < n polls words[i], so the
+// n waits overlap; the verdicts are combined by the barrier.
+__device__ __forceinline__ bool cta_wait_n(const unsigned* words, int n, unsigned target,
+                                           unsigned* abort_word, unsigned* status) {
+  __syncthreads();
+  bool ok = true;
+  if ((int)threadIdx.x < n) {
+    ok = wait_at_least(&words[threadIdx.x], target, abort_word, status);
+    __threadfence();
+  }
+  return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
 // this CTA's 32 entries [32 s, 32 s + 32) of y = T^(op) v for the 256 x 256 block T
 // (T[m][t]; CONJ: conj(T)); v in shared memory; result to out (L2).  The block's entries
 // are loaded first (slice_load, before the waits: T is read-only during the solve).
@@ -963,8 +976,9 @@ __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
       if (q % G != me) continue;
       C w[32];
       slice_load<C>(Tf + (int64_t)k * SB * SB, s, w);
-      for (int s2 = 0; s2 < SPB && k0 + (int64_t)s2 * TS < P; ++s2)
-        if (!cta_wait(&cnt[k * SPB + s2], (unsigned)k, abort_word, status)) return;
+      if (!cta_wait_n(&cnt[k * SPB], min(SPB, (kw + TS - 1) / TS), (unsigned)k,
+                      abort_word, status))
+        return;
       vv[tid] = (tid < kw) ? __ldcg(&b[k0 + tid]) : mk<C>(0.0, 0.0);
       __syncthreads();
       slice_matvec<C, false>(w, vv, s, kw, y + k0, red);
@@ -1045,8 +1059,9 @@ __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
       if (q % G != me) continue;
       C w[32];
       slice_load<C>(Tb + (int64_t)k * SB * SB, s, w);
-      for (int s2 = 0; s2 < SPB && k0 + (int64_t)s2 * TS < P; ++s2)
-        if (!cta_wait(&cnt[k * SPB + s2], need, abort_word, status)) return;
+      if (!cta_wait_n(&cnt[k * SPB], min(SPB, (kw + TS - 1) / TS), need,
+                      abort_word, status))
+        return;
       vv[tid] = (tid < kw) ? __ldcg(&c[k0 + tid]) : mk<C>(0.0, 0.0);
       __syncthreads();
       slice_matvec<C, true>(w, vv, s, kw, x + k0, red);
