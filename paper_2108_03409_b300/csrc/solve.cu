@@ -888,32 +888,66 @@ __global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t
 // ---------------------------------------------------------------------------------------
 // Triangular solves as a dataflow over 32-row slices, one cooperative launch each.  The
 // right-hand side is cut into slices (j, s) = rows 256 j + 32 s .. + 31 of 256-row block j;
-// each slice has a fixed owner CTA (slice index mod grid) and a counter of the block
-// updates applied to it.  Forward step k (L y = b):
-//   * the owners of block k's eight slices wait until every slice of block k has received
-//     its k updates, then each computes its 32 entries of y_k = Linv_kk b_k (Linv_kk from
-//     the precomputed 256 x 256 inverses), stores them and counts into flag[k];
-//   * the owner of every slice of a later block waits for flag[k] = 8, subtracts
-//     L[rows][block k] y_k from its rows and increments the slice's counter.
+// each slice has a fixed owner CTA (slice index mod grid), which applies all of the
+// slice's block updates in order.  Forward step k (L y = b):
+//   * the owners of block k's eight slices read the block's final right-hand side, each
+//     computes its 32 entries of y_k = Linv_kk b_k (Linv_kk from the precomputed 256 x 256
+//     inverses) and stores them;
+//   * the owner of every slice of a later block subtracts L[rows][block k] y_k from its
+//     rows; the last of these updates (block k + 1) goes to the final buffer.
 // The backward solve (L^H x = y) runs the same scheme from the last block to the first with
-// x_k = Linv_kk^H c_k and the rows above.  There is no grid-wide barrier: a step's
-// critical path is the eight-CTA product and one flag.  Every wait is bounded (iteration
-// and clock limits); an expired wait sets DEV_ERR_TIMEOUT and the abort word, which every
-// other wait also checks.  Right-hand sides go through L2 only (ld/st.global.cg).
+// x_k = Linv_kk^H c_k and the rows above.  The data are their own flags: the solution and
+// the final buffer are filled with an all-ones bit pattern (a NaN that arithmetic does not
+// produce) before the launch, every entry is written once, and a reader polls the entries
+// it needs until no component holds the pattern.  There is no counter, flag or fence on
+// the critical path, which is the eight-CTA product and two polled reads per block.  Every
+// wait is bounded (iteration and clock limits); an expired wait sets DEV_ERR_TIMEOUT and
+// the abort word, which every other wait also checks.  Right-hand sides go through L2
+// only (ld/st.global.cg, volatile polls).
 // ---------------------------------------------------------------------------------------
 constexpr int TS = 32;                          // slice rows
 constexpr int SPB = SB / TS;                    // slices per 256-row block
 
-// CTA-wide wait until words[0 .. n) all reach target: thread i < n polls words[i], so the
-// n waits overlap; the verdicts are combined by the barrier.
-__device__ __forceinline__ bool cta_wait_n(const unsigned* words, int n, unsigned target,
-                                           unsigned* abort_word, unsigned* status) {
-  __syncthreads();
-  bool ok = true;
-  if ((int)threadIdx.x < n) {
-    ok = wait_at_least(&words[threadIdx.x], target, abort_word, status);
-    __threadfence();
+// One component word of a right-hand-side entry; all ones marks "not written yet".
+template <typename C> struct WordOf;
+template <> struct WordOf<float2> { typedef unsigned T; };
+template <> struct WordOf<double2> { typedef unsigned long long T; };
+
+// Wait (bounded) until both components of *p are written, and return the entry.
+template <typename C>
+__device__ __forceinline__ bool poll_entry(const C* p, C* out, unsigned* abort_word,
+                                           unsigned* status) {
+  typedef typename WordOf<C>::T W;
+  const W NONE = ~(W)0;
+  volatile const W* w = reinterpret_cast<volatile const W*>(p);
+  volatile unsigned* vab = abort_word;
+  const long long t0 = clock64();
+  unsigned it = 0;
+  for (;;) {
+    const W x = w[0], y = w[1];
+    if (x != NONE && y != NONE) {
+      W* o = reinterpret_cast<W*>(out);
+      o[0] = x;
+      o[1] = y;
+      return true;
+    }
+    if (*vab) return false;
+    if ((++it & 255u) == 0 && clock64() - t0 > 2000000000ll) {
+      atomicExch(abort_word, 1u);
+      flag_error(status, DEV_ERR_TIMEOUT);
+      return false;
+    }
   }
+}
+
+// dst[t] = src[t] for t < n, waiting for each entry; CTA-wide verdict
+template <typename C>
+__device__ __forceinline__ bool cta_poll_block(const C* src, C* dst, int n, unsigned* abort_word,
+                                               unsigned* status) {
+  bool ok = true;
+  const int t = threadIdx.x;
+  if (t < n) ok = poll_entry<C>(&src[t], &dst[t], abort_word, status);
+  else if (t < SB) dst[t] = mk<C>(0.0, 0.0);
   return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
@@ -947,16 +981,17 @@ __device__ __forceinline__ void slice_matvec(const C (&w)[32], const C* vv, int 
     for (int q = 1; q < 8; ++q) { tot.x += red[q * 32 + lane].x; tot.y += red[q * 32 + lane].y; }
     if (t < kw) __stcg(&out[t], tot);
   }
-  __threadfence();
   __syncthreads();
 }
 
-// bar: [0] abort word; flags[nsb]; counters[nsb * SPB]
+// sync: [0] abort word.  y (and fin) hold the all-ones pattern at launch; fin receives the
+// final right-hand side of every block after the first.
 template <typename C>
 __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
                                                   const C* __restrict__ Tf, int64_t P,
                                                   C* __restrict__ b, C* __restrict__ y,
-                                                  unsigned* sync, unsigned* status) {
+                                                  C* __restrict__ fin, unsigned* sync,
+                                                  unsigned* status) {
   __shared__ C vv[SB];
   __shared__ C red[SB];
   __shared__ C yk[SB];
@@ -964,8 +999,6 @@ __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
   const int nsb = (int)((P + SB - 1) / SB);
   const int G = gridDim.x, me = blockIdx.x;
   unsigned* abort_word = sync;
-  unsigned* flags = sync + 1;
-  unsigned* cnt = flags + nsb;
   const int nslices = nsb * SPB;
   for (int k = 0; k < nsb; ++k) {
     const int64_t k0 = (int64_t)k * SB;
@@ -976,13 +1009,13 @@ __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
       if (q % G != me) continue;
       C w[32];
       slice_load<C>(Tf + (int64_t)k * SB * SB, s, w);
-      if (!cta_wait_n(&cnt[k * SPB], min(SPB, (kw + TS - 1) / TS), (unsigned)k,
-                      abort_word, status))
+      if (k == 0) {
+        vv[tid] = (tid < kw) ? __ldcg(&b[tid]) : mk<C>(0.0, 0.0);
+        __syncthreads();
+      } else if (!cta_poll_block<C>(fin + k0, vv, kw, abort_word, status)) {
         return;
-      vv[tid] = (tid < kw) ? __ldcg(&b[k0 + tid]) : mk<C>(0.0, 0.0);
-      __syncthreads();
+      }
       slice_matvec<C, false>(w, vv, s, kw, y + k0, red);
-      if (tid == 0) atomicAdd(&flags[k], 1u);
     }
     // 2. owners of later slices: b_rows -= L[rows][block k] y_k
     bool have_y = false;
@@ -1005,11 +1038,10 @@ __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
       C cur = mk<C>(0.0, 0.0);
       if (lane < 4 && r0 + warp * 4 + lane < P) cur = __ldcg(&b[r0 + warp * 4 + lane]);
       if (!have_y) {
-        if (!cta_wait(&flags[k], (unsigned)SPB, abort_word, status)) return;
-        yk[tid] = (tid < kw) ? __ldcg(&y[k0 + tid]) : mk<C>(0.0, 0.0);
-        __syncthreads();
+        if (!cta_poll_block<C>(y + k0, yk, kw, abort_word, status)) return;
         have_y = true;
       }
+      C* dst = (j == k + 1) ? fin : b;             // block k+1's last update is final
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         C sacc = mk<C>(0.0, 0.0);
@@ -1024,22 +1056,22 @@ __global__ void __launch_bounds__(256) k_fwd_coop(const C* __restrict__ A,
           C t = cur;
           t.x -= sacc.x;
           t.y -= sacc.y;
-          __stcg(&b[row], t);
+          __stcg(&dst[row], t);
         }
       }
-      __threadfence();
-      __syncthreads();
-      if (tid == 0) atomicAdd(&cnt[q], 1u);
     }
     if (have_y) __syncthreads();                   // yk is rewritten at the next step
   }
 }
 
+// sync: [0] abort word.  x (and fin) hold the all-ones pattern at launch; fin receives the
+// final right-hand side of every block before the last.
 template <typename C>
 __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
                                                   const C* __restrict__ Tb, int64_t P,
                                                   C* __restrict__ c, C* __restrict__ x,
-                                                  unsigned* sync, unsigned* status) {
+                                                  C* __restrict__ fin, unsigned* sync,
+                                                  unsigned* status) {
   __shared__ C vv[SB];
   __shared__ C red[SB];
   __shared__ C xk[SB];
@@ -1047,25 +1079,22 @@ __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
   const int nsb = (int)((P + SB - 1) / SB);
   const int G = gridDim.x, me = blockIdx.x;
   unsigned* abort_word = sync;
-  unsigned* flags = sync + 1;
-  unsigned* cnt = flags + nsb;
   const int nslices = nsb * SPB;
   for (int k = nsb - 1; k >= 0; --k) {
     const int64_t k0 = (int64_t)k * SB;
     const int kw = (int)min((int64_t)SB, P - k0);
-    const unsigned need = (unsigned)(nsb - 1 - k);
     for (int s = 0; s < SPB; ++s) {
       const int q = k * SPB + s;
       if (q % G != me) continue;
       C w[32];
       slice_load<C>(Tb + (int64_t)k * SB * SB, s, w);
-      if (!cta_wait_n(&cnt[k * SPB], min(SPB, (kw + TS - 1) / TS), need,
-                      abort_word, status))
+      if (k == nsb - 1) {
+        vv[tid] = (tid < kw) ? __ldcg(&c[k0 + tid]) : mk<C>(0.0, 0.0);
+        __syncthreads();
+      } else if (!cta_poll_block<C>(fin + k0, vv, kw, abort_word, status)) {
         return;
-      vv[tid] = (tid < kw) ? __ldcg(&c[k0 + tid]) : mk<C>(0.0, 0.0);
-      __syncthreads();
+      }
       slice_matvec<C, true>(w, vv, s, kw, x + k0, red);
-      if (tid == 0) atomicAdd(&flags[k], 1u);
     }
     // owners of earlier slices: c_rows -= L[block k][rows]^H x_k; lanes over the 32 rows,
     // warp w over the columns [32 w, 32 w + 32) of block k, shared-memory reduction
@@ -1083,9 +1112,7 @@ __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
       }
       const C cur = (warp == 0) ? __ldcg(&c[r]) : mk<C>(0.0, 0.0);
       if (!have_x) {
-        if (!cta_wait(&flags[k], (unsigned)SPB, abort_word, status)) return;
-        xk[tid] = (tid < kw) ? __ldcg(&x[k0 + tid]) : mk<C>(0.0, 0.0);
-        __syncthreads();
+        if (!cta_poll_block<C>(x + k0, xk, kw, abort_word, status)) return;
         have_x = true;
       }
       C sacc = mk<C>(0.0, 0.0);
@@ -1100,11 +1127,9 @@ __global__ void __launch_bounds__(256) k_bwd_coop(const C* __restrict__ A,
         C t = cur;
         t.x -= tot.x;
         t.y -= tot.y;
-        __stcg(&c[r], t);
+        __stcg((j == k - 1) ? &fin[r] : &c[r], t);  // block k-1's last update is final
       }
-      __threadfence();
       __syncthreads();
-      if (tid == 0) atomicAdd(&cnt[q], 1u);
     }
     if (have_x) __syncthreads();
   }
@@ -1492,21 +1517,25 @@ static cudaError_t chol_solve(const C* A, const C* Dinv_unused, int64_t P, C* b,
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     grid = sms * per_sm;
   }
-  // w.bar: abort word, one flag per 256-row block, one counter per 32-row slice
+  // w.bar[0]: abort word; outputs and the final buffer start as the all-ones pattern
   unsigned* sync = w.bar;
-  const int64_t nsb = (P + SB - 1) / SB;
-  const size_t sync_bytes = (1 + nsb + nsb * SPB) * sizeof(unsigned);
-  VMC_TRY(cudaMemsetAsync(sync, 0, sync_bytes, st));
+  C* fin = reinterpret_cast<C*>(w.fin);
+  const size_t vbytes = (size_t)P * sizeof(C);
+  VMC_TRY(cudaMemsetAsync(sync, 0, sizeof(unsigned), st));
+  VMC_TRY(cudaMemsetAsync(y, 0xff, vbytes, st));
+  VMC_TRY(cudaMemsetAsync(fin, 0xff, vbytes, st));
   {
-    void* args[] = {(void*)&A, (void*)&Dinv, (void*)&P, (void*)&b, (void*)&y, (void*)&sync,
-                    (void*)&status};
+    void* args[] = {(void*)&A, (void*)&Dinv, (void*)&P, (void*)&b, (void*)&y, (void*)&fin,
+                    (void*)&sync, (void*)&status};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_fwd_coop<C>, dim3(grid), dim3(256), args, 0, st));
   }
-  VMC_TRY(cudaMemsetAsync(sync, 0, sync_bytes, st));
+  VMC_TRY(cudaMemsetAsync(sync, 0, sizeof(unsigned), st));
+  VMC_TRY(cudaMemsetAsync(x, 0xff, vbytes, st));
+  VMC_TRY(cudaMemsetAsync(fin, 0xff, vbytes, st));
   {
     const C* Dinvb = inv_bwd<C>(w);
-    void* args[] = {(void*)&A, (void*)&Dinvb, (void*)&P, (void*)&y, (void*)&x, (void*)&sync,
-                    (void*)&status};
+    void* args[] = {(void*)&A, (void*)&Dinvb, (void*)&P, (void*)&y, (void*)&x, (void*)&fin,
+                    (void*)&sync, (void*)&status};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_bwd_coop<C>, dim3(grid), dim3(256), args, 0, st));
   }
   *launches += 2;
