@@ -68,10 +68,9 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
 //    takes the pivot from its diagonal lane by a shuffle, scales and publishes the column
 //    (double-buffered), one barrier, then every later column of the panel applies its
 //    rank-1 update.  After the panel the trailing triangle gets one rank-16 update.
-//  * Inverse: the four 16 x 16 diagonal blocks are inverted at once (one 64-thread group
-//    each, named barriers) as products of I - N, I + N^2, I + N^4, I + N^8 with N the
-//    nilpotent strictly lower part scaled by the pivots, then the off-diagonal 16-blocks by
-//    levels, X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj (D_i = diagonal inverse).
+//  * Inverse: the four 16 x 16 diagonal blocks are inverted at once (forward substitution
+//    on the identity, one 64-thread group each, named barriers), then the off-diagonal
+//    16-blocks by levels, X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj (D_i = diagonal inverse).
 constexpr int POTRF_THREADS = 256;
 constexpr int PLD = NB + 1;
 
@@ -243,78 +242,46 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
   }
   if (bad) flag_error(status, DEV_ERR_NUMERIC);
   // ---- inverse: 16 x 16 diagonal blocks, one 64-thread group each ----
-  // L_gg = D (I + N) with D its diagonal and N = D^-1 (L_gg - D) strictly lower, so N^16 = 0
-  // and (I + N)^-1 = (I - N)(I + N^2)(I + N^4)(I + N^8): five passes of 16 x 16 products
-  // (thread (rr, cq) forms row rr, columns cq + 4j) with a group barrier after each, then
-  // L_gg^-1 = (I + N)^-1 D^-1.  Work in tt + cb (four padded 16 x 17 buffers per group).
   {
     const int g = tid >> 6, gt = tid & 63, rr = gt >> 2, cq = gt & 3;
     const int b0 = 16 * g;
-    constexpr int QL = 17, QS = 16 * QL;
-    C* B0 = tt + g * 4 * QS;                       // N, later Y2
-    C* B1 = B0 + QS;                               // N^2, later N^8
-    C* B2 = B1 + QS;                               // N^4
-    C* B3 = B2 + QS;                               // Y1
-    auto gbar = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory"); };
-    // row rr of X (.) Y for the columns cq + 4j
-    auto prod = [&](const C* X, const C* Y, C (&o)[4]) {
+    C x[4];
 #pragma unroll
-      for (int j2 = 0; j2 < 4; ++j2) o[j2] = mk<C>(0.0, 0.0);
+    for (int j = 0; j < 4; ++j) x[j] = mk<C>((cq + 4 * j == rr) ? 1.0 : 0.0, 0.0);
+    C* rb = cb;                                    // group g uses entries [16g, 16g + 16)
+    int q2 = 0;
+    for (int m = 0; m < 16; ++m) {
+      if (rr == m) {
+        const R il = dg[b0 + m];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const C xv = X[rr * QL + k];
-#pragma unroll
-        for (int j2 = 0; j2 < 4; ++j2) cfma(o[j2], xv, Y[k * QL + cq + 4 * j2]);
+        for (int j = 0; j < 4; ++j) {
+          const int c = cq + 4 * j;
+          if (c <= m) {
+            x[j].x *= il;
+            x[j].y *= il;
+            rb[q2 * NB + b0 + c] = x[j];
+          }
+        }
       }
-    };
-    {
-      const R il = dg[b0 + rr];
+      asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory");
+      if (rr > m) {
+        const C lrm = a[(b0 + rr) * PLD + b0 + m];
 #pragma unroll
-      for (int j2 = 0; j2 < 4; ++j2) {
-        const int c = cq + 4 * j2;
-        const C l = a[(b0 + rr) * PLD + b0 + c];
-        B0[rr * QL + c] = (c < rr) ? mk<C>((double)(l.x * il), (double)(l.y * il)) : mk<C>(0.0, 0.0);
+        for (int j = 0; j < 4; ++j) {
+          const int c = cq + 4 * j;
+          if (c <= m) {
+            const C xm = rb[q2 * NB + b0 + c];
+            x[j].x -= lrm.x * xm.x - lrm.y * xm.y;      // x -= L[rr][m] Linv[m][c]
+            x[j].y -= lrm.x * xm.y + lrm.y * xm.x;
+          }
+        }
       }
+      q2 ^= 1;
     }
-    gbar();
-    C o[4], o2[4];
-    prod(B0, B0, o);                               // N^2
 #pragma unroll
-    for (int j2 = 0; j2 < 4; ++j2) B1[rr * QL + cq + 4 * j2] = o[j2];
-    gbar();
-    prod(B1, B1, o);                               // N^4
-    prod(B0, B1, o2);                              // N^3
-#pragma unroll
-    for (int j2 = 0; j2 < 4; ++j2) {
-      const int c = cq + 4 * j2;
-      const C n1 = B0[rr * QL + c], n2 = B1[rr * QL + c];
-      C y;                                         // Y1 = I - N + N^2 - N^3
-      y.x = ((c == rr) ? (R)1 : (R)0) - n1.x + n2.x - o2[j2].x;
-      y.y = -n1.y + n2.y - o2[j2].y;
-      B2[rr * QL + c] = o[j2];
-      B3[rr * QL + c] = y;
-    }
-    gbar();
-    prod(B2, B2, o);                               // N^8
-    prod(B3, B2, o2);                              // Y1 N^4
-#pragma unroll
-    for (int j2 = 0; j2 < 4; ++j2) {
-      const int c = cq + 4 * j2;
-      const C y1 = B3[rr * QL + c];
-      B1[rr * QL + c] = o[j2];
-      B0[rr * QL + c] = mk<C>((double)(y1.x + o2[j2].x), (double)(y1.y + o2[j2].y));   // Y2
-    }
-    gbar();
-    prod(B0, B1, o);                               // Y2 N^8
-#pragma unroll
-    for (int j2 = 0; j2 < 4; ++j2) {
-      const int c = cq + 4 * j2;
-      if (c <= rr) {
-        const C y2 = B0[rr * QL + c];
-        const R il = dg[b0 + c];
-        li[(b0 + rr) * PLD + b0 + c] =
-            mk<C>((double)((y2.x + o[j2].x) * il), (double)((y2.y + o[j2].y) * il));
-      }
+    for (int j = 0; j < 4; ++j) {
+      const int c = cq + 4 * j;
+      if (c <= rr) li[(b0 + rr) * PLD + b0 + c] = x[j];
     }
   }
   __syncthreads();
