@@ -261,10 +261,11 @@ vmc_status vmc_set_state(vmc_ctx* ctx, const void* buf, size_t len);
 
 /* Failure-path self-test (no GPU fault): which = 0 runs the cooperative kernels' bounded
  * flag wait on a word that nothing sets, which = 1 the tensor-core kernels' bounded mbarrier
- * wait on a barrier that nothing arrives at.  Each gives up after about 2e9 SM clock cycles
- * (about a second), records the expiry in the context's status word and returns: the call
- * returns VMC_ERR_TIMEOUT (the designed outcome) and the context stays usable.  Allocates a
- * two-word scratch; synchronises. */
+ * wait on a barrier that nothing arrives at, which = 2 the triangular solves' bounded poll
+ * on a right-hand-side entry that nothing writes.  Each gives up after about 2e9 SM clock
+ * cycles (about a second), records the expiry in the context's status word and returns:
+ * the call returns VMC_ERR_TIMEOUT (the designed outcome) and the context stays usable.
+ * Any other which: VMC_ERR_ARG.  Allocates a four-word scratch; synchronises. */
 vmc_status vmc_selftest_wait_timeout(vmc_ctx* ctx, int which);
 
 /* Number of kernel launches the library has issued on this context since it was created

@@ -1210,11 +1210,12 @@ vmc_status vmc_set_state(vmc_ctx* ctx, const void* buf, size_t len) {
 }
 
 vmc_status vmc_selftest_wait_timeout(vmc_ctx* ctx, int which) {
-  if (!ctx || which < 0 || which > 1) return VMC_ERR_ARG;
+  if (!ctx || which < 0 || which > 2) return VMC_ERR_ARG;
   unsigned* word = nullptr;
-  CK(cudaMalloc(&word, 2 * sizeof(unsigned)), "selftest");
-  cudaError_t e = which == 0 ? launch_selftest_flag_wait(word, ctx->status, ctx->st)
-                             : launch_selftest_mbar_wait(ctx->status, ctx->st);
+  CK(cudaMalloc(&word, 4 * sizeof(unsigned)), "selftest");
+  cudaError_t e = which == 0   ? launch_selftest_flag_wait(word, ctx->status, ctx->st)
+                  : which == 1 ? launch_selftest_mbar_wait(ctx->status, ctx->st)
+                               : launch_selftest_poll_wait(word, ctx->status, ctx->st);
   ++ctx->launches;
   vmc_status s = (e == cudaSuccess) ? check_status(ctx, "selftest") : cuda_fail(ctx, e, "selftest");
   cudaFree(word);

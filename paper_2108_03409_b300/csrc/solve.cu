@@ -1381,6 +1381,23 @@ cudaError_t launch_selftest_flag_wait(unsigned* word2, unsigned* status, cudaStr
   return cudaGetLastError();
 }
 
+// ... and the triangular solves' bounded poll on an entry that nothing writes (word4[0..1]
+// hold the all-ones pattern, word4[2] is the abort word).
+__global__ void k_selftest_poll_wait(unsigned* word4, unsigned* status) {
+  if (threadIdx.x == 0) {
+    float2 v;
+    poll_entry<float2>(reinterpret_cast<const float2*>(word4), &v, word4 + 2, status);
+  }
+}
+
+cudaError_t launch_selftest_poll_wait(unsigned* word4, unsigned* status, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(word4, 0xff, 2 * sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(word4 + 2, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  k_selftest_poll_wait<<<1, 32, 0, st>>>(word4, status);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------------------

@@ -209,6 +209,7 @@ cudaError_t launch_cg_ohu_tc(const __nv_bfloat16* Bs, const CgTcShape& sh, const
 // failure-path self-tests of the bounded waits (a flag / an mbarrier that nothing sets)
 cudaError_t launch_selftest_flag_wait(unsigned* word2, unsigned* status, cudaStream_t st);
 cudaError_t launch_selftest_mbar_wait(unsigned* status, cudaStream_t st);
+cudaError_t launch_selftest_poll_wait(unsigned* word4, unsigned* status, cudaStream_t st);
 
 // ---- cg.cu ----------------------------------------------------------------------------
 struct CgProblem {

@@ -74,11 +74,12 @@ def test_state_of_another_configuration_is_rejected():
             vmc.vmc_destroy(ctx)
 
 
-@pytest.mark.parametrize("which", [0, 1], ids=["flag", "mbarrier"])
+@pytest.mark.parametrize("which", [0, 1, 2], ids=["flag", "mbarrier", "entry"])
 def test_bounded_wait_reports_timeout_and_context_survives(which):
-    """The bounded waits of the cooperative kernels (flag) and of the tensor-core kernels
-    (mbarrier) give up on a condition that never comes true, the call reports
-    VMC_ERR_TIMEOUT, and the context keeps working afterwards."""
+    """The bounded waits of the cooperative kernels (flag), of the tensor-core kernels
+    (mbarrier) and of the triangular solves (an entry that is never written) give up on a
+    condition that never comes true, the call reports VMC_ERR_TIMEOUT, and the context keeps
+    working afterwards."""
     N, M = 10, 10
     ctx = vmc.vmc_init(vmc.make_config(n_chains=64, solver=vmc.SOLVER_CG),
                        [vmc.make_lattice(T, N, 1, 1.0, 1.0, 1)])
