@@ -63,11 +63,12 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
 
 // Factor the 64 x 64 diagonal block (rows/cols k0..k0+kw) and store its inverse; one CTA
 // of 256 threads, the block in shared memory (identity padding beyond kw, masked on output).
-//  * Factorisation in four 16-column panels.  Within a panel thread (col, rg) keeps rows
-//    c0 + rg + 16i of panel column col in registers; step c: the half-warp owning column c
-//    takes the pivot from its diagonal lane by a shuffle, scales and publishes the column
-//    (double-buffered), one barrier, then every later column of the panel applies its
-//    rank-1 update.  After the panel the trailing triangle gets one rank-16 update.
+//  * Factorisation in four 16-column panels.  Within a panel warp w keeps the columns
+//    c0 + 2w, c0 + 2w + 1 in registers, lane l rows c0 + l and c0 + l + 32 of both; per
+//    column pair the owner warp resolves the 2x2 pivot block (two pivot shuffles and one
+//    for L[c+1][c]; every lane scales and updates its own rows), publishes both columns
+//    (double-buffered), one barrier, then the later warps apply the rank-2 update.  After
+//    the panel the trailing triangle gets one rank-16 update.
 //  * Inverse: the four 16 x 16 diagonal blocks are inverted at once (forward substitution
 //    on the identity, one 64-thread group each, named barriers), then the off-diagonal
 //    16-blocks by levels, X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj (D_i = diagonal inverse).
@@ -117,106 +118,100 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
   }
   __syncthreads();
   bool bad = false;
-  const int col = tid >> 4, rg = tid & 15;
+  const int warp = tid >> 5, lane = tid & 31;
   int pb = 0;
   for (int pp = 0; pp < 4; ++pp) {
     const int c0 = 16 * pp;
-    C e[4];
+    // warp w owns the panel columns c0 + 2w + q (q = 0, 1); lane l the rows c0 + l + 32h
+    C e[2][2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = c0 + rg + 16 * i;
-      e[i] = (r < NB) ? a[r * PLD + c0 + col] : mk<C>(0.0, 0.0);
-    }
-    // columns in pairs (c, c+1): both owner half-warps are in warp cl/2, which resolves the
-    // 2x2 pivot block by shuffles; one barrier, then a rank-2 update of the later columns
-    for (int cl = 0; cl < 16; cl += 2) {
-      const int c = c0 + cl;
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int r = c0 + lane + 32 * h;
+        e[h][q] = (r < NB) ? a[r * PLD + c0 + 2 * warp + q] : mk<C>(0.0, 0.0);
+      }
+    // column pairs (c, c+1) = (c0 + 2w, c0 + 2w + 1): the owner warp resolves the 2x2 pivot
+    // block (each lane scales its own rows of column c and updates its own rows of column
+    // c+1; three shuffles), publishes both columns, one barrier, then the later warps apply
+    // the rank-2 update to their columns
+    for (int w = 0; w < 8; ++w) {
+      const int c = c0 + 2 * w;
       C* cbA = cb + pb * 2 * NB;                     // column c
       C* cbB = cbA + NB;                             // column c + 1
-      if ((tid >> 5) == (cl >> 1)) {
-        const int lane = tid & 31;
-        R d0 = __shfl_sync(0xffffffffu, e[0].x, cl);            // (c, c): half 0, rg = cl
-        if (!(d0 > (R)0) || !isfinite(d0)) { bad |= (col == cl); d0 = (R)1; }
+      if (warp == w) {
+        R d0 = __shfl_sync(0xffffffffu, e[0][0].x, 2 * w);      // (c, c): row c0 + 2w
+        if (!(d0 > (R)0) || !isfinite(d0)) { bad |= (lane == 0); d0 = (R)1; }
         R l0, il0;
         pivot_root(d0, &l0, &il0);
-        if (col == cl) {
-          if (rg == cl) dg[c] = il0;
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int r = c0 + rg + 16 * i;
-            if (r > c && r < NB) {
-              e[i].x *= il0;
-              e[i].y *= il0;
-            } else if (r == c) {
-              e[i] = mk<C>((double)l0, 0.0);
-            }
+        for (int h = 0; h < 2; ++h) {
+          const int r = c0 + lane + 32 * h;
+          if (r > c) {
+            e[h][0].x *= il0;
+            e[h][0].y *= il0;
+          } else if (r == c) {
+            e[h][0] = mk<C>((double)l0, 0.0);
           }
         }
-        // column c+1: subtract L[r][c] conj(L[c+1][c]) (L[r][c] from the partner lane)
-        C lcol[4];
+        C lw;                                                    // L[c+1][c]
+        lw.x = __shfl_sync(0xffffffffu, e[0][0].x, 2 * w + 1);
+        lw.y = __shfl_sync(0xffffffffu, e[0][0].y, 2 * w + 1);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          lcol[i].x = __shfl_sync(0xffffffffu, e[i].x, lane & 15);
-          lcol[i].y = __shfl_sync(0xffffffffu, e[i].y, lane & 15);
-        }
-        const R wr = __shfl_sync(0xffffffffu, e[0].x, cl + 1);  // L[c+1][c]: half 0, rg = cl+1
-        const R wi = __shfl_sync(0xffffffffu, e[0].y, cl + 1);
-        if (col == cl + 1) {
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int r = c0 + rg + 16 * i;
-            if (r > c && r < NB) {
-              e[i].x -= lcol[i].x * wr + lcol[i].y * wi;
-              e[i].y -= lcol[i].y * wr - lcol[i].x * wi;
-            }
+        for (int h = 0; h < 2; ++h) {
+          const int r = c0 + lane + 32 * h;
+          if (r > c) {
+            e[h][1].x -= e[h][0].x * lw.x + e[h][0].y * lw.y;
+            e[h][1].y -= e[h][0].y * lw.x - e[h][0].x * lw.y;
           }
         }
-        R d1 = __shfl_sync(0xffffffffu, e[0].x, 16 + cl + 1);   // (c+1, c+1): half 1
-        if (!(d1 > (R)0) || !isfinite(d1)) { bad |= (col == cl + 1); d1 = (R)1; }
+        R d1 = __shfl_sync(0xffffffffu, e[0][1].x, 2 * w + 1);  // (c+1, c+1)
+        if (!(d1 > (R)0) || !isfinite(d1)) { bad |= (lane == 0); d1 = (R)1; }
         R l1, il1;
         pivot_root(d1, &l1, &il1);
-        if (col == cl + 1) {
-          if (rg == cl + 1) dg[c + 1] = il1;
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int r = c0 + rg + 16 * i;
-            if (r > c + 1 && r < NB) {
-              e[i].x *= il1;
-              e[i].y *= il1;
-              cbB[r] = e[i];
-            } else if (r == c + 1) {
-              e[i] = mk<C>((double)l1, 0.0);
-            }
-          }
+        if (lane == 0) {
+          dg[c] = il0;
+          dg[c + 1] = il1;
         }
-        if (col == cl) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int r = c0 + rg + 16 * i;
-            if (r > c && r < NB) cbA[r] = e[i];
+        for (int h = 0; h < 2; ++h) {
+          const int r = c0 + lane + 32 * h;
+          if (r > c + 1 && r < NB) {
+            e[h][1].x *= il1;
+            e[h][1].y *= il1;
+            cbB[r] = e[h][1];
+          } else if (r == c + 1) {
+            e[h][1] = mk<C>((double)l1, 0.0);
           }
+          if (r > c && r < NB) cbA[r] = e[h][0];
         }
       }
       __syncthreads();
-      if (col > cl + 1) {
-        const C la = cbA[c0 + col], lb = cbB[c0 + col];         // L[c0+col][c], [c+1]
+      if (warp > w) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int r = c0 + rg + 16 * i;
-          if (r >= c0 + col && r < NB) {
-            const C ra = cbA[r], rb = cbB[r];
-            e[i].x -= ra.x * la.x + ra.y * la.y + rb.x * lb.x + rb.y * lb.y;
-            e[i].y -= ra.y * la.x - ra.x * la.y + rb.y * lb.x - rb.x * lb.y;
+        for (int q = 0; q < 2; ++q) {
+          const int cc = c0 + 2 * warp + q;
+          const C la = cbA[cc], lb = cbB[cc];                    // L[cc][c], L[cc][c+1]
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = c0 + lane + 32 * h;
+            if (r >= cc && r < NB) {
+              const C ra = cbA[r], rb = cbB[r];
+              e[h][q].x -= ra.x * la.x + ra.y * la.y + rb.x * lb.x + rb.y * lb.y;
+              e[h][q].y -= ra.y * la.x - ra.x * la.y + rb.y * lb.x - rb.x * lb.y;
+            }
           }
         }
       }
       pb ^= 1;
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int r = c0 + rg + 16 * i;
-      if (r < NB) a[r * PLD + c0 + col] = e[i];
-    }
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int r = c0 + lane + 32 * h;
+        if (r < NB) a[r * PLD + c0 + 2 * warp + q] = e[h][q];
+      }
     __syncthreads();
     if (pp < 3) {
       // trailing rank-16 update of rows/cols >= c0 + 16 (lower triangle)
