@@ -70,8 +70,8 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
 //    (double-buffered), one barrier, then the later warps apply the rank-2 update.  After
 //    the panel the trailing triangle gets one rank-16 update.
 //  * Inverse: the four 16 x 16 diagonal blocks are inverted at once (forward substitution
-//    on the identity, one 64-thread group each, named barriers), then the off-diagonal
-//    16-blocks by levels, X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj (D_i = diagonal inverse).
+//    on the identity, one warp each, a column per lane), then the off-diagonal 16-blocks by
+//    levels, X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj (D_i = diagonal inverse).
 constexpr int POTRF_THREADS = 256;
 constexpr int PLD = NB + 1;
 
@@ -236,73 +236,81 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
     }
   }
   if (bad) flag_error(status, DEV_ERR_NUMERIC);
-  // ---- inverse: 16 x 16 diagonal blocks, one 64-thread group each ----
-  {
-    const int g = tid >> 6, gt = tid & 63, rr = gt >> 2, cq = gt & 3;
-    const int b0 = 16 * g;
-    C x[4];
+  // ---- inverse: 16 x 16 diagonal blocks, one warp each; lane (j, h) forms column j of
+  // the block's inverse by forward substitution (both row halves form the whole column,
+  // each stores its own rows); no barrier ----
+  if (warp < 4) {
+    const int b0 = 16 * warp, j = lane & 15, h = lane >> 4;
+    C x[16];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) x[j] = mk<C>((cq + 4 * j == rr) ? 1.0 : 0.0, 0.0);
-    C* rb = cb;                                    // group g uses entries [16g, 16g + 16)
-    int q2 = 0;
-    for (int m = 0; m < 16; ++m) {
-      if (rr == m) {
-        const R il = dg[b0 + m];
+    for (int m = 0; m < 16; ++m) x[m] = mk<C>((m == j) ? 1.0 : 0.0, 0.0);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = cq + 4 * j;
-          if (c <= m) {
-            x[j].x *= il;
-            x[j].y *= il;
-            rb[q2 * NB + b0 + c] = x[j];
-          }
-        }
+    for (int k = 0; k < 16; ++k) {
+      const R il = dg[b0 + k];
+      x[k].x *= il;
+      x[k].y *= il;
+#pragma unroll
+      for (int m = k + 1; m < 16; ++m) {
+        const C lmk = a[(b0 + m) * PLD + b0 + k];
+        x[m].x -= lmk.x * x[k].x - lmk.y * x[k].y;
+        x[m].y -= lmk.x * x[k].y + lmk.y * x[k].x;
       }
-      asm volatile("bar.sync %0, 64;" ::"r"(1 + g) : "memory");
-      if (rr > m) {
-        const C lrm = a[(b0 + rr) * PLD + b0 + m];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int c = cq + 4 * j;
-          if (c <= m) {
-            const C xm = rb[q2 * NB + b0 + c];
-            x[j].x -= lrm.x * xm.x - lrm.y * xm.y;      // x -= L[rr][m] Linv[m][c]
-            x[j].y -= lrm.x * xm.y + lrm.y * xm.x;
-          }
-        }
-      }
-      q2 ^= 1;
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = cq + 4 * j;
-      if (c <= rr) li[(b0 + rr) * PLD + b0 + c] = x[j];
-    }
+    for (int m = 0; m < 16; ++m)
+      if ((m >> 3) == h && m >= j) li[(b0 + m) * PLD + b0 + j] = x[m];
   }
   __syncthreads();
-  // ---- off-diagonal 16-blocks by levels d = i - j ----
+  // ---- off-diagonal 16-blocks by levels d = i - j (each thread holds 4 - d entries of a
+  // level; the levels and entry counts are compile-time, so a thread's entries interleave) ----
+#pragma unroll
   for (int d = 1; d < 4; ++d) {
+    constexpr int kMaxNb = 3;
     const int nb = 4 - d;                          // blocks (j + d, j), j < nb
     // T_ij = sum_{k=j}^{i-1} L_ik X_kj, into tt at block (i, j)
-    for (int e = tid; e < nb * 256; e += POTRF_THREADS) {
-      const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
-      C acc = mk<C>(0.0, 0.0);
-      for (int k = j; k < i; ++k)
+    C acc[kMaxNb];
 #pragma unroll
-        for (int m = 0; m < 16; ++m)
-          cfma(acc, a[(16 * i + r) * PLD + 16 * k + m], li[(16 * k + m) * PLD + 16 * j + c]);
-      tt[(16 * i + r) * PLD + 16 * j + c] = acc;
+    for (int u = 0; u < kMaxNb; ++u) {
+      acc[u] = mk<C>(0.0, 0.0);
+      if (u < nb) {
+        const int e = tid + POTRF_THREADS * u;
+        const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
+#pragma unroll
+        for (int k2 = 0; k2 < d; ++k2) {
+          const int k = j + k2;
+#pragma unroll
+          for (int m = 0; m < 16; ++m)
+            cfma(acc[u], a[(16 * i + r) * PLD + 16 * k + m], li[(16 * k + m) * PLD + 16 * j + c]);
+        }
+      }
     }
+#pragma unroll
+    for (int u = 0; u < kMaxNb; ++u)
+      if (u < nb) {
+        const int e = tid + POTRF_THREADS * u;
+        const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
+        tt[(16 * i + r) * PLD + 16 * j + c] = acc[u];
+      }
     __syncthreads();
     // X_ij = -D_i T_ij
-    for (int e = tid; e < nb * 256; e += POTRF_THREADS) {
-      const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
-      C acc = mk<C>(0.0, 0.0);
 #pragma unroll
-      for (int m = 0; m < 16; ++m)
-        cfma(acc, li[(16 * i + r) * PLD + 16 * i + m], tt[(16 * i + m) * PLD + 16 * j + c]);
-      li[(16 * i + r) * PLD + 16 * j + c] = mk<C>(-(double)acc.x, -(double)acc.y);
+    for (int u = 0; u < kMaxNb; ++u) {
+      acc[u] = mk<C>(0.0, 0.0);
+      if (u < nb) {
+        const int e = tid + POTRF_THREADS * u;
+        const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
+#pragma unroll
+        for (int m = 0; m < 16; ++m)
+          cfma(acc[u], li[(16 * i + r) * PLD + 16 * i + m], tt[(16 * i + m) * PLD + 16 * j + c]);
+      }
     }
+#pragma unroll
+    for (int u = 0; u < kMaxNb; ++u)
+      if (u < nb) {
+        const int e = tid + POTRF_THREADS * u;
+        const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
+        li[(16 * i + r) * PLD + 16 * j + c] = mk<C>(-(double)acc[u].x, -(double)acc[u].y);
+      }
     __syncthreads();
   }
   for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
