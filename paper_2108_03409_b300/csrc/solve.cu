@@ -785,9 +785,10 @@ constexpr int SB = 256;
 // Inverse of each 256 x 256 diagonal block of L, assembled from the inverses D_i of its
 // four 64 x 64 diagonal blocks (left by the factorisation) by block forward substitution:
 //   X_jj = D_j,   X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj   (i > j, 64 x 64 blocks),
-// one CTA per 256-block doing its 64 x 64 complex products in shared memory (4 x 4
-// register tiles).  Stored twice: Tb[r][c] = Linv[r][c] (backward solve) and
-// Tf[c][r] = Linv[r][c] (forward solve), both [nsb][SB][SB].
+// one CTA per (256-block, 64-column block) doing the column's 64 x 64 complex products in
+// shared memory (4 x 4 register tiles): the block columns of an inverse are independent.
+// Stored twice: Tb[r][c] = Linv[r][c] (backward solve) and Tf[c][r] = Linv[r][c] (forward
+// solve), both [nsb][SB][SB].
 template <typename C>
 __device__ void tile_load(C* sm_t, const C* __restrict__ g, int64_t ld, int rows, int cols,
                           bool transpose) {
@@ -807,22 +808,23 @@ __global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t
   extern __shared__ unsigned char ism[];
   C* At = reinterpret_cast<C*>(ism);          // left operand, transposed: At[m][r]
   C* Bs = At + NB * (NB + 1);                 // right operand: Bs[m][c]
-  const int sb = blockIdx.x;
+  const int sb = blockIdx.x, j = blockIdx.y;      // 256-block, and its 64-column block j
   const int64_t k0 = (int64_t)sb * SB;
   const int kw = (int)min((int64_t)SB, P - k0);
   const int nblk = (kw + NB - 1) / NB;
   C* tb = Tb + (int64_t)sb * SB * SB;
   C* tf = Tf + (int64_t)sb * SB * SB;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  // diagonal blocks and zeros elsewhere
-  for (int e = tid; e < SB * SB; e += 256) {
-    const int r = e / SB, c = e % SB, i = r / NB, j = c / NB;
-    tb[e] = (i == j && i < nblk) ? Dinv[((int64_t)(k0 / NB) + i) * NB * NB + (r % NB) * NB + (c % NB)]
-                                 : mk<C>(0.0, 0.0);
+  // column block j: the diagonal block and zeros elsewhere
+  for (int e = tid; e < SB * NB; e += 256) {
+    const int r = e / NB, c = NB * j + e % NB, i = r / NB;
+    tb[(int64_t)r * SB + c] =
+        (i == j && i < nblk) ? Dinv[((int64_t)(k0 / NB) + i) * NB * NB + (r % NB) * NB + (c % NB)]
+                             : mk<C>(0.0, 0.0);
   }
   __syncthreads();
   auto rows_of = [&](int i) { return min(NB, kw - NB * i); };
-  for (int j = 0; j < nblk; ++j) {
+  if (j < nblk) {
     for (int i = j + 1; i < nblk; ++i) {
       C acc[4][4];
 #pragma unroll
@@ -882,9 +884,9 @@ __global__ void __launch_bounds__(256) k_inv_sb(const C* __restrict__ A, int64_t
       __syncthreads();
     }
   }
-  for (int e = tid; e < SB * SB; e += 256) {
-    const int r = e / SB, c = e % SB;
-    tf[(int64_t)c * SB + r] = tb[e];
+  for (int e = tid; e < SB * NB; e += 256) {
+    const int r = e % SB, c = NB * j + e / SB;
+    tf[(int64_t)c * SB + r] = tb[(int64_t)r * SB + c];
   }
 }
 
@@ -1514,7 +1516,7 @@ static cudaError_t invert_blocks(const C* A, int64_t P, SolveWork& w, cudaStream
                                  int64_t* launches) {
   const int64_t nsb = (P + SB - 1) / SB;
   const C* Dinv = dinv_of<C>(w);
-  k_inv_sb<C><<<(unsigned)nsb, 256, 2 * NB * (NB + 1) * sizeof(C), st>>>(A, P, Dinv, inv_fwd<C>(w),
+  k_inv_sb<C><<<dim3((unsigned)nsb, SB / NB), 256, 2 * NB * (NB + 1) * sizeof(C), st>>>(A, P, Dinv, inv_fwd<C>(w),
                                                                            inv_bwd<C>(w));
   ++*launches;
   return cudaGetLastError();
