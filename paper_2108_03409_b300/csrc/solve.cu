@@ -1327,8 +1327,9 @@ __global__ void __launch_bounds__(256) k_resid_df(const float4* __restrict__ S2,
   const int64_t row = blockIdx.x;
   const float4* srow = S2 + row * P;
   float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+#pragma unroll 4
   for (int64_t c = threadIdx.x; c < P; c += blockDim.x) {
-    const float4 a = srow[c];      // hi.re, hi.im, lo.re, lo.im
+    const float4 a = __ldcs(&srow[c]);   // hi.re, hi.im, lo.re, lo.im (streamed once)
     const float4 v = x2[c];
     const float p1 = a.x * v.x, e1 = fmaf(a.x, v.x, -p1);
     const float p2 = -(a.y * v.y), e2 = fmaf(-a.y, v.y, -p2);
