@@ -329,12 +329,37 @@ __global__ void __launch_bounds__(POTRF_THREADS) k_potrf_diag(C* __restrict__ A,
   potrf_body<C>(A, P, k0, kw, Dinv, status, psm);
 }
 
+// Where the row solves of a tensor-core panel also write their results: rows r0 .. r0+n-1
+// (the rows below the panel) become rows 2(row - r0) (real) and 2(row - r0) + 1 (imaginary)
+// of the BF16 hi/lo operand planes [rows_pad][K] of the panel's Schur update, column m.
+// hi == nullptr: no operand output.
+struct XOut {
+  __nv_bfloat16* hi;
+  __nv_bfloat16* lo;
+  int64_t r0, n;
+  int K, m0;                                     // m0: the panel column of the block's column 0
+};
+
+template <typename C>
+__device__ __forceinline__ void x_store(const XOut& xo, int64_t row, int c, C v) {}
+template <>
+__device__ __forceinline__ void x_store<float2>(const XOut& xo, int64_t row, int c, float2 v) {
+  if (xo.hi == nullptr || row < xo.r0 || row - xo.r0 >= xo.n) return;
+  const int64_t r = row - xo.r0, m = xo.m0 + c;
+  const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
+  xo.hi[(2 * r) * xo.K + m] = hr;
+  xo.hi[(2 * r + 1) * xo.K + m] = hi;
+  xo.lo[(2 * r) * xo.K + m] = __float2bfloat16_rn(v.x - __bfloat162float(hr));
+  xo.lo[(2 * r + 1) * xo.K + m] = __float2bfloat16_rn(v.y - __bfloat162float(hi));
+}
+
 // Panel: X = B L_kk^{-H}, X[r][c] = sum_m B[r][m] conj(Linv[c][m]) (Linv is zero above its
 // diagonal) for the rows below the diagonal block; 64 rows per block, written over the
 // panel of A.  Thread (ty, tx) accumulates the 4 x 4 outputs (ty + 16a, tx + 16b).
 template <typename C>
 __device__ void trsm_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
-                          const C* __restrict__ Dinv, int64_t r0, unsigned char* tsm) {
+                          const C* __restrict__ Dinv, int64_t r0, unsigned char* tsm,
+                          const XOut& xo = XOut{nullptr, nullptr, 0, 0, 0, 0}) {
   C* Bt = reinterpret_cast<C*>(tsm);           // [NB (m)][NB+1 (r)]
   C* Lt = Bt + NB * (NB + 1);                  // [NB (m)][NB+1 (c)]
   const int tid = threadIdx.x;
@@ -379,7 +404,10 @@ __device__ void trsm_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = tx + 16 * j;
-      if (row < P && c < kw) A[row * P + k0 + c] = acc[i][j];
+      if (row < P && c < kw) {
+        A[row * P + k0 + c] = acc[i][j];
+        x_store<C>(xo, row, c, acc[i][j]);
+      }
     }
   }
 }
@@ -592,7 +620,8 @@ __device__ __forceinline__ bool cta_wait(const unsigned* word, unsigned target,
 // ---------------------------------------------------------------------------------------
 // 16 rows r0 .. r0 + 15 of X = B L_kk^{-H} (as trsm_body); thread (row ry, columns tx + 16 b)
 __device__ void trsm_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw,
-                          const float2* __restrict__ Dinv, int64_t r0, unsigned char* sm) {
+                          const float2* __restrict__ Dinv, int64_t r0, unsigned char* sm,
+                          const XOut& xo) {
   float2* Bt = reinterpret_cast<float2*>(sm);    // [NB (m)][17 (row)]
   float2* Lt = Bt + NB * 17;                     // [NB (m)][NB + 1 (c)]
   const int tid = threadIdx.x;
@@ -632,7 +661,10 @@ __device__ void trsm_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw,
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int c = tx + 16 * q;
-      if (c < kw) A[row * P + k0 + c] = acc[q];
+      if (c < kw) {
+        A[row * P + k0 + c] = acc[q];
+        x_store<float2>(xo, row, c, acc[q]);
+      }
     }
 }
 
@@ -688,7 +720,8 @@ static_assert(PANEL_SYNC_WORDS <= 128, "panel sync words");
 __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int64_t P,
                                                     int64_t p0, int64_t pend,
                                                     float2* __restrict__ Dinv,
-                                                    GridBarrier* bar, unsigned* status) {
+                                                    GridBarrier* bar, unsigned* status,
+                                                    XOut xpanel) {
   extern __shared__ unsigned char csm[];
   const unsigned G = gridDim.x, b = blockIdx.x;
   const unsigned NC = (G >= 8) ? 4u : 1u;        // chain CTAs
@@ -705,8 +738,10 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
     const float2* Di = Dinv + (k0 / NB) * NB * NB;
     const int64_t nrb = (rest + NB - 1) / NB;
     const bool last = k1 >= pend;                  // no update inside the panel after this
+    XOut xo = xpanel;                              // this block's columns of the operand
+    xo.m0 = (int)(k0 - p0);
     if (b < NC && NC > 1) {
-      trsm_slab(A, P, k0, kw, Di, k1 + 16 * (int64_t)b, csm);
+      trsm_slab(A, P, k0, kw, Di, k1 + 16 * (int64_t)b, csm, xo);
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
@@ -724,11 +759,11 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
         potrf_body<float2>(A, P, k1, (int)min((int64_t)NB, P - k1), Dinv + (k1 / NB) * NB * NB, status, csm);
       }
     } else if (b == 0) {
-      trsm_body<float2>(A, P, k0, kw, Di, k1, csm);
+      trsm_body<float2>(A, P, k0, kw, Di, k1, csm, xo);
       __syncthreads();
       if (G == 1)
         for (int64_t rb = 1; rb < nrb; ++rb) {
-          trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm);
+          trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm, xo);
           __syncthreads();
         }
       if (last) break;
@@ -753,7 +788,7 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
       const unsigned W = G - NC, me = b - NC;
       unsigned mine = 0;
       for (int64_t rb = 1 + me; rb < nrb; rb += W) {
-        trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm);
+        trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm, xo);
         __syncthreads();
         ++mine;
       }
@@ -1237,26 +1272,6 @@ __global__ void k_update(double2* __restrict__ p, const double2* __restrict__ x,
   }
 }
 
-// Panel L[r0 + r][c0 + m] (0 <= r < n, 0 <= m < K) of the FP32 factor as real rows for the
-// tensor-core update: X[2r][m] = Re, X[2r+1][m] = Im, BF16 hi/lo pair, zero padded rows.
-__global__ void k_panel_to_x(const float2* __restrict__ A, int64_t P, int64_t r0, int64_t c0,
-                             int64_t n, int K, int64_t rows_pad, __nv_bfloat16* __restrict__ Xhi,
-                             __nv_bfloat16* __restrict__ Xlo) {
-  const int64_t total = (rows_pad / 2) * K;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / K;
-    const int m = (int)(e % K);
-    float2 v = make_float2(0.f, 0.f);
-    if (r < n) v = A[(r0 + r) * P + c0 + m];
-    const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
-    Xhi[(2 * r) * K + m] = hr;
-    Xhi[(2 * r + 1) * K + m] = hi;
-    Xlo[(2 * r) * K + m] = __float2bfloat16_rn(v.x - __bfloat162float(hr));
-    Xlo[(2 * r + 1) * K + m] = __float2bfloat16_rn(v.y - __bfloat162float(hi));
-  }
-}
-
 // ---------------------------------------------------------------------------------------
 // Residuals of the mixed solvers in compensated FP32 arithmetic.  S and x are held as
 // FP32 hi/lo pairs (S = S_hi + S_lo to ~2^-48); each row's sum of S_hi x_hi products is
@@ -1476,23 +1491,31 @@ static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, u
   GridBarrier* bar = reinterpret_cast<GridBarrier*>(w.bar);
   for (int64_t p0 = 0; p0 < P; p0 += NBO) {
     const int64_t pend = std::min<int64_t>(P, p0 + NBO);
+    // the rows below the panel go, as they are solved, into the BF16 hi/lo operand planes of
+    // the panel's Schur update (rows_pad rows; the padding rows are zeroed here)
+    const int64_t n = P - pend;
+    const int K = (int)(pend - p0);
+    const int64_t rows_pad = (2 * n + 127) / 128 * 128;
+    XOut xo{nullptr, nullptr, pend, n, K, 0};
+    if (n > 0) {
+      if (rows_pad * NBO > w.x_elems || K != NBO) return cudaErrorInvalidValue;
+      const size_t pad = (size_t)(rows_pad - 2 * n) * K * sizeof(__nv_bfloat16);
+      if (pad) {
+        VMC_TRY(cudaMemsetAsync(w.Xhi + 2 * n * K, 0, pad, st));
+        VMC_TRY(cudaMemsetAsync(w.Xlo + 2 * n * K, 0, pad, st));
+      }
+      xo.hi = w.Xhi;
+      xo.lo = w.Xlo;
+    }
     VMC_TRY(cudaMemsetAsync(bar, 0, PANEL_SYNC_WORDS * sizeof(unsigned), st));
-    void* args[] = {(void*)&A, (void*)&P, (void*)&p0, (void*)&pend, (void*)&Dinv, (void*)&bar,
-                    (void*)&status};
+    void* args[] = {(void*)&A,   (void*)&P,      (void*)&p0, (void*)&pend, (void*)&Dinv,
+                    (void*)&bar, (void*)&status, (void*)&xo};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3(grid), dim3(256), args,
                                         PANEL_SMEM, st));
     ++*launches;
-    const int64_t n = P - pend;
     if (n > 0) {
-      const int64_t rows_pad = (2 * n + 127) / 128 * 128;
-      if (rows_pad * NBO > w.x_elems) return cudaErrorInvalidValue;
-      const int K = (int)(pend - p0);
-      if (K != NBO) return cudaErrorInvalidValue;
-      const int64_t total = (rows_pad / 2) * K;
-      k_panel_to_x<<<grid_for(total, 256), 256, 0, st>>>(A, P, pend, p0, n, K, rows_pad, w.Xhi, w.Xlo);
-      VMC_TRY(cudaGetLastError());
       VMC_TRY(launch_herk_tc(w.Xhi, w.Xlo, rows_pad, K, n, A, P, pend, status, st));
-      *launches += 2;
+      ++*launches;
     }
   }
   return cudaSuccess;
