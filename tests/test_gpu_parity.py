@@ -266,8 +266,9 @@ def test_qfm_8x8_sampled_entries():
 
 @pytest.mark.parametrize("solver", [vmc.SOLVER_CHOLESKY_FP64, vmc.SOLVER_CHOLESKY_MIXED,
                                     vmc.SOLVER_CHOLESKY_TC])
-@pytest.mark.parametrize("shape", [(T, 10, 1, 1, 1e-4, 0), (H, 4, 4, 2, 1e-3, 0), (T, 6, 6, 1, 1e-2, 1)],
-                         ids=["P120", "P560", "P1332_additive"])
+@pytest.mark.parametrize("shape", [(T, 10, 1, 1, 1e-4, 0), (H, 4, 4, 2, 1e-3, 0), (T, 6, 6, 1, 1e-2, 1),
+                                   (T, 11, 1, 4, 1e-3, 0)],
+                         ids=["P120", "P560", "P1332_additive", "P539_odd"])
 def test_solve_matches_oracle(solver, shape):
     model, Lx, Ly, alpha, nu, mode = shape
     N, M = Lx * Ly, alpha * Lx * Ly
