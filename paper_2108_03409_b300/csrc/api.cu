@@ -401,7 +401,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &ctx->sw.r, P)) || (e = dalloc(ctx, &ctx->sw.c, P)) ||
         (e = dalloc(ctx, &ctx->sw.r32, P)) || (e = dalloc(ctx, &ctx->sw.y32, P)) ||
         (e = dalloc(ctx, &ctx->sw.c32, P)) || (e = dalloc(ctx, &ctx->sw.scal, 8)) ||
-        (e = dalloc(ctx, &ctx->sw.bar, 128 + 9 * (size_t)((P + 255) / 256))) ||
+        (e = dalloc(ctx, &ctx->sw.bar, 128)) ||
         (e = dalloc(ctx, &ctx->sw.fin, P)))
       return oom(e);
     // split-K Gram partials: up to 8M complex FP32 (64 MB), used only when P is small

@@ -146,7 +146,7 @@ struct SolveWork {
   float2* y32;     // [P]
   float2* c32;     // [P]
   double* scal;    // [8] device scalars
-  unsigned* bar;   // [128 + 9 ceil(P/256)] grid barrier / abort word / counters of the cooperative kernels
+  unsigned* bar;   // [128] the cooperative kernels' grid barrier, abort word and step counters
   double2* fin;    // [P] final right-hand sides of the triangular solves (float2 or double2 entries)
   float2 *T32f, *T32b;    // [ceil(P/256)][256][256] inverses of the 256-wide diagonal blocks
   double2 *T64f, *T64b;   //   (transposed for the forward solve; FP32 or FP64 solver)
