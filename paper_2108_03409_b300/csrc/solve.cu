@@ -1251,17 +1251,17 @@ __global__ void k_eq_scales(const float2* __restrict__ A, int64_t P, float* __re
   }
 }
 
+// one block per row r: the lower part c <= r, coalesced along the row
 __global__ void k_equilibrate(float2* __restrict__ A, int64_t P, const float* __restrict__ dsc) {
-  const int64_t total = P * P;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = e / P, c = e - r * P;
-    if (c > r) continue;
-    const float s = dsc[r] * dsc[c];
-    float2 v = A[e];
+  const int64_t r = blockIdx.x;
+  const float dr = dsc[r];
+  float2* row = A + r * P;
+  for (int64_t c = threadIdx.x; c <= r; c += blockDim.x) {
+    const float s = dr * dsc[c];
+    float2 v = row[c];
     v.x *= s;
     v.y *= s;
-    A[e] = v;
+    row[c] = v;
   }
 }
 
@@ -1640,7 +1640,7 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
                                  double* relres) {
   const int64_t P = w.P;
   k_eq_scales<<<grid_for(P, 256, 1024), 256, 0, st>>>(w.A32, P, w.dsc);
-  k_equilibrate<<<grid_for(P * P, 256), 256, 0, st>>>(w.A32, P, w.dsc);
+  k_equilibrate<<<(unsigned)P, 256, 0, st>>>(w.A32, P, w.dsc);
   *launches += 2;
   if (tc && P > NBO) VMC_TRY(factor_tc(w.A32, w.D32, P, w, status, st, launches));
   else VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
@@ -1663,7 +1663,7 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
     // is too slow, refactor in FP32 and keep refining from the current x.
     if (tc_factor && it >= 1 && rel > 0.25 * prev) {
       k_s2_to_a32<<<grid_for(P * P, 256), 256, 0, st>>>(w.S2, w.A32, P, nu, mode);
-      k_equilibrate<<<grid_for(P * P, 256), 256, 0, st>>>(w.A32, P, w.dsc);
+      k_equilibrate<<<(unsigned)P, 256, 0, st>>>(w.A32, P, w.dsc);
       *launches += 2;
       VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
       VMC_TRY(invert_blocks<float2>(w.A32, P, w, st, launches));
