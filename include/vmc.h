@@ -96,6 +96,7 @@ typedef struct {
   float ms_sample, ms_grad, ms_qfm, ms_solve, ms_update;  /* phase times (CUDA events)    */
   float ms_gram;                /* the S contraction kernel alone (CUDA events)             */
   int64_t launches;             /* kernels launched by this step                            */
+  int solver_converged;         /* 1 if the solve reached cg_tol (the update was applied)   */
 } vmc_sr_stats;
 
 typedef struct vmc_ctx vmc_ctx;
@@ -126,7 +127,8 @@ vmc_status vmc_set_chains(vmc_ctx* ctx, int lattice, const int8_t* spins_host);
 vmc_status vmc_get_chains(vmc_ctx* ctx, int lattice, int8_t* spins_host);
 
 /* log psi for a batch (Eq. rbm_ex; the __call__ of the NQS class).
- * spins: dev int8 [n][N]; logpsi: dev float [n][2].  n = 0 is a no-op. */
+ * spins: dev int8 [n][N]; logpsi: dev float [n][2].  n = 0 is a no-op.  The imaginary
+ * part (the phase) is returned reduced to [-pi, pi]; so is the sampler's logpsi_out. */
 vmc_status vmc_logpsi(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
                       float* logpsi);
 
@@ -179,7 +181,9 @@ vmc_status vmc_solve(vmc_ctx* ctx, int lattice, const double* S, const double* F
  * with Obar v and Obar^H u evaluated from the RBM structure (O = [s | t | t (x) s]), never
  * forming S.  x0 = 0; stops when ||r|| <= cg_tol ||F|| or after cg_maxit iterations.
  * F, x: dev double [P][2].  iters / relres (host, may be NULL) report the finish
- * (relres is the recursively updated residual).  Synchronises once per iteration. */
+ * (relres is the recursively updated residual).  Synchronises once per iteration.
+ * Returns VMC_ERR_NUMERIC if relres is still above cg_tol after cg_maxit iterations (x then
+ * holds the last iterate, iters and relres are filled). */
 vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
                         const double* F, double* x, int* iters, double* relres);
 
@@ -193,7 +197,9 @@ vmc_status vmc_sr_apply(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
 /* One full SR step (Algorithm 1, then the Euler update theta <- theta - dt x of
  * imaginary-time TDVP, Eq. stochastic_reconfiguration): sample Ns configurations, local
  * energies, log-derivatives, S and F, regularised solve, parameter update.  stats (host)
- * may be NULL.  Synchronises. */
+ * may be NULL.  Synchronises.  With the CG solver, a solve that does not reach cg_tol within
+ * cg_maxit iterations returns VMC_ERR_NUMERIC without updating the parameters (the chains
+ * have advanced; stats, if given, is filled with solver_converged = 0). */
 vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats);
 
 /* ---- learned proposal (masked autoregressive MLP; requires made_hidden > 0) -------------
@@ -288,17 +294,20 @@ int64_t vmc_num_params(const vmc_ctx* ctx, int lattice);
  *   meanO_out  dev double [P][2] or NULL   <O_k>
  *   stream     cudaStream_t (NULL = legacy default stream); nothing is synchronised.
  * with P = N + M + N*M and the parameter order of this header.
- * Scratch: one file-scope device array of 2^21 doubles (16 MiB) that every GPU loading
- * the library holds until the process exits.  The call needs
- * 8 + ceil(n/1024) * 4 * (M+1) * (N+1) doubles of it and returns VMC_ERR_ARG when that
- * exceeds the array (e.g. N = 64, M = 128 allows n <= 62 * 1024).  It also returns
+ * Scratch: one file-scope device array of 2^21 doubles (16 MiB), held by a GPU from the
+ * first call on it (or from library load with CUDA_MODULE_LOADING=EAGER) until the process
+ * exits.  The call needs 8 + ceil(n/1024) * 4 * (M+1) * (N+1) doubles of it and returns
+ * VMC_ERR_ARG when that exceeds the array (e.g. N = 64, M = 128 allows n <= 62 * 1024) or
+ * when ceil(n/1024) > 65535 (one block column per 1024 samples).  It also returns
  * VMC_ERR_ARG for NULL inputs or sizes outside 1 <= N <= 1024, 1 <= M <= 512, n >= 1, and
  * VMC_ERR_CUDA if a launch fails.  Non-finite inputs give non-finite outputs (no status
  * word is kept).
  * The first call on a device looks up the array's device address with that device
  * current (a one-time set-up per device); make that first call before any stream
- * capture.  All calls share the array and leave their partial sums in it: two calls
- * whose work overlaps on the GPU (different streams, no ordering) race on it. */
+ * capture.  The address is kept for the life of the process: after a cudaDeviceReset
+ * of that device this entry point must not be called again in the same process.  All
+ * calls share the array and leave their partial sums in it: two calls whose work
+ * overlaps on the GPU (different streams, no ordering) race on it. */
 vmc_status vmc_force_noalloc(const int8_t* spins, const float* tanh_theta, const float* eloc,
                              int64_t n, int N, int M, double* F_out, double* meanO_out,
                              void* stream);

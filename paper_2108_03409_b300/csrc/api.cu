@@ -642,6 +642,9 @@ vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
   if (relres) *relres = rel;
   if ((s = check_status(ctx, "cg_solve"))) return s;
   if (!(rel == rel)) return fail(ctx, VMC_ERR_NUMERIC, "CG produced a non-finite residual");
+  if (!(rel <= c.cg_tol))
+    return fail(ctx, VMC_ERR_NUMERIC, "CG did not reach cg_tol within cg_maxit iterations "
+                                      "(x holds the last iterate)");
   return VMC_OK;
 }
 
@@ -712,6 +715,7 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   CK(cudaEventRecord(ctx->ev[2], ctx->st), "sr_step");
   int iters = 0;
   double rel = 0.0;
+  bool converged = true;
   if (ctx->dense) {
     // 3. S (moments + centred X + Gram); with the tensor-core Gram and a mixed solver the
     //    Gram writes the solver's inputs directly
@@ -757,13 +761,18 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
                 &rel), "cg_solve");
     if ((s = check_status(ctx, "cg"))) return s;
     if (!(rel == rel)) return fail(ctx, VMC_ERR_NUMERIC, "CG produced a non-finite residual");
+    // an iterate that did not reach cg_tol is not applied (section "Diagonal shift": the
+    // update is the solution of the shifted equation, not an approximation of unknown quality)
+    converged = rel <= c.cg_tol;
   }
   CK(cudaEventRecord(ctx->ev[4], ctx->st), "sr_step");
   // 5. Euler update of the FP64 master parameters, refresh the FP32 copies
-  CK(launch_update(L.params, ctx->x, L.P, dt, ctx->st), "update");
-  L.chain_cache = false;
-  ++ctx->launches;
-  if ((s = refresh_fp32(ctx, L))) return s;
+  if (converged) {
+    CK(launch_update(L.params, ctx->x, L.P, dt, ctx->st), "update");
+    L.chain_cache = false;
+    ++ctx->launches;
+    if ((s = refresh_fp32(ctx, L))) return s;
+  }
   CK(cudaEventRecord(ctx->ev[5], ctx->st), "sr_step");
   double es[4];
   unsigned long long acc = 0;
@@ -788,7 +797,11 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
     stats->ms_update = t[4];
     cudaEventElapsedTime(&stats->ms_gram, ctx->ev[6], ctx->ev[7]);
     stats->launches = ctx->launches - launches0;
+    stats->solver_converged = converged ? 1 : 0;
   }
+  if (!converged)
+    return fail(ctx, VMC_ERR_NUMERIC, "CG did not reach cg_tol within cg_maxit iterations; "
+                                      "the parameters were not updated");
   return VMC_OK;
 }
 

@@ -10,15 +10,19 @@
 
 namespace vmc {
 
-// 2^21 doubles = 16 MiB.  Every GPU that loads this library holds the array until the
-// process exits.
+// 2^21 doubles = 16 MiB.  A GPU holds the array from the first call on it (the module is
+// placed on a device when it is first used there; with CUDA_MODULE_LOADING=EAGER, from
+// library load) until the process exits.
 static constexpr size_t kNoAllocScratchDoubles = (size_t)1 << 21;
 static constexpr size_t kNoAllocStatsDoubles = 8;   // energy statistics, then the partials
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 // Device address of g_noalloc_scratch per device.  In host code the symbol's name is only
 // a host-side stand-in, so the address is looked up once per device with that device
-// current, and the kernels receive the looked-up pointer.
+// current, and the kernels receive the looked-up pointer.  The cached address belongs to
+// the device's primary context: a cudaDeviceReset by the host program invalidates it (the
+// module may be placed elsewhere afterwards), so this entry point must not be used on a
+// device after a reset in the same process.
 static constexpr int kMaxDevices = 64;
 static double* g_scratch_ptr[kMaxDevices] = {};
 static std::mutex g_scratch_mu;
@@ -49,6 +53,7 @@ extern "C" vmc_status vmc_force_noalloc(const int8_t* spins, const float* tanh_t
   if (n < 1 || N < 1 || N > 1024 || M < 1 || M > 512) return VMC_ERR_ARG;
   const int64_t need = (int64_t)kNoAllocStatsDoubles + moments_partial_doubles(n, N, M);
   if (need > (int64_t)kNoAllocScratchDoubles) return VMC_ERR_ARG;
+  if ((n + 1023) / 1024 > kMomentsMaxChunks) return VMC_ERR_ARG;   // grid z limit
   double* scratch = nullptr;
   if (scratch_for_current_device(&scratch) != cudaSuccess) return VMC_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

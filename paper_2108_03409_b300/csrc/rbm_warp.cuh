@@ -35,7 +35,8 @@ __device__ __forceinline__ void warp_theta(const RbmDev& R, const int8_t* s, int
   }
 }
 
-// log psi = sum_i a_i s_i + sum_j log cosh theta_j (all lanes return the same value).
+// log psi = sum_i a_i s_i + sum_j log cosh theta_j (all lanes return the same value); the
+// imaginary part is returned reduced to [-pi, pi] (a phase is defined mod 2 pi).
 template <int MPL>
 __device__ __forceinline__ float2 warp_logpsi(const RbmDev& R, const int8_t* s, int lane,
                                               const float2 (&th)[MPL]) {
@@ -43,17 +44,17 @@ __device__ __forceinline__ float2 warp_logpsi(const RbmDev& R, const int8_t* s, 
   for (int i = lane; i < R.N; i += 32) {
     float si = (float)s[i];
     re = fmaf(si, R.a[i].x, re);
-    im = fmaf(si, R.a[i].y, im);
+    im = wrap_phase(fmaf(si, R.a[i].y, im));
   }
 #pragma unroll
   for (int k = 0; k < MPL; ++k) {
     if (lane + 32 * k < R.M) {
       float2 lc = logcosh_c(th[k].x, th[k].y);
       re += lc.x;
-      im += lc.y;
+      im = wrap_phase(im + lc.y);
     }
   }
-  return make_float2(warp_sum(re), warp_sum(im));
+  return make_float2(warp_sum(re), warp_sum_phase(im));
 }
 
 // A move q (a site flip, or a bond exchange of anti-parallel spins) with s_i the spin of
@@ -183,7 +184,7 @@ __device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, 
       if (want_logpsi) {
         const float2 lc = logcosh_c(th.x, th.y);
         lr += lc.x;
-        li += lc.y;
+        li = wrap_phase(li + lc.y);
       }
     }
   }
@@ -191,9 +192,9 @@ __device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, 
   for (int i = lane; i < R.N; i += 32) {
     const float si = (float)s[i];
     lr = fmaf(si, R.a[i].x, lr);
-    li = fmaf(si, R.a[i].y, li);
+    li = wrap_phase(fmaf(si, R.a[i].y, li));
   }
-  return make_float2(warp_sum(lr), warp_sum(li));
+  return make_float2(warp_sum(lr), warp_sum_phase(li));
 }
 
 // All sweeps of one chain (the whole warp); s is the warp's shared-memory spin buffer.

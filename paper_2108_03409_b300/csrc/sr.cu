@@ -173,6 +173,7 @@ cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E
                            double2* meanO, double2* F, cudaStream_t st) {
   if (n <= 0) return cudaErrorInvalidValue;
   const int64_t chunks = (n + kChunk - 1) / kChunk;
+  if (chunks > kMomentsMaxChunks) return cudaErrorInvalidValue;   // one chunk per grid z
   dim3 grid((N + 1 + kTile - 1) / kTile, (M + 1 + kTile - 1) / kTile, (unsigned)chunks);
   dim3 block(kTile, 32);
   k_moments_partial<<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, partial);

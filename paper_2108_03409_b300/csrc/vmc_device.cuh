@@ -147,6 +147,24 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// A phase reduced to [-pi, pi]: y - k 2 pi with k = rint(y / 2 pi), the product k 2 pi
+// taken in two FP32 parts (2 pi = C1 + C2, C1 the FP32 value nearest 2 pi; Cody and Waite's
+// reduction) so that the result keeps FP32 accuracy for |k| up to a few thousand.
+__device__ __forceinline__ float wrap_phase(float y) {
+  const float k = rintf(y * 0.15915494309189533577f);
+  y = fmaf(-k, 6.28318548202514648438f, y);
+  return fmaf(k, 1.74845553146951715578e-7f, y);
+}
+
+// Warp sum of phases: every partial sum is reduced to [-pi, pi], so that a log psi whose
+// imaginary part runs to many multiples of 2 pi (a Marshall sign, large weights) still has
+// an absolute error of a few FP32 units of pi mod 2 pi.  Same bits in every lane.
+__device__ __forceinline__ float warp_sum_phase(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = wrap_phase(v + __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -82,7 +82,9 @@ cudaError_t launch_estats(const float2* E, int64_t n, double* out, unsigned* sta
 // Column sums of the log-derivatives and of the force in FP64:
 //   meanO[k] = (1/n) sum_q O_qk,  F[k] = (1/n) sum_q conj(O_qk) (E_q - <E>),
 // with O = [s | t | t (x) s] built on the fly from spins and T = tanh theta.
-// partial: scratch of moments_partial_doubles(n, N, M) doubles.
+// partial: scratch of moments_partial_doubles(n, N, M) doubles.  One chunk of 1024 samples
+// per grid z index, so n <= kMomentsMaxChunks * 1024.
+static constexpr int64_t kMomentsMaxChunks = 65535;
 int64_t moments_partial_doubles(int64_t n, int N, int M);
 cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E,
                            const double* estats, int64_t n, int N, int M, double* partial,

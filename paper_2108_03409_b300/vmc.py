@@ -52,7 +52,7 @@ class vmc_sr_stats(ctypes.Structure):
                 ("ms_sample", ctypes.c_float), ("ms_grad", ctypes.c_float),
                 ("ms_qfm", ctypes.c_float), ("ms_solve", ctypes.c_float),
                 ("ms_update", ctypes.c_float), ("ms_gram", ctypes.c_float),
-                ("launches", ctypes.c_int64)]
+                ("launches", ctypes.c_int64), ("solver_converged", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -232,10 +232,16 @@ def vmc_solve(ctx, lattice, S, F, x):
 
 
 def vmc_cg_solve(ctx, lattice, spins, F, x):
+    """Matrix-free CG; raises VmcError (with ``iters`` and ``relres`` attributes) if cg_tol
+    was not reached within cg_maxit iterations."""
     it = ctypes.c_int(0)
     rr = ctypes.c_double(0.0)
-    _check(ctx, load().vmc_cg_solve(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(F), _ptr(x),
-                                    ctypes.byref(it), ctypes.byref(rr)))
+    try:
+        _check(ctx, load().vmc_cg_solve(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(F),
+                                        _ptr(x), ctypes.byref(it), ctypes.byref(rr)))
+    except VmcError as e:
+        e.iters, e.relres = it.value, rr.value
+        raise
     return it.value, rr.value
 
 
@@ -245,8 +251,14 @@ def vmc_sr_apply(ctx, lattice, spins, v, y):
 
 
 def vmc_sr_step(ctx, lattice, dt) -> vmc_sr_stats:
+    """One SR step.  A failed step raises VmcError; its ``stats`` attribute holds the step's
+    statistics (e.g. solver_converged = 0 when the CG did not reach cg_tol)."""
     st = vmc_sr_stats()
-    _check(ctx, load().vmc_sr_step(ctx, lattice, float(dt), ctypes.byref(st)))
+    try:
+        _check(ctx, load().vmc_sr_step(ctx, lattice, float(dt), ctypes.byref(st)))
+    except VmcError as e:
+        e.stats = st
+        raise
     return st
 
 

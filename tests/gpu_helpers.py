@@ -50,6 +50,26 @@ def phase_diff(a, b):
     return np.abs(np.angle(np.exp(1j * (a - b))))
 
 
+# Weights up to this scale count as "init-scale" (the workloads draw N(0, 0.01^2)), where
+# log psi is held to the absolute bound; larger weights get the relative one.
+INIT_SCALE_SIGMA = 0.05
+
+
+def assert_logpsi_close(got, ref, sigma):
+    """log psi of the FP32 path against the FP64 oracle: absolute LOGPSI_ABS on the real part
+    and on the phase (mod 2 pi) at init-scale weights; LOGPSI_ABS * max(1, |log psi|) for
+    larger weights, where |log psi| >> 10 puts an absolute 1e-5 beyond FP32."""
+    dre = np.abs(got.real - ref.real)
+    dph = phase_diff(got.imag, ref.imag)
+    if sigma <= INIT_SCALE_SIGMA:
+        assert np.max(dre) <= LOGPSI_ABS, np.max(dre)
+        assert np.max(dph) <= LOGPSI_ABS, np.max(dph)
+    else:
+        scale = np.maximum(1.0, np.abs(ref))
+        assert np.all(dre <= LOGPSI_ABS * scale), np.max(dre / scale)
+        assert np.all(dph <= LOGPSI_ABS * scale), np.max(dph / scale)
+
+
 def to_dev_spins(s):
     import torch
     return torch.from_numpy(np.ascontiguousarray(s, dtype=np.int8)).cuda()

@@ -36,7 +36,8 @@ def test_made_logq_matches_oracle(N, H, scale):
     assert np.all(np.abs(got - ref) <= LOGQ_ABS_PER_SITE * N + LOGQ_REL * np.abs(ref))
 
 
-@pytest.mark.parametrize("N,H,n", [(10, 32, 512), (36, 64, 1000)])
+@pytest.mark.parametrize("N,H,n", [(10, 32, 512), (36, 64, 1000), (144, 256, 4096)],
+                         ids=["N10H32", "N36H64", "N144H256_batch4096"])
 def test_made_grad_matches_oracle(N, H, n):
     """Backpropagation through the masked layers; the batch sum is FP32 (n terms), so the
     gradient error is stated relative to the largest gradient entry: n * 2^-24 * 8."""

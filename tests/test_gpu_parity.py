@@ -11,9 +11,9 @@ import oracle
 from paper_2108_03409_b300 import inputs
 from paper_2108_03409_b300 import vmc
 
-from gpu_helpers import (ELOC_PER_SITE_ABS, F_REL, LOGPSI_ABS, OK_ABS, OK_REL, context, cplx,
-                         eloc_tolerance, lattice, phase_diff, s_tol_bf16, s_tol_fp32,
-                         to_dev_spins, well_conditioned)
+from gpu_helpers import (ELOC_PER_SITE_ABS, F_REL, INIT_SCALE_SIGMA, LOGPSI_ABS, OK_ABS, OK_REL,
+                         assert_logpsi_close, context, cplx, eloc_tolerance, lattice, phase_diff,
+                         s_tol_bf16, s_tol_fp32, to_dev_spins, well_conditioned)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -54,9 +54,46 @@ def test_logpsi_matches_oracle(case):
     ref = oracle.logpsi(N, M, p, s)
     ok = well_conditioned(p, s, N, M)
     assert ok.mean() >= 0.98 and np.all(np.isfinite(got))
-    got, ref = got[ok], ref[ok]
-    assert np.max(np.abs(got.real - ref.real)) <= LOGPSI_ABS * max(1.0, np.abs(ref.real).max())
-    assert np.max(phase_diff(got.imag, ref.imag)) <= LOGPSI_ABS * max(1.0, np.abs(ref.imag).max())
+    assert np.all(np.abs(got.imag) <= np.pi * (1 + 1e-6))      # the phase comes reduced
+    assert_logpsi_close(got[ok], ref[ok], case[6])
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_logpsi_ratios_of_connected_configurations(case):
+    """Delta log psi = log psi(s') - log psi(s) between each sample and every configuration
+    H connects it to (the quantity E_loc and the acceptance test are built from), at the
+    absolute 1e-5 bound (real part and phase mod 2 pi), computed from two vmc_logpsi
+    calls.  Samples near a node of psi (for s or any s') are excluded as above."""
+    model, Lx, Ly, J, h, alpha, N, M, p, s = _setup(case)
+    s = s[:min(len(s), 96)]
+    sp_all, owner = [], []
+    for q, c in enumerate(s):
+        sp, _ = oracle.connected(model, Lx, Ly, J, h, c)
+        sp_all.append(sp)
+        owner.append(np.full(len(sp), q))
+    sp_all = np.concatenate(sp_all)
+    owner = np.concatenate(owner)
+    with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=max(len(sp_all), len(s)),
+                 solver=vmc.SOLVER_CG) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        out = torch.zeros((len(sp_all), 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_logpsi(ctx, 0, to_dev_spins(sp_all), out)
+        got = cplx(out)
+    ref = oracle.logpsi(N, M, p, sp_all)
+    ok = well_conditioned(p, sp_all, N, M)
+    ok_owner = np.ones(len(s), bool)
+    np.logical_and.at(ok_owner, owner, ok)
+    keep = ok_owner[owner]
+    assert keep.mean() >= 0.9
+    # entry 0 of each block is s itself (oracle.connected lists the diagonal first)
+    first = np.searchsorted(owner, np.arange(len(s)))
+    dgot = got - got[first][owner]
+    dref = ref - ref[first][owner]
+    # absolute at init-scale weights; relative to |log psi(s)| for larger ones (c13 reading)
+    bound = LOGPSI_ABS * (1.0 if case[6] <= INIT_SCALE_SIGMA
+                          else np.maximum(1.0, np.abs(ref[first][owner])))
+    assert np.all((np.abs(dgot.real - dref.real) <= bound)[keep])
+    assert np.all((phase_diff(dgot.imag, dref.imag) <= bound)[keep])
 
 
 @pytest.mark.parametrize("case", CASES, ids=IDS)
@@ -138,8 +175,7 @@ def test_sampler_trajectories_match_oracle(case):
     assert ok.mean() >= 0.98
     first, lp1 = first[ok], lp1[ok]
     ref_lp = oracle.logpsi(N, M, p, first)
-    assert np.max(np.abs(lp1.real - ref_lp.real)) <= LOGPSI_ABS * max(1.0, np.abs(ref_lp.real).max())
-    assert np.max(phase_diff(lp1.imag, ref_lp.imag)) <= LOGPSI_ABS * max(1.0, np.abs(ref_lp.imag).max())
+    assert_logpsi_close(lp1, ref_lp, sigma)
 
 
 def test_sampler_thermalisation_and_sweep_len():
@@ -222,10 +258,12 @@ def test_qfm_bf16split_tensor_cores_match_oracle(case):
     assert np.array_equal(S16, S16.conj().T)
 
 
-def test_qfm_8x8_sampled_entries():
-    """At the 8x8 Heisenberg shape (P = 8384, 67 x 67 Gram tiles of 128 rows) compare
+@pytest.mark.parametrize("n", [1024, 8192])
+def test_qfm_8x8_sampled_entries(n):
+    """At the 8x8 Heisenberg benchmark shape (P = 8384, 67 x 67 Gram tiles of 128 rows; at
+    n = 8192 the benchmark's sample count, i.e. the timed kernel's full K loop) compare
     sampled entries of S, every F_k and the diagonal with the oracle."""
-    model, Lx, Ly, alpha, n = H, 8, 8, 2, 1024
+    model, Lx, Ly, alpha = H, 8, 8, 2
     N, M = 64, 128
     P = N + M + N * M
     p = inputs.rbm_params(N, M, 0.01, seed=2, marshall=(Lx, Ly))
@@ -260,8 +298,47 @@ def test_qfm_8x8_sampled_entries():
     v = np.zeros(P, np.complex128)
     v[:N] = 1.0
     Sc = Sd[..., 0] + 1j * Sd[..., 1]
-    assert np.linalg.norm(Sc @ v) <= 1e-5 * np.linalg.norm(Sc[:, :N])
+    # S v is rounding only; its bound grows with n like the FP32 accumulation bound n 2^-24
+    # (1e-5 of the a-block's norm at n = 1024)
+    assert np.linalg.norm(Sc @ v) <= 1e-5 * (n / 1024) * np.linalg.norm(Sc[:, :N])
     assert np.array_equal(Sd[..., 0], Sd[..., 0].T) and np.array_equal(Sd[..., 1], -Sd[..., 1].T)
+
+
+def test_tc_solve_8x8_full_size_residual():
+    """The tensor-core solver at the benchmark's size: S (P = 8384) formed by the BF16-split
+    Gram from n = 8192 samples, the benchmark's shift 1e-3, vmc_solve with the tensor-core
+    Cholesky (17 panels of 512, 131 diagonal blocks, 33 dataflow blocks per triangular
+    solve) and refinement.  The returned x must solve the shifted system S~ x = F to a
+    relative residual of 1e-10, computed here in FP64 on the host from the same S and F."""
+    model, Lx, Ly, alpha, n, nu = H, 8, 8, 2, 8192, 1e-3
+    N, M = 64, 128
+    P = N + M + N * M
+    p = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(Lx, Ly))
+    s = inputs.random_sz0_spins(n, N, seed=17)
+    with context(lattice(model, Lx, Ly, 1.0, 0.0, alpha), n_chains=n, shift=nu,
+                 precision=vmc.PREC_BF16SPLIT, solver=vmc.SOLVER_CHOLESKY_TC, cg_tol=1e-10,
+                 cg_maxit=50) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        sd = to_dev_spins(s)
+        e = torch.zeros((n, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_local_energy(ctx, 0, sd, e)
+        F = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        vmc.vmc_grad(ctx, 0, sd, e, None, F)
+        S = torch.zeros((P, P, 2), dtype=torch.float64, device="cuda")
+        vmc.vmc_qfm(ctx, 0, sd, vmc.PREC_BF16SPLIT, S)
+        x = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        it, rel = vmc.vmc_solve(ctx, 0, S, F, x)
+        Sh = S.cpu().numpy()
+        del S
+        F, x = cplx(F), cplx(x)
+    Sc = Sh[..., 0] + 1j * Sh[..., 1]
+    del Sh
+    d = np.real(np.diag(Sc)).copy()
+    r = Sc @ x + nu * d * x - F
+    res = np.linalg.norm(r) / np.linalg.norm(F)
+    assert res <= 1e-10, res
+    assert abs(rel - res) <= 0.5 * res + 1e-12
+    assert 0 < it <= 50
 
 
 @pytest.mark.parametrize("solver", [vmc.SOLVER_CHOLESKY_FP64, vmc.SOLVER_CHOLESKY_MIXED,
@@ -508,3 +585,69 @@ def test_sr_step_bf16_split_recovers_from_indefinite_s():
     assert out[vmc.PREC_FP32][0].e_mean_re == out[vmc.PREC_BF16SPLIT][0].e_mean_re
     for prec in out:
         assert np.linalg.norm(out[prec][1] - p) > 0
+
+
+def test_cfg1_sampled_sr_reaches_jordan_wigner_energy():
+    """The sampled GPU SR loop of the 1D TFIM workload (N = 10, J = h = 1, alpha = 1, 256
+    chains x 200 samples, dt 0.02, shift 1e-4, plain FP32 path) drives the RBM to within
+    1e-3 (relative) of the Jordan-Wigner ground energy E0 = -12.784906443 (section "Ground
+    state search": the fermionised chain is the exact reference).  The energy judged is the
+    exact variational energy of the GPU's parameters (oracle enumeration of all 1024
+    states), checked every 25 steps, at most 2000 steps."""
+    N, M, J, h = 10, 10, 1.0, 1.0
+    k = (2 * np.arange(N) + 1) * np.pi / N
+    E0 = -np.sum(np.sqrt(J * J + h * h - 2 * J * h * np.cos(k)))
+    assert abs(E0 + 12.784906443) < 1e-8
+    p = inputs.rbm_params(N, M, 0.01, seed=1234)
+    with context(lattice(T, N, 1, J, h, 1), n_chains=256, samples_per_chain=200,
+                 therm_sweeps=20, seed=1, solver=vmc.SOLVER_CHOLESKY_MIXED, shift=1e-4,
+                 precision=vmc.PREC_FP32, cg_tol=1e-10, cg_maxit=50) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vmc.vmc_set_chains(ctx, 0, inputs.random_spins(256, N, seed=99))
+        hist = []
+        for step in range(1, 2001):
+            st = vmc.vmc_sr_step(ctx, 0, 0.02)
+            hist.append(st.e_mean_re)
+            if step % 25 == 0:
+                pk = vmc.vmc_get_params(ctx, 0)
+                e_exact = oracle.exact_energy(T, N, 1, J, h, M, pk)[0].real
+                if abs(e_exact - E0) / abs(E0) <= 1e-3:
+                    break
+    assert abs(e_exact - E0) / abs(E0) <= 1e-3, (step, e_exact, E0)
+    # the sampled estimate of the last steps agrees with the exact energy
+    assert abs(np.mean(hist[-10:]) - e_exact) <= 0.01 * abs(E0)
+
+
+def test_cg_non_convergence_is_reported():
+    """A CG that stops at cg_maxit above cg_tol is an error (VMC_ERR_NUMERIC), both from
+    vmc_cg_solve (x holds the last iterate) and from vmc_sr_step (the parameters are left
+    unchanged and the statistics say solver_converged = 0); the context keeps working."""
+    N, M, C = 10, 10, 512
+    p = inputs.rbm_params(N, M, 0.1, seed=51)
+    s = inputs.random_spins(C, N, seed=52)
+    P = N + M + N * M
+    with context(lattice(T, N, 1, 1.0, 1.0, 1), n_chains=C, solver=vmc.SOLVER_CG, shift=1e-4,
+                 cg_tol=1e-14, cg_maxit=2, therm_sweeps=2) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vmc.vmc_set_chains(ctx, 0, s)
+        sd = to_dev_spins(s)
+        e = torch.zeros((C, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_local_energy(ctx, 0, sd, e)
+        F = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        vmc.vmc_grad(ctx, 0, sd, e, None, F)
+        x = torch.zeros((P, 2), dtype=torch.float64, device="cuda")
+        with pytest.raises(vmc.VmcError) as ei:
+            vmc.vmc_cg_solve(ctx, 0, sd, F, x)
+        assert ei.value.status == vmc.VMC_ERR_NUMERIC
+        assert ei.value.iters == 2 and ei.value.relres > 1e-14
+        assert np.all(np.isfinite(x.cpu().numpy())) and torch.any(x != 0)
+        with pytest.raises(vmc.VmcError) as ei:
+            vmc.vmc_sr_step(ctx, 0, 0.02)
+        assert ei.value.status == vmc.VMC_ERR_NUMERIC
+        st = ei.value.stats
+        assert st.solver_converged == 0 and st.solver_iters == 2 and st.solver_relres > 1e-14
+        assert np.isfinite(st.e_mean_re)
+        assert np.array_equal(vmc.vmc_get_params(ctx, 0), p)
+        out = torch.zeros((C, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_logpsi(ctx, 0, sd, out)
+        assert np.all(np.isfinite(out.cpu().numpy()))
