@@ -28,6 +28,8 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   made_grad       -- pinned: central finite differences of the loss
   adam_step       -- pinned: closed form of the first two steps
   made_sample     -- pinned: chi-square of the sample histogram against q
+  tdvp.*          -- regularised TDVP right-hand side and adaptive Heun integrator
+                     (oracle/tdvp.py); pinned in tests/test_oracle_tdvp_pins.py
 """
 from __future__ import annotations
 
