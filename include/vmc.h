@@ -82,6 +82,8 @@ typedef struct {
   int made_hidden;          /* width H of the learned proposal's two hidden layers (multiple   */
                             /* of 32, <= 512); 0 = no learned proposal                         */
   int made_batch;           /* training batch of the learned proposal (0 = 4096)               */
+  int tdvp;                 /* 1: allocate the TDVP workspaces (vmc_tdvp_rhs / vmc_tdvp_step;  */
+                            /* every lattice's P <= 4096)                                      */
 } vmc_config;
 
 /* Statistics of one SR step (host struct filled by vmc_sr_step). */
@@ -264,6 +266,73 @@ int vmc_autotuned_warps_per_block(const vmc_ctx* ctx);
  * synchronise. */
 vmc_status vmc_get_state(vmc_ctx* ctx, void* buf, size_t* len);
 vmc_status vmc_set_state(vmc_ctx* ctx, const void* buf, size_t len);
+
+/* ---- TDVP: regularised right-hand side and adaptive Heun integrator --------------------
+ * (sections "Unitary dynamics", "Regularization to invert the (quantum) Fisher matrix" and
+ * "Utilities": TDVP, Stepper; requires a context created with tdvp = 1.)
+ * The right-hand side solves Eq. tdvp_util with the identity for [[.]] (holomorphic RBM):
+ *     S thetadot = -gamma F,  gamma = 1 (imaginary time: the SR step) or i (real time),
+ * with S, F the connected correlators of Eq. qfm / Eq. force_vector over a weighted sample
+ * set, computed in FP64 from the FP32 tanh(theta) and E_loc of the samples.  S (after the
+ * optional multiplicative shift (1 + shift) S_kk) is diagonalised, S = V diag(lambda) V^H
+ * (parallel cyclic Jacobi, FP64, to an off-diagonal norm of 1e-14 ||S||), rho = V^H F, and
+ *     thetadot = -gamma V diag(lambda^+) rho,
+ *     lambda^+_k = 1/lambda_k * d_pinv(|lambda_k / lambda_1|) * d_snr(SNR_k),
+ * d_pinv = 1/(1 + (eps_pinv/r)^6) (soft) or [r >= eps_pinv] (hard, Eq. pinv_cutoff), 1 if
+ * eps_pinv = 0 (then only lambda = 0 is dropped); d_snr = 1/(1 + (eps_snr/SNR)^6) with
+ * SNR_k = |rho_k| / sqrt(var_s(rho_k(s)) / n), rho_k(s) = sum_l conj(V_lk) conj(Obar_l(s))
+ * (E(s) - <E>), applied to Monte Carlo sample sets only (eps_snr = 0: off). */
+typedef struct {
+  double gamma_re, gamma_im;  /* gamma: (1, 0) imaginary time, (0, 1) real time             */
+  double eps_pinv;            /* pseudo-inverse cutoff relative to lambda_1 (0 = none)     */
+  int pinv_soft;              /* 1: soft cutoff, 0: hard cutoff (Eq. pinv_cutoff)          */
+  double eps_snr;             /* SNR cutoff (0 = none)                                      */
+  double shift;               /* multiplicative diagonal shift of S before the solve (>= 0) */
+  int exact;                  /* vmc_tdvp_step / sample-less vmc_tdvp_rhs: 1 = exact sums   */
+                              /* over all 2^N basis states (2^N <= Ns, N <= 24), Born weights */
+  double eps_step;            /* vmc_tdvp_step: tolerance of the adaptive Heun step          */
+  double tau_max;             /* vmc_tdvp_step: largest step size (0 = no limit)            */
+  int max_retries;            /* vmc_tdvp_step: rejected attempts before giving up (0 = 50) */
+  int jacobi_max_sweeps;      /* Jacobi sweep cap (0 = 40)                                  */
+} vmc_tdvp_opts;
+
+typedef struct {
+  double e_mean_re, e_mean_im, e_var, e_stderr;  /* <E_loc> etc. at the (first) evaluation */
+  double lam_max, lam_min;    /* lambda_1 = max |lambda| and the smallest eigenvalue of S   */
+  int kept;                   /* eigen-components with damping factor >= 1/2                */
+  double snr_min;             /* smallest SNR (0 when SNR damping is off)                   */
+  int jacobi_sweeps;          /* sweeps the eigen-decomposition took                        */
+  double jacobi_off;          /* its final off-diagonal norm relative to ||S||_F            */
+  double tau_used, tau_next;  /* vmc_tdvp_step: accepted step size, proposed next one       */
+  double delta;               /* vmc_tdvp_step: Fisher-norm difference of the two solutions */
+  int retries;                /* vmc_tdvp_step: rejected attempts                            */
+  int rhs_evals;              /* right-hand-side evaluations of the call                    */
+  float ms;                   /* device time of the call (CUDA events)                      */
+} vmc_tdvp_stats;
+
+/* thetadot of the current parameters on a sample set.  spins dev int8 [n][N] with
+ * weights dev double [n] (normalised inside; NULL = uniform, i.e. Monte Carlo samples),
+ * n <= Ns; or spins = NULL: the context makes the set itself, all 2^N basis states with
+ * Born weights (opts->exact = 1) or Ns Metropolis samples of its chains (the chains
+ * advance as in vmc_sr_step).  thetadot: dev double [P][2].  stats (host) may be NULL.
+ * Synchronises.  Returns VMC_ERR_STATE without TDVP workspaces, VMC_ERR_NUMERIC for
+ * non-finite results or a Jacobi iteration that did not converge. */
+vmc_status vmc_tdvp_rhs(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                        const double* weights, const vmc_tdvp_opts* opts, double* thetadot,
+                        vmc_tdvp_stats* stats);
+
+/* One accepted step of the adaptive Heun integrator (section "Utilities", Stepper) on the
+ * lattice's parameters y: with k1 = f(y, t), a Heun step of size tau,
+ *     y_tau = y + tau/2 (k1 + f(y + tau k1)),
+ * and two of size tau/2 (y_h = y + tau/4 (k1 + f(y + tau/2 k1)), then the same from y_h);
+ * delta = ||y_tau - y_tau/2||_S with the Fisher norm ||v||_S = (1/P) sqrt(v^H S v), S taken
+ * at y; tau <- tau (eps_step / delta)^(1/3) (capped at tau_max).  If delta <= eps_step the
+ * two-half-step solution is kept and t advances by the step used, else the attempt is
+ * repeated with the new tau (at most max_retries times; then the parameters are restored
+ * and VMC_ERR_NUMERIC returned).  Every f evaluation is vmc_tdvp_rhs without spins.
+ * t and tau (host, in/out): time and proposed step size.  Synchronises. */
+vmc_status vmc_tdvp_step(vmc_ctx* ctx, int lattice, const vmc_tdvp_opts* opts, double* t,
+                         double* tau, vmc_tdvp_stats* stats);
 
 /* Failure-path self-test (no GPU fault): which = 0 runs the cooperative kernels' bounded
  * flag wait on a word that nothing sets, which = 1 the tensor-core kernels' bounded mbarrier

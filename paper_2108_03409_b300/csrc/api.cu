@@ -74,6 +74,7 @@ struct vmc_ctx {
   CgWork cg{};
   MadeWork mw{};
   int64_t made_cap = 0;           // rows of the MADE batch workspaces
+  TdvpWork tw{};                  // TDVP workspaces (cfg.tdvp)
   // batched sampler
   SampleArgs* d_bargs = nullptr;  // [n_lattices] device descriptors
   int* d_order = nullptr;         // heavy-first lattice order
@@ -257,7 +258,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
     return VMC_ERR_ARG;
   if (!(cfg->shift >= 0.0)) return VMC_ERR_ARG;
   if (cfg->made_hidden < 0 || cfg->made_hidden > 512 || cfg->made_hidden % 32 != 0 ||
-      cfg->made_batch < 0)
+      cfg->made_batch < 0 || (cfg->tdvp != 0 && cfg->tdvp != 1))
     return VMC_ERR_ARG;
   for (int l = 0; l < n_lattices; ++l) {
     const vmc_lattice& L = lattices[l];
@@ -389,6 +390,40 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
           (e = dalloc(ctx, &w.ovpart, (size_t)w.cap_ov)))
         return oom(e);
     }
+  }
+  if (cfg->tdvp) {
+    // TDVP workspaces: FP64 S, Q, the Jacobi work matrix, V and the integrator's S at y
+    TdvpWork& tw = ctx->tw;
+    const int64_t P = ctx->Pmax;
+    if (P > 4096) {
+      vmc_destroy(ctx);
+      return VMC_ERR_ARG;
+    }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    tw.n_sm = sms;
+    tw.Pcap = P;
+    tw.ncap = Ns;
+    tw.status = ctx->status;
+    tw.red_cap = 64 * sms;
+    tw.mom_part_cap = 2 * P * 512;
+    tw.gram_part_cap = tdvp_gram_partial_doubles2(Ns, P, sms);
+    if ((e = dalloc(ctx, &tw.w, (size_t)Ns)) || (e = dalloc(ctx, &tw.lp, (size_t)Ns)) ||
+        (e = dalloc(ctx, &tw.estats, 8)) || (e = dalloc(ctx, &tw.meanO, P)) ||
+        (e = dalloc(ctx, &tw.F, P)) || (e = dalloc(ctx, &tw.mom_part, (size_t)tw.mom_part_cap)) ||
+        (e = dalloc(ctx, &tw.gram_part, (size_t)tw.gram_part_cap)) ||
+        (e = dalloc(ctx, &tw.S, (size_t)P * P)) || (e = dalloc(ctx, &tw.Q, (size_t)P * P)) ||
+        (e = dalloc(ctx, &tw.A, (size_t)P * P)) || (e = dalloc(ctx, &tw.V, (size_t)P * P)) ||
+        (e = dalloc(ctx, &tw.S0, (size_t)P * P)) || (e = dalloc(ctx, &tw.lam, P)) ||
+        (e = dalloc(ctx, &tw.rot, P + 2)) || (e = dalloc(ctx, &tw.bar, 4)) ||
+        (e = dalloc(ctx, &tw.red, (size_t)tw.red_cap)) || (e = dalloc(ctx, &tw.info, 2)) ||
+        (e = dalloc(ctx, &tw.rho, P)) || (e = dalloc(ctx, &tw.qd, P)) ||
+        (e = dalloc(ctx, &tw.lamp, P)) || (e = dalloc(ctx, &tw.lstats, 4)) ||
+        (e = dalloc(ctx, &tw.qpart, (size_t)(P + 255) / 256 + 1)))
+      return oom(e);
+    for (int k = 0; k < 8; ++k)
+      if ((e = dalloc(ctx, &tw.vec[k], P))) return oom(e);
   }
   if (ctx->dense) {
     const int64_t P = ctx->Pmax;
@@ -669,16 +704,10 @@ vmc_status vmc_sr_apply(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
   return check_status(ctx, "cg_apply");
 }
 
-vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats) {
-  vmc_status s = lattice_ok(ctx, lattice);
-  if (s) return s;
-  LatticeState& L = ctx->lats[lattice];
+// The samples of one SR step (Ns = n_chains * samples_per_chain) from the lattice's chains:
+// spins, E_loc and tanh(theta) into the step buffers; *steps = Metropolis steps per chain.
+static vmc_status sample_step_set(vmc_ctx* ctx, LatticeState& L, int lattice, uint64_t* steps_out) {
   const vmc_config& c = ctx->cfg;
-  const int64_t Ns = ctx->Ns;
-  const int64_t launches0 = ctx->launches;
-  CK(cudaMemsetAsync(ctx->n_accept, 0, sizeof(unsigned long long), ctx->st), "sr_step");
-  CK(cudaEventRecord(ctx->ev[0], ctx->st), "sr_step");
-  // 1. sample Ns configurations; E_loc and tanh(theta) fused at every record point
   SampleArgs A{};
   A.rbm = rbm_of(L);
   A.lat = lat_of(L);
@@ -705,9 +734,24 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   A.theta_in = ctx->s_T;
   CK(launch_sample(A, ctx->st), "sample");
   ++ctx->launches;
-  const uint64_t steps = (uint64_t)(A.n_therm + A.n_samples * A.sweeps_per_sample) * (uint64_t)A.L;
+  *steps_out = (uint64_t)(A.n_therm + A.n_samples * A.sweeps_per_sample) * (uint64_t)A.L;
   L.sweep += (uint64_t)A.n_therm + (uint64_t)A.n_samples * A.sweeps_per_sample;
   L.thermalized = true;
+  return VMC_OK;
+}
+
+vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  LatticeState& L = ctx->lats[lattice];
+  const vmc_config& c = ctx->cfg;
+  const int64_t Ns = ctx->Ns;
+  const int64_t launches0 = ctx->launches;
+  CK(cudaMemsetAsync(ctx->n_accept, 0, sizeof(unsigned long long), ctx->st), "sr_step");
+  CK(cudaEventRecord(ctx->ev[0], ctx->st), "sr_step");
+  // 1. sample Ns configurations; E_loc and tanh(theta) fused at every record point
+  uint64_t steps = 0;
+  if ((s = sample_step_set(ctx, L, lattice, &steps))) return s;
   CK(cudaEventRecord(ctx->ev[1], ctx->st), "sr_step");
   // 2. energy statistics, <O>, F (the b- and W-block factors come from the sampler)
   CK(launch_estats(ctx->s_E, Ns, ctx->estats, ctx->status, ctx->st), "estats");
@@ -805,6 +849,202 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   return VMC_OK;
 }
 
+
+// ---------------------------------------------------------------------------------------
+// TDVP (sections "Unitary dynamics", "Regularization...", "Utilities")
+// ---------------------------------------------------------------------------------------
+static vmc_status tdvp_opts_ok(vmc_ctx* ctx, const vmc_tdvp_opts* o) {
+  if (!o) return fail(ctx, VMC_ERR_ARG, "NULL options");
+  if (!(o->eps_pinv >= 0.0) || !(o->eps_snr >= 0.0) || !(o->shift >= 0.0) ||
+      (o->pinv_soft != 0 && o->pinv_soft != 1) || (o->exact != 0 && o->exact != 1) ||
+      o->jacobi_max_sweeps < 0 || o->max_retries < 0 || !std::isfinite(o->gamma_re) ||
+      !std::isfinite(o->gamma_im))
+    return fail(ctx, VMC_ERR_ARG, "bad TDVP options");
+  return VMC_OK;
+}
+
+// thetadot of the lattice's current parameters into `out` (dev [P]); the sample set is
+// `spins` (weights w or uniform) or, with spins = null, made here (exact enumeration or
+// Metropolis samples).  save_S0 keeps a copy of S for the Fisher norm.  Stats (host) are
+// filled from the device after a synchronisation when `st` is given.
+static vmc_status tdvp_eval(vmc_ctx* ctx, int lattice, LatticeState& L, const int8_t* spins,
+                            int64_t n, const double* w, const vmc_tdvp_opts& o, double2* out,
+                            bool save_S0, vmc_tdvp_stats* st) {
+  TdvpWork& tw = ctx->tw;
+  const int64_t P = L.P;
+  const int8_t* sp = spins;
+  const double* wp = w;
+  bool have_tE = false;
+  if (!sp) {
+    if (o.exact) {
+      if (L.N > 24 || (1ll << L.N) > ctx->Ns)
+        return fail(ctx, VMC_ERR_ARG, "exact sums need 2^N <= Ns (N <= 24)");
+      n = 1ll << L.N;
+      CK(launch_enum_states(ctx->s_spins, L.N, n, ctx->st), "enum_states");
+      CK(launch_logpsi(rbm_of(L), ctx->s_spins, n, tw.lp, ctx->status, ctx->st), "logpsi");
+      CK(launch_born_weights(tw.lp, n, tw.w, ctx->status, ctx->st), "born_weights");
+      ctx->launches += 3;
+      wp = tw.w;
+    } else {
+      uint64_t steps = 0;
+      vmc_status s = sample_step_set(ctx, L, lattice, &steps);
+      if (s) return s;
+      n = ctx->Ns;
+      wp = nullptr;
+      have_tE = true;
+    }
+    sp = ctx->s_spins;
+  }
+  if (!have_tE) {
+    CK(launch_theta_tanh(rbm_of(L), sp, n, ctx->s_T, ctx->st), "theta_tanh");
+    CK(launch_eloc(rbm_of(L), lat_of(L), sp, n, ctx->s_E, ctx->status, ctx->st), "eloc");
+    ctx->launches += 2;
+  }
+  CK(tdvp_moments(sp, ctx->s_T, ctx->s_E, wp, n, L.N, L.M, tw, ctx->st), "tdvp_moments");
+  CK(tdvp_gram(sp, ctx->s_T, ctx->s_E, wp, n, L.N, L.M, tw, ctx->st), "tdvp_gram");
+  ctx->launches += 5;
+  if (o.shift > 0.0) {
+    CK(tdvp_shift(tw, P, o.shift, ctx->st), "tdvp_shift");
+    ++ctx->launches;
+  }
+  if (save_S0) CK(cudaMemcpyAsync(tw.S0, tw.S, sizeof(double2) * P * P, cudaMemcpyDeviceToDevice,
+                                  ctx->st), "tdvp_S0");
+  CK(tdvp_eig(tw, P, o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40, 1e-14, ctx->st), "jacobi");
+  const bool snr = o.eps_snr > 0.0 && wp == nullptr;
+  CK(tdvp_solve(tw, P, snr, o.eps_pinv, o.pinv_soft, o.eps_snr, (double)n, o.gamma_re,
+                o.gamma_im, out, ctx->st), "tdvp_solve");
+  ctx->launches += 4;
+  if (st) {
+    double es[4], ls[4], info[2];
+    CK(cudaMemcpyAsync(es, tw.estats, sizeof(es), cudaMemcpyDeviceToHost, ctx->st), "tdvp");
+    CK(cudaMemcpyAsync(ls, tw.lstats, sizeof(ls), cudaMemcpyDeviceToHost, ctx->st), "tdvp");
+    CK(cudaMemcpyAsync(info, tw.info, sizeof(info), cudaMemcpyDeviceToHost, ctx->st), "tdvp");
+    CK(cudaStreamSynchronize(ctx->st), "tdvp");
+    st->e_mean_re = es[0];
+    st->e_mean_im = es[1];
+    st->e_var = es[2];
+    st->e_stderr = es[3];
+    st->lam_max = ls[0];
+    st->lam_min = ls[1];
+    st->kept = (int)ls[2];
+    st->snr_min = ls[3];
+    st->jacobi_sweeps = (int)info[0];
+    st->jacobi_off = info[1];
+  }
+  return VMC_OK;
+}
+
+vmc_status vmc_tdvp_rhs(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                        const double* weights, const vmc_tdvp_opts* opts, double* thetadot,
+                        vmc_tdvp_stats* stats) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if ((s = tdvp_opts_ok(ctx, opts))) return s;
+  if (!ctx->cfg.tdvp) return fail(ctx, VMC_ERR_STATE, "context was created without TDVP workspaces");
+  if (!thetadot) return fail(ctx, VMC_ERR_ARG, "NULL output");
+  if (spins && (n < 1 || n > ctx->Ns)) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  CK(cudaEventRecord(ctx->ev[0], ctx->st), "tdvp_rhs");
+  vmc_tdvp_stats local{};
+  if ((s = tdvp_eval(ctx, lattice, L, spins, n, spins ? weights : nullptr, *opts,
+                     reinterpret_cast<double2*>(thetadot), false, &local)))
+    return s;
+  CK(cudaEventRecord(ctx->ev[1], ctx->st), "tdvp_rhs");
+  if ((s = check_status(ctx, "tdvp_rhs"))) return s;
+  local.rhs_evals = 1;
+  cudaEventElapsedTime(&local.ms, ctx->ev[0], ctx->ev[1]);
+  if (stats) *stats = local;
+  return VMC_OK;
+}
+
+// the lattice's parameters := y (FP64 master), FP32 copies and move tables refreshed
+static vmc_status tdvp_set_params(vmc_ctx* ctx, LatticeState& L, const double2* y) {
+  CK(cudaMemcpyAsync(L.params, y, sizeof(double2) * L.P, cudaMemcpyDeviceToDevice, ctx->st),
+     "tdvp_params");
+  L.chain_cache = false;
+  return refresh_fp32(ctx, L);
+}
+
+vmc_status vmc_tdvp_step(vmc_ctx* ctx, int lattice, const vmc_tdvp_opts* opts, double* t,
+                         double* tau, vmc_tdvp_stats* stats) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if ((s = tdvp_opts_ok(ctx, opts))) return s;
+  if (!ctx->cfg.tdvp) return fail(ctx, VMC_ERR_STATE, "context was created without TDVP workspaces");
+  if (!t || !tau || !(*tau > 0.0) || !(opts->eps_step > 0.0) || !(opts->tau_max >= 0.0))
+    return fail(ctx, VMC_ERR_ARG, "bad step arguments");
+  LatticeState& L = ctx->lats[lattice];
+  TdvpWork& tw = ctx->tw;
+  const vmc_tdvp_opts& o = *opts;
+  const int64_t P = L.P;
+  const double tmax = o.tau_max > 0.0 ? o.tau_max : INFINITY;
+  double2 *y0 = tw.vec[0], *k1 = tw.vec[1], *k2 = tw.vec[2], *g1 = tw.vec[3], *g2 = tw.vec[4],
+          *ytmp = tw.vec[5], *yfull = tw.vec[6], *yh = tw.vec[7];
+  CK(cudaEventRecord(ctx->ev[0], ctx->st), "tdvp_step");
+  CK(cudaMemcpyAsync(y0, L.params, sizeof(double2) * P, cudaMemcpyDeviceToDevice, ctx->st), "tdvp_step");
+  vmc_tdvp_stats local{};
+  if ((s = tdvp_eval(ctx, lattice, L, nullptr, 0, nullptr, o, k1, true, &local))) return s;
+  int evals = 1;
+  double h = std::min(*tau, tmax);
+  auto eval_at = [&](const double2* y, double2* out) -> vmc_status {
+    vmc_status r = tdvp_set_params(ctx, L, y);
+    if (r) return r;
+    ++evals;
+    return tdvp_eval(ctx, lattice, L, nullptr, 0, nullptr, o, out, false, nullptr);
+  };
+  const int max_retries = o.max_retries > 0 ? o.max_retries : 50;
+  for (int retry = 0; retry <= max_retries; ++retry) {
+    // one step of size h: y_full = y0 + h/2 (k1 + f(y0 + h k1))
+    CK(launch_axpy2(y0, h, k1, 0.0, nullptr, P, ytmp, ctx->st), "axpy");
+    if ((s = eval_at(ytmp, k2))) return s;
+    CK(launch_axpy2(y0, 0.5 * h, k1, 0.5 * h, k2, P, yfull, ctx->st), "axpy");
+    // two steps of size h/2
+    CK(launch_axpy2(y0, 0.5 * h, k1, 0.0, nullptr, P, ytmp, ctx->st), "axpy");
+    if ((s = eval_at(ytmp, k2))) return s;
+    CK(launch_axpy2(y0, 0.25 * h, k1, 0.25 * h, k2, P, yh, ctx->st), "axpy");
+    if ((s = eval_at(yh, g1))) return s;
+    CK(launch_axpy2(yh, 0.5 * h, g1, 0.0, nullptr, P, ytmp, ctx->st), "axpy");
+    if ((s = eval_at(ytmp, g2))) return s;
+    CK(launch_axpy2(yh, 0.25 * h, g1, 0.25 * h, g2, P, ytmp, ctx->st), "axpy");   // y_half
+    ctx->launches += 7;
+    // delta = (1/P) sqrt((y_full - y_half)^H S0 (y_full - y_half))
+    int np = 0;
+    CK(launch_quad_form(tw.S0, yfull, ytmp, P, tw.qpart, &np, ctx->st), "quad_form");
+    ++ctx->launches;
+    std::vector<double> qp(np);
+    CK(cudaMemcpyAsync(qp.data(), tw.qpart, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->st),
+       "quad_form");
+    if ((s = check_status(ctx, "tdvp_step"))) return s;
+    double q = 0.0;
+    for (double v : qp) q += v;
+    const double delta = std::sqrt(std::max(q, 0.0)) / (double)P;
+    if (!std::isfinite(delta)) {
+      tdvp_set_params(ctx, L, y0);
+      return fail(ctx, VMC_ERR_NUMERIC, "TDVP step: non-finite error estimate");
+    }
+    double hn = delta > 0.0 ? h * std::cbrt(o.eps_step / delta) : tmax;
+    if (!std::isfinite(hn)) hn = tmax;
+    hn = std::min(hn, tmax);
+    if (delta <= o.eps_step) {
+      if ((s = tdvp_set_params(ctx, L, ytmp))) return s;
+      CK(cudaEventRecord(ctx->ev[1], ctx->st), "tdvp_step");
+      if ((s = check_status(ctx, "tdvp_step"))) return s;
+      *t += h;
+      *tau = hn;
+      local.tau_used = h;
+      local.tau_next = hn;
+      local.delta = delta;
+      local.retries = retry;
+      local.rhs_evals = evals;
+      cudaEventElapsedTime(&local.ms, ctx->ev[0], ctx->ev[1]);
+      if (stats) *stats = local;
+      return VMC_OK;
+    }
+    h = hn;
+  }
+  tdvp_set_params(ctx, L, y0);
+  return fail(ctx, VMC_ERR_NUMERIC, "TDVP step: no step accepted within max_retries");
+}
 
 static vmc_status made_ok(vmc_ctx* ctx, int lattice) {
   vmc_status s = lattice_ok(ctx, lattice);

@@ -526,45 +526,6 @@ __global__ void __launch_bounds__(256) k_herk(C* __restrict__ A, int64_t P, int6
 // with L2-only accesses (ld/st.global.cg): rows move between blocks from step to step, so
 // an L1 copy from an earlier step could be stale.
 // ---------------------------------------------------------------------------------------
-struct GridBarrier {
-  unsigned count;
-  unsigned gen;
-  unsigned abort;
-};
-
-__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, unsigned* status) {
-  __syncthreads();
-  __shared__ int ok;
-  if (threadIdx.x == 0) {
-    ok = 1;
-    volatile unsigned* vgen = &bar->gen;
-    volatile unsigned* vab = &bar->abort;
-    const unsigned g = *vgen;
-    __threadfence();
-    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
-      bar->count = 0;
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      unsigned it = 0;
-      while (*vgen == g) {
-        if (*vab) { ok = 0; break; }
-        if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
-          atomicExch(&bar->abort, 1u);
-          flag_error(status, DEV_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
 // Bounded waits on a counter in global memory: iteration and clock limits; an expired wait
 // sets DEV_ERR_TIMEOUT and the abort word, which every other wait also checks.
 __device__ __forceinline__ bool wait_at_least(const unsigned* word, unsigned target,

@@ -139,6 +139,49 @@ __device__ __forceinline__ void grouped_tri_tile(int64_t t, int nt, int group, i
   *bn = r1;
 }
 
+// Grid-wide barrier of a cooperative launch: a counter plus a generation word in global
+// memory (zeroed before the launch).  Every wait is bounded (iteration and clock limits);
+// an expired wait sets DEV_ERR_TIMEOUT and an abort word that makes every other block's
+// wait give up too, so that all blocks leave their loops.  Returns false on abort.
+struct GridBarrier {
+  unsigned count;
+  unsigned gen;
+  unsigned abort;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, unsigned* status) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = &bar->gen;
+    volatile unsigned* vab = &bar->abort;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&bar->count, 1u) == nblocks - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      unsigned it = 0;
+      while (*vgen == g) {
+        if (*vab) { ok = 0; break; }
+        if ((++it & 1023u) == 0 && clock64() - t0 > 2000000000ll) {
+          atomicExch(&bar->abort, 1u);
+          flag_error(status, DEV_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
 // warp reductions with xor butterflies: every lane ends with the same bits (each level
 // adds the same two operands in both partner lanes).
 __device__ __forceinline__ float warp_sum(float v) {

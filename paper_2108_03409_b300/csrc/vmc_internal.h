@@ -269,6 +269,59 @@ cudaError_t cg_apply(const CgProblem& pb, CgWork& w, const double2* v, double2* 
 cudaError_t cg_solve(const CgProblem& pb, const double2* F, double2* x, double tol, int maxit,
                      CgWork& w, cudaStream_t st, int64_t* launches, int* iters, double* relres);
 
+// ---- tdvp.cu --------------------------------------------------------------------------
+// Workspaces of the regularised TDVP right-hand side (P <= Pcap, n <= ncap samples).
+struct TdvpWork {
+  int64_t Pcap = 0, ncap = 0;
+  int n_sm = 148;
+  unsigned* status = nullptr;      // the context's status word
+  double* w = nullptr;             // [ncap] sample weights (exact enumeration)
+  float2* lp = nullptr;            // [ncap] log psi (exact enumeration)
+  double* estats = nullptr;        // [8]
+  double2* meanO = nullptr;        // [Pcap]
+  double2* F = nullptr;            // [Pcap]
+  double2* mom_part = nullptr;     // moments chunk partials
+  int64_t mom_part_cap = 0;        // in double2
+  double2* gram_part = nullptr;    // Gram chunk partials
+  int64_t gram_part_cap = 0;       // in double2
+  double2 *S = nullptr, *Q = nullptr, *A = nullptr, *V = nullptr, *S0 = nullptr;  // [Pcap]^2
+  double* lam = nullptr;           // [Pcap] eigenvalues
+  double2* rot = nullptr;          // [Pcap + 2] Jacobi rotations (c, sigma) per pair
+  unsigned* bar = nullptr;         // grid barrier words [4]
+  double* red = nullptr;           // [red_cap] per-block partials
+  int red_cap = 0;
+  double* info = nullptr;          // [2] Jacobi sweeps, relative off-diagonal norm
+  double2* rho = nullptr;          // [Pcap] V^H F
+  double* qd = nullptr;            // [Pcap] (V^H Q V)_kk
+  double* lamp = nullptr;          // [Pcap] lambda^+
+  double* lstats = nullptr;        // [4] lambda_1, lambda_min, kept components, min SNR
+  double2* vec[8] = {};            // [Pcap] integrator vectors
+  double* qpart = nullptr;         // [Pcap/256 + 1] quadratic-form partials
+};
+int64_t tdvp_gram_chunks(int64_t n, int64_t P, int n_sm);
+int64_t tdvp_gram_partial_doubles2(int64_t n, int64_t P, int n_sm);
+cudaError_t launch_enum_states(int8_t* spins, int N, int64_t n, cudaStream_t st);
+cudaError_t launch_born_weights(const float2* lp, int64_t n, double* w, unsigned* status,
+                                cudaStream_t st);
+// weighted <E> (tw.estats), <O> (tw.meanO) and F (tw.F); w = null: uniform 1/n
+cudaError_t tdvp_moments(const int8_t* spins, const float2* T, const float2* E, const double* w,
+                         int64_t n, int N, int M, TdvpWork& tw, cudaStream_t st);
+// weighted S (tw.S) and energy-weighted Q (tw.Q), full Hermitian, FP64
+cudaError_t tdvp_gram(const int8_t* spins, const float2* T, const float2* E, const double* w,
+                      int64_t n, int N, int M, TdvpWork& tw, cudaStream_t st);
+// tw.S_kk *= 1 + nu
+cudaError_t tdvp_shift(TdvpWork& tw, int64_t P, double nu, cudaStream_t st);
+// tw.S = tw.V diag(tw.lam) tw.V^H (cooperative Jacobi on a copy in tw.A)
+cudaError_t tdvp_eig(TdvpWork& tw, int64_t P, int max_sweeps, double tol, cudaStream_t st);
+// out = -gamma V diag(lambda^+) V^H F
+cudaError_t tdvp_solve(TdvpWork& tw, int64_t P, bool snr, double eps_pinv, int soft,
+                       double eps_snr, double n_eff, double g_re, double g_im, double2* out,
+                       cudaStream_t st);
+cudaError_t launch_axpy2(const double2* y, double a, const double2* k1, double b, const double2* k2,
+                         int64_t P, double2* out, cudaStream_t st);
+cudaError_t launch_quad_form(const double2* S, const double2* x, const double2* y, int64_t P,
+                             double* part, int* nparts, cudaStream_t st);
+
 // ---- made.cu ---------------------------------------------------------------------------
 struct MadeDev {
   int N, H;

@@ -41,7 +41,8 @@ class vmc_config(ctypes.Structure):
                 ("samples_per_chain", ctypes.c_int), ("precision", ctypes.c_int),
                 ("solver", ctypes.c_int), ("shift", ctypes.c_double), ("shift_mode", ctypes.c_int),
                 ("cg_maxit", ctypes.c_int), ("cg_tol", ctypes.c_double),
-                ("made_hidden", ctypes.c_int), ("made_batch", ctypes.c_int)]
+                ("made_hidden", ctypes.c_int), ("made_batch", ctypes.c_int),
+                ("tdvp", ctypes.c_int)]
 
 
 class vmc_sr_stats(ctypes.Structure):
@@ -58,13 +59,35 @@ class vmc_sr_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class vmc_tdvp_opts(ctypes.Structure):
+    _fields_ = [("gamma_re", ctypes.c_double), ("gamma_im", ctypes.c_double),
+                ("eps_pinv", ctypes.c_double), ("pinv_soft", ctypes.c_int),
+                ("eps_snr", ctypes.c_double), ("shift", ctypes.c_double), ("exact", ctypes.c_int),
+                ("eps_step", ctypes.c_double), ("tau_max", ctypes.c_double),
+                ("max_retries", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int)]
+
+
+class vmc_tdvp_stats(ctypes.Structure):
+    _fields_ = [("e_mean_re", ctypes.c_double), ("e_mean_im", ctypes.c_double),
+                ("e_var", ctypes.c_double), ("e_stderr", ctypes.c_double),
+                ("lam_max", ctypes.c_double), ("lam_min", ctypes.c_double), ("kept", ctypes.c_int),
+                ("snr_min", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int),
+                ("jacobi_off", ctypes.c_double), ("tau_used", ctypes.c_double),
+                ("tau_next", ctypes.c_double), ("delta", ctypes.c_double),
+                ("retries", ctypes.c_int), ("rhs_evals", ctypes.c_int), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
             "vmc_set_chains", "vmc_get_chains", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
             "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
             "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve", "vmc_sr_apply",
             "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
             "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned", "vmc_sample_all",
-            "vmc_autotuned_warps_per_block", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout"]
+            "vmc_autotuned_warps_per_block", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout",
+            "vmc_tdvp_rhs", "vmc_tdvp_step"]
 
 _lib = None
 
@@ -113,6 +136,10 @@ def load(path: str = LIB_PATH):
         "vmc_get_state": (i32, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
         "vmc_set_state": (i32, [P, P, ctypes.c_size_t]),
         "vmc_selftest_wait_timeout": (i32, [P, i32]),
+        "vmc_tdvp_rhs": (i32, [P, i32, P, i64, P, ctypes.POINTER(vmc_tdvp_opts), P,
+                               ctypes.POINTER(vmc_tdvp_stats)]),
+        "vmc_tdvp_step": (i32, [P, i32, ctypes.POINTER(vmc_tdvp_opts), ctypes.POINTER(f64),
+                                ctypes.POINTER(f64), ctypes.POINTER(vmc_tdvp_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -141,10 +168,17 @@ def _check(ctx, status: int):
 def make_config(seed=1, n_chains=256, sweep_len=0, therm_sweeps=20, sweeps_per_sample=1,
                 samples_per_chain=1, precision=PREC_FP32, solver=SOLVER_CHOLESKY_FP64,
                 shift=1e-4, shift_mode=SHIFT_MULTIPLICATIVE, cg_maxit=100,
-                cg_tol=1e-10, made_hidden=0, made_batch=0) -> vmc_config:
+                cg_tol=1e-10, made_hidden=0, made_batch=0, tdvp=0) -> vmc_config:
     return vmc_config(seed, n_chains, sweep_len, therm_sweeps, sweeps_per_sample,
                       samples_per_chain, precision, solver, shift, shift_mode, cg_maxit, cg_tol,
-                      made_hidden, made_batch)
+                      made_hidden, made_batch, tdvp)
+
+
+def make_tdvp_opts(gamma=1j, eps_pinv=0.0, pinv_soft=1, eps_snr=0.0, shift=0.0, exact=0,
+                   eps_step=1e-6, tau_max=0.0, max_retries=0, jacobi_max_sweeps=0) -> vmc_tdvp_opts:
+    g = complex(gamma)
+    return vmc_tdvp_opts(g.real, g.imag, eps_pinv, pinv_soft, eps_snr, shift, exact, eps_step,
+                         tau_max, max_retries, jacobi_max_sweeps)
 
 
 def make_lattice(model, Lx, Ly=1, J=1.0, h=0.0, alpha=1) -> vmc_lattice:
@@ -356,3 +390,22 @@ def vmc_set_state(ctx, state: bytes):
 def vmc_selftest_wait_timeout(ctx, which: int) -> int:
     """Run a bounded wait that nothing satisfies; returns the status (VMC_ERR_TIMEOUT expected)."""
     return int(load().vmc_selftest_wait_timeout(ctx, int(which)))
+
+
+def vmc_tdvp_rhs(ctx, lattice, opts, thetadot, spins=None, weights=None) -> vmc_tdvp_stats:
+    """thetadot (dev float64 [P][2]) of the current parameters; spins (dev int8 [n][N]) with
+    optional weights (dev float64 [n]), or None: the context's own sample set."""
+    st = vmc_tdvp_stats()
+    n = spins.shape[0] if spins is not None else 0
+    _check(ctx, load().vmc_tdvp_rhs(ctx, lattice, _ptr(spins), n, _ptr(weights),
+                                    ctypes.byref(opts), _ptr(thetadot), ctypes.byref(st)))
+    return st
+
+
+def vmc_tdvp_step(ctx, lattice, opts, t, tau):
+    """One accepted adaptive Heun step; returns (t, tau_next, stats)."""
+    tt, hh = ctypes.c_double(t), ctypes.c_double(tau)
+    st = vmc_tdvp_stats()
+    _check(ctx, load().vmc_tdvp_step(ctx, lattice, ctypes.byref(opts), ctypes.byref(tt),
+                                     ctypes.byref(hh), ctypes.byref(st)))
+    return tt.value, hh.value, st

@@ -45,9 +45,12 @@ def test_struct_layout_matches_header():
 int main(void) {
   printf("vmc_lattice %zu\nvmc_config %zu\nvmc_sr_stats %zu\n", sizeof(vmc_lattice),
          sizeof(vmc_config), sizeof(vmc_sr_stats));
+  printf("vmc_tdvp_opts %zu\nvmc_tdvp_stats %zu\n", sizeof(vmc_tdvp_opts), sizeof(vmc_tdvp_stats));
   F(vmc_lattice, J) F(vmc_lattice, alpha) F(vmc_config, shift) F(vmc_config, cg_tol)
-  F(vmc_config, solver) F(vmc_sr_stats, n_samples) F(vmc_sr_stats, solver_relres)
-  F(vmc_sr_stats, ms_update)
+  F(vmc_config, solver) F(vmc_config, tdvp) F(vmc_sr_stats, n_samples)
+  F(vmc_sr_stats, solver_relres) F(vmc_sr_stats, ms_update) F(vmc_sr_stats, solver_converged)
+  F(vmc_tdvp_opts, eps_snr) F(vmc_tdvp_opts, exact) F(vmc_tdvp_opts, jacobi_max_sweeps)
+  F(vmc_tdvp_stats, kept) F(vmc_tdvp_stats, jacobi_off) F(vmc_tdvp_stats, ms)
   return 0;
 }
 """
@@ -61,6 +64,8 @@ int main(void) {
     assert int(got["vmc_lattice"]) == ctypes.sizeof(vmc.vmc_lattice)
     assert int(got["vmc_config"]) == ctypes.sizeof(vmc.vmc_config)
     assert int(got["vmc_sr_stats"]) == ctypes.sizeof(vmc.vmc_sr_stats)
+    assert int(got["vmc_tdvp_opts"]) == ctypes.sizeof(vmc.vmc_tdvp_opts)
+    assert int(got["vmc_tdvp_stats"]) == ctypes.sizeof(vmc.vmc_tdvp_stats)
     for key, val in got.items():
         if "." in key:
             t, f = key.split(".")
@@ -69,7 +74,7 @@ int main(void) {
 
 @pytest.mark.parametrize("bad", [
     dict(n_chains=0), dict(samples_per_chain=0), dict(sweeps_per_sample=0), dict(solver=7),
-    dict(precision=5), dict(shift=-1.0), dict(shift_mode=3),
+    dict(precision=5), dict(shift=-1.0), dict(shift_mode=3), dict(tdvp=2),
 ])
 def test_init_rejects_bad_config_without_gpu(lib, bad):
     cfg = vmc.make_config(**bad)
@@ -95,5 +100,7 @@ def test_init_rejects_bad_lattice_without_gpu(lib, lat):
 def test_null_context_is_rejected(lib):
     assert lib.vmc_logpsi(None, 0, None, 0, None) == vmc.VMC_ERR_ARG
     assert lib.vmc_sr_step(None, 0, 0.1, None) == vmc.VMC_ERR_ARG
+    assert lib.vmc_tdvp_rhs(None, 0, None, 0, None, None, None, None) == vmc.VMC_ERR_ARG
+    assert lib.vmc_tdvp_step(None, 0, None, None, None, None) == vmc.VMC_ERR_ARG
     assert lib.vmc_kernel_launches(None) == 0
     lib.vmc_destroy(None)
