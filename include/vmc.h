@@ -94,11 +94,15 @@ typedef struct {
   double acceptance;            /* accepted / proposed Metropolis steps in this step        */
   int64_t n_samples;            /* Ns                                                       */
   int solver_iters;             /* CG or refinement iterations (0 for the direct solve)     */
-  double solver_relres;         /* ||S~ x - F|| / ||F|| of the returned update, FP64        */
+  double solver_relres;         /* ||S~ x - F|| / ||F|| of the returned update, FP64 (for    */
+                                /* the BF16-split dense path: the preconditioned CG's own    */
+                                /* recursive residual on the matrix-free FP32 operator)      */
   float ms_sample, ms_grad, ms_qfm, ms_solve, ms_update;  /* phase times (CUDA events)    */
   float ms_gram;                /* the S contraction kernel alone (CUDA events)             */
   int64_t launches;             /* kernels launched by this step                            */
   int solver_converged;         /* 1 if the solve reached cg_tol (the update was applied)   */
+  double solver_relres_explicit; /* ||S~ x - F|| / ||F|| recomputed with the operator after  */
+                                 /* an iterative solve (the recursive value is solver_relres) */
 } vmc_sr_stats;
 
 typedef struct vmc_ctx vmc_ctx;
@@ -308,6 +312,8 @@ typedef struct {
   int retries;                /* vmc_tdvp_step: rejected attempts                            */
   int rhs_evals;              /* right-hand-side evaluations of the call                    */
   float ms;                   /* device time of the call (CUDA events)                      */
+  float ms_gram, ms_eig;      /* the S/Q Gram and the eigen-decomposition of the first       */
+                              /* evaluation (CUDA events)                                    */
 } vmc_tdvp_stats;
 
 /* thetadot of the current parameters on a sample set.  spins dev int8 [n][N] with

@@ -436,6 +436,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         (e = dalloc(ctx, &ctx->sw.r, P)) || (e = dalloc(ctx, &ctx->sw.c, P)) ||
         (e = dalloc(ctx, &ctx->sw.r32, P)) || (e = dalloc(ctx, &ctx->sw.y32, P)) ||
         (e = dalloc(ctx, &ctx->sw.c32, P)) || (e = dalloc(ctx, &ctx->sw.scal, 8)) ||
+        (e = dalloc(ctx, &ctx->sw.scal_part, 256)) ||
         (e = dalloc(ctx, &ctx->sw.bar, 128)) ||
         (e = dalloc(ctx, &ctx->sw.fin, P)))
       return oom(e);
@@ -706,6 +707,40 @@ vmc_status vmc_sr_apply(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
 
 // The samples of one SR step (Ns = n_chains * samples_per_chain) from the lattice's chains:
 // spins, E_loc and tanh(theta) into the step buffers; *steps = Metropolis steps per chain.
+// The SR step's solve of S~ x = F.  With the BF16-split S (the tensor-core Gram writes the
+// factor's input) the system solved is that of the samples' own S applied matrix-free in
+// FP32 (the CG operator, O^H (O v) / n + D v), by conjugate gradients preconditioned with the
+// Cholesky factor of the BF16-split S~: the split's rounding (about 2^-16 of |S_kl|) then
+// only slows the iteration instead of moving the solution along the poorly conditioned
+// directions of S~.  Otherwise solve_core on the formed S.  *rel_ex (may be null) receives
+// the explicit residual of the preconditioned CG (the recursive one in *rel).
+static vmc_status step_solve(vmc_ctx* ctx, LatticeState& L, bool fused, int* iters, double* rel,
+                             double* rel_ex) {
+  const vmc_config& c = ctx->cfg;
+  if (!(fused && c.precision == VMC_PREC_BF16SPLIT)) {
+    vmc_status s = solve_core(ctx, L, fused ? nullptr : ctx->S, ctx->F, ctx->x, iters, rel);
+    if (rel_ex) *rel_ex = *rel;
+    return s;
+  }
+  ctx->sw.P = L.P;
+  CgProblem pb{ctx->s_spins, ctx->s_T, ctx->Ns, L.N, L.M, ctx->meanO, false, ctx->status};
+  CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches), "cg_prepare");
+  CgWork& w = ctx->cg;
+  PcgOperator apply = [&](const double2* v, double2* y) {
+    return cg_apply(pb, w, v, y, ctx->st, &ctx->launches);
+  };
+  double ex = 0.0;
+  CK(solve_pcg_factor(ctx->F, ctx->x, c.cg_tol, c.cg_maxit, c.solver == VMC_SOLVER_CHOLESKY_TC,
+                      apply, w.r, w.z, w.p, w.q, ctx->sw, ctx->status, ctx->st, &ctx->launches,
+                      iters, &ex, rel), "pcg");
+  if (rel_ex) *rel_ex = ex;
+  vmc_status s = check_status(ctx, "solve");
+  if (s) return s;
+  if (!(*rel <= c.cg_tol) || !(ex == ex))
+    return fail(ctx, VMC_ERR_NUMERIC, "preconditioned CG did not reach the tolerance");
+  return VMC_OK;
+}
+
 static vmc_status sample_step_set(vmc_ctx* ctx, LatticeState& L, int lattice, uint64_t* steps_out) {
   const vmc_config& c = ctx->cfg;
   SampleArgs A{};
@@ -758,7 +793,7 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   ++ctx->launches;
   CK(cudaEventRecord(ctx->ev[2], ctx->st), "sr_step");
   int iters = 0;
-  double rel = 0.0;
+  double rel = 0.0, rel_ex = NAN;
   bool converged = true;
   if (ctx->dense) {
     // 3. S (moments + centred X + Gram); with the tensor-core Gram and a mixed solver the
@@ -773,13 +808,13 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
     // 4. solve (synchronises).  The three-product BF16 split can leave S indefinite by up
     //    to the dropped lo.lo^T term; if the shifted matrix then has a non-positive pivot,
     //    S is formed again with the fourth product (PSD) and the solve repeated once.
-    s = solve_core(ctx, L, fused ? nullptr : ctx->S, ctx->F, ctx->x, &iters, &rel);
+    s = step_solve(ctx, L, fused, &iters, &rel, &rel_ex);
     if (s == VMC_ERR_NUMERIC && c.precision == VMC_PREC_BF16SPLIT) {
       if ((s = qfm_core(ctx, L, ctx->s_spins, ctx->s_E, Ns, c.precision, fused ? nullptr : ctx->S,
                         true, fused, true)))
         return s;
       ++ctx->psd_retries;
-      s = solve_core(ctx, L, fused ? nullptr : ctx->S, ctx->F, ctx->x, &iters, &rel);
+      s = step_solve(ctx, L, fused, &iters, &rel, &rel_ex);
     }
     if (s) return s;
   } else {
@@ -842,6 +877,7 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
     cudaEventElapsedTime(&stats->ms_gram, ctx->ev[6], ctx->ev[7]);
     stats->launches = ctx->launches - launches0;
     stats->solver_converged = converged ? 1 : 0;
+    stats->solver_relres_explicit = rel_ex == rel_ex ? rel_ex : rel;
   }
   if (!converged)
     return fail(ctx, VMC_ERR_NUMERIC, "CG did not reach cg_tol within cg_maxit iterations; "
@@ -901,7 +937,9 @@ static vmc_status tdvp_eval(vmc_ctx* ctx, int lattice, LatticeState& L, const in
     ctx->launches += 2;
   }
   CK(tdvp_moments(sp, ctx->s_T, ctx->s_E, wp, n, L.N, L.M, tw, ctx->st), "tdvp_moments");
+  if (st) cudaEventRecord(ctx->ev[2], ctx->st);
   CK(tdvp_gram(sp, ctx->s_T, ctx->s_E, wp, n, L.N, L.M, tw, ctx->st), "tdvp_gram");
+  if (st) cudaEventRecord(ctx->ev[3], ctx->st);
   ctx->launches += 5;
   if (o.shift > 0.0) {
     CK(tdvp_shift(tw, P, o.shift, ctx->st), "tdvp_shift");
@@ -909,7 +947,9 @@ static vmc_status tdvp_eval(vmc_ctx* ctx, int lattice, LatticeState& L, const in
   }
   if (save_S0) CK(cudaMemcpyAsync(tw.S0, tw.S, sizeof(double2) * P * P, cudaMemcpyDeviceToDevice,
                                   ctx->st), "tdvp_S0");
+  if (st) cudaEventRecord(ctx->ev[4], ctx->st);
   CK(tdvp_eig(tw, P, o.jacobi_max_sweeps > 0 ? o.jacobi_max_sweeps : 40, 1e-14, ctx->st), "jacobi");
+  if (st) cudaEventRecord(ctx->ev[5], ctx->st);
   const bool snr = o.eps_snr > 0.0 && wp == nullptr;
   CK(tdvp_solve(tw, P, snr, o.eps_pinv, o.pinv_soft, o.eps_snr, (double)n, o.gamma_re,
                 o.gamma_im, out, ctx->st), "tdvp_solve");
@@ -930,6 +970,8 @@ static vmc_status tdvp_eval(vmc_ctx* ctx, int lattice, LatticeState& L, const in
     st->snr_min = ls[3];
     st->jacobi_sweeps = (int)info[0];
     st->jacobi_off = info[1];
+    cudaEventElapsedTime(&st->ms_gram, ctx->ev[2], ctx->ev[3]);
+    cudaEventElapsedTime(&st->ms_eig, ctx->ev[4], ctx->ev[5]);
   }
   return VMC_OK;
 }

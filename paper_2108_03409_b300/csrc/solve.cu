@@ -1637,6 +1637,160 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
   return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------------------
+// Conjugate gradients on an exactly applied operator A (a callback), preconditioned by the
+// FP32 Cholesky factor of an approximation of A held in w.A32 (lower triangle, shift
+// included).  With the factor of the BF16-split S this solves the system of the samples'
+// own S to the accuracy of the operator, whatever the split's rounding, since the factor
+// only preconditions.  Dot products: fixed-order FP64 block partials summed on the host.
+// ---------------------------------------------------------------------------------------
+constexpr int PCG_DOT_BLOCKS = 128;
+
+// part[b] = Re sum a^H b, part[nb + b] = sum |a|^2 over this block's share
+__global__ void k_pcg_dots(const double2* __restrict__ a, const double2* __restrict__ b, int64_t P,
+                           double* part) {
+  __shared__ double s1[256], s2[256];
+  double d = 0.0, n2 = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double2 u = a[k], v = b[k];
+    d = fma(u.x, v.x, fma(u.y, v.y, d));
+    n2 = fma(u.x, u.x, fma(u.y, u.y, n2));
+  }
+  s1[threadIdx.x] = d;
+  s2[threadIdx.x] = n2;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s1[0];
+    part[gridDim.x + blockIdx.x] = s2[0];
+  }
+}
+
+// x += alpha p, r -= alpha q
+__global__ void k_pcg_update(double2* x, double2* r, const double2* p, const double2* q,
+                             double alpha, int64_t P) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    x[k].x = fma(alpha, p[k].x, x[k].x);
+    x[k].y = fma(alpha, p[k].y, x[k].y);
+    r[k].x = fma(-alpha, q[k].x, r[k].x);
+    r[k].y = fma(-alpha, q[k].y, r[k].y);
+  }
+}
+
+// p = z + beta p
+__global__ void k_pcg_dir(double2* p, const double2* z, double beta, int64_t P) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    p[k] = make_double2(fma(beta, p[k].x, z[k].x), fma(beta, p[k].y, z[k].y));
+  }
+}
+
+// z = D c (the equilibrated factor's correction mapped back)
+__global__ void k_set_f32(double2* __restrict__ z, const float2* __restrict__ c, int64_t P,
+                          const float* __restrict__ dsc) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const double d = dsc ? (double)dsc[k] : 1.0;
+    z[k] = make_double2((double)c[k].x * d, (double)c[k].y * d);
+  }
+}
+
+// r = F - q
+__global__ void k_sub(const double2* F, const double2* q, double2* r, int64_t P) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
+       k += (int64_t)gridDim.x * blockDim.x)
+    r[k] = make_double2(F[k].x - q[k].x, F[k].y - q[k].y);
+}
+
+static cudaError_t pcg_dots(const double2* a, const double2* b, int64_t P, double* part,
+                            cudaStream_t st, double* dot, double* n2) {
+  k_pcg_dots<<<PCG_DOT_BLOCKS, 256, 0, st>>>(a, b, P, part);
+  VMC_TRY(cudaGetLastError());
+  double h[2 * PCG_DOT_BLOCKS];
+  VMC_TRY(cudaMemcpyAsync(h, part, sizeof(h), cudaMemcpyDeviceToHost, st));
+  VMC_TRY(cudaStreamSynchronize(st));
+  double d = 0.0, n = 0.0;
+  for (int b2 = 0; b2 < PCG_DOT_BLOCKS; ++b2) {
+    d += h[b2];
+    n += h[PCG_DOT_BLOCKS + b2];
+  }
+  *dot = d;
+  *n2 = n;
+  return cudaSuccess;
+}
+
+cudaError_t solve_pcg_factor(const double2* F, double2* x, double tol, int maxit, bool tc,
+                             const PcgOperator& apply, double2* r, double2* z, double2* p,
+                             double2* q, SolveWork& w, unsigned* status, cudaStream_t st,
+                             int64_t* launches, int* iters, double* relres, double* relres_rec) {
+  const int64_t P = w.P;
+  k_eq_scales<<<grid_for(P, 256, 1024), 256, 0, st>>>(w.A32, P, w.dsc);
+  k_equilibrate<<<(unsigned)P, 256, 0, st>>>(w.A32, P, w.dsc);
+  *launches += 2;
+  if (tc && P > NBO) VMC_TRY(factor_tc(w.A32, w.D32, P, w, status, st, launches));
+  else VMC_TRY(factor<float2>(w.A32, w.D32, P, status, st, launches));
+  VMC_TRY(invert_blocks<float2>(w.A32, P, w, st, launches));
+  const unsigned g = grid_for(P, 256, 1024);
+  auto precondition = [&](const double2* rin, double2* zout) -> cudaError_t {
+    k_to_f32<<<g, 256, 0, st>>>(rin, w.r32, P, w.dsc);
+    VMC_TRY(chol_solve<float2>(w.A32, w.D32, P, w.r32, w.y32, w.c32, w, status, st, launches));
+    k_set_f32<<<g, 256, 0, st>>>(zout, w.c32, P, w.dsc);
+    *launches += 2;
+    return cudaGetLastError();
+  };
+  VMC_TRY(cudaMemsetAsync(x, 0, P * sizeof(double2), st));
+  VMC_TRY(cudaMemcpyAsync(r, F, P * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  VMC_TRY(precondition(r, z));
+  double rz = 0.0, f2 = 0.0;
+  VMC_TRY(pcg_dots(r, z, P, w.scal_part, st, &rz, &f2));
+  ++*launches;
+  const double fn = std::sqrt(f2);
+  VMC_TRY(cudaMemcpyAsync(p, z, P * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  double rel = fn > 0.0 ? 1.0 : 0.0;
+  int it = 0;
+  for (; it < std::max(1, maxit) && fn > 0.0; ++it) {
+    VMC_TRY(apply(p, q));
+    double pq = 0.0, dummy = 0.0;
+    VMC_TRY(pcg_dots(p, q, P, w.scal_part, st, &pq, &dummy));
+    if (!(pq > 0.0)) { rel = NAN; break; }
+    const double alpha = rz / pq;
+    k_pcg_update<<<g, 256, 0, st>>>(x, r, p, q, alpha, P);
+    VMC_TRY(precondition(r, z));
+    double rz_new = 0.0, r2 = 0.0;
+    VMC_TRY(pcg_dots(r, z, P, w.scal_part, st, &rz_new, &r2));
+    *launches += 3;
+    rel = std::sqrt(r2) / fn;
+    if (!(rel == rel)) break;
+    if (rel <= tol) { ++it; break; }
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    k_pcg_dir<<<g, 256, 0, st>>>(p, z, beta, P);
+    ++*launches;
+  }
+  if (relres_rec) *relres_rec = rel;
+  // explicit residual of the returned x with the operator itself
+  double rel_ex = rel;
+  if (fn > 0.0 && rel == rel) {
+    VMC_TRY(apply(x, q));
+    k_sub<<<g, 256, 0, st>>>(F, q, r, P);
+    double d0 = 0.0, e2 = 0.0;
+    VMC_TRY(pcg_dots(r, r, P, w.scal_part, st, &d0, &e2));
+    *launches += 2;
+    rel_ex = std::sqrt(e2) / fn;
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = rel_ex;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_update(double2* params, const double2* x, int64_t P, double dt,
                           cudaStream_t st) {
   k_update<<<grid_for(P, 256, 4096), 256, 0, st>>>(params, x, P, dt);

@@ -3,6 +3,7 @@
 #pragma once
 #include <algorithm>
 #include <cstdint>
+#include <functional>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -148,6 +149,7 @@ struct SolveWork {
   float2* y32;     // [P]
   float2* c32;     // [P]
   double* scal;    // [8] device scalars
+  double* scal_part = nullptr;  // [256] block partials of the preconditioned CG's dots
   unsigned* bar;   // [128] the cooperative kernels' grid barrier, abort word and step counters
   double2* fin;    // [P] final right-hand sides of the triangular solves (float2 or double2 entries)
   float2 *T32f, *T32b;    // [ceil(P/256)][256][256] inverses of the 256-wide diagonal blocks
@@ -175,6 +177,16 @@ cudaError_t solve_cholesky_mixed(const double2* F, double2* x, double nu, int mo
                                  int maxit, bool tc, SolveWork& w, unsigned* status,
                                  cudaStream_t st, int64_t* launches, int* iters,
                                  double* relres);
+// Preconditioned CG with an exactly applied operator y = A v (callback) and the FP32
+// Cholesky factor of w.A32 (factored here; tensor-core Schur updates when tc) as the
+// preconditioner; r, z, p, q are [P] work vectors.  Stops when the recursive residual is at
+// most tol ||F|| (relres_rec) or after maxit iterations; relres is the explicit residual
+// ||F - A x|| / ||F|| of the returned x.  Synchronises every iteration.
+using PcgOperator = std::function<cudaError_t(const double2*, double2*)>;
+cudaError_t solve_pcg_factor(const double2* F, double2* x, double tol, int maxit, bool tc,
+                             const PcgOperator& apply, double2* r, double2* z, double2* p,
+                             double2* q, SolveWork& w, unsigned* status, cudaStream_t st,
+                             int64_t* launches, int* iters, double* relres, double* relres_rec);
 // FP64 relative residual ||(S + shift) x - F|| / ||F|| (synchronises).
 cudaError_t residual_fp64(const double2* S, const double2* F, const double2* x, double nu,
                           int mode, SolveWork& w, cudaStream_t st, double* relres);

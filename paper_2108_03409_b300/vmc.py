@@ -53,7 +53,8 @@ class vmc_sr_stats(ctypes.Structure):
                 ("ms_sample", ctypes.c_float), ("ms_grad", ctypes.c_float),
                 ("ms_qfm", ctypes.c_float), ("ms_solve", ctypes.c_float),
                 ("ms_update", ctypes.c_float), ("ms_gram", ctypes.c_float),
-                ("launches", ctypes.c_int64), ("solver_converged", ctypes.c_int)]
+                ("launches", ctypes.c_int64), ("solver_converged", ctypes.c_int),
+                ("solver_relres_explicit", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -74,7 +75,8 @@ class vmc_tdvp_stats(ctypes.Structure):
                 ("snr_min", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int),
                 ("jacobi_off", ctypes.c_double), ("tau_used", ctypes.c_double),
                 ("tau_next", ctypes.c_double), ("delta", ctypes.c_double),
-                ("retries", ctypes.c_int), ("rhs_evals", ctypes.c_int), ("ms", ctypes.c_float)]
+                ("retries", ctypes.c_int), ("rhs_evals", ctypes.c_int), ("ms", ctypes.c_float),
+                ("ms_gram", ctypes.c_float), ("ms_eig", ctypes.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -51,6 +51,7 @@ int main(void) {
   F(vmc_sr_stats, solver_relres) F(vmc_sr_stats, ms_update) F(vmc_sr_stats, solver_converged)
   F(vmc_tdvp_opts, eps_snr) F(vmc_tdvp_opts, exact) F(vmc_tdvp_opts, jacobi_max_sweeps)
   F(vmc_tdvp_stats, kept) F(vmc_tdvp_stats, jacobi_off) F(vmc_tdvp_stats, ms)
+  F(vmc_tdvp_stats, ms_eig)
   return 0;
 }
 """
