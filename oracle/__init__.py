@@ -30,6 +30,8 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   made_sample     -- pinned: chi-square of the sample histogram against q
   tdvp.*          -- regularised TDVP right-hand side and adaptive Heun integrator
                      (oracle/tdvp.py); pinned in tests/test_oracle_tdvp_pins.py
+  excited.*       -- excited-state search by projection (oracle/excited.py); pinned in
+                     tests/test_oracle_excited_pins.py
 """
 from __future__ import annotations
 
