@@ -340,6 +340,39 @@ vmc_status vmc_tdvp_rhs(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
 vmc_status vmc_tdvp_step(vmc_ctx* ctx, int lattice, const vmc_tdvp_opts* opts, double* t,
                          double* tau, vmc_tdvp_stats* stats);
 
+/* ---- excited states by projection (section "Finding low-energy states") ----------------
+ * With a converged ground state phi on lattice ref_lattice (same model size, its parameters
+ * fixed), the excited-state ansatz of `lattice` is Psi = psi - lambda phi (Eq.
+ * excited_state_ansatz), lambda = <phi|psi>/<phi|phi> = <psi/phi> over |phi|^2.  With
+ * rho(s) = lambda phi(s)/psi(s): E_loc^Psi = (E_loc^psi - rho E_loc^phi)/(1 - rho) (both with
+ * the Hamiltonian of `lattice`), O^Psi_k = O^psi_k / (1 - rho).  Expectations under |Psi|^2
+ * are taken over samples of |psi|^2 with importance weights |1 - rho|^2 (times the Born
+ * weights of psi for exact sums).  Needs a context created with tdvp = 1. */
+typedef struct {
+  double lambda_re, lambda_im;  /* the overlap ratio used                                    */
+  double ess;                   /* (sum w)^2 / sum w^2 of the importance weights              */
+  vmc_tdvp_stats tdvp;          /* the right-hand side's statistics (energy of Psi, S, ...)   */
+} vmc_excited_stats;
+
+/* lambda from samples of |phi|^2: spins_phi dev int8 [n][N] (n <= Ns), or NULL: Ns
+ * Metropolis samples of ref_lattice's chains (exact = 0) or all 2^N states with phi's Born
+ * weights (exact = 1).  lambda_out host double [2].  Synchronises. */
+vmc_status vmc_excited_lambda(vmc_ctx* ctx, int lattice, int ref_lattice, const int8_t* spins_phi,
+                              int64_t n, int exact, double* lambda_out);
+/* SR direction thetadot = -S^+ F of Psi (opts: gamma, shift, eps_pinv as for vmc_tdvp_rhs;
+ * SNR damping is not applied to importance-weighted sets) on samples of |psi|^2: spins_psi
+ * dev int8 [n][N] (n <= Ns), or NULL: Ns Metropolis samples of lattice's chains (opts->exact
+ * = 0) or all basis states (opts->exact = 1).  lambda host double [2], or NULL for the last
+ * value vmc_excited_lambda computed.  thetadot dev double [P][2]; stats may be NULL.
+ * Synchronises. */
+vmc_status vmc_excited_rhs(vmc_ctx* ctx, int lattice, int ref_lattice, const int8_t* spins_psi,
+                           int64_t n, const double* lambda, const vmc_tdvp_opts* opts,
+                           double* thetadot, vmc_excited_stats* stats);
+/* One step of the search: lambda from fresh samples of |phi|^2 (or exact sums), then one
+ * Euler step theta <- theta + dt thetadot with thetadot of vmc_excited_rhs (gamma = 1: SR). */
+vmc_status vmc_excited_step(vmc_ctx* ctx, int lattice, int ref_lattice, double dt,
+                            const vmc_tdvp_opts* opts, vmc_excited_stats* stats);
+
 /* Failure-path self-test (no GPU fault): which = 0 runs the cooperative kernels' bounded
  * flag wait on a word that nothing sets, which = 1 the tensor-core kernels' bounded mbarrier
  * wait on a barrier that nothing arrives at, which = 2 the triangular solves' bounded poll

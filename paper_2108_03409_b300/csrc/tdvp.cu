@@ -102,6 +102,30 @@ __global__ void k_born_weights(const float2* lp, int64_t n, double* w, unsigned*
   for (int64_t k = threadIdx.x; k < n; k += blockDim.x) w[k] *= inv;
 }
 
+// w_out = w_in / sum(w_in) (one block); a non-positive or non-finite sum sets the status
+// (sums, if given: sum w and sum w^2 of the input)
+__global__ void k_normalize_weights(const double* w_in, int64_t n, double* w_out,
+                                    unsigned* status, double* sums) {
+  __shared__ double sh[32];
+  double z = 0.0, z2 = 0.0;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+    z += w_in[k];
+    z2 += w_in[k] * w_in[k];
+  }
+  z = block_sum(z, sh);
+  z2 = block_sum(z2, sh);
+  if (sums && threadIdx.x == 0) {
+    sums[0] = z;
+    sums[1] = z2;
+  }
+  if (!(z > 0.0) || !isfinite(z)) {
+    if (threadIdx.x == 0) flag_error(status, DEV_ERR_NUMERIC);
+    return;
+  }
+  const double inv = 1.0 / z;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) w_out[k] = w_in[k] * inv;
+}
+
 // ---------------------------------------------------------------------------------------
 // weighted energy statistics: out[0..3] = <E>.re, <E>.im, <|E - <E>|^2>, stderr; one block.
 // w == null: uniform weights 1/n (stderr = sqrt(var / n)); otherwise stderr = 0 (exact).
@@ -138,6 +162,7 @@ __global__ void k_tdvp_energy(const float2* E, const double* w, int64_t n, doubl
 // chunk of samples; partial[chunk][k] = {sum w O_k, sum w conj(O_k)(E - <E>)}.
 __global__ void k_tdvp_moments(const int8_t* __restrict__ spins, const float2* __restrict__ T,
                                const float2* __restrict__ E, const double* __restrict__ w,
+                               const float2* __restrict__ osc,
                                const double* __restrict__ estats, int64_t n, int N, int M,
                                int64_t P, int64_t chunk, double2* __restrict__ partial) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -148,7 +173,8 @@ __global__ void k_tdvp_moments(const int8_t* __restrict__ spins, const float2* _
   double mr = 0, mi = 0, fr = 0, fi = 0;
   for (int64_t q = q0; q < q1; ++q) {
     const double wq = w ? w[q] : u;
-    const double2 o = o_entry(spins + q * N, T + q * M, N, M, k);
+    double2 o = o_entry(spins + q * N, T + q * M, N, M, k);
+    if (osc) o = cmul_d(o, make_double2((double)osc[q].x, (double)osc[q].y));
     const double dr = (double)E[q].x - er, di = (double)E[q].y - ei;
     mr = fma(wq, o.x, mr);
     mi = fma(wq, o.y, mi);
@@ -193,9 +219,9 @@ __device__ __forceinline__ void tri_tile(int64_t t, int* bm, int* bn) {
 
 __global__ void __launch_bounds__(256) k_tdvp_gram(
     const int8_t* __restrict__ spins, const float2* __restrict__ T, const float2* __restrict__ E,
-    const double* __restrict__ w, const double* __restrict__ estats,
-    const double2* __restrict__ meanO, int64_t n, int N, int M, int64_t P, int64_t chunk,
-    int64_t ntiles, double2* __restrict__ partial) {
+    const double* __restrict__ w, const float2* __restrict__ osc,
+    const double* __restrict__ estats, const double2* __restrict__ meanO, int64_t n, int N,
+    int M, int64_t P, int64_t chunk, int64_t ntiles, double2* __restrict__ partial) {
   __shared__ double2 Ok[kBatch][kTile];
   __shared__ double2 Ol[kBatch][kTile];
   __shared__ double ws[kBatch], wq[kBatch];
@@ -221,7 +247,8 @@ __global__ void __launch_bounds__(256) k_tdvp_gram(
       double2 v = make_double2(0, 0);
       if (qs < nb && kk < P) {
         const int64_t q = qb + qs;
-        const double2 o = o_entry(spins + q * N, T + q * M, N, M, kk);
+        double2 o = o_entry(spins + q * N, T + q * M, N, M, kk);
+        if (osc) o = cmul_d(o, make_double2((double)osc[q].x, (double)osc[q].y));
         const double2 m = meanO[kk];
         v = make_double2(o.x - m.x, o.y - m.y);
       }
@@ -617,8 +644,15 @@ cudaError_t launch_born_weights(const float2* lp, int64_t n, double* w, unsigned
   return cudaGetLastError();
 }
 
+cudaError_t launch_normalize_weights(const double* w_in, int64_t n, double* w_out,
+                                     unsigned* status, cudaStream_t st, double* sums) {
+  k_normalize_weights<<<1, 1024, 0, st>>>(w_in, n, w_out, status, sums);
+  return cudaGetLastError();
+}
+
 cudaError_t tdvp_moments(const int8_t* spins, const float2* T, const float2* E, const double* w,
-                         int64_t n, int N, int M, TdvpWork& tw, cudaStream_t st) {
+                         const float2* osc, int64_t n, int N, int M, TdvpWork& tw,
+                         cudaStream_t st) {
   const int64_t P = (int64_t)N + M + (int64_t)N * M;
   k_tdvp_energy<<<1, 1024, 0, st>>>(E, w, n, tw.estats, tw.status);
   cudaError_t e = cudaGetLastError();
@@ -630,14 +664,15 @@ cudaError_t tdvp_moments(const int8_t* spins, const float2* T, const float2* E, 
   const int64_t chunk = (n + chunks - 1) / chunks;
   chunks = (n + chunk - 1) / chunk;
   k_tdvp_moments<<<dim3((unsigned)kb, (unsigned)chunks), 256, 0, st>>>(
-      spins, T, E, w, tw.estats, n, N, M, P, chunk, tw.mom_part);
+      spins, T, E, w, osc, tw.estats, n, N, M, P, chunk, tw.mom_part);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_tdvp_moments_reduce<<<(unsigned)kb, 256, 0, st>>>(tw.mom_part, (int)chunks, P, tw.meanO, tw.F);
   return cudaGetLastError();
 }
 
 cudaError_t tdvp_gram(const int8_t* spins, const float2* T, const float2* E, const double* w,
-                      int64_t n, int N, int M, TdvpWork& tw, cudaStream_t st) {
+                      const float2* osc, int64_t n, int N, int M, TdvpWork& tw,
+                      cudaStream_t st) {
   const int64_t P = (int64_t)N + M + (int64_t)N * M;
   const int64_t tiles_1d = (P + kTile - 1) / kTile;
   const int64_t ntiles = tiles_1d * (tiles_1d + 1) / 2;
@@ -647,7 +682,7 @@ cudaError_t tdvp_gram(const int8_t* spins, const float2* T, const float2* E, con
   const int64_t chunk = (n + chunks - 1) / chunks;
   chunks = (n + chunk - 1) / chunk;
   k_tdvp_gram<<<dim3((unsigned)ntiles, (unsigned)chunks), 256, 0, st>>>(
-      spins, T, E, w, tw.estats, tw.meanO, n, N, M, P, chunk, ntiles, tw.gram_part);
+      spins, T, E, w, osc, tw.estats, tw.meanO, n, N, M, P, chunk, ntiles, tw.gram_part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_tdvp_gram_reduce<<<(unsigned)ntiles, kTile * kTile, 0, st>>>(tw.gram_part, (int)chunks, ntiles,

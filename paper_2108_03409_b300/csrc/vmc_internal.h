@@ -309,18 +309,31 @@ struct TdvpWork {
   double* lstats = nullptr;        // [4] lambda_1, lambda_min, kept components, min SNR
   double2* vec[8] = {};            // [Pcap] integrator vectors
   double* qpart = nullptr;         // [Pcap/256 + 1] quadratic-form partials
+  // excited-state search (projected ansatz)
+  float2* lp2 = nullptr;           // [ncap] log amplitudes of the reference state
+  float2* e2 = nullptr;            // [ncap] local energies of the reference state
+  float2* osc = nullptr;           // [ncap] 1 / (1 - rho) per sample
+  float2* eexc = nullptr;          // [ncap] local energies of the projected ansatz
+  double* wraw = nullptr;          // [ncap] unnormalised weights
+  double* olap = nullptr;          // [8] overlap ratio lambda (see excited.cu)
 };
 int64_t tdvp_gram_chunks(int64_t n, int64_t P, int n_sm);
 int64_t tdvp_gram_partial_doubles2(int64_t n, int64_t P, int n_sm);
 cudaError_t launch_enum_states(int8_t* spins, int N, int64_t n, cudaStream_t st);
 cudaError_t launch_born_weights(const float2* lp, int64_t n, double* w, unsigned* status,
                                 cudaStream_t st);
-// weighted <E> (tw.estats), <O> (tw.meanO) and F (tw.F); w = null: uniform 1/n
+// weighted <E> (tw.estats), <O> (tw.meanO) and F (tw.F); w = null: uniform 1/n (w must be
+// normalised); osc = null or a per-sample complex factor multiplying every O_k(s)
 cudaError_t tdvp_moments(const int8_t* spins, const float2* T, const float2* E, const double* w,
-                         int64_t n, int N, int M, TdvpWork& tw, cudaStream_t st);
+                         const float2* osc, int64_t n, int N, int M, TdvpWork& tw,
+                         cudaStream_t st);
 // weighted S (tw.S) and energy-weighted Q (tw.Q), full Hermitian, FP64
 cudaError_t tdvp_gram(const int8_t* spins, const float2* T, const float2* E, const double* w,
-                      int64_t n, int N, int M, TdvpWork& tw, cudaStream_t st);
+                      const float2* osc, int64_t n, int N, int M, TdvpWork& tw,
+                      cudaStream_t st);
+// w_out = w_in / sum(w_in); sums (may be null): sum w and sum w^2 of the input
+cudaError_t launch_normalize_weights(const double* w_in, int64_t n, double* w_out,
+                                     unsigned* status, cudaStream_t st, double* sums = nullptr);
 // tw.S_kk *= 1 + nu
 cudaError_t tdvp_shift(TdvpWork& tw, int64_t P, double nu, cudaStream_t st);
 // tw.S = tw.V diag(tw.lam) tw.V^H (cooperative Jacobi on a copy in tw.A)
@@ -329,6 +342,16 @@ cudaError_t tdvp_eig(TdvpWork& tw, int64_t P, int max_sweeps, double tol, cudaSt
 cudaError_t tdvp_solve(TdvpWork& tw, int64_t P, bool snr, double eps_pinv, int soft,
                        double eps_snr, double n_eff, double g_re, double g_im, double2* out,
                        cudaStream_t st);
+// ---- excited.cu -----------------------------------------------------------------------
+// overlap ratio lambda = exp(out[0]) (out[1] + i out[2]) from log amplitudes of psi and phi
+// on samples of |phi|^2 (weights w or uniform)
+cudaError_t launch_excited_lambda(const float2* lpsi, const float2* lphi, const double* w,
+                                  int64_t n, double* out, unsigned* status, cudaStream_t st);
+// per-sample 1/(1 - rho), unnormalised importance weights |1 - rho|^2 (x pw) and E_loc^Psi
+cudaError_t launch_excited_prep(const float2* lpsi, const float2* lphi, const float2* epsi,
+                                const float2* ephi, const double* pw, const double* olap,
+                                int64_t n, float2* osc, double* wraw, float2* eexc,
+                                cudaStream_t st);
 cudaError_t launch_axpy2(const double2* y, double a, const double2* k1, double b, const double2* k2,
                          int64_t P, double2* out, cudaStream_t st);
 cudaError_t launch_quad_form(const double2* S, const double2* x, const double2* y, int64_t P,

@@ -82,6 +82,11 @@ class vmc_tdvp_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class vmc_excited_stats(ctypes.Structure):
+    _fields_ = [("lambda_re", ctypes.c_double), ("lambda_im", ctypes.c_double),
+                ("ess", ctypes.c_double), ("tdvp", vmc_tdvp_stats)]
+
+
 EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
             "vmc_set_chains", "vmc_get_chains", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
             "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
@@ -89,7 +94,8 @@ EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_
             "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
             "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned", "vmc_sample_all",
             "vmc_autotuned_warps_per_block", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout",
-            "vmc_tdvp_rhs", "vmc_tdvp_step"]
+            "vmc_tdvp_rhs", "vmc_tdvp_step", "vmc_excited_lambda", "vmc_excited_rhs",
+            "vmc_excited_step"]
 
 _lib = None
 
@@ -142,6 +148,11 @@ def load(path: str = LIB_PATH):
                                ctypes.POINTER(vmc_tdvp_stats)]),
         "vmc_tdvp_step": (i32, [P, i32, ctypes.POINTER(vmc_tdvp_opts), ctypes.POINTER(f64),
                                 ctypes.POINTER(f64), ctypes.POINTER(vmc_tdvp_stats)]),
+        "vmc_excited_lambda": (i32, [P, i32, i32, P, i64, i32, P]),
+        "vmc_excited_rhs": (i32, [P, i32, i32, P, i64, P, ctypes.POINTER(vmc_tdvp_opts), P,
+                                  ctypes.POINTER(vmc_excited_stats)]),
+        "vmc_excited_step": (i32, [P, i32, i32, f64, ctypes.POINTER(vmc_tdvp_opts),
+                                   ctypes.POINTER(vmc_excited_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -411,3 +422,31 @@ def vmc_tdvp_step(ctx, lattice, opts, t, tau):
     _check(ctx, load().vmc_tdvp_step(ctx, lattice, ctypes.byref(opts), ctypes.byref(tt),
                                      ctypes.byref(hh), ctypes.byref(st)))
     return tt.value, hh.value, st
+
+
+def vmc_excited_lambda(ctx, lattice, ref_lattice, spins_phi=None, exact=0) -> complex:
+    """lambda = <psi/phi> over |phi|^2 (caller's samples, Metropolis samples or exact sums)."""
+    import numpy as np
+    out = np.zeros(2, dtype=np.float64)
+    n = spins_phi.shape[0] if spins_phi is not None else 0
+    _check(ctx, load().vmc_excited_lambda(ctx, lattice, ref_lattice, _ptr(spins_phi), n, int(exact),
+                                          out.ctypes.data))
+    return complex(out[0], out[1])
+
+
+def vmc_excited_rhs(ctx, lattice, ref_lattice, opts, thetadot, spins_psi=None, lam=None):
+    import numpy as np
+    st = vmc_excited_stats()
+    n = spins_psi.shape[0] if spins_psi is not None else 0
+    la = None if lam is None else np.array([complex(lam).real, complex(lam).imag], np.float64)
+    _check(ctx, load().vmc_excited_rhs(ctx, lattice, ref_lattice, _ptr(spins_psi), n,
+                                       None if la is None else la.ctypes.data, ctypes.byref(opts),
+                                       _ptr(thetadot), ctypes.byref(st)))
+    return st
+
+
+def vmc_excited_step(ctx, lattice, ref_lattice, dt, opts) -> vmc_excited_stats:
+    st = vmc_excited_stats()
+    _check(ctx, load().vmc_excited_step(ctx, lattice, ref_lattice, float(dt), ctypes.byref(opts),
+                                        ctypes.byref(st)))
+    return st

@@ -46,6 +46,8 @@ int main(void) {
   printf("vmc_lattice %zu\nvmc_config %zu\nvmc_sr_stats %zu\n", sizeof(vmc_lattice),
          sizeof(vmc_config), sizeof(vmc_sr_stats));
   printf("vmc_tdvp_opts %zu\nvmc_tdvp_stats %zu\n", sizeof(vmc_tdvp_opts), sizeof(vmc_tdvp_stats));
+  printf("vmc_excited_stats %zu\n", sizeof(vmc_excited_stats));
+  F(vmc_excited_stats, ess) F(vmc_excited_stats, tdvp) F(vmc_sr_stats, solver_relres_explicit)
   F(vmc_lattice, J) F(vmc_lattice, alpha) F(vmc_config, shift) F(vmc_config, cg_tol)
   F(vmc_config, solver) F(vmc_config, tdvp) F(vmc_sr_stats, n_samples)
   F(vmc_sr_stats, solver_relres) F(vmc_sr_stats, ms_update) F(vmc_sr_stats, solver_converged)
@@ -67,6 +69,7 @@ int main(void) {
     assert int(got["vmc_sr_stats"]) == ctypes.sizeof(vmc.vmc_sr_stats)
     assert int(got["vmc_tdvp_opts"]) == ctypes.sizeof(vmc.vmc_tdvp_opts)
     assert int(got["vmc_tdvp_stats"]) == ctypes.sizeof(vmc.vmc_tdvp_stats)
+    assert int(got["vmc_excited_stats"]) == ctypes.sizeof(vmc.vmc_excited_stats)
     for key, val in got.items():
         if "." in key:
             t, f = key.split(".")
@@ -103,5 +106,6 @@ def test_null_context_is_rejected(lib):
     assert lib.vmc_sr_step(None, 0, 0.1, None) == vmc.VMC_ERR_ARG
     assert lib.vmc_tdvp_rhs(None, 0, None, 0, None, None, None, None) == vmc.VMC_ERR_ARG
     assert lib.vmc_tdvp_step(None, 0, None, None, None, None) == vmc.VMC_ERR_ARG
+    assert lib.vmc_excited_step(None, 0, 1, 0.1, None, None) == vmc.VMC_ERR_ARG
     assert lib.vmc_kernel_launches(None) == 0
     lib.vmc_destroy(None)
