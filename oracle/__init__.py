@@ -32,6 +32,8 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                      (oracle/tdvp.py); pinned in tests/test_oracle_tdvp_pins.py
   excited.*       -- excited-state search by projection (oracle/excited.py); pinned in
                      tests/test_oracle_excited_pins.py
+  ar.*            -- the autoregressive network as the ansatz (oracle/ar.py); pinned in
+                     tests/test_oracle_ar_pins.py
 """
 from __future__ import annotations
 
