@@ -84,6 +84,8 @@ typedef struct {
   int made_batch;           /* training batch of the learned proposal (0 = 4096)               */
   int tdvp;                 /* 1: allocate the TDVP workspaces (vmc_tdvp_rhs / vmc_tdvp_step;  */
                             /* every lattice's P <= 4096)                                      */
+  int ar_ansatz;            /* 1: also allocate the workspaces of the autoregressive ansatz    */
+                            /* (vmc_ar_*; needs made_hidden > 0 and a dense solver)            */
 } vmc_config;
 
 /* Statistics of one SR step (host struct filled by vmc_sr_step). */
@@ -372,6 +374,38 @@ vmc_status vmc_excited_rhs(vmc_ctx* ctx, int lattice, int ref_lattice, const int
  * Euler step theta <- theta + dt thetadot with thetadot of vmc_excited_rhs (gamma = 1: SR). */
 vmc_status vmc_excited_step(vmc_ctx* ctx, int lattice, int ref_lattice, double dt,
                             const vmc_tdvp_opts* opts, vmc_excited_stats* stats);
+
+/* ---- the autoregressive network as the ansatz (section "Autoregressive neural quantum
+ * states"; requires ar_ansatz = 1) --------------------------------------------------------
+ * psi(s) = q(s)^(1/2) with q the masked autoregressive network described above for the
+ * learned proposal (same layout and width made_hidden, its own FP64 master parameters):
+ * q is normalised, so samples are exact independent draws (no Markov chain).  Real
+ * parameters, real positive amplitudes; P = made parameter count (<= 16384).  The SR step is
+ * real: O_k = (1/2) d log q / d theta_k, E_loc(s) = sum_s' H_ss' (q(s')/q(s))^(1/2),
+ * theta <- theta - dt Re[(S + shift)^-1 F] with the context's dense solver; S is formed by
+ * the FP32 SIMT Gram, and parameters whose S row is exactly zero (masked weights, inactive
+ * units) are left unchanged. */
+vmc_status vmc_ar_set_params(vmc_ctx* ctx, int lattice, const double* params_host);
+vmc_status vmc_ar_get_params(vmc_ctx* ctx, int lattice, double* params_host);
+/* log psi = (1/2) log q: spins dev int8 [n][N], logpsi dev float [n]. */
+vmc_status vmc_ar_logpsi(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                         float* logpsi);
+/* n exact draws (autoregressive sampling with the Philox stream of vmc_made_sample, round
+ * counter of the lattice): spins_out dev int8 [n][N], logpsi_out dev float [n] (may be NULL). */
+vmc_status vmc_ar_sample(vmc_ctx* ctx, int lattice, int64_t n, int8_t* spins_out,
+                         float* logpsi_out);
+/* E_loc for a batch (n <= Ns): eloc dev float [n][2] (imaginary part 0). */
+vmc_status vmc_ar_local_energy(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n,
+                               float* eloc);
+/* Per-sample O_k (O_out dev float [n][P] or NULL), <O_k> (meanO_out dev double [P] or NULL),
+ * F_k = <O_k (E - <E>)> (F_out dev double [P] or NULL) and E_stats (host [4] or NULL) for a
+ * batch (n <= Ns) with its local energies (dev float [n][2]).  Synchronises if E_stats. */
+vmc_status vmc_ar_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, const float* eloc,
+                       int64_t n, float* O_out, double* meanO_out, double* F_out,
+                       double* E_stats);
+/* One SR step: Ns direct samples, E_loc, O, S (FP32 Gram, FP64 result), F, shifted solve,
+ * Euler update.  stats as for vmc_sr_step (acceptance 1: every draw is new).  Synchronises. */
+vmc_status vmc_ar_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats);
 
 /* Failure-path self-test (no GPU fault): which = 0 runs the cooperative kernels' bounded
  * flag wait on a word that nothing sets, which = 1 the tensor-core kernels' bounded mbarrier

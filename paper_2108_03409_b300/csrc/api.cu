@@ -41,6 +41,9 @@ struct LatticeState {
   float* prop_lq = nullptr;
   float2* prop_lp = nullptr;
   bool chain_cache = false;
+  // autoregressive ansatz: FP64 master parameters (the FP32 copy is `made`)
+  double* ar_params = nullptr;
+  int64_t ar_P = 0;
 };
 
 }  // namespace
@@ -75,6 +78,13 @@ struct vmc_ctx {
   MadeWork mw{};
   int64_t made_cap = 0;           // rows of the MADE batch workspaces
   TdvpWork tw{};                  // TDVP workspaces (cfg.tdvp)
+  // autoregressive ansatz (cfg.ar_ansatz)
+  int8_t* ar_conn = nullptr;      // [Ns][Kmax][Nmax] connected configurations
+  float* ar_lqc = nullptr;        // [Ns][Kmax] their log q
+  float* ar_lq = nullptr;         // [Ns] log q of the samples
+  double* ar_part = nullptr;      // moments chunk partials
+  int64_t ar_part_cap = 0;
+  int ar_Kmax = 0;
   // batched sampler
   SampleArgs* d_bargs = nullptr;  // [n_lattices] device descriptors
   int* d_order = nullptr;         // heavy-first lattice order
@@ -211,9 +221,9 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
 }
 
 // S (FP64) may be null for the mixed solvers when the Gram already wrote their inputs.
-vmc_status solve_core(vmc_ctx* ctx, LatticeState& L, const double2* S, const double2* F,
+vmc_status solve_core(vmc_ctx* ctx, int64_t P, const double2* S, const double2* F,
                       double2* x, int* iters, double* relres) {
-  ctx->sw.P = L.P;
+  ctx->sw.P = P;
   const vmc_config& c = ctx->cfg;
   int it = 0;
   double rel = 0.0;
@@ -258,8 +268,10 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
     return VMC_ERR_ARG;
   if (!(cfg->shift >= 0.0)) return VMC_ERR_ARG;
   if (cfg->made_hidden < 0 || cfg->made_hidden > 512 || cfg->made_hidden % 32 != 0 ||
-      cfg->made_batch < 0 || (cfg->tdvp != 0 && cfg->tdvp != 1))
+      cfg->made_batch < 0 || (cfg->tdvp != 0 && cfg->tdvp != 1) ||
+      (cfg->ar_ansatz != 0 && cfg->ar_ansatz != 1))
     return VMC_ERR_ARG;
+  if (cfg->ar_ansatz && (cfg->made_hidden <= 0 || cfg->solver == VMC_SOLVER_CG)) return VMC_ERR_ARG;
   for (int l = 0; l < n_lattices; ++l) {
     const vmc_lattice& L = lattices[l];
     const int N = L.Lx * L.Ly;
@@ -281,8 +293,18 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
     ctx->Nmax = std::max(ctx->Nmax, S.N);
     ctx->Mmax = std::max(ctx->Mmax, S.M);
     ctx->Pmax = std::max(ctx->Pmax, S.P);
+    if (cfg->ar_ansatz) {
+      S.ar_P = made_nparams(S.N, cfg->made_hidden);
+      ctx->Pmax = std::max(ctx->Pmax, S.ar_P);
+      ctx->ar_Kmax = std::max(ctx->ar_Kmax, S.lat.model == 0 ? S.N : num_bonds(S.lat.Lx, S.lat.Ly));
+    }
     ctx->lats.push_back(S);
   }
+  for (auto& L : ctx->lats)
+    if (cfg->ar_ansatz && L.ar_P > 16384) {
+      delete ctx;
+      return VMC_ERR_ARG;
+    }
   ctx->dense = cfg->solver != VMC_SOLVER_CG;
   auto oom = [&](cudaError_t e) {
     vmc_destroy(ctx);
@@ -318,6 +340,10 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
       cudaMemset(L.made_m, 0, np * sizeof(float));
       cudaMemset(L.made_v, 0, np * sizeof(float));
       launch_made_transpose(made_view(L.made, L.W1t, L.W2t, L.W3t, L.N, H), ctx->st);
+      if (cfg->ar_ansatz) {
+        if ((e = dalloc(ctx, &L.ar_params, np))) return oom(e);
+        cudaMemset(L.ar_params, 0, np * sizeof(double));
+      }
     }
   }
   {
@@ -330,7 +356,8 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
   }
   if (cfg->made_hidden > 0) {
     const int H = cfg->made_hidden;
-    const int64_t B = std::max<int64_t>(cfg->made_batch > 0 ? cfg->made_batch : 4096, cfg->n_chains);
+    int64_t B = std::max<int64_t>(cfg->made_batch > 0 ? cfg->made_batch : 4096, cfg->n_chains);
+    if (cfg->ar_ansatz) B = std::max<int64_t>(B, (int64_t)cfg->n_chains * cfg->samples_per_chain);
     ctx->made_cap = B;
     if ((e = dalloc(ctx, &ctx->mw.logq, B)) || (e = dalloc(ctx, &ctx->mw.H1, (size_t)B * H)) ||
         (e = dalloc(ctx, &ctx->mw.H2, (size_t)B * H)) || (e = dalloc(ctx, &ctx->mw.G1, (size_t)B * H)) ||
@@ -390,6 +417,14 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
           (e = dalloc(ctx, &w.ovpart, (size_t)w.cap_ov)))
         return oom(e);
     }
+  }
+  if (cfg->ar_ansatz) {
+    const size_t K = (size_t)ctx->ar_Kmax;
+    ctx->ar_part_cap = 2 * ctx->Pmax * 512;
+    if ((e = dalloc(ctx, &ctx->ar_conn, (size_t)Ns * K * ctx->Nmax)) ||
+        (e = dalloc(ctx, &ctx->ar_lqc, (size_t)Ns * K)) || (e = dalloc(ctx, &ctx->ar_lq, (size_t)Ns)) ||
+        (e = dalloc(ctx, &ctx->ar_part, (size_t)ctx->ar_part_cap)))
+      return oom(e);
   }
   if (cfg->tdvp) {
     // TDVP workspaces: FP64 S, Q, the Jacobi work matrix, V and the integrator's S at y
@@ -656,7 +691,7 @@ vmc_status vmc_solve(vmc_ctx* ctx, int lattice, const double* S, const double* F
   if (!S || !F || !x) return fail(ctx, VMC_ERR_ARG, "NULL buffer");
   if (!ctx->dense) return fail(ctx, VMC_ERR_STATE, "context was created for the CG solver");
   LatticeState& L = ctx->lats[lattice];
-  return solve_core(ctx, L, reinterpret_cast<const double2*>(S), reinterpret_cast<const double2*>(F),
+  return solve_core(ctx, L.P, reinterpret_cast<const double2*>(S), reinterpret_cast<const double2*>(F),
                     reinterpret_cast<double2*>(x), iters, relres);
 }
 
@@ -722,7 +757,7 @@ static vmc_status step_solve(vmc_ctx* ctx, LatticeState& L, bool fused, int* ite
                              double* rel_ex) {
   const vmc_config& c = ctx->cfg;
   if (!(fused && c.precision == VMC_PREC_BF16SPLIT)) {
-    vmc_status s = solve_core(ctx, L, fused ? nullptr : ctx->S, ctx->F, ctx->x, iters, rel);
+    vmc_status s = solve_core(ctx, L.P, fused ? nullptr : ctx->S, ctx->F, ctx->x, iters, rel);
     if (rel_ex) *rel_ex = *rel;
     return s;
   }
@@ -1270,6 +1305,194 @@ vmc_status vmc_excited_step(vmc_ctx* ctx, int lattice, int ref_lattice, double d
   local.tdvp.rhs_evals = 1;
   cudaEventElapsedTime(&local.tdvp.ms, ctx->ev[0], ctx->ev[1]);
   if (stats) *stats = local;
+  return VMC_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// the autoregressive network as the ansatz (section "Autoregressive neural quantum states")
+// ---------------------------------------------------------------------------------------
+static vmc_status ar_ok(vmc_ctx* ctx, int lattice) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!ctx->cfg.ar_ansatz) return fail(ctx, VMC_ERR_STATE, "context was created without ar_ansatz");
+  return VMC_OK;
+}
+
+static MadeDev ar_dev(vmc_ctx* ctx, LatticeState& L) {
+  return made_view(L.made, L.W1t, L.W2t, L.W3t, L.N, ctx->cfg.made_hidden);
+}
+
+vmc_status vmc_ar_set_params(vmc_ctx* ctx, int lattice, const double* params_host) {
+  vmc_status s = ar_ok(ctx, lattice);
+  if (s) return s;
+  if (!params_host) return fail(ctx, VMC_ERR_ARG, "NULL parameters");
+  LatticeState& L = ctx->lats[lattice];
+  CK(cudaMemcpyAsync(L.ar_params, params_host, sizeof(double) * L.ar_P, cudaMemcpyHostToDevice,
+                     ctx->st), "ar_set_params");
+  CK(launch_to_f32(L.ar_params, L.ar_P, L.made, ctx->st), "ar_set_params");
+  CK(launch_made_transpose(ar_dev(ctx, L), ctx->st), "ar_set_params");
+  ctx->launches += 2;
+  CK(cudaStreamSynchronize(ctx->st), "ar_set_params");
+  return VMC_OK;
+}
+
+vmc_status vmc_ar_get_params(vmc_ctx* ctx, int lattice, double* params_host) {
+  vmc_status s = ar_ok(ctx, lattice);
+  if (s) return s;
+  if (!params_host) return fail(ctx, VMC_ERR_ARG, "NULL output");
+  LatticeState& L = ctx->lats[lattice];
+  CK(cudaMemcpyAsync(params_host, L.ar_params, sizeof(double) * L.ar_P, cudaMemcpyDeviceToHost,
+                     ctx->st), "ar_get_params");
+  CK(cudaStreamSynchronize(ctx->st), "ar_get_params");
+  return VMC_OK;
+}
+
+vmc_status vmc_ar_logpsi(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* logpsi) {
+  vmc_status s = ar_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!spins || !logpsi))) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_made_logq(ar_dev(ctx, L), spins, n, logpsi, ctx->st), "ar_logpsi");
+  CK(launch_scale_f32(logpsi, n, 0.5f, ctx->st), "ar_logpsi");
+  ctx->launches += 2;
+  return check_status(ctx, "ar_logpsi");
+}
+
+vmc_status vmc_ar_sample(vmc_ctx* ctx, int lattice, int64_t n, int8_t* spins_out, float* logpsi_out) {
+  vmc_status s = ar_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && !spins_out)) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  if (n > 0 && !logpsi_out && n > ctx->Ns) return fail(ctx, VMC_ERR_ARG, "n > Ns needs logpsi_out");
+  LatticeState& L = ctx->lats[lattice];
+  float* lq = logpsi_out ? logpsi_out : ctx->ar_lq;
+  CK(launch_made_sample(ar_dev(ctx, L), n, ctx->cfg.seed, (uint64_t)lattice, L.made_round, spins_out,
+                        lq, ctx->st), "ar_sample");
+  ++L.made_round;
+  if (logpsi_out) CK(launch_scale_f32(logpsi_out, n, 0.5f, ctx->st), "ar_sample");
+  ctx->launches += 2;
+  return check_status(ctx, "ar_sample");
+}
+
+// E_loc of a batch (n <= Ns) into E; lq receives log q of the batch
+static vmc_status ar_eloc_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, int64_t n,
+                               float2* E) {
+  const MadeDev D = ar_dev(ctx, L);
+  const LatDev lat = lat_of(L);
+  const int64_t K = L.lat.model == 0 ? L.N : L.nb;
+  CK(launch_ar_connected(spins, n, lat, ctx->ar_conn, ctx->st), "ar_connected");
+  CK(launch_made_logq(D, ctx->ar_conn, n * K, ctx->ar_lqc, ctx->st), "ar_logq");
+  CK(launch_made_logq(D, spins, n, ctx->ar_lq, ctx->st), "ar_logq");
+  CK(launch_ar_eloc(spins, ctx->ar_lq, ctx->ar_lqc, n, lat, E, ctx->status, ctx->st), "ar_eloc");
+  ctx->launches += 4;
+  return VMC_OK;
+}
+
+vmc_status vmc_ar_local_energy(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* eloc) {
+  vmc_status s = ar_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || n > ctx->Ns || (n > 0 && (!spins || !eloc))) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  if (n == 0) return VMC_OK;
+  if ((s = ar_eloc_core(ctx, ctx->lats[lattice], spins, n, reinterpret_cast<float2*>(eloc)))) return s;
+  return check_status(ctx, "ar_local_energy");
+}
+
+// <E> into ctx->estats, per-sample backward into ctx->mw, <O> and F into ctx->meanO / ctx->F
+static vmc_status ar_grad_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const float2* E,
+                               int64_t n) {
+  CK(launch_estats(E, n, ctx->estats, ctx->status, ctx->st), "estats");
+  CK(launch_made_fwd_bwd(ar_dev(ctx, L), spins, n, ctx->mw, ctx->st), "ar_backward");
+  CK(launch_ar_moments(spins, ctx->mw, E, ctx->estats, n, L.N, ctx->cfg.made_hidden, ctx->ar_part,
+                       ctx->ar_part_cap, ctx->meanO, ctx->F, ctx->st), "ar_moments");
+  ctx->launches += 4;
+  return VMC_OK;
+}
+
+vmc_status vmc_ar_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, const float* eloc, int64_t n,
+                       float* O_out, double* meanO_out, double* F_out, double* E_stats) {
+  vmc_status s = ar_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 1 || n > ctx->Ns || !spins || !eloc) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  if ((s = ar_grad_core(ctx, L, spins, reinterpret_cast<const float2*>(eloc), n))) return s;
+  if (O_out) {
+    CK(launch_ar_dense_o(spins, ctx->mw, n, L.N, ctx->cfg.made_hidden, O_out, ctx->st), "ar_dense_o");
+    ++ctx->launches;
+  }
+  // <O> and F are real: copy the real parts out
+  if (meanO_out)
+    CK(cudaMemcpy2DAsync(meanO_out, sizeof(double), ctx->meanO, sizeof(double2), sizeof(double),
+                         L.ar_P, cudaMemcpyDeviceToDevice, ctx->st), "ar_grad");
+  if (F_out)
+    CK(cudaMemcpy2DAsync(F_out, sizeof(double), ctx->F, sizeof(double2), sizeof(double), L.ar_P,
+                         cudaMemcpyDeviceToDevice, ctx->st), "ar_grad");
+  if (E_stats) CK(cudaMemcpyAsync(E_stats, ctx->estats, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  ctx->st), "ar_grad");
+  return check_status(ctx, "ar_grad");
+}
+
+vmc_status vmc_ar_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats) {
+  vmc_status s = ar_ok(ctx, lattice);
+  if (s) return s;
+  if (!ctx->dense) return fail(ctx, VMC_ERR_STATE, "the autoregressive SR step needs a dense solver");
+  LatticeState& L = ctx->lats[lattice];
+  const int64_t Ns = ctx->Ns, P = L.ar_P;
+  const int64_t launches0 = ctx->launches;
+  CK(cudaEventRecord(ctx->ev[0], ctx->st), "ar_sr_step");
+  // 1. Ns exact draws
+  CK(launch_made_sample(ar_dev(ctx, L), Ns, ctx->cfg.seed, (uint64_t)lattice, L.made_round,
+                        ctx->s_spins, ctx->ar_lq, ctx->st), "ar_sample");
+  ++L.made_round;
+  ++ctx->launches;
+  CK(cudaEventRecord(ctx->ev[1], ctx->st), "ar_sr_step");
+  // 2. E_loc, <E>, per-sample O, <O>, F
+  if ((s = ar_eloc_core(ctx, L, ctx->s_spins, Ns, ctx->s_E))) return s;
+  if ((s = ar_grad_core(ctx, L, ctx->s_spins, ctx->s_E, Ns))) return s;
+  CK(cudaEventRecord(ctx->ev[2], ctx->st), "ar_sr_step");
+  // 3. S = <Obar Obar^T> (FP32 SIMT Gram of the real rows, FP64 result)
+  if (2 * P > ctx->rows_pad || Ns > ctx->ld) return fail(ctx, VMC_ERR_ARG, "S workspace too small");
+  CK(launch_ar_build_x(ctx->s_spins, ctx->mw, ctx->meanO, Ns, L.N, ctx->cfg.made_hidden,
+                       ctx->rows_pad, ctx->ld, ctx->X32, ctx->st), "ar_build_x");
+  cudaEventRecord(ctx->ev[6], ctx->st);
+  CK(launch_gram_f32(ctx->X32, ctx->rows_pad, ctx->ld, P, 1.0 / (double)Ns, ctx->S, true, ctx->gpart,
+                     ctx->gpart_cap, ctx->st), "gram_f32");
+  cudaEventRecord(ctx->ev[7], ctx->st);
+  CK(launch_freeze_zero_rows(ctx->S, ctx->F, P, ctx->st), "freeze");
+  ctx->launches += 3;
+  CK(cudaEventRecord(ctx->ev[3], ctx->st), "ar_sr_step");
+  // 4. shifted solve, 5. update
+  int iters = 0;
+  double rel = 0.0;
+  if ((s = solve_core(ctx, P, ctx->S, ctx->F, ctx->x, &iters, &rel))) return s;
+  CK(cudaEventRecord(ctx->ev[4], ctx->st), "ar_sr_step");
+  CK(launch_ar_update(L.ar_params, ctx->x, P, dt, L.made, ctx->st), "ar_update");
+  CK(launch_made_transpose(ar_dev(ctx, L), ctx->st), "ar_update");
+  ctx->launches += 2;
+  CK(cudaEventRecord(ctx->ev[5], ctx->st), "ar_sr_step");
+  double es[4];
+  CK(cudaMemcpyAsync(es, ctx->estats, sizeof(es), cudaMemcpyDeviceToHost, ctx->st), "ar_sr_step");
+  if ((s = check_status(ctx, "ar_sr_step"))) return s;
+  if (stats) {
+    *stats = vmc_sr_stats{};
+    stats->e_mean_re = es[0];
+    stats->e_mean_im = es[1];
+    stats->e_var = es[2];
+    stats->e_stderr = es[3];
+    stats->n_samples = Ns;
+    stats->acceptance = 1.0;
+    stats->solver_iters = iters;
+    stats->solver_relres = rel;
+    stats->solver_relres_explicit = rel;
+    stats->solver_converged = 1;
+    float t[5];
+    for (int k = 0; k < 5; ++k) cudaEventElapsedTime(&t[k], ctx->ev[k], ctx->ev[k + 1]);
+    stats->ms_sample = t[0];
+    stats->ms_grad = t[1];
+    stats->ms_qfm = t[2];
+    stats->ms_solve = t[3];
+    stats->ms_update = t[4];
+    cudaEventElapsedTime(&stats->ms_gram, ctx->ev[6], ctx->ev[7]);
+    stats->launches = ctx->launches - launches0;
+  }
   return VMC_OK;
 }
 

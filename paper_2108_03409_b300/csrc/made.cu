@@ -416,6 +416,15 @@ cudaError_t launch_made_grad(const MadeDev& D, const int8_t* spins, int64_t n, M
   return cudaGetLastError();
 }
 
+cudaError_t launch_made_fwd_bwd(const MadeDev& D, const int8_t* spins, int64_t n, MadeWork& w,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned grid = (unsigned)((n + 3) / 4);
+  MADE_DISPATCH(D.H, k_made_fwd<HPL><<<grid, 128, made_smem(D.N, D.H), st>>>(
+                         D, spins, n, w.logq, w.H1, w.H2, w.G1, w.G2, w.G3, 1.f));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_adam(float* th, float* m, float* v, const float* g, int64_t np, int t, float lr,
                         cudaStream_t st) {
   const double b1 = 0.9, b2 = 0.999;

@@ -378,6 +378,9 @@ cudaError_t launch_made_grad(const MadeDev& D, const int8_t* spins, int64_t n, M
                              float* grad, cudaStream_t st);
 cudaError_t launch_adam(float* th, float* m, float* v, const float* g, int64_t np, int t, float lr,
                         cudaStream_t st);
+// per-sample forward and backward of -log q(s) (no batch sum): w.logq, H1, H2, G1, G2, G3
+cudaError_t launch_made_fwd_bwd(const MadeDev& D, const int8_t* spins, int64_t n, MadeWork& w,
+                                cudaStream_t st);
 cudaError_t launch_made_sample(const MadeDev& D, int64_t n, uint64_t seed, uint64_t stream,
                                uint64_t round, int8_t* spins, float* logq, cudaStream_t st);
 cudaError_t launch_made_mh(int64_t C, int N, const int8_t* prop, const float2* prop_lp,
@@ -388,5 +391,35 @@ cudaError_t launch_made_mh(int64_t C, int N, const int8_t* prop, const float2* p
 // theta <- theta - dt * x, then refresh the FP32 copies
 cudaError_t launch_update(double2* params, const double2* x, int64_t P, double dt,
                           cudaStream_t st);
+
+// ---- ar.cu ----------------------------------------------------------------------------
+// The autoregressive network as the ansatz, psi = q^(1/2) (see ar.cu).
+// configurations H connects each sample to: K = N (TFIM flips) or the bond count (Heisenberg
+// exchanges; a parallel bond repeats the sample), out [n][K][N]
+cudaError_t launch_ar_connected(const int8_t* spins, int64_t n, const LatDev& L, int8_t* out,
+                                cudaStream_t st);
+// E_loc(s) = diag + sum_k H_k exp((lq_k - lq) / 2) into E [n] (imaginary part 0)
+cudaError_t launch_ar_eloc(const int8_t* spins, const float* lq, const float* lq_conn, int64_t n,
+                           const LatDev& L, float2* E, unsigned* status, cudaStream_t st);
+// <O_k> and F_k = <O_k (E - <E>)> (FP64, imaginary parts 0) from the per-sample backward in w
+cudaError_t launch_ar_moments(const int8_t* spins, const MadeWork& w, const float2* E,
+                              const double* estats, int64_t n, int N, int H, double* part,
+                              int64_t part_cap, double2* meanO, double2* F, cudaStream_t st);
+// X for the Gram: row 2k = O_k(q) - <O_k>, row 2k+1 = 0, zero padded to [rows_pad][ld]
+cudaError_t launch_ar_build_x(const int8_t* spins, const MadeWork& w, const double2* meanO,
+                              int64_t n, int N, int H, int64_t rows_pad, int64_t ld, float* X,
+                              cudaStream_t st);
+// rows of S with a zero diagonal (masked weights, inactive units) become identity rows with
+// F_k = 0, so that the solve leaves those parameters unchanged
+cudaError_t launch_freeze_zero_rows(double2* S, double2* F, int64_t P, cudaStream_t st);
+// theta_k -= dt Re x_k (FP64 master), then the FP32 copy
+cudaError_t launch_ar_update(double* theta, const double2* x, int64_t P, double dt, float* theta32,
+                             cudaStream_t st);
+cudaError_t launch_to_f32(const double* a, int64_t n, float* b, cudaStream_t st);
+cudaError_t launch_scale_f32(float* x, int64_t n, float a, cudaStream_t st);
+// dense per-sample O [n][P] (FP32) from the per-sample backward in w
+cudaError_t launch_ar_dense_o(const int8_t* spins, const MadeWork& w, int64_t n, int N, int H,
+                              float* O, cudaStream_t st);
+
 
 }  // namespace vmc

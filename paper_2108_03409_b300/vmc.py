@@ -42,7 +42,7 @@ class vmc_config(ctypes.Structure):
                 ("solver", ctypes.c_int), ("shift", ctypes.c_double), ("shift_mode", ctypes.c_int),
                 ("cg_maxit", ctypes.c_int), ("cg_tol", ctypes.c_double),
                 ("made_hidden", ctypes.c_int), ("made_batch", ctypes.c_int),
-                ("tdvp", ctypes.c_int)]
+                ("tdvp", ctypes.c_int), ("ar_ansatz", ctypes.c_int)]
 
 
 class vmc_sr_stats(ctypes.Structure):
@@ -95,7 +95,8 @@ EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_
             "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned", "vmc_sample_all",
             "vmc_autotuned_warps_per_block", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout",
             "vmc_tdvp_rhs", "vmc_tdvp_step", "vmc_excited_lambda", "vmc_excited_rhs",
-            "vmc_excited_step"]
+            "vmc_excited_step", "vmc_ar_set_params", "vmc_ar_get_params", "vmc_ar_logpsi",
+            "vmc_ar_sample", "vmc_ar_local_energy", "vmc_ar_grad", "vmc_ar_sr_step"]
 
 _lib = None
 
@@ -153,6 +154,13 @@ def load(path: str = LIB_PATH):
                                   ctypes.POINTER(vmc_excited_stats)]),
         "vmc_excited_step": (i32, [P, i32, i32, f64, ctypes.POINTER(vmc_tdvp_opts),
                                    ctypes.POINTER(vmc_excited_stats)]),
+        "vmc_ar_set_params": (i32, [P, i32, P]),
+        "vmc_ar_get_params": (i32, [P, i32, P]),
+        "vmc_ar_logpsi": (i32, [P, i32, P, i64, P]),
+        "vmc_ar_sample": (i32, [P, i32, i64, P, P]),
+        "vmc_ar_local_energy": (i32, [P, i32, P, i64, P]),
+        "vmc_ar_grad": (i32, [P, i32, P, P, i64, P, P, P, P]),
+        "vmc_ar_sr_step": (i32, [P, i32, f64, ctypes.POINTER(vmc_sr_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -181,10 +189,10 @@ def _check(ctx, status: int):
 def make_config(seed=1, n_chains=256, sweep_len=0, therm_sweeps=20, sweeps_per_sample=1,
                 samples_per_chain=1, precision=PREC_FP32, solver=SOLVER_CHOLESKY_FP64,
                 shift=1e-4, shift_mode=SHIFT_MULTIPLICATIVE, cg_maxit=100,
-                cg_tol=1e-10, made_hidden=0, made_batch=0, tdvp=0) -> vmc_config:
+                cg_tol=1e-10, made_hidden=0, made_batch=0, tdvp=0, ar_ansatz=0) -> vmc_config:
     return vmc_config(seed, n_chains, sweep_len, therm_sweeps, sweeps_per_sample,
                       samples_per_chain, precision, solver, shift, shift_mode, cg_maxit, cg_tol,
-                      made_hidden, made_batch, tdvp)
+                      made_hidden, made_batch, tdvp, ar_ansatz)
 
 
 def make_tdvp_opts(gamma=1j, eps_pinv=0.0, pinv_soft=1, eps_snr=0.0, shift=0.0, exact=0,
@@ -449,4 +457,46 @@ def vmc_excited_step(ctx, lattice, ref_lattice, dt, opts) -> vmc_excited_stats:
     st = vmc_excited_stats()
     _check(ctx, load().vmc_excited_step(ctx, lattice, ref_lattice, float(dt), ctypes.byref(opts),
                                         ctypes.byref(st)))
+    return st
+
+
+# ---- the autoregressive network as the ansatz -------------------------------------------
+def vmc_ar_set_params(ctx, lattice, params_host):
+    """params_host: numpy float64 [P] (canonical layout of the masked network)."""
+    import numpy as np
+    p = np.ascontiguousarray(params_host, dtype=np.float64)
+    _check(ctx, load().vmc_ar_set_params(ctx, lattice, p.ctypes.data))
+
+
+def vmc_ar_get_params(ctx, lattice, P):
+    import numpy as np
+    out = np.zeros(P, dtype=np.float64)
+    _check(ctx, load().vmc_ar_get_params(ctx, lattice, out.ctypes.data))
+    return out
+
+
+def vmc_ar_logpsi(ctx, lattice, spins, logpsi):
+    _check(ctx, load().vmc_ar_logpsi(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(logpsi)))
+
+
+def vmc_ar_sample(ctx, lattice, spins_out, logpsi_out=None):
+    _check(ctx, load().vmc_ar_sample(ctx, lattice, spins_out.shape[0], _ptr(spins_out),
+                                     _ptr(logpsi_out)))
+
+
+def vmc_ar_local_energy(ctx, lattice, spins, eloc):
+    _check(ctx, load().vmc_ar_local_energy(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(eloc)))
+
+
+def vmc_ar_grad(ctx, lattice, spins, eloc, O_out=None, meanO_out=None, F_out=None):
+    import numpy as np
+    es = np.zeros(4, dtype=np.float64)
+    _check(ctx, load().vmc_ar_grad(ctx, lattice, _ptr(spins), _ptr(eloc), spins.shape[0],
+                                   _ptr(O_out), _ptr(meanO_out), _ptr(F_out), es.ctypes.data))
+    return es
+
+
+def vmc_ar_sr_step(ctx, lattice, dt) -> vmc_sr_stats:
+    st = vmc_sr_stats()
+    _check(ctx, load().vmc_ar_sr_step(ctx, lattice, float(dt), ctypes.byref(st)))
     return st
