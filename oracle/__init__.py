@@ -34,6 +34,8 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
                      tests/test_oracle_excited_pins.py
   ar.*            -- the autoregressive network as the ansatz (oracle/ar.py); pinned in
                      tests/test_oracle_ar_pins.py
+  cnn.*           -- the translation-symmetric CNN-ELU ansatz (oracle/cnn.py); pinned in
+                     tests/test_oracle_cnn_pins.py
 """
 from __future__ import annotations
 
