@@ -86,6 +86,8 @@ typedef struct {
                             /* every lattice's P <= 4096)                                      */
   int ar_ansatz;            /* 1: also allocate the workspaces of the autoregressive ansatz    */
                             /* (vmc_ar_*; needs made_hidden > 0 and a dense solver)            */
+  int cnn_ansatz;           /* 1: also allocate the CNN-ELU ansatz (vmc_cnn_*; needs tdvp = 1; */
+                            /* TFIM chains only, alpha = channels, alpha * N <= 512)          */
 } vmc_config;
 
 /* Statistics of one SR step (host struct filled by vmc_sr_step). */
@@ -406,6 +408,30 @@ vmc_status vmc_ar_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, const flo
 /* One SR step: Ns direct samples, E_loc, O, S (FP32 Gram, FP64 result), F, shifted solve,
  * Euler update.  stats as for vmc_sr_step (acceptance 1: every draw is new).  Synchronises. */
 vmc_status vmc_ar_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats);
+
+/* ---- the translation-symmetric CNN-ELU ansatz (section "Ground state search", Eq.
+ * gs_nqs; requires cnn_ansatz = 1) ----------------------------------------------------------
+ * log psi(s) = sum_{a < alpha} sum_r f_ELU(sum_l W_al s_{(l+r) mod N} + b_a) on a periodic
+ * TFIM chain, alpha = the lattice's alpha (channels), real parameters [W (alpha x N) | b],
+ * P = alpha (N + 1).  It uses the lattice's chains with its own sweep counter, the same
+ * Philox stream and acceptance rule as vmc_sample (ln u < 2 [log psi(s') - log psi(s)]). */
+vmc_status vmc_cnn_set_params(vmc_ctx* ctx, int lattice, const double* params_host);
+vmc_status vmc_cnn_get_params(vmc_ctx* ctx, int lattice, double* params_host);
+/* log psi (dev float [n], may be NULL) and E_loc (dev float [n][2], may be NULL) of a batch. */
+vmc_status vmc_cnn_eval(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* logpsi,
+                        float* eloc);
+/* dense log-derivatives O [n][P] (dev float): O_{W_al} = sum_r f'(z_ar) s_{(l+r) mod N},
+ * O_{b_a} = sum_r f'(z_ar). */
+vmc_status vmc_cnn_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* O_out);
+/* Metropolis as vmc_sample (outputs dev, may be NULL: spins [n_samples*C][N], logpsi
+ * [n_samples*C], eloc [n_samples*C][2]). */
+vmc_status vmc_cnn_sample(vmc_ctx* ctx, int lattice, int n_therm, int n_samples, int8_t* spins_out,
+                          float* logpsi_out, float* eloc_out);
+/* One ground-state step of the paper's recipe: Ns samples, thetadot = -S^+ F from the FP64
+ * TDVP core (opts: gamma = 1, the diagonal shift nu and the pseudo-inverse cutoff; the
+ * caller lowers nu from step to step, e.g. nu = nu0 0.95^n), theta <- theta + dt thetadot. */
+vmc_status vmc_cnn_sr_step(vmc_ctx* ctx, int lattice, double dt, const vmc_tdvp_opts* opts,
+                           vmc_tdvp_stats* stats);
 
 /* Failure-path self-test (no GPU fault): which = 0 runs the cooperative kernels' bounded
  * flag wait on a word that nothing sets, which = 1 the tensor-core kernels' bounded mbarrier

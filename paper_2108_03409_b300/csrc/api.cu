@@ -44,6 +44,12 @@ struct LatticeState {
   // autoregressive ansatz: FP64 master parameters (the FP32 copy is `made`)
   double* ar_params = nullptr;
   int64_t ar_P = 0;
+  // CNN-ELU ansatz: FP64 master [alpha(N+1)], FP32 copies, its own Metropolis counter
+  double* cnn_params = nullptr;
+  float *cnn_W = nullptr, *cnn_b = nullptr;
+  int64_t cnn_P = 0;
+  uint64_t cnn_sweep = 0;
+  bool cnn_thermalized = false;
 };
 
 }  // namespace
@@ -85,6 +91,7 @@ struct vmc_ctx {
   double* ar_part = nullptr;      // moments chunk partials
   int64_t ar_part_cap = 0;
   int ar_Kmax = 0;
+  float* cnn_O = nullptr;         // [Ns][P] dense log-derivatives of the CNN ansatz
   // batched sampler
   SampleArgs* d_bargs = nullptr;  // [n_lattices] device descriptors
   int* d_order = nullptr;         // heavy-first lattice order
@@ -272,6 +279,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
       (cfg->ar_ansatz != 0 && cfg->ar_ansatz != 1))
     return VMC_ERR_ARG;
   if (cfg->ar_ansatz && (cfg->made_hidden <= 0 || cfg->solver == VMC_SOLVER_CG)) return VMC_ERR_ARG;
+  if ((cfg->cnn_ansatz != 0 && cfg->cnn_ansatz != 1) || (cfg->cnn_ansatz && !cfg->tdvp)) return VMC_ERR_ARG;
   for (int l = 0; l < n_lattices; ++l) {
     const vmc_lattice& L = lattices[l];
     const int N = L.Lx * L.Ly;
@@ -293,6 +301,14 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
     ctx->Nmax = std::max(ctx->Nmax, S.N);
     ctx->Mmax = std::max(ctx->Mmax, S.M);
     ctx->Pmax = std::max(ctx->Pmax, S.P);
+    if (cfg->cnn_ansatz) {
+      if (S.lat.Ly != 1 || S.lat.model != 0 || S.lat.alpha * S.N > 512) {
+        delete ctx;
+        return VMC_ERR_ARG;
+      }
+      S.cnn_P = (int64_t)S.lat.alpha * (S.N + 1);
+      ctx->Pmax = std::max(ctx->Pmax, S.cnn_P);
+    }
     if (cfg->ar_ansatz) {
       S.ar_P = made_nparams(S.N, cfg->made_hidden);
       ctx->Pmax = std::max(ctx->Pmax, S.ar_P);
@@ -344,6 +360,14 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
         if ((e = dalloc(ctx, &L.ar_params, np))) return oom(e);
         cudaMemset(L.ar_params, 0, np * sizeof(double));
       }
+    }
+    if (cfg->cnn_ansatz) {
+      if ((e = dalloc(ctx, &L.cnn_params, L.cnn_P)) ||
+          (e = dalloc(ctx, &L.cnn_W, (size_t)L.lat.alpha * L.N)) ||
+          (e = dalloc(ctx, &L.cnn_b, (size_t)L.lat.alpha)))
+        return oom(e);
+      cudaMemset(L.cnn_params, 0, L.cnn_P * sizeof(double));
+      launch_cnn_prep(L.cnn_params, L.lat.alpha, L.N, L.cnn_W, L.cnn_b, ctx->st);
     }
   }
   {
@@ -417,6 +441,11 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
           (e = dalloc(ctx, &w.ovpart, (size_t)w.cap_ov)))
         return oom(e);
     }
+  }
+  if (cfg->cnn_ansatz) {
+    int64_t pc = 0;
+    for (auto& L : ctx->lats) pc = std::max(pc, L.cnn_P);
+    if ((e = dalloc(ctx, &ctx->cnn_O, (size_t)Ns * pc))) return oom(e);
   }
   if (cfg->ar_ansatz) {
     const size_t K = (size_t)ctx->ar_Kmax;
@@ -944,12 +973,12 @@ static vmc_status tdvp_opts_ok(vmc_ctx* ctx, const vmc_tdvp_opts* o) {
 static vmc_status tdvp_core(vmc_ctx* ctx, LatticeState& L, const int8_t* sp, const float2* E,
                             const double* w, const float2* osc, int64_t n, bool snr,
                             const vmc_tdvp_opts& o, double2* out, bool save_S0,
-                            vmc_tdvp_stats* st) {
+                            vmc_tdvp_stats* st, const float* Od = nullptr, int64_t Pd = 0) {
   TdvpWork& tw = ctx->tw;
-  const int64_t P = L.P;
-  CK(tdvp_moments(sp, ctx->s_T, E, w, osc, n, L.N, L.M, tw, ctx->st), "tdvp_moments");
+  const int64_t P = Od ? Pd : L.P;
+  CK(tdvp_moments(sp, ctx->s_T, E, w, osc, n, L.N, L.M, tw, ctx->st, Od, Pd), "tdvp_moments");
   if (st) cudaEventRecord(ctx->ev[2], ctx->st);
-  CK(tdvp_gram(sp, ctx->s_T, E, w, osc, n, L.N, L.M, tw, ctx->st), "tdvp_gram");
+  CK(tdvp_gram(sp, ctx->s_T, E, w, osc, n, L.N, L.M, tw, ctx->st, Od, Pd), "tdvp_gram");
   if (st) cudaEventRecord(ctx->ev[3], ctx->st);
   ctx->launches += 5;
   if (o.shift > 0.0) {
@@ -1493,6 +1522,134 @@ vmc_status vmc_ar_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* st
     cudaEventElapsedTime(&stats->ms_gram, ctx->ev[6], ctx->ev[7]);
     stats->launches = ctx->launches - launches0;
   }
+  return VMC_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// the translation-symmetric CNN-ELU ansatz (section "Ground state search", Eq. gs_nqs)
+// ---------------------------------------------------------------------------------------
+static vmc_status cnn_ok(vmc_ctx* ctx, int lattice) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!ctx->cfg.cnn_ansatz) return fail(ctx, VMC_ERR_STATE, "context was created without cnn_ansatz");
+  return VMC_OK;
+}
+
+static CnnDev cnn_dev(const LatticeState& L) { return CnnDev{L.N, L.lat.alpha, L.cnn_W, L.cnn_b}; }
+
+vmc_status vmc_cnn_set_params(vmc_ctx* ctx, int lattice, const double* params_host) {
+  vmc_status s = cnn_ok(ctx, lattice);
+  if (s) return s;
+  if (!params_host) return fail(ctx, VMC_ERR_ARG, "NULL parameters");
+  LatticeState& L = ctx->lats[lattice];
+  CK(cudaMemcpyAsync(L.cnn_params, params_host, sizeof(double) * L.cnn_P, cudaMemcpyHostToDevice,
+                     ctx->st), "cnn_set_params");
+  CK(launch_cnn_prep(L.cnn_params, L.lat.alpha, L.N, L.cnn_W, L.cnn_b, ctx->st), "cnn_set_params");
+  ++ctx->launches;
+  CK(cudaStreamSynchronize(ctx->st), "cnn_set_params");
+  return VMC_OK;
+}
+
+vmc_status vmc_cnn_get_params(vmc_ctx* ctx, int lattice, double* params_host) {
+  vmc_status s = cnn_ok(ctx, lattice);
+  if (s) return s;
+  if (!params_host) return fail(ctx, VMC_ERR_ARG, "NULL output");
+  LatticeState& L = ctx->lats[lattice];
+  CK(cudaMemcpyAsync(params_host, L.cnn_params, sizeof(double) * L.cnn_P, cudaMemcpyDeviceToHost,
+                     ctx->st), "cnn_get_params");
+  CK(cudaStreamSynchronize(ctx->st), "cnn_get_params");
+  return VMC_OK;
+}
+
+vmc_status vmc_cnn_eval(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* logpsi,
+                        float* eloc) {
+  vmc_status s = cnn_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!spins || (!logpsi && !eloc)))) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_cnn_eval(cnn_dev(L), lat_of(L), spins, n, logpsi, reinterpret_cast<float2*>(eloc),
+                     ctx->status, ctx->st), "cnn_eval");
+  ++ctx->launches;
+  return check_status(ctx, "cnn_eval");
+}
+
+vmc_status vmc_cnn_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* O_out) {
+  vmc_status s = cnn_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!spins || !O_out))) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  LatticeState& L = ctx->lats[lattice];
+  CK(launch_cnn_ok(cnn_dev(L), spins, n, O_out, ctx->st), "cnn_grad");
+  ++ctx->launches;
+  return check_status(ctx, "cnn_grad");
+}
+
+static vmc_status cnn_sample_core(vmc_ctx* ctx, int lattice, LatticeState& L, int n_therm,
+                                  int n_samples, int8_t* spins_out, float* logpsi_out,
+                                  float2* eloc_out) {
+  const vmc_config& c = ctx->cfg;
+  CnnSampleArgs A{};
+  A.D = cnn_dev(L);
+  A.lat = lat_of(L);
+  A.chains = L.chains;
+  A.C = c.n_chains;
+  A.L = c.sweep_len > 0 ? c.sweep_len : L.N;
+  A.seed = c.seed;
+  A.stream = (uint64_t)lattice;
+  A.sweep0 = L.cnn_sweep;
+  A.n_therm = n_therm;
+  A.n_samples = n_samples;
+  A.sweeps_per_sample = c.sweeps_per_sample;
+  A.spins_out = spins_out;
+  A.logpsi_out = logpsi_out;
+  A.eloc_out = eloc_out;
+  A.n_accept = ctx->n_accept;
+  A.status = ctx->status;
+  CK(launch_cnn_sample(A, ctx->st), "cnn_sample");
+  ++ctx->launches;
+  L.cnn_sweep += (uint64_t)n_therm + (uint64_t)n_samples * c.sweeps_per_sample;
+  L.cnn_thermalized = true;
+  return VMC_OK;
+}
+
+vmc_status vmc_cnn_sample(vmc_ctx* ctx, int lattice, int n_therm, int n_samples, int8_t* spins_out,
+                          float* logpsi_out, float* eloc_out) {
+  vmc_status s = cnn_ok(ctx, lattice);
+  if (s) return s;
+  if (n_therm < 0 || n_samples < 0) return fail(ctx, VMC_ERR_ARG, "bad counts");
+  if ((s = cnn_sample_core(ctx, lattice, ctx->lats[lattice], n_therm, n_samples, spins_out,
+                           logpsi_out, reinterpret_cast<float2*>(eloc_out))))
+    return s;
+  return check_status(ctx, "cnn_sample");
+}
+
+vmc_status vmc_cnn_sr_step(vmc_ctx* ctx, int lattice, double dt, const vmc_tdvp_opts* opts,
+                           vmc_tdvp_stats* stats) {
+  vmc_status s = cnn_ok(ctx, lattice);
+  if (s) return s;
+  if ((s = tdvp_opts_ok(ctx, opts))) return s;
+  if (!std::isfinite(dt)) return fail(ctx, VMC_ERR_ARG, "bad dt");
+  LatticeState& L = ctx->lats[lattice];
+  const vmc_config& c = ctx->cfg;
+  CK(cudaEventRecord(ctx->ev[0], ctx->st), "cnn_sr_step");
+  // Ns Metropolis samples with fused E_loc, then the dense log-derivatives
+  if ((s = cnn_sample_core(ctx, lattice, L, L.cnn_thermalized ? 0 : c.therm_sweeps,
+                           c.samples_per_chain, ctx->s_spins, nullptr, ctx->s_E)))
+    return s;
+  CK(launch_cnn_ok(cnn_dev(L), ctx->s_spins, ctx->Ns, ctx->cnn_O, ctx->st), "cnn_ok");
+  ++ctx->launches;
+  // the regularised solve (diagonal shift and pseudo-inverse of opts), then the Euler step
+  vmc_tdvp_stats local{};
+  if ((s = tdvp_core(ctx, L, ctx->s_spins, ctx->s_E, nullptr, nullptr, ctx->Ns, true, *opts,
+                     ctx->tw.vec[1], false, &local, ctx->cnn_O, L.cnn_P)))
+    return s;
+  CK(launch_cnn_update(L.cnn_params, ctx->tw.vec[1], L.cnn_P, dt, ctx->st), "cnn_update");
+  CK(launch_cnn_prep(L.cnn_params, L.lat.alpha, L.N, L.cnn_W, L.cnn_b, ctx->st), "cnn_update");
+  ctx->launches += 2;
+  CK(cudaEventRecord(ctx->ev[1], ctx->st), "cnn_sr_step");
+  if ((s = check_status(ctx, "cnn_sr_step"))) return s;
+  local.rhs_evals = 1;
+  cudaEventElapsedTime(&local.ms, ctx->ev[0], ctx->ev[1]);
+  if (stats) *stats = local;
   return VMC_OK;
 }
 

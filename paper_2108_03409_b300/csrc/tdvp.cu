@@ -162,7 +162,7 @@ __global__ void k_tdvp_energy(const float2* E, const double* w, int64_t n, doubl
 // chunk of samples; partial[chunk][k] = {sum w O_k, sum w conj(O_k)(E - <E>)}.
 __global__ void k_tdvp_moments(const int8_t* __restrict__ spins, const float2* __restrict__ T,
                                const float2* __restrict__ E, const double* __restrict__ w,
-                               const float2* __restrict__ osc,
+                               const float2* __restrict__ osc, const float* __restrict__ Od,
                                const double* __restrict__ estats, int64_t n, int N, int M,
                                int64_t P, int64_t chunk, double2* __restrict__ partial) {
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -173,7 +173,8 @@ __global__ void k_tdvp_moments(const int8_t* __restrict__ spins, const float2* _
   double mr = 0, mi = 0, fr = 0, fi = 0;
   for (int64_t q = q0; q < q1; ++q) {
     const double wq = w ? w[q] : u;
-    double2 o = o_entry(spins + q * N, T + q * M, N, M, k);
+    double2 o = Od ? make_double2((double)Od[q * P + k], 0.0)
+                   : o_entry(spins + q * N, T + q * M, N, M, k);
     if (osc) o = cmul_d(o, make_double2((double)osc[q].x, (double)osc[q].y));
     const double dr = (double)E[q].x - er, di = (double)E[q].y - ei;
     mr = fma(wq, o.x, mr);
@@ -219,7 +220,7 @@ __device__ __forceinline__ void tri_tile(int64_t t, int* bm, int* bn) {
 
 __global__ void __launch_bounds__(256) k_tdvp_gram(
     const int8_t* __restrict__ spins, const float2* __restrict__ T, const float2* __restrict__ E,
-    const double* __restrict__ w, const float2* __restrict__ osc,
+    const double* __restrict__ w, const float2* __restrict__ osc, const float* __restrict__ Od,
     const double* __restrict__ estats, const double2* __restrict__ meanO, int64_t n, int N,
     int M, int64_t P, int64_t chunk, int64_t ntiles, double2* __restrict__ partial) {
   __shared__ double2 Ok[kBatch][kTile];
@@ -247,7 +248,8 @@ __global__ void __launch_bounds__(256) k_tdvp_gram(
       double2 v = make_double2(0, 0);
       if (qs < nb && kk < P) {
         const int64_t q = qb + qs;
-        double2 o = o_entry(spins + q * N, T + q * M, N, M, kk);
+        double2 o = Od ? make_double2((double)Od[q * P + kk], 0.0)
+                       : o_entry(spins + q * N, T + q * M, N, M, kk);
         if (osc) o = cmul_d(o, make_double2((double)osc[q].x, (double)osc[q].y));
         const double2 m = meanO[kk];
         v = make_double2(o.x - m.x, o.y - m.y);
@@ -652,8 +654,8 @@ cudaError_t launch_normalize_weights(const double* w_in, int64_t n, double* w_ou
 
 cudaError_t tdvp_moments(const int8_t* spins, const float2* T, const float2* E, const double* w,
                          const float2* osc, int64_t n, int N, int M, TdvpWork& tw,
-                         cudaStream_t st) {
-  const int64_t P = (int64_t)N + M + (int64_t)N * M;
+                         cudaStream_t st, const float* Od, int64_t Pd) {
+  const int64_t P = Od ? Pd : (int64_t)N + M + (int64_t)N * M;
   k_tdvp_energy<<<1, 1024, 0, st>>>(E, w, n, tw.estats, tw.status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -664,7 +666,7 @@ cudaError_t tdvp_moments(const int8_t* spins, const float2* T, const float2* E, 
   const int64_t chunk = (n + chunks - 1) / chunks;
   chunks = (n + chunk - 1) / chunk;
   k_tdvp_moments<<<dim3((unsigned)kb, (unsigned)chunks), 256, 0, st>>>(
-      spins, T, E, w, osc, tw.estats, n, N, M, P, chunk, tw.mom_part);
+      spins, T, E, w, osc, Od, tw.estats, n, N, M, P, chunk, tw.mom_part);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_tdvp_moments_reduce<<<(unsigned)kb, 256, 0, st>>>(tw.mom_part, (int)chunks, P, tw.meanO, tw.F);
   return cudaGetLastError();
@@ -672,8 +674,8 @@ cudaError_t tdvp_moments(const int8_t* spins, const float2* T, const float2* E, 
 
 cudaError_t tdvp_gram(const int8_t* spins, const float2* T, const float2* E, const double* w,
                       const float2* osc, int64_t n, int N, int M, TdvpWork& tw,
-                      cudaStream_t st) {
-  const int64_t P = (int64_t)N + M + (int64_t)N * M;
+                      cudaStream_t st, const float* Od, int64_t Pd) {
+  const int64_t P = Od ? Pd : (int64_t)N + M + (int64_t)N * M;
   const int64_t tiles_1d = (P + kTile - 1) / kTile;
   const int64_t ntiles = tiles_1d * (tiles_1d + 1) / 2;
   int64_t chunks = tdvp_gram_chunks(n, P, tw.n_sm);
@@ -682,7 +684,7 @@ cudaError_t tdvp_gram(const int8_t* spins, const float2* T, const float2* E, con
   const int64_t chunk = (n + chunks - 1) / chunks;
   chunks = (n + chunk - 1) / chunk;
   k_tdvp_gram<<<dim3((unsigned)ntiles, (unsigned)chunks), 256, 0, st>>>(
-      spins, T, E, w, osc, tw.estats, tw.meanO, n, N, M, P, chunk, ntiles, tw.gram_part);
+      spins, T, E, w, osc, Od, tw.estats, tw.meanO, n, N, M, P, chunk, ntiles, tw.gram_part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_tdvp_gram_reduce<<<(unsigned)ntiles, kTile * kTile, 0, st>>>(tw.gram_part, (int)chunks, ntiles,

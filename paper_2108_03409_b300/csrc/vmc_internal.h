@@ -323,14 +323,15 @@ cudaError_t launch_enum_states(int8_t* spins, int N, int64_t n, cudaStream_t st)
 cudaError_t launch_born_weights(const float2* lp, int64_t n, double* w, unsigned* status,
                                 cudaStream_t st);
 // weighted <E> (tw.estats), <O> (tw.meanO) and F (tw.F); w = null: uniform 1/n (w must be
-// normalised); osc = null or a per-sample complex factor multiplying every O_k(s)
+// normalised); osc = null or a per-sample complex factor multiplying every O_k(s); Od: a
+// dense real O [n][Pd] (FP32) in place of the RBM's structured one (spins, T unused)
 cudaError_t tdvp_moments(const int8_t* spins, const float2* T, const float2* E, const double* w,
                          const float2* osc, int64_t n, int N, int M, TdvpWork& tw,
-                         cudaStream_t st);
+                         cudaStream_t st, const float* Od = nullptr, int64_t Pd = 0);
 // weighted S (tw.S) and energy-weighted Q (tw.Q), full Hermitian, FP64
 cudaError_t tdvp_gram(const int8_t* spins, const float2* T, const float2* E, const double* w,
                       const float2* osc, int64_t n, int N, int M, TdvpWork& tw,
-                      cudaStream_t st);
+                      cudaStream_t st, const float* Od = nullptr, int64_t Pd = 0);
 // w_out = w_in / sum(w_in); sums (may be null): sum w and sum w^2 of the input
 cudaError_t launch_normalize_weights(const double* w_in, int64_t n, double* w_out,
                                      unsigned* status, cudaStream_t st, double* sums = nullptr);
@@ -391,6 +392,36 @@ cudaError_t launch_made_mh(int64_t C, int N, const int8_t* prop, const float2* p
 // theta <- theta - dt * x, then refresh the FP32 copies
 cudaError_t launch_update(double2* params, const double2* x, int64_t P, double dt,
                           cudaStream_t st);
+
+// ---- cnn.cu ---------------------------------------------------------------------------
+// The translation-symmetric CNN-ELU ansatz (see cnn.cu).
+struct CnnDev {
+  int N, alpha;
+  const float* W;   // [alpha][N]
+  const float* b;   // [alpha]
+};
+struct CnnSampleArgs {
+  CnnDev D;
+  LatDev lat;
+  int8_t* chains;                 // [C][N] in/out
+  int64_t C;
+  int L;                          // steps per sweep
+  uint64_t seed, stream, sweep0;
+  int n_therm, n_samples, sweeps_per_sample;
+  int8_t* spins_out;              // [n_samples*C][N] or null
+  float* logpsi_out;              // [n_samples*C] or null
+  float2* eloc_out;               // [n_samples*C] or null
+  unsigned long long* n_accept;
+  unsigned* status;
+};
+cudaError_t launch_cnn_prep(const double* p, int alpha, int N, float* W, float* b, cudaStream_t st);
+cudaError_t launch_cnn_sample(const CnnSampleArgs& A, cudaStream_t st);
+cudaError_t launch_cnn_eval(const CnnDev& D, const LatDev& L, const int8_t* spins, int64_t n,
+                            float* logpsi, float2* eloc, unsigned* status, cudaStream_t st);
+// dense O [n][alpha (N + 1)] (FP32)
+cudaError_t launch_cnn_ok(const CnnDev& D, const int8_t* spins, int64_t n, float* O, cudaStream_t st);
+// theta += dt Re(thetadot)
+cudaError_t launch_cnn_update(double* p, const double2* td, int64_t P, double dt, cudaStream_t st);
 
 // ---- ar.cu ----------------------------------------------------------------------------
 // The autoregressive network as the ansatz, psi = q^(1/2) (see ar.cu).

@@ -42,7 +42,7 @@ class vmc_config(ctypes.Structure):
                 ("solver", ctypes.c_int), ("shift", ctypes.c_double), ("shift_mode", ctypes.c_int),
                 ("cg_maxit", ctypes.c_int), ("cg_tol", ctypes.c_double),
                 ("made_hidden", ctypes.c_int), ("made_batch", ctypes.c_int),
-                ("tdvp", ctypes.c_int), ("ar_ansatz", ctypes.c_int)]
+                ("tdvp", ctypes.c_int), ("ar_ansatz", ctypes.c_int), ("cnn_ansatz", ctypes.c_int)]
 
 
 class vmc_sr_stats(ctypes.Structure):
@@ -96,7 +96,9 @@ EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_
             "vmc_autotuned_warps_per_block", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout",
             "vmc_tdvp_rhs", "vmc_tdvp_step", "vmc_excited_lambda", "vmc_excited_rhs",
             "vmc_excited_step", "vmc_ar_set_params", "vmc_ar_get_params", "vmc_ar_logpsi",
-            "vmc_ar_sample", "vmc_ar_local_energy", "vmc_ar_grad", "vmc_ar_sr_step"]
+            "vmc_ar_sample", "vmc_ar_local_energy", "vmc_ar_grad", "vmc_ar_sr_step",
+            "vmc_cnn_set_params", "vmc_cnn_get_params", "vmc_cnn_eval", "vmc_cnn_grad",
+            "vmc_cnn_sample", "vmc_cnn_sr_step"]
 
 _lib = None
 
@@ -161,6 +163,13 @@ def load(path: str = LIB_PATH):
         "vmc_ar_local_energy": (i32, [P, i32, P, i64, P]),
         "vmc_ar_grad": (i32, [P, i32, P, P, i64, P, P, P, P]),
         "vmc_ar_sr_step": (i32, [P, i32, f64, ctypes.POINTER(vmc_sr_stats)]),
+        "vmc_cnn_set_params": (i32, [P, i32, P]),
+        "vmc_cnn_get_params": (i32, [P, i32, P]),
+        "vmc_cnn_eval": (i32, [P, i32, P, i64, P, P]),
+        "vmc_cnn_grad": (i32, [P, i32, P, i64, P]),
+        "vmc_cnn_sample": (i32, [P, i32, i32, i32, P, P, P]),
+        "vmc_cnn_sr_step": (i32, [P, i32, f64, ctypes.POINTER(vmc_tdvp_opts),
+                                  ctypes.POINTER(vmc_tdvp_stats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -189,10 +198,11 @@ def _check(ctx, status: int):
 def make_config(seed=1, n_chains=256, sweep_len=0, therm_sweeps=20, sweeps_per_sample=1,
                 samples_per_chain=1, precision=PREC_FP32, solver=SOLVER_CHOLESKY_FP64,
                 shift=1e-4, shift_mode=SHIFT_MULTIPLICATIVE, cg_maxit=100,
-                cg_tol=1e-10, made_hidden=0, made_batch=0, tdvp=0, ar_ansatz=0) -> vmc_config:
+                cg_tol=1e-10, made_hidden=0, made_batch=0, tdvp=0, ar_ansatz=0,
+                cnn_ansatz=0) -> vmc_config:
     return vmc_config(seed, n_chains, sweep_len, therm_sweeps, sweeps_per_sample,
                       samples_per_chain, precision, solver, shift, shift_mode, cg_maxit, cg_tol,
-                      made_hidden, made_batch, tdvp, ar_ansatz)
+                      made_hidden, made_batch, tdvp, ar_ansatz, cnn_ansatz)
 
 
 def make_tdvp_opts(gamma=1j, eps_pinv=0.0, pinv_soft=1, eps_snr=0.0, shift=0.0, exact=0,
@@ -499,4 +509,39 @@ def vmc_ar_grad(ctx, lattice, spins, eloc, O_out=None, meanO_out=None, F_out=Non
 def vmc_ar_sr_step(ctx, lattice, dt) -> vmc_sr_stats:
     st = vmc_sr_stats()
     _check(ctx, load().vmc_ar_sr_step(ctx, lattice, float(dt), ctypes.byref(st)))
+    return st
+
+
+# ---- the translation-symmetric CNN-ELU ansatz --------------------------------------------
+def vmc_cnn_set_params(ctx, lattice, params_host):
+    import numpy as np
+    p = np.ascontiguousarray(params_host, dtype=np.float64)
+    _check(ctx, load().vmc_cnn_set_params(ctx, lattice, p.ctypes.data))
+
+
+def vmc_cnn_get_params(ctx, lattice, P):
+    import numpy as np
+    out = np.zeros(P, dtype=np.float64)
+    _check(ctx, load().vmc_cnn_get_params(ctx, lattice, out.ctypes.data))
+    return out
+
+
+def vmc_cnn_eval(ctx, lattice, spins, logpsi=None, eloc=None):
+    _check(ctx, load().vmc_cnn_eval(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(logpsi),
+                                    _ptr(eloc)))
+
+
+def vmc_cnn_grad(ctx, lattice, spins, O_out):
+    _check(ctx, load().vmc_cnn_grad(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(O_out)))
+
+
+def vmc_cnn_sample(ctx, lattice, n_therm, n_samples, spins_out=None, logpsi_out=None,
+                   eloc_out=None):
+    _check(ctx, load().vmc_cnn_sample(ctx, lattice, n_therm, n_samples, _ptr(spins_out),
+                                      _ptr(logpsi_out), _ptr(eloc_out)))
+
+
+def vmc_cnn_sr_step(ctx, lattice, dt, opts) -> vmc_tdvp_stats:
+    st = vmc_tdvp_stats()
+    _check(ctx, load().vmc_cnn_sr_step(ctx, lattice, float(dt), ctypes.byref(opts), ctypes.byref(st)))
     return st

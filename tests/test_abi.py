@@ -49,7 +49,7 @@ int main(void) {
   printf("vmc_excited_stats %zu\n", sizeof(vmc_excited_stats));
   F(vmc_excited_stats, ess) F(vmc_excited_stats, tdvp) F(vmc_sr_stats, solver_relres_explicit)
   F(vmc_lattice, J) F(vmc_lattice, alpha) F(vmc_config, shift) F(vmc_config, cg_tol)
-  F(vmc_config, solver) F(vmc_config, tdvp) F(vmc_config, ar_ansatz) F(vmc_sr_stats, n_samples)
+  F(vmc_config, solver) F(vmc_config, tdvp) F(vmc_config, ar_ansatz) F(vmc_config, cnn_ansatz) F(vmc_sr_stats, n_samples)
   F(vmc_sr_stats, solver_relres) F(vmc_sr_stats, ms_update) F(vmc_sr_stats, solver_converged)
   F(vmc_tdvp_opts, eps_snr) F(vmc_tdvp_opts, exact) F(vmc_tdvp_opts, jacobi_max_sweeps)
   F(vmc_tdvp_stats, kept) F(vmc_tdvp_stats, jacobi_off) F(vmc_tdvp_stats, ms)
@@ -79,7 +79,7 @@ int main(void) {
 @pytest.mark.parametrize("bad", [
     dict(n_chains=0), dict(samples_per_chain=0), dict(sweeps_per_sample=0), dict(solver=7),
     dict(precision=5), dict(shift=-1.0), dict(shift_mode=3), dict(tdvp=2),
-    dict(ar_ansatz=1), dict(ar_ansatz=1, made_hidden=32, solver=1),
+    dict(ar_ansatz=1), dict(ar_ansatz=1, made_hidden=32, solver=1), dict(cnn_ansatz=1),
 ])
 def test_init_rejects_bad_config_without_gpu(lib, bad):
     cfg = vmc.make_config(**bad)

@@ -174,14 +174,14 @@ def test_ar_draws_are_independent():
             series.append(e[:, 0].double().cpu().numpy())
     finally:
         vmc.vmc_destroy(ctx)
-    x = np.array(series)                      # [R][C]
-    d = x - x.mean(axis=0, keepdims=True)
+    x = np.array(series)                      # [R][C], every entry an independent draw
+    d = x - x.mean()                          # (a per-column mean would bias rho(t) by -1/R)
     var = np.sum(d * d)
     for lag in (1, 2):
         rho = np.sum(d[:-lag] * d[lag:]) / var
         assert abs(rho) <= 0.025, (lag, rho)
     tau = 0.5 + sum(np.sum(d[:-t] * d[t:]) / var for t in (1, 2, 3))
-    assert abs(tau - 0.5) <= 0.06, tau
+    assert abs(tau - 0.5) <= 0.04, tau
 
 
 def test_ar_sr_reaches_jordan_wigner():
