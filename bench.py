@@ -59,6 +59,14 @@ LEARNED = {"tfim2d_12x12_h3.04_alpha2_c16384_made256": dict(L=12, h=3.04, alpha=
 TDVP = {"tfim1d_N10_alpha1_c256_tdvp": dict(N=10, alpha=1, chains=256, spc=200, J=1.0, h=1.0,
                                              eps_pinv=1e-8, eps_snr=2.0, eps_step=1e-6,
                                              tau0=1e-3)}
+# the other ansatz families and the excited-state search (section 8(f) workloads, 1D chain)
+FAMILIES = {
+    "tfim1d_N10_made32_c51200_ar": dict(kind="ar", N=10, H=32, chains=256, spc=200, h=1.0, dt=0.05),
+    "tfim1d_L10_g0.7_cnn2_c200x200": dict(kind="cnn", N=10, alpha=2, chains=200, spc=200, h=0.7,
+                                          dt=1e-2),
+    "tfim1d_N10_alpha1_c256_excited": dict(kind="excited", N=10, alpha=1, chains=256, spc=200,
+                                           h=1.0, dt=0.05),
+}
 DEFAULT_WORKLOAD = "heis2d_8x8_alpha2_c8192"
 W = WORKLOADS[DEFAULT_WORKLOAD]
 LX, LY, ALPHA, CHAINS, SHIFT = W["Lx"], W["Ly"], W["alpha"], W["chains"], W["shift"]
@@ -845,6 +853,17 @@ def run_learned(args):
            "samplers": res, "speedup_eff_vs_local": eff_lrn / eff_loc,
            "equal_accuracy": {"dE_per_site": dE, "combined_err_per_site": comb,
                               "ok": bool(dE <= 1e-4 and dE <= 3 * comb)},
+           # the learned part is accepted only if <E> agrees within error bars AND the
+           # integrated autocorrelation time of E drops (and, for the >= 3x target, the
+           # effective samples/s are at least 3x those of the local moves)
+           "learned_proposal_verdict": {
+               "energy_agrees": bool(dE <= 1e-4 and dE <= 3 * comb),
+               "tau_int_drops": bool(res["learned"]["tau_int_E"] < res["local"]["tau_int_E"]),
+               "eff_speedup": eff_lrn / eff_loc,
+               "meets_3x": bool(eff_lrn >= 3 * eff_loc),
+               "verdict": ("accepted" if (dE <= 1e-4 and dE <= 3 * comb and
+                                          res["learned"]["tau_int_E"] < res["local"]["tau_int_E"])
+                           else "rejected")},
            "checkpoint": {"e_per_site": e_sr, "s": t_sr}, "train": {"loss": loss, "s": t_train},
            "roofline": None,
            "note": "sampler comparison; rooflines of the sweep and Gram kernels are in the "
@@ -963,6 +982,129 @@ def run_tdvp(args):
         torch.distributed.destroy_process_group()
 
 
+def run_family(args):
+    """One step of another ansatz family (autoregressive network, CNN-ELU) or of the
+    excited-state search on the 1D chain, timed like the SR step: W untimed steps, K timed
+    with CUDA events; the dominant kernel's roofline from its own event timing."""
+    import torch
+    from paper_2108_03409_b300 import build as vbuild
+    from paper_2108_03409_b300 import inputs, vmc
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    vbuild.build()
+    wl = FAMILIES[args.workload]
+    kind, N, C, spc = wl["kind"], wl["N"], wl["chains"], wl["spc"]
+    Ns = C * spc
+    stream = torch.cuda.current_stream()
+    pk, pk_kind = peaks()
+    fp32_peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    lat = vmc.make_lattice(vmc.MODEL_TFIM, N, 1, 1.0, wl["h"], wl.get("alpha", 1))
+    if kind == "ar":
+        H = wl["H"]
+        P = inputs.made_params(N, H, seed=5).size
+        cfg = vmc.make_config(seed=1 + rank, n_chains=C, samples_per_chain=spc,
+                              solver=vmc.SOLVER_CHOLESKY_MIXED, shift=1e-3, shift_mode=1,
+                              made_hidden=H, ar_ansatz=1, cg_tol=1e-10, cg_maxit=50)
+        ctx = vmc.vmc_init(cfg, [lat], stream.cuda_stream)
+        vmc.vmc_ar_set_params(ctx, 0, inputs.made_params(N, H, seed=5).astype(np.float64))
+        step = lambda: vmc.vmc_ar_sr_step(ctx, 0, wl["dt"])
+        unit = "SR steps/s (autoregressive ansatz, direct sampling)"
+    elif kind == "cnn":
+        alpha = wl["alpha"]
+        P = alpha * (N + 1)
+        cfg = vmc.make_config(seed=1 + rank, n_chains=C, samples_per_chain=spc, therm_sweeps=20,
+                              solver=vmc.SOLVER_CG, tdvp=1, cnn_ansatz=1)
+        ctx = vmc.vmc_init(cfg, [lat], stream.cuda_stream)
+        vmc.vmc_cnn_set_params(ctx, 0, np.random.default_rng(1).normal(0, 0.1, P))
+        vmc.vmc_set_chains(ctx, 0, inputs.random_spins(C, N, seed=9 + rank))
+        counter = [0]
+
+        def step():
+            opts = vmc.make_tdvp_opts(gamma=1.0, shift=10.0 * 0.95 ** counter[0], eps_pinv=1e-8)
+            counter[0] += 1
+            return vmc.vmc_cnn_sr_step(ctx, 0, wl["dt"], opts)
+        unit = "SR steps/s (CNN-ELU ansatz, shift + pseudo-inverse recipe)"
+    else:
+        M = wl["alpha"] * N
+        P = N + M + N * M
+        cfg = vmc.make_config(seed=1 + rank, n_chains=C, samples_per_chain=spc, therm_sweeps=20,
+                              solver=vmc.SOLVER_CG, tdvp=1)
+        ctx = vmc.vmc_init(cfg, [lat, lat], stream.cuda_stream)
+        vmc.vmc_set_params(ctx, 0, inputs.rbm_params(N, M, 0.1, seed=77))
+        vmc.vmc_set_params(ctx, 1, inputs.rbm_params(N, M, 0.01, seed=1234))
+        for l in (0, 1):
+            vmc.vmc_set_chains(ctx, l, inputs.random_spins(C, N, seed=8 + l + 10 * rank))
+        opts = vmc.make_tdvp_opts(gamma=1.0, shift=1e-3)
+        step = lambda: vmc.vmc_excited_step(ctx, 0, 1, wl["dt"], opts)
+        unit = "excited-state search steps/s"
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    launches0 = vmc.vmc_kernel_launches(ctx)
+    sts = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sts.append(step())
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = vmc.vmc_kernel_launches(ctx) - launches0
+    ms_t = torch.tensor([ms], device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    value = ws * args.steps / (ms / 1e3)
+    if kind == "ar":
+        ms_k = statistics.mean(s.ms_gram for s in sts)
+        flops = 1.0 * P * P * Ns     # the useful work: the lower half of the real P x P Gram
+        roof = {"bound": "alu", "kernel": "gram_f32", "peak": fp32_peak, "algorithmic":
+                "P^2 Ns FP32 flops (lower half of the real Gram: P(P+1)/2 entries x Ns x 2)",
+                "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock"}
+        extra = {"energy_per_site": sts[-1].e_mean_re / N, "phases_ms": {
+            k: statistics.mean(getattr(s, k) for s in sts) for k in ("ms_sample", "ms_grad",
+                                                                     "ms_qfm", "ms_solve")}}
+    else:
+        td = [s.tdvp if kind == "excited" else s for s in sts]
+        ms_k = statistics.mean(t.ms_gram for t in td)
+        flops = 14.0 * P * (P + 1) / 2 * Ns
+        roof = {"bound": "alu", "kernel": "tdvp_gram", "peak": 1.25, "algorithmic":
+                "14 FP64 flops per lower-triangle entry of S and sample",
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (no measured FP64 peak)"}
+        extra = {"energy_per_site": td[-1].e_mean_re / N,
+                 "per_step_ms": {"gram": ms_k, "eig": statistics.mean(t.ms_eig for t in td)}}
+        if kind == "excited":
+            extra["ess_fraction"] = sts[-1].ess / Ns
+    achieved = flops / (ms_k / 1e3) / 1e12
+    roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
+                 "traffic": None, "ms_per_launch": ms_k})
+    out = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 sampling, f32/f64 reductions",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "N": N, "P": P, "samples_per_step": Ns,
+                      "l2": "working set below L2 except the sample buffers; not flushed",
+                      "parallelism": f"replicas x{ws}"},
+           "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(),
+           "e2e": None, **extra}
+    vmc.vmc_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -973,7 +1115,8 @@ def main():
                     help="default: the workload's (bf16split, fp32 for the 1D chain)")
     ap.add_argument("--solver", default=None, choices=["mixed", "tc", "fp64", "cg"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(LEARNED) + sorted(TDVP))
+                    choices=sorted(WORKLOADS) + sorted(BATCHED) + sorted(LEARNED) + sorted(TDVP)
+                    + sorted(FAMILIES))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the plain FP32 comparison arm of the default workload")
@@ -986,6 +1129,8 @@ def main():
         run_learned(args)
     elif args.workload in TDVP:
         run_tdvp(args)
+    elif args.workload in FAMILIES:
+        run_family(args)
     else:
         run_ours(args)
 
