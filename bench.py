@@ -1068,7 +1068,7 @@ def run_family(args):
     value = ws * args.steps / (ms / 1e3)
     if kind == "ar":
         ms_k = statistics.mean(s.ms_gram for s in sts)
-        flops = 1.0 * P * P * Ns     # the useful work: the lower half of the real P x P Gram
+        flops = 1.0 * P * P * Ns     # the lower half of the real P x P Gram: P(P+1)/2 x Ns x 2
         roof = {"bound": "alu", "kernel": "gram_f32", "peak": fp32_peak, "algorithmic":
                 "P^2 Ns FP32 flops (lower half of the real Gram: P(P+1)/2 entries x Ns x 2)",
                 "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock"}

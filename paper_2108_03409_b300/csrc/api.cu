@@ -1477,13 +1477,14 @@ vmc_status vmc_ar_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* st
   if ((s = ar_eloc_core(ctx, L, ctx->s_spins, Ns, ctx->s_E))) return s;
   if ((s = ar_grad_core(ctx, L, ctx->s_spins, ctx->s_E, Ns))) return s;
   CK(cudaEventRecord(ctx->ev[2], ctx->st), "ar_sr_step");
-  // 3. S = <Obar Obar^T> (FP32 SIMT Gram of the real rows, FP64 result)
-  if (2 * P > ctx->rows_pad || Ns > ctx->ld) return fail(ctx, VMC_ERR_ARG, "S workspace too small");
+  // 3. S = <Obar Obar^T> (FP32 SIMT Gram of the P real rows, FP64 result)
+  const int64_t rows_real = (P + 127) / 128 * 128;
+  if (rows_real > ctx->rows_pad || Ns > ctx->ld) return fail(ctx, VMC_ERR_ARG, "S workspace too small");
   CK(launch_ar_build_x(ctx->s_spins, ctx->mw, ctx->meanO, Ns, L.N, ctx->cfg.made_hidden,
-                       ctx->rows_pad, ctx->ld, ctx->X32, ctx->st), "ar_build_x");
+                       rows_real, ctx->ld, ctx->X32, ctx->st), "ar_build_x");
   cudaEventRecord(ctx->ev[6], ctx->st);
-  CK(launch_gram_f32(ctx->X32, ctx->rows_pad, ctx->ld, P, 1.0 / (double)Ns, ctx->S, true, ctx->gpart,
-                     ctx->gpart_cap, ctx->st), "gram_f32");
+  CK(launch_gram_f32(ctx->X32, rows_real, ctx->ld, P, 1.0 / (double)Ns, ctx->S, true, ctx->gpart,
+                     ctx->gpart_cap, ctx->st, true), "gram_f32");
   cudaEventRecord(ctx->ev[7], ctx->st);
   CK(launch_freeze_zero_rows(ctx->S, ctx->F, P, ctx->st), "freeze");
   ctx->launches += 3;

@@ -135,22 +135,20 @@ __global__ void k_ar_moments_reduce(const double2* __restrict__ part, int chunks
   F[k] = make_double2(sf * inv_n, 0.0);
 }
 
-// X[2k][q] = O_k(q) - <O_k>, X[2k+1][q] = 0; zero beyond n and beyond 2P
+// X[k][q] = O_k(q) - <O_k> (the Gram's real-row mode); zero beyond n and beyond P
 __global__ void k_ar_build_x(const int8_t* __restrict__ spins, const float* __restrict__ G1,
                              const float* __restrict__ G2, const float* __restrict__ G3,
                              const float* __restrict__ H1, const float* __restrict__ H2,
                              const double2* __restrict__ meanO, int64_t n, int N, int H,
                              int64_t P, int64_t rows_pad, int64_t ld, float* __restrict__ X) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t row = blockIdx.y;                  // real rows 0 .. rows_pad / 2 - 1
+  const int64_t k = blockIdx.y;
   if (q >= ld) return;
-  const int64_t k = row;
   float v = 0.f;
   if (k < P && q < n)
     v = (float)(-0.5 * (double)ar_dl(spins + q * N, G1 + q * H, G2 + q * H, G3 + q * N,
                                      H1 + q * H, H2 + q * H, N, H, k) - meanO[k].x);
-  X[(2 * row) * ld + q] = v;
-  X[(2 * row + 1) * ld + q] = 0.f;
+  X[k * ld + q] = v;
 }
 
 __global__ void k_freeze_zero_rows(double2* S, double2* F, int64_t P) {
@@ -235,8 +233,8 @@ cudaError_t launch_ar_build_x(const int8_t* spins, const MadeWork& w, const doub
                               int64_t n, int N, int H, int64_t rows_pad, int64_t ld, float* X,
                               cudaStream_t st) {
   const int64_t P = made_nparams(N, H);
-  if (2 * P > rows_pad || n > ld) return cudaErrorInvalidValue;
-  k_ar_build_x<<<dim3(blocks_for(ld), (unsigned)(rows_pad / 2)), 256, 0, st>>>(
+  if (P > rows_pad || n > ld || rows_pad > 65535) return cudaErrorInvalidValue;
+  k_ar_build_x<<<dim3(blocks_for(ld), (unsigned)rows_pad), 256, 0, st>>>(
       spins, w.G1, w.G2, w.G3, w.H1, w.H2, meanO, n, N, H, P, rows_pad, ld, X);
   return cudaGetLastError();
 }

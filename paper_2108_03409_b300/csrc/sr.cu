@@ -305,7 +305,7 @@ static constexpr int GB = 128, GK = 16, GPAD = 4;
 __global__ void __launch_bounds__(256) k_gram_f32(const float* __restrict__ X, int64_t ld,
                                                   int nt, int64_t P, double inv_n,
                                                   double2* __restrict__ S, int mirror,
-                                                  int ktpc, float2* __restrict__ part) {
+                                                  int ktpc, float2* __restrict__ part, int real) {
   extern __shared__ float gsm[];
   float* As = gsm;                              // [2][GK][GB + GPAD]
   float* Bs = gsm + 2 * GK * (GB + GPAD);       // [2][GK][GB + GPAD]
@@ -394,6 +394,23 @@ __global__ void __launch_bounds__(256) k_gram_f32(const float* __restrict__ X, i
     }
   }
   __syncthreads();
+  if (real) {
+    // real rows (row k = parameter k): S_kl = G_kl / n, imaginary part 0
+    for (int e = tid; e < GB * GB; e += 256) {
+      const int r = e / GB, c = e % GB;
+      const int64_t k = (int64_t)bm * GB + r, l = (int64_t)bn * GB + c;
+      if (k >= P || l >= P || (bm == bn && l > k)) continue;
+      const float g = Cs[r * (GB + 1) + c];
+      if (part) {
+        part[((int64_t)blockIdx.y * P + k) * P + l] = make_float2(g, 0.f);
+        continue;
+      }
+      const double v = (double)g * inv_n;
+      S[k * P + l] = make_double2(v, 0.0);
+      if (mirror && l != k) S[l * P + k] = make_double2(v, 0.0);
+    }
+    return;
+  }
   for (int e = tid; e < 64 * 64; e += 256) {
     const int r = e >> 6, c = e & 63;
     const int64_t k = (int64_t)bm * 64 + r, l = (int64_t)bn * 64 + c;
@@ -467,7 +484,7 @@ cudaError_t launch_gram_reduce(const float2* part, int kchunks, int64_t P, doubl
 
 cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_t P,
                             double inv_n, double2* S, bool mirror, float2* part,
-                            int64_t part_cap, cudaStream_t st) {
+                            int64_t part_cap, cudaStream_t st, bool real) {
   if (rows_pad % GB != 0 || ld % GK != 0) return cudaErrorInvalidValue;
   const int64_t nt = rows_pad / GB;
   const int64_t tiles = nt * (nt + 1) / 2;
@@ -486,7 +503,7 @@ cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_
   kchunks = (int)((ld / GK + ktpc - 1) / ktpc);
   dim3 grid((unsigned)tiles, (unsigned)kchunks);
   k_gram_f32<<<grid, 256, smem, st>>>(X, ld, (int)nt, P, inv_n, S, mirror ? 1 : 0, ktpc,
-                                      kchunks > 1 ? part : nullptr);
+                                      kchunks > 1 ? part : nullptr, real ? 1 : 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || kchunks == 1) return e;
   return launch_gram_reduce(part, kchunks, P, inv_n, S, nullptr, nullptr, 0.0, 0, mirror, st);

@@ -104,7 +104,7 @@ cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* 
 //   [P][P]; mirror = also write the upper triangle.
 cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_t P,
                             double inv_n, double2* S, bool mirror, float2* part,
-                            int64_t part_cap, cudaStream_t st);
+                            int64_t part_cap, cudaStream_t st, bool real = false);
 
 // Same contraction on the tensor cores (tcgen05, BF16 hi/lo split, FP32 accumulation
 // in TMEM).  Returns cudaErrorNotSupported when the shapes are not supported.
@@ -436,7 +436,7 @@ cudaError_t launch_ar_eloc(const int8_t* spins, const float* lq, const float* lq
 cudaError_t launch_ar_moments(const int8_t* spins, const MadeWork& w, const float2* E,
                               const double* estats, int64_t n, int N, int H, double* part,
                               int64_t part_cap, double2* meanO, double2* F, cudaStream_t st);
-// X for the Gram: row 2k = O_k(q) - <O_k>, row 2k+1 = 0, zero padded to [rows_pad][ld]
+// X for the Gram in real rows: row k = O_k(q) - <O_k>, zero padded to [rows_pad][ld]
 cudaError_t launch_ar_build_x(const int8_t* spins, const MadeWork& w, const double2* meanO,
                               int64_t n, int N, int H, int64_t rows_pad, int64_t ld, float* X,
                               cudaStream_t st);
