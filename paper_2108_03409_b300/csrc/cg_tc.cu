@@ -54,22 +54,8 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
   return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
 
-// one lane waits, the warp shares the verdict (tcgen05.ld needs the whole warp)
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int lane) {
-  int ok = 0;
-  if (lane == 0) ok = tc::mbar_wait(bar, parity, abort_flag) && !*abort_flag;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-// two FP32 values as packed BF16 pairs x = hi + lo (hi = RN(x), lo = RN(x - hi))
-__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-  const float2 hf = __bfloat1622float2(h);
-  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-  hi = *reinterpret_cast<const uint32_t*>(&h);
-  lo = *reinterpret_cast<const uint32_t*>(&l);
-}
+using tc::split_pair;
+using tc::warp_wait;
 }  // namespace cgtc
 
 // ---------------------------------------------------------------------------------------

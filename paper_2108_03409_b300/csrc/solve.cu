@@ -3,6 +3,7 @@
 // S~ = L L^H, in FP64, or in FP32 followed by FP64 iterative refinement against the
 // FP64 S~.  Diagonal blocks of L are inverted once so that the panel solve and the
 // triangular solves become small matrix products.
+#include "tc_ptx.cuh"
 #include "vmc_device.cuh"
 #include "vmc_internal.h"
 
@@ -89,33 +90,64 @@ __device__ __forceinline__ void pivot_root(double d, double* l, double* il) {
 
 // (Global loads bypass L1 (ld.global.cg): inside the cooperative panel kernel the block
 // may have been written by other CTAs since this SM last cached it.)
-template <typename C>
-__device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
-                           C* __restrict__ Dinv, unsigned* status, unsigned char* psm) {
-  typedef typename RealOf<C>::T R;
-  C* a = reinterpret_cast<C*>(psm);           // [64][PLD]: A -> L
-  C* li = a + NB * PLD;                       // [64][PLD]: Linv
-  C* tt = li + NB * PLD;                      // [64][PLD]: products of the inverse
-  C* cb = tt + NB * PLD;                      // [2][2][64]: published column pair / row
-  R* dg = reinterpret_cast<R*>(cb + 4 * NB);  // [64]: 1 / L_cc
-  const int tid = threadIdx.x;
-  {
-    // all of a thread's loads are issued before any shared-memory store
-    constexpr int PER = NB * NB / POTRF_THREADS;
-    C v[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = tid + POTRF_THREADS * u, r = e >> 6, c = e & 63;
-      v[u] = (r < kw && c <= r) ? __ldcg(&A[(k0 + r) * P + k0 + c])
-                                : mk<C>((r == c && r >= kw) ? 1.0 : 0.0, 0.0);
-    }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = tid + POTRF_THREADS * u, r = e >> 6, c = e & 63;
-      a[r * PLD + c] = v[u];
-      li[r * PLD + c] = mk<C>(0.0, 0.0);
-    }
+// Shared-memory layout of the diagonal-block factorisation (psm: potrf_smem bytes)
+template <typename C> struct PotrfSmem {
+  C* a;    // [64][PLD]: A -> L
+  C* li;   // [64][PLD]: Linv
+  C* tt;   // [64][PLD]: products of the inverse
+  C* cb;   // [2][2][64]: published column pair / row
+  typename RealOf<C>::T* dg;  // [64]: 1 / L_cc
+  __device__ explicit PotrfSmem(unsigned char* psm) {
+    a = reinterpret_cast<C*>(psm);
+    li = a + NB * PLD;
+    tt = li + NB * PLD;
+    cb = tt + NB * PLD;
+    dg = reinterpret_cast<typename RealOf<C>::T*>(cb + 4 * NB);
   }
+};
+
+// the lower triangle of the diagonal block (identity padding beyond kw) into a
+template <typename C>
+__device__ void potrf_load(const C* __restrict__ A, int64_t P, int64_t k0, int kw, C* a) {
+  // all of a thread's loads are issued before any shared-memory store
+  constexpr int PER = NB * NB / POTRF_THREADS;
+  C v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + POTRF_THREADS * u, r = e >> 6, c = e & 63;
+    v[u] = (r < kw && c <= r) ? __ldcg(&A[(k0 + r) * P + k0 + c])
+                              : mk<C>((r == c && r >= kw) ? 1.0 : 0.0, 0.0);
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + POTRF_THREADS * u, r = e >> 6, c = e & 63;
+    a[r * PLD + c] = v[u];
+  }
+}
+
+// L and Linv back to A and Dinv
+template <typename C>
+__device__ void potrf_store(C* __restrict__ A, int64_t P, int64_t k0, int kw,
+                            C* __restrict__ Dinv, const C* a, const C* li) {
+  for (int e = threadIdx.x; e < NB * NB; e += POTRF_THREADS) {
+    const int r = e >> 6, c = e & 63;
+    if (r < kw && c <= r) A[(k0 + r) * P + k0 + c] = a[r * PLD + c];
+    Dinv[e] = (r < kw && c < kw && c <= r) ? li[r * PLD + c] : mk<C>(0.0, 0.0);
+  }
+}
+
+// Factor the block held in sm.a (lower triangle, identity padding) in place and form its
+// inverse in sm.li; returns with a barrier passed after the last shared-memory write.
+template <typename C>
+__device__ void potrf_core(unsigned* status, const PotrfSmem<C>& sm) {
+  typedef typename RealOf<C>::T R;
+  C* a = sm.a;
+  C* li = sm.li;
+  C* tt = sm.tt;
+  C* cb = sm.cb;
+  R* dg = sm.dg;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += POTRF_THREADS) li[(e >> 6) * PLD + (e & 63)] = mk<C>(0.0, 0.0);
   __syncthreads();
   bool bad = false;
   const int warp = tid >> 5, lane = tid & 31;
@@ -313,11 +345,15 @@ __device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
       }
     __syncthreads();
   }
-  for (int e = tid; e < NB * NB; e += POTRF_THREADS) {
-    const int r = e >> 6, c = e & 63;
-    if (r < kw && c <= r) A[(k0 + r) * P + k0 + c] = a[r * PLD + c];
-    Dinv[e] = (r < kw && c < kw && c <= r) ? li[r * PLD + c] : mk<C>(0.0, 0.0);
-  }
+}
+
+template <typename C>
+__device__ void potrf_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
+                           C* __restrict__ Dinv, unsigned* status, unsigned char* psm) {
+  const PotrfSmem<C> sm(psm);
+  potrf_load<C>(A, P, k0, kw, sm.a);
+  potrf_core<C>(status, sm);
+  potrf_store<C>(A, P, k0, kw, Dinv, sm.a, sm.li);
 }
 
 template <typename C>
@@ -563,22 +599,206 @@ __device__ __forceinline__ bool cta_wait(const unsigned* word, unsigned target,
 }
 
 // ---------------------------------------------------------------------------------------
-// Factorisation of one 512-wide panel (columns p0 .. pend, all rows below) in a single
-// cooperative launch.  Per 64-column block k (k1 = the next block):
-//   * the chain CTAs 0..3 solve the row block k1 against the block inverse in 16-row slabs,
-//     count them done, wait (bounded) for all four, update their 16-row slabs of the
-//     diagonal tile (k1, k1) and count again; CTA 0 waits for the four and factors the
-//     tile (look-ahead: the critical path is one slab solve, one slab update and one
-//     diagonal factorisation);
-//   * the other CTAs solve the remaining row blocks, count them done, wait (bounded) until
-//     every row block of step k is solved, and apply block k's update to the rest of the
-//     panel (all trapezoid tiles but the diagonal one);
-//   * one grid barrier ends the step.
-// With fewer than 8 CTAs, CTA 0 alone does the chain's work on whole 64-row blocks.
-// The panel's first diagonal block is factored before the loop.  sync: the grid barrier
-// (3 words, then a spare), then per step the row-block counter, the slab-solve counter and
-// the slab-update counter, zeroed before the launch.
+// In-panel trailing update on the tensor cores: the other CTAs' tiles of a panel step,
+//   A[r][c] -= sum_m X[r][m] conj(X[c][m]),  X = the step's 64 solved columns,
+// as one real product per 64 x 64 tile.  The 64 rows of X of a tile row (or column) become
+// a 128 x 64 BF16 operand, real row 2 rho = Re X[rho], 2 rho + 1 = Im X[rho], split into
+// hi + lo (three products hi.hi^T + hi.lo^T + lo.hi^T accumulate in FP32 in tensor memory,
+// as in the Schur updates between panels); the 2 x 2 blocks of the 128 x 128 product fold
+// to the complex tile.  A CTA takes whole tile rows: the row operand is formed once, the
+// column operands per tile; the operands are written into shared memory in the 128-byte
+// swizzled K-major layout the MMA descriptors name.  One thread issues the products and
+// commits them to an mbarrier; the wait is bounded.
 // ---------------------------------------------------------------------------------------
+namespace ptc {
+constexpr int OP = 128 * 128;                    // one operand plane: 128 rows x 128 bytes
+constexpr int A_HI = 0, A_LO = OP, B_HI = 2 * OP, B_LO = 3 * OP, STG = 4 * OP;
+constexpr int STG_LD = NB + 1;                   // staging row stride (float2)
+constexpr size_t SMEM = 4 * OP + (size_t)NB * STG_LD * sizeof(float2);
+constexpr int TMEM_COLS = 128;                   // one 128 x 128 FP32 accumulator
+}  // namespace ptc
+
+// rows row0 .. row0 + 63 of the block columns k0 .. k0 + kw of A into stg (zero beyond P
+// and kw), coalesced along rows
+__device__ __forceinline__ void ptc_stage(const float2* __restrict__ A, int64_t P, int64_t k0,
+                                          int kw, int64_t row0, float2* stg) {
+  constexpr int PER = NB * NB / 256;
+  float2 v[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + 256 * u, rho = e >> 6, m = e & 63;
+    const int64_t row = row0 + rho;
+    v[u] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int e = threadIdx.x + 256 * u;
+    stg[(e >> 6) * ptc::STG_LD + (e & 63)] = v[u];
+  }
+}
+
+// the staged 64 x 64 complex block as the swizzled BF16 hi/lo operand planes; work item
+// (rho, ch) packs columns 8 ch .. 8 ch + 7 of row rho into one 16-byte chunk of each of
+// the real rows 2 rho (Re) and 2 rho + 1 (Im) of both planes
+__device__ __forceinline__ void ptc_pack(const float2* stg, uint8_t* hi, uint8_t* lo) {
+  for (int it = threadIdx.x; it < NB * 8; it += 256) {
+    const int rho = it >> 3, ch = it & 7;
+    const float2* src = stg + rho * ptc::STG_LD + 8 * ch;
+    uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 a = src[2 * e], b = src[2 * e + 1];
+      tc::split_pair(a.x, b.x, rh[e], rl[e]);
+      tc::split_pair(a.y, b.y, ih[e], il[e]);
+    }
+    const uint32_t o0 = tc::sw128_offset(2 * rho, ch), o1 = tc::sw128_offset(2 * rho + 1, ch);
+    *reinterpret_cast<uint4*>(hi + o0) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+    *reinterpret_cast<uint4*>(lo + o0) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+    *reinterpret_cast<uint4*>(hi + o1) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+    *reinterpret_cast<uint4*>(lo + o1) = make_uint4(il[0], il[1], il[2], il[3]);
+  }
+  tc::fence_proxy_async_smem();                  // generic writes -> the MMA's async reads
+}
+
+// Row block g (rows r0 ..) of step k against the panel's column blocks c = c_lo .. c_hi
+// (columns p0 + 64 c ..; c_hi <= g, tile (g, g) lower only).  Before the column operand of
+// block c != g is formed, the CTA waits (bounded) until xready[c] reaches 1 (nchain for
+// block c_lo, which the chain CTAs solve in slabs): the step's solved rows of block c are
+// in A.  sm: 1024-byte aligned, ptc::SMEM bytes.  Returns
+// false if a wait expired (DEV_ERR_TIMEOUT recorded, the abort word set).
+__device__ __noinline__ bool herk_row_tc(float2* __restrict__ A, int64_t P, int64_t k0, int kw,
+                                         int64_t p0, int g, int c_lo, int c_hi,
+                                         const unsigned* xready, unsigned nchain, uint8_t* sm,
+                                         uint32_t tmem,
+                                         uint32_t mbar, uint32_t* phase, volatile int* tc_abort,
+                                         int* issued, unsigned* abort_word, unsigned* status) {
+  using namespace ptc;
+  float2* stg = reinterpret_cast<float2*>(sm + STG);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t r0 = p0 + (int64_t)g * NB;
+  if (c_lo > c_hi) return true;
+  __syncthreads();                               // the previous user of the buffers is done
+  ptc_stage(A, P, k0, kw, r0, stg);
+  __syncthreads();
+  ptc_pack(stg, sm + A_HI, sm + A_LO);
+  for (int c = c_lo; c <= c_hi; ++c) {
+    const int64_t c0 = p0 + (int64_t)c * NB;
+    const bool diag = c == g;
+    if (!diag) {
+      if (!cta_wait(&xready[c], c == c_lo ? nchain : 1u, abort_word, status)) return false;
+      ptc_stage(A, P, k0, kw, c0, stg);          // (cta_wait ends with a barrier)
+      __syncthreads();
+      ptc_pack(stg, sm + B_HI, sm + B_LO);
+    }
+    // the tile's current values, fetched before the products complete
+    float2 cur[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * u, rho = e >> 6, q = e & 63;
+      const int64_t row = r0 + rho, col = c0 + q;
+      cur[u] = (row < P && col < P && (!diag || q <= rho)) ? __ldcg(&A[row * P + col])
+                                                           : make_float2(0.f, 0.f);
+    }
+    tc::fence_before();
+    __syncthreads();                             // operands written; accumulator drained
+    if (tid == 0) {
+      tc::fence_after();
+      constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+      const uint64_t ah = tc::smem_desc_sw128(tc::smem_u32(sm + A_HI));
+      const uint64_t al = tc::smem_desc_sw128(tc::smem_u32(sm + A_LO));
+      const uint64_t bh = tc::smem_desc_sw128(tc::smem_u32(sm + (diag ? A_HI : B_HI)));
+      const uint64_t bl = tc::smem_desc_sw128(tc::smem_u32(sm + (diag ? A_LO : B_LO)));
+#pragma unroll
+      for (int kk = 0; kk < NB / 16; ++kk) {
+        const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 BF16 along K
+        tc::mma_bf16(tmem, ah + o, bh + o, idesc, kk > 0 ? 1u : 0u);
+        tc::mma_bf16(tmem, ah + o, bl + o, idesc, 1u);
+        tc::mma_bf16(tmem, al + o, bh + o, idesc, 1u);
+      }
+      tc::mma_commit(mbar);
+      *issued = 1;
+    }
+    const bool okw = tc::warp_wait(mbar, *phase, tc_abort, lane);
+    *phase ^= 1u;
+    if (!__syncthreads_and(okw ? 1 : 0)) {
+      if (tid == 0) {
+        atomicExch(abort_word, 1u);
+        flag_error(status, DEV_ERR_TIMEOUT);
+      }
+      return false;
+    }
+    tc::fence_after();
+    // fold: warp w reads TMEM lanes 32 (w % 4) .. (real rows) and columns 64 (w / 4) ..;
+    // row pairs (2 rho, 2 rho + 1) sit in adjacent lanes.  The even row stages the even
+    // column pairs, the odd row the odd ones.
+    const int qd = warp & 3, hs = warp >> 2;
+    const int i = 32 * qd + lane, rho = i >> 1;
+    const bool even = (i & 1) == 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      float v[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(64 * hs + 32 * j), v);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
+        const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
+        const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
+        if ((q & 1) == (even ? 0 : 1)) {
+          // X_r conj(X_c) = (Re_r Re_c + Im_r Im_c) + i (Im_r Re_c - Re_r Im_c)
+          const float re = even ? mine0 + oth1 : oth0 + mine1;
+          const float im = even ? oth0 - mine1 : mine0 - oth1;
+          stg[rho * STG_LD + 32 * hs + 16 * j + q] = make_float2(re, im);
+        }
+      }
+    }
+    tc::fence_before();
+    __syncthreads();                             // staging complete
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int e = tid + 256 * u, rr = e >> 6, q = e & 63;
+      const int64_t row = r0 + rr, col = c0 + q;
+      if (row < P && col < P && (!diag || q <= rr)) {
+        const float2 f = stg[rr * STG_LD + q];
+        float2 v = cur[u];
+        v.x -= f.x;
+        if (row != col) v.y -= f.y;              // the diagonal stays real
+        A[row * P + col] = v;
+      }
+    }
+    __syncthreads();                             // stg read before it is restaged
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Factorisation of one 512-wide panel (columns p0 .. pend, all rows below) in a single
+// cooperative launch, as a dataflow without grid barriers.  Blocks of 64 rows/columns are
+// numbered from p0 (block g = rows p0 + 64 g ..); the panel holds blocks 0 .. ns - 1.
+// Step k (k < ns) solves every row block g > k against the inverse of the diagonal block
+// k, X_gk = A_gk Linv_k^H, and updates A_gc -= X_gk X_ck^H for k < c <= min(g, ns - 1).
+//   * The chain CTAs 0 .. 3 take row block k + 1 through step k: once the owner of that
+//     block has finished step k - 1 on it (and Linv_k is out), each solves a 16-row slab
+//     and counts it on the step's ready word of the block; CTA 0 then reads the four slabs
+//     and the diagonal tile, updates the tile, factors it and publishes Linv_{k+1}.  The
+//     critical path per step is one slab solve, one tile update and one diagonal
+//     factorisation, with no grid barrier.
+//   * Every other row block g has an owner CTA, 4 + (g - 1) mod (G - 4), which runs the
+//     steps k the chain does not (all k for g >= ns; k <= g - 2 for panel blocks): wait
+//     for Linv_k, solve, publish the solved rows if g is a panel block (later steps' tiles
+//     read them), then update its tiles on the tensor cores, waiting for each column
+//     block's solved rows.  A panel block's owner reports when its step g - 2 is done.
+// Owners take their blocks in ascending order within a step, and steps in order; every
+// wait is on an earlier step or a smaller block, so the waits form no cycle.  Every wait is
+// bounded; an expired one sets DEV_ERR_TIMEOUT and the abort word, which every wait checks.
+// Sync words (zeroed before the launch): [2] the abort word, then linv[ns] (Linv_k in
+// Dinv), xready[ns][ns] (step k's solved rows of block c in A: one count per chain slab
+// for c = k + 1, else 1), own[ns] (step g - 2 done on panel block g).
+// ---------------------------------------------------------------------------------------
+constexpr int PANEL_MAX_STEPS = 8;                 // 64-column blocks per panel (NBO / 64)
+constexpr int PANEL_SYNC_WORDS = 4 + PANEL_MAX_STEPS * (PANEL_MAX_STEPS + 2);
+constexpr unsigned PANEL_CHAIN = 4;                // chain CTAs (16-row slabs of a block)
+static_assert(PANEL_SYNC_WORDS <= 128, "panel sync words");
+
 // 16 rows r0 .. r0 + 15 of X = B L_kk^{-H} (as trsm_body); thread (row ry, columns tx + 16 b)
 __device__ void trsm_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw,
                           const float2* __restrict__ Dinv, int64_t r0, unsigned char* sm,
@@ -629,148 +849,182 @@ __device__ void trsm_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw,
     }
 }
 
-// Rows k1 + 16 sl .. + 15 of the diagonal tile (k1, k1), lower part:
-// A[r][c] -= sum_m X[r][m] conj(X[c][m]) for c <= r (as herk_tile_body), X = A[.][k0 .. k0+kw)
-__device__ void herk_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw, int64_t k1,
-                          int sl, unsigned char* sm) {
-  float2* Xc = reinterpret_cast<float2*>(sm);    // [NB (m)][NB + 1 (tile row)]
-  const int tid = threadIdx.x;
-  const int nr = 16 * sl + 16;                   // tile rows 0 .. nr - 1 are needed
-  const int ry = tid >> 4, tx = tid & 15;
-  const int64_t r = k1 + 16 * sl + ry;
-  float2 cur[4];
+// CTA 0's part of a chain step: the diagonal tile of block g (rows r0 .., width kw1) less
+// X X^H (X = the step's solved rows of block g, columns k0 .. k0 + kw, already in A),
+// factored; L and Linv go to A and Dinv1.  The tile is read before the wait for the slabs.
+__device__ void chain_diag(float2* __restrict__ A, int64_t P, int64_t k0, int kw, int64_t r0,
+                           int kw1, float2* __restrict__ Dinv1, const unsigned* ready,
+                           unsigned* abort_word, unsigned* status, unsigned char* csm,
+                           bool* ok) {
+  const PotrfSmem<float2> sm(csm);
+  float2* X = sm.tt;                             // [64][PLD]
+  potrf_load<float2>(A, P, r0, kw1, sm.a);
+  if (!cta_wait(ready, PANEL_CHAIN, abort_word, status)) { *ok = false; return; }
+  {
+    constexpr int PER = NB * NB / 256;
+    float2 xv[PER];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t c = k1 + tx + 16 * q;
-    cur[q] = (q <= sl && r < P && c <= r) ? __ldcg(&A[r * P + c]) : make_float2(0.f, 0.f);
-  }
-  for (int e = tid; e < nr * NB; e += 256) {
-    const int rr = e / NB, m = e % NB;
-    const int64_t row = k1 + rr;
-    Xc[m * (NB + 1) + rr] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  float2 acc[4];
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + 256 * u, r = e >> 6, m = e & 63;
+      const int64_t row = r0 + r;
+      xv[u] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : make_float2(0.f, 0.f);
+    }
 #pragma unroll
-  for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
-  for (int m = 0; m < kw; ++m) {
-    const float2 xr = Xc[m * (NB + 1) + 16 * sl + ry];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (q <= sl) cfmac(acc[q], xr, Xc[m * (NB + 1) + tx + 16 * q]);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int64_t c = k1 + tx + 16 * q;
-    if (q <= sl && r < P && c <= r) {
-      float2 v = cur[q];
-      v.x -= acc[q].x;
-      v.y -= acc[q].y;
-      A[r * P + c] = v;
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      X[(e >> 6) * PLD + (e & 63)] = xv[u];
     }
   }
+  __syncthreads();
+  // a[r][c] -= sum_m X[r][m] conj(X[c][m]) for c <= r: thread (ty, tx) holds the entries
+  // (ty + 16 p, tx + 16 q) with q <= p (the blocks above the diagonal are never formed)
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float2 acc[10];
+#pragma unroll
+  for (int u = 0; u < 10; ++u) acc[u] = make_float2(0.f, 0.f);
+#pragma unroll 4
+  for (int m = 0; m < kw; ++m) {
+    float2 xr[4], xc[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) xr[p] = X[(ty + 16 * p) * PLD + m];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) xc[q] = X[(tx + 16 * q) * PLD + m];
+#pragma unroll
+    for (int p = 0, u = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q <= p; ++q, ++u) cfmac(acc[u], xr[p], xc[q]);
+  }
+#pragma unroll
+  for (int p = 0, u = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q <= p; ++q, ++u) {
+      const int r = ty + 16 * p, c = tx + 16 * q;
+      if (c <= r && r < kw1) {
+        float2& d = sm.a[r * PLD + c];
+        d.x -= acc[u].x;
+        if (c != r) d.y -= acc[u].y;
+      }
+    }
+  potrf_core<float2>(status, sm);
+  potrf_store<float2>(A, P, r0, kw1, Dinv1, sm.a, sm.li);
 }
-
-constexpr size_t PANEL_SMEM = (size_t)(3 * NB * (NB + 1) + 5 * NB) * sizeof(float2);
-constexpr int PANEL_MAX_STEPS = 32;                // 64-column blocks per panel (>= NBO / 64)
-// grid barrier + spare, then three counters per step; the context allocates at least 128
-// words for the solve's sync buffer
-constexpr int PANEL_SYNC_WORDS = 4 + 3 * PANEL_MAX_STEPS;
-static_assert(PANEL_SYNC_WORDS <= 128, "panel sync words");
 
 __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int64_t P,
                                                     int64_t p0, int64_t pend,
                                                     float2* __restrict__ Dinv,
-                                                    GridBarrier* bar, unsigned* status,
+                                                    unsigned* sync, unsigned* status,
                                                     XOut xpanel) {
-  extern __shared__ unsigned char csm[];
+  extern __shared__ unsigned char csm_raw[];
+  unsigned char* csm = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(csm_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t tc_bar[2];                 // products done; drain after an abort
+  __shared__ uint32_t tc_slot;
+  __shared__ int tc_abort;
   const unsigned G = gridDim.x, b = blockIdx.x;
-  const unsigned NC = (G >= 8) ? 4u : 1u;        // chain CTAs
-  unsigned* done = reinterpret_cast<unsigned*>(bar) + 4;
-  unsigned* xdone = done + PANEL_MAX_STEPS;
-  unsigned* hdone = xdone + PANEL_MAX_STEPS;
-  if (b == 0) potrf_body<float2>(A, P, p0, (int)min((int64_t)NB, P - p0), Dinv + (p0 / NB) * NB * NB, status, csm);
-  if (!grid_sync(bar, G, status)) return;
-  int step = 0;
-  for (int64_t k0 = p0; k0 < pend; k0 += NB, ++step) {
-    const int kw = (int)min((int64_t)NB, P - k0);
-    const int64_t k1 = k0 + kw, rest = P - k1;
-    if (rest <= 0) break;
-    const float2* Di = Dinv + (k0 / NB) * NB * NB;
-    const int64_t nrb = (rest + NB - 1) / NB;
-    const bool last = k1 >= pend;                  // no update inside the panel after this
-    XOut xo = xpanel;                              // this block's columns of the operand
-    xo.m0 = (int)(k0 - p0);
-    if (b < NC && NC > 1) {
-      trsm_slab(A, P, k0, kw, Di, k1 + 16 * (int64_t)b, csm, xo);
+  const int ns = (int)((pend - p0 + NB - 1) / NB);
+  const int NG = (int)((P - p0 + NB - 1) / NB); // row blocks from p0
+  unsigned* abort_word = sync + 2;
+  unsigned* linv = sync + 4;                     // [ns]
+  unsigned* xready = linv + PANEL_MAX_STEPS;     // [ns][ns]
+  unsigned* own = xready + PANEL_MAX_STEPS * PANEL_MAX_STEPS;   // [ns]
+  const int warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(tc::smem_u32(&tc_bar[0]), 1);
+    tc::mbar_init(tc::smem_u32(&tc_bar[1]), 1);
+    tc_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(tc::smem_u32(&tc_slot)), "r"(ptc::TMEM_COLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tc_slot;
+  uint32_t tc_phase = 0;
+  int tc_issued = 0;
+  auto blk_w = [&](int g) { return (int)min((int64_t)NB, P - (p0 + (int64_t)g * NB)); };
+  auto xo_of = [&](int k) { XOut xo = xpanel; xo.m0 = k * NB; return xo; };
+  auto dinv_of = [&](int g) { return Dinv + ((p0 + (int64_t)g * NB) / NB) * NB * NB; };
+
+  if (b < PANEL_CHAIN) {
+    // ---------------- the chain ----------------
+    bool ok = true;
+    if (b == 0) {
+      potrf_body<float2>(A, P, p0, blk_w(0), dinv_of(0), status, csm);
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) {
-        atomicAdd(&done[step], 1u);
-        atomicAdd(&xdone[step], 1u);
-      }
-      if (last) break;
-      if (!cta_wait(&xdone[step], NC, &bar->abort, status)) return;
-      herk_slab(A, P, k0, kw, k1, (int)b, csm);
+      if (threadIdx.x == 0) atomicExch(&linv[0], 1u);
+    }
+    for (int k = 0; ok && k + 1 < ns; ++k) {
+      const int g = k + 1;
+      if (k >= 1 && !cta_wait(&own[g], 1u, abort_word, status)) break;
+      if (b != 0 && !cta_wait(&linv[k], 1u, abort_word, status)) break;
+      const int64_t k0 = p0 + (int64_t)k * NB, r0 = p0 + (int64_t)g * NB;
+      trsm_slab(A, P, k0, blk_w(k), dinv_of(k), r0 + 16 * (int64_t)b, csm, xo_of(k));
       __threadfence();
       __syncthreads();
-      if (threadIdx.x == 0) atomicAdd(&hdone[step], 1u);
+      if (threadIdx.x == 0) atomicAdd(&xready[k * PANEL_MAX_STEPS + g], 1u);
       if (b == 0) {
-        if (!cta_wait(&hdone[step], NC, &bar->abort, status)) return;
-        potrf_body<float2>(A, P, k1, (int)min((int64_t)NB, P - k1), Dinv + (k1 / NB) * NB * NB, status, csm);
-      }
-    } else if (b == 0) {
-      trsm_body<float2>(A, P, k0, kw, Di, k1, csm, xo);
-      __syncthreads();
-      if (G == 1)
-        for (int64_t rb = 1; rb < nrb; ++rb) {
-          trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm, xo);
-          __syncthreads();
-        }
-      if (last) break;
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0) atomicAdd(&done[step], 1u);
-      herk_tile_body<float2>(A, P, k0, kw, k1, k1, csm);
-      __syncthreads();
-      if (G == 1) {
-        const int64_t nt = nrb, nct = (pend - k1 + NB - 1) / NB;
-        const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
-        for (int64_t t = 1; t < tiles; ++t) {
-          int64_t tm, tn;
-          trapezoid_tile(t, nt, &tm, &tn);
-          herk_tile_body<float2>(A, P, k0, kw, k1 + tm * NB, k1 + tn * NB, csm);
-          __syncthreads();
-        }
-      }
-      potrf_body<float2>(A, P, k1, (int)min((int64_t)NB, P - k1), Dinv + (k1 / NB) * NB * NB, status, csm);
-    } else if (b >= NC) {
-      // row blocks 1 .. nrb-1 and trapezoid tiles 1 .. over the CTAs NC .. G-1
-      const unsigned W = G - NC, me = b - NC;
-      unsigned mine = 0;
-      for (int64_t rb = 1 + me; rb < nrb; rb += W) {
-        trsm_body<float2>(A, P, k0, kw, Di, k1 + rb * NB, csm, xo);
+        chain_diag(A, P, k0, blk_w(k), r0, blk_w(g), dinv_of(g),
+                   &xready[k * PANEL_MAX_STEPS + g], abort_word, status, csm, &ok);
+        if (!ok) break;
+        __threadfence();
         __syncthreads();
-        ++mine;
-      }
-      if (last) break;
-      __threadfence();
-      __syncthreads();
-      if (threadIdx.x == 0 && mine) atomicAdd(&done[step], mine);
-      // every row block of this step solved (the chain CTAs' slabs count one each)
-      if (!cta_wait(&done[step], (unsigned)(nrb - 1) + NC, &bar->abort, status)) return;
-      const int64_t nt = nrb, nct = (pend - k1 + NB - 1) / NB;
-      const int64_t tiles = nct * nt - nct * (nct - 1) / 2;
-      for (int64_t t = 1 + me; t < tiles; t += W) {
-        int64_t tm, tn;
-        trapezoid_tile(t, nt, &tm, &tn);
-        herk_tile_body<float2>(A, P, k0, kw, k1 + tm * NB, k1 + tn * NB, csm);
-        __syncthreads();
+        if (threadIdx.x == 0) atomicExch(&linv[g], 1u);
       }
     }
-    if (!grid_sync(bar, G, status)) return;
+  } else if (G > PANEL_CHAIN) {
+    // ---------------- row-block owners ----------------
+    const int W = (int)(G - PANEL_CHAIN);
+    bool ok = true;
+    for (int k = 0; ok && k < ns; ++k) {
+      bool waited = false;
+      for (int g = 1 + (int)(b - PANEL_CHAIN); ok && g < NG; g += W) {
+        if (g <= k || (g < ns && k > g - 2)) continue;   // solved, or the chain's step
+        if (!waited) {
+          if (!cta_wait(&linv[k], 1u, abort_word, status)) { ok = false; break; }
+          waited = true;
+        }
+        const int64_t k0 = p0 + (int64_t)k * NB;
+        const int kw = blk_w(k);
+        trsm_body<float2>(A, P, k0, kw, dinv_of(k), p0 + (int64_t)g * NB, csm, xo_of(k));
+        __threadfence();
+        __syncthreads();
+        if (g < ns && threadIdx.x == 0) atomicExch(&xready[k * PANEL_MAX_STEPS + g], 1u);
+        ok = herk_row_tc(A, P, k0, kw, p0, g, k + 1, min(g, ns - 1),
+                         &xready[k * PANEL_MAX_STEPS], PANEL_CHAIN, csm, tmem,
+                         tc::smem_u32(&tc_bar[0]), &tc_phase, &tc_abort, &tc_issued, abort_word,
+                         status);
+        if (ok && g < ns && k == g - 2) {
+          __threadfence();
+          __syncthreads();
+          if (threadIdx.x == 0) atomicExch(&own[g], 1u);
+        }
+      }
+    }
+  }
+  // products still in flight after an expired wait finish before the tensor memory is
+  // freed (bounded)
+  tc::fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && tc_abort && tc_issued) {
+    volatile int dummy = 0;
+    tc::mma_commit(tc::smem_u32(&tc_bar[1]));
+    tc::mbar_wait(tc::smem_u32(&tc_bar[1]), 0, &dummy);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(ptc::TMEM_COLS) : "memory");
   }
 }
+
+constexpr size_t PANEL_SMEM = 1024 + (size_t)(3 * NB * (NB + 1) + 5 * NB) * sizeof(float2);
+static_assert(PANEL_SMEM >= 1024 + ptc::SMEM, "panel shared memory holds the tensor-core tiles");
 
 // Steps of SB = 256 rows.  After the factorisation the inverse of every 256 x 256 diagonal
 // block is formed once (k_inv_sb); each block of the cooperative solve then applies it to
@@ -1446,10 +1700,11 @@ static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, u
     VMC_TRY(cudaGetDevice(&dev));
     VMC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     VMC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_coop, 256, PANEL_SMEM));
-    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    grid = sms;                                     // one CTA per SM
+    // one CTA per SM; the chain needs at least one row-block owner beside it
+    if (per_sm < 1 || sms <= (int)PANEL_CHAIN) return cudaErrorCooperativeLaunchTooLarge;
+    grid = sms;
   }
-  GridBarrier* bar = reinterpret_cast<GridBarrier*>(w.bar);
+  unsigned* sync = w.bar;
   for (int64_t p0 = 0; p0 < P; p0 += NBO) {
     const int64_t pend = std::min<int64_t>(P, p0 + NBO);
     // the rows below the panel go, as they are solved, into the BF16 hi/lo operand planes of
@@ -1468,9 +1723,9 @@ static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, u
       xo.hi = w.Xhi;
       xo.lo = w.Xlo;
     }
-    VMC_TRY(cudaMemsetAsync(bar, 0, PANEL_SYNC_WORDS * sizeof(unsigned), st));
-    void* args[] = {(void*)&A,   (void*)&P,      (void*)&p0, (void*)&pend, (void*)&Dinv,
-                    (void*)&bar, (void*)&status, (void*)&xo};
+    VMC_TRY(cudaMemsetAsync(sync, 0, PANEL_SYNC_WORDS * sizeof(unsigned), st));
+    void* args[] = {(void*)&A,    (void*)&P,      (void*)&p0, (void*)&pend, (void*)&Dinv,
+                    (void*)&sync, (void*)&status, (void*)&xo};
     VMC_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3(grid), dim3(256), args,
                                         PANEL_SMEM, st));
     ++*launches;

@@ -236,6 +236,24 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// one lane waits, the warp shares the verdict (tcgen05.ld needs the whole warp)
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          int lane) {
+  int ok = 0;
+  if (lane == 0) ok = mbar_wait(bar, parity, abort_flag) && !*abort_flag;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// two FP32 values as packed BF16 pairs x = hi + lo (hi = RN(x), lo = RN(x - hi)); the first
+// value in the low half (the lower address, i.e. the lower K index)
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
 // Byte offset of the 16-byte chunk ch (0..7) of row r in a K-major tile with 128-byte rows
 // and 128-byte swizzle (the layout TMA writes with CU_TENSOR_MAP_SWIZZLE_128B): chunks are
 // permuted by XOR with the row's position in its 8-row atom.
