@@ -380,7 +380,7 @@ def _sr_arm(wl, prec, solver, steps, warmup, rank, stream, clk_index, vmc, input
     cg = solver == vmc.SOLVER_CG
     cfg = vmc.make_config(seed=1 + rank, n_chains=CHAINS, therm_sweeps=20, sweeps_per_sample=1,
                           samples_per_chain=wl["spc"], precision=prec, solver=solver, shift=SHIFT,
-                          cg_tol=1e-6, cg_maxit=100 if cg else 50)
+                          cg_tol=1e-6, cg_maxit=1000 if cg else 50)
     lat = vmc.make_lattice(wl["model"], LX, LY, wl["J"], wl["h"], ALPHA)
     ctx = vmc.vmc_init(cfg, [lat], stream.cuda_stream)
     p0 = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(LX, LY) if wl["marshall"] else None)

@@ -44,12 +44,38 @@ static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 }  // namespace tc
 
+// Tile t of the lower triangle of nt x nt tiles.  tail > 0 (Schur updates): the tiles of
+// the first tail tile columns -- the next panel's columns -- come last, column by column,
+// so that they are the most recently written lines in L2 when the next panel starts.
+__device__ __forceinline__ void schur_tile(int64_t t, int nt, int tail, int* bm, int* bn) {
+  if (tail <= 0) {
+    grouped_tri_tile(t, nt, 12, bm, bn);
+    return;
+  }
+  const int n1 = nt - tail;
+  const int64_t t1 = (int64_t)n1 * (n1 + 1) / 2;
+  if (t < t1) {
+    grouped_tri_tile(t, n1, 12, bm, bn);
+    *bm += tail;
+    *bn += tail;
+    return;
+  }
+  int64_t u = t - t1;                  // column c < tail holds tile rows c .. nt - 1
+  int c = 0;
+  while (c < tail - 1 && u >= nt - c) {
+    u -= nt - c;
+    ++c;
+  }
+  *bn = c;
+  *bm = c + (int)u;
+}
+
 template <bool LOLO>
 __global__ void __launch_bounds__(tc::THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
           int nk, int nt, int64_t tiles, int64_t P, double inv_n, double2* __restrict__ S,
           float4* __restrict__ S2, float2* __restrict__ Af, double nu, int shift_mode, int mirror,
-          float2* __restrict__ A32, int64_t ldA, int64_t off, int kchunks, int nkpc,
+          float2* __restrict__ A32, int64_t ldA, int64_t off, int tail, int kchunks, int nkpc,
           float2* __restrict__ part, unsigned* status) {
   using namespace tc;
   extern __shared__ uint8_t gsm_raw[];
@@ -92,7 +118,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       int64_t g = 0;                                  // k-blocks issued so far
       for (int64_t t = blockIdx.x; t < tiles * kchunks && !*abort_flag; t += gridDim.x) {
         int bm, bn;
-        grouped_tri_tile(t % tiles, nt, 12, &bm, &bn);
+        schur_tile(t % tiles, nt, tail, &bm, &bn);
         const int kbeg = (int)(t / tiles) * nkpc, kend = min(nk, kbeg + nkpc);
         for (int kb = kbeg; kb < kend; ++kb, ++g) {
           const int s = (int)(g % STAGES);
@@ -168,7 +194,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     for (int64_t t = blockIdx.x; t < tiles * kchunks; t += gridDim.x, ++i) {
       const int acc = i & 1, u = i >> 1;
       int bm, bn;
-      grouped_tri_tile(t % tiles, nt, 12, &bm, &bn);
+      schur_tile(t % tiles, nt, tail, &bm, &bn);
       const int kc = (int)(t / tiles);
       // Schur mode: fetch this thread's 32 entries of the factor's tile now, so that their
       // memory latency overlaps the wait for the products (no stores intervene).
@@ -405,7 +431,7 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
   auto kern = lolo ? k_gram_tc<true> : k_gram_tc<false>;
   kern<<<persistent_grid(tiles * kchunks), tc::THREADS, tc::SMEM_BYTES, st>>>(
       mhi, mlo, nkb, (int)nt, tiles, P, inv_n, S, S2, Af, nu, shift_mode, mirror ? 1 : 0,
-      nullptr, 0, 0, kchunks, nkpc, kchunks > 1 ? part : nullptr, status);
+      nullptr, 0, 0, 0, kchunks, nkpc, kchunks > 1 ? part : nullptr, status);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (kchunks > 1)
     return launch_gram_reduce(part, kchunks, P, inv_n, S, S2, Af, nu, shift_mode, mirror, st);
@@ -414,7 +440,7 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
 
 cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, int64_t rows_pad,
                            int64_t K, int64_t n, float2* A32, int64_t ldA, int64_t off,
-                           unsigned* status, cudaStream_t st) {
+                           int tail_cols, unsigned* status, cudaStream_t st) {
   if (rows_pad % tc::BM != 0 || K % tc::BK != 0 || K < tc::BK) return cudaErrorNotSupported;
   CUtensorMap mhi, mlo;
   cudaError_t e;
@@ -432,9 +458,12 @@ cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, i
   }
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
+  // the first tail_cols columns (128-row tiles of the real operand = 64 complex columns)
+  // are updated last
+  const int tail = (int)std::min<int64_t>(nt, std::max<int64_t>(0, (tail_cols + 63) / 64));
   k_gram_tc<false><<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
       mhi, mlo, (int)(K / tc::BK), (int)nt, tiles, n, 1.0, nullptr, nullptr, nullptr, 0.0, 0, 0,
-      A32, ldA, off, 1, (int)(K / tc::BK), nullptr, status);
+      A32, ldA, off, tail, 1, (int)(K / tc::BK), nullptr, status);
   return cudaGetLastError();
 }
 

@@ -618,20 +618,21 @@ constexpr size_t SMEM = 4 * OP + (size_t)NB * STG_LD * sizeof(float2);
 constexpr int TMEM_COLS = 128;                   // one 128 x 128 FP32 accumulator
 }  // namespace ptc
 
-// rows row0 .. row0 + 63 of the block columns k0 .. k0 + kw of A into stg (zero beyond P
-// and kw), coalesced along rows
-__device__ __forceinline__ void ptc_stage(const float2* __restrict__ A, int64_t P, int64_t k0,
-                                          int kw, int64_t row0, float2* stg) {
-  constexpr int PER = NB * NB / 256;
-  float2 v[PER];
+// rows row0 .. row0 + 63 of the block columns k0 .. k0 + kw of A (zero beyond P and kw), 16
+// entries per thread, coalesced along rows; ptc_put stages them into stg
+__device__ __forceinline__ void ptc_load(const float2* __restrict__ A, int64_t P, int64_t k0,
+                                         int kw, int64_t row0, float2 (&v)[NB * NB / 256]) {
 #pragma unroll
-  for (int u = 0; u < PER; ++u) {
+  for (int u = 0; u < NB * NB / 256; ++u) {
     const int e = threadIdx.x + 256 * u, rho = e >> 6, m = e & 63;
     const int64_t row = row0 + rho;
     v[u] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : make_float2(0.f, 0.f);
   }
+}
+
+__device__ __forceinline__ void ptc_put(const float2 (&v)[NB * NB / 256], float2* stg) {
 #pragma unroll
-  for (int u = 0; u < PER; ++u) {
+  for (int u = 0; u < NB * NB / 256; ++u) {
     const int e = threadIdx.x + 256 * u;
     stg[(e >> 6) * ptc::STG_LD + (e & 63)] = v[u];
   }
@@ -677,16 +678,23 @@ __device__ __noinline__ bool herk_row_tc(float2* __restrict__ A, int64_t P, int6
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t r0 = p0 + (int64_t)g * NB;
   if (c_lo > c_hi) return true;
+  float2 v[NB * NB / 256];
+  ptc_load(A, P, k0, kw, r0, v);
   __syncthreads();                               // the previous user of the buffers is done
-  ptc_stage(A, P, k0, kw, r0, stg);
+  ptc_put(v, stg);
   __syncthreads();
   ptc_pack(stg, sm + A_HI, sm + A_LO);
+  // the column operand's rows are loaded one tile ahead (during the previous products)
+  if (c_lo != g) {
+    if (!cta_wait(&xready[c_lo], nchain, abort_word, status)) return false;
+    ptc_load(A, P, k0, kw, p0 + (int64_t)c_lo * NB, v);
+  }
   for (int c = c_lo; c <= c_hi; ++c) {
     const int64_t c0 = p0 + (int64_t)c * NB;
     const bool diag = c == g;
     if (!diag) {
-      if (!cta_wait(&xready[c], c == c_lo ? nchain : 1u, abort_word, status)) return false;
-      ptc_stage(A, P, k0, kw, c0, stg);          // (cta_wait ends with a barrier)
+      __syncthreads();                           // stg: the previous tile's update read it
+      ptc_put(v, stg);
       __syncthreads();
       ptc_pack(stg, sm + B_HI, sm + B_LO);
     }
@@ -718,6 +726,14 @@ __device__ __noinline__ bool herk_row_tc(float2* __restrict__ A, int64_t P, int6
       tc::mma_commit(mbar);
       *issued = 1;
     }
+    if (c + 1 <= c_hi && c + 1 != g) {           // the next column operand, during the products
+      if (!cta_wait(&xready[c + 1], 1u, abort_word, status)) {
+        // the products in flight finish before the caller frees the tensor memory
+        *tc_abort = 1;
+        return false;
+      }
+      ptc_load(A, P, k0, kw, c0 + NB, v);
+    }
     const bool okw = tc::warp_wait(mbar, *phase, tc_abort, lane);
     *phase ^= 1u;
     if (!__syncthreads_and(okw ? 1 : 0)) {
@@ -736,11 +752,11 @@ __device__ __noinline__ bool herk_row_tc(float2* __restrict__ A, int64_t P, int6
     const bool even = (i & 1) == 0;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      float v[32];
-      tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(64 * hs + 32 * j), v);
+      float d[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(64 * hs + 32 * j), d);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
-        const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
+        const float mine0 = d[2 * q], mine1 = d[2 * q + 1];
         const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
         const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
         if ((q & 1) == (even ? 0 : 1)) {
@@ -759,13 +775,12 @@ __device__ __noinline__ bool herk_row_tc(float2* __restrict__ A, int64_t P, int6
       const int64_t row = r0 + rr, col = c0 + q;
       if (row < P && col < P && (!diag || q <= rr)) {
         const float2 f = stg[rr * STG_LD + q];
-        float2 v = cur[u];
-        v.x -= f.x;
-        if (row != col) v.y -= f.y;              // the diagonal stays real
-        A[row * P + col] = v;
+        float2 a = cur[u];
+        a.x -= f.x;
+        if (row != col) a.y -= f.y;              // the diagonal stays real
+        A[row * P + col] = a;
       }
     }
-    __syncthreads();                             // stg read before it is restaged
   }
   return true;
 }
@@ -1730,7 +1745,7 @@ static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, u
                                         PANEL_SMEM, st));
     ++*launches;
     if (n > 0) {
-      VMC_TRY(launch_herk_tc(w.Xhi, w.Xlo, rows_pad, K, n, A, P, pend, status, st));
+      VMC_TRY(launch_herk_tc(w.Xhi, w.Xlo, rows_pad, K, n, A, P, pend, NBO, status, st));
       ++*launches;
     }
   }

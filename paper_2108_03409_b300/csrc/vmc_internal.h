@@ -132,9 +132,11 @@ cudaError_t launch_gram_reduce(const float2* part, int kchunks, int64_t P, doubl
 // Schur-complement update of an FP32 complex Cholesky factor on the tensor cores:
 // A[off+k][off+l] -= sum_m L_km conj(L_lm) for 0 <= l <= k < n, with L's panel given as
 // real rows (row 2k = Re L_k., row 2k+1 = Im L_k.) split into BF16 hi/lo, K columns.
+// A[off + k][off + l] -= (X X^H)_kl on l <= k < n from the BF16 hi/lo planes of X (real rows
+// 2k, 2k + 1); the tiles of the first tail_cols complex columns are updated last.
 cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, int64_t rows_pad,
                            int64_t K, int64_t n, float2* A32, int64_t ldA, int64_t off,
-                           unsigned* status, cudaStream_t st);
+                           int tail_cols, unsigned* status, cudaStream_t st);
 
 // ---- solve.cu -------------------------------------------------------------------------
 struct SolveWork {

@@ -567,6 +567,59 @@ def test_sr_step_cg_heisenberg_16x16(precision):
     assert np.all(np.isfinite(p1)) and np.linalg.norm(p1 - p) > 0
 
 
+@pytest.mark.parametrize("precision", [vmc.PREC_FP32, vmc.PREC_BF16SPLIT], ids=["simt", "tc"])
+def test_sr_step_cg_16x16_solves_oracle_equation(precision):
+    """The CG step at the 16x16 shape (P = 131 840) on a sub-sampled set of 64 chains: the
+    samples are read back through a twin context, the oracle forms E_loc, O_k and F, and the
+    GPU's update delta = (p - p1) / dt must solve the oracle's shifted equation
+    (S + nu diag S) delta = F, applied matrix-free in FP64 (S = Obar^H Obar / n, Eq. qfm),
+    to the CG tolerance plus the operator's rounding.  The matrix-free product is first
+    checked against the oracle's explicit S on a small slice of the same samples."""
+    Lx = Ly = 16
+    N, M = 256, 512
+    C, therm, dt, nu, seed = 64, 5, 0.02, 1e-3, 21
+    p = inputs.rbm_params(N, M, 0.01, seed=1234, marshall=(Lx, Ly))
+    s0 = inputs.random_sz0_spins(C, N, seed=3)
+    kw = dict(n_chains=C, samples_per_chain=1, therm_sweeps=therm, seed=seed,
+              solver=vmc.SOLVER_CG, precision=precision, shift=nu, cg_tol=1e-6, cg_maxit=400)
+    with context(lattice(H, Lx, Ly, 1.0, 0.0, 2), **kw) as twin:
+        vmc.vmc_set_params(twin, 0, p)
+        vmc.vmc_set_chains(twin, 0, s0)
+        out = torch.zeros((C, N), dtype=torch.int8, device="cuda")
+        vmc.vmc_sample(twin, 0, therm, 1, out)
+        samples = out.cpu().numpy()
+    with context(lattice(H, Lx, Ly, 1.0, 0.0, 2), **kw) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vmc.vmc_set_chains(ctx, 0, s0)
+        st = vmc.vmc_sr_step(ctx, 0, dt)
+        p1 = vmc.vmc_get_params(ctx, 0)
+    assert st.solver_relres <= 1e-6 and st.solver_iters <= 400
+    E = oracle.eloc(H, Lx, Ly, 1.0, 0.0, M, p, samples)
+    O = oracle.ok(N, M, p, samples)
+    _, F, Em = oracle.sr_matrices(O, E, want_S=False)
+    assert abs(st.e_mean_re - Em.real) / N <= ELOC_PER_SITE_ABS
+    Ob = O - O.mean(axis=0)
+    dS = np.mean(np.abs(Ob) ** 2, axis=0)
+
+    def s_tilde(v, Obar=Ob, d=dS):
+        return Obar.conj().T @ (Obar @ v) / len(Obar) + nu * d * v
+
+    # the matrix-free product against the oracle's explicit S on a slice of parameters
+    cols = np.r_[0:40, N:N + 40, N + M:N + M + 80]
+    Ssl, _, _ = oracle.sr_matrices(O[:, cols], E)
+    v = np.random.default_rng(5).normal(size=len(cols)) + 0j
+    Obs = O[:, cols] - O[:, cols].mean(axis=0)
+    assert np.allclose(oracle.shift(Ssl, nu, 0) @ v,
+                       s_tilde(v, Obs, np.mean(np.abs(Obs) ** 2, axis=0)), rtol=1e-12, atol=1e-14)
+    delta = (p - p1) / dt
+    res = np.linalg.norm(s_tilde(delta) - F) / np.linalg.norm(F)
+    # |S~|_2 <= |Obar|_2^2 / n + nu max diag S (the Gram of the n x n side is small)
+    norm_s = np.linalg.eigvalsh(Ob @ Ob.conj().T / C).max() + nu * dS.max()
+    op = CG_OPERATOR_REL if precision == vmc.PREC_FP32 else CG_OPERATOR_REL_TC
+    bound = 2e-6 + op * (1 + norm_s * np.linalg.norm(delta) / np.linalg.norm(F))
+    assert res <= bound, (res, bound)
+
+
 def test_sr_step_bf16_split_recovers_from_indefinite_s():
     """1D TFIM N = 10 near the uniform state with a 1e-4 relative shift: the three-product
     BF16 split can make the shifted S indefinite (its error is minus the PSD lo.lo^T term);
