@@ -3,6 +3,8 @@
 // S~ = L L^H, in FP64, or in FP32 followed by FP64 iterative refinement against the
 // FP64 S~.  Diagonal blocks of L are inverted once so that the panel solve and the
 // triangular solves become small matrix products.
+#include <type_traits>
+
 #include "tc_ptx.cuh"
 #include "vmc_device.cuh"
 #include "vmc_internal.h"
@@ -70,6 +72,9 @@ __global__ void k_copy_shift(const double2* __restrict__ S, C* __restrict__ A, i
 //    for L[c+1][c]; every lane scales and updates its own rows), publishes both columns
 //    (double-buffered), one barrier, then the later warps apply the rank-2 update.  After
 //    the panel the trailing triangle gets one rank-16 update.
+//  * The outer loops stay rolled: inside the panel kernel the code is fetched while the
+//    other CTAs stream the panel through L2, and a compact loop body runs faster there
+//    than the fully unrolled one (which wins only on an idle GPU).
 //  * Inverse: the four 16 x 16 diagonal blocks are inverted at once (forward substitution
 //    on the identity, one warp each, a column per lane), then the off-diagonal 16-blocks by
 //    levels, X_ij = -D_i sum_{k=j}^{i-1} L_ik X_kj (D_i = diagonal inverse).
@@ -152,6 +157,7 @@ __device__ void potrf_core(unsigned* status, const PotrfSmem<C>& sm) {
   bool bad = false;
   const int warp = tid >> 5, lane = tid & 31;
   int pb = 0;
+#pragma unroll 1
   for (int pp = 0; pp < 4; ++pp) {
     const int c0 = 16 * pp;
     // warp w owns the panel columns c0 + 2w + q (q = 0, 1); lane l the rows c0 + l + 32h
@@ -167,6 +173,7 @@ __device__ void potrf_core(unsigned* status, const PotrfSmem<C>& sm) {
     // block (each lane scales its own rows of column c and updates its own rows of column
     // c+1; three shuffles), publishes both columns, one barrier, then the later warps apply
     // the rank-2 update to their columns
+#pragma unroll 1
     for (int w = 0; w < 8; ++w) {
       const int c = c0 + 2 * w;
       C* cbA = cb + pb * 2 * NB;                     // column c
@@ -249,16 +256,16 @@ __device__ void potrf_core(unsigned* status, const PotrfSmem<C>& sm) {
       // trailing rank-16 update of rows/cols >= c0 + 16 (lower triangle)
       const int t0 = c0 + 16;
       const int ty = tid & 15, tx = tid >> 4;
-#pragma unroll
+#pragma unroll 1
       for (int p = 0; p < 4; ++p) {
         const int r = ty + 16 * p;
         if (r < t0) continue;
-#pragma unroll
+#pragma unroll 1
         for (int q = 0; q < 4; ++q) {
           const int cc = tx + 16 * q;
           if (cc < t0 || cc > r) continue;
           C acc = mk<C>(0.0, 0.0);
-#pragma unroll
+#pragma unroll 4
           for (int m = 0; m < 16; ++m) cfmac(acc, a[r * PLD + c0 + m], a[cc * PLD + c0 + m]);
           a[r * PLD + cc].x -= acc.x;
           a[r * PLD + cc].y -= acc.y;
@@ -295,7 +302,7 @@ __device__ void potrf_core(unsigned* status, const PotrfSmem<C>& sm) {
   __syncthreads();
   // ---- off-diagonal 16-blocks by levels d = i - j (each thread holds 4 - d entries of a
   // level; the levels and entry counts are compile-time, so a thread's entries interleave) ----
-#pragma unroll
+#pragma unroll 1
   for (int d = 1; d < 4; ++d) {
     constexpr int kMaxNb = 3;
     const int nb = 4 - d;                          // blocks (j + d, j), j < nb
@@ -307,10 +314,10 @@ __device__ void potrf_core(unsigned* status, const PotrfSmem<C>& sm) {
       if (u < nb) {
         const int e = tid + POTRF_THREADS * u;
         const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
-#pragma unroll
+#pragma unroll 1
         for (int k2 = 0; k2 < d; ++k2) {
           const int k = j + k2;
-#pragma unroll
+#pragma unroll 4
           for (int m = 0; m < 16; ++m)
             cfma(acc[u], a[(16 * i + r) * PLD + 16 * k + m], li[(16 * k + m) * PLD + 16 * j + c]);
         }
@@ -331,7 +338,7 @@ __device__ void potrf_core(unsigned* status, const PotrfSmem<C>& sm) {
       if (u < nb) {
         const int e = tid + POTRF_THREADS * u;
         const int j = e >> 8, i = j + d, r = (e >> 4) & 15, c = e & 15;
-#pragma unroll
+#pragma unroll 4
         for (int m = 0; m < 16; ++m)
           cfma(acc[u], li[(16 * i + r) * PLD + 16 * i + m], tt[(16 * i + m) * PLD + 16 * j + c]);
       }
@@ -376,17 +383,36 @@ struct XOut {
   int K, m0;                                     // m0: the panel column of the block's column 0
 };
 
-template <typename C>
-__device__ __forceinline__ void x_store(const XOut& xo, int64_t row, int c, C v) {}
-template <>
-__device__ __forceinline__ void x_store<float2>(const XOut& xo, int64_t row, int c, float2 v) {
-  if (xo.hi == nullptr || row < xo.r0 || row - xo.r0 >= xo.n) return;
-  const int64_t r = row - xo.r0, m = xo.m0 + c;
-  const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
-  xo.hi[(2 * r) * xo.K + m] = hr;
-  xo.hi[(2 * r + 1) * xo.K + m] = hi;
-  xo.lo[(2 * r) * xo.K + m] = __float2bfloat16_rn(v.x - __bfloat162float(hr));
-  xo.lo[(2 * r + 1) * xo.K + m] = __float2bfloat16_rn(v.y - __bfloat162float(hi));
+// The solved rows r0 .. r0 + nrow - 1, staged in st (row stride NB + 1, columns 0 .. kw-1):
+// those below the panel go into the operand planes, 16 bytes (eight columns of one real
+// row, hi or lo) per store.  Work item (row, component, eight-column chunk).
+__device__ __forceinline__ void x_store_rows(const XOut& xo, const float2* st, int64_t r0,
+                                             int nrow, int kw) {
+  if (xo.hi == nullptr) return;
+  for (int it = threadIdx.x; it < nrow * 16; it += blockDim.x) {
+    const int r = it >> 4, comp = (it >> 3) & 1, ch = it & 7;
+    const int64_t row = r0 + r;
+    if (row < xo.r0 || row - xo.r0 >= xo.n || 8 * ch >= kw) continue;
+    const float2* src = st + r * (NB + 1) + 8 * ch;
+    const int64_t off = (2 * (row - xo.r0) + comp) * xo.K + xo.m0 + 8 * ch;
+    if (8 * ch + 8 <= kw) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float2 a = src[2 * e], b = src[2 * e + 1];
+        tc::split_pair(comp ? a.y : a.x, comp ? b.y : b.x, h[e], l[e]);
+      }
+      *reinterpret_cast<uint4*>(xo.hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint4*>(xo.lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    } else {
+      for (int e = 0; 8 * ch + e < kw; ++e) {
+        const float x = comp ? src[e].y : src[e].x;
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        xo.hi[off + e] = h;
+        xo.lo[off + e] = __float2bfloat16_rn(x - __bfloat162float(h));
+      }
+    }
+  }
 }
 
 // Panel: X = B L_kk^{-H}, X[r][c] = sum_m B[r][m] conj(Linv[c][m]) (Linv is zero above its
@@ -423,29 +449,36 @@ __device__ void trsm_body(C* __restrict__ A, int64_t P, int64_t k0, int kw,
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = mk<C>(0.0, 0.0);
-  for (int m = 0; m < kw; ++m) {
-    C br[4], lc[4];
+  // Linv is lower triangular: columns m of block jb reach only the column blocks j >= jb
 #pragma unroll
-    for (int i = 0; i < 4; ++i) br[i] = Bt[m * (NB + 1) + ty + 16 * i];
+  for (int jb = 0; jb < 4; ++jb) {
+    const int mend = min(kw, 16 * jb + 16);
+    for (int m = 16 * jb; m < mend; ++m) {
+      C br[4], lc[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) lc[j] = Lt[m * (NB + 1) + tx + 16 * j];
+      for (int i = 0; i < 4; ++i) br[i] = Bt[m * (NB + 1) + ty + 16 * i];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+      for (int j = jb; j < 4; ++j) lc[j] = Lt[m * (NB + 1) + tx + 16 * j];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) cfmac(acc[i][j], br[i], lc[j]);
-  }
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t row = r0 + ty + 16 * i;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = tx + 16 * j;
-      if (row < P && c < kw) {
-        A[row * P + k0 + c] = acc[i][j];
-        x_store<C>(xo, row, c, acc[i][j]);
-      }
+        for (int j = jb; j < 4; ++j) cfmac(acc[i][j], br[i], lc[j]);
     }
   }
+  // stage X (over B^T, once every thread is done reading it), then store it coalesced
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) Bt[(ty + 16 * i) * (NB + 1) + tx + 16 * j] = acc[i][j];
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < NB * NB / 256; ++u) {
+    const int e = tid + 256 * u, r = e >> 6, c = e & 63;
+    const int64_t row = r0 + r;
+    if (row < P && c < kw) A[row * P + k0 + c] = Bt[r * (NB + 1) + c];
+  }
+  if constexpr (std::is_same<C, float2>::value) x_store_rows(xo, Bt, r0, NB, kw);
 }
 
 template <typename C>
@@ -847,21 +880,27 @@ __device__ void trsm_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw,
   float2 acc[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
-  for (int m = 0; m < kw; ++m) {
-    const float2 br = Bt[m * 17 + ry];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) cfmac(acc[q], br, Lt[m * (NB + 1) + tx + 16 * q]);
-  }
-  const int64_t row = r0 + ry;
-  if (row < P)
+  for (int jb = 0; jb < 4; ++jb) {                 // Linv lower triangular (as trsm_body)
+    const int mend = min(kw, 16 * jb + 16);
+    for (int m = 16 * jb; m < mend; ++m) {
+      const float2 br = Bt[m * 17 + ry];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int c = tx + 16 * q;
-      if (c < kw) {
-        A[row * P + k0 + c] = acc[q];
-        x_store<float2>(xo, row, c, acc[q]);
-      }
+      for (int q = jb; q < 4; ++q) cfmac(acc[q], br, Lt[m * (NB + 1) + tx + 16 * q]);
     }
+  }
+  // stage the 16 rows (over L^T, once every thread is done reading it), store coalesced
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) Lt[ry * (NB + 1) + tx + 16 * q] = acc[q];
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = tid + 256 * u, r = e >> 6, c = e & 63;
+    const int64_t row = r0 + r;
+    if (row < P && c < kw) A[row * P + k0 + c] = Lt[r * (NB + 1) + c];
+  }
+  x_store_rows(xo, Lt, r0, 16, kw);
 }
 
 // CTA 0's part of a chain step: the diagonal tile of block g (rows r0 .., width kw1) less
