@@ -845,6 +845,9 @@ __device__ __noinline__ bool herk_row_tc(float2* __restrict__ A, int64_t P, int6
 constexpr int PANEL_MAX_STEPS = 8;                 // 64-column blocks per panel (NBO / 64)
 constexpr int PANEL_SYNC_WORDS = 4 + PANEL_MAX_STEPS * (PANEL_MAX_STEPS + 2);
 constexpr unsigned PANEL_CHAIN = 4;                // chain CTAs (16-row slabs of a block)
+// the chain's tensor-core operand planes (hi, lo) sit after the factorisation's arrays
+constexpr size_t CHAIN_PLANES =
+    ((size_t)(3 * NB * (NB + 1) + 5 * NB) * sizeof(float2) + 1023) / 1024 * 1024;
 static_assert(PANEL_SYNC_WORDS <= 128, "panel sync words");
 
 // 16 rows r0 .. r0 + 15 of X = B L_kk^{-H} (as trsm_body); thread (row ry, columns tx + 16 b)
@@ -906,61 +909,80 @@ __device__ void trsm_slab(float2* __restrict__ A, int64_t P, int64_t k0, int kw,
 // CTA 0's part of a chain step: the diagonal tile of block g (rows r0 .., width kw1) less
 // X X^H (X = the step's solved rows of block g, columns k0 .. k0 + kw, already in A),
 // factored; L and Linv go to A and Dinv1.  The tile is read before the wait for the slabs.
-__device__ void chain_diag(float2* __restrict__ A, int64_t P, int64_t k0, int kw, int64_t r0,
+// X X^H is one tensor-core product (BF16 hi/lo split of X in the swizzled operand planes at
+// pl, FP32 accumulation in TMEM), folded into the tile in shared memory.  Returns false if
+// a wait expired.
+__device__ __noinline__ bool chain_diag(float2* __restrict__ A, int64_t P, int64_t k0, int kw, int64_t r0,
                            int kw1, float2* __restrict__ Dinv1, const unsigned* ready,
                            unsigned* abort_word, unsigned* status, unsigned char* csm,
-                           bool* ok) {
+                           uint8_t* pl, uint32_t tmem, uint32_t mbar, uint32_t* phase,
+                           volatile int* tc_abort, int* issued) {
   const PotrfSmem<float2> sm(csm);
   float2* X = sm.tt;                             // [64][PLD]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   potrf_load<float2>(A, P, r0, kw1, sm.a);
-  if (!cta_wait(ready, PANEL_CHAIN, abort_word, status)) { *ok = false; return; }
+  if (!cta_wait(ready, PANEL_CHAIN, abort_word, status)) return false;
   {
-    constexpr int PER = NB * NB / 256;
-    float2 xv[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = threadIdx.x + 256 * u, r = e >> 6, m = e & 63;
-      const int64_t row = r0 + r;
-      xv[u] = (row < P && m < kw) ? __ldcg(&A[row * P + k0 + m]) : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int u = 0; u < PER; ++u) {
-      const int e = threadIdx.x + 256 * u;
-      X[(e >> 6) * PLD + (e & 63)] = xv[u];
-    }
+    float2 xv[NB * NB / 256];
+    ptc_load(A, P, k0, kw, r0, xv);
+    ptc_put(xv, X);                              // (PLD is the staging stride)
   }
   __syncthreads();
-  // a[r][c] -= sum_m X[r][m] conj(X[c][m]) for c <= r: thread (ty, tx) holds the entries
-  // (ty + 16 p, tx + 16 q) with q <= p (the blocks above the diagonal are never formed)
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  float2 acc[10];
+  ptc_pack(X, pl, pl + ptc::OP);
+  tc::fence_before();
+  __syncthreads();
+  if (tid == 0) {
+    tc::fence_after();
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
+    const uint64_t h = tc::smem_desc_sw128(tc::smem_u32(pl));
+    const uint64_t l = tc::smem_desc_sw128(tc::smem_u32(pl + ptc::OP));
 #pragma unroll
-  for (int u = 0; u < 10; ++u) acc[u] = make_float2(0.f, 0.f);
-#pragma unroll 4
-  for (int m = 0; m < kw; ++m) {
-    float2 xr[4], xc[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) xr[p] = X[(ty + 16 * p) * PLD + m];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) xc[q] = X[(tx + 16 * q) * PLD + m];
-#pragma unroll
-    for (int p = 0, u = 0; p < 4; ++p)
-#pragma unroll
-      for (int q = 0; q <= p; ++q, ++u) cfmac(acc[u], xr[p], xc[q]);
+    for (int kk = 0; kk < NB / 16; ++kk) {
+      const uint64_t o = (uint64_t)(kk * 32) >> 4;
+      tc::mma_bf16(tmem, h + o, h + o, idesc, kk > 0 ? 1u : 0u);
+      tc::mma_bf16(tmem, h + o, l + o, idesc, 1u);
+      tc::mma_bf16(tmem, l + o, h + o, idesc, 1u);
+    }
+    tc::mma_commit(mbar);
+    *issued = 1;
   }
+  const bool okw = tc::warp_wait(mbar, *phase, tc_abort, lane);
+  *phase ^= 1u;
+  if (!__syncthreads_and(okw ? 1 : 0)) {
+    if (tid == 0) {
+      atomicExch(abort_word, 1u);
+      flag_error(status, DEV_ERR_TIMEOUT);
+    }
+    return false;
+  }
+  tc::fence_after();
+  // fold (as in herk_row_tc) straight into the tile: entry (rho, col) with col <= rho
+  {
+    const int qd = warp & 3, hs = warp >> 2;
+    const int i = 32 * qd + lane, rho = i >> 1;
+    const bool even = (i & 1) == 0;
 #pragma unroll
-  for (int p = 0, u = 0; p < 4; ++p)
+    for (int j = 0; j < 2; ++j) {
+      float d[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(64 * hs + 32 * j), d);
 #pragma unroll
-    for (int q = 0; q <= p; ++q, ++u) {
-      const int r = ty + 16 * p, c = tx + 16 * q;
-      if (c <= r && r < kw1) {
-        float2& d = sm.a[r * PLD + c];
-        d.x -= acc[u].x;
-        if (c != r) d.y -= acc[u].y;
+      for (int q = 0; q < 16; ++q) {
+        const float mine0 = d[2 * q], mine1 = d[2 * q + 1];
+        const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
+        const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
+        const int col = 32 * hs + 16 * j + q;
+        if ((q & 1) == (even ? 0 : 1) && col <= rho && rho < kw1) {
+          float2& t = sm.a[rho * PLD + col];
+          t.x -= even ? mine0 + oth1 : oth0 + mine1;
+          if (col != rho) t.y -= even ? oth0 - mine1 : mine0 - oth1;
+        }
       }
     }
-  potrf_core<float2>(status, sm);
+  }
+  tc::fence_before();
+  potrf_core<float2>(status, sm);                // (begins with a barrier)
   potrf_store<float2>(A, P, r0, kw1, Dinv1, sm.a, sm.li);
+  return true;
 }
 
 __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int64_t P,
@@ -1022,8 +1044,10 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
       __syncthreads();
       if (threadIdx.x == 0) atomicAdd(&xready[k * PANEL_MAX_STEPS + g], 1u);
       if (b == 0) {
-        chain_diag(A, P, k0, blk_w(k), r0, blk_w(g), dinv_of(g),
-                   &xready[k * PANEL_MAX_STEPS + g], abort_word, status, csm, &ok);
+        ok = chain_diag(A, P, k0, blk_w(k), r0, blk_w(g), dinv_of(g),
+                        &xready[k * PANEL_MAX_STEPS + g], abort_word, status, csm,
+                        csm + CHAIN_PLANES, tmem, tc::smem_u32(&tc_bar[0]), &tc_phase,
+                        &tc_abort, &tc_issued);
         if (!ok) break;
         __threadfence();
         __syncthreads();
@@ -1077,7 +1101,7 @@ __global__ void __launch_bounds__(256) k_panel_coop(float2* __restrict__ A, int6
   }
 }
 
-constexpr size_t PANEL_SMEM = 1024 + (size_t)(3 * NB * (NB + 1) + 5 * NB) * sizeof(float2);
+constexpr size_t PANEL_SMEM = 1024 + CHAIN_PLANES + 2 * ptc::OP;
 static_assert(PANEL_SMEM >= 1024 + ptc::SMEM, "panel shared memory holds the tensor-core tiles");
 
 // Steps of SB = 256 rows.  After the factorisation the inverse of every 256 x 256 diagonal
