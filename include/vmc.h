@@ -136,6 +136,15 @@ vmc_status vmc_get_params(vmc_ctx* ctx, int lattice, double* params_host);
 vmc_status vmc_set_chains(vmc_ctx* ctx, int lattice, const int8_t* spins_host);
 vmc_status vmc_get_chains(vmc_ctx* ctx, int lattice, int8_t* spins_host);
 
+/* theta_j = b_j + sum_i W_ji s_i of the hidden units for a batch (Eq. rbm_ex; the chains'
+ * theta cache at the start of a sampling run).  With VMC_PREC_BF16SPLIT the product runs on
+ * the tensor cores: spins +-1 are exact in BF16, W enters as a BF16 hi + lo pair (2^-18
+ * relative) and the sums accumulate in FP32; otherwise in FP32 on the SIMT cores (the FMA
+ * chain of the sampler's own formation).  spins: dev int8 [n][N]; theta: dev float [n][M][2]
+ * (interleaved Re, Im).  n = 0 is a no-op.  VMC_ERR_TIMEOUT if a tensor-core wait expired.
+ * The sampler (vmc_sample, vmc_sr_step) starts its chains from this theta. */
+vmc_status vmc_theta(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* theta);
+
 /* log psi for a batch (Eq. rbm_ex; the __call__ of the NQS class).
  * spins: dev int8 [n][N]; logpsi: dev float [n][2].  n = 0 is a no-op.  The imaginary
  * part (the phase) is returned reduced to [-pi, pi]; so is the sampler's logpsi_out. */

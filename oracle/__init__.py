@@ -76,6 +76,7 @@ def _load():
             "orc_set_num_threads": (None, [i32]),
             "orc_philox4x64": (i32, [P, P, P]),
             "orc_bonds": (i32, [i32, i32, P, P]),
+            "orc_theta": (i32, [i32, i32, P, P, i64, P]),
             "orc_logpsi": (i32, [i32, i32, P, P, i64, P]),
             "orc_connected": (i32, [i32, i32, i32, f64, f64, P, P, P]),
             "orc_max_connected": (i32, [i32, i32, i32]),
@@ -181,6 +182,15 @@ def connected(model: int, Lx: int, Ly: int, J: float, h: float, s: np.ndarray):
 # ----------------------------------------------------------------------------------------
 # RBM quantities
 # ----------------------------------------------------------------------------------------
+def theta(N: int, M: int, params: np.ndarray, spins: np.ndarray) -> np.ndarray:
+    """theta_j = b_j + sum_i W_ji s_i (Eq. rbm_ex) of each configuration, [n][M] complex."""
+    s = _spins(spins).reshape(-1, N)
+    p = _cplx(params)
+    out = np.zeros((s.shape[0], M, 2), dtype=np.float64)
+    _check(_load().orc_theta(N, M, _ptr(p), _ptr(s), s.shape[0], _ptr(out)), "theta")
+    return out[..., 0] + 1j * out[..., 1]
+
+
 def logpsi(N: int, M: int, params: np.ndarray, spins: np.ndarray) -> np.ndarray:
     s = _spins(spins).reshape(-1, N)
     p = _cplx(params)

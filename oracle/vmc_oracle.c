@@ -132,6 +132,16 @@ static cd rbm_logpsi(int N, int M, const cd* par, const int8_t* s, cd* theta_scr
 }
 
 /* log psi for a batch: out[n][2] = (re, im). */
+/* theta_j = b_j + sum_i W_ji s_i of n configurations (Eq. rbm_ex), out: [n][M] complex. */
+int orc_theta(int N, int M, const double* params, const int8_t* spins, int64_t n, double* out) {
+  if (N < 1 || M < 1 || !params || (n > 0 && (!spins || !out))) return ORC_ERR_ARG;
+  const cd* par = (const cd*)params;
+#pragma omp parallel for schedule(static)
+  for (int64_t k = 0; k < n; ++k)
+    rbm_theta(N, M, par + N, par + N + M, spins + k * N, (cd*)(out + 2 * k * M));
+  return ORC_OK;
+}
+
 int orc_logpsi(int N, int M, const double* params, const int8_t* spins, int64_t n, double* out) {
   if (N < 1 || M < 1 || !params || (n > 0 && (!spins || !out))) return ORC_ERR_ARG;
   const cd* par = (const cd*)params;

@@ -615,6 +615,25 @@ vmc_status vmc_get_chains(vmc_ctx* ctx, int lattice, int8_t* spins_host) {
   return VMC_OK;
 }
 
+// theta of n configurations with the context's precision (the chains' starting cache)
+static cudaError_t theta_of(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, int64_t n,
+                            float2* theta) {
+  if (ctx->cfg.precision == VMC_PREC_BF16SPLIT)
+    return launch_theta_tc(rbm_of(L), spins, n, theta, ctx->status, ctx->st);
+  return launch_theta_gemm(rbm_of(L), spins, n, theta, ctx->st);
+}
+
+vmc_status vmc_theta(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* theta) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (n < 0 || (n > 0 && (!spins || !theta))) return fail(ctx, VMC_ERR_ARG, "bad batch");
+  if (n == 0) return VMC_OK;
+  LatticeState& L = ctx->lats[lattice];
+  CK(theta_of(ctx, L, spins, n, reinterpret_cast<float2*>(theta)), "theta");
+  ++ctx->launches;
+  return check_status(ctx, "theta");
+}
+
 vmc_status vmc_logpsi(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, float* logpsi) {
   vmc_status s = lattice_ok(ctx, lattice);
   if (s) return s;
@@ -665,6 +684,13 @@ vmc_status vmc_sample(vmc_ctx* ctx, int lattice, int n_therm, int n_samples, int
   A.n_accept = ctx->n_accept;
   A.status = ctx->status;
   if (n_therm + n_samples == 0) return VMC_OK;
+  if (ctx->cfg.precision == VMC_PREC_BF16SPLIT) {
+    // the chains start from the same theta as in vmc_sr_step (the t buffer is scratch here:
+    // a chain reads its row before anything else is written there)
+    CK(theta_of(ctx, L, L.chains, A.C, ctx->s_T), "theta");
+    ++ctx->launches;
+    A.theta_in = ctx->s_T;
+  }
   CK(launch_sample(A, ctx->st), "sample");
   ++ctx->launches;
   L.sweep += (uint64_t)n_therm + (uint64_t)n_samples * ctx->cfg.sweeps_per_sample;
@@ -832,7 +858,7 @@ static vmc_status sample_step_set(vmc_ctx* ctx, LatticeState& L, int lattice, ui
   // theta of the chains' spins as one tiled product (bit-identical to the sampler's own
   // per-chain formation, which would read W once per chain).  It goes into the t buffer: a
   // chain reads its row before it writes its first record there.
-  CK(launch_theta_gemm(A.rbm, L.chains, c.n_chains, ctx->s_T, ctx->st), "theta");
+  CK(theta_of(ctx, L, L.chains, c.n_chains, ctx->s_T), "theta");
   ++ctx->launches;
   A.theta_in = ctx->s_T;
   CK(launch_sample(A, ctx->st), "sample");

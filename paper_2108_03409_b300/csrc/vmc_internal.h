@@ -64,6 +64,10 @@ cudaError_t launch_theta_tanh(const RbmDev& R, const int8_t* spins, int64_t n, f
 // sampler's own per-chain formation, so the results are bit-identical to it
 cudaError_t launch_theta_gemm(const RbmDev& R, const int8_t* spins, int64_t C, float2* theta,
                               cudaStream_t st);
+// theta = b + W s of n configurations on the tensor cores (spins exact in BF16, W as a BF16
+// hi/lo pair, FP32 accumulation); a wait that expires sets DEV_ERR_TIMEOUT in status
+cudaError_t launch_theta_tc(const RbmDev& R, const int8_t* spins, int64_t n, float2* theta,
+                            unsigned* status, cudaStream_t st);
 cudaError_t launch_ok_dense(const int8_t* spins, const float2* T, int64_t n, int N, int M,
                             float2* O, cudaStream_t st);
 cudaError_t launch_sample(const SampleArgs& A, cudaStream_t st);

@@ -88,7 +88,7 @@ class vmc_excited_stats(ctypes.Structure):
 
 
 EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
-            "vmc_set_chains", "vmc_get_chains", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
+            "vmc_set_chains", "vmc_get_chains", "vmc_theta", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
             "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
             "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve", "vmc_sr_apply",
             "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
@@ -122,6 +122,7 @@ def load(path: str = LIB_PATH):
         "vmc_get_params": (i32, [P, i32, P]),
         "vmc_set_chains": (i32, [P, i32, P]),
         "vmc_get_chains": (i32, [P, i32, P]),
+        "vmc_theta": (i32, [P, i32, P, i64, P]),
         "vmc_logpsi": (i32, [P, i32, P, i64, P]),
         "vmc_local_energy": (i32, [P, i32, P, i64, P]),
         "vmc_sample": (i32, [P, i32, i32, i32, P, P, P]),
@@ -261,6 +262,10 @@ def vmc_get_chains(ctx, lattice, n_chains, N):
     out = np.zeros((n_chains, N), dtype=np.int8)
     _check(ctx, load().vmc_get_chains(ctx, lattice, out.ctypes.data))
     return out
+
+
+def vmc_theta(ctx, lattice, spins, out):
+    _check(ctx, load().vmc_theta(ctx, lattice, _ptr(spins), spins.shape[0], _ptr(out)))
 
 
 def vmc_logpsi(ctx, lattice, spins, out):

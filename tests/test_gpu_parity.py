@@ -42,6 +42,34 @@ def _setup(case, seed=0):
     return model, Lx, Ly, J, h, alpha, N, M, p, s
 
 
+@pytest.mark.parametrize("precision", [vmc.PREC_FP32, vmc.PREC_BF16SPLIT], ids=["simt", "tc"])
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_theta_matches_oracle(case, precision):
+    """theta = b + W s (Eq. rbm_ex) against the oracle.  FP32 SIMT: the FMA chain's rounding,
+    2 (N + 1) 2^-24 (|b_j| + sum_i |W_ji|).  Tensor cores: the spins are exact in BF16, each
+    component of W is a BF16 hi + lo pair within 2^-18 of it, and the FP32 accumulation adds
+    the same chain bound: (2^-17 + 2 (N + 2) 2^-24) (|b_j| + sum_i |W_ji|).  The batches span
+    several 128-configuration tiles with a ragged tail (and M against the 64-unit tiles)."""
+    model, Lx, Ly, J, h, alpha, N, M, p, s = _setup(case)
+    if N == 256:
+        s = inputs.initial_spins(model, 300, N, seed=11)
+    n = len(s)
+    with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=1, precision=precision,
+                 solver=vmc.SOLVER_CG) as ctx:           # (no dense S at 16x16)
+        vmc.vmc_set_params(ctx, 0, p)
+        th = torch.zeros((n, M, 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_theta(ctx, 0, to_dev_spins(s), th)
+        got = cplx(th).reshape(n, M)
+    ref = oracle.theta(N, M, p, s)
+    mag = np.abs(p[N:N + M]) + np.abs(p[N + M:].reshape(M, N)).sum(axis=1)
+    if precision == vmc.PREC_FP32:
+        bound = 2 * (N + 1) * 2.0 ** -24 * mag
+    else:
+        bound = (2.0 ** -17 + 2 * (N + 2) * 2.0 ** -24) * mag
+    err = np.abs(got - ref)
+    assert np.all(err <= bound[None, :]), (err / bound[None, :]).max()
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_logpsi_matches_oracle(case):
     model, Lx, Ly, J, h, alpha, N, M, p, s = _setup(case)

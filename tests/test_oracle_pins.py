@@ -103,6 +103,32 @@ def test_logpsi_equals_sum_over_hidden_units():
         assert abs(got - ref) <= 1e-12 * abs(ref)
 
 
+def test_theta_invariants_and_log_derivative():
+    """theta of the oracle against what its definition fixes without retyping it: it is
+    affine in s (theta(s) + theta(-s) = 2 b), a flip of site i changes theta_j by
+    2 s_i W_ji with W read from the documented parameter layout [a | b | W (M x N)], and
+    d log psi / d b_j = tanh theta_j by central finite differences of log psi."""
+    N, M = 9, 6
+    p = inputs.rbm_params(N, M, 0.4, seed=21)          # complex [a | b | W]
+    b = p[N:N + M]
+    W = p[N + M:].reshape(M, N)
+    s = inputs.random_spins(7, N, seed=22)
+    th = oracle.theta(N, M, p, s)
+    assert np.allclose(th + oracle.theta(N, M, p, -s), 2 * b[None, :], atol=1e-13)
+    for i in (0, 4, N - 1):
+        sf = s.copy()
+        sf[:, i] *= -1
+        d = th - oracle.theta(N, M, p, sf)
+        assert np.allclose(d, 2 * s[:, i, None] * W[None, :, i], atol=1e-13)
+    eps = 1e-6
+    for j in (0, M - 1):
+        for unit in (1.0, 1j):
+            dp = np.zeros_like(p)
+            dp[N + j] = eps * unit
+            fd = (oracle.logpsi(N, M, p + dp, s) - oracle.logpsi(N, M, p - dp, s)) / (2 * eps * unit)
+            assert np.allclose(fd, np.tanh(th[:, j]), atol=1e-8)
+
+
 @pytest.mark.parametrize("z", [0.3 + 0.2j, -45.0 + 3.0j, 400.0 - 7.5j, -2.0 + 1.5707j, 1e-9 + 0j])
 def test_logcosh_against_high_precision(z):
     """N = 1, M = 1, a = 0, W = 0: log psi = log cosh(b).  Compared with mpmath at 50 digits,
