@@ -67,6 +67,9 @@ FAMILIES = {
     "tfim1d_N10_alpha1_c256_excited": dict(kind="excited", N=10, alpha=1, chains=256, spc=200,
                                            h=1.0, dt=0.05),
 }
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one S-Gram launch (one FP16
+# product) of the default workload, from an ncu capture of the same command; None until taken
+GRAM_F16_TRAFFIC = None
 DEFAULT_WORKLOAD = "heis2d_8x8_alpha2_c8192"
 W = WORKLOADS[DEFAULT_WORKLOAD]
 LX, LY, ALPHA, CHAINS, SHIFT = W["Lx"], W["Ly"], W["alpha"], W["chains"], W["shift"]
@@ -492,7 +495,16 @@ def run_ours(args):
     # 8 P^2 Ns flops for the full real Gram of [Re Obar | Im Obar], half of it for the
     # symmetric (lower) tiles, times 3 for the BF16 hi/lo split = 12 P^2 Ns on the tensor
     # pipe (4 P^2 Ns "plain-equivalent" flops of one FP32 product).
-    if prec == vmc.PREC_BF16SPLIT:
+    # The SR step's tensor-core S only feeds the factor that preconditions CG on the exact
+    # FP32 operator: one FP16 product, 4 P^2 Ns flops, against the FP16 dense peak (the
+    # measured BF16 peak x the nominal FP16 : BF16 ratio of 1).
+    fused_f16 = prec == vmc.PREC_BF16SPLIT and solver_name in ("tc", "mixed")
+    if fused_f16:
+        alg_flops, alg_text = 4.0 * P * P * Ns, "4*P^2*Ns flops (Hermitian half of the real Gram, one FP16 product)"
+        roof = {"bound": "tensor", "peak": pk.get("bf16_tflops", 1766.8),
+                "peak_kind": f"fp16 dense burst = bf16 dense burst ({pk_kind}) x 1 (nominal ratio); "
+                             "the step keeps the SM clock at max"}
+    elif prec == vmc.PREC_BF16SPLIT:
         alg_flops, alg_text = 12.0 * P * P * Ns, "12*P^2*Ns flops (Hermitian half of the real Gram, x3 BF16 split)"
         roof = {"bound": "tensor", "peak": pk.get("bf16_tflops", 1766.8),
                 "peak_kind": f"bf16 dense burst ({pk_kind}); the step keeps the SM clock at max"}
@@ -504,14 +516,15 @@ def run_ours(args):
     achieved = alg_flops / (ms_gram / 1e3) / 1e12
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one S-Gram launch of
     # this kernel on this workload, from an ncu capture of the same command
-    traffic = 7.56e9 if (prec == vmc.PREC_BF16SPLIT and args.workload == DEFAULT_WORKLOAD) else None
+    traffic = GRAM_F16_TRAFFIC if (fused_f16 and args.workload == DEFAULT_WORKLOAD) else None
     roofline = {"bound": roof["bound"], "achieved": achieved, "peak": roof["peak"],
                 "unit": "TFLOP/s", "frac": achieved / roof["peak"], "traffic": traffic,
                 "kernel": "gram_tc" if prec == vmc.PREC_BF16SPLIT else "gram_f32",
                 "peak_source": roof["peak_kind"], "algorithmic": alg_text,
                 "ms_per_launch": ms_gram}
     if prec == vmc.PREC_BF16SPLIT:
-        roofline["plain_equivalent_frac"] = achieved / 3.0 / roof["peak"]
+        if not fused_f16:
+            roofline["plain_equivalent_frac"] = achieved / 3.0 / roof["peak"]
         roofline["frac_of_sustained"] = achieved / pk.get("bf16_tflops_sustained", 1387.8)
     # bytes the step streams (each larger than the 126 MB L2, so no flush between steps)
     if solver_name == "cg":
@@ -525,7 +538,9 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": "SR steps/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32" if prec == vmc.PREC_FP32 else "bf16x3-split/f32-accum",
+           "dtype": ("f32" if prec == vmc.PREC_FP32 else
+                     "f16 S for the CG preconditioner / f32 CG operator and accumulation" if fused_f16
+                     else "bf16x3-split/f32-accum"),
            "data": "synthetic",
            "config": {"workload": args.workload, "N": N, "M": M, "P": P,
                       "chains": CHAINS, "Ns": Ns, "shift": SHIFT, "dt": DT,
@@ -572,11 +587,20 @@ def run_ours(args):
         eff_pl = Ns / (ms_samp_pl / 1e3) / (2 * tau)
         theta0 = vmc.vmc_get_params(pctx, 0)
         chains0 = vmc.vmc_get_chains(pctx, 0, CHAINS, N)
-        e_before = None
         for c in (ctx, pctx):
             vmc.vmc_set_params(c, 0, theta0)
             vmc.vmc_set_chains(c, 0, chains0)
-            e_before = vmc.vmc_sr_step(c, 0, DT).e_mean_re / N
+        # one sample set (the plain arm's sampler from the shared state) for both arms' steps,
+        # so that the difference is the arithmetic's and not the Monte Carlo noise of two
+        # sample sets (the arms' theta differ in their last bits, which can flip a
+        # near-threshold Metropolis decision)
+        spc = wl["spc"]
+        ss = torch.zeros((CHAINS * spc, N), dtype=torch.int8, device="cuda")
+        vmc.vmc_sample(pctx, 0, 0, spc, ss)
+        vmc.vmc_set_chains(pctx, 0, chains0)
+        e_before = None
+        for c in (ctx, pctx):
+            e_before = vmc.vmc_sr_step_on(c, 0, ss, DT).e_mean_re / N
         dE, err, e_v, e_p = _paired_energy_difference(ctx, pctx, vmc, vstats, torch, CHAINS, N)
         vmc.vmc_destroy(pctx)
         out["plain_fp32"] = {"sr_steps_per_s": ws * 1e3 / ms_pl, "ms_per_step": ms_pl,
@@ -588,7 +612,8 @@ def run_ours(args):
         out["vs_plain_fp32"] = {"sr_steps_per_s": value / (ws * 1e3 / ms_pl),
                                 "eff_samples_per_s": (eff * ws) / (eff_pl * ws)}
         out["equal_accuracy"] = {
-            "how": ("one SR step of each arm from the same theta and chains; <E>/N at the two "
+            "how": ("one SR step of each arm from the same theta on one sample set (drawn by the "
+                    "plain arm's sampler from the shared chains); <E>/N at the two "
                     "updated parameter sets from one set of 32 sweeps x all chains drawn at the "
                     "variant's parameters, the plain one reweighted by |psi_plain/psi_variant|^2; "
                     "ok = |dE|/N + 3 sigma <= 1e-4"),

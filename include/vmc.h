@@ -221,6 +221,14 @@ vmc_status vmc_sr_apply(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
  * have advanced; stats, if given, is filled with solver_converged = 0). */
 vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats);
 
+/* The same SR step on a given sample set instead of the chains' next samples (so that two
+ * contexts, e.g. two precisions, can be compared on identical configurations): spins dev
+ * int8 [n][N] with n = n_chains * samples_per_chain; E_loc and tanh(theta) are formed for
+ * them, the chains do not move, acceptance is reported as 0.  VMC_ERR_ARG for another n;
+ * otherwise as vmc_sr_step. */
+vmc_status vmc_sr_step_on(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, double dt,
+                          vmc_sr_stats* stats);
+
 /* ---- learned proposal (masked autoregressive MLP; requires made_hidden > 0) -------------
  * q(s) = prod_d sigma(s_d z_d), z = W3 relu(W2 relu(W1 s + b1) + b2) + b3 with MADE masks
  * (Germain et al. 2015): hidden unit k has degree m(k) = (k mod (N-1)) + 1, W1[k][d] is used

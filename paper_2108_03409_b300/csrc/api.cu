@@ -188,8 +188,9 @@ vmc_status refresh_fp32(vmc_ctx* ctx, LatticeState& L) {
 }
 
 // S of a sample set with T = tanh theta already in ctx->s_T; E may be null.  S_out (FP64)
-// may be null when `fused` (tensor-core Gram only): the Gram then writes the mixed solvers'
-// inputs (ctx->sw.S2 and the shifted lower triangle in ctx->sw.A32) directly.
+// may be null when `fused` (tensor-core Gram only, the SR step): the Gram then writes the
+// shifted lower triangle that the preconditioner's factorisation takes (ctx->sw.A32)
+// directly.
 vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const float2* E,
                     int64_t n, int precision, double2* S_out, bool mirror, bool fused = false,
                     bool lolo = false) {
@@ -202,13 +203,19 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
   if (rows_pad > ctx->rows_pad || ld > ctx->ld) return fail(ctx, VMC_ERR_ARG, "S workspace too small");
   const double inv_n = 1.0 / (double)n;
   if (precision == VMC_PREC_BF16SPLIT) {
-    CK(launch_build_x(spins, ctx->s_T, ctx->meanO, ctx->mean2, n, L.N, L.M, rows_pad, ld, nullptr, ctx->Xhi,
-                      ctx->Xlo, ctx->st), "build_x");
+    // In the SR step (fused) S only feeds the factor that preconditions CG on the exact
+    // operator: one FP16 product (an 11-bit mantissa), no FP32 pair copy of S.  Elsewhere,
+    // and when a factorisation met a non-positive pivot (lolo), the BF16 hi/lo split.
+    const int prod = lolo ? 4 : fused ? 1 : 3;
+    __half* x16 = prod == 1 ? reinterpret_cast<__half*>(ctx->Xhi) : nullptr;
+    CK(launch_build_x(spins, ctx->s_T, ctx->meanO, ctx->mean2, n, L.N, L.M, rows_pad, ld, nullptr,
+                      prod == 1 ? nullptr : ctx->Xhi, prod == 1 ? nullptr : ctx->Xlo, x16,
+                      ctx->st), "build_x");
     ctx->launches += 2;
     cudaEventRecord(ctx->ev[6], ctx->st);
     cudaError_t e = launch_gram_tc(ctx->Xhi, ctx->Xlo, rows_pad, ld, L.P, inv_n, S_out, mirror,
-                                   fused ? ctx->sw.S2 : nullptr, fused ? ctx->sw.A32 : nullptr,
-                                   ctx->cfg.shift, ctx->cfg.shift_mode, lolo, ctx->gpart,
+                                   nullptr, fused ? ctx->sw.A32 : nullptr,
+                                   ctx->cfg.shift, ctx->cfg.shift_mode, prod, ctx->gpart,
                                    ctx->gpart_cap, ctx->status, ctx->st);
     cudaEventRecord(ctx->ev[7], ctx->st);
     if (e == cudaErrorNotSupported) return fail(ctx, VMC_ERR_ARG, "tensor-core Gram: shape not supported");
@@ -216,7 +223,7 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
     ++ctx->launches;
   } else {
     CK(launch_build_x(spins, ctx->s_T, ctx->meanO, ctx->mean2, n, L.N, L.M, rows_pad, ld, ctx->X32, nullptr,
-                      nullptr, ctx->st), "build_x");
+                      nullptr, nullptr, ctx->st), "build_x");
     ctx->launches += 2;
     cudaEventRecord(ctx->ev[6], ctx->st);
     CK(launch_gram_f32(ctx->X32, rows_pad, ld, L.P, inv_n, S_out, mirror, ctx->gpart,
@@ -869,7 +876,9 @@ static vmc_status sample_step_set(vmc_ctx* ctx, LatticeState& L, int lattice, ui
   return VMC_OK;
 }
 
-vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats) {
+// One SR step; `given` (dev int8 [Ns][N]) replaces the sampling by a given sample set.
+static vmc_status sr_step_impl(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats,
+                               const int8_t* given) {
   vmc_status s = lattice_ok(ctx, lattice);
   if (s) return s;
   LatticeState& L = ctx->lats[lattice];
@@ -878,9 +887,19 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
   const int64_t launches0 = ctx->launches;
   CK(cudaMemsetAsync(ctx->n_accept, 0, sizeof(unsigned long long), ctx->st), "sr_step");
   CK(cudaEventRecord(ctx->ev[0], ctx->st), "sr_step");
-  // 1. sample Ns configurations; E_loc and tanh(theta) fused at every record point
+  // 1. sample Ns configurations; E_loc and tanh(theta) fused at every record point (or take
+  //    the given configurations and form both for them)
   uint64_t steps = 0;
-  if ((s = sample_step_set(ctx, L, lattice, &steps))) return s;
+  if (given) {
+    CK(cudaMemcpyAsync(ctx->s_spins, given, (size_t)Ns * L.N, cudaMemcpyDeviceToDevice, ctx->st),
+       "sr_step");
+    CK(launch_theta_tanh(rbm_of(L), ctx->s_spins, Ns, ctx->s_T, ctx->st), "theta_tanh");
+    CK(launch_eloc(rbm_of(L), lat_of(L), ctx->s_spins, Ns, ctx->s_E, ctx->status, ctx->st),
+       "eloc");
+    ctx->launches += 2;
+  } else if ((s = sample_step_set(ctx, L, lattice, &steps))) {
+    return s;
+  }
   CK(cudaEventRecord(ctx->ev[1], ctx->st), "sr_step");
   // 2. energy statistics, <O>, F (the b- and W-block factors come from the sampler)
   CK(launch_estats(ctx->s_E, Ns, ctx->estats, ctx->status, ctx->st), "estats");
@@ -977,6 +996,19 @@ vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats
     return fail(ctx, VMC_ERR_NUMERIC, "CG did not reach cg_tol within cg_maxit iterations; "
                                       "the parameters were not updated");
   return VMC_OK;
+}
+
+vmc_status vmc_sr_step(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stats* stats) {
+  return sr_step_impl(ctx, lattice, dt, stats, nullptr);
+}
+
+vmc_status vmc_sr_step_on(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t n, double dt,
+                          vmc_sr_stats* stats) {
+  vmc_status s = lattice_ok(ctx, lattice);
+  if (s) return s;
+  if (!spins || n != ctx->Ns)
+    return fail(ctx, VMC_ERR_ARG, "vmc_sr_step_on: n must equal n_chains * samples_per_chain");
+  return sr_step_impl(ctx, lattice, dt, stats, spins);
 }
 
 

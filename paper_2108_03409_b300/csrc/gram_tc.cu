@@ -4,8 +4,10 @@
 // The centred log-derivatives are stored as real rows X (row 2k = Re Obar_k, row 2k+1 =
 // Im Obar_k, samples contiguous), split into BF16 pairs X = hi + lo.  The real Gram
 // G = X X^T is accumulated in FP32 in tensor memory as hi.hi^T + hi.lo^T + lo.hi^T (the
-// lo.lo^T term is 2^-16 below the others), one 128 x 128 tile of G at a time, lower tiles
-// only.  The epilogue folds each 2x2 block of G into one complex entry:
+// lo.lo^T term is 2^-16 below the others; PROD = 4 adds it), one 128 x 128 tile of G at a
+// time, lower tiles only.  PROD = 1 takes X as one FP16 plane and one product: the S that
+// only preconditions the SR step's CG (an 11-bit mantissa keeps the factor a good
+// preconditioner at a third of the products).  The epilogue folds each 2x2 block of G into one complex entry:
 //   S_kl = (G[2k][2l] + G[2k+1][2l+1] + i (G[2k][2l+1] - G[2k+1][2l])) / n.
 //
 // The kernel is persistent (one CTA per SM walks the tile list) and warp-specialised:
@@ -70,7 +72,7 @@ __device__ __forceinline__ void schur_tile(int64_t t, int nt, int tail, int* bm,
   *bm = c + (int)u;
 }
 
-template <bool LOLO>
+template <int PROD>
 __global__ void __launch_bounds__(tc::THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
           int nk, int nt, int64_t tiles, int64_t P, double inv_n, double2* __restrict__ S,
@@ -126,11 +128,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
           if (j > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((j - 1) & 1), abort_flag)) break;
           uint8_t* st = smem + s * STAGE_BYTES;
           const uint32_t fb = smem_u32(&full[s]);
-          mbar_expect_tx(fb, STAGE_BYTES);
+          mbar_expect_tx(fb, PROD == 1 ? 2 * TILE_BYTES : STAGE_BYTES);
           tma_load_2d(smem_u32(st + 0 * TILE_BYTES), &map_hi, kb * BK, bm * BM, fb);
-          tma_load_2d(smem_u32(st + 1 * TILE_BYTES), &map_lo, kb * BK, bm * BM, fb);
+          if (PROD != 1) tma_load_2d(smem_u32(st + 1 * TILE_BYTES), &map_lo, kb * BK, bm * BM, fb);
           tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &map_hi, kb * BK, bn * BN, fb);
-          tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &map_lo, kb * BK, bn * BN, fb);
+          if (PROD != 1) tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &map_lo, kb * BK, bn * BN, fb);
         }
       }
       if (*abort_flag) {
@@ -143,7 +145,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+      constexpr uint32_t idesc = PROD == 1 ? idesc_f16_f32(BM, BN) : idesc_bf16_f32(BM, BN);
       int64_t g = 0;
       int i = 0;
       bool issued_any = false;
@@ -167,9 +169,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
             mma_bf16(d, ah + o, bh + o, idesc, (kb > kbeg || kk > 0) ? 1u : 0u);
-            mma_bf16(d, ah + o, bl + o, idesc, 1u);
-            mma_bf16(d, al + o, bh + o, idesc, 1u);
-            if (LOLO) mma_bf16(d, al + o, bl + o, idesc, 1u);   // (hi+lo)(hi+lo)^T: PSD
+            if (PROD >= 3) {
+              mma_bf16(d, ah + o, bl + o, idesc, 1u);
+              mma_bf16(d, al + o, bh + o, idesc, 1u);
+            }
+            if (PROD == 4) mma_bf16(d, al + o, bl + o, idesc, 1u);   // (hi+lo)(hi+lo)^T: PSD
           }
           issued_any = true;
           mma_commit(smem_u32(&empty[s]));            // frees the stage when these finish
@@ -400,35 +404,45 @@ unsigned persistent_grid(int64_t tiles) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, sms));
 }
 
+static cudaError_t gram_attrs() {
+  static bool attr = false;
+  if (attr) return cudaSuccess;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gram_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gram_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES)) != cudaSuccess)
+    return e;
+  attr = true;
+  return cudaSuccess;
+}
+
+// prod: 1 (one FP16 plane in Xhi, Xlo unused), 3 or 4 (BF16 hi/lo planes)
 cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
                            bool mirror, float4* S2, float2* Af, double nu, int shift_mode,
-                           bool lolo, float2* part, int64_t part_cap, unsigned* status,
+                           int prod, float2* part, int64_t part_cap, unsigned* status,
                            cudaStream_t st) {
   if (rows_pad % tc::BM != 0 || ld % tc::BK != 0 || ld < tc::BK) return cudaErrorNotSupported;
+  if (prod != 1 && prod != 3 && prod != 4) return cudaErrorInvalidValue;
+  if (prod == 1) Xlo = Xhi;                          // (the map of an unused plane)
   if ((reinterpret_cast<uintptr_t>(Xhi) | reinterpret_cast<uintptr_t>(Xlo)) & 15)
     return cudaErrorNotSupported;
   CUtensorMap mhi, mlo;
   cudaError_t e;
+  // the maps move 2-byte elements bit for bit: the same map serves BF16 and FP16 planes
   if ((e = make_map(&mhi, Xhi, rows_pad, ld)) != cudaSuccess) return e;
   if ((e = make_map(&mlo, Xlo, rows_pad, ld)) != cudaSuccess) return e;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             tc::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             tc::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if ((e = gram_attrs()) != cudaSuccess) return e;
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
   const int nkb = (int)(ld / tc::BK);
   int kchunks = gram_kchunks(tiles, nkb, P, part_cap);
   const int nkpc = (nkb + kchunks - 1) / kchunks;
   kchunks = (nkb + nkpc - 1) / nkpc;                 // no empty chunk
-  auto kern = lolo ? k_gram_tc<true> : k_gram_tc<false>;
+  auto kern = prod == 1 ? k_gram_tc<1> : prod == 4 ? k_gram_tc<4> : k_gram_tc<3>;
   kern<<<persistent_grid(tiles * kchunks), tc::THREADS, tc::SMEM_BYTES, st>>>(
       mhi, mlo, nkb, (int)nt, tiles, P, inv_n, S, S2, Af, nu, shift_mode, mirror ? 1 : 0,
       nullptr, 0, 0, 0, kchunks, nkpc, kchunks > 1 ? part : nullptr, status);
@@ -440,28 +454,22 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
 
 cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, int64_t rows_pad,
                            int64_t K, int64_t n, float2* A32, int64_t ldA, int64_t off,
-                           int tail_cols, unsigned* status, cudaStream_t st) {
+                           int tail_cols, int prod, unsigned* status, cudaStream_t st) {
   if (rows_pad % tc::BM != 0 || K % tc::BK != 0 || K < tc::BK) return cudaErrorNotSupported;
+  if (prod != 1 && prod != 3) return cudaErrorInvalidValue;
+  if (prod == 1) Xlo = Xhi;
   CUtensorMap mhi, mlo;
   cudaError_t e;
   if ((e = make_map(&mhi, Xhi, rows_pad, K)) != cudaSuccess) return e;
   if ((e = make_map(&mlo, Xlo, rows_pad, K)) != cudaSuccess) return e;
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(k_gram_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             tc::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_gram_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             tc::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  if ((e = gram_attrs()) != cudaSuccess) return e;
   const int64_t nt = rows_pad / tc::BM;
   const int64_t tiles = nt * (nt + 1) / 2;
   // the first tail_cols columns (128-row tiles of the real operand = 64 complex columns)
   // are updated last
   const int tail = (int)std::min<int64_t>(nt, std::max<int64_t>(0, (tail_cols + 63) / 64));
-  k_gram_tc<false><<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
+  auto kern = prod == 1 ? k_gram_tc<1> : k_gram_tc<3>;
+  kern<<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
       mhi, mlo, (int)(K / tc::BK), (int)nt, tiles, n, 1.0, nullptr, nullptr, nullptr, 0.0, 0, 0,
       A32, ldA, off, tail, 1, (int)(K / tc::BK), nullptr, status);
   return cudaGetLastError();

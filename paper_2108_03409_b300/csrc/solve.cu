@@ -1808,7 +1808,7 @@ static cudaError_t factor_tc(float2* A, float2* Dinv, int64_t P, SolveWork& w, u
                                         PANEL_SMEM, st));
     ++*launches;
     if (n > 0) {
-      VMC_TRY(launch_herk_tc(w.Xhi, w.Xlo, rows_pad, K, n, A, P, pend, NBO, status, st));
+      VMC_TRY(launch_herk_tc(w.Xhi, w.Xlo, rows_pad, K, n, A, P, pend, NBO, 3, status, st));
       ++*launches;
     }
   }

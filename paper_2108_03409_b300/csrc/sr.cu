@@ -3,6 +3,8 @@
 // gives S = <O^H O> - <O^H><O>.
 #include <cstring>
 
+#include <cuda_fp16.h>
+
 #include "vmc_device.cuh"
 #include "vmc_internal.h"
 
@@ -197,6 +199,7 @@ struct XOut {
   float* X32;
   __nv_bfloat16* Xhi;
   __nv_bfloat16* Xlo;
+  __half* X16;                                   // one FP16 plane (the preconditioner's S)
   int64_t ld;
 };
 
@@ -212,6 +215,10 @@ __device__ __forceinline__ void put_x(const XOut& o, int64_t k, int64_t q, float
     o.Xhi[r1] = hi;
     o.Xlo[r0] = __float2bfloat16_rn(vr - __bfloat162float(hr));
     o.Xlo[r1] = __float2bfloat16_rn(vi - __bfloat162float(hi));
+  }
+  if (o.X16) {
+    o.X16[r0] = __float2half_rn(vr);
+    o.X16[r1] = __float2half_rn(vi);
   }
 }
 
@@ -284,12 +291,13 @@ __global__ void __launch_bounds__(256) k_build_x(const int8_t* __restrict__ spin
 
 cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* meanO,
                            float4* mean2, int64_t n, int N, int M, int64_t rows_pad, int64_t ld,
-                           float* X32, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, cudaStream_t st) {
+                           float* X32, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, __half* X16,
+                           cudaStream_t st) {
   if (N > BX_NMAX) return cudaErrorInvalidValue;
   const int64_t P = (int64_t)N + M + (int64_t)N * M;
   k_split_mean<<<(unsigned)std::min<int64_t>((P + 255) / 256, 1024), 256, 0, st>>>(meanO, P, mean2);
   dim3 grid((unsigned)((ld + 31) / 32), (unsigned)((M + 7) / 8));
-  XOut o{X32, Xhi, Xlo, ld};
+  XOut o{X32, Xhi, Xlo, X16, ld};
   const bool vec16 = (N % 16) == 0 && (reinterpret_cast<uintptr_t>(spins) & 15) == 0;
   k_build_x<<<grid, 256, 0, st>>>(spins, T, mean2, n, N, M, rows_pad, vec16, o);
   return cudaGetLastError();

@@ -6,6 +6,7 @@
 #include <functional>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 namespace vmc {
 
@@ -101,7 +102,8 @@ cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E
 // mean2 [P] is a workspace (the mean as FP32 hi/lo pairs).
 cudaError_t launch_build_x(const int8_t* spins, const float2* T, const double2* meanO,
                            float4* mean2, int64_t n, int N, int M, int64_t rows_pad, int64_t ld,
-                           float* X32, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, cudaStream_t st);
+                           float* X32, __nv_bfloat16* Xhi, __nv_bfloat16* Xlo, __half* X16,
+                           cudaStream_t st);
 
 // S_kl = (1/n) sum_q conj(Xc_qk) Xc_ql from the real row Gram G = X X^T (FP32 SIMT):
 //   S = (G_{2k,2l} + G_{2k+1,2l+1}) + i (G_{2k,2l+1} - G_{2k+1,2l}), written as double2
@@ -123,7 +125,7 @@ cudaError_t launch_gram_f32(const float* X, int64_t rows_pad, int64_t ld, int64_
 cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
                            bool mirror, float4* S2, float2* Af, double nu, int shift_mode,
-                           bool lolo, float2* part, int64_t part_cap, unsigned* status,
+                           int prod, float2* part, int64_t part_cap, unsigned* status,
                            cudaStream_t st);
 // split-K support shared by both Gram kernels: number of sample chunks for `tiles` lower
 // tiles over nkb blocks of samples (>= 16 blocks a chunk, P*P*chunks <= part_cap), and the
@@ -137,10 +139,11 @@ cudaError_t launch_gram_reduce(const float2* part, int kchunks, int64_t P, doubl
 // A[off+k][off+l] -= sum_m L_km conj(L_lm) for 0 <= l <= k < n, with L's panel given as
 // real rows (row 2k = Re L_k., row 2k+1 = Im L_k.) split into BF16 hi/lo, K columns.
 // A[off + k][off + l] -= (X X^H)_kl on l <= k < n from the BF16 hi/lo planes of X (real rows
-// 2k, 2k + 1); the tiles of the first tail_cols complex columns are updated last.
+// 2k, 2k + 1) (prod 3) or one FP16 plane (prod 1); the tiles of the first tail_cols complex
+// columns are updated last.
 cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, int64_t rows_pad,
                            int64_t K, int64_t n, float2* A32, int64_t ldA, int64_t off,
-                           int tail_cols, unsigned* status, cudaStream_t st);
+                           int tail_cols, int prod, unsigned* status, cudaStream_t st);
 
 // ---- solve.cu -------------------------------------------------------------------------
 struct SolveWork {

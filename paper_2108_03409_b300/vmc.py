@@ -89,7 +89,7 @@ class vmc_excited_stats(ctypes.Structure):
 
 EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_get_params",
             "vmc_set_chains", "vmc_get_chains", "vmc_theta", "vmc_logpsi", "vmc_local_energy", "vmc_sample",
-            "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_kernel_launches",
+            "vmc_grad", "vmc_qfm", "vmc_solve", "vmc_sr_step", "vmc_sr_step_on", "vmc_kernel_launches",
             "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve", "vmc_sr_apply",
             "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
             "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned", "vmc_sample_all",
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH):
         "vmc_qfm": (i32, [P, i32, P, i64, i32, P]),
         "vmc_solve": (i32, [P, i32, P, P, P, ctypes.POINTER(i32), ctypes.POINTER(f64)]),
         "vmc_sr_step": (i32, [P, i32, f64, ctypes.POINTER(vmc_sr_stats)]),
+        "vmc_sr_step_on": (i32, [P, i32, P, i64, f64, ctypes.POINTER(vmc_sr_stats)]),
         "vmc_kernel_launches": (i64, [P]),
         "vmc_num_samples": (i64, [P]),
         "vmc_num_params": (i64, [P, i32]),
@@ -326,6 +327,18 @@ def vmc_sr_step(ctx, lattice, dt) -> vmc_sr_stats:
     st = vmc_sr_stats()
     try:
         _check(ctx, load().vmc_sr_step(ctx, lattice, float(dt), ctypes.byref(st)))
+    except VmcError as e:
+        e.stats = st
+        raise
+    return st
+
+
+def vmc_sr_step_on(ctx, lattice, spins, dt) -> vmc_sr_stats:
+    """The SR step on a given sample set (dev int8 [n_chains * samples_per_chain][N])."""
+    st = vmc_sr_stats()
+    try:
+        _check(ctx, load().vmc_sr_step_on(ctx, lattice, _ptr(spins), spins.shape[0], float(dt),
+                                          ctypes.byref(st)))
     except VmcError as e:
         e.stats = st
         raise

@@ -737,3 +737,44 @@ def test_cg_non_convergence_is_reported():
         out = torch.zeros((C, 2), dtype=torch.float32, device="cuda")
         vmc.vmc_logpsi(ctx, 0, sd, out)
         assert np.all(np.isfinite(out.cpu().numpy()))
+
+
+@pytest.mark.parametrize("solver,precision", [(vmc.SOLVER_CHOLESKY_MIXED, vmc.PREC_FP32),
+                                              (vmc.SOLVER_CHOLESKY_TC, vmc.PREC_BF16SPLIT)],
+                         ids=["fp32_mixed", "tc"])
+def test_sr_step_on_given_samples_solves_oracle_equation(solver, precision):
+    """vmc_sr_step_on: the SR step on a caller's sample set.  6x6 TFIM with alpha = 2 (P =
+    2700: six 512-column panels of the tensor-core factorisation, whose S is one FP16
+    product preconditioning CG on the exact FP32 operator); the oracle forms E_loc, O_k, S
+    and F from the very same configurations, and the GPU's update must solve the oracle's
+    shifted equation (Eq. qfm, the diagonal shift) as in the sampled SR step.  The chains
+    do not move, and a sample count other than n_chains * samples_per_chain is refused."""
+    model, Lx, Ly, J, h, alpha = T, 6, 6, 1.0, 3.0, 2
+    N, M = Lx * Ly, alpha * Lx * Ly
+    C, spc, dt, nu = 256, 8, 0.02, 1e-3
+    p = inputs.rbm_params(N, M, 0.05, seed=1234)
+    s0 = inputs.random_spins(C, N, seed=98)
+    samples = inputs.random_spins(C * spc, N, seed=97)
+    with context(lattice(model, Lx, Ly, J, h, alpha), n_chains=C, samples_per_chain=spc,
+                 therm_sweeps=2, seed=5, solver=solver, precision=precision, shift=nu,
+                 cg_tol=1e-8, cg_maxit=200) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        vmc.vmc_set_chains(ctx, 0, s0)
+        sd = to_dev_spins(samples)
+        with pytest.raises(vmc.VmcError) as ei:
+            vmc.vmc_sr_step_on(ctx, 0, sd[:-1], dt)
+        assert ei.value.status == vmc.VMC_ERR_ARG
+        st = vmc.vmc_sr_step_on(ctx, 0, sd, dt)
+        p1 = vmc.vmc_get_params(ctx, 0)
+        assert np.array_equal(vmc.vmc_get_chains(ctx, 0, C, N), s0)
+    E = oracle.eloc(model, Lx, Ly, J, h, M, p, samples)
+    O = oracle.ok(N, M, p, samples)
+    S, F, Em = oracle.sr_matrices(O, E)
+    assert abs(st.e_mean_re - Em.real) / N <= ELOC_PER_SITE_ABS
+    assert st.n_samples == C * spc and st.acceptance == 0.0
+    assert st.solver_converged == 1 and st.solver_relres <= 1e-8
+    St = oracle.shift(S, nu, 0)
+    delta = (p - p1) / dt
+    res = np.linalg.norm(St @ delta - F) / np.linalg.norm(F)
+    bound = 1e-4 * (1 + np.linalg.norm(St, 2) * np.linalg.norm(delta) / np.linalg.norm(F))
+    assert res <= bound, (res, bound)
