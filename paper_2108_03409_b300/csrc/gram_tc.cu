@@ -11,9 +11,10 @@
 //   S_kl = (G[2k][2l] + G[2k+1][2l+1] + i (G[2k][2l+1] - G[2k+1][2l])) / n.
 //
 // The kernel is persistent (one CTA per SM walks the tile list) and warp-specialised:
-// warp 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle) into a 3-stage ring,
-// warp 1 issues tcgen05.mma (kind::f16, BF16 in, FP32 accumulate, 128 x 128 x 16) into one
-// of two TMEM accumulators, and warps 2-5 drain the other accumulator with tcgen05.ld, so
+// warp 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle) into a ring of 3
+// stages (6 for one FP16 plane, whose stages are half as large), warp 1 issues
+// tcgen05.mma (kind::f16, BF16 or FP16 in, FP32 accumulate, 128 x 128 x 16) into one of two
+// TMEM accumulators, and warps 2-5 drain the other accumulator with tcgen05.ld, so
 // the epilogue of one tile overlaps the loads and products of the next.  Ring stages and
 // accumulators are handed over through mbarriers (tcgen05.commit arrives on them).  Every
 // wait is bounded (iteration and clock limits); on expiry the kernel records
@@ -33,13 +34,16 @@ namespace vmc {
 namespace tc {
 
 constexpr int BM = 128, BN = 128, BK = 64;      // tile; BK = one 128-byte swizzle row of BF16
-constexpr int STAGES = 3;
+constexpr int STAGES = 3;                       // ring depth of the BF16 hi/lo products
 constexpr int TILE_BYTES = BM * BK * 2;         // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;     // A_hi, A_lo, B_hi, B_lo
+constexpr int RING_BYTES = STAGES * STAGE_BYTES;
+// One FP16 plane needs half a stage, so the same ring holds twice the stages in flight
+constexpr int MAX_STAGES = RING_BYTES / (2 * TILE_BYTES);
 constexpr int STG_LD = 66;                      // staging row stride (float2) of the Schur epilogue
 constexpr int STG_BYTES = 64 * STG_LD * 8;
-constexpr int NUM_BARS = 2 * STAGES + 5;        // full, empty, acc full x2, acc empty x2, final
-constexpr int SMEM_BYTES = 1024 /*align*/ + STAGES * STAGE_BYTES + STG_BYTES + 256;
+constexpr int NUM_BARS = 2 * MAX_STAGES + 5;    // full, empty, acc full x2, acc empty x2, final
+constexpr int SMEM_BYTES = 1024 /*align*/ + RING_BYTES + STG_BYTES + 256;
 constexpr int THREADS = 192;                    // TMA warp, MMA warp, 4 epilogue warps
 constexpr int TMEM_COLS = 256;                  // two 128-column accumulators
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
@@ -83,13 +87,20 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
                                              ~uintptr_t(1023));
-  float2* stg = reinterpret_cast<float2*>(smem + STAGES * STAGE_BYTES);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + STG_BYTES);
+  // ring: PROD = 1 stages hold {A, B} (one FP16 plane), twice as many as the {A_hi, A_lo,
+  // B_hi, B_lo} stages of the BF16 products
+  constexpr int NST = PROD == 1 ? MAX_STAGES : STAGES;
+  constexpr int SB = PROD == 1 ? 2 * TILE_BYTES : STAGE_BYTES;
+  constexpr int OFF_AL = TILE_BYTES, OFF_BH = PROD == 1 ? TILE_BYTES : 2 * TILE_BYTES,
+                OFF_BL = 3 * TILE_BYTES;
+  static_assert(NST * SB <= RING_BYTES, "ring");
+  float2* stg = reinterpret_cast<float2*>(smem + RING_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES + STG_BYTES);
   uint64_t* full = bars;
-  uint64_t* empty = bars + STAGES;
-  uint64_t* accf = bars + 2 * STAGES;
-  uint64_t* acce = bars + 2 * STAGES + 2;
-  uint64_t* fin = bars + 2 * STAGES + 4;
+  uint64_t* empty = bars + MAX_STAGES;
+  uint64_t* accf = bars + 2 * MAX_STAGES;
+  uint64_t* acce = bars + 2 * MAX_STAGES + 2;
+  uint64_t* fin = bars + 2 * MAX_STAGES + 4;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + NUM_BARS);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   // the epilogue leader's verdict per tile, in two slots by tile parity: a slot is rewritten
@@ -123,23 +134,23 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
         schur_tile(t % tiles, nt, tail, &bm, &bn);
         const int kbeg = (int)(t / tiles) * nkpc, kend = min(nk, kbeg + nkpc);
         for (int kb = kbeg; kb < kend; ++kb, ++g) {
-          const int s = (int)(g % STAGES);
-          const int64_t j = g / STAGES;
+          const int s = (int)(g % NST);
+          const int64_t j = g / NST;
           if (j > 0 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((j - 1) & 1), abort_flag)) break;
-          uint8_t* st = smem + s * STAGE_BYTES;
+          uint8_t* st = smem + s * SB;
           const uint32_t fb = smem_u32(&full[s]);
-          mbar_expect_tx(fb, PROD == 1 ? 2 * TILE_BYTES : STAGE_BYTES);
-          tma_load_2d(smem_u32(st + 0 * TILE_BYTES), &map_hi, kb * BK, bm * BM, fb);
-          if (PROD != 1) tma_load_2d(smem_u32(st + 1 * TILE_BYTES), &map_lo, kb * BK, bm * BM, fb);
-          tma_load_2d(smem_u32(st + 2 * TILE_BYTES), &map_hi, kb * BK, bn * BN, fb);
-          if (PROD != 1) tma_load_2d(smem_u32(st + 3 * TILE_BYTES), &map_lo, kb * BK, bn * BN, fb);
+          mbar_expect_tx(fb, SB);
+          tma_load_2d(smem_u32(st), &map_hi, kb * BK, bm * BM, fb);
+          if (PROD != 1) tma_load_2d(smem_u32(st + OFF_AL), &map_lo, kb * BK, bm * BM, fb);
+          tma_load_2d(smem_u32(st + OFF_BH), &map_hi, kb * BK, bn * BN, fb);
+          if (PROD != 1) tma_load_2d(smem_u32(st + OFF_BL), &map_lo, kb * BK, bn * BN, fb);
         }
       }
       if (*abort_flag) {
         // let the copies in flight land before the CTA exits (bounded)
         volatile int dummy = 0;
-        for (int64_t h = (g > STAGES ? g - STAGES : 0); h < g; ++h)
-          mbar_wait(smem_u32(&full[h % STAGES]), (uint32_t)((h / STAGES) & 1), &dummy);
+        for (int64_t h = (g > NST ? g - NST : 0); h < g; ++h)
+          mbar_wait(smem_u32(&full[h % NST]), (uint32_t)((h / NST) & 1), &dummy);
       }
     }
   } else if (warp == 1) {
@@ -157,14 +168,14 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
         bool ok = true;
         const int kbeg = (int)(t / tiles) * nkpc, kend = min(nk, kbeg + nkpc);
         for (int kb = kbeg; kb < kend; ++kb, ++g) {
-          const int s = (int)(g % STAGES);
-          if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((g / STAGES) & 1), abort_flag)) { ok = false; break; }
+          const int s = (int)(g % NST);
+          if (!mbar_wait(smem_u32(&full[s]), (uint32_t)((g / NST) & 1), abort_flag)) { ok = false; break; }
           fence_after();
-          uint8_t* st = smem + s * STAGE_BYTES;
-          const uint64_t ah = smem_desc_sw128(smem_u32(st + 0 * TILE_BYTES));
-          const uint64_t al = smem_desc_sw128(smem_u32(st + 1 * TILE_BYTES));
-          const uint64_t bh = smem_desc_sw128(smem_u32(st + 2 * TILE_BYTES));
-          const uint64_t bl = smem_desc_sw128(smem_u32(st + 3 * TILE_BYTES));
+          uint8_t* st = smem + s * SB;
+          const uint64_t ah = smem_desc_sw128(smem_u32(st));
+          const uint64_t al = smem_desc_sw128(smem_u32(st + OFF_AL));
+          const uint64_t bh = smem_desc_sw128(smem_u32(st + OFF_BH));
+          const uint64_t bl = smem_desc_sw128(smem_u32(st + OFF_BL));
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint64_t o = (uint64_t)(kk * 32) >> 4;   // 16 BF16 = 32 bytes along K
