@@ -70,7 +70,7 @@ FAMILIES = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one S-Gram launch (one FP16
 # product) of the default workload, from an ncu capture of the same command (2.254 GB read,
 # 0.274 GB written); None once the kernel changes until it is taken again
-GRAM_F16_TRAFFIC = 2.52756864e9
+GRAM_F16_TRAFFIC = None
 DEFAULT_WORKLOAD = "heis2d_8x8_alpha2_c8192"
 W = WORKLOADS[DEFAULT_WORKLOAD]
 LX, LY, ALPHA, CHAINS, SHIFT = W["Lx"], W["Ly"], W["alpha"], W["chains"], W["shift"]

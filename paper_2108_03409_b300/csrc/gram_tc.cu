@@ -45,12 +45,12 @@ constexpr int STG_BYTES = 64 * STG_LD * 8;
 constexpr int NUM_BARS = 2 * MAX_STAGES + 5;    // full, empty, acc full x2, acc empty x2, final
 constexpr int SMEM_BYTES = 1024 /*align*/ + RING_BYTES + STG_BYTES + 256;
 constexpr int THREADS = 192;                    // TMA warp, MMA warp, 4 epilogue warps
-constexpr int TMEM_COLS = 256;                  // two 128-column accumulators
+constexpr int TMEM_COLS = 256;                  // two 128-column accumulators (BNT = 128)
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 }  // namespace tc
 
-// Tile t of the lower triangle of nt x nt tiles.  tail > 0 (Schur updates): the tiles of
+// Tile t of the lower triangle of nt x nt tiles (square 128 x 128 tiles).  tail > 0 (Schur updates): the tiles of
 // the first tail tile columns -- the next panel's columns -- come last, column by column,
 // so that they are the most recently written lines in L2 when the next panel starts.
 __device__ __forceinline__ void schur_tile(int64_t t, int nt, int tail, int* bm, int* bn) {
@@ -76,7 +76,17 @@ __device__ __forceinline__ void schur_tile(int64_t t, int nt, int tail, int* bm,
   *bm = c + (int)u;
 }
 
-template <int PROD>
+// 128 x 256 tiles (BNT = 256): tile t is row tile bm = 2c + (t & 1) of the pair c and
+// column tile bn <= c, with (c, bn) the lower triangle of the pairs walked as the square
+// tiles are.  With an odd nt the pairs' last odd row lies past the operand (its boxes
+// read the zero fill and the epilogue writes nothing for it).
+__device__ __forceinline__ void wide_tile(int64_t t, int nt, int* bm, int* bn) {
+  int c;
+  grouped_tri_tile(t >> 1, (nt + 1) / 2, 6, &c, bn);
+  *bm = 2 * c + (int)(t & 1);
+}
+
+template <int PROD, int BNT>
 __global__ void __launch_bounds__(tc::THREADS, 1)
 k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
           int nk, int nt, int64_t tiles, int64_t P, double inv_n, double2* __restrict__ S,
@@ -87,10 +97,13 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   extern __shared__ uint8_t gsm_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
                                              ~uintptr_t(1023));
-  // ring: PROD = 1 stages hold {A, B} (one FP16 plane), twice as many as the {A_hi, A_lo,
-  // B_hi, B_lo} stages of the BF16 products
-  constexpr int NST = PROD == 1 ? MAX_STAGES : STAGES;
-  constexpr int SB = PROD == 1 ? 2 * TILE_BYTES : STAGE_BYTES;
+  // ring: PROD = 1 stages hold {A, B} (one FP16 plane; B is 256 rows when BNT = 256), the
+  // others {A_hi, A_lo, B_hi, B_lo} of the BF16 products.  BNT = 256 serves only the S
+  // Gram's factor-input epilogue (Af), with one sample chunk.
+  static_assert(BNT == BN || (BNT == 2 * BN && PROD == 1), "wide tiles: one FP16 plane only");
+  constexpr int NST = PROD == 1 ? RING_BYTES / ((1 + BNT / BM) * TILE_BYTES) : STAGES;
+  constexpr int SB = PROD == 1 ? (1 + BNT / BM) * TILE_BYTES : STAGE_BYTES;
+  constexpr int TCOLS = 2 * BNT;                   // two accumulators of BNT columns
   constexpr int OFF_AL = TILE_BYTES, OFF_BH = PROD == 1 ? TILE_BYTES : 2 * TILE_BYTES,
                 OFF_BL = 3 * TILE_BYTES;
   static_assert(NST * SB <= RING_BYTES, "ring");
@@ -117,7 +130,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(TMEM_COLS) : "memory");
+                 ::"r"(smem_u32(tmem_slot)), "r"(TCOLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   fence_before();
@@ -131,7 +144,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       int64_t g = 0;                                  // k-blocks issued so far
       for (int64_t t = blockIdx.x; t < tiles * kchunks && !*abort_flag; t += gridDim.x) {
         int bm, bn;
-        schur_tile(t % tiles, nt, tail, &bm, &bn);
+        if (BNT == BN) schur_tile(t % tiles, nt, tail, &bm, &bn);
+        else wide_tile(t, nt, &bm, &bn);
         const int kbeg = (int)(t / tiles) * nkpc, kend = min(nk, kbeg + nkpc);
         for (int kb = kbeg; kb < kend; ++kb, ++g) {
           const int s = (int)(g % NST);
@@ -142,7 +156,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
           mbar_expect_tx(fb, SB);
           tma_load_2d(smem_u32(st), &map_hi, kb * BK, bm * BM, fb);
           if (PROD != 1) tma_load_2d(smem_u32(st + OFF_AL), &map_lo, kb * BK, bm * BM, fb);
-          tma_load_2d(smem_u32(st + OFF_BH), &map_hi, kb * BK, bn * BN, fb);
+          tma_load_2d(smem_u32(st + OFF_BH), &map_hi, kb * BK, bn * BNT, fb);
+          if (BNT != BN)
+            tma_load_2d(smem_u32(st + OFF_BH + TILE_BYTES), &map_hi, kb * BK, bn * BNT + BN, fb);
           if (PROD != 1) tma_load_2d(smem_u32(st + OFF_BL), &map_lo, kb * BK, bn * BN, fb);
         }
       }
@@ -156,7 +172,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
-      constexpr uint32_t idesc = PROD == 1 ? idesc_f16_f32(BM, BN) : idesc_bf16_f32(BM, BN);
+      constexpr uint32_t idesc = PROD == 1 ? idesc_f16_f32(BM, BNT) : idesc_bf16_f32(BM, BNT);
       int64_t g = 0;
       int i = 0;
       bool issued_any = false;
@@ -164,7 +180,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
         const int acc = i & 1, u = i >> 1;
         if (u > 0 && !mbar_wait(smem_u32(&acce[acc]), (uint32_t)((u - 1) & 1), abort_flag)) break;
         fence_after();
-        const uint32_t d = tmem + (uint32_t)(acc * BN);
+        const uint32_t d = tmem + (uint32_t)(acc * BNT);
         bool ok = true;
         const int kbeg = (int)(t / tiles) * nkpc, kend = min(nk, kbeg + nkpc);
         for (int kb = kbeg; kb < kend; ++kb, ++g) {
@@ -209,12 +225,13 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     for (int64_t t = blockIdx.x; t < tiles * kchunks; t += gridDim.x, ++i) {
       const int acc = i & 1, u = i >> 1;
       int bm, bn;
-      schur_tile(t % tiles, nt, tail, &bm, &bn);
+      if (BNT == BN) schur_tile(t % tiles, nt, tail, &bm, &bn);
+      else wide_tile(t, nt, &bm, &bn);
       const int kc = (int)(t / tiles);
       // Schur mode: fetch this thread's 32 entries of the factor's tile now, so that their
       // memory latency overlaps the wait for the products (no stores intervene).
       float2 cur[32];
-      if (A32) {
+      if (BNT == BN && A32) {
         const int64_t kb0 = (int64_t)bm * (BM / 2), lb0 = (int64_t)bn * (BN / 2);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -230,11 +247,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       if (!epi_go[i & 1]) break;
       fence_after();
       const int64_t k = (int64_t)bm * (BM / 2) + (r >> 1);
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 0; c0 < BNT; c0 += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(acc * BN + c0), v);
-        const int64_t l0 = (int64_t)bn * (BN / 2) + (c0 >> 1);
-        if (A32) {
+        tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(acc * BNT + c0), v);
+        const int64_t l0 = (int64_t)bn * (BNT / 2) + (c0 >> 1);
+        if (BNT == BN && A32) {
           // Schur update: stage the fold (FP32) of this row pair; the even row keeps the
           // even q, the odd row the odd q.
 #pragma unroll
@@ -248,7 +265,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
               stg[(r >> 1) * STG_LD + (c0 >> 1) + q] = make_float2(re, im);
             }
           }
-        } else if (part) {
+        } else if (BNT == BN && part) {
           // split over K: this chunk's fold (FP32, unnormalised) for l <= k; the chunks
           // are summed in FP64 afterwards
 #pragma unroll
@@ -273,7 +290,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             const double re = even ? (double)mine0 + (double)oth1 : (double)oth0 + (double)mine1;
             const double im = even ? (double)mine1 - (double)oth0 : (double)oth1 - (double)mine0;
             const int64_t l = l0 + q;
-            if (k < P && l < P && (bm != bn || l <= k)) {
+            if (k < P && l < P && l <= k) {
               const double vr = re * inv_n, vi = (l == k) ? 0.0 : im * inv_n;
               if (even) {
                 if (S) S[k * P + l] = make_double2(vr, vi);
@@ -301,7 +318,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acce[acc]));
-      if (A32) {
+      if (BNT == BN && A32) {
         named_bar_sync(1, 128);                      // staging complete
         // A[off+k][off+l] -= conj(fold) on l <= k, coalesced along rows; the diagonal
         // stays real.  (The next tile's writes to the staging buffer come after the next
@@ -327,7 +344,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(TMEM_COLS) : "memory");
+                 "r"(TCOLS) : "memory");
   }
   if (threadIdx.x == 0 && *abort_flag) flag_error(status, DEV_ERR_TIMEOUT);
 }
@@ -419,11 +436,13 @@ static cudaError_t gram_attrs() {
   static bool attr = false;
   if (attr) return cudaSuccess;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if ((e = cudaFuncSetAttribute(k_gram_tc<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::SMEM_BYTES)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_gram_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (e = cudaFuncSetAttribute(k_gram_tc<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::SMEM_BYTES)) != cudaSuccess ||
-      (e = cudaFuncSetAttribute(k_gram_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (e = cudaFuncSetAttribute(k_gram_tc<3, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                tc::SMEM_BYTES)) != cudaSuccess ||
+      (e = cudaFuncSetAttribute(k_gram_tc<4, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 tc::SMEM_BYTES)) != cudaSuccess)
     return e;
   attr = true;
@@ -453,7 +472,16 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
   int kchunks = gram_kchunks(tiles, nkb, P, part_cap);
   const int nkpc = (nkb + kchunks - 1) / kchunks;
   kchunks = (nkb + nkpc - 1) / nkpc;                 // no empty chunk
-  auto kern = prod == 1 ? k_gram_tc<1> : prod == 4 ? k_gram_tc<4> : k_gram_tc<3>;
+  if (prod == 1 && kchunks == 1 && Af && !S && !S2) {
+    // the factor input alone from one FP16 plane: 128 x 256 tiles (each A tile feeds twice
+    // the columns, a quarter less operand traffic per product)
+    const int64_t ntc = (nt + 1) / 2, wide = ntc * (ntc + 1);
+    k_gram_tc<1, 256><<<persistent_grid(wide), tc::THREADS, tc::SMEM_BYTES, st>>>(
+        mhi, mlo, nkb, (int)nt, wide, P, inv_n, nullptr, nullptr, Af, nu, shift_mode, 0,
+        nullptr, 0, 0, 0, 1, nkb, nullptr, status);
+    return cudaGetLastError();
+  }
+  auto kern = prod == 1 ? k_gram_tc<1, 128> : prod == 4 ? k_gram_tc<4, 128> : k_gram_tc<3, 128>;
   kern<<<persistent_grid(tiles * kchunks), tc::THREADS, tc::SMEM_BYTES, st>>>(
       mhi, mlo, nkb, (int)nt, tiles, P, inv_n, S, S2, Af, nu, shift_mode, mirror ? 1 : 0,
       nullptr, 0, 0, 0, kchunks, nkpc, kchunks > 1 ? part : nullptr, status);
@@ -479,7 +507,7 @@ cudaError_t launch_herk_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo, i
   // the first tail_cols columns (128-row tiles of the real operand = 64 complex columns)
   // are updated last
   const int tail = (int)std::min<int64_t>(nt, std::max<int64_t>(0, (tail_cols + 63) / 64));
-  auto kern = prod == 1 ? k_gram_tc<1> : k_gram_tc<3>;
+  auto kern = prod == 1 ? k_gram_tc<1, 128> : k_gram_tc<3, 128>;
   kern<<<persistent_grid(tiles), tc::THREADS, tc::SMEM_BYTES, st>>>(
       mhi, mlo, (int)(K / tc::BK), (int)nt, tiles, n, 1.0, nullptr, nullptr, nullptr, 0.0, 0, 0,
       A32, ldA, off, tail, 1, (int)(K / tc::BK), nullptr, status);

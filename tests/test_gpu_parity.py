@@ -773,6 +773,10 @@ def test_sr_step_on_given_samples_solves_oracle_equation(solver, precision):
     assert abs(st.e_mean_re - Em.real) / N <= ELOC_PER_SITE_ABS
     assert st.n_samples == C * spc and st.acceptance == 0.0
     assert st.solver_converged == 1 and st.solver_relres <= 1e-8
+    if solver == vmc.SOLVER_CHOLESKY_TC:
+        # the factor of the FP16 Gram is a near-exact preconditioner: a wrong factor input
+        # would show as a long CG, not as a wrong answer
+        assert st.solver_iters <= 25, st.solver_iters
     St = oracle.shift(S, nu, 0)
     delta = (p - p1) / dt
     res = np.linalg.norm(St @ delta - F) / np.linalg.norm(F)
