@@ -45,7 +45,6 @@ constexpr int STG_BYTES = 64 * STG_LD * 8;
 constexpr int NUM_BARS = 2 * MAX_STAGES + 5;    // full, empty, acc full x2, acc empty x2, final
 constexpr int SMEM_BYTES = 1024 /*align*/ + RING_BYTES + STG_BYTES + 256;
 constexpr int THREADS = 192;                    // TMA warp, MMA warp, 4 epilogue warps
-constexpr int TMEM_COLS = 256;                  // two 128-column accumulators (BNT = 128)
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 }  // namespace tc
@@ -99,8 +98,12 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
                                              ~uintptr_t(1023));
   // ring: PROD = 1 stages hold {A, B} (one FP16 plane; B is 256 rows when BNT = 256), the
   // others {A_hi, A_lo, B_hi, B_lo} of the BF16 products.  BNT = 256 serves only the S
-  // Gram's factor-input epilogue (Af), with one sample chunk.
+  // Gram's factor-input epilogue (Af), with one sample chunk, and runs as clusters of two
+  // CTAs on the row tiles 2c and 2c + 1 of one column tile: each CTA loads its own A and
+  // one half of the shared B, which TMA writes into both CTAs' rings (this GPU's memory
+  // only); a stage is free once both CTAs' products have read it.
   static_assert(BNT == BN || (BNT == 2 * BN && PROD == 1), "wide tiles: one FP16 plane only");
+  constexpr bool PAIR = BNT != BN;
   constexpr int NST = PROD == 1 ? RING_BYTES / ((1 + BNT / BM) * TILE_BYTES) : STAGES;
   constexpr int SB = PROD == 1 ? (1 + BNT / BM) * TILE_BYTES : STAGE_BYTES;
   constexpr int TCOLS = 2 * BNT;                   // two accumulators of BNT columns
@@ -125,6 +128,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
     for (int s = 0; s < NUM_BARS; ++s) mbar_init(smem_u32(&bars[s]), 1);
     mbar_init(smem_u32(&acce[0]), 4);
     mbar_init(smem_u32(&acce[1]), 4);
+    if (PAIR)
+      for (int s = 0; s < NST; ++s) mbar_init(smem_u32(&empty[s]), 2);   // both CTAs' products
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -136,6 +141,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   fence_before();
   __syncthreads();
   fence_after();
+  if (PAIR) cluster_sync();                          // the peer's barriers are initialised
+  const uint32_t crank = PAIR ? cluster_ctarank() : 0u;
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
@@ -156,9 +163,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
           mbar_expect_tx(fb, SB);
           tma_load_2d(smem_u32(st), &map_hi, kb * BK, bm * BM, fb);
           if (PROD != 1) tma_load_2d(smem_u32(st + OFF_AL), &map_lo, kb * BK, bm * BM, fb);
-          tma_load_2d(smem_u32(st + OFF_BH), &map_hi, kb * BK, bn * BNT, fb);
-          if (BNT != BN)
-            tma_load_2d(smem_u32(st + OFF_BH + TILE_BYTES), &map_hi, kb * BK, bn * BNT + BN, fb);
+          if (PAIR)
+            tma_load_2d_mc(smem_u32(st + OFF_BH + crank * TILE_BYTES), &map_hi, kb * BK,
+                           bn * BNT + (int)crank * BN, fb, (uint16_t)3);
+          else
+            tma_load_2d(smem_u32(st + OFF_BH), &map_hi, kb * BK, bn * BNT, fb);
           if (PROD != 1) tma_load_2d(smem_u32(st + OFF_BL), &map_lo, kb * BK, bn * BN, fb);
         }
       }
@@ -203,7 +212,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             if (PROD == 4) mma_bf16(d, al + o, bl + o, idesc, 1u);   // (hi+lo)(hi+lo)^T: PSD
           }
           issued_any = true;
-          mma_commit(smem_u32(&empty[s]));            // frees the stage when these finish
+          if (PAIR) mma_commit_mc(smem_u32(&empty[s]), (uint16_t)3);   // in both CTAs
+          else mma_commit(smem_u32(&empty[s]));        // frees the stage when these finish
         }
         if (!ok) break;
         mma_commit(smem_u32(&accf[acc]));              // accumulator complete
@@ -247,6 +257,7 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       if (!epi_go[i & 1]) break;
       fence_after();
       const int64_t k = (int64_t)bm * (BM / 2) + (r >> 1);
+      const float inv_nf = (float)inv_n, nuf = (float)nu;
       for (int c0 = 0; c0 < BNT; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(acc * BNT + c0), v);
@@ -276,6 +287,22 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
             const int64_t l = l0 + q;
             if (even && k < P && l < P && (bm != bn || l <= k))
               part[((int64_t)kc * P + k) * P + l] = make_float2(mine0 + oth1, mine1 - oth0);
+          }
+        } else if (Af && !S && !S2) {
+          // the factor input alone (the preconditioner's S): FP32 arithmetic throughout --
+          // an FP64 fold per entry would bound the tile on B300's FP64 pipe
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const float mine0 = v[2 * q], mine1 = v[2 * q + 1];
+            const float oth0 = __shfl_xor_sync(0xffffffffu, mine0, 1);
+            const float oth1 = __shfl_xor_sync(0xffffffffu, mine1, 1);
+            const int64_t l = l0 + q;
+            if (even && k < P && l < P && l <= k) {
+              const float vr = (mine0 + oth1) * inv_nf;
+              const float vi = (l == k) ? 0.f : (mine1 - oth0) * inv_nf;
+              Af[k * P + l] = make_float2(
+                  (l == k) ? (shift_mode == 0 ? vr * (1.f + nuf) : vr + nuf) : vr, vi);
+            }
           }
         } else {
           // row 2k holds G[2k][2l], G[2k][2l+1]; row 2k+1 holds G[2k+1][2l], G[2k+1][2l+1].
@@ -341,6 +368,9 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   }
   fence_before();
   __syncthreads();
+  // the peer's copies into this CTA's ring and its products' arrivals on this CTA's
+  // barriers are complete before either CTA of a pair exits
+  if (PAIR) cluster_sync();
   if (warp == 1) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
@@ -449,6 +479,33 @@ static cudaError_t gram_attrs() {
   return cudaSuccess;
 }
 
+// Launch configuration of the paired (128 x 256 tile) kernel: clusters of two CTAs, as many
+// clusters as fit on the GPU at once (each CTA takes a whole SM); grid 0 if none fit.
+static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int64_t pairs, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(tc::THREADS, 1, 1);
+  cfg.dynamicSmemBytes = tc::SMEM_BYTES;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  static int clusters = -1;
+  if (clusters < 0) {
+    cfg.gridDim = dim3(2, 1, 1);
+    int c = 0;
+    if (cudaOccupancyMaxActiveClusters(&c, (const void*)k_gram_tc<1, 256>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      c = 0;
+    }
+    clusters = c;
+  }
+  cfg.gridDim = dim3((unsigned)(2 * std::min<int64_t>(clusters, pairs)), 1, 1);
+  return cfg;
+}
+
 // prod: 1 (one FP16 plane in Xhi, Xlo unused), 3 or 4 (BF16 hi/lo planes)
 cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
                            int64_t rows_pad, int64_t ld, int64_t P, double inv_n, double2* S,
@@ -473,13 +530,20 @@ cudaError_t launch_gram_tc(const __nv_bfloat16* Xhi, const __nv_bfloat16* Xlo,
   const int nkpc = (nkb + kchunks - 1) / kchunks;
   kchunks = (nkb + nkpc - 1) / nkpc;                 // no empty chunk
   if (prod == 1 && kchunks == 1 && Af && !S && !S2) {
-    // the factor input alone from one FP16 plane: 128 x 256 tiles (each A tile feeds twice
-    // the columns, a quarter less operand traffic per product)
-    const int64_t ntc = (nt + 1) / 2, wide = ntc * (ntc + 1);
-    k_gram_tc<1, 256><<<persistent_grid(wide), tc::THREADS, tc::SMEM_BYTES, st>>>(
-        mhi, mlo, nkb, (int)nt, wide, P, inv_n, nullptr, nullptr, Af, nu, shift_mode, 0,
-        nullptr, 0, 0, 0, 1, nkb, nullptr, status);
-    return cudaGetLastError();
+    // the factor input alone from one FP16 plane: 128 x 256 tiles computed by CTA pairs
+    // that share the B tile (each CTA loads 32 KB per 64 samples for a 128 x 256 block:
+    // two thirds of the operand traffic of the 128 x 128 tiles per product)
+    const int64_t ntc = (nt + 1) / 2, pairs = ntc * (ntc + 1) / 2;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = pair_config(attr, pairs, st);
+    if (cfg.gridDim.x > 0) {
+      double2* no_s = nullptr;
+      float4* no_s2 = nullptr;
+      float2* no_f2 = nullptr;
+      return cudaLaunchKernelEx(&cfg, k_gram_tc<1, 256>, mhi, mlo, nkb, (int)nt, 2 * pairs, P,
+                                inv_n, no_s, no_s2, Af, nu, shift_mode, 0, no_f2, (int64_t)0,
+                                (int64_t)0, 0, 1, nkb, no_f2, status);
+    }
   }
   auto kern = prod == 1 ? k_gram_tc<1, 128> : prod == 4 ? k_gram_tc<4, 128> : k_gram_tc<3, 128>;
   kern<<<persistent_grid(tiles * kchunks), tc::THREADS, tc::SMEM_BYTES, st>>>(
