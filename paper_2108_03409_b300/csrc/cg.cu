@@ -453,8 +453,22 @@ __global__ void __launch_bounds__(256) k_add_diag(const double2* __restrict__ y,
   block_partial(pq, vpart + OFF_PQ, red);
 }
 
+// Compensated FP32 sum (Neumaier): s + c is the sum of the added FP32 values to within
+// about one FP32 rounding of the result (plus count * 2^-48 of their magnitudes), with FP32
+// operations only (on B300 an FP64 add per partial would bound the reduction on the FP64
+// pipe).
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v;
+    c += (fabsf(s) >= fabsf(v)) ? (s - t) + v : (v - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 // q_k = y_k + D_k p_k with y_k = (1/n) sum_q conj(Obar_qk) w_q from the K-chunk partials
-// (FP64 sum over chunks in order): a_i: out rows 2M / 2M+1, column i; b_j: ybpart[.][j];
+// (compensated sum over chunks in order): a_i: out rows 2M / 2M+1, column i; b_j: ybpart[.][j];
 // W_ji: out rows 2j / 2j+1, column i.  Partials of Re p^H q.  Without D: q = y (conjugated
 // if conj_out), no partials.
 __global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ out,
@@ -474,13 +488,13 @@ __global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ 
   double pq = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
        k += (int64_t)gridDim.x * blockDim.x) {
-    double re = 0.0, im = 0.0;
+    CSum sr, si;
     if (k >= N && k < N + M) {
 #pragma unroll 8
       for (int c = 0; c < kchunks; ++c) {
         const float2 v = ybpart[(int64_t)c * M + (k - N)];
-        re += (double)v.x;
-        im += (double)v.y;
+        sr.add(v.x);
+        si.add(v.y);
       }
     } else {
       int64_t row, col;
@@ -490,10 +504,11 @@ __global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ 
       const int64_t cs = a_rows * ncols;
 #pragma unroll 8
       for (int c = 0; c < kchunks; ++c) {
-        re += (double)g[(int64_t)c * cs];
-        im += (double)g[(int64_t)c * cs + ncols];
+        sr.add(g[(int64_t)c * cs]);
+        si.add(g[(int64_t)c * cs + ncols]);
       }
     }
+    const double re = sr.value(), im = si.value();
     if (D) {
       const double2 pk = p[k];
       const double2 qk = make_double2(re * inv + D[k] * pk.x, im * inv + D[k] * pk.y);

@@ -480,7 +480,8 @@ def test_sr_step_matches_oracle_pipeline(solver, precision):
 CG_OPERATOR_REL = 128 * 2.0 ** -24 * 8
 # On the tensor cores the direction's W block and conj(t) u' are BF16 hi/lo pairs (~2^-17
 # relative each, lo.lo dropped: 4 * 2^-16 as for S) and the Obar^H u sums accumulate in FP32
-# over K chunks of 2048 samples (worst case 2048 * 2^-24) before the FP64 sum of the chunks.
+# over K chunks of 2048 samples (worst case 2048 * 2^-24) before the compensated sum of the
+# chunks (about one FP32 rounding of the result).
 CG_OPERATOR_REL_TC = 4 * 2.0 ** -16 + 2048 * 2.0 ** -24
 
 
