@@ -453,20 +453,6 @@ __global__ void __launch_bounds__(256) k_add_diag(const double2* __restrict__ y,
   block_partial(pq, vpart + OFF_PQ, red);
 }
 
-// Compensated FP32 sum (Neumaier): s + c is the sum of the added FP32 values to within
-// about one FP32 rounding of the result (plus count * 2^-48 of their magnitudes), with FP32
-// operations only (on B300 an FP64 add per partial would bound the reduction on the FP64
-// pipe).
-struct CSum {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float t = s + v;
-    c += (fabsf(s) >= fabsf(v)) ? (s - t) + v : (v - t) + s;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
 // q_k = y_k + D_k p_k with y_k = (1/n) sum_q conj(Obar_qk) w_q from the K-chunk partials
 // (compensated sum over chunks in order): a_i: out rows 2M / 2M+1, column i; b_j: ybpart[.][j];
 // W_ji: out rows 2j / 2j+1, column i.  Partials of Re p^H q.  Without D: q = y (conjugated
@@ -556,7 +542,8 @@ static cudaError_t apply_s(const CgProblem& pb, CgWork& w, const double2* p, dou
   k_vs_partial<<<grid, 256, 0, st>>>(w.V, w.vb, pb.spins, pb.T, n, N, M, w.upart);
   k_vs_finish<<<g1d(n), 256, 0, st>>>(w.upart, mtiles, pb.spins, w.va, w.sc + 2, n, N, w.u);
   VMC_TRY(launch_estats(w.u, n, w.ustats, nullptr, st));
-  VMC_TRY(launch_moments(pb.spins, pb.T, w.u, w.ustats, n, N, M, w.mpart, nullptr, w.y, st));
+  VMC_TRY(launch_moments(pb.spins, pb.T, w.u, w.ustats, n, N, M, w.mpart, nullptr, w.y, st,
+                         moments_chunk(n)));
   k_add_diag<<<CG_RB, 256, 0, st>>>(w.y, w.D, p, P, q, w.vpart, w.flag);
   *launches += 8;
   return cudaGetLastError();

@@ -184,6 +184,20 @@ __device__ __forceinline__ bool grid_sync(GridBarrier* bar, unsigned nblocks, un
 
 // warp reductions with xor butterflies: every lane ends with the same bits (each level
 // adds the same two operands in both partner lanes).
+// Compensated FP32 sum (Neumaier): s + c is the sum of the added FP32 values to within
+// about one FP32 rounding of the result (plus count * 2^-48 of their magnitudes), with FP32
+// operations only (on B300 an FP64 add per partial would bound the reduction on the FP64
+// pipe).
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v;
+    c += (fabsf(s) >= fabsf(v)) ? (s - t) + v : (v - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
