@@ -14,7 +14,8 @@
 // warp 0 issues TMA loads (cp.async.bulk.tensor, 128-byte swizzle) into a ring of 3
 // stages (6 for one FP16 plane, whose stages are half as large), warp 1 issues
 // tcgen05.mma (kind::f16, BF16 or FP16 in, FP32 accumulate, 128 x 128 x 16) into one of two
-// TMEM accumulators, and warps 2-5 drain the other accumulator with tcgen05.ld, so
+// TMEM accumulators, and warps 2-9 (two per TMEM lane quadrant, each taking half of the
+// columns) drain the other accumulator with tcgen05.ld, so
 // the epilogue of one tile overlaps the loads and products of the next.  Ring stages and
 // accumulators are handed over through mbarriers (tcgen05.commit arrives on them).  Every
 // wait is bounded (iteration and clock limits); on expiry the kernel records
@@ -44,7 +45,9 @@ constexpr int STG_LD = 66;                      // staging row stride (float2) o
 constexpr int STG_BYTES = 64 * STG_LD * 8;
 constexpr int NUM_BARS = 2 * MAX_STAGES + 5;    // full, empty, acc full x2, acc empty x2, final
 constexpr int SMEM_BYTES = 1024 /*align*/ + RING_BYTES + STG_BYTES + 256;
-constexpr int THREADS = 192;                    // TMA warp, MMA warp, 4 epilogue warps
+constexpr int EPI_WARPS = 8;                    // two per TMEM lane quadrant
+constexpr int EPI_THREADS = 32 * EPI_WARPS;
+constexpr int THREADS = 64 + EPI_THREADS;       // TMA warp, MMA warp, 8 epilogue warps
 static_assert(SMEM_BYTES <= 232448, "shared memory budget");
 
 }  // namespace tc
@@ -126,8 +129,8 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NUM_BARS; ++s) mbar_init(smem_u32(&bars[s]), 1);
-    mbar_init(smem_u32(&acce[0]), 4);
-    mbar_init(smem_u32(&acce[1]), 4);
+    mbar_init(smem_u32(&acce[0]), EPI_WARPS);
+    mbar_init(smem_u32(&acce[1]), EPI_WARPS);
     if (PAIR)
       for (int s = 0; s < NST; ++s) mbar_init(smem_u32(&empty[s]), 2);   // both CTAs' products
     *abort_flag = 0;
@@ -226,10 +229,11 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       }
     }
   } else {
-    // ---------------- epilogue: warps 2-5; TMEM lane quadrant = warp % 4 ----------------
+    // ------- epilogue: warps 2-9; TMEM lane quadrant = warp % 4, column half by warp -------
     const int qd = warp & 3;
+    const int half = (warp - 2) >> 2;                // warps 2-5: first half of the columns
     const int r = qd * 32 + lane;                    // tile row held by this thread
-    const int et = (warp - 2) * 32 + lane;           // 0..127 within the epilogue group
+    const int et = (warp - 2) * 32 + lane;           // 0..255 within the epilogue group
     const bool even = (r & 1) == 0;
     int i = 0;
     for (int64_t t = blockIdx.x; t < tiles * kchunks; t += gridDim.x, ++i) {
@@ -238,14 +242,15 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       if (BNT == BN) schur_tile(t % tiles, nt, tail, &bm, &bn);
       else wide_tile(t, nt, &bm, &bn);
       const int kc = (int)(t / tiles);
-      // Schur mode: fetch this thread's 32 entries of the factor's tile now, so that their
+      // Schur mode: fetch this thread's 16 entries of the factor's tile now, so that their
       // memory latency overlaps the wait for the products (no stores intervene).
-      float2 cur[32];
+      constexpr int PER = 64 * 64 / EPI_THREADS;
+      float2 cur[PER];
       if (BNT == BN && A32) {
         const int64_t kb0 = (int64_t)bm * (BM / 2), lb0 = (int64_t)bn * (BN / 2);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int e = et + 128 * j, rr = e >> 6, cc = e & 63;
+        for (int j = 0; j < PER; ++j) {
+          const int e = et + EPI_THREADS * j, rr = e >> 6, cc = e & 63;
           const int64_t kk = kb0 + rr, ll = lb0 + cc;
           cur[j] = (kk < P && ll < P && (bm != bn || ll <= kk)) ? A32[(off + kk) * ldA + off + ll]
                                                               : make_float2(0.f, 0.f);
@@ -253,12 +258,12 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       }
       if (et == 0)
         epi_go[i & 1] = mbar_wait(smem_u32(&accf[acc]), (uint32_t)(u & 1), abort_flag) && !*abort_flag;
-      named_bar_sync(1, 128);                        // the leader's verdict is uniform
+      named_bar_sync(1, EPI_THREADS);                // the leader's verdict is uniform
       if (!epi_go[i & 1]) break;
       fence_after();
       const int64_t k = (int64_t)bm * (BM / 2) + (r >> 1);
       const float inv_nf = (float)inv_n, nuf = (float)nu;
-      for (int c0 = 0; c0 < BNT; c0 += 32) {
+      for (int c0 = half * (BNT / 2); c0 < (half + 1) * (BNT / 2); c0 += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(acc * BNT + c0), v);
         const int64_t l0 = (int64_t)bn * (BNT / 2) + (c0 >> 1);
@@ -346,14 +351,14 @@ k_gram_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CU
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acce[acc]));
       if (BNT == BN && A32) {
-        named_bar_sync(1, 128);                      // staging complete
+        named_bar_sync(1, EPI_THREADS);              // staging complete
         // A[off+k][off+l] -= conj(fold) on l <= k, coalesced along rows; the diagonal
         // stays real.  (The next tile's writes to the staging buffer come after the next
         // named barrier, which every thread reaches only after this loop.)
         const int64_t kb0 = (int64_t)bm * (BM / 2), lb0 = (int64_t)bn * (BN / 2);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int e = et + 128 * j, rr = e >> 6, cc = e & 63;
+        for (int j = 0; j < PER; ++j) {
+          const int e = et + EPI_THREADS * j, rr = e >> 6, cc = e & 63;
           const int64_t kk = kb0 + rr, ll = lb0 + cc;
           if (kk < P && ll < P && (bm != bn || ll <= kk)) {
             const float2 f = stg[rr * STG_LD + cc];
