@@ -70,7 +70,7 @@ FAMILIES = {
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one S-Gram launch (one FP16
 # product) of the default workload, from an ncu capture of the same command (2.211 GB read,
 # 0.271 GB written); None once the kernel changes until it is taken again
-GRAM_F16_TRAFFIC = 2.482312192e9
+GRAM_F16_TRAFFIC = None
 DEFAULT_WORKLOAD = "heis2d_8x8_alpha2_c8192"
 W = WORKLOADS[DEFAULT_WORKLOAD]
 LX, LY, ALPHA, CHAINS, SHIFT = W["Lx"], W["Ly"], W["alpha"], W["chains"], W["shift"]
@@ -791,7 +791,7 @@ def run_learned(args):
     N, M = L * L, wl["alpha"] * L * L
     stream = torch.cuda.current_stream()
     cfg = vmc.make_config(seed=1 + rank, n_chains=C, therm_sweeps=20, solver=vmc.SOLVER_CG,
-                          shift=1e-3, cg_maxit=100, cg_tol=1e-6, made_hidden=H, made_batch=4096)
+                          shift=1e-3, cg_maxit=1000, cg_tol=1e-6, made_hidden=H, made_batch=4096)
     ctx = vmc.vmc_init(cfg, [vmc.make_lattice(vmc.MODEL_TFIM, L, L, 1.0, wl["h"], wl["alpha"])],
                        stream.cuda_stream)
     vmc.vmc_set_params(ctx, 0, inputs.rbm_params(N, M, 0.01, seed=1234))
