@@ -68,9 +68,9 @@ FAMILIES = {
                                            h=1.0, dt=0.05),
 }
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one S-Gram launch (one FP16
-# product) of the default workload, from an ncu capture of the same command (2.211 GB read,
-# 0.271 GB written); None once the kernel changes until it is taken again
-GRAM_F16_TRAFFIC = None
+# product) of the default workload, from an ncu capture of the same command (2.207 GB read,
+# 0.273 GB written); None once the kernel changes until it is taken again
+GRAM_F16_TRAFFIC = 2.479496e9
 DEFAULT_WORKLOAD = "heis2d_8x8_alpha2_c8192"
 W = WORKLOADS[DEFAULT_WORKLOAD]
 LX, LY, ALPHA, CHAINS, SHIFT = W["Lx"], W["Ly"], W["alpha"], W["chains"], W["shift"]
