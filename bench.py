@@ -790,17 +790,38 @@ def run_learned(args):
     L, C, H = wl["L"], wl["chains"], wl["hidden"]
     N, M = L * L, wl["alpha"] * L * L
     stream = torch.cuda.current_stream()
-    cfg = vmc.make_config(seed=1 + rank, n_chains=C, therm_sweeps=20, solver=vmc.SOLVER_CG,
-                          shift=1e-3, cg_maxit=1000, cg_tol=1e-6, made_hidden=H, made_batch=4096)
-    ctx = vmc.vmc_init(cfg, [vmc.make_lattice(vmc.MODEL_TFIM, L, L, 1.0, wl["h"], wl["alpha"])],
-                       stream.cuda_stream)
-    vmc.vmc_set_params(ctx, 0, inputs.rbm_params(N, M, 0.01, seed=1234))
-    vmc.vmc_set_chains(ctx, 0, inputs.random_spins(C, N, seed=99 + rank))
+    lat = [vmc.make_lattice(vmc.MODEL_TFIM, L, L, 1.0, wl["h"], wl["alpha"])]
+    # the checkpoint: plain SR steps by matrix-free CG with the operator on the tensor cores
+    # and a diagonal shift of 1e-2 (with 1e-3 near this critical point the CG needs 700-1000
+    # iterations and more per step and stalls: the FP32 SIMT operator at its 1e-6 rounding
+    # floor, the BF16-split one above it); a step whose CG stops above cg_tol is counted and
+    # not applied
+    pcfg = vmc.make_config(seed=1 + rank, n_chains=C, therm_sweeps=20, solver=vmc.SOLVER_CG,
+                           precision=vmc.PREC_BF16SPLIT, shift=1e-2, cg_maxit=1000, cg_tol=1e-6)
+    pctx = vmc.vmc_init(pcfg, lat, stream.cuda_stream)
+    vmc.vmc_set_params(pctx, 0, inputs.rbm_params(N, M, 0.01, seed=1234))
+    vmc.vmc_set_chains(pctx, 0, inputs.random_spins(C, N, seed=99 + rank))
     t0 = time.perf_counter()
+    unconverged, sr_iters = 0, []
     for _ in range(wl["sr_steps"]):
-        st = vmc.vmc_sr_step(ctx, 0, DT)
+        try:
+            st = vmc.vmc_sr_step(pctx, 0, DT)
+        except vmc.VmcError as e:
+            if e.status != vmc.VMC_ERR_NUMERIC or getattr(e, "stats", None) is None:
+                raise
+            st = e.stats
+            unconverged += 1
+        sr_iters.append(st.solver_iters)
     t_sr = time.perf_counter() - t0
     e_sr = st.e_mean_re / N
+    theta_ck, chains_ck = vmc.vmc_get_params(pctx, 0), vmc.vmc_get_chains(pctx, 0, C, N)
+    vmc.vmc_destroy(pctx)
+    # both samplers run in FP32 from the checkpoint
+    cfg = vmc.make_config(seed=1 + rank, n_chains=C, therm_sweeps=20, solver=vmc.SOLVER_CG,
+                          shift=1e-3, cg_maxit=1000, cg_tol=1e-6, made_hidden=H, made_batch=4096)
+    ctx = vmc.vmc_init(cfg, lat, stream.cuda_stream)
+    vmc.vmc_set_params(ctx, 0, theta_ck)
+    vmc.vmc_set_chains(ctx, 0, chains_ck)
     # training set: 2^18 samples of the local chains (one sweep apart)
     R = wl["train_records"]
     train = torch.zeros((R * C, N), dtype=torch.int8, device="cuda")
@@ -890,7 +911,11 @@ def run_learned(args):
                "verdict": ("accepted" if (dE <= 1e-4 and dE <= 3 * comb and
                                           res["learned"]["tau_int_E"] < res["local"]["tau_int_E"])
                            else "rejected")},
-           "checkpoint": {"e_per_site": e_sr, "s": t_sr}, "train": {"loss": loss, "s": t_train},
+           "checkpoint": {"e_per_site": e_sr, "s": t_sr, "cg_iters_max": max(sr_iters),
+                          "cg_iters_mean": float(np.mean(sr_iters)),
+                          "unconverged_steps": unconverged,
+                          "solver": "CG, BF16-split operator, shift 1e-2, relative residual 1e-6"},
+           "train": {"loss": loss, "s": t_train},
            "roofline": None,
            "note": "sampler comparison; rooflines of the sweep and Gram kernels are in the "
                    "default workload's line",
