@@ -221,6 +221,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(values, ws, device="cuda"):
+    """Each entry's largest value over the ranks (a timed region lasts as long as its slowest
+    replica); every rank gets the result.  One rank: the values as they are."""
+    vals = [float(v) for v in values]
+    if ws <= 1:
+        return vals
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_rate(ws, units_per_rank, ms):
+    """Whole-job throughput of ws replicas that each processed units_per_rank units in a
+    region of ms milliseconds (the max over the ranks)."""
+    return ws * units_per_rank / (ms / 1e3)
+
+
 # ----------------------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of the same workload
 # ----------------------------------------------------------------------------------------
@@ -455,12 +473,9 @@ def run_ours(args):
     arm = _sr_arm(wl, prec, solver, args.steps, args.warmup, rank, stream, local, vmc, inputs,
                   barrier, torch)
     ctx, st_list, clk, launches = arm["ctx"], arm["st"], arm["clk"], arm["launches"]
-    ms_t = torch.tensor([arm["ms"]], device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks([arm["ms"]], ws)[0]
     ms_step = ms / args.steps
-    value = ws * args.steps / (ms / 1e3)
+    value = replica_rate(ws, args.steps, ms)
 
     # e2e: parameters in from pinned host memory, parameters + statistics out, every step
     host_p = torch.from_numpy(vmc.vmc_get_params(ctx, 0).view(np.float64).copy()).pin_memory()
@@ -710,10 +725,7 @@ def run_batched(args):
             vmc.vmc_sample(ctx, l, 0, 1, outs[l], None, eloc[l * C:(l + 1) * C])
     ms_p = timed(per_lattice)
     ms_ng = timed(lambda: vmc.vmc_sample_all(ctx, 0, 1, spins, eloc, False))
-    ms_t = torch.tensor([ms_b, ms_p, ms_ng], device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_b, ms_p, ms_ng = (float(x) for x in ms_t.tolist())
+    ms_b, ms_p, ms_ng = max_over_ranks([ms_b, ms_p, ms_ng], ws)
     samples = n_lat * C
     value = ws * samples * args.steps / (ms_b / 1e3)
 
@@ -979,10 +991,7 @@ def run_tdvp(args):
         barrier()
     ms = ev0.elapsed_time(ev1)
     launches = vmc.vmc_kernel_launches(ctx) - launches0
-    ms_t = torch.tensor([ms], device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks([ms], ws)[0]
     evals = sum(s.rhs_evals for s in sts)
     value = ws * args.steps / (ms / 1e3)
     # e2e: the parameters in from pinned host memory and out again around every step
@@ -1112,10 +1121,7 @@ def run_family(args):
         barrier()
     ms = ev0.elapsed_time(ev1)
     launches = vmc.vmc_kernel_launches(ctx) - launches0
-    ms_t = torch.tensor([ms], device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms = float(ms_t.item())
+    ms = max_over_ranks([ms], ws)[0]
     value = ws * args.steps / (ms / 1e3)
     if kind == "ar":
         ms_k = statistics.mean(s.ms_gram for s in sts)

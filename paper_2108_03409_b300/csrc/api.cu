@@ -187,13 +187,6 @@ vmc_status refresh_fp32(vmc_ctx* ctx, LatticeState& L) {
   return VMC_OK;
 }
 
-// The contexts' <O>/F scratch: moments_chunk(n) makes at most 32 chunks for any n <= Ns
-// (the size also covers the fixed 1024-sample chunks of Ns samples)
-static size_t moments_scratch(int64_t Ns, int N, int M) {
-  return (size_t)std::max<int64_t>(moments_partial_doubles(Ns, N, M),
-                                   32 * 4 * (int64_t)(M + 1) * (N + 1));
-}
-
 // S of a sample set with T = tanh theta already in ctx->s_T; E may be null.  S_out (FP64)
 // may be null when `fused` (tensor-core Gram only, the SR step): the Gram then writes the
 // shifted lower triangle that the preconditioner's factorisation takes (ctx->sw.A32)
@@ -202,7 +195,7 @@ vmc_status qfm_core(vmc_ctx* ctx, LatticeState& L, const int8_t* spins, const fl
                     int64_t n, int precision, double2* S_out, bool mirror, bool fused = false,
                     bool lolo = false) {
   CK(launch_moments(spins, ctx->s_T, E, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
-                    E ? ctx->F : nullptr, ctx->st, moments_chunk(n)), "moments");
+                    E ? ctx->F : nullptr, ctx->st), "moments");
   ctx->launches += 2;
   const int64_t rows = 2 * L.P;
   const int64_t rows_pad = (rows + 127) / 128 * 128;
@@ -407,7 +400,7 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
   if ((e = dalloc(ctx, &ctx->s_spins, (size_t)Ns * ctx->Nmax)) ||
       (e = dalloc(ctx, &ctx->s_T, (size_t)Ns * ctx->Mmax)) || (e = dalloc(ctx, &ctx->s_E, (Ns + 255) / 256 * 256)) ||
       (e = dalloc(ctx, &ctx->estats, 8)) ||
-      (e = dalloc(ctx, &ctx->partial, moments_scratch(Ns, ctx->Nmax, ctx->Mmax))) ||
+      (e = dalloc(ctx, &ctx->partial, (size_t)moments_partial_doubles(Ns, ctx->Nmax, ctx->Mmax))) ||
       (e = dalloc(ctx, &ctx->meanO, ctx->Pmax)) || (e = dalloc(ctx, &ctx->mean2, ctx->Pmax)) || (e = dalloc(ctx, &ctx->F, ctx->Pmax)) ||
       (e = dalloc(ctx, &ctx->x, ctx->Pmax)) || (e = dalloc(ctx, &ctx->status, 1)) ||
       (e = dalloc(ctx, &ctx->n_accept, 1)))
@@ -723,7 +716,7 @@ vmc_status vmc_grad(vmc_ctx* ctx, int lattice, const int8_t* spins, const float*
   CK(launch_theta_tanh(rbm_of(L), spins, n, ctx->s_T, ctx->st), "theta_tanh");
   CK(launch_estats(E, n, ctx->estats, ctx->status, ctx->st), "estats");
   CK(launch_moments(spins, ctx->s_T, E, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO, ctx->F,
-                    ctx->st, moments_chunk(n)), "moments");
+                    ctx->st), "moments");
   ctx->launches += 4;
   if (F_out)
     CK(cudaMemcpyAsync(F_out, ctx->F, L.P * sizeof(double2), cudaMemcpyDeviceToDevice, ctx->st), "grad");
@@ -773,7 +766,7 @@ vmc_status vmc_cg_solve(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
   const vmc_config& c = ctx->cfg;
   CK(launch_theta_tanh(rbm_of(L), spins, n, ctx->s_T, ctx->st), "theta_tanh");
   CK(launch_moments(spins, ctx->s_T, nullptr, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
-                    nullptr, ctx->st, moments_chunk(n)), "moments");
+                    nullptr, ctx->st), "moments");
   ctx->launches += 3;
   CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO,
                ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, n).ok, ctx->status};
@@ -802,7 +795,7 @@ vmc_status vmc_sr_apply(vmc_ctx* ctx, int lattice, const int8_t* spins, int64_t 
   const vmc_config& c = ctx->cfg;
   CK(launch_theta_tanh(rbm_of(L), spins, n, ctx->s_T, ctx->st), "theta_tanh");
   CK(launch_moments(spins, ctx->s_T, nullptr, ctx->estats, n, L.N, L.M, ctx->partial, ctx->meanO,
-                    nullptr, ctx->st, moments_chunk(n)), "moments");
+                    nullptr, ctx->st), "moments");
   ctx->launches += 3;
   CgProblem pb{spins, ctx->s_T, n, L.N, L.M, ctx->meanO,
                ctx->cg.Sb != nullptr && cg_tc_shape(L.N, L.M, n).ok, ctx->status};
@@ -947,7 +940,7 @@ static vmc_status sr_step_impl(vmc_ctx* ctx, int lattice, double dt, vmc_sr_stat
                        &ctx->launches), "moments");
     } else {
       CK(launch_moments(ctx->s_spins, ctx->s_T, ctx->s_E, ctx->estats, Ns, L.N, L.M, ctx->partial,
-                        ctx->meanO, ctx->F, ctx->st, moments_chunk(Ns)), "moments");
+                        ctx->meanO, ctx->F, ctx->st), "moments");
       ctx->launches += 2;
     }
     CK(cg_prepare(pb, ctx->cg, c.shift, c.shift_mode, ctx->st, &ctx->launches, pb.tc),
