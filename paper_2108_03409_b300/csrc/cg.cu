@@ -542,8 +542,7 @@ static cudaError_t apply_s(const CgProblem& pb, CgWork& w, const double2* p, dou
   k_vs_partial<<<grid, 256, 0, st>>>(w.V, w.vb, pb.spins, pb.T, n, N, M, w.upart);
   k_vs_finish<<<g1d(n), 256, 0, st>>>(w.upart, mtiles, pb.spins, w.va, w.sc + 2, n, N, w.u);
   VMC_TRY(launch_estats(w.u, n, w.ustats, nullptr, st));
-  VMC_TRY(launch_moments(pb.spins, pb.T, w.u, w.ustats, n, N, M, w.mpart, nullptr, w.y, st,
-                         moments_chunk(n)));
+  VMC_TRY(launch_moments(pb.spins, pb.T, w.u, w.ustats, n, N, M, w.mpart, nullptr, w.y, st));
   k_add_diag<<<CG_RB, 256, 0, st>>>(w.y, w.D, p, P, q, w.vpart, w.flag);
   *launches += 8;
   return cudaGetLastError();

@@ -73,32 +73,26 @@ cudaError_t launch_estats(const float2* E, int64_t n, double* out, unsigned* sta
 // j = M whose factor is 1 and a virtual visible unit i = N whose spin is 1:
 //   (j < M, i < N): O = t_j s_i (W block);  (j < M, i = N): O = t_j (b block);
 //   (j = M, i < N): O = s_i (a block).
-// Each block sums a 32x32 tile over a chunk of samples: FP32 within sub-chunks of kSub
-// samples, FP64 across them; chunk partials are then added in a fixed order.
+// Each block sums a 32x32 tile over a chunk of kChunk samples: FP32 within sub-chunks of
+// kSub samples, FP64 across them; chunk partials are then added in a fixed order.
 // ---------------------------------------------------------------------------------------
-static constexpr int kSub = 128, kTile = 32;
+static constexpr int kChunk = 1024, kSub = 128, kTile = 32;
 
-// at most 32 chunks of at least 256 samples: enough blocks for the GPU at n = 8192
-int64_t moments_chunk(int64_t n) {
-  return std::max<int64_t>(256, ((n + 31) / 32 + 31) / 32 * 32);
-}
-
-int64_t moments_partial_doubles(int64_t n, int N, int M, int64_t chunk) {
-  int64_t chunks = (n + chunk - 1) / chunk;
+int64_t moments_partial_doubles(int64_t n, int N, int M) {
+  int64_t chunks = (n + kChunk - 1) / kChunk;
   return chunks * 4 * (int64_t)(M + 1) * (N + 1);
 }
 
 __global__ void __launch_bounds__(1024) k_moments_partial(
     const int8_t* __restrict__ spins, const float2* __restrict__ T, const float2* __restrict__ E,
-    const double* __restrict__ estats, int64_t n, int N, int M, int64_t chunk,
-    double* __restrict__ partial) {
+    const double* __restrict__ estats, int64_t n, int N, int M, double* __restrict__ partial) {
   __shared__ float2 Ts[32][kTile + 1];
   __shared__ float2 Us[32][kTile + 1];
   __shared__ float Ss[32][kTile + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile;
-  const int64_t q0 = (int64_t)blockIdx.z * chunk;
-  const int64_t q1 = min(n, q0 + chunk);
+  const int64_t q0 = (int64_t)blockIdx.z * kChunk;
+  const int64_t q1 = min(n, q0 + kChunk);
   const float emr = E ? (float)estats[0] : 0.f, emi = E ? (float)estats[1] : 0.f;
   const int i = i0 + tx, j = j0 + ty;
   double dm_r = 0, dm_i = 0, df_r = 0, df_i = 0;
@@ -181,18 +175,18 @@ __global__ void k_moments_reduce(const double* __restrict__ partial, int64_t chu
 
 cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E,
                            const double* estats, int64_t n, int N, int M, double* partial,
-                           double2* meanO, double2* F, cudaStream_t st, int64_t chunk) {
-  if (n <= 0 || chunk < 32 || chunk % 32) return cudaErrorInvalidValue;
-  const int64_t chunks = (n + chunk - 1) / chunk;
+                           double2* meanO, double2* F, cudaStream_t st) {
+  if (n <= 0) return cudaErrorInvalidValue;
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
   if (chunks > kMomentsMaxChunks) return cudaErrorInvalidValue;   // one chunk per grid z
   dim3 grid((N + 1 + kTile - 1) / kTile, (M + 1 + kTile - 1) / kTile, (unsigned)chunks);
   dim3 block(kTile, 32);
-  k_moments_partial<<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, chunk, partial);
+  k_moments_partial<<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, partial);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t plane = (int64_t)(M + 1) * (N + 1);
-  int blocks = (int)std::min<int64_t>((plane + 63) / 64, 8192);
-  k_moments_reduce<<<blocks, 64, 0, st>>>(partial, chunks, n, N, M, meanO, F);
+  int blocks = (int)std::min<int64_t>((plane + 255) / 256, 4096);
+  k_moments_reduce<<<blocks, 256, 0, st>>>(partial, chunks, n, N, M, meanO, F);
   return cudaGetLastError();
 }
 
