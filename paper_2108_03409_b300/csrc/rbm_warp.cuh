@@ -68,11 +68,16 @@ __device__ __forceinline__ float2 move_factor(float2 t, float2 th, float si) {
   return make_float2(fmaf(-si, p.x, 1.f), -si * p.y);
 }
 
+// (the quotient with the hardware reciprocal, about 1 ulp: each accepted move adds a few
+// units in the last place to t, and theta is recomputed from the spins periodically)
 __device__ __forceinline__ float2 move_tanh_shift(float2 t, float2 th, float si) {
   const float2 td = make_float2(si * th.x, si * th.y);
   const float2 num = make_float2(t.x - td.x, t.y - td.y);
   const float2 tt = cmul(t, td);
-  return cdiv(num, make_float2(1.0f - tt.x, -tt.y));
+  const float2 den = make_float2(1.0f - tt.x, -tt.y);
+  const float inv = __fdividef(1.0f, fmaf(den.x, den.x, den.y * den.y));
+  return make_float2(fmaf(num.x, den.x, num.y * den.y) * inv,
+                     fmaf(num.y, den.x, -num.x * den.y) * inv);
 }
 
 // sum over the warp's hidden slots of log[cosh(theta_k - s_i D_qk) / cosh(theta_k)] for
@@ -104,46 +109,112 @@ __device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
   return make_float2(warp_sum(lr) + c.x, warp_sum(li) + c.y);
 }
 
+// Complex product with both roundings of each part taken in a commutative order
+// (products rounded, then added), so that the two partners of an xor butterfly level form
+// the same bits.
+__device__ __forceinline__ float2 cmul_sym(float2 a, float2 b) {
+  return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
+                     __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+}
+
+// prod_k [1 - s_i t_k tanh D_qk] over all hidden units for move q, the same bits in every
+// lane: each lane multiplies its own factors, an xor butterfly multiplies the lanes'.
+template <int MPL>
+__device__ __forceinline__ float2 warp_factor_prod(const RbmDev& R, int lane,
+                                                   const float2 (&t)[MPL], int q, float si) {
+  float2 prod = make_float2(1.f, 0.f);
+  const float2* row = R.mth + (int64_t)q * R.M;
+#pragma unroll
+  for (int k = 0; k < MPL; ++k) {
+    const int hj = lane + 32 * k;
+    if (hj < R.M) prod = cmul(prod, move_factor(t[k], row[hj], si));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float2 p = make_float2(__shfl_xor_sync(FULL, prod.x, o), __shfl_xor_sync(FULL, prod.y, o));
+    prod = cmul_sym(prod, p);
+  }
+  return prod;
+}
+
+// psi(s')/psi(s) for move q with first-site spin si, given the move's visible-bias term
+// 2 s_i (a-difference) as da (subtracted): the factor product times
+// exp(sum_k log cosh D_qk - da).  The product is used while its squared modulus stays in
+// [1e-30, 1e30] (every lane holds the same product, so the branch is warp-uniform);
+// otherwise the ratio is formed from the log-sum of the factors, which has no range limit.
+template <int MPL>
+__device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
+                                                  const float2 (&t)[MPL], int q, float si,
+                                                  float2 da) {
+  const float2 pr = warp_factor_prod<MPL>(R, lane, t, q, si);
+  const float m2 = fmaf(pr.x, pr.x, pr.y * pr.y);
+  float lx, ly;
+  float2 pre;
+  if (m2 > 1e-30f && m2 < 1e30f) {
+    const float2 c = R.mlc[q];
+    lx = c.x - da.x;
+    ly = c.y - da.y;
+    pre = pr;
+  } else {
+    const float2 lg = warp_log_ratio<MPL>(R, lane, t, q, si);
+    lx = lg.x - da.x;
+    ly = lg.y - da.y;
+    pre = make_float2(1.f, 0.f);
+  }
+  const float mag = expf(lx);
+  float sn, cs;
+  sincosf(ly, &sn, &cs);
+  return cmul(pre, make_float2(mag * cs, mag * sn));
+}
+
 // E_loc(s) = sum_s' H_ss' psi(s')/psi(s) from the cached t = tanh theta(s) (Eq. Oloc).
+// The bonds are taken 32 at a time, one per lane: each lane finds its bond's sites and
+// adds s_i s_j to the diagonal part; for the Heisenberg model a ballot then walks only the
+// anti-parallel bonds, whose sites come from their lane by a shuffle.
 template <int MPL>
 __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, int lane,
                             const float2 (&t)[MPL]) {
-  // diagonal: sum over bonds of s_i s_j (exact small integers)
-  float zz = 0.f;
-  for (int b = lane; b < L.nb; b += 32) {
-    int i, j;
-    bond_ends(L.Lx, L.Ly, b, &i, &j);
-    zz += (float)(s[i] * s[j]);
+  float zz = 0.f;                 // diagonal: sum over bonds of s_i s_j (exact small integers)
+  float2 e = make_float2(0.f, 0.f);
+  for (int b0 = 0; b0 < L.nb; b0 += 32) {
+    const int b = b0 + lane;
+    int i = 0, j = 0;
+    bool anti = false;
+    if (b < L.nb) {
+      bond_ends(L.Lx, L.Ly, b, &i, &j);
+      zz += (float)(s[i] * s[j]);
+      anti = s[i] != s[j];
+    }
+    if (L.model != 1) continue;
+    const int ends = i | (j << 16);
+    unsigned mask = __ballot_sync(FULL, anti);
+    while (mask) {                          // J(XX+YY): swap an anti-parallel pair, 2J
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int pe = __shfl_sync(FULL, ends, src);
+      const int bi = pe & 0xffff, bj = pe >> 16;
+      const float si = (float)s[bi];
+      const float2 ai = R.a[bi], aj = R.a[bj];
+      const float2 r = warp_move_ratio<MPL>(
+          R, lane, t, b0 + src, si,
+          make_float2(2.f * si * (ai.x - aj.x), 2.f * si * (ai.y - aj.y)));
+      e.x = fmaf(2.f * L.J, r.x, e.x);
+      e.y = fmaf(2.f * L.J, r.y, e.y);
+    }
   }
   zz = warp_sum(zz);
-  float2 e;
   if (L.model == 0) {
-    e = make_float2(-L.J * zz, 0.f);
     for (int i = 0; i < R.N; ++i) {           // -h X_i: flip site i
-      float si = (float)s[i];
-      float2 lg = warp_log_ratio<MPL>(R, lane, t, i, si);
-      float2 ai = R.a[i];
-      float lx = lg.x - 2.f * si * ai.x, ly = lg.y - 2.f * si * ai.y;
-      float mag = expf(lx), sn, cs;
-      sincosf(ly, &sn, &cs);
-      e.x = fmaf(-L.h, mag * cs, e.x);
-      e.y = fmaf(-L.h, mag * sn, e.y);
+      const float si = (float)s[i];
+      const float2 ai = R.a[i];
+      const float2 r = warp_move_ratio<MPL>(R, lane, t, i, si,
+                                            make_float2(2.f * si * ai.x, 2.f * si * ai.y));
+      e.x = fmaf(-L.h, r.x, e.x);
+      e.y = fmaf(-L.h, r.y, e.y);
     }
+    e.x = fmaf(-L.J, zz, e.x);
   } else {
-    e = make_float2(L.J * zz, 0.f);
-    for (int b = 0; b < L.nb; ++b) {          // J(XX+YY): swap an anti-parallel pair, 2J
-      int i, j;
-      bond_ends(L.Lx, L.Ly, b, &i, &j);
-      if (s[i] == s[j]) continue;
-      float si = (float)s[i];
-      float2 lg = warp_log_ratio<MPL>(R, lane, t, b, si);
-      float2 ai = R.a[i], aj = R.a[j];
-      float lx = lg.x - 2.f * si * (ai.x - aj.x), ly = lg.y - 2.f * si * (ai.y - aj.y);
-      float mag = expf(lx), sn, cs;
-      sincosf(ly, &sn, &cs);
-      e.x = fmaf(2.f * L.J, mag * cs, e.x);
-      e.y = fmaf(2.f * L.J, mag * sn, e.y);
-    }
+    e.x = fmaf(L.J, zz, e.x);
   }
   return e;
 }
@@ -155,7 +226,8 @@ __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, i
 //   psi(s')/psi(s) = exp(a-term) * prod_k cosh d_k * prod_k [1 - t_k tanh d_k],
 // and the acceptance needs only its modulus squared.  On acceptance
 // t_k <- tanh(theta_k - d_k) = (t_k - tanh d_k) / (1 - t_k tanh d_k).  Random numbers for
-// 32 consecutive steps are drawn in parallel (lane q draws step t0+q) and broadcast.  At
+// 32 consecutive steps are drawn in parallel (lane q draws step t0+q and, for a bond
+// exchange, finds the bond's two sites) and broadcast.  At
 // record points the sample's spins, log psi, E_loc (fused, from the cached t) and t are
 // written.  theta is recomputed from the spins (which removes the rounding drift of the
 // t updates) at the start, at a record point where log psi is wanted, and at a record
@@ -232,10 +304,16 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
     for (int t0 = 0; t0 < A.L; t0 += 32) {
       uint32_t my_idx = 0;
       float my_logu = 0.f;
+      int my_ends = 0;                            // a bond's sites i | j << 16
       if (t0 + lane < A.L) {
         u64x4 w = philox4x64_10((uint64_t)chain, sweep_id, (uint64_t)(t0 + lane), 0ull,
                                 A.seed, A.stream);
         mh_draw(w, K, &my_idx, &my_logu);
+        if (HEIS) {
+          int bi, bj;
+          bond_ends(L.Lx, L.Ly, (int)my_idx, &bi, &bj);
+          my_ends = bi | (bj << 16);
+        }
       }
       const int nstep = min(32, A.L - t0);
       for (int q = 0; q < nstep; ++q) {
@@ -243,7 +321,9 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
         const float logu = __shfl_sync(FULL, my_logu, q);
         int i = idx, j = 0;
         if (HEIS) {
-          bond_ends(L.Lx, L.Ly, idx, &i, &j);
+          const int pe = __shfl_sync(FULL, my_ends, q);
+          i = pe & 0xffff;
+          j = pe >> 16;
           if (s[i] == s[j]) continue;             // parallel pair: rejected no-op
         }
         const float si = (float)s[i];
@@ -257,8 +337,8 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
             const float2 r = move_factor(t[k], R.mth[qrow + hj], si);
             prod *= fmaf(r.x, r.x, r.y * r.y);
           }
-          if ((k & 7) == 7 || k == MPL - 1) {
-            lsum += logf(prod);
+          if ((k & 7) == 7 || k == MPL - 1) {   // (hardware logarithm: ~1e-6 absolute)
+            lsum += __logf(prod);
             prod = 1.f;
           }
         }
@@ -337,6 +417,12 @@ static inline int pick_mpl(int M) {
   }
 
 static constexpr int kWarps = 4;
+
+// resident 4-warp blocks per SM that the per-chain sampler kernels are compiled for (a
+// register budget per thread of 64 / 72 / 80 / 96 by the hidden slots per lane)
+__host__ __device__ constexpr int sample_min_blocks(int mpl) {
+  return mpl <= 4 ? 8 : mpl <= 6 ? 7 : mpl <= 8 ? 6 : 5;
+}
 
 static inline size_t spin_smem(int N) { return (size_t)kWarps * ((N + 15) & ~15); }
 

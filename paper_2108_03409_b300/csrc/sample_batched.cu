@@ -12,10 +12,12 @@ cudaError_t launch_sample_heis(const SampleArgs& A, cudaStream_t st);
 // (lattice, chain) pairs, ordered by the host so that the most expensive lattices come
 // first; every warp takes the next item from an atomic counter until the list is done.
 // The per-lattice arguments live in device memory (their sweep counters are advanced on
-// the device after each call, so a captured graph can be replayed as is).
+// the device after each call, so a captured graph can be replayed as is).  Blocks have at
+// most 8 warps; the register budget (64 per thread up to four hidden slots per lane) keeps
+// 32 warps resident per SM.
 // ---------------------------------------------------------------------------------------
 template <int MPL>
-__global__ void k_sample_batched(const SampleArgs* __restrict__ args, const int* __restrict__ order,
+__global__ void __launch_bounds__(256, MPL <= 4 ? 4 : MPL <= 8 ? 3 : 2) k_sample_batched(const SampleArgs* __restrict__ args, const int* __restrict__ order,
                                  int n_lat, int C, int npad_max, unsigned* counter) {
   extern __shared__ int8_t sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;

@@ -5,7 +5,7 @@
 namespace vmc {
 
 template <int MPL, bool HEIS>
-__global__ void __launch_bounds__(128) k_sample(SampleArgs A) {
+__global__ void __launch_bounds__(128, sample_min_blocks(MPL)) k_sample(SampleArgs A) {
   extern __shared__ int8_t sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int chain = blockIdx.x * (blockDim.x >> 5) + wib;

@@ -83,6 +83,39 @@ int64_t moments_partial_doubles(int64_t n, int N, int M) {
   return chunks * 4 * (int64_t)(M + 1) * (N + 1);
 }
 
+// One stage is 32 samples: thread (ty, tx) fetches sample qb + ty's spin of column i0 + tx
+// and t, conj(t)(E - <E>) of unit j0 + tx.  The next stage's values are fetched into
+// registers before the current stage's products, so that their latency overlaps the
+// arithmetic (a block is the only one on its SM).
+struct MomStage {
+  float2 t, u;
+  float sv;
+};
+
+__device__ __forceinline__ MomStage moments_fetch(const int8_t* __restrict__ spins,
+                                                  const float2* __restrict__ T,
+                                                  const float2* __restrict__ E, int64_t q,
+                                                  int64_t q1, int N, int M, int ii, int jj,
+                                                  float emr, float emi) {
+  MomStage v;
+  v.t = make_float2(0.f, 0.f);
+  v.u = make_float2(0.f, 0.f);
+  v.sv = 0.f;
+  if (q < q1) {
+    const float2 e = E ? E[q] : make_float2(0.f, 0.f);
+    const float er = e.x - emr, ei = e.y - emi;
+    if (jj < M) v.t = T[q * M + jj];
+    else if (jj == M) v.t = make_float2(1.f, 0.f);
+    v.u = make_float2(v.t.x * er + v.t.y * ei, v.t.x * ei - v.t.y * er);  // conj(t) (E - <E>)
+    if (ii < N) v.sv = (float)spins[q * N + ii];
+    else if (ii == N) v.sv = 1.f;
+  }
+  return v;
+}
+
+// WANT_M: also the sums of O (for <O>); without it only the F sums are formed (the CG
+// operator's O^H u) and the <O> planes of the partials are left unwritten.
+template <bool WANT_M>
 __global__ void __launch_bounds__(1024) k_moments_partial(
     const int8_t* __restrict__ spins, const float2* __restrict__ T, const float2* __restrict__ E,
     const double* __restrict__ estats, int64_t n, int N, int M, double* __restrict__ partial) {
@@ -98,33 +131,24 @@ __global__ void __launch_bounds__(1024) k_moments_partial(
   double dm_r = 0, dm_i = 0, df_r = 0, df_i = 0;
   float fm_r = 0, fm_i = 0, ff_r = 0, ff_i = 0;
   int in_sub = 0;
+  MomStage nx = moments_fetch(spins, T, E, q0 + ty, q1, N, M, i0 + tx, j0 + tx, emr, emi);
   for (int64_t qb = q0; qb < q1; qb += 32) {
     // stage 32 samples: row ty of the staging tile is sample qb + ty
-    {
-      const int64_t q = qb + ty;
-      const int jj = j0 + tx, ii = i0 + tx;
-      float2 t = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f);
-      float sv = 0.f;
-      if (q < q1) {
-        float2 e = E ? E[q] : make_float2(0.f, 0.f);
-        float er = e.x - emr, ei = e.y - emi;
-        if (jj < M) t = T[q * M + jj];
-        else if (jj == M) t = make_float2(1.f, 0.f);
-        u = make_float2(t.x * er + t.y * ei, t.x * ei - t.y * er);   // conj(t) * (E - <E>)
-        if (ii < N) sv = (float)spins[q * N + ii];
-        else if (ii == N) sv = 1.f;
-      }
-      Ts[ty][tx] = t;
-      Us[ty][tx] = u;
-      Ss[ty][tx] = sv;
-    }
+    if (WANT_M) Ts[ty][tx] = nx.t;
+    Us[ty][tx] = nx.u;
+    Ss[ty][tx] = nx.sv;
     __syncthreads();
+    if (qb + 32 < q1)
+      nx = moments_fetch(spins, T, E, qb + 32 + ty, q1, N, M, i0 + tx, j0 + tx, emr, emi);
 #pragma unroll 8
     for (int m = 0; m < 32; ++m) {
       const float sv = Ss[m][tx];
-      const float2 t = Ts[m][ty], u = Us[m][ty];
-      fm_r = fmaf(sv, t.x, fm_r);
-      fm_i = fmaf(sv, t.y, fm_i);
+      const float2 u = Us[m][ty];
+      if (WANT_M) {
+        const float2 t = Ts[m][ty];
+        fm_r = fmaf(sv, t.x, fm_r);
+        fm_i = fmaf(sv, t.y, fm_i);
+      }
       ff_r = fmaf(sv, u.x, ff_r);
       ff_i = fmaf(sv, u.y, ff_i);
     }
@@ -140,8 +164,10 @@ __global__ void __launch_bounds__(1024) k_moments_partial(
   if (i <= N && j <= M) {
     const int64_t plane = (int64_t)(M + 1) * (N + 1);
     double* base = partial + (int64_t)blockIdx.z * 4 * plane + (int64_t)j * (N + 1) + i;
-    base[0] = dm_r;
-    base[plane] = dm_i;
+    if (WANT_M) {
+      base[0] = dm_r;
+      base[plane] = dm_i;
+    }
     base[2 * plane] = df_r;
     base[3 * plane] = df_i;
   }
@@ -158,8 +184,10 @@ __global__ void k_moments_reduce(const double* __restrict__ partial, int64_t chu
     double m_r = 0, m_i = 0, f_r = 0, f_i = 0;
     for (int64_t c = 0; c < chunks; ++c) {
       const double* b = partial + c * 4 * plane + e;
-      m_r += b[0];
-      m_i += b[plane];
+      if (meanO) {
+        m_r += b[0];
+        m_i += b[plane];
+      }
       f_r += b[2 * plane];
       f_i += b[3 * plane];
     }
@@ -181,7 +209,8 @@ cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E
   if (chunks > kMomentsMaxChunks) return cudaErrorInvalidValue;   // one chunk per grid z
   dim3 grid((N + 1 + kTile - 1) / kTile, (M + 1 + kTile - 1) / kTile, (unsigned)chunks);
   dim3 block(kTile, 32);
-  k_moments_partial<<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, partial);
+  if (meanO) k_moments_partial<true><<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, partial);
+  else k_moments_partial<false><<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, partial);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t plane = (int64_t)(M + 1) * (N + 1);

@@ -142,10 +142,16 @@ def test_sr_limit_equals_the_shifted_solve():
 
 def test_adaptive_heun_step_exact_matches_oracle_and_conserves_energy():
     """vmc_tdvp_step with exact sums against the oracle's adaptive Heun step from the same
-    parameters (first step: same accepted size to 1e-6, same parameters to the FP32 input
+    parameters (first step: same accepted size to 1e-5, same parameters to the FP32 input
     bound), then 15 real-time steps whose exact energy stays within 1e-4 of the start (the
     oracle's own integrator drifts by 2e-5 over these steps at this tolerance, and by
-    8.6e-4 at eps_step = 1e-5: the drift is the integration error)."""
+    8.6e-4 at eps_step = 1e-5: the drift is the integration error).  The accepted size is
+    tau (eps/delta)^(1/3) after the retries, and delta, the Fisher-norm distance of one full
+    and two half Heun steps, is a difference of two integrations of a right-hand side
+    formed from FP32 log-derivatives and local energies: two FP32 evaluations of the same
+    local energies that both agree with FP64 to 2e-7 (a log-sum and a product of the
+    factors) move the accepted size by 1.8e-6 on this case.  A wrong order or norm in the
+    step-size rule changes it by far more than 1e-5."""
     N, M, J, h, eps, step_eps = 6, 6, 1.0, 0.8, 1e-4, 1e-7
     P = N + M + N * M
     p = inputs.rbm_params(N, M, 0.3, seed=11)
@@ -163,7 +169,7 @@ def test_adaptive_heun_step_exact_matches_oracle_and_conserves_energy():
     norm = lambda v, info: tdvp.fisher_norm(v, info["S"])
     yo, to, tauo, used, delta, retries = tdvp.adaptive_heun_step(f, p, 0.0, 0.01, step_eps, norm)
     assert st1.rhs_evals == 1 + 4 * (st1.retries + 1) and retries == st1.retries
-    assert abs(st1.tau_used - used) <= 1e-6 * used and abs(t1 - to) <= 1e-6 * to
+    assert abs(st1.tau_used - used) <= 1e-5 * used and abs(t1 - to) <= 1e-5 * to
     assert np.linalg.norm(y1 - yo) <= 40 * (N + 1) * U24 / eps * np.linalg.norm(yo - p)
     e0 = E(p)
     assert abs(E(y) - e0) <= 1e-4 * abs(e0), (E(y), e0)
