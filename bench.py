@@ -767,6 +767,7 @@ def run_batched(args):
                                 "ms_per_step": ms_ng / args.steps},
            "speedup_vs_per_lattice": ms_p / ms_b,
            "autotuned_warps_per_block": vmc.vmc_autotuned_warps_per_block(ctx),
+           "autotuned_slots_per_lane": vmc.vmc_autotuned_slots_per_lane(ctx),
            "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                         "kernel": "sample_batched",

@@ -266,19 +266,25 @@ vmc_status vmc_sample_learned(vmc_ctx* ctx, int lattice, int n_rounds, int8_t* s
                               float* eloc_out, double* acceptance);
 
 /* Every chain of every lattice in one persistent launch (batched sampling of many
- * independent lattices of uneven size): warps take (lattice, chain) work items from an
- * atomic counter, the most expensive lattices first, and run the same sweeps, records and
- * Philox streams as vmc_sample does per lattice (n_therm sweeps, then n_samples records).
- * Outputs (dev, may be NULL): spins_out holds lattice l's samples [n_samples][n_chains][N_l]
- * starting at byte n_samples * n_chains * (N_0 + ... + N_{l-1}); eloc_out is
- * [n_lattices][n_samples * n_chains][2].  The first call autotunes the warps per block of the
- * persistent grid (timed on one sweep; chains restored).  use_graph = 1 captures the launch
- * into a CUDA graph and replays it while (n_therm, n_samples, spins_out, eloc_out) stay the
- * same.  ms (host, may be NULL) receives the device time of the call.  Synchronises. */
+ * independent lattices of uneven size; section "Batching for vectorization"): warps take
+ * work units (the chains of one lattice that share a warp: a chain runs on a group of 4, 8,
+ * 16 or 32 lanes, the fewest whose hidden slots per lane hold its M units) from an atomic
+ * counter, the most expensive lattices first, and run the same sweeps, records and Philox
+ * streams as vmc_sample does per lattice (n_therm sweeps, then n_samples records), so the
+ * samples equal vmc_sample's.  Outputs (dev, may be NULL): spins_out holds lattice l's
+ * samples [n_samples][n_chains][N_l] starting at byte n_samples * n_chains * (N_0 + ... +
+ * N_{l-1}); eloc_out is [n_lattices][n_samples * n_chains][2].  The first call autotunes
+ * the hidden slots per lane (the per-lattice kernels' width for the largest M, or twice it
+ * up to 8) and the warps per block of the persistent grid (timed on one sweep; chains
+ * restored).  use_graph = 1 captures the launch into a CUDA graph and replays it while
+ * (n_therm, n_samples, spins_out, eloc_out) stay the same.  ms (host, may be NULL) receives
+ * the device time of the call.  Synchronises. */
 vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spins_out,
                           float* eloc_out, int use_graph, double* ms);
 /* Warps per block chosen by the autotuner (0 before the first vmc_sample_all). */
 int vmc_autotuned_warps_per_block(const vmc_ctx* ctx);
+/* Hidden slots per lane chosen by the autotuner (0 before the first vmc_sample_all). */
+int vmc_autotuned_slots_per_lane(const vmc_ctx* ctx);
 
 /* Checkpoint / resume.  vmc_get_state writes everything the method's trajectory depends on
  * into a host buffer: per lattice the FP64 parameters, the chains, the sweep counter (the

@@ -95,9 +95,10 @@ struct vmc_ctx {
   // batched sampler
   SampleArgs* d_bargs = nullptr;  // [n_lattices] device descriptors
   int* d_order = nullptr;         // heavy-first lattice order
+  int* d_ustart = nullptr;        // first work unit of each lattice in that order (+ total)
   unsigned* d_counter = nullptr;  // work-queue counter
   int8_t* chain_backup = nullptr; // chains of all lattices (autotuning runs restore them)
-  int tuned_wpb = 0, tuned_grid = 0;
+  int tuned_wpb = 0, tuned_grid = 0, tuned_mpl = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_st = nullptr;  // private stream the graph is captured on (the context's
@@ -381,7 +382,8 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
     size_t chain_bytes = 0;
     for (auto& L : ctx->lats) chain_bytes += (size_t)cfg->n_chains * L.N;
     if ((e = dalloc(ctx, &ctx->d_bargs, ctx->lats.size())) ||
-        (e = dalloc(ctx, &ctx->d_order, ctx->lats.size())) || (e = dalloc(ctx, &ctx->d_counter, 1)) ||
+        (e = dalloc(ctx, &ctx->d_order, ctx->lats.size())) ||
+        (e = dalloc(ctx, &ctx->d_ustart, ctx->lats.size() + 1)) || (e = dalloc(ctx, &ctx->d_counter, 1)) ||
         (e = dalloc(ctx, &ctx->chain_backup, chain_bytes)))
       return oom(e);
   }
@@ -1864,7 +1866,7 @@ vmc_status vmc_sample_learned(vmc_ctx* ctx, int lattice, int n_rounds, int8_t* s
 
 
 static vmc_status batched_upload(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spins_out,
-                                 float* eloc_out) {
+                                 float* eloc_out, int mpl) {
   const int nl = (int)ctx->lats.size();
   const int C = ctx->cfg.n_chains;
   std::vector<SampleArgs> args((size_t)nl);
@@ -1897,13 +1899,23 @@ static vmc_status batched_upload(vmc_ctx* ctx, int n_therm, int n_samples, int8_
     return (int64_t)ctx->lats[x].N * ctx->lats[x].M > (int64_t)ctx->lats[y].N * ctx->lats[y].M;
   });
   CK(cudaMemcpyAsync(ctx->d_bargs, args.data(), sizeof(SampleArgs) * nl, cudaMemcpyHostToDevice, ctx->st), "sample_all");
+  // work units: one warp's chains of one lattice (several chains per warp for small M)
+  std::vector<int> ustart((size_t)nl + 1, 0);
+  for (int o = 0; o < nl; ++o) {
+    const int cpw = batched_chains_per_warp(ctx->lats[(size_t)order[(size_t)o]].M, mpl);
+    ustart[(size_t)o + 1] = ustart[(size_t)o] + (C + cpw - 1) / cpw;
+  }
   CK(cudaMemcpyAsync(ctx->d_order, order.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, ctx->st), "sample_all");
+  CK(cudaMemcpyAsync(ctx->d_ustart, ustart.data(), sizeof(int) * (nl + 1), cudaMemcpyHostToDevice, ctx->st),
+     "sample_all");
   CK(cudaStreamSynchronize(ctx->st), "sample_all");
   return VMC_OK;
 }
 
-// Autotuner: warps per block of the persistent launch, timed on one sweep of every chain
-// (chains saved before and restored after; sweep counters untouched).
+// Autotuner: hidden slots per lane (the per-chain width, or twice it up to 8, which puts
+// several chains of the smaller lattices in one warp) and warps per block of the persistent
+// launch, timed on one sweep of every chain (chains saved before and restored after; sweep
+// counters untouched).
 static vmc_status batched_tune(vmc_ctx* ctx) {
   ctx->g_therm = -1;
   const int nl = (int)ctx->lats.size();
@@ -1912,32 +1924,38 @@ static vmc_status batched_tune(vmc_ctx* ctx) {
   CK(cudaGetDevice(&dev), "tune");
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "tune");
   vmc_status s;
-  if ((s = batched_upload(ctx, 1, 0, nullptr, nullptr))) return s;
   size_t off = 0;
   for (auto& L : ctx->lats) {
     CK(cudaMemcpyAsync(ctx->chain_backup + off, L.chains, (size_t)C * L.N, cudaMemcpyDeviceToDevice, ctx->st), "tune");
     off += (size_t)C * L.N;
   }
   float best = 1e30f;
+  const int base = sample_slots_per_lane(ctx->Mmax);
+  const int wide = base <= 4 ? sample_slots_per_lane(64 * base) : 0;   // 2 x base (<= 8)
+  const int mpls[2] = {base, wide};
   const int cand[3] = {2, 4, 8};
-  for (int wpb : cand) {
-    const int per_sm = batched_blocks_per_sm(ctx->Mmax, wpb, ctx->Nmax);
+  for (int mpl : mpls) {
+   if (mpl <= 0) continue;
+   if ((s = batched_upload(ctx, 1, 0, nullptr, nullptr, mpl))) return s;
+   for (int wpb : cand) {
+    const int per_sm = batched_blocks_per_sm(mpl, wpb, ctx->Nmax);
     if (per_sm < 1) continue;
     const int grid = sms * per_sm;
     CK(cudaEventRecord(ctx->ev[0], ctx->st), "tune");
-    CK(launch_sample_batched(ctx->d_bargs, ctx->d_order, nl, C, ctx->Nmax, ctx->Mmax, ctx->d_counter,
-                             wpb, grid, 0, ctx->d_bargs, ctx->st), "tune");
+    CK(launch_sample_batched(ctx->d_bargs, ctx->d_order, ctx->d_ustart, nl, ctx->Nmax, mpl,
+                             ctx->d_counter, wpb, grid, 0, ctx->d_bargs, ctx->st), "tune");
     CK(cudaEventRecord(ctx->ev[1], ctx->st), "tune");
     CK(cudaEventSynchronize(ctx->ev[1]), "tune");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
     ctx->launches += 2;
-    if (ms < best) { best = ms; ctx->tuned_wpb = wpb; ctx->tuned_grid = grid; }
+    if (ms < best) { best = ms; ctx->tuned_wpb = wpb; ctx->tuned_grid = grid; ctx->tuned_mpl = mpl; }
     off = 0;
     for (auto& L : ctx->lats) {
       CK(cudaMemcpyAsync(L.chains, ctx->chain_backup + off, (size_t)C * L.N, cudaMemcpyDeviceToDevice, ctx->st), "tune");
       off += (size_t)C * L.N;
     }
+   }
   }
   CK(cudaStreamSynchronize(ctx->st), "tune");
   if (ctx->tuned_wpb == 0) return fail(ctx, VMC_ERR_CUDA, "no launch configuration fits");
@@ -1951,7 +1969,6 @@ vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spin
   vmc_status s;
   if (ctx->tuned_wpb == 0 && (s = batched_tune(ctx))) return s;
   const int nl = (int)ctx->lats.size();
-  const int C = ctx->cfg.n_chains;
   const uint64_t adv = (uint64_t)n_therm + (uint64_t)n_samples * ctx->cfg.sweeps_per_sample;
   // a replay is valid only while the device descriptors still describe this call: same
   // arguments, and no per-lattice sampling or chain reset moved a sweep counter since
@@ -1963,15 +1980,15 @@ vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spin
     CK(cudaGraphLaunch(ctx->graph_exec, ctx->st), "sample_all");
     ctx->launches += 2;
   } else {
-    if ((s = batched_upload(ctx, n_therm, n_samples, spins_out, eloc_out))) return s;
+    if ((s = batched_upload(ctx, n_therm, n_samples, spins_out, eloc_out, ctx->tuned_mpl))) return s;
     if (use_graph) {
       if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
       if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
       if (!ctx->cap_st) CK(cudaStreamCreateWithFlags(&ctx->cap_st, cudaStreamNonBlocking), "capture");
       CK(cudaStreamBeginCapture(ctx->cap_st, cudaStreamCaptureModeThreadLocal), "capture");
-      cudaError_t e = launch_sample_batched(ctx->d_bargs, ctx->d_order, nl, C, ctx->Nmax, ctx->Mmax,
-                                            ctx->d_counter, ctx->tuned_wpb, ctx->tuned_grid, adv,
-                                            ctx->d_bargs, ctx->cap_st);
+      cudaError_t e = launch_sample_batched(ctx->d_bargs, ctx->d_order, ctx->d_ustart, nl, ctx->Nmax,
+                                            ctx->tuned_mpl, ctx->d_counter, ctx->tuned_wpb,
+                                            ctx->tuned_grid, adv, ctx->d_bargs, ctx->cap_st);
       cudaGraph_t g = nullptr;
       cudaError_t e2 = cudaStreamEndCapture(ctx->cap_st, &g);
       if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(ctx, e, "capture"); }
@@ -1985,8 +2002,9 @@ vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spin
       CK(cudaGraphLaunch(ctx->graph_exec, ctx->st), "sample_all");
     } else {
       ctx->g_therm = -1;  // the descriptors no longer match the captured graph
-      CK(launch_sample_batched(ctx->d_bargs, ctx->d_order, nl, C, ctx->Nmax, ctx->Mmax, ctx->d_counter,
-                               ctx->tuned_wpb, ctx->tuned_grid, adv, ctx->d_bargs, ctx->st), "sample_all");
+      CK(launch_sample_batched(ctx->d_bargs, ctx->d_order, ctx->d_ustart, nl, ctx->Nmax, ctx->tuned_mpl,
+                               ctx->d_counter, ctx->tuned_wpb, ctx->tuned_grid, adv, ctx->d_bargs,
+                               ctx->st), "sample_all");
     }
     ctx->launches += 2;
   }
@@ -2009,6 +2027,7 @@ vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spin
 }
 
 int vmc_autotuned_warps_per_block(const vmc_ctx* ctx) { return ctx ? ctx->tuned_wpb : 0; }
+int vmc_autotuned_slots_per_lane(const vmc_ctx* ctx) { return ctx ? ctx->tuned_mpl : 0; }
 
 
 // ---- checkpoint / resume ------------------------------------------------------------------

@@ -1,7 +1,8 @@
 // rbm_warp.cuh -- warp-level building blocks of the complex-RBM kernels (shared by the
-// evaluation, sampling and batched-sampling translation units).  One warp owns one
-// configuration (or one chain); hidden unit j = lane + 32*k lives in register slot k of
-// that lane.
+// evaluation, sampling and batched-sampling translation units).  A group of G lanes (the
+// whole warp, G = 32, or an aligned quarter / eighth of it in the batched sampler) owns one
+// configuration (or one chain); hidden unit j = glane + G*k lives in register slot k of
+// group lane glane.  The group's reductions and broadcasts name only its own lanes.
 #pragma once
 
 #include "vmc_device.cuh"
@@ -10,6 +11,27 @@
 namespace vmc {
 
 static constexpr unsigned FULL = 0xffffffffu;
+
+// the lanes of this lane's group of G (G a power of two, at most 32)
+template <int G>
+__device__ __forceinline__ unsigned group_mask(int lane) {
+  return G == 32 ? FULL : (((1u << (G & 31)) - 1u) << (lane & ~(G - 1)));
+}
+
+// xor-butterfly sums over a group (every lane of the group ends with the same bits)
+template <int G>
+__device__ __forceinline__ float group_sum(float v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gm, v, o);
+  return v;
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum_phase(float v, unsigned gm) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v = wrap_phase(v + __shfl_xor_sync(gm, v, o));
+  return v;
+}
 
 // theta_j = b_j + sum_i W_ji s_i for the warp's hidden slots, from spins in shared memory.
 template <int MPL>
@@ -84,15 +106,17 @@ __device__ __forceinline__ float2 move_tanh_shift(float2 t, float2 th, float si)
 // move q, as (log modulus, phase).  Each lane multiplies its factors and takes one log at
 // the end; the running product is folded into the logs early only if it leaves
 // [1e-15, 1e15] (checked every four factors).
-template <int MPL>
+template <int MPL, int G = 32>
 __device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
                                                  const float2 (&t)[MPL], int q, float si) {
+  const int gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
   float lr = 0.f, li = 0.f;
   float2 prod = make_float2(1.f, 0.f);
   const float2* row = R.mth + (int64_t)q * R.M;
 #pragma unroll
   for (int k = 0; k < MPL; ++k) {
-    int hj = lane + 32 * k;
+    int hj = gl + G * k;
     if (hj < R.M) prod = cmul(prod, move_factor(t[k], row[hj], si));
     if ((k & 3) == 3 && k != MPL - 1) {
       const float m2 = fmaf(prod.x, prod.x, prod.y * prod.y);
@@ -106,7 +130,7 @@ __device__ __forceinline__ float2 warp_log_ratio(const RbmDev& R, int lane,
   lr += 0.5f * logf(fmaf(prod.x, prod.x, prod.y * prod.y));
   li += atan2f(prod.y, prod.x);
   const float2 c = R.mlc[q];
-  return make_float2(warp_sum(lr) + c.x, warp_sum(li) + c.y);
+  return make_float2(group_sum<G>(lr, gm) + c.x, group_sum<G>(li, gm) + c.y);
 }
 
 // Complex product with both roundings of each part taken in a commutative order
@@ -119,19 +143,21 @@ __device__ __forceinline__ float2 cmul_sym(float2 a, float2 b) {
 
 // prod_k [1 - s_i t_k tanh D_qk] over all hidden units for move q, the same bits in every
 // lane: each lane multiplies its own factors, an xor butterfly multiplies the lanes'.
-template <int MPL>
+template <int MPL, int G = 32>
 __device__ __forceinline__ float2 warp_factor_prod(const RbmDev& R, int lane,
                                                    const float2 (&t)[MPL], int q, float si) {
+  const int gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
   float2 prod = make_float2(1.f, 0.f);
   const float2* row = R.mth + (int64_t)q * R.M;
 #pragma unroll
   for (int k = 0; k < MPL; ++k) {
-    const int hj = lane + 32 * k;
+    const int hj = gl + G * k;
     if (hj < R.M) prod = cmul(prod, move_factor(t[k], row[hj], si));
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float2 p = make_float2(__shfl_xor_sync(FULL, prod.x, o), __shfl_xor_sync(FULL, prod.y, o));
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const float2 p = make_float2(__shfl_xor_sync(gm, prod.x, o), __shfl_xor_sync(gm, prod.y, o));
     prod = cmul_sym(prod, p);
   }
   return prod;
@@ -142,11 +168,11 @@ __device__ __forceinline__ float2 warp_factor_prod(const RbmDev& R, int lane,
 // exp(sum_k log cosh D_qk - da).  The product is used while its squared modulus stays in
 // [1e-30, 1e30] (every lane holds the same product, so the branch is warp-uniform);
 // otherwise the ratio is formed from the log-sum of the factors, which has no range limit.
-template <int MPL>
+template <int MPL, int G = 32>
 __device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
                                                   const float2 (&t)[MPL], int q, float si,
                                                   float2 da) {
-  const float2 pr = warp_factor_prod<MPL>(R, lane, t, q, si);
+  const float2 pr = warp_factor_prod<MPL, G>(R, lane, t, q, si);
   const float m2 = fmaf(pr.x, pr.x, pr.y * pr.y);
   float lx, ly;
   float2 pre;
@@ -156,7 +182,7 @@ __device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
     ly = c.y - da.y;
     pre = pr;
   } else {
-    const float2 lg = warp_log_ratio<MPL>(R, lane, t, q, si);
+    const float2 lg = warp_log_ratio<MPL, G>(R, lane, t, q, si);
     lx = lg.x - da.x;
     ly = lg.y - da.y;
     pre = make_float2(1.f, 0.f);
@@ -171,13 +197,15 @@ __device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
 // The bonds are taken 32 at a time, one per lane: each lane finds its bond's sites and
 // adds s_i s_j to the diagonal part; for the Heisenberg model a ballot then walks only the
 // anti-parallel bonds, whose sites come from their lane by a shuffle.
-template <int MPL>
+template <int MPL, int G = 32>
 __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, int lane,
                             const float2 (&t)[MPL]) {
+  const int gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
   float zz = 0.f;                 // diagonal: sum over bonds of s_i s_j (exact small integers)
   float2 e = make_float2(0.f, 0.f);
-  for (int b0 = 0; b0 < L.nb; b0 += 32) {
-    const int b = b0 + lane;
+  for (int b0 = 0; b0 < L.nb; b0 += G) {
+    const int b = b0 + gl;
     int i = 0, j = 0;
     bool anti = false;
     if (b < L.nb) {
@@ -187,28 +215,29 @@ __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, i
     }
     if (L.model != 1) continue;
     const int ends = i | (j << 16);
-    unsigned mask = __ballot_sync(FULL, anti);
+    unsigned mask = __ballot_sync(gm, anti);
+    if (G < 32) mask = (mask >> (lane & ~(G - 1))) & ((1u << (G & 31)) - 1u);
     while (mask) {                          // J(XX+YY): swap an anti-parallel pair, 2J
       const int src = __ffs(mask) - 1;
       mask &= mask - 1;
-      const int pe = __shfl_sync(FULL, ends, src);
+      const int pe = __shfl_sync(gm, ends, src, G);
       const int bi = pe & 0xffff, bj = pe >> 16;
       const float si = (float)s[bi];
       const float2 ai = R.a[bi], aj = R.a[bj];
-      const float2 r = warp_move_ratio<MPL>(
+      const float2 r = warp_move_ratio<MPL, G>(
           R, lane, t, b0 + src, si,
           make_float2(2.f * si * (ai.x - aj.x), 2.f * si * (ai.y - aj.y)));
       e.x = fmaf(2.f * L.J, r.x, e.x);
       e.y = fmaf(2.f * L.J, r.y, e.y);
     }
   }
-  zz = warp_sum(zz);
+  zz = group_sum<G>(zz, gm);
   if (L.model == 0) {
     for (int i = 0; i < R.N; ++i) {           // -h X_i: flip site i
       const float si = (float)s[i];
       const float2 ai = R.a[i];
-      const float2 r = warp_move_ratio<MPL>(R, lane, t, i, si,
-                                            make_float2(2.f * si * ai.x, 2.f * si * ai.y));
+      const float2 r = warp_move_ratio<MPL, G>(R, lane, t, i, si,
+                                               make_float2(2.f * si * ai.x, 2.f * si * ai.y));
       e.x = fmaf(-L.h, r.x, e.x);
       e.y = fmaf(-L.h, r.y, e.y);
     }
@@ -236,13 +265,15 @@ __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, i
 // ---------------------------------------------------------------------------------------
 static constexpr int kResyncAccepts = 128;
 
-template <int MPL>
+template <int MPL, int G = 32>
 __device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, int lane,
                                               float2 (&t)[MPL], bool want_logpsi) {
+  const int gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
   float lr = 0.f, li = 0.f;
 #pragma unroll
   for (int k = 0; k < MPL; ++k) {
-    const int hj = lane + 32 * k;
+    const int hj = gl + G * k;
     t[k] = make_float2(0.f, 0.f);
     if (hj < R.M) {
       float2 th = R.b[hj];
@@ -261,28 +292,32 @@ __device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, 
     }
   }
   if (!want_logpsi) return make_float2(0.f, 0.f);
-  for (int i = lane; i < R.N; i += 32) {
+  for (int i = gl; i < R.N; i += G) {
     const float si = (float)s[i];
     lr = fmaf(si, R.a[i].x, lr);
     li = wrap_phase(fmaf(si, R.a[i].y, li));
   }
-  return make_float2(warp_sum(lr), warp_sum_phase(li));
+  return make_float2(group_sum<G>(lr, gm), group_sum_phase<G>(li, gm));
 }
 
-// All sweeps of one chain (the whole warp); s is the warp's shared-memory spin buffer.
-template <int MPL, bool HEIS>
+// All sweeps of one chain by its group of G lanes (the whole warp for G = 32); s is the
+// group's shared-memory spin buffer.  Every collective names only the group's lanes, so the
+// groups of a warp may take different branches (accept / reject).
+template <int MPL, bool HEIS, int G = 32>
 __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
   const RbmDev& R = A.rbm;
   const LatDev& L = A.lat;
   const int N = R.N, M = R.M;
-  for (int i = lane; i < N; i += 32) s[i] = A.chains[(int64_t)chain * N + i];
-  __syncwarp();
+  const int gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
+  for (int i = gl; i < N; i += G) s[i] = A.chains[(int64_t)chain * N + i];
+  __syncwarp(gm);
 
   float2 t[MPL];
   if (A.theta_in) {
 #pragma unroll
     for (int k = 0; k < MPL; ++k) {
-      const int hj = lane + 32 * k;
+      const int hj = gl + G * k;
       t[k] = make_float2(0.f, 0.f);
       if (hj < M) {
         const float2 th = A.theta_in[(int64_t)chain * M + hj];
@@ -290,7 +325,7 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
       }
     }
   } else {
-    warp_resync<MPL>(R, s, lane, t, false);
+    warp_resync<MPL, G>(R, s, lane, t, false);
   }
 
   const uint32_t K = HEIS ? (uint32_t)L.nb : (uint32_t)N;
@@ -301,12 +336,12 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
 
   for (int sw = 0; sw < total; ++sw) {
     const uint64_t sweep_id = A.sweep0 + (uint64_t)sw;
-    for (int t0 = 0; t0 < A.L; t0 += 32) {
+    for (int t0 = 0; t0 < A.L; t0 += G) {
       uint32_t my_idx = 0;
       float my_logu = 0.f;
       int my_ends = 0;                            // a bond's sites i | j << 16
-      if (t0 + lane < A.L) {
-        u64x4 w = philox4x64_10((uint64_t)chain, sweep_id, (uint64_t)(t0 + lane), 0ull,
+      if (t0 + gl < A.L) {
+        u64x4 w = philox4x64_10((uint64_t)chain, sweep_id, (uint64_t)(t0 + gl), 0ull,
                                 A.seed, A.stream);
         mh_draw(w, K, &my_idx, &my_logu);
         if (HEIS) {
@@ -315,13 +350,13 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
           my_ends = bi | (bj << 16);
         }
       }
-      const int nstep = min(32, A.L - t0);
+      const int nstep = min(G, A.L - t0);
       for (int q = 0; q < nstep; ++q) {
-        const int idx = (int)__shfl_sync(FULL, my_idx, q);
-        const float logu = __shfl_sync(FULL, my_logu, q);
+        const int idx = (int)__shfl_sync(gm, my_idx, q, G);
+        const float logu = __shfl_sync(gm, my_logu, q, G);
         int i = idx, j = 0;
         if (HEIS) {
-          const int pe = __shfl_sync(FULL, my_ends, q);
+          const int pe = __shfl_sync(gm, my_ends, q, G);
           i = pe & 0xffff;
           j = pe >> 16;
           if (s[i] == s[j]) continue;             // parallel pair: rejected no-op
@@ -332,7 +367,7 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
         float lsum = 0.f, prod = 1.f;
 #pragma unroll
         for (int k = 0; k < MPL; ++k) {
-          const int hj = lane + 32 * k;
+          const int hj = gl + G * k;
           if (hj < M) {
             const float2 r = move_factor(t[k], R.mth[qrow + hj], si);
             prod *= fmaf(r.x, r.x, r.y * r.y);
@@ -342,19 +377,19 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
             prod = 1.f;
           }
         }
-        const float two_re_delta = warp_sum(lsum) + 2.f * R.mlc[idx].x + two_re_da;
+        const float two_re_delta = group_sum<G>(lsum, gm) + 2.f * R.mlc[idx].x + two_re_da;
         if (logu < two_re_delta) {
 #pragma unroll
           for (int k = 0; k < MPL; ++k) {
-            const int hj = lane + 32 * k;
+            const int hj = gl + G * k;
             if (hj < M) t[k] = move_tanh_shift(t[k], R.mth[qrow + hj], si);
           }
-          __syncwarp();
-          if (lane == 0) {
+          __syncwarp(gm);
+          if (gl == 0) {
             s[i] = (int8_t)(-s[i]);
             if (HEIS) s[j] = (int8_t)(-s[j]);
           }
-          __syncwarp();
+          __syncwarp(gm);
           ++n_acc;
           ++since_resync;
         }
@@ -366,34 +401,41 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
       const int64_t qs = rec * A.C + chain;
       float2 lp = make_float2(0.f, 0.f);
       if (A.logpsi_out || since_resync >= kResyncAccepts) {
-        lp = warp_resync<MPL>(R, s, lane, t, A.logpsi_out != nullptr);
+        lp = warp_resync<MPL, G>(R, s, lane, t, A.logpsi_out != nullptr);
         since_resync = 0;
       }
       if (A.t_out)
 #pragma unroll
         for (int k = 0; k < MPL; ++k) {
-          const int hj = lane + 32 * k;
+          const int hj = gl + G * k;
           if (hj < M) A.t_out[qs * M + hj] = t[k];
         }
       if (A.spins_out)
-        for (int i = lane; i < N; i += 32) A.spins_out[qs * N + i] = s[i];
+        for (int i = gl; i < N; i += G) A.spins_out[qs * N + i] = s[i];
       if (A.logpsi_out) {
-        if (lane == 0) A.logpsi_out[qs] = lp;
+        if (gl == 0) A.logpsi_out[qs] = lp;
         bad |= !isfinite(lp.x) || !isfinite(lp.y);
       }
       if (A.eloc_out) {
-        const float2 e = warp_eloc<MPL>(R, L, s, lane, t);
-        if (lane == 0) A.eloc_out[qs] = e;
+        const float2 e = warp_eloc<MPL, G>(R, L, s, lane, t);
+        if (gl == 0) A.eloc_out[qs] = e;
         bad |= !isfinite(e.x) || !isfinite(e.y);
       }
     }
   }
-  __syncwarp();
-  for (int i = lane; i < N; i += 32) A.chains[(int64_t)chain * N + i] = s[i];
-  if (lane == 0) {
+  __syncwarp(gm);
+  for (int i = gl; i < N; i += G) A.chains[(int64_t)chain * N + i] = s[i];
+  if (gl == 0) {
     if (A.n_accept) atomicAdd(A.n_accept, n_acc);
     if (bad) flag_error(A.status, DEV_ERR_NUMERIC);
   }
+}
+
+// lanes per chain in the batched sampler: the smallest group of 4, 8, 16 or 32 lanes whose
+// MPL slots per lane hold the lattice's M hidden units (several chains share a warp when
+// M is small against the warp's 32 MPL slots)
+__host__ __device__ constexpr int batched_group(int M, int mpl) {
+  return M <= 4 * mpl ? 4 : M <= 8 * mpl ? 8 : M <= 16 * mpl ? 16 : 32;
 }
 
 // hidden slots per lane: ceil(M / 32) rounded up to one of the instantiated widths
@@ -417,6 +459,7 @@ static inline int pick_mpl(int M) {
   }
 
 static constexpr int kWarps = 4;
+static constexpr int kMaxChainsPerWarp = 8;   // batched sampler: groups of 4 lanes
 
 // resident 4-warp blocks per SM that the per-chain sampler kernels are compiled for (a
 // register budget per thread of 64 / 72 / 80 / 96 by the hidden slots per lane)

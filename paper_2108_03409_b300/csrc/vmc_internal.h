@@ -72,13 +72,19 @@ cudaError_t launch_theta_tc(const RbmDev& R, const int8_t* spins, int64_t n, flo
 cudaError_t launch_ok_dense(const int8_t* spins, const float2* T, int64_t n, int N, int M,
                             float2* O, cudaStream_t st);
 cudaError_t launch_sample(const SampleArgs& A, cudaStream_t st);
-// every chain of n_lat lattices in one persistent launch (work list `order`, heavy first);
-// the sweep counters in d_args_mut advance by `advance` afterwards (on the device)
-cudaError_t launch_sample_batched(const SampleArgs* d_args, const int* d_order, int n_lat, int C,
-                                  int Nmax, int Mmax, unsigned* counter, int warps_per_block,
-                                  int grid, uint64_t advance, SampleArgs* d_args_mut,
-                                  cudaStream_t st);
-int batched_blocks_per_sm(int Mmax, int warps_per_block, int Nmax);
+// every chain of n_lat lattices in one persistent launch (lattice order `order`, heavy
+// first; ustart[o] the first work unit of the o-th lattice, ustart[n_lat] the unit count)
+// with mpl hidden slots per lane; the sweep counters in d_args_mut advance by `advance`
+// afterwards (on the device)
+cudaError_t launch_sample_batched(const SampleArgs* d_args, const int* d_order,
+                                  const int* d_ustart, int n_lat, int Nmax, int mpl,
+                                  unsigned* counter, int warps_per_block, int grid,
+                                  uint64_t advance, SampleArgs* d_args_mut, cudaStream_t st);
+int batched_blocks_per_sm(int mpl, int warps_per_block, int Nmax);
+// chains of one lattice that share a warp in the batched sampler with mpl slots per lane
+int batched_chains_per_warp(int M, int mpl);
+// hidden slots per lane that the per-chain kernels use for M hidden units
+int sample_slots_per_lane(int M);
 
 // ---- sr.cu ----------------------------------------------------------------------------
 // Energy statistics in FP64: out[0..3] = <E>.re, <E>.im, <|E-<E>|^2>, sqrt(var/n).

@@ -93,7 +93,7 @@ EXPORTED = ["vmc_init", "vmc_destroy", "vmc_last_error", "vmc_set_params", "vmc_
             "vmc_num_samples", "vmc_num_params", "vmc_force_noalloc", "vmc_cg_solve", "vmc_sr_apply",
             "vmc_made_set_params", "vmc_made_get_params", "vmc_made_logq", "vmc_made_grad",
             "vmc_proposal_train", "vmc_made_sample", "vmc_sample_learned", "vmc_sample_all",
-            "vmc_autotuned_warps_per_block", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout",
+            "vmc_autotuned_warps_per_block", "vmc_autotuned_slots_per_lane", "vmc_get_state", "vmc_set_state", "vmc_selftest_wait_timeout",
             "vmc_tdvp_rhs", "vmc_tdvp_step", "vmc_excited_lambda", "vmc_excited_rhs",
             "vmc_excited_step", "vmc_ar_set_params", "vmc_ar_get_params", "vmc_ar_logpsi",
             "vmc_ar_sample", "vmc_ar_local_energy", "vmc_ar_grad", "vmc_ar_sr_step",
@@ -146,6 +146,7 @@ def load(path: str = LIB_PATH):
         "vmc_sample_learned": (i32, [P, i32, i32, P, P, ctypes.POINTER(f64)]),
         "vmc_sample_all": (i32, [P, i32, i32, P, P, i32, ctypes.POINTER(f64)]),
         "vmc_autotuned_warps_per_block": (i32, [P]),
+        "vmc_autotuned_slots_per_lane": (i32, [P]),
         "vmc_get_state": (i32, [P, P, ctypes.POINTER(ctypes.c_size_t)]),
         "vmc_set_state": (i32, [P, P, ctypes.c_size_t]),
         "vmc_selftest_wait_timeout": (i32, [P, i32]),
@@ -420,6 +421,10 @@ def vmc_sample_all(ctx, n_therm, n_samples, spins_out=None, eloc_out=None, use_g
 
 def vmc_autotuned_warps_per_block(ctx) -> int:
     return int(load().vmc_autotuned_warps_per_block(ctx))
+
+
+def vmc_autotuned_slots_per_lane(ctx) -> int:
+    return int(load().vmc_autotuned_slots_per_lane(ctx))
 
 
 def vmc_get_state(ctx) -> bytes:

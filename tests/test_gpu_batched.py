@@ -1,6 +1,10 @@
 """Batched sampling of many independent lattices of uneven size in one persistent launch
 (vmc_sample_all): same Philox streams and sweeps as per-lattice vmc_sample, so the records
-must agree with it and with the oracle's Metropolis trajectories."""
+must agree with it and with the oracle's Metropolis trajectories.  The persistent launch may
+run a small lattice's chains on groups of 4, 8 or 16 lanes, which sums the same FP32 terms in
+another order than the per-lattice kernel's warp per chain; as between the FP32 kernels and
+the FP64 oracle, a chain may then take a near-threshold decision the other way, so chains
+agree except those whose oracle decision margin fell below 1e-4."""
 import numpy as np
 import pytest
 
@@ -75,6 +79,24 @@ def _per_lattice(ctx, n_therm, n_samples):
     return sp, el
 
 
+def _margins(ps, ss, n_sweeps):
+    """Smallest oracle decision margin per chain of each lattice over n_sweeps sweeps from
+    the initial chains (the GPU runs take the same Philox streams)."""
+    out = []
+    for l, (model, Lx, Ly, J, h, alpha) in enumerate(LATS):
+        _, _, margin, _ = oracle.metropolis(model, Lx, Ly, alpha * Lx * Ly, ps[l], ss[l],
+                                            seed=SEED, stream=l, n_sweeps=n_sweeps)
+        out.append(margin)
+    return out
+
+
+def _same_chains(got, ref, margin):
+    """Chains whose records agree; the others must have met a near-threshold decision."""
+    same = np.all(got == ref, axis=tuple(k for k in range(got.ndim) if k != got.ndim - 2))
+    assert np.all(margin[~same] < 1e-4) and same.mean() >= 0.97, np.sum(~same)
+    return same
+
+
 def _batched(ctx, n_therm, n_samples, spins, eloc, use_graph):
     vmc.vmc_sample_all(ctx, n_therm, n_samples, spins, eloc, use_graph)
     sp = _split(spins.cpu().numpy(), n_samples)
@@ -84,13 +106,16 @@ def _batched(ctx, n_therm, n_samples, spins, eloc, use_graph):
 
 def test_batched_equals_per_lattice_and_graph_replay():
     """Three batched calls (plain launch, graph capture, graph replay) against the same
-    sequence of per-lattice calls: identical spins and E_loc, identical final chains."""
+    sequence of per-lattice calls: the same spins and final chains (up to near-threshold
+    decisions, see the module note), and on the chains that agree, local energies within
+    twice the FP32 bound of each against the oracle."""
     a, b = _ctx(), _ctx()
     try:
-        _setup(a)
+        ps, ss = _setup(a)
         _setup(b)
         tot = sum(_sizes())
         calls = [(3, 2, False), (0, 2, True), (0, 2, True)]
+        margins = _margins(ps, ss, sum(nt + ns for nt, ns, _ in calls))
         bufs = {}
         for k, (nt, ns, g) in enumerate(calls):
             ref_s, ref_e = _per_lattice(a, nt, ns)
@@ -99,12 +124,17 @@ def test_batched_equals_per_lattice_and_graph_replay():
                 bufs[key] = (torch.zeros(ns * C * tot, dtype=torch.int8, device="cuda"),
                              torch.zeros((len(LATS) * ns * C, 2), dtype=torch.float32, device="cuda"))
             got_s, got_e = _batched(b, nt, ns, *bufs[key], g)
-            for l in range(len(LATS)):
-                assert np.array_equal(got_s[l], ref_s[l]), (k, l)
-                np.testing.assert_allclose(got_e[l], ref_e[l], rtol=1e-6, atol=1e-5)
+            for l, (model, Lx, Ly, J, h, alpha) in enumerate(LATS):
+                same = _same_chains(got_s[l], ref_s[l], margins[l])
+                flat = got_s[l][:, same].reshape(-1, Lx * Ly)
+                tol = eloc_tolerance(model, Lx, Ly, J, h, alpha * Lx * Ly, ps[l], flat)
+                d = np.abs(got_e[l][:, same] - ref_e[l][:, same]).reshape(-1)
+                assert np.all(d <= 2 * tol), (k, l)
         for l, N in enumerate(_sizes()):
-            assert np.array_equal(vmc.vmc_get_chains(a, l, C, N), vmc.vmc_get_chains(b, l, C, N))
+            _same_chains(vmc.vmc_get_chains(a, l, C, N), vmc.vmc_get_chains(b, l, C, N),
+                         margins[l])
         assert vmc.vmc_autotuned_warps_per_block(b) in (2, 4, 8)
+        assert vmc.vmc_autotuned_slots_per_lane(b) in (4, 8)
     finally:
         vmc.vmc_destroy(a)
         vmc.vmc_destroy(b)
@@ -161,7 +191,9 @@ def test_graph_not_replayed_after_per_lattice_sampling():
         ref_s, _ = _per_lattice(a, 0, 1)
         got_s, _ = _batched(b, 0, 1, spins, eloc, True)
         for l in range(len(LATS)):
-            assert np.array_equal(got_s[l], ref_s[l]), l
+            # a replay of stale descriptors would draw other random numbers for every chain
+            same = np.all(got_s[l] == ref_s[l], axis=(0, 2))
+            assert same.mean() >= 0.97, (l, np.sum(~same))
     finally:
         vmc.vmc_destroy(a)
         vmc.vmc_destroy(b)
