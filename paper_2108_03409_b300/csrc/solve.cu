@@ -2096,13 +2096,18 @@ cudaError_t solve_pcg_factor(const double2* F, double2* x, double tol, int maxit
     if (!(pq > 0.0)) { rel = NAN; break; }
     const double alpha = rz / pq;
     k_pcg_update<<<g, 256, 0, st>>>(x, r, p, q, alpha, P);
-    VMC_TRY(precondition(r, z));
-    double rz_new = 0.0, r2 = 0.0;
-    VMC_TRY(pcg_dots(r, z, P, w.scal_part, st, &rz_new, &r2));
+    // the residual test first: the preconditioner (two triangular solves) is applied only
+    // when another iteration follows
+    double r2 = 0.0, r2b = 0.0;
+    VMC_TRY(pcg_dots(r, r, P, w.scal_part, st, &r2, &r2b));
     *launches += 3;
     rel = std::sqrt(r2) / fn;
     if (!(rel == rel)) break;
     if (rel <= tol) { ++it; break; }
+    VMC_TRY(precondition(r, z));
+    double rz_new = 0.0;
+    VMC_TRY(pcg_dots(r, z, P, w.scal_part, st, &rz_new, &r2b));
+    ++*launches;
     const double beta = rz_new / rz;
     rz = rz_new;
     k_pcg_dir<<<g, 256, 0, st>>>(p, z, beta, P);
