@@ -145,7 +145,10 @@ cudaError_t dalloc(vmc_ctx* ctx, T** p, size_t count) {
   return cudaSuccess;
 }
 
-RbmDev rbm_of(const LatticeState& L) { return RbmDev{L.N, L.M, L.a, L.b, L.Wt, L.mth, L.mlc}; }
+int moves_of(const LatticeState& L);
+RbmDev rbm_of(const LatticeState& L) {
+  return RbmDev{L.N, L.M, L.a, L.b, L.Wt, L.mth, L.mlc, L.mlc + moves_of(L)};
+}
 
 int moves_of(const LatticeState& L) { return L.lat.model == 1 ? L.nb : L.N; }
 
@@ -182,6 +185,7 @@ vmc_status lattice_ok(vmc_ctx* ctx, int lattice) {
 vmc_status refresh_fp32(vmc_ctx* ctx, LatticeState& L) {
   CK(launch_param_prep(L.params, L.N, L.M, L.a, L.b, L.Wt, ctx->st), "param_prep");
   CK(launch_move_tables(L.params, L.N, L.M, L.lat.model, L.lat.Lx, L.lat.Ly, L.mth, L.mlc,
+                        L.mlc + moves_of(L),
                         ctx->st), "move_tables");
   ++ctx->launches;
   ++ctx->launches;
@@ -341,14 +345,15 @@ vmc_status vmc_init(const vmc_config* cfg, const vmc_lattice* lattices, int n_la
     if ((e = dalloc(ctx, &L.params, L.P)) || (e = dalloc(ctx, &L.a, L.N)) ||
         (e = dalloc(ctx, &L.b, L.M)) || (e = dalloc(ctx, &L.Wt, (size_t)L.N * L.M)) ||
         (e = dalloc(ctx, &L.mth, (size_t)moves_of(L) * L.M)) ||
-        (e = dalloc(ctx, &L.mlc, (size_t)moves_of(L))) ||
+        (e = dalloc(ctx, &L.mlc, (size_t)3 * moves_of(L))) ||   // mlc [moves], mpre [moves][2]
         (e = dalloc(ctx, &L.chains, (size_t)cfg->n_chains * L.N)))
       return oom(e);
     cudaMemset(L.params, 0, L.P * sizeof(double2));
     std::vector<int8_t> up((size_t)cfg->n_chains * L.N, 1);
     cudaMemcpy(L.chains, up.data(), up.size(), cudaMemcpyHostToDevice);
     launch_param_prep(L.params, L.N, L.M, L.a, L.b, L.Wt, ctx->st);
-    launch_move_tables(L.params, L.N, L.M, L.lat.model, L.lat.Lx, L.lat.Ly, L.mth, L.mlc, ctx->st);
+    launch_move_tables(L.params, L.N, L.M, L.lat.model, L.lat.Lx, L.lat.Ly, L.mth, L.mlc,
+                       L.mlc + moves_of(L), ctx->st);
     if (cfg->made_hidden > 0) {
       const int H = cfg->made_hidden;
       const int64_t np = made_nparams(L.N, H);

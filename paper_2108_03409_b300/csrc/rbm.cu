@@ -26,13 +26,16 @@ __global__ void k_param_prep(const double2* __restrict__ p, int N, int M, float2
 }
 
 // Move tables (see RbmDev), one block per move: D from the FP64 W, tanh D and log cosh D in
-// FP64, the tanh rounded once to FP32 and the log cosh summed over k in FP64 first.
+// FP64, the tanh rounded once to FP32 and the log cosh summed over k in FP64 first; the
+// prefactors exp(sum_k log cosh D_qk - da) for both spins of the move's first site from
+// that FP64 sum and the FP64 visible biases.
 //   log cosh z = z' - ln 2 + log(1 + exp(-2 z')),  z' = z or -z with Re z' >= 0,
 // which stays finite for any |Re D|.
 __global__ void __launch_bounds__(128) k_move_tables(const double2* __restrict__ p, int N, int M,
                                                      int model, int Lx, int Ly,
                                                      float2* __restrict__ mth,
-                                                     float2* __restrict__ mlc) {
+                                                     float2* __restrict__ mlc,
+                                                     float2* __restrict__ mpre) {
   const int q = blockIdx.x;
   const double2* W = p + N + M;                  // W[k][i] at k * N + i
   int i = q, j = -1;
@@ -77,13 +80,24 @@ __global__ void __launch_bounds__(128) k_move_tables(const double2* __restrict__
     const double im = red[1][0] + red[1][1] + red[1][2] + red[1][3];
     const double twopi = 6.28318530717958647692;
     mlc[q] = make_float2((float)re, (float)(im - twopi * rint(im / twopi)));
+    double2 da = p[i];                            // a_i (- a_j): the visible-bias difference
+    if (j >= 0) {
+      da.x -= p[j].x;
+      da.y -= p[j].y;
+    }
+    for (int h = 0; h < 2; ++h) {
+      const double s2 = h ? -2.0 : 2.0;
+      const double lx = re - s2 * da.x, ly = im - s2 * da.y;
+      const double mag = exp(lx);
+      mpre[2 * q + h] = make_float2((float)(mag * cos(ly)), (float)(mag * sin(ly)));
+    }
   }
 }
 
 cudaError_t launch_move_tables(const double2* p, int N, int M, int model, int Lx, int Ly,
-                               float2* mth, float2* mlc, cudaStream_t st) {
+                               float2* mth, float2* mlc, float2* mpre, cudaStream_t st) {
   const int moves = model == 1 ? num_bonds(Lx, Ly) : N;
-  k_move_tables<<<moves, 128, 0, st>>>(p, N, M, model, Lx, Ly, mth, mlc);
+  k_move_tables<<<moves, 128, 0, st>>>(p, N, M, model, Lx, Ly, mth, mlc, mpre);
   return cudaGetLastError();
 }
 

@@ -163,34 +163,30 @@ __device__ __forceinline__ float2 warp_factor_prod(const RbmDev& R, int lane,
   return prod;
 }
 
-// psi(s')/psi(s) for move q with first-site spin si, given the move's visible-bias term
-// 2 s_i (a-difference) as da (subtracted): the factor product times
-// exp(sum_k log cosh D_qk - da).  The product is used while its squared modulus stays in
-// [1e-30, 1e30] (every lane holds the same product, so the branch is warp-uniform);
-// otherwise the ratio is formed from the log-sum of the factors, which has no range limit.
+// psi(s')/psi(s) for move q (a flip of site i, j < 0, or the exchange on bond (i, j)) with
+// first-site spin si: the factor product times the tabulated exp(sum_k log cosh D_qk - da),
+// da = 2 si (a_i - a_j) or 2 si a_i.  The product is used while its squared modulus stays in
+// [1e-30, 1e30] (every lane of the group holds the same product, so the branch is
+// group-uniform); otherwise the ratio is formed from the log-sum of the factors, which has
+// no range limit.
 template <int MPL, int G = 32>
 __device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
                                                   const float2 (&t)[MPL], int q, float si,
-                                                  float2 da) {
+                                                  int i, int j) {
   const float2 pr = warp_factor_prod<MPL, G>(R, lane, t, q, si);
   const float m2 = fmaf(pr.x, pr.x, pr.y * pr.y);
-  float lx, ly;
-  float2 pre;
-  if (m2 > 1e-30f && m2 < 1e30f) {
-    const float2 c = R.mlc[q];
-    lx = c.x - da.x;
-    ly = c.y - da.y;
-    pre = pr;
-  } else {
-    const float2 lg = warp_log_ratio<MPL, G>(R, lane, t, q, si);
-    lx = lg.x - da.x;
-    ly = lg.y - da.y;
-    pre = make_float2(1.f, 0.f);
+  if (m2 > 1e-30f && m2 < 1e30f) return cmul(pr, R.mpre[2 * q + (si < 0.f ? 1 : 0)]);
+  const float2 lg = warp_log_ratio<MPL, G>(R, lane, t, q, si);
+  float2 da = R.a[i];
+  if (j >= 0) {
+    da.x -= R.a[j].x;
+    da.y -= R.a[j].y;
   }
-  const float mag = expf(lx);
+  da = make_float2(2.f * si * da.x, 2.f * si * da.y);
+  const float mag = expf(lg.x - da.x);
   float sn, cs;
-  sincosf(ly, &sn, &cs);
-  return cmul(pre, make_float2(mag * cs, mag * sn));
+  sincosf(lg.y - da.y, &sn, &cs);
+  return make_float2(mag * cs, mag * sn);
 }
 
 // E_loc(s) = sum_s' H_ss' psi(s')/psi(s) from the cached t = tanh theta(s) (Eq. Oloc).
@@ -223,10 +219,7 @@ __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, i
       const int pe = __shfl_sync(gm, ends, src, G);
       const int bi = pe & 0xffff, bj = pe >> 16;
       const float si = (float)s[bi];
-      const float2 ai = R.a[bi], aj = R.a[bj];
-      const float2 r = warp_move_ratio<MPL, G>(
-          R, lane, t, b0 + src, si,
-          make_float2(2.f * si * (ai.x - aj.x), 2.f * si * (ai.y - aj.y)));
+      const float2 r = warp_move_ratio<MPL, G>(R, lane, t, b0 + src, si, bi, bj);
       e.x = fmaf(2.f * L.J, r.x, e.x);
       e.y = fmaf(2.f * L.J, r.y, e.y);
     }
@@ -235,9 +228,7 @@ __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, i
   if (L.model == 0) {
     for (int i = 0; i < R.N; ++i) {           // -h X_i: flip site i
       const float si = (float)s[i];
-      const float2 ai = R.a[i];
-      const float2 r = warp_move_ratio<MPL, G>(R, lane, t, i, si,
-                                               make_float2(2.f * si * ai.x, 2.f * si * ai.y));
+      const float2 r = warp_move_ratio<MPL, G>(R, lane, t, i, si, i, -1);
       e.x = fmaf(-L.h, r.x, e.x);
       e.y = fmaf(-L.h, r.y, e.y);
     }

@@ -22,6 +22,10 @@ struct RbmDev {
   // move with s_i changes theta_k by -s_i D_qk.
   const float2* mth;  // [moves][M]
   const float2* mlc;  // [moves]
+  // mpre[2q + h] = exp(sum_k log cosh D_qk - da) with da = 2 s (a_i - a_j) for a bond (i, j),
+  // 2 s a_q for a flip, s = +1 (h = 0) or -1 (h = 1): the factor of psi(s')/psi(s) that does
+  // not depend on theta (rounded once from FP64)
+  const float2* mpre; // [moves][2]
 };
 
 struct LatDev {
@@ -51,7 +55,7 @@ struct SampleArgs {
 // ---- rbm.cu -------------------------------------------------------------------------
 // move tables of the lattice's model from the FP64 parameters (computed in FP64)
 cudaError_t launch_move_tables(const double2* p, int N, int M, int model, int Lx, int Ly,
-                               float2* mth, float2* mlc, cudaStream_t st);
+                               float2* mth, float2* mlc, float2* mpre, cudaStream_t st);
 cudaError_t launch_param_prep(const double2* p, int N, int M, float2* a, float2* b, float2* Wt,
                               cudaStream_t st);
 cudaError_t launch_logpsi(const RbmDev& R, const int8_t* spins, int64_t n, float2* out,
