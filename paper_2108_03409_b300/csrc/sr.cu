@@ -73,103 +73,106 @@ cudaError_t launch_estats(const float2* E, int64_t n, double* out, unsigned* sta
 // j = M whose factor is 1 and a virtual visible unit i = N whose spin is 1:
 //   (j < M, i < N): O = t_j s_i (W block);  (j < M, i = N): O = t_j (b block);
 //   (j = M, i < N): O = s_i (a block).
-// Each block sums a 32x32 tile over a chunk of kChunk samples: FP32 within sub-chunks of
+// Each block sums a 32 x 16 tile over a chunk of kChunk samples: FP32 within sub-chunks of
 // kSub samples, FP64 across them; chunk partials are then added in a fixed order.
 // ---------------------------------------------------------------------------------------
-static constexpr int kChunk = 1024, kSub = 128, kTile = 32;
+static constexpr int kChunk = 1024, kSub = 128;
+static_assert(kChunk == 8 * kSub, "one warp of the moments block per sub-chunk");
 
 int64_t moments_partial_doubles(int64_t n, int N, int M) {
   int64_t chunks = (n + kChunk - 1) / kChunk;
   return chunks * 4 * (int64_t)(M + 1) * (N + 1);
 }
 
-// One stage is 32 samples: thread (ty, tx) fetches sample qb + ty's spin of column i0 + tx
-// and t, conj(t)(E - <E>) of unit j0 + tx.  The next stage's values are fetched into
-// registers before the current stage's products, so that their latency overlaps the
-// arithmetic (a block is the only one on its SM).
-struct MomStage {
-  float2 t, u;
-  float sv;
-};
-
-__device__ __forceinline__ MomStage moments_fetch(const int8_t* __restrict__ spins,
-                                                  const float2* __restrict__ T,
-                                                  const float2* __restrict__ E, int64_t q,
-                                                  int64_t q1, int N, int M, int ii, int jj,
-                                                  float emr, float emi) {
-  MomStage v;
-  v.t = make_float2(0.f, 0.f);
-  v.u = make_float2(0.f, 0.f);
-  v.sv = 0.f;
-  if (q < q1) {
-    const float2 e = E ? E[q] : make_float2(0.f, 0.f);
-    const float er = e.x - emr, ei = e.y - emi;
-    if (jj < M) v.t = T[q * M + jj];
-    else if (jj == M) v.t = make_float2(1.f, 0.f);
-    v.u = make_float2(v.t.x * er + v.t.y * ei, v.t.x * ei - v.t.y * er);  // conj(t) (E - <E>)
-    if (ii < N) v.sv = (float)spins[q * N + ii];
-    else if (ii == N) v.sv = 1.f;
-  }
-  return v;
-}
-
+// One block per (32 x 16 tile of the (i, j) index space, chunk of kChunk samples).  Warp w
+// sums sub-chunk w of the chunk (kSub consecutive samples) in FP32; lane (li, lj) =
+// (lane & 7, lane >> 3) holds the 4 x 4 entries i = i0 + 4 li + a, j = j0 + 4 lj + b and
+// reads their spins, t and E itself (the tile's rows stay in L1 across the lanes that share
+// them).  The warps' sub-chunk sums are then added in FP64 in sub-chunk order through
+// shared memory, so a chunk's partial is the FP64 sum of its FP32 sub-chunk sums.
 // WANT_M: also the sums of O (for <O>); without it only the F sums are formed (the CG
 // operator's O^H u) and the <O> planes of the partials are left unwritten.
+constexpr int MT_I = 32, MT_J = 16;
+
 template <bool WANT_M>
-__global__ void __launch_bounds__(1024) k_moments_partial(
+__global__ void __launch_bounds__(256, 2) k_moments_partial(
     const int8_t* __restrict__ spins, const float2* __restrict__ T, const float2* __restrict__ E,
     const double* __restrict__ estats, int64_t n, int N, int M, double* __restrict__ partial) {
-  __shared__ float2 Ts[32][kTile + 1];
-  __shared__ float2 Us[32][kTile + 1];
-  __shared__ float Ss[32][kTile + 1];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i0 = blockIdx.x * kTile, j0 = blockIdx.y * kTile;
-  const int64_t q0 = (int64_t)blockIdx.z * kChunk;
-  const int64_t q1 = min(n, q0 + kChunk);
+  constexpr int NPL = WANT_M ? 4 : 2;
+  __shared__ double acc[NPL][MT_J][MT_I];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int li = lane & 7, lj = lane >> 3;
+  const int ib = blockIdx.x * MT_I + 4 * li, jb = blockIdx.y * MT_J + 4 * lj;
+  const int64_t q0 = (int64_t)blockIdx.z * kChunk + (int64_t)w * kSub;
+  const int64_t q1 = min(n, q0 + kSub);
   const float emr = E ? (float)estats[0] : 0.f, emi = E ? (float)estats[1] : 0.f;
-  const int i = i0 + tx, j = j0 + ty;
-  double dm_r = 0, dm_i = 0, df_r = 0, df_i = 0;
-  float fm_r = 0, fm_i = 0, ff_r = 0, ff_i = 0;
-  int in_sub = 0;
-  MomStage nx = moments_fetch(spins, T, E, q0 + ty, q1, N, M, i0 + tx, j0 + tx, emr, emi);
-  for (int64_t qb = q0; qb < q1; qb += 32) {
-    // stage 32 samples: row ty of the staging tile is sample qb + ty
-    if (WANT_M) Ts[ty][tx] = nx.t;
-    Us[ty][tx] = nx.u;
-    Ss[ty][tx] = nx.sv;
-    __syncthreads();
-    if (qb + 32 < q1)
-      nx = moments_fetch(spins, T, E, qb + 32 + ty, q1, N, M, i0 + tx, j0 + tx, emr, emi);
-#pragma unroll 8
-    for (int m = 0; m < 32; ++m) {
-      const float sv = Ss[m][tx];
-      const float2 u = Us[m][ty];
-      if (WANT_M) {
-        const float2 t = Ts[m][ty];
-        fm_r = fmaf(sv, t.x, fm_r);
-        fm_i = fmaf(sv, t.y, fm_i);
+  float fr[4][4], fi[4][4], mr[4][4], mi[4][4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) fr[b][a] = fi[b][a] = mr[b][a] = mi[b][a] = 0.f;
+#pragma unroll 2
+  for (int64_t q = q0; q < q1; ++q) {
+    float sv[4];
+    float2 t[4], u[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = ib + a;
+      sv[a] = (i < N) ? (float)spins[q * N + i] : (i == N ? 1.f : 0.f);
+    }
+    const float2 e = E ? E[q] : make_float2(0.f, 0.f);
+    const float er = e.x - emr, ei = e.y - emi;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int j = jb + b;
+      t[b] = (j < M) ? T[q * M + j] : make_float2(j == M ? 1.f : 0.f, 0.f);
+      u[b] = make_float2(t[b].x * er + t[b].y * ei, t[b].x * ei - t[b].y * er);  // conj(t)(E-<E>)
+    }
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        if (WANT_M) {
+          mr[b][a] = fmaf(sv[a], t[b].x, mr[b][a]);
+          mi[b][a] = fmaf(sv[a], t[b].y, mi[b][a]);
+        }
+        fr[b][a] = fmaf(sv[a], u[b].x, fr[b][a]);
+        fi[b][a] = fmaf(sv[a], u[b].y, fi[b][a]);
       }
-      ff_r = fmaf(sv, u.x, ff_r);
-      ff_i = fmaf(sv, u.y, ff_i);
+  }
+  // FP64 sum over the sub-chunks, in order
+  for (int k = 0; k < 8; ++k) {
+    if (w == k) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int r = 4 * lj + b, c = 4 * li + a;
+          const double v[4] = {(double)fr[b][a], (double)fi[b][a], (double)mr[b][a],
+                               (double)mi[b][a]};
+#pragma unroll
+          for (int pl = 0; pl < NPL; ++pl)
+            acc[pl][r][c] = (k == 0) ? v[pl] : acc[pl][r][c] + v[pl];
+        }
     }
     __syncthreads();
-    in_sub += 32;
-    if (in_sub >= kSub) {
-      dm_r += fm_r; dm_i += fm_i; df_r += ff_r; df_i += ff_i;
-      fm_r = fm_i = ff_r = ff_i = 0.f;
-      in_sub = 0;
-    }
   }
-  dm_r += fm_r; dm_i += fm_i; df_r += ff_r; df_i += ff_i;
-  if (i <= N && j <= M) {
-    const int64_t plane = (int64_t)(M + 1) * (N + 1);
-    double* base = partial + (int64_t)blockIdx.z * 4 * plane + (int64_t)j * (N + 1) + i;
-    if (WANT_M) {
-      base[0] = dm_r;
-      base[plane] = dm_i;
+  // planes of the partials: 0, 1 = <O> sums (WANT_M), 2, 3 = F sums; acc planes 0, 1 hold
+  // the F sums, 2, 3 the <O> sums
+  const int64_t plane = (int64_t)(M + 1) * (N + 1);
+  double* base = partial + (int64_t)blockIdx.z * 4 * plane;
+  for (int e = threadIdx.x; e < MT_J * MT_I; e += 256) {
+    const int r = e / MT_I, c = e % MT_I;
+    const int j = blockIdx.y * MT_J + r, i = blockIdx.x * MT_I + c;
+    if (i <= N && j <= M) {
+      const int64_t off = (int64_t)j * (N + 1) + i;
+      base[2 * plane + off] = acc[0][r][c];
+      base[3 * plane + off] = acc[1][r][c];
+      if (WANT_M) {
+        base[off] = acc[2][r][c];
+        base[plane + off] = acc[3][r][c];
+      }
     }
-    base[2 * plane] = df_r;
-    base[3 * plane] = df_i;
   }
 }
 
@@ -207,10 +210,9 @@ cudaError_t launch_moments(const int8_t* spins, const float2* T, const float2* E
   if (n <= 0) return cudaErrorInvalidValue;
   const int64_t chunks = (n + kChunk - 1) / kChunk;
   if (chunks > kMomentsMaxChunks) return cudaErrorInvalidValue;   // one chunk per grid z
-  dim3 grid((N + 1 + kTile - 1) / kTile, (M + 1 + kTile - 1) / kTile, (unsigned)chunks);
-  dim3 block(kTile, 32);
-  if (meanO) k_moments_partial<true><<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, partial);
-  else k_moments_partial<false><<<grid, block, 0, st>>>(spins, T, E, estats, n, N, M, partial);
+  dim3 grid((N + 1 + MT_I - 1) / MT_I, (M + 1 + MT_J - 1) / MT_J, (unsigned)chunks);
+  if (meanO) k_moments_partial<true><<<grid, 256, 0, st>>>(spins, T, E, estats, n, N, M, partial);
+  else k_moments_partial<false><<<grid, 256, 0, st>>>(spins, T, E, estats, n, N, M, partial);
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t plane = (int64_t)(M + 1) * (N + 1);
