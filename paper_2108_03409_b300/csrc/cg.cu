@@ -453,6 +453,8 @@ __global__ void __launch_bounds__(256) k_add_diag(const double2* __restrict__ y,
   block_partial(pq, vpart + OFF_PQ, red);
 }
 
+constexpr int RED_U = 16;   // chunk partials of one entry loaded together
+
 // q_k = y_k + D_k p_k with y_k = (1/n) sum_q conj(Obar_qk) w_q from the K-chunk partials
 // (compensated sum over chunks in order): a_i: out rows 2M / 2M+1, column i; b_j: ybpart[.][j];
 // W_ji: out rows 2j / 2j+1, column i.  Partials of Re p^H q.  Without D: q = y (conjugated
@@ -474,25 +476,37 @@ __global__ void __launch_bounds__(128) k_cg_reduce_tc(const float* __restrict__ 
   double pq = 0.0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < P;
        k += (int64_t)gridDim.x * blockDim.x) {
+    // the chunk partials of entry k, RED_U chunks at a time: all their loads are issued
+    // before the (in-order, compensated) sums, so that a thread keeps 2 RED_U loads in flight
     CSum sr, si;
+    const float* g;
+    int64_t cs, off_im;
     if (k >= N && k < N + M) {
-#pragma unroll 8
-      for (int c = 0; c < kchunks; ++c) {
-        const float2 v = ybpart[(int64_t)c * M + (k - N)];
-        sr.add(v.x);
-        si.add(v.y);
-      }
+      g = reinterpret_cast<const float*>(ybpart + (k - N));
+      cs = 2 * (int64_t)M;
+      off_im = 1;
     } else {
       int64_t row, col;
       if (k < N) { row = 2 * (int64_t)M; col = k; }
-      else { const int64_t rr = k - N - M; row = 2 * (rr / N); col = rr % N; }
-      const float* g = out + row * ncols + col;
-      const int64_t cs = a_rows * ncols;
-#pragma unroll 8
-      for (int c = 0; c < kchunks; ++c) {
-        sr.add(g[(int64_t)c * cs]);
-        si.add(g[(int64_t)c * cs + ncols]);
+      else { const int rr = (int)(k - N - M); row = 2 * (int64_t)(rr / N); col = rr % N; }
+      g = out + row * ncols + col;
+      cs = a_rows * ncols;
+      off_im = ncols;
+    }
+    for (int c0 = 0; c0 < kchunks; c0 += RED_U) {
+      float vr[RED_U], vi[RED_U];
+#pragma unroll
+      for (int u = 0; u < RED_U; ++u) {
+        const int64_t o = (int64_t)min(c0 + u, kchunks - 1) * cs;
+        vr[u] = __ldg(g + o);
+        vi[u] = __ldg(g + o + off_im);
       }
+#pragma unroll
+      for (int u = 0; u < RED_U; ++u)
+        if (c0 + u < kchunks) {
+          sr.add(vr[u]);
+          si.add(vi[u]);
+        }
     }
     const double re = sr.value(), im = si.value();
     if (D) {
