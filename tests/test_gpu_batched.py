@@ -21,13 +21,16 @@ T, H = inputs.MODEL_TFIM, inputs.MODEL_HEIS
 
 # (model, Lx, Ly, J, h, alpha): uneven sizes, both models, Lx != Ly, M from 10 to 128.  The
 # 8x8 alpha = 2 lattices (M = 128, as in the 48-lattice benchmark) make the persistent launch
-# run its four-slots-per-lane instantiation, the one the benchmark times.
+# run its four-slots-per-lane instantiation, the one the benchmark times; with four slots per
+# lane, M <= 16 runs chains on groups of 4 lanes, M = 32 on 8, M = 36 on 16 (the 6x6
+# Heisenberg lattice) and M > 64 on whole warps.
 LATS = [
     (T, 10, 1, 1.0, 1.0, 1),
     (T, 4, 4, 1.0, 3.0, 2),
     (T, 3, 5, 1.0, 2.5, 1),
     (H, 4, 4, 1.0, 0.0, 1),
     (T, 6, 6, 1.0, 3.0, 2),
+    (H, 6, 6, 1.0, 0.0, 1),
     (T, 2, 2, 1.0, 2.0, 3),
     (T, 8, 8, 1.0, 3.0, 2),
     (H, 8, 8, 1.0, 0.0, 2),

@@ -140,6 +140,46 @@ def test_local_energy_matches_oracle(case):
         assert np.max(np.abs(got - ref)) / N <= ELOC_PER_SITE_ABS
 
 
+@pytest.mark.parametrize("model", [T, H], ids=["tfim4x4", "heis4x4"])
+def test_local_energy_log_sum_fallback_matches_oracle(model):
+    """A move's factor product 1 - s t tanh D over the hidden units is the E_loc ratio's
+    fast path while it stays in [1e-15, 1e15]; otherwise the kernel forms the ratio from
+    the log-sum of the factors.  Real parameters (no nodes of cosh theta) with one column
+    of large weights (|W_j,i0| = 0.9, b_j = 0.6, M = 64) send every move touching site i0
+    through the log-sum path while the ratio itself stays moderate (|log| <= 3); both
+    paths' local energies against the oracle at the FP32 bound."""
+    Lx = Ly = 4
+    N, M, alpha, i0 = 16, 64, 4, 5
+    h = 2.0 if model == T else 0.0
+    rng = np.random.default_rng(71)
+    a = rng.normal(0, 0.05, N)
+    b = 0.6 + rng.normal(0, 0.05, M)
+    W = rng.normal(0, 0.02, (M, N))
+    W[:, i0] = np.where(np.arange(M) % 2 == 0, 0.9, -0.9)
+    p = np.concatenate([a, b, W.reshape(-1)]).astype(np.complex128)
+    s = inputs.initial_spins(model, 400, N, seed=72)
+    # host check that the log-sum path is exercised: moves whose product leaves the range
+    t = np.tanh(b[None, :] + s.astype(np.float64) @ W.T)
+    n_log_sum = 0
+    for q in range(len(s)):
+        sp, _ = oracle.connected(model, Lx, Ly, 1.0, h, s[q])
+        for c in sp[1:]:
+            flip = np.nonzero(c != s[q])[0]
+            D = 2 * W[:, flip[0]] - (2 * W[:, flip[1]] if len(flip) == 2 else 0)
+            lp = np.sum(np.log(np.abs(1 - s[q, flip[0]] * t[q] * np.tanh(D))))
+            n_log_sum += abs(lp) > 15 * np.log(10)
+    assert n_log_sum >= len(s), n_log_sum
+    with context(lattice(model, Lx, Ly, 1.0, h, alpha), n_chains=len(s),
+                 solver=vmc.SOLVER_CG) as ctx:
+        vmc.vmc_set_params(ctx, 0, p)
+        out = torch.zeros((len(s), 2), dtype=torch.float32, device="cuda")
+        vmc.vmc_local_energy(ctx, 0, to_dev_spins(s), out)
+        got = cplx(out)
+    ref = oracle.eloc(model, Lx, Ly, 1.0, h, M, p, s)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= eloc_tolerance(model, Lx, Ly, 1.0, h, M, p, s))
+
+
 def test_empty_batch_is_a_noop():
     with context(lattice(T, 10, 1, 1.0, 1.0, 1), n_chains=4) as ctx:
         e = torch.zeros((0, 2), dtype=torch.float32, device="cuda")
