@@ -747,9 +747,11 @@ def run_batched(args):
 
     # ALU roofline of the persistent sweep kernel: per proposed flip and hidden unit the
     # ratio cosh(theta - d)/cosh(theta) = cosh d - tanh(theta) sinh d and its squared
-    # modulus take 22 FP32 operations (18 arithmetic, 4 elementary functions counted once), so one
-    # step does 22 * sum_l C * N_l * M_l flops of the acceptance test.
-    flops = 22.0 * sum(C * N * alpha * N for N in Ns_)
+    # modulus take 22 FP32 operations (18 arithmetic, 4 elementary functions counted once);
+    # the record's local energy evaluates the same ratio, without the modulus (19), for each
+    # of the N flips.  One step (one sweep of N proposals and one record per chain) does
+    # (22 + 19) * sum_l C * N_l * M_l flops.
+    flops = (22.0 + 19.0) * sum(C * N * alpha * N for N in Ns_)
     pk, pk_kind = peaks()
     fp32_peak = 148 * 128 * 2 * pk.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     achieved = flops / (ms_b / args.steps / 1e3) / 1e12
@@ -772,7 +774,7 @@ def run_batched(args):
                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                         "kernel": "sample_batched",
                         "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 flop x max SM clock",
-                        "algorithmic": "22 flops per proposed flip per hidden unit"},
+                        "algorithmic": "22 flops per proposed flip and 19 per local-energy flip ratio, per hidden unit"},
            "e2e": {"value": e2e, "unit": "samples/s (incl. E_loc)",
                    "h2d_bytes_per_step": C * tot, "d2h_bytes_per_step": C * tot + n_lat * C * 8},
            "gpu_launches": launches,
