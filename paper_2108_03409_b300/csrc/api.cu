@@ -1917,10 +1917,10 @@ static vmc_status batched_upload(vmc_ctx* ctx, int n_therm, int n_samples, int8_
   return VMC_OK;
 }
 
-// Autotuner: hidden slots per lane (the per-chain width, or twice it up to 8, which puts
-// several chains of the smaller lattices in one warp) and warps per block of the persistent
-// launch, timed on one sweep of every chain (chains saved before and restored after; sweep
-// counters untouched).
+// Autotuner: hidden slots per lane (the per-chain width, or a wider one up to twice it and at
+// most 8, which puts several chains of the smaller lattices in one warp) and warps per block
+// of the persistent launch, timed on one sweep of every chain (chains saved before and
+// restored after; sweep counters untouched).
 static vmc_status batched_tune(vmc_ctx* ctx) {
   ctx->g_therm = -1;
   const int nl = (int)ctx->lats.size();
@@ -1935,12 +1935,15 @@ static vmc_status batched_tune(vmc_ctx* ctx) {
     off += (size_t)C * L.N;
   }
   float best = 1e30f;
+  // slots per lane: the per-chain width for the largest M and every instantiated width up to
+  // twice it (at most 8), each putting the chains of more of the lattices several to a warp
   const int base = sample_slots_per_lane(ctx->Mmax);
-  const int wide = base <= 4 ? sample_slots_per_lane(64 * base) : 0;   // 2 x base (<= 8)
-  const int mpls[2] = {base, wide};
+  int mpls[4] = {base, 0, 0, 0}, nm = 1;
+  for (int m = base + 1; m <= std::min(2 * base, 8) && nm < 4; ++m)
+    if (sample_slots_per_lane(32 * m) == m) mpls[nm++] = m;
   const int cand[3] = {2, 4, 8};
-  for (int mpl : mpls) {
-   if (mpl <= 0) continue;
+  for (int im = 0; im < nm; ++im) {
+   const int mpl = mpls[im];
    if ((s = batched_upload(ctx, 1, 0, nullptr, nullptr, mpl))) return s;
    for (int wpb : cand) {
     const int per_sm = batched_blocks_per_sm(mpl, wpb, ctx->Nmax);

@@ -137,7 +137,7 @@ def test_batched_equals_per_lattice_and_graph_replay():
             _same_chains(vmc.vmc_get_chains(a, l, C, N), vmc.vmc_get_chains(b, l, C, N),
                          margins[l])
         assert vmc.vmc_autotuned_warps_per_block(b) in (2, 4, 8)
-        assert vmc.vmc_autotuned_slots_per_lane(b) in (4, 8)
+        assert vmc.vmc_autotuned_slots_per_lane(b) in (4, 5, 6, 8)
     finally:
         vmc.vmc_destroy(a)
         vmc.vmc_destroy(b)
