@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128) k_eloc(RbmDev R, LatDev L,
   warp_theta<MPL>(R, s, lane, th);
 #pragma unroll
   for (int k = 0; k < MPL; ++k) t[k] = tanh_c(th[k].x, th[k].y);
-  float2 e = warp_eloc<MPL>(R, L, s, lane, t);
+  float2 e = warp_eloc<MPL>(R, L, s, lane, t, eloc_buffer(sm, R.N, wib));
   if (lane == 0) {
     out[q] = e;
     if (!isfinite(e.x) || !isfinite(e.y)) flag_error(status, DEV_ERR_NUMERIC);
@@ -278,7 +278,7 @@ cudaError_t launch_eloc(const RbmDev& R, const LatDev& L, const int8_t* spins, i
                         float2* out, unsigned* status, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   unsigned grid = (unsigned)((n + kWarps - 1) / kWarps);
-  VMC_DISPATCH_MPL(R.M, k_eloc<MPL><<<grid, 32 * kWarps, spin_smem(R.N), st>>>(R, L, spins, n, out, status));
+  VMC_DISPATCH_MPL(R.M, k_eloc<MPL><<<grid, 32 * kWarps, sample_smem(R.N), st>>>(R, L, spins, n, out, status));
   return cudaGetLastError();
 }
 

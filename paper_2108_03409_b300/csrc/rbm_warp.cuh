@@ -170,12 +170,9 @@ __device__ __forceinline__ float2 warp_factor_prod(const RbmDev& R, int lane,
 // group-uniform); otherwise the ratio is formed from the log-sum of the factors, which has
 // no range limit.
 template <int MPL, int G = 32>
-__device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
-                                                  const float2 (&t)[MPL], int q, float si,
-                                                  int i, int j) {
-  const float2 pr = warp_factor_prod<MPL, G>(R, lane, t, q, si);
-  const float m2 = fmaf(pr.x, pr.x, pr.y * pr.y);
-  if (m2 > 1e-30f && m2 < 1e30f) return cmul(pr, R.mpre[2 * q + (si < 0.f ? 1 : 0)]);
+__device__ __forceinline__ float2 warp_move_ratio_logsum(const RbmDev& R, int lane,
+                                                         const float2 (&t)[MPL], int q,
+                                                         float si, int i, int j) {
   const float2 lg = warp_log_ratio<MPL, G>(R, lane, t, q, si);
   float2 da = R.a[i];
   if (j >= 0) {
@@ -189,13 +186,126 @@ __device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
   return make_float2(mag * cs, mag * sn);
 }
 
+template <int MPL, int G = 32>
+__device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
+                                                  const float2 (&t)[MPL], int q, float si,
+                                                  int i, int j) {
+  const float2 pr = warp_factor_prod<MPL, G>(R, lane, t, q, si);
+  const float m2 = fmaf(pr.x, pr.x, pr.y * pr.y);
+  if (m2 > 1e-30f && m2 < 1e30f) return cmul(pr, R.mpre[2 * q + (si < 0.f ? 1 : 0)]);
+  return warp_move_ratio_logsum<MPL, G>(R, lane, t, q, si, i, j);
+}
+
+// Local-energy ratios of a whole warp (G = 32) kElocBatch moves at a time: lane m of the
+// warp holds move m (myq, first-site spin mysi, sites myi, myj; myj < 0 for a flip).  Each
+// lane multiplies its own hidden slots' factors for every move (the table rows are read
+// coalesced, as in a proposal), the partial products go through the warp's shared-memory
+// buffer eb, and lane m multiplies move m's 32 partials in lane order: no butterfly per
+// move.  A move whose product leaves [1e-15, 1e15] in modulus takes the warp-wide log-sum
+// path.  Returns coef times this lane's move's ratio (0 for lanes >= nm).
+static constexpr int kElocBatch = 16;
+static constexpr int kElocLd = 33;                     // row stride (float2), against conflicts
+static constexpr int kElocBufBytes = kElocBatch * kElocLd * (int)sizeof(float2);
+
+template <int MPL>
+__device__ __forceinline__ float2 warp_eloc_batch(const RbmDev& R, int lane,
+                                                  const float2 (&t)[MPL], int nm, int myq,
+                                                  float mysi, int myi, int myj, float coef,
+                                                  float2* eb) {
+  for (int m = 0; m < nm; ++m) {
+    const int q = __shfl_sync(FULL, myq, m);
+    const float si = __shfl_sync(FULL, mysi, m);
+    const float2* row = R.mth + (int64_t)q * R.M;
+    float2 prod = make_float2(1.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < MPL; ++k) {
+      const int hj = lane + 32 * k;
+      if (hj < R.M) prod = cmul(prod, move_factor(t[k], row[hj], si));
+    }
+    eb[m * kElocLd + lane] = prod;
+  }
+  __syncwarp();
+  float2 r = make_float2(0.f, 0.f);
+  bool ok = true;
+  if (lane < nm) {
+    float2 p = eb[lane * kElocLd];
+    for (int j = 1; j < 32; ++j) p = cmul(p, eb[lane * kElocLd + j]);
+    const float m2 = fmaf(p.x, p.x, p.y * p.y);
+    ok = m2 > 1e-30f && m2 < 1e30f;
+    if (ok) r = cmul(p, R.mpre[2 * myq + (mysi < 0.f ? 1 : 0)]);
+  }
+  __syncwarp();                                         // eb is rewritten by the next batch
+  unsigned fb = __ballot_sync(FULL, !ok);
+  while (fb) {
+    const int m = __ffs(fb) - 1;
+    fb &= fb - 1;
+    const float2 rr = warp_move_ratio_logsum<MPL, 32>(
+        R, lane, t, __shfl_sync(FULL, myq, m), __shfl_sync(FULL, mysi, m),
+        __shfl_sync(FULL, myi, m), __shfl_sync(FULL, myj, m));
+    if (lane == m) r = rr;
+  }
+  return make_float2(coef * r.x, coef * r.y);
+}
+
 // E_loc(s) = sum_s' H_ss' psi(s')/psi(s) from the cached t = tanh theta(s) (Eq. Oloc).
 // The bonds are taken 32 at a time, one per lane: each lane finds its bond's sites and
 // adds s_i s_j to the diagonal part; for the Heisenberg model a ballot then walks only the
 // anti-parallel bonds, whose sites come from their lane by a shuffle.
 template <int MPL, int G = 32>
 __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, int lane,
-                            const float2 (&t)[MPL]) {
+                            const float2 (&t)[MPL], float2* eb = nullptr) {
+  if constexpr (G == 32) {
+    if (eb) {                     // a whole warp with a ratio buffer: batched ratios
+      float zz = 0.f;
+      float2 acc = make_float2(0.f, 0.f);   // this lane's moves' contributions
+      for (int b0 = 0; b0 < L.nb; b0 += 32) {
+        const int b = b0 + lane;
+        int i = 0, j = 0;
+        bool anti = false;
+        if (b < L.nb) {
+          bond_ends(L.Lx, L.Ly, b, &i, &j);
+          zz += (float)(s[i] * s[j]);
+          anti = s[i] != s[j];
+        }
+        if (L.model != 1) continue;
+        const int ends = i | (j << 16);
+        unsigned mask = __ballot_sync(FULL, anti);
+        while (mask) {                      // J(XX+YY): swap an anti-parallel pair, 2J
+          int nm = 0, myq = 0, myi = 0, myj = 0;
+          float mysi = 0.f;
+          for (; nm < kElocBatch && mask; ++nm) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int pe = __shfl_sync(FULL, ends, src);
+            if (lane == nm) {
+              myq = b0 + src;
+              myi = pe & 0xffff;
+              myj = pe >> 16;
+              mysi = (float)s[myi];
+            }
+          }
+          const float2 c = warp_eloc_batch<MPL>(R, lane, t, nm, myq, mysi, myi, myj,
+                                                2.f * L.J, eb);
+          acc.x += c.x;
+          acc.y += c.y;
+        }
+      }
+      if (L.model == 0) {
+        for (int i0 = 0; i0 < R.N; i0 += kElocBatch) {   // -h X_i: flip site i
+          const int nm = min(kElocBatch, R.N - i0);
+          const int myq = i0 + lane;
+          const float mysi = (lane < nm) ? (float)s[myq] : 0.f;
+          const float2 c = warp_eloc_batch<MPL>(R, lane, t, nm, myq, mysi, myq, -1, -L.h, eb);
+          acc.x += c.x;
+          acc.y += c.y;
+        }
+      }
+      float2 e = make_float2(warp_sum(acc.x), warp_sum(acc.y));
+      zz = warp_sum(zz);
+      e.x = fmaf(L.model == 0 ? -L.J : L.J, zz, e.x);
+      return e;
+    }
+  }
   const int gl = lane & (G - 1);
   const unsigned gm = group_mask<G>(lane);
   float zz = 0.f;                 // diagonal: sum over bonds of s_i s_j (exact small integers)
@@ -295,7 +405,8 @@ __device__ __forceinline__ float2 warp_resync(const RbmDev& R, const int8_t* s, 
 // group's shared-memory spin buffer.  Every collective names only the group's lanes, so the
 // groups of a warp may take different branches (accept / reject).
 template <int MPL, bool HEIS, int G = 32>
-__device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
+__device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane,
+                          float2* eb = nullptr) {
   const RbmDev& R = A.rbm;
   const LatDev& L = A.lat;
   const int N = R.N, M = R.M;
@@ -408,7 +519,7 @@ __device__ void run_chain(const SampleArgs& A, int chain, int8_t* s, int lane) {
         bad |= !isfinite(lp.x) || !isfinite(lp.y);
       }
       if (A.eloc_out) {
-        const float2 e = warp_eloc<MPL, G>(R, L, s, lane, t);
+        const float2 e = warp_eloc<MPL, G>(R, L, s, lane, t, eb);
         if (gl == 0) A.eloc_out[qs] = e;
         bad |= !isfinite(e.x) || !isfinite(e.y);
       }
@@ -459,5 +570,12 @@ __host__ __device__ constexpr int sample_min_blocks(int mpl) {
 }
 
 static inline size_t spin_smem(int N) { return (size_t)kWarps * ((N + 15) & ~15); }
+
+// Dynamic shared memory of the 4-warp sampling / local-energy blocks: the warps' spin
+// buffers, then one local-energy ratio buffer per warp (spin_smem is a multiple of 16).
+static inline size_t sample_smem(int N) { return spin_smem(N) + (size_t)kWarps * kElocBufBytes; }
+__device__ __forceinline__ float2* eloc_buffer(int8_t* sm, int N, int wib) {
+  return reinterpret_cast<float2*>(sm + kWarps * ((N + 15) & ~15) + wib * kElocBufBytes);
+}
 
 }  // namespace vmc

@@ -20,9 +20,10 @@ cudaError_t launch_sample_heis(const SampleArgs& A, cudaStream_t st);
 // hidden slots per lane) keeps 32 warps resident per SM.
 // ---------------------------------------------------------------------------------------
 template <int MPL, int G>
-__device__ __forceinline__ void run_group(const SampleArgs& A, int chain, int8_t* s, int lane) {
-  if (A.lat.model == 1) run_chain<MPL, true, G>(A, chain, s, lane);
-  else run_chain<MPL, false, G>(A, chain, s, lane);
+__device__ __forceinline__ void run_group(const SampleArgs& A, int chain, int8_t* s, int lane,
+                                          float2* eb) {
+  if (A.lat.model == 1) run_chain<MPL, true, G>(A, chain, s, lane, eb);
+  else run_chain<MPL, false, G>(A, chain, s, lane, eb);
 }
 
 template <int MPL>
@@ -32,6 +33,9 @@ __global__ void __launch_bounds__(256, MPL <= 4 ? 4 : MPL <= 8 ? 3 : 2)
   extern __shared__ int8_t sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int8_t* sw = sm + wib * kMaxChainsPerWarp * npad_max;
+  // the warp's local-energy ratio buffer, after all warps' spin buffers (whole-warp chains)
+  float2* eb = reinterpret_cast<float2*>(sm + (blockDim.x >> 5) * kMaxChainsPerWarp * npad_max +
+                                         wib * kElocBufBytes);
   const unsigned total = (unsigned)ustart[n_lat];
   while (true) {
     unsigned unit = 0;
@@ -48,13 +52,13 @@ __global__ void __launch_bounds__(256, MPL <= 4 ? 4 : MPL <= 8 ? 3 : 2)
       int8_t* s = sw + gi * npad_max;
       if constexpr (MPL <= 8) {
         switch (G) {
-          case 4: run_group<MPL, 4>(A, chain, s, lane); break;
-          case 8: run_group<MPL, 8>(A, chain, s, lane); break;
-          case 16: run_group<MPL, 16>(A, chain, s, lane); break;
-          default: run_group<MPL, 32>(A, chain, s, lane); break;
+          case 4: run_group<MPL, 4>(A, chain, s, lane, nullptr); break;
+          case 8: run_group<MPL, 8>(A, chain, s, lane, nullptr); break;
+          case 16: run_group<MPL, 16>(A, chain, s, lane, nullptr); break;
+          default: run_group<MPL, 32>(A, chain, s, lane, eb); break;
         }
       } else {
-        run_group<MPL, 32>(A, chain, s, lane);
+        run_group<MPL, 32>(A, chain, s, lane, eb);
       }
     }
     __syncwarp();
@@ -71,7 +75,7 @@ cudaError_t launch_sample_batched(const SampleArgs* d_args, const int* d_order,
                                   unsigned* counter, int warps_per_block, int grid,
                                   uint64_t advance, SampleArgs* d_args_mut, cudaStream_t st) {
   const int npad = (Nmax + 15) & ~15;
-  const size_t smem = (size_t)warps_per_block * kMaxChainsPerWarp * npad;
+  const size_t smem = (size_t)warps_per_block * (kMaxChainsPerWarp * npad + kElocBufBytes);
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   VMC_DISPATCH_MPL(32 * mpl, k_sample_batched<MPL><<<grid, 32 * warps_per_block, smem, st>>>(
@@ -92,7 +96,7 @@ static int batched_occupancy(int threads, size_t smem) {
 }
 
 int batched_blocks_per_sm(int mpl, int warps_per_block, int Nmax) {
-  const size_t smem = (size_t)warps_per_block * kMaxChainsPerWarp * ((Nmax + 15) & ~15);
+  const size_t smem = (size_t)warps_per_block * (kMaxChainsPerWarp * ((Nmax + 15) & ~15) + kElocBufBytes);
   if (pick_mpl(32 * mpl) != mpl) return 0;   // (the dispatch default below is then unreachable)
   auto occ = [&]() -> int {
     VMC_DISPATCH_MPL(32 * mpl, return batched_occupancy<MPL>(32 * warps_per_block, smem));

@@ -11,13 +11,13 @@ __global__ void __launch_bounds__(128, sample_min_blocks(MPL)) k_sample(SampleAr
   const int chain = blockIdx.x * (blockDim.x >> 5) + wib;
   if (chain >= A.C) return;
   const int Npad = (A.rbm.N + 15) & ~15;
-  run_chain<MPL, HEIS>(A, chain, sm + wib * Npad, lane);
+  run_chain<MPL, HEIS>(A, chain, sm + wib * Npad, lane, eloc_buffer(sm, A.rbm.N, wib));
 }
 
 cudaError_t launch_sample_tfim(const SampleArgs& A, cudaStream_t st) {
   if (A.C <= 0) return cudaSuccess;
   const unsigned grid = (unsigned)((A.C + kWarps - 1) / kWarps);
-  const size_t smem = spin_smem(A.rbm.N);
+  const size_t smem = sample_smem(A.rbm.N);
   VMC_DISPATCH_MPL(A.rbm.M, k_sample<MPL, false><<<grid, 32 * kWarps, smem, st>>>(A));
   return cudaGetLastError();
 }
