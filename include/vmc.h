@@ -275,8 +275,9 @@ vmc_status vmc_sample_learned(vmc_ctx* ctx, int lattice, int n_rounds, int8_t* s
  * samples [n_samples][n_chains][N_l] starting at byte n_samples * n_chains * (N_0 + ... +
  * N_{l-1}); eloc_out is [n_lattices][n_samples * n_chains][2].  The first call autotunes
  * the hidden slots per lane (the per-lattice kernels' width for the largest M, or a wider
- * instantiated width up to twice it and at most 8) and the warps per block of the persistent grid (timed on one sweep; chains
- * restored).  use_graph = 1 captures the launch into a CUDA graph and replays it while
+ * instantiated width up to twice it and at most 8) and the warps per block of the
+ * persistent grid (timed on one sweep, the faster of two launches each; chains restored).
+ * use_graph = 1 captures the launch into a CUDA graph and replays it while
  * (n_therm, n_samples, spins_out, eloc_out) stay the same.  ms (host, may be NULL) receives
  * the device time of the call.  Synchronises. */
 vmc_status vmc_sample_all(vmc_ctx* ctx, int n_therm, int n_samples, int8_t* spins_out,

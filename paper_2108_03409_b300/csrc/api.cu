@@ -1919,8 +1919,8 @@ static vmc_status batched_upload(vmc_ctx* ctx, int n_therm, int n_samples, int8_
 
 // Autotuner: hidden slots per lane (the per-chain width, or a wider one up to twice it and at
 // most 8, which puts several chains of the smaller lattices in one warp) and warps per block
-// of the persistent launch, timed on one sweep of every chain (chains saved before and
-// restored after; sweep counters untouched).
+// of the persistent launch, timed on one sweep of every chain, the faster of two launches
+// per configuration (chains saved before and restored after each; sweep counters untouched).
 static vmc_status batched_tune(vmc_ctx* ctx) {
   ctx->g_therm = -1;
   const int nl = (int)ctx->lats.size();
@@ -1949,19 +1949,22 @@ static vmc_status batched_tune(vmc_ctx* ctx) {
     const int per_sm = batched_blocks_per_sm(mpl, wpb, ctx->Nmax);
     if (per_sm < 1) continue;
     const int grid = sms * per_sm;
-    CK(cudaEventRecord(ctx->ev[0], ctx->st), "tune");
-    CK(launch_sample_batched(ctx->d_bargs, ctx->d_order, ctx->d_ustart, nl, ctx->Nmax, mpl,
-                             ctx->d_counter, wpb, grid, 0, ctx->d_bargs, ctx->st), "tune");
-    CK(cudaEventRecord(ctx->ev[1], ctx->st), "tune");
-    CK(cudaEventSynchronize(ctx->ev[1]), "tune");
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
-    ctx->launches += 2;
-    if (ms < best) { best = ms; ctx->tuned_wpb = wpb; ctx->tuned_grid = grid; ctx->tuned_mpl = mpl; }
-    off = 0;
-    for (auto& L : ctx->lats) {
-      CK(cudaMemcpyAsync(L.chains, ctx->chain_backup + off, (size_t)C * L.N, cudaMemcpyDeviceToDevice, ctx->st), "tune");
-      off += (size_t)C * L.N;
+    // the faster of two timed launches (the first also pays for the first use of the code)
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(cudaEventRecord(ctx->ev[0], ctx->st), "tune");
+      CK(launch_sample_batched(ctx->d_bargs, ctx->d_order, ctx->d_ustart, nl, ctx->Nmax, mpl,
+                               ctx->d_counter, wpb, grid, 0, ctx->d_bargs, ctx->st), "tune");
+      CK(cudaEventRecord(ctx->ev[1], ctx->st), "tune");
+      CK(cudaEventSynchronize(ctx->ev[1]), "tune");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+      ctx->launches += 2;
+      if (ms < best) { best = ms; ctx->tuned_wpb = wpb; ctx->tuned_grid = grid; ctx->tuned_mpl = mpl; }
+      off = 0;
+      for (auto& L : ctx->lats) {
+        CK(cudaMemcpyAsync(L.chains, ctx->chain_backup + off, (size_t)C * L.N, cudaMemcpyDeviceToDevice, ctx->st), "tune");
+        off += (size_t)C * L.N;
+      }
     }
    }
   }
