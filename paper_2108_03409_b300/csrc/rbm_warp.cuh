@@ -196,53 +196,65 @@ __device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
   return warp_move_ratio_logsum<MPL, G>(R, lane, t, q, si, i, j);
 }
 
-// Local-energy ratios of a whole warp (G = 32) kElocBatch moves at a time: lane m of the
-// warp holds move m (myq, first-site spin mysi, sites myi, myj; myj < 0 for a flip).  Each
-// lane multiplies its own hidden slots' factors for every move (the table rows are read
-// coalesced, as in a proposal), the partial products go through the warp's shared-memory
-// buffer eb, and lane m multiplies move m's 32 partials in lane order: no butterfly per
-// move.  A move whose product leaves [1e-15, 1e15] in modulus takes the warp-wide log-sum
-// path.  Returns coef times this lane's move's ratio (0 for lanes >= nm).
+// Local-energy ratios of a lane group (G lanes, G <= 32), up to eloc_batch(G) moves at a
+// time: group lane m holds move m (myq, first-site spin mysi, sites myi, myj; myj < 0 for a
+// flip).  Each lane multiplies its own hidden slots' factors for every move (the table rows
+// are read coalesced, as in a proposal), the partial products go through the group's part
+// of the warp's shared-memory buffer eb, and lane m multiplies move m's G partials in lane
+// order: no butterfly per move.  A move whose product leaves [1e-15, 1e15] in modulus takes
+// the group-wide log-sum path.  Returns coef times this lane's move's ratio (0 for lanes
+// >= nm).
 static constexpr int kElocBatch = 16;
-static constexpr int kElocLd = 33;                     // row stride (float2), against conflicts
-static constexpr int kElocBufBytes = kElocBatch * kElocLd * (int)sizeof(float2);
+__host__ __device__ constexpr int eloc_batch(int G) { return G < kElocBatch ? G : kElocBatch; }
+// float2 elements of one warp's buffer for groups of G lanes: 32 / G groups, eloc_batch(G)
+// rows of G + 1 (padding against bank conflicts)
+__host__ __device__ constexpr int eloc_buf_elems(int G) { return (32 / G) * eloc_batch(G) * (G + 1); }
+__host__ __device__ constexpr int imax_c(int a, int b) { return a > b ? a : b; }
+static constexpr int kElocBufBytes =
+    8 * imax_c(imax_c(eloc_buf_elems(32), eloc_buf_elems(16)),
+               imax_c(eloc_buf_elems(8), eloc_buf_elems(4)));
 
-template <int MPL>
+template <int MPL, int G>
 __device__ __forceinline__ float2 warp_eloc_batch(const RbmDev& R, int lane,
                                                   const float2 (&t)[MPL], int nm, int myq,
                                                   float mysi, int myi, int myj, float coef,
                                                   float2* eb) {
+  constexpr int LD = G + 1;
+  const int gl = lane & (G - 1);
+  const unsigned gm = group_mask<G>(lane);
+  float2* ebg = eb + (lane / G) * (eloc_batch(G) * LD);
   for (int m = 0; m < nm; ++m) {
-    const int q = __shfl_sync(FULL, myq, m);
-    const float si = __shfl_sync(FULL, mysi, m);
+    const int q = __shfl_sync(gm, myq, m, G);
+    const float si = __shfl_sync(gm, mysi, m, G);
     const float2* row = R.mth + (int64_t)q * R.M;
     float2 prod = make_float2(1.f, 0.f);
 #pragma unroll
     for (int k = 0; k < MPL; ++k) {
-      const int hj = lane + 32 * k;
+      const int hj = gl + G * k;
       if (hj < R.M) prod = cmul(prod, move_factor(t[k], row[hj], si));
     }
-    eb[m * kElocLd + lane] = prod;
+    ebg[m * LD + gl] = prod;
   }
-  __syncwarp();
+  __syncwarp(gm);
   float2 r = make_float2(0.f, 0.f);
   bool ok = true;
-  if (lane < nm) {
-    float2 p = eb[lane * kElocLd];
-    for (int j = 1; j < 32; ++j) p = cmul(p, eb[lane * kElocLd + j]);
+  if (gl < nm) {
+    float2 p = ebg[gl * LD];
+    for (int j = 1; j < G; ++j) p = cmul(p, ebg[gl * LD + j]);
     const float m2 = fmaf(p.x, p.x, p.y * p.y);
     ok = m2 > 1e-30f && m2 < 1e30f;
     if (ok) r = cmul(p, R.mpre[2 * myq + (mysi < 0.f ? 1 : 0)]);
   }
-  __syncwarp();                                         // eb is rewritten by the next batch
-  unsigned fb = __ballot_sync(FULL, !ok);
+  __syncwarp(gm);                                       // ebg is rewritten by the next batch
+  unsigned fb = __ballot_sync(gm, !ok);
+  if (G < 32) fb = (fb >> (lane & ~(G - 1))) & ((1u << (G & 31)) - 1u);
   while (fb) {
     const int m = __ffs(fb) - 1;
     fb &= fb - 1;
-    const float2 rr = warp_move_ratio_logsum<MPL, 32>(
-        R, lane, t, __shfl_sync(FULL, myq, m), __shfl_sync(FULL, mysi, m),
-        __shfl_sync(FULL, myi, m), __shfl_sync(FULL, myj, m));
-    if (lane == m) r = rr;
+    const float2 rr = warp_move_ratio_logsum<MPL, G>(
+        R, lane, t, __shfl_sync(gm, myq, m, G), __shfl_sync(gm, mysi, m, G),
+        __shfl_sync(gm, myi, m, G), __shfl_sync(gm, myj, m, G));
+    if (gl == m) r = rr;
   }
   return make_float2(coef * r.x, coef * r.y);
 }
@@ -254,57 +266,59 @@ __device__ __forceinline__ float2 warp_eloc_batch(const RbmDev& R, int lane,
 template <int MPL, int G = 32>
 __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, int lane,
                             const float2 (&t)[MPL], float2* eb = nullptr) {
-  if constexpr (G == 32) {
-    if (eb) {                     // a whole warp with a ratio buffer: batched ratios
-      float zz = 0.f;
-      float2 acc = make_float2(0.f, 0.f);   // this lane's moves' contributions
-      for (int b0 = 0; b0 < L.nb; b0 += 32) {
-        const int b = b0 + lane;
-        int i = 0, j = 0;
-        bool anti = false;
-        if (b < L.nb) {
-          bond_ends(L.Lx, L.Ly, b, &i, &j);
-          zz += (float)(s[i] * s[j]);
-          anti = s[i] != s[j];
-        }
-        if (L.model != 1) continue;
-        const int ends = i | (j << 16);
-        unsigned mask = __ballot_sync(FULL, anti);
-        while (mask) {                      // J(XX+YY): swap an anti-parallel pair, 2J
-          int nm = 0, myq = 0, myi = 0, myj = 0;
-          float mysi = 0.f;
-          for (; nm < kElocBatch && mask; ++nm) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int pe = __shfl_sync(FULL, ends, src);
-            if (lane == nm) {
-              myq = b0 + src;
-              myi = pe & 0xffff;
-              myj = pe >> 16;
-              mysi = (float)s[myi];
-            }
+  if (eb) {                       // a ratio buffer: the moves' ratios in batches
+    const int gl = lane & (G - 1);
+    const unsigned gm = group_mask<G>(lane);
+    constexpr int B = eloc_batch(G);
+    float zz = 0.f;
+    float2 acc = make_float2(0.f, 0.f);     // this lane's moves' contributions
+    for (int b0 = 0; b0 < L.nb; b0 += G) {
+      const int b = b0 + gl;
+      int i = 0, j = 0;
+      bool anti = false;
+      if (b < L.nb) {
+        bond_ends(L.Lx, L.Ly, b, &i, &j);
+        zz += (float)(s[i] * s[j]);
+        anti = s[i] != s[j];
+      }
+      if (L.model != 1) continue;
+      const int ends = i | (j << 16);
+      unsigned mask = __ballot_sync(gm, anti);
+      if (G < 32) mask = (mask >> (lane & ~(G - 1))) & ((1u << (G & 31)) - 1u);
+      while (mask) {                        // J(XX+YY): swap an anti-parallel pair, 2J
+        int nm = 0, myq = 0, myi = 0, myj = 0;
+        float mysi = 0.f;
+        for (; nm < B && mask; ++nm) {
+          const int src = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const int pe = __shfl_sync(gm, ends, src, G);
+          if (gl == nm) {
+            myq = b0 + src;
+            myi = pe & 0xffff;
+            myj = pe >> 16;
+            mysi = (float)s[myi];
           }
-          const float2 c = warp_eloc_batch<MPL>(R, lane, t, nm, myq, mysi, myi, myj,
-                                                2.f * L.J, eb);
-          acc.x += c.x;
-          acc.y += c.y;
         }
+        const float2 c = warp_eloc_batch<MPL, G>(R, lane, t, nm, myq, mysi, myi, myj,
+                                                 2.f * L.J, eb);
+        acc.x += c.x;
+        acc.y += c.y;
       }
-      if (L.model == 0) {
-        for (int i0 = 0; i0 < R.N; i0 += kElocBatch) {   // -h X_i: flip site i
-          const int nm = min(kElocBatch, R.N - i0);
-          const int myq = i0 + lane;
-          const float mysi = (lane < nm) ? (float)s[myq] : 0.f;
-          const float2 c = warp_eloc_batch<MPL>(R, lane, t, nm, myq, mysi, myq, -1, -L.h, eb);
-          acc.x += c.x;
-          acc.y += c.y;
-        }
-      }
-      float2 e = make_float2(warp_sum(acc.x), warp_sum(acc.y));
-      zz = warp_sum(zz);
-      e.x = fmaf(L.model == 0 ? -L.J : L.J, zz, e.x);
-      return e;
     }
+    if (L.model == 0) {
+      for (int i0 = 0; i0 < R.N; i0 += B) {   // -h X_i: flip site i
+        const int nm = min(B, R.N - i0);
+        const int myq = i0 + gl;
+        const float mysi = (gl < nm) ? (float)s[myq] : 0.f;
+        const float2 c = warp_eloc_batch<MPL, G>(R, lane, t, nm, myq, mysi, myq, -1, -L.h, eb);
+        acc.x += c.x;
+        acc.y += c.y;
+      }
+    }
+    float2 e = make_float2(group_sum<G>(acc.x, gm), group_sum<G>(acc.y, gm));
+    zz = group_sum<G>(zz, gm);
+    e.x = fmaf(L.model == 0 ? -L.J : L.J, zz, e.x);
+    return e;
   }
   const int gl = lane & (G - 1);
   const unsigned gm = group_mask<G>(lane);

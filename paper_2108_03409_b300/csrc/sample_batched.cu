@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(256, MPL <= 4 ? 4 : MPL <= 8 ? 3 : 2)
   extern __shared__ int8_t sm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int8_t* sw = sm + wib * kMaxChainsPerWarp * npad_max;
-  // the warp's local-energy ratio buffer, after all warps' spin buffers (whole-warp chains)
+  // the warp's local-energy ratio buffer (shared by its lane groups), after all warps' spin
+  // buffers
   float2* eb = reinterpret_cast<float2*>(sm + (blockDim.x >> 5) * kMaxChainsPerWarp * npad_max +
                                          wib * kElocBufBytes);
   const unsigned total = (unsigned)ustart[n_lat];
@@ -52,9 +53,9 @@ __global__ void __launch_bounds__(256, MPL <= 4 ? 4 : MPL <= 8 ? 3 : 2)
       int8_t* s = sw + gi * npad_max;
       if constexpr (MPL <= 8) {
         switch (G) {
-          case 4: run_group<MPL, 4>(A, chain, s, lane, nullptr); break;
-          case 8: run_group<MPL, 8>(A, chain, s, lane, nullptr); break;
-          case 16: run_group<MPL, 16>(A, chain, s, lane, nullptr); break;
+          case 4: run_group<MPL, 4>(A, chain, s, lane, eb); break;
+          case 8: run_group<MPL, 8>(A, chain, s, lane, eb); break;
+          case 16: run_group<MPL, 16>(A, chain, s, lane, eb); break;
           default: run_group<MPL, 32>(A, chain, s, lane, eb); break;
         }
       } else {
