@@ -164,11 +164,8 @@ __device__ __forceinline__ float2 warp_factor_prod(const RbmDev& R, int lane,
 }
 
 // psi(s')/psi(s) for move q (a flip of site i, j < 0, or the exchange on bond (i, j)) with
-// first-site spin si: the factor product times the tabulated exp(sum_k log cosh D_qk - da),
-// da = 2 si (a_i - a_j) or 2 si a_i.  The product is used while its squared modulus stays in
-// [1e-30, 1e30] (every lane of the group holds the same product, so the branch is
-// group-uniform); otherwise the ratio is formed from the log-sum of the factors, which has
-// no range limit.
+// first-site spin si from the log-sum of its factors (group-wide): exp(sum_k log(1 - si t_k
+// tanh D_qk) + sum_k log cosh D_qk - da), da = 2 si (a_i - a_j) or 2 si a_i.  No range limit.
 template <int MPL, int G = 32>
 __device__ __forceinline__ float2 warp_move_ratio_logsum(const RbmDev& R, int lane,
                                                          const float2 (&t)[MPL], int q,
@@ -186,6 +183,9 @@ __device__ __forceinline__ float2 warp_move_ratio_logsum(const RbmDev& R, int la
   return make_float2(mag * cs, mag * sn);
 }
 
+// The same ratio as the factor product times the tabulated exp(sum_k log cosh D_qk - da),
+// used while the product's squared modulus stays in [1e-30, 1e30] (every lane of the group
+// holds the same product, so the branch is group-uniform); otherwise the log-sum form.
 template <int MPL, int G = 32>
 __device__ __forceinline__ float2 warp_move_ratio(const RbmDev& R, int lane,
                                                   const float2 (&t)[MPL], int q, float si,
@@ -260,9 +260,11 @@ __device__ __forceinline__ float2 warp_eloc_batch(const RbmDev& R, int lane,
 }
 
 // E_loc(s) = sum_s' H_ss' psi(s')/psi(s) from the cached t = tanh theta(s) (Eq. Oloc).
-// The bonds are taken 32 at a time, one per lane: each lane finds its bond's sites and
-// adds s_i s_j to the diagonal part; for the Heisenberg model a ballot then walks only the
-// anti-parallel bonds, whose sites come from their lane by a shuffle.
+// The bonds are taken G at a time, one per lane of the chain's group: each lane finds its
+// bond's sites and adds s_i s_j to the diagonal part; for the Heisenberg model a ballot then
+// walks only the anti-parallel bonds, whose sites come from their lane by a shuffle.  With a
+// ratio buffer eb the moves' ratios are formed in batches (warp_eloc_batch); without one,
+// one at a time across the group (warp_move_ratio).
 template <int MPL, int G = 32>
 __device__ float2 warp_eloc(const RbmDev& R, const LatDev& L, const int8_t* s, int lane,
                             const float2 (&t)[MPL], float2* eb = nullptr) {
